@@ -13,6 +13,10 @@ Sec. 16.6, predictor-corrector for inequality-constrained QPs):
       (P + G^T diag(lam/s) G) dz + E^T dnu = r,  E dz = -r_e,
     by a dense Cholesky of H = P + G^T D G and of the Schur complement
     E H^-1 E^T;
+    when that Cholesky breaks down (H numerically singular as lam/s grows on
+    the active rows near a vertex), the same Newton step is taken from the
+    equivalent augmented system [[P, E^T, G^T], [E, 0, 0], [G, 0, -S/Lam]]
+    by an LU factorisation instead;
   * affine predictor, centring sigma = (mu_aff/mu)^3, corrector;
   * step to 0.99 of the boundary.
 Stops when mu <= tol_mu and the scaled residuals are <= tol_res.
@@ -80,6 +84,12 @@ def solve_qp(P, q, E, e, C, lo, hi, *, tol_mu=1e-13, tol_res=1e-11, max_iter=200
         dlam = (rc - lam * ds) / s
         return dz, dnu, ds, dlam
 
+    def newton_aug(rd, re, ri, rc, lu):
+        sol = sla.lu_solve(lu, np.concatenate([-rd, -re, -ri - rc / lam]))
+        dz, dnu, dlam = sol[:n], sol[n:n + p], sol[n + p:]
+        ds = (rc - s * dlam) / lam
+        return dz, dnu, ds, dlam
+
     def max_step(v, dv):
         neg = dv < 0
         if not neg.any():
@@ -100,17 +110,29 @@ def solve_qp(P, q, E, e, C, lo, hi, *, tol_mu=1e-13, tol_res=1e-11, max_iter=200
             break
         D = lam / s
         H = P + G.T @ (D[:, None] * G)
-        chol = sla.cho_factor(H, lower=True, check_finite=False)
-        Hinv_EaT = sla.cho_solve(chol, Ea.T)
-        Schol = sla.cho_factor(Ea @ Hinv_EaT, lower=True, check_finite=False)
+        try:
+            chol = sla.cho_factor(H, lower=True, check_finite=False)
+            Hinv_EaT = sla.cho_solve(chol, Ea.T)
+            Schol = sla.cho_factor(Ea @ Hinv_EaT, lower=True, check_finite=False)
+
+            def step(rc):
+                return newton(rd, re, ri, rc, chol, Hinv_EaT, Schol)
+        except np.linalg.LinAlgError:
+            K = np.block([[P, Ea.T, G.T],
+                          [Ea, np.zeros((p, p)), np.zeros((p, m))],
+                          [G, np.zeros((m, p)), -np.diag(s / lam)]])
+            lu = sla.lu_factor(K, check_finite=False)
+
+            def step(rc):
+                return newton_aug(rd, re, ri, rc, lu)
         # predictor
-        dz_a, _, ds_a, dl_a = newton(rd, re, ri, -s * lam, chol, Hinv_EaT, Schol)
+        dz_a, _, ds_a, dl_a = step(-s * lam)
         a_aff = min(max_step(s, ds_a), max_step(lam, dl_a))
         mu_aff = float((s + a_aff * ds_a) @ (lam + a_aff * dl_a)) / max(m, 1)
         sigma = (mu_aff / mu) ** 3 if mu > 0 else 0.0
         # corrector
         rc = -s * lam - ds_a * dl_a + sigma * mu
-        dz, dnu, ds, dl = newton(rd, re, ri, rc, chol, Hinv_EaT, Schol)
+        dz, dnu, ds, dl = step(rc)
         a = min(0.99 * min(max_step(s, ds), max_step(lam, dl)), 1.0)
         z = z + a * dz
         nu = nu + a * dnu
