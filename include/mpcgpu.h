@@ -1,0 +1,208 @@
+/*
+ * mpcgpu.h - C ABI of the batched kinodynamic-MPC solver (B300, sm_103a).
+ *
+ * One call of the library replans many independent humanoid agents at once:
+ * for each agent it forms the horizon QP of the paper's kinodynamic MPC
+ * (Sec. III-A, Eq. (mpc_formulation); desired trajectory Eqs. (des_traj_1)-
+ * (des_traj_5); contact schedule of Sec. III-A), linearised about the
+ * agent's current state (real-time iteration, Sec. III-B), solves it with
+ * OSQP-style ADMM (Sec. III-B, Eq. (kkt_system); the KKT solve is done by a
+ * per-stage Riccati recursion instead of a sparse LDL, Eqs. (ldl),
+ * (backsolve_1)-(backsolve_2)), and maps the first-stage solution to joint
+ * torques (Sec. III-C, Eqs. (rnea), (mpc_torque)); Alg. 1 is the whole path.
+ *
+ * Conventions used by every entry point:
+ *   - Pointers are DEVICE pointers unless the argument name ends in _host.
+ *   - The caller owns every buffer it passes; the library never frees one.
+ *     The library owns its device arenas (models, warm starts, factor
+ *     caches, scratch), allocated in mpc_create and freed in mpc_destroy.
+ *   - Work is enqueued on the context's stream (mpc_config.stream); results
+ *     are valid once that stream has reached the point after the call.
+ *   - Errors are return codes; nothing throws or aborts across the ABI.
+ *     mpc_last_error() gives a one-line description of the last failure.
+ *   - One host thread per context.
+ *
+ * Per-agent layouts (float32, row-major, agent-major):
+ *   x0[n][30]      state: p(3), Theta = (roll, pitch, yaw)(3), v(3) world,
+ *                  w(3) world, q(18): joints 0-4 left leg, 5-9 right leg,
+ *                  10-17 arms
+ *   qd_meas[n][18] measured joint velocities (the K_d term of Eq. mpc_torque)
+ *   cmd[n][4]      command (c_h, c_vx, c_vy, c_wz) of Eqs. (des_traj_*)
+ *   phase[n]       gait phase in [0, 1)
+ *   tau[n][18], q_set[n][18], qd_set[n][18], value[n], agent_status[n]
+ */
+#ifndef MPCGPU_H
+#define MPCGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MPC_NX 30    /* state size */
+#define MPC_NU 30    /* input size: f_L(3) m_L(3) f_R(3) m_R(3) qdot(18) */
+#define MPC_NJ 18    /* joints */
+#define MPC_NROW 56  /* inequality rows per stage */
+#define MPC_MAX_HORIZON 32
+
+typedef enum {
+  MPC_OK = 0,
+  MPC_ERR_INVALID = 1,   /* bad argument, unknown agent, unsupported option */
+  MPC_ERR_BUDGET = 2,    /* arenas would exceed hbm_budget_bytes */
+  MPC_ERR_CUDA = 3,      /* a CUDA runtime call failed */
+  MPC_ERR_NOT_READY = 4, /* ticket not solved yet / unknown ticket */
+  MPC_ERR_TIMEOUT = 5,   /* a bounded device wait gave up */
+  MPC_ERR_STATE = 6      /* call out of order (e.g. solve before submit) */
+} mpc_status;
+
+typedef enum {
+  MPC_AGENT_SOLVED = 0,        /* ADMM met its tolerances */
+  MPC_AGENT_MAX_ITER = 1,      /* iteration cap reached (or fixed-N_QP mode) */
+  MPC_AGENT_PRIMAL_INFEAS = 2,
+  MPC_AGENT_DUAL_INFEAS = 3,
+  MPC_AGENT_NAN = 4            /* non-finite input or iterate; outputs zeroed */
+} mpc_agent_status;
+
+typedef enum { MPC_FP32 = 0, MPC_TF32 = 1, MPC_BF16 = 2, MPC_FP64 = 3 } mpc_precision;
+
+typedef enum { MPC_FORM_PLAIN = 0, MPC_FORM_FUSED = 1 } mpc_form;
+
+typedef enum {
+  MPC_GAIT_WALK = 0, MPC_GAIT_STAND = 1, MPC_GAIT_HOP = 2,
+  MPC_GAIT_SINGLE_L = 3, MPC_GAIT_SINGLE_R = 4
+} mpc_gait;
+
+/* Solver and context options.  mpc_default_config() fills the defaults:
+ * rho0 0.1, sigma 1e-6, alpha 1.6, eps_abs = eps_rel = 1e-5, max_iter 4000,
+ * fixed_iters 0, check_every 10, adaptive_rho 1, polish 1, form FUSED,
+ * precision FP32, max_horizon 20.  OSQP's parameters (Stellato et al. 2020,
+ * Sec. 3.2, to which the paper defers after Eq. (backsolve_2)). */
+typedef struct mpc_config {
+  int device;                 /* CUDA device ordinal */
+  void* stream;               /* cudaStream_t; NULL = the legacy default stream */
+  int max_agents;             /* agent ids are 0 .. max_agents-1 */
+  int max_horizon;            /* largest N any agent may use (<= MPC_MAX_HORIZON) */
+  size_t hbm_budget_bytes;    /* cap on all device arenas; 0 = no cap */
+  int precision;              /* mpc_precision; only MPC_FP32 is implemented */
+  int form;                   /* mpc_form: separate step kernels or one fused kernel */
+  float rho0, sigma, alpha;   /* ADMM step size, proximal weight, relaxation */
+  float eps_abs, eps_rel;     /* OSQP-style stopping tolerances */
+  int max_iter;               /* iteration cap */
+  int fixed_iters;            /* >0: run exactly this many iterations (paper's N_QP) */
+  int check_every;            /* residual / rho check period */
+  int adaptive_rho;           /* OSQP rho update (refactor when off by 5x) */
+  int polish;                 /* OSQP-style active-set polish after ADMM */
+  int warm_start;             /* start from the agent's previous solution */
+} mpc_config;
+
+/* One agent's model (host memory, float64; stored as float32 on the device,
+ * except the schedule fields dt, period, duty, offset, which stay float64 so
+ * that stance/swing decisions are taken in double precision). */
+typedef struct mpc_agent_model {
+  double mass;              /* kg */
+  double inertia[3];        /* body-frame principal inertia, kg m^2 */
+  double lever[2][3];       /* nominal foot lever arms from the CoM, m */
+  double J_leg[2][6][5];    /* per foot: wrench rows (f 0-2, m 3-5) x 5 leg joints */
+  double M_j[18];           /* joint inertia (diagonal joint-space model) */
+  double h_j[18];           /* joint bias torque */
+  double Kp[18], Kd[18];    /* PD gains of Eq. (mpc_torque) */
+  double Q[30], R[30];      /* diagonal cost weights of Eq. (mpc_formulation) */
+  double mu, fz_max, qd_max, q_lim;
+  int N;                    /* horizon (2 .. max_horizon) */
+  double dt;                /* node spacing, s */
+  int gait;                 /* mpc_gait (informational; duty/offset define it) */
+  double period;            /* gait period, s */
+  double duty[2];           /* stance fraction per foot (1 = always stance) */
+  double offset[2];         /* phase offset per foot */
+  double q_nom[18];         /* nominal joint angles */
+} mpc_agent_model;
+
+typedef struct mpc_ctx mpc_ctx;
+
+/* Fill *cfg with the defaults above (device 0, NULL stream, max_agents 16384). */
+mpc_status mpc_default_config(mpc_config* cfg);
+
+/* Create a context: allocates every device arena for cfg->max_agents agents
+ * of horizon up to cfg->max_horizon.  MPC_ERR_BUDGET if that exceeds
+ * cfg->hbm_budget_bytes (non-zero).  *out is NULL on failure. */
+mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out);
+
+/* Free everything the context owns (synchronises its stream first). */
+mpc_status mpc_destroy(mpc_ctx* ctx);
+
+/* Admit or update agents: copies n host models (models_host[n]) into the
+ * device model arena at agent_ids_host[n] and clears their warm starts.
+ * Synchronous with respect to the host buffers. */
+mpc_status mpc_set_models(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host,
+                          const mpc_agent_model* models_host);
+
+/* Single-agent form of mpc_set_models. */
+mpc_status mpc_set_model(mpc_ctx* ctx, int32_t agent_id, const mpc_agent_model* model_host);
+
+/* Remove an agent: its slot no longer accepts submissions. */
+mpc_status mpc_release_agent(mpc_ctx* ctx, int32_t agent_id);
+
+/* Register one replan batch of n agents (device buffers, layouts above).
+ * Nothing runs yet; the buffers must stay valid until mpc_solve has been
+ * enqueued.  *ticket identifies the batch.  At most 64 tickets are pending. */
+mpc_status mpc_submit(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids,
+                      const float* x0, const float* qd_meas, const float* cmd,
+                      const float* phase, uint64_t* ticket);
+
+/* Enqueue the whole hot path (Alg. 1) for the ticket's agents on the stream:
+ * schedule/references/bounds, linearisation, assembly, Riccati factor, ADMM
+ * iterations with residual checks and rho updates, polish, torque map, and
+ * the write-back of each agent's warm start. */
+mpc_status mpc_solve(mpc_ctx* ctx, uint64_t ticket);
+
+/* Enqueue a gather of the ticket's results into caller buffers (any may be
+ * NULL): tau, q_set, qd_set [n][18], value[n] = QP objective at the
+ * solution, agent_status[n] (mpc_agent_status; -1 and zero outputs for a
+ * batch row whose id is out of range or not admitted, which the solve
+ * skipped).  Releases the ticket. */
+mpc_status mpc_get_torques(mpc_ctx* ctx, uint64_t ticket, float* tau, float* q_set,
+                           float* qd_set, float* value, int32_t* agent_status);
+
+/* Host-buffer convenience (the end-to-end path): copies the inputs from host
+ * memory, submits, solves, gathers and copies the results back, then
+ * synchronises the stream.  Output pointers may be NULL. */
+mpc_status mpc_solve_host(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host,
+                          const float* x0_host, const float* qd_meas_host,
+                          const float* cmd_host, const float* phase_host,
+                          float* tau_host, float* q_set_host, float* qd_set_host,
+                          float* value_host, int32_t* agent_status_host);
+
+/* Per-agent solver statistics of the last solve of each agent, copied to
+ * host arrays (any may be NULL): ADMM iterations, refactorisations, polish
+ * accepted (0/1), final unscaled primal and dual residuals (inf-norms).
+ * Synchronises the stream. */
+mpc_status mpc_get_agent_stats(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host,
+                               int32_t* iters_host, int32_t* refactors_host,
+                               int32_t* polished_host, float* prim_res_host,
+                               float* dual_res_host);
+
+/* Checkpoint / inspection of one agent's solver state (host buffers):
+ * x[(N+1)][30], u[N][30] = last primal solution (after polish, if accepted),
+ * w[N][56] = projected constraint values, y[N][56] = row multipliers,
+ * rho.  Synchronises the stream. */
+mpc_status mpc_export_state(mpc_ctx* ctx, int32_t agent_id, float* x_host, float* u_host,
+                            float* w_host, float* y_host, float* rho_host);
+
+/* Restore a state written by mpc_export_state (sets the warm start). */
+mpc_status mpc_import_state(mpc_ctx* ctx, int32_t agent_id, const float* x_host,
+                            const float* u_host, const float* w_host, const float* y_host,
+                            float rho);
+
+/* JSON summary of the context (sizes, arenas, counters) into buf. */
+mpc_status mpc_get_stats(mpc_ctx* ctx, char* buf, size_t cap);
+
+/* One-line description of the last error on this context (never NULL). */
+const char* mpc_last_error(mpc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MPCGPU_H */

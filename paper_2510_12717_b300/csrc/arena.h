@@ -1,0 +1,99 @@
+// Device-side data layout of the batched MPC solver.
+//
+// Every per-agent array lives in an arena indexed by the agent's slot
+// (agent id).  Strides are fixed by the context's max_horizon (maxN).
+//
+// Index conventions (paper Sec. III-A, state and input of Eq. mpc_formulation
+// in the centroidal reading):
+//   x = [p 0-2, Theta 3-5, v 6-8, w 9-11, q 12-29]
+//   u = [f_L 0-2, m_L 3-5, f_R 6-8, m_R 9-11, qdot 12-29]
+// Indices 0-21 of x and u form the coupled block (base + leg joints): its
+// stage matrices are dense 22x22.  Indices 22-29 are the eight arm joints,
+// which decouple into scalar problems q+ = q + dt qdot.  Lane i of the warp
+// that owns an agent handles index i of both x and u.
+#pragma once
+#include <stdint.h>
+
+namespace mpc {
+
+constexpr int NX = 30;
+constexpr int NC = 22;      // coupled block size
+constexpr int LD = 23;      // column stride of a 22x22 block (odd: no bank conflicts)
+constexpr int MB = 512;     // floats reserved per 22x22 block (22*23 = 506 used)
+constexpr int NA = 8;       // arm joints
+constexpr int NR = 56;      // inequality rows per stage
+constexpr int RS = 64;      // stride of per-stage row arrays
+constexpr int VS = 32;      // stride of per-stage lane vectors
+constexpr int MAXN = 32;
+
+// float model record (MODEL_F floats per agent)
+enum : int {
+  M_MASS = 0, M_INVM = 1, M_INERTIA = 2, M_LEVER = 5, M_JLEG = 11,   // J_leg[f][r][j] at 11 + 30f + 5r + j
+  M_MJ = 71, M_HJ = 89, M_KP = 107, M_KD = 125, M_Q = 143, M_R = 173,
+  M_MU = 203, M_FZMAX = 204, M_QDMAX = 205, M_QLIM = 206, M_DT = 207,
+  M_QNOM = 208, MODEL_F = 256
+};
+// double schedule record (SCHED_D doubles per agent)
+enum : int { S_DT = 0, S_PERIOD = 1, S_DUTY = 2, S_OFF = 4, SCHED_D = 8 };
+// per-agent input record (IN_F floats): x0, qd_meas, cmd, phase
+enum : int { I_X0 = 0, I_QD = 32, I_CMD = 50, I_PHASE = 54, IN_F = 64 };
+// per-agent output record (OUT_F floats)
+enum : int { O_TAU = 0, O_QSET = 18, O_QDSET = 36, O_V = 54, O_PRIM = 55, O_DUAL = 56, OUT_F = 64 };
+// per-agent integer record (ST_I ints)
+enum : int { T_STATUS = 0, T_ITERS = 1, T_REFAC = 2, T_POLISHED = 3, T_N = 4, ST_I = 8 };
+
+struct Arena {
+  int max_agents;
+  int maxN;
+  // model
+  const float* model;     // [A][MODEL_F]
+  const double* sched;    // [A][SCHED_D]
+  const int* horizon;     // [A]
+  // warm-start / solution state
+  float* xs;              // [A][(maxN+1)*VS]   x_k, lane-indexed
+  float* us;              // [A][maxN*VS]
+  float* ws;              // [A][maxN*RS]
+  float* ys;              // [A][maxN*RS]
+  float* rho;             // [A]
+  int* warm_valid;        // [A] horizon the warm start was written with (0 = none)
+  // outputs
+  float* out;             // [A][OUT_F]
+  int* stat;              // [A][ST_I]
+  // scratch (solver workspace; contents meaningful only during a solve)
+  float* inp;             // [A][IN_F]
+  float* xref;            // [A][(maxN+1)*VS]
+  float* uref;            // [A][maxN*VS]
+  float* rlo;             // [A][maxN*RS] row lower bounds
+  float* rhi;             // [A][maxN*RS]
+  float* rcls;            // [A][maxN*RS] rho multiplier per row: 0 free, 1 ineq, 1e3 eq
+  float* lin;             // [A][LIN_F]  A_base, B, per-stage dA (3x10) and c
+  float* cK;              // [A][maxN*MB] Riccati gains K_k
+  float* cH;              // [A][maxN*MB] inverse Schur blocks H_uu^-1
+  float* cE;              // [A][maxN*64] e_k = P_{k+1} c_k (lanes 0-21), arm gain (22-29),
+                          //   arm e (32-39), arm H_uu^-1 (54-61)
+  float* cB;              // [A][maxN*MB] polish: per-stage reduced B
+  float* cC;              // [A][maxN*64] polish: reduced c (0-29), reduced linear cost (32-61)
+  float* xt;              // [A][(maxN+1)*VS] KKT-solve primal (x tilde)
+  float* ut;              // [A][maxN*VS]
+  float* dv;              // [A][maxN*VS]    feed-forward terms d_k
+};
+
+// lin record layout
+__host__ __device__ inline int lin_floats(int maxN) { return 2 * MB + maxN * (2 * VS); }
+enum : int { L_ABASE = 0, L_B = MB, L_STAGE = 2 * MB };   // stage k: dA at L_STAGE + k*64 (30 used), c at +32
+
+struct Batch {
+  int n;
+  const int* ids;         // [n] agent slot per batch row
+  const float* x0;        // [n][30]
+  const float* qd;        // [n][18]
+  const float* cmd;       // [n][4]
+  const float* phase;     // [n]
+};
+
+struct SolverParams {
+  float rho0, sigma, alpha, eps_abs, eps_rel;
+  int max_iter, fixed_iters, check_every, adaptive_rho, polish, warm_start;
+};
+
+}  // namespace mpc

@@ -1,0 +1,533 @@
+// C ABI of the batched MPC solver: context, device arenas, tickets.
+// Declarations and argument conventions: include/mpcgpu.h.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <string>
+#include <vector>
+
+#include "mpcgpu.h"
+#include "solver.h"
+
+using mpc::Arena;
+
+namespace {
+
+constexpr int kMaxTickets = 64;
+
+struct Ticket {
+  uint64_t id = 0;
+  int state = 0;   // 0 free, 1 submitted, 2 solved
+  mpc::Batch b{};
+};
+
+}  // namespace
+
+struct mpc_ctx {
+  mpc_config cfg{};
+  cudaStream_t stream = nullptr;
+  Arena ar{};
+  // non-const views of the model arenas
+  float* model = nullptr;
+  double* sched = nullptr;
+  int* horizon = nullptr;
+  std::vector<void*> allocs;
+  size_t bytes = 0;
+  std::vector<int> live;            // host copy: horizon of live slots, 0 = free
+  Ticket tickets[kMaxTickets];
+  uint64_t next_ticket = 1;
+  // staging for the host-buffer path and model uploads
+  int* d_ids = nullptr;
+  float *d_x0 = nullptr, *d_qd = nullptr, *d_cmd = nullptr, *d_phase = nullptr;
+  float *d_tau = nullptr, *d_qset = nullptr, *d_qdset = nullptr, *d_val = nullptr;
+  int* d_status = nullptr;
+  float* d_mstage = nullptr;
+  double* d_sstage = nullptr;
+  int* d_hstage = nullptr;
+  long long launches = 0;
+  long long solves = 0;
+  std::string err = "ok";
+};
+
+static mpc_status fail(mpc_ctx* c, mpc_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+static mpc_status cuda_fail(mpc_ctx* c, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  return fail(c, MPC_ERR_CUDA, m);
+}
+
+#define CK(call)                                              \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);  \
+  } while (0)
+
+template <class T>
+static cudaError_t alloc(mpc_ctx* ctx, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+  if (e != cudaSuccess) return e;
+  ctx->allocs.push_back(q);
+  ctx->bytes += count * sizeof(T);
+  *p = static_cast<T*>(q);
+  return cudaMemset(q, 0, count * sizeof(T));
+}
+
+// bytes of all arenas for A agents of horizon up to n
+static size_t arena_bytes(size_t A, size_t n) {
+  using namespace mpc;
+  size_t f = 0;
+  f += A * MODEL_F;                                  // model
+  f += A * SCHED_D * 2;                              // sched (doubles)
+  f += A;                                            // horizon
+  f += A * ((n + 1) * VS + n * VS + 2 * n * RS + 1); // xs us ws ys rho
+  f += A;                                            // warm
+  f += A * (OUT_F + ST_I);                           // out, stat
+  f += A * IN_F;
+  f += A * ((n + 1) * VS + n * VS + 3 * n * RS);     // xref uref rlo rhi rcls
+  f += A * lin_floats((int)n);
+  f += A * (3 * n * MB + 2 * n * 64);                // cK cH cB cE cC
+  f += A * ((n + 1) * VS + 2 * n * VS);              // xt ut dv
+  f += A * (1 + 30 + 18 + 4 + 1 + 18 * 3 + 2);       // host-path staging
+  f += A * (MODEL_F + 2 * SCHED_D + 1);              // model upload staging
+  return f * 4;
+}
+
+extern "C" {
+
+mpc_status mpc_default_config(mpc_config* cfg) {
+  if (!cfg) return MPC_ERR_INVALID;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->stream = nullptr;
+  cfg->max_agents = 16384;
+  cfg->max_horizon = 20;
+  cfg->hbm_budget_bytes = 0;
+  cfg->precision = MPC_FP32;
+  cfg->form = MPC_FORM_FUSED;
+  cfg->rho0 = 0.1f;
+  cfg->sigma = 1e-6f;
+  cfg->alpha = 1.6f;
+  cfg->eps_abs = 1e-5f;
+  cfg->eps_rel = 1e-5f;
+  cfg->max_iter = 4000;
+  cfg->fixed_iters = 0;
+  cfg->check_every = 10;
+  cfg->adaptive_rho = 1;
+  cfg->polish = 1;
+  cfg->warm_start = 1;
+  return MPC_OK;
+}
+
+mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
+  if (!out) return MPC_ERR_INVALID;
+  *out = nullptr;
+  if (!cfg) return MPC_ERR_INVALID;
+  if (cfg->max_agents <= 0 || cfg->max_horizon < 2 || cfg->max_horizon > MPC_MAX_HORIZON)
+    return MPC_ERR_INVALID;
+  if (cfg->precision != MPC_FP32) return MPC_ERR_INVALID;
+  if (cfg->form != MPC_FORM_PLAIN && cfg->form != MPC_FORM_FUSED) return MPC_ERR_INVALID;
+  if (!(cfg->rho0 > 0.f) || !(cfg->sigma > 0.f) || !(cfg->alpha > 0.f && cfg->alpha < 2.f) ||
+      !(cfg->eps_abs >= 0.f) || !(cfg->eps_rel >= 0.f) || cfg->max_iter <= 0 || cfg->fixed_iters < 0 ||
+      cfg->check_every <= 0)
+    return MPC_ERR_INVALID;
+  const size_t A = (size_t)cfg->max_agents, n = (size_t)cfg->max_horizon;
+  if (cfg->hbm_budget_bytes && arena_bytes(A, n) > cfg->hbm_budget_bytes) return MPC_ERR_BUDGET;
+
+  mpc_ctx* ctx = new mpc_ctx();
+  ctx->cfg = *cfg;
+  ctx->stream = static_cast<cudaStream_t>(cfg->stream);
+  ctx->live.assign(A, 0);
+  auto bail = [&](mpc_status s) {
+    for (void* p : ctx->allocs) cudaFree(p);
+    delete ctx;
+    return s;
+  };
+  if (cudaSetDevice(cfg->device) != cudaSuccess) return bail(MPC_ERR_CUDA);
+  Arena& a = ctx->ar;
+  a.max_agents = (int)A;
+  a.maxN = (int)n;
+  using namespace mpc;
+  cudaError_t e = cudaSuccess;
+#define AL(ptr, cnt) if (e == cudaSuccess) e = alloc(ctx, &(ptr), (cnt))
+  AL(ctx->model, A * MODEL_F);
+  AL(ctx->sched, A * SCHED_D);
+  AL(ctx->horizon, A);
+  AL(a.xs, A * (n + 1) * VS);
+  AL(a.us, A * n * VS);
+  AL(a.ws, A * n * RS);
+  AL(a.ys, A * n * RS);
+  AL(a.rho, A);
+  AL(a.warm_valid, A);
+  AL(a.out, A * OUT_F);
+  AL(a.stat, A * ST_I);
+  AL(a.inp, A * IN_F);
+  AL(a.xref, A * (n + 1) * VS);
+  AL(a.uref, A * n * VS);
+  AL(a.rlo, A * n * RS);
+  AL(a.rhi, A * n * RS);
+  AL(a.rcls, A * n * RS);
+  AL(a.lin, A * (size_t)lin_floats((int)n));
+  AL(a.cK, A * n * MB);
+  AL(a.cH, A * n * MB);
+  AL(a.cE, A * n * 64);
+  AL(a.cB, A * n * MB);
+  AL(a.cC, A * n * 64);
+  AL(a.xt, A * (n + 1) * VS);
+  AL(a.ut, A * n * VS);
+  AL(a.dv, A * n * VS);
+  AL(ctx->d_ids, A);
+  AL(ctx->d_x0, A * 30);
+  AL(ctx->d_qd, A * 18);
+  AL(ctx->d_cmd, A * 4);
+  AL(ctx->d_phase, A);
+  AL(ctx->d_tau, A * 18);
+  AL(ctx->d_qset, A * 18);
+  AL(ctx->d_qdset, A * 18);
+  AL(ctx->d_val, A);
+  AL(ctx->d_status, A);
+  AL(ctx->d_mstage, A * MODEL_F);
+  AL(ctx->d_sstage, A * SCHED_D);
+  AL(ctx->d_hstage, A);
+#undef AL
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return bail(e == cudaErrorMemoryAllocation ? MPC_ERR_BUDGET : MPC_ERR_CUDA);
+  }
+  if (cfg->hbm_budget_bytes && ctx->bytes > cfg->hbm_budget_bytes) return bail(MPC_ERR_BUDGET);
+  a.model = ctx->model;
+  a.sched = ctx->sched;
+  a.horizon = ctx->horizon;
+  *out = ctx;
+  return MPC_OK;
+}
+
+mpc_status mpc_destroy(mpc_ctx* ctx) {
+  if (!ctx) return MPC_ERR_INVALID;
+  cudaSetDevice(ctx->cfg.device);
+  cudaStreamSynchronize(ctx->stream);
+  for (void* p : ctx->allocs) cudaFree(p);
+  delete ctx;
+  return MPC_OK;
+}
+
+static bool finite_all(const double* v, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!isfinite(v[i])) return false;
+  return true;
+}
+
+static const char* check_model(const mpc_agent_model& m, int maxN) {
+  if (m.N < 2 || m.N > maxN) return "horizon N outside [2, max_horizon]";
+  if (!(m.dt > 0) || !(m.period > 0) || !isfinite(m.dt) || !isfinite(m.period)) return "dt and period must be > 0";
+  if (!(m.mass > 0)) return "mass must be > 0";
+  for (int i = 0; i < 3; ++i) if (!(m.inertia[i] > 0)) return "inertia must be > 0";
+  for (int i = 0; i < 30; ++i) {
+    if (!(m.R[i] > 0) || !isfinite(m.R[i])) return "R must be > 0 (strictly convex QP)";
+    if (!(m.Q[i] >= 0) || !isfinite(m.Q[i])) return "Q must be >= 0";
+  }
+  if (!(m.mu > 0) || !(m.fz_max > 0) || !(m.qd_max > 0) || !(m.q_lim > 0)) return "bounds must be > 0";
+  if (!finite_all(&m.lever[0][0], 6) || !finite_all(&m.J_leg[0][0][0], 60) || !finite_all(m.M_j, 18) ||
+      !finite_all(m.h_j, 18) || !finite_all(m.Kp, 18) || !finite_all(m.Kd, 18) || !finite_all(m.q_nom, 18) ||
+      !finite_all(m.duty, 2) || !finite_all(m.offset, 2))
+    return "non-finite model entry";
+  return nullptr;
+}
+
+static void pack_model(const mpc_agent_model& m, float* f, double* s) {
+  using namespace mpc;
+  memset(f, 0, sizeof(float) * MODEL_F);
+  f[M_MASS] = (float)m.mass;
+  f[M_INVM] = (float)(1.0 / m.mass);
+  for (int i = 0; i < 3; ++i) f[M_INERTIA + i] = (float)m.inertia[i];
+  for (int i = 0; i < 2; ++i)
+    for (int c = 0; c < 3; ++c) f[M_LEVER + 3 * i + c] = (float)m.lever[i][c];
+  for (int i = 0; i < 2; ++i)
+    for (int r = 0; r < 6; ++r)
+      for (int j = 0; j < 5; ++j) f[M_JLEG + 30 * i + 5 * r + j] = (float)m.J_leg[i][r][j];
+  for (int j = 0; j < 18; ++j) {
+    f[M_MJ + j] = (float)m.M_j[j];
+    f[M_HJ + j] = (float)m.h_j[j];
+    f[M_KP + j] = (float)m.Kp[j];
+    f[M_KD + j] = (float)m.Kd[j];
+    f[M_QNOM + j] = (float)m.q_nom[j];
+  }
+  for (int i = 0; i < 30; ++i) {
+    f[M_Q + i] = (float)m.Q[i];
+    f[M_R + i] = (float)m.R[i];
+  }
+  f[M_MU] = (float)m.mu;
+  f[M_FZMAX] = (float)m.fz_max;
+  f[M_QDMAX] = (float)m.qd_max;
+  f[M_QLIM] = (float)m.q_lim;
+  f[M_DT] = (float)m.dt;
+  memset(s, 0, sizeof(double) * SCHED_D);
+  s[S_DT] = m.dt;
+  s[S_PERIOD] = m.period;
+  s[S_DUTY] = m.duty[0];
+  s[S_DUTY + 1] = m.duty[1];
+  s[S_OFF] = m.offset[0];
+  s[S_OFF + 1] = m.offset[1];
+}
+
+}  // extern "C"
+
+// scatter packed models into their slots, clear warm starts
+__global__ void mpc_k_scatter_models(int n, const int* ids, const float* mf, const double* ms, const int* hz,
+                                     float* model, double* sched, int* horizon, int* warm) {
+  const int row = blockIdx.x;
+  if (row >= n) return;
+  const int s = ids[row];
+  for (int t = threadIdx.x; t < mpc::MODEL_F; t += blockDim.x)
+    model[(size_t)s * mpc::MODEL_F + t] = mf[(size_t)row * mpc::MODEL_F + t];
+  for (int t = threadIdx.x; t < mpc::SCHED_D; t += blockDim.x)
+    sched[(size_t)s * mpc::SCHED_D + t] = ms[(size_t)row * mpc::SCHED_D + t];
+  if (threadIdx.x == 0) {
+    horizon[s] = hz[row];
+    warm[s] = 0;
+  }
+}
+
+extern "C" {
+
+mpc_status mpc_set_models(mpc_ctx* ctx, int32_t n, const int32_t* ids, const mpc_agent_model* models) {
+  if (!ctx) return MPC_ERR_INVALID;
+  if (n < 0 || n > ctx->cfg.max_agents || (n > 0 && (!ids || !models)))
+    return fail(ctx, MPC_ERR_INVALID, "set_models: bad count or NULL buffer");
+  if (n == 0) return MPC_OK;
+  std::vector<float> mf((size_t)n * mpc::MODEL_F);
+  std::vector<double> ms((size_t)n * mpc::SCHED_D);
+  std::vector<int> hz(n);
+  for (int i = 0; i < n; ++i) {
+    if (ids[i] < 0 || ids[i] >= ctx->cfg.max_agents)
+      return fail(ctx, MPC_ERR_INVALID, "set_models: agent id out of range");
+    const char* why = check_model(models[i], ctx->cfg.max_horizon);
+    if (why) return fail(ctx, MPC_ERR_INVALID, std::string("set_models: ") + why);
+    pack_model(models[i], &mf[(size_t)i * mpc::MODEL_F], &ms[(size_t)i * mpc::SCHED_D]);
+    hz[i] = models[i].N;
+  }
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaMemcpyAsync(ctx->d_ids, ids, sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_mstage, mf.data(), sizeof(float) * mf.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_sstage, ms.data(), sizeof(double) * ms.size(), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_hstage, hz.data(), sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+  mpc_k_scatter_models<<<n, 128, 0, ctx->stream>>>(n, ctx->d_ids, ctx->d_mstage, ctx->d_sstage, ctx->d_hstage,
+                                                    ctx->model, ctx->sched, ctx->horizon, ctx->ar.warm_valid);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int i = 0; i < n; ++i) ctx->live[ids[i]] = hz[i];
+  return MPC_OK;
+}
+
+mpc_status mpc_set_model(mpc_ctx* ctx, int32_t agent_id, const mpc_agent_model* model) {
+  return mpc_set_models(ctx, 1, &agent_id, model);
+}
+
+mpc_status mpc_release_agent(mpc_ctx* ctx, int32_t agent_id) {
+  if (!ctx) return MPC_ERR_INVALID;
+  if (agent_id < 0 || agent_id >= ctx->cfg.max_agents || !ctx->live[agent_id])
+    return fail(ctx, MPC_ERR_INVALID, "release: unknown agent");
+  ctx->live[agent_id] = 0;
+  int zero = 0;
+  CK(cudaMemcpyAsync(ctx->ar.warm_valid + agent_id, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->horizon + agent_id, &zero, sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return MPC_OK;
+}
+
+mpc_status mpc_submit(mpc_ctx* ctx, int32_t n, const int32_t* ids, const float* x0, const float* qd,
+                      const float* cmd, const float* phase, uint64_t* ticket) {
+  if (!ctx) return MPC_ERR_INVALID;
+  if (!ticket) return fail(ctx, MPC_ERR_INVALID, "submit: NULL ticket");
+  if (n < 0 || n > ctx->cfg.max_agents) return fail(ctx, MPC_ERR_INVALID, "submit: n outside [0, max_agents]");
+  if (n > 0 && (!ids || !x0 || !qd || !cmd || !phase)) return fail(ctx, MPC_ERR_INVALID, "submit: NULL buffer");
+  for (int t = 0; t < kMaxTickets; ++t) {
+    Ticket& tk = ctx->tickets[t];
+    if (tk.state == 0) {
+      tk.id = ctx->next_ticket++;
+      tk.state = 1;
+      tk.b = mpc::Batch{n, ids, x0, qd, cmd, phase};
+      *ticket = tk.id;
+      return MPC_OK;
+    }
+  }
+  return fail(ctx, MPC_ERR_STATE, "submit: too many pending tickets (64)");
+}
+
+static Ticket* find_ticket(mpc_ctx* ctx, uint64_t id) {
+  for (int t = 0; t < kMaxTickets; ++t)
+    if (ctx->tickets[t].state && ctx->tickets[t].id == id) return &ctx->tickets[t];
+  return nullptr;
+}
+
+static mpc::SolverParams params_of(const mpc_config& c) {
+  mpc::SolverParams p;
+  p.rho0 = c.rho0; p.sigma = c.sigma; p.alpha = c.alpha; p.eps_abs = c.eps_abs; p.eps_rel = c.eps_rel;
+  p.max_iter = c.max_iter; p.fixed_iters = c.fixed_iters; p.check_every = c.check_every;
+  p.adaptive_rho = c.adaptive_rho; p.polish = c.polish; p.warm_start = c.warm_start;
+  return p;
+}
+
+mpc_status mpc_solve(mpc_ctx* ctx, uint64_t ticket) {
+  if (!ctx) return MPC_ERR_INVALID;
+  Ticket* tk = find_ticket(ctx, ticket);
+  if (!tk) return fail(ctx, MPC_ERR_NOT_READY, "solve: unknown ticket");
+  if (tk->state != 1) return fail(ctx, MPC_ERR_STATE, "solve: ticket already solved");
+  CK(cudaSetDevice(ctx->cfg.device));
+  int launches = 0;
+  cudaError_t e = mpc::launch_solve(ctx->ar, tk->b, params_of(ctx->cfg), ctx->cfg.form, 0, ctx->stream, &launches);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "solve: kernel launch");
+  ctx->launches += launches;
+  ctx->solves += 1;
+  tk->state = 2;
+  return MPC_OK;
+}
+
+mpc_status mpc_get_torques(mpc_ctx* ctx, uint64_t ticket, float* tau, float* q_set, float* qd_set, float* value,
+                           int32_t* agent_status) {
+  if (!ctx) return MPC_ERR_INVALID;
+  Ticket* tk = find_ticket(ctx, ticket);
+  if (!tk) return fail(ctx, MPC_ERR_NOT_READY, "get_torques: unknown ticket");
+  if (tk->state != 2) return fail(ctx, MPC_ERR_NOT_READY, "get_torques: ticket not solved");
+  CK(cudaSetDevice(ctx->cfg.device));
+  cudaError_t e = mpc::launch_gather(ctx->ar, tk->b.n, tk->b.ids, tau, q_set, qd_set, value, agent_status,
+                                     ctx->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "get_torques: gather");
+  ctx->launches += 1;
+  tk->state = 0;
+  return MPC_OK;
+}
+
+mpc_status mpc_solve_host(mpc_ctx* ctx, int32_t n, const int32_t* ids, const float* x0, const float* qd,
+                          const float* cmd, const float* phase, float* tau, float* q_set, float* qd_set,
+                          float* value, int32_t* agent_status) {
+  if (!ctx) return MPC_ERR_INVALID;
+  if (n < 0 || n > ctx->cfg.max_agents) return fail(ctx, MPC_ERR_INVALID, "solve_host: bad n");
+  if (n > 0 && (!ids || !x0 || !qd || !cmd || !phase)) return fail(ctx, MPC_ERR_INVALID, "solve_host: NULL input");
+  CK(cudaSetDevice(ctx->cfg.device));
+  cudaStream_t st = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->d_ids, ids, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_x0, x0, sizeof(float) * 30 * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_qd, qd, sizeof(float) * 18 * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_cmd, cmd, sizeof(float) * 4 * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_phase, phase, sizeof(float) * n, cudaMemcpyHostToDevice, st));
+  uint64_t t = 0;
+  mpc_status s = mpc_submit(ctx, n, ctx->d_ids, ctx->d_x0, ctx->d_qd, ctx->d_cmd, ctx->d_phase, &t);
+  if (s != MPC_OK) return s;
+  s = mpc_solve(ctx, t);
+  if (s != MPC_OK) return s;
+  s = mpc_get_torques(ctx, t, ctx->d_tau, ctx->d_qset, ctx->d_qdset, ctx->d_val, ctx->d_status);
+  if (s != MPC_OK) return s;
+  if (tau) CK(cudaMemcpyAsync(tau, ctx->d_tau, sizeof(float) * 18 * n, cudaMemcpyDeviceToHost, st));
+  if (q_set) CK(cudaMemcpyAsync(q_set, ctx->d_qset, sizeof(float) * 18 * n, cudaMemcpyDeviceToHost, st));
+  if (qd_set) CK(cudaMemcpyAsync(qd_set, ctx->d_qdset, sizeof(float) * 18 * n, cudaMemcpyDeviceToHost, st));
+  if (value) CK(cudaMemcpyAsync(value, ctx->d_val, sizeof(float) * n, cudaMemcpyDeviceToHost, st));
+  if (agent_status) CK(cudaMemcpyAsync(agent_status, ctx->d_status, sizeof(int) * n, cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  return MPC_OK;
+}
+
+mpc_status mpc_get_agent_stats(mpc_ctx* ctx, int32_t n, const int32_t* ids, int32_t* iters, int32_t* refactors,
+                               int32_t* polished, float* prim, float* dual) {
+  if (!ctx) return MPC_ERR_INVALID;
+  if (n < 0 || (n > 0 && !ids)) return fail(ctx, MPC_ERR_INVALID, "get_agent_stats: bad arguments");
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const size_t A = ctx->cfg.max_agents;
+  std::vector<int> st(A * mpc::ST_I);
+  std::vector<float> out(A * mpc::OUT_F);
+  CK(cudaMemcpy(st.data(), ctx->ar.stat, sizeof(int) * st.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(out.data(), ctx->ar.out, sizeof(float) * out.size(), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i) {
+    if (ids[i] < 0 || ids[i] >= (int)A) return fail(ctx, MPC_ERR_INVALID, "get_agent_stats: id out of range");
+    const int* s = &st[(size_t)ids[i] * mpc::ST_I];
+    const float* o = &out[(size_t)ids[i] * mpc::OUT_F];
+    if (iters) iters[i] = s[mpc::T_ITERS];
+    if (refactors) refactors[i] = s[mpc::T_REFAC];
+    if (polished) polished[i] = s[mpc::T_POLISHED];
+    if (prim) prim[i] = o[mpc::O_PRIM];
+    if (dual) dual[i] = o[mpc::O_DUAL];
+  }
+  return MPC_OK;
+}
+
+mpc_status mpc_export_state(mpc_ctx* ctx, int32_t id, float* x, float* u, float* w, float* y, float* rho) {
+  if (!ctx) return MPC_ERR_INVALID;
+  if (id < 0 || id >= ctx->cfg.max_agents || !ctx->live[id]) return fail(ctx, MPC_ERR_INVALID, "export: unknown agent");
+  using namespace mpc;
+  const int N = ctx->live[id], n = ctx->cfg.max_horizon;
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<float> bx((N + 1) * VS), bu(N * VS), bw(N * RS), by(N * RS);
+  CK(cudaMemcpy(bx.data(), ctx->ar.xs + (size_t)id * (n + 1) * VS, sizeof(float) * bx.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(bu.data(), ctx->ar.us + (size_t)id * n * VS, sizeof(float) * bu.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(bw.data(), ctx->ar.ws + (size_t)id * n * RS, sizeof(float) * bw.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(by.data(), ctx->ar.ys + (size_t)id * n * RS, sizeof(float) * by.size(), cudaMemcpyDeviceToHost));
+  for (int k = 0; k <= N; ++k)
+    for (int i = 0; i < 30; ++i)
+      if (x) x[k * 30 + i] = bx[k * VS + i];
+  for (int k = 0; k < N; ++k) {
+    for (int i = 0; i < 30; ++i)
+      if (u) u[k * 30 + i] = bu[k * VS + i];
+    for (int r = 0; r < 56; ++r) {
+      if (w) w[k * 56 + r] = bw[k * RS + r];
+      if (y) y[k * 56 + r] = by[k * RS + r];
+    }
+  }
+  if (rho) CK(cudaMemcpy(rho, ctx->ar.rho + id, sizeof(float), cudaMemcpyDeviceToHost));
+  return MPC_OK;
+}
+
+mpc_status mpc_import_state(mpc_ctx* ctx, int32_t id, const float* x, const float* u, const float* w,
+                            const float* y, float rho) {
+  if (!ctx) return MPC_ERR_INVALID;
+  if (id < 0 || id >= ctx->cfg.max_agents || !ctx->live[id]) return fail(ctx, MPC_ERR_INVALID, "import: unknown agent");
+  if (!x || !u || !w || !y || !(rho > 0.f)) return fail(ctx, MPC_ERR_INVALID, "import: bad state");
+  using namespace mpc;
+  const int N = ctx->live[id], n = ctx->cfg.max_horizon;
+  std::vector<float> bx((N + 1) * VS, 0.f), bu(N * VS, 0.f), bw(N * RS, 0.f), by(N * RS, 0.f);
+  for (int k = 0; k <= N; ++k)
+    for (int i = 0; i < 30; ++i) bx[k * VS + i] = x[k * 30 + i];
+  for (int k = 0; k < N; ++k) {
+    for (int i = 0; i < 30; ++i) bu[k * VS + i] = u[k * 30 + i];
+    for (int r = 0; r < 56; ++r) {
+      bw[k * RS + r] = w[k * 56 + r];
+      by[k * RS + r] = y[k * 56 + r];
+    }
+  }
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaMemcpy(ctx->ar.xs + (size_t)id * (n + 1) * VS, bx.data(), sizeof(float) * bx.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->ar.us + (size_t)id * n * VS, bu.data(), sizeof(float) * bu.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->ar.ws + (size_t)id * n * RS, bw.data(), sizeof(float) * bw.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->ar.ys + (size_t)id * n * RS, by.data(), sizeof(float) * by.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->ar.rho + id, &rho, sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(ctx->ar.warm_valid + id, &N, sizeof(int), cudaMemcpyHostToDevice));
+  return MPC_OK;
+}
+
+mpc_status mpc_get_stats(mpc_ctx* ctx, char* buf, size_t cap) {
+  if (!ctx || !buf || cap == 0) return MPC_ERR_INVALID;
+  int live = 0;
+  for (int h : ctx->live) live += h != 0;
+  snprintf(buf, cap,
+           "{\"max_agents\": %d, \"max_horizon\": %d, \"live_agents\": %d, \"arena_bytes\": %zu, "
+           "\"form\": \"%s\", \"kernel_launches\": %lld, \"solves\": %lld, \"smem_per_block\": %zu, "
+           "\"warps_per_block\": %d}",
+           ctx->cfg.max_agents, ctx->cfg.max_horizon, live, ctx->bytes,
+           ctx->cfg.form == MPC_FORM_FUSED ? "fused" : "plain", ctx->launches, ctx->solves,
+           mpc::smem_bytes_per_block(), mpc::WARPS_PER_BLOCK);
+  return MPC_OK;
+}
+
+const char* mpc_last_error(mpc_ctx* ctx) {
+  if (!ctx) return "NULL context";
+  return ctx->err.c_str();
+}
+
+}  // extern "C"

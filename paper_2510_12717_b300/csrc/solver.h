@@ -1,0 +1,27 @@
+// Host-visible interface of the solver kernels (used by the C ABI layer).
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include "arena.h"
+
+namespace mpc {
+
+constexpr int WARPS_PER_BLOCK = 4;
+
+// per-agent status codes (same values as mpc_agent_status in the public header)
+constexpr int MPC_AGENT_SOLVED_ = 0;
+constexpr int MPC_AGENT_MAX_ITER_ = 1;
+constexpr int MPC_AGENT_NAN_ = 4;
+
+size_t smem_bytes_per_block();
+
+// Enqueue the whole hot path for a batch.  form 0 = plain (five step
+// kernels), 1 = fused (one kernel; grid_fused > 0 caps its grid).
+// *launches is incremented by the number of kernels enqueued.
+cudaError_t launch_solve(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
+                         cudaStream_t st, int* launches);
+
+cudaError_t launch_gather(const Arena& a, int n, const int* ids, float* tau, float* qset, float* qdset,
+                          float* value, int* status, cudaStream_t st);
+
+}  // namespace mpc

@@ -1,0 +1,240 @@
+"""ctypes binding of libmpcgpu.so (C ABI in include/mpcgpu.h).
+
+Argument marshalling only: every step of the hot path runs in the library's
+CUDA kernels.  Device buffers are torch CUDA tensors (passed by data_ptr());
+streams are torch streams.  There is no CPU fallback: load() raises when the
+library is missing or cannot be loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmpcgpu.so")
+
+MPC_OK, MPC_ERR_INVALID, MPC_ERR_BUDGET, MPC_ERR_CUDA = 0, 1, 2, 3
+MPC_ERR_NOT_READY, MPC_ERR_TIMEOUT, MPC_ERR_STATE = 4, 5, 6
+AGENT_SOLVED, AGENT_MAX_ITER, AGENT_PRIMAL_INFEAS, AGENT_DUAL_INFEAS, AGENT_NAN = 0, 1, 2, 3, 4
+FORM_PLAIN, FORM_FUSED = 0, 1
+FP32, TF32, BF16, FP64 = 0, 1, 2, 3
+
+STATUS_NAMES = {0: "MPC_OK", 1: "MPC_ERR_INVALID", 2: "MPC_ERR_BUDGET", 3: "MPC_ERR_CUDA",
+                4: "MPC_ERR_NOT_READY", 5: "MPC_ERR_TIMEOUT", 6: "MPC_ERR_STATE"}
+
+
+class MpcConfig(C.Structure):
+    _fields_ = [
+        ("device", C.c_int), ("stream", C.c_void_p), ("max_agents", C.c_int),
+        ("max_horizon", C.c_int), ("hbm_budget_bytes", C.c_size_t), ("precision", C.c_int),
+        ("form", C.c_int), ("rho0", C.c_float), ("sigma", C.c_float), ("alpha", C.c_float),
+        ("eps_abs", C.c_float), ("eps_rel", C.c_float), ("max_iter", C.c_int),
+        ("fixed_iters", C.c_int), ("check_every", C.c_int), ("adaptive_rho", C.c_int),
+        ("polish", C.c_int), ("warm_start", C.c_int),
+    ]
+
+
+class MpcAgentModel(C.Structure):
+    _fields_ = [
+        ("mass", C.c_double), ("inertia", C.c_double * 3), ("lever", (C.c_double * 3) * 2),
+        ("J_leg", ((C.c_double * 5) * 6) * 2), ("M_j", C.c_double * 18), ("h_j", C.c_double * 18),
+        ("Kp", C.c_double * 18), ("Kd", C.c_double * 18), ("Q", C.c_double * 30),
+        ("R", C.c_double * 30), ("mu", C.c_double), ("fz_max", C.c_double),
+        ("qd_max", C.c_double), ("q_lim", C.c_double), ("N", C.c_int), ("dt", C.c_double),
+        ("gait", C.c_int), ("period", C.c_double), ("duty", C.c_double * 2),
+        ("offset", C.c_double * 2), ("q_nom", C.c_double * 18),
+    ]
+
+
+# numpy mirror of mpc_agent_model (C alignment), for vectorised packing
+MODEL_DTYPE = np.dtype([
+    ("mass", "f8"), ("inertia", "f8", 3), ("lever", "f8", (2, 3)), ("J_leg", "f8", (2, 6, 5)),
+    ("M_j", "f8", 18), ("h_j", "f8", 18), ("Kp", "f8", 18), ("Kd", "f8", 18), ("Q", "f8", 30),
+    ("R", "f8", 30), ("mu", "f8"), ("fz_max", "f8"), ("qd_max", "f8"), ("q_lim", "f8"),
+    ("N", "i4"), ("dt", "f8"), ("gait", "i4"), ("period", "f8"), ("duty", "f8", 2),
+    ("offset", "f8", 2), ("q_nom", "f8", 18),
+], align=True)
+
+# every function the header declares: name -> (restype, argtypes)
+_P, _I32P, _U64P = C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)
+SIGNATURES = {
+    "mpc_default_config": (C.c_int, [C.POINTER(MpcConfig)]),
+    "mpc_create": (C.c_int, [C.POINTER(MpcConfig), C.POINTER(C.c_void_p)]),
+    "mpc_destroy": (C.c_int, [_P]),
+    "mpc_set_models": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "mpc_set_model": (C.c_int, [_P, C.c_int32, _P]),
+    "mpc_release_agent": (C.c_int, [_P, C.c_int32]),
+    "mpc_submit": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _U64P]),
+    "mpc_solve": (C.c_int, [_P, C.c_uint64]),
+    "mpc_get_torques": (C.c_int, [_P, C.c_uint64, _P, _P, _P, _P, _P]),
+    "mpc_solve_host": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
+    "mpc_get_agent_stats": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P]),
+    "mpc_export_state": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P]),
+    "mpc_import_state": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_float]),
+    "mpc_get_stats": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
+    "mpc_last_error": (C.c_char_p, [_P]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libmpcgpu.so and declare its signatures.  Raises if missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmpcgpu.so not built ({path}); run __graft_entry__.build() "
+                           "or python -m paper_2510_12717_b300.build")
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class MpcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def pack_models(model: dict, idx=None) -> np.ndarray:
+    """SoA model dict (workload.make_agents layout) -> mpc_agent_model array."""
+    B = len(model["mass"])
+    idx = np.arange(B) if idx is None else np.asarray(idx)
+    out = np.zeros(len(idx), dtype=MODEL_DTYPE)
+    for name in MODEL_DTYPE.names:
+        out[name] = np.asarray(model[name])[idx]
+    return out
+
+
+class Solver:
+    """One library context (mpc_create ... mpc_destroy)."""
+
+    def __init__(self, max_agents: int = 16384, max_horizon: int = 20, *, form: int = FORM_FUSED,
+                 device: int = 0, stream=None, hbm_budget_bytes: int = 0, **opts):
+        self.lib = load()
+        cfg = MpcConfig()
+        self._check(self.lib.mpc_default_config(C.byref(cfg)), None)
+        cfg.device = device
+        cfg.stream = stream
+        cfg.max_agents = max_agents
+        cfg.max_horizon = max_horizon
+        cfg.form = form
+        cfg.hbm_budget_bytes = hbm_budget_bytes
+        for k, v in opts.items():
+            if not hasattr(cfg, k):
+                raise TypeError(f"unknown solver option {k}")
+            setattr(cfg, k, v)
+        self.cfg = cfg
+        h = C.c_void_p()
+        st = self.lib.mpc_create(C.byref(cfg), C.byref(h))
+        if st != MPC_OK:
+            raise MpcError(st, "mpc_create failed")
+        self.ctx = h
+
+    def _check(self, st, ctx=True):
+        if st != MPC_OK:
+            msg = self.lib.mpc_last_error(self.ctx).decode() if ctx else ""
+            raise MpcError(st, msg)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            self.lib.mpc_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- models
+    def set_models(self, model: dict, agent_ids, idx=None):
+        recs = pack_models(model, idx)
+        ids = np.ascontiguousarray(agent_ids, dtype=np.int32)
+        assert len(ids) == len(recs)
+        self._check(self.lib.mpc_set_models(self.ctx, len(ids), _ptr(ids), recs.ctypes.data))
+
+    def release(self, agent_id: int):
+        self._check(self.lib.mpc_release_agent(self.ctx, int(agent_id)))
+
+    # -- device-buffer path
+    def submit(self, ids, x0, qd_meas, cmd, phase) -> int:
+        t = C.c_uint64()
+        self._check(self.lib.mpc_submit(self.ctx, int(ids.shape[0]), _ptr(ids), _ptr(x0), _ptr(qd_meas),
+                                        _ptr(cmd), _ptr(phase), C.byref(t)))
+        return t.value
+
+    def solve(self, ticket: int):
+        self._check(self.lib.mpc_solve(self.ctx, C.c_uint64(ticket)))
+
+    def get_torques(self, ticket: int, tau=None, q_set=None, qd_set=None, value=None, status=None):
+        self._check(self.lib.mpc_get_torques(self.ctx, C.c_uint64(ticket), _ptr(tau), _ptr(q_set),
+                                             _ptr(qd_set), _ptr(value), _ptr(status)))
+
+    # -- host-buffer path (numpy in, numpy out)
+    def solve_host(self, ids, x0, qd_meas, cmd, phase, *, tau=None, q_set=None, qd_set=None,
+                   value=None, status=None):
+        n = len(ids)
+        ids = np.ascontiguousarray(ids, np.int32)
+        x0 = np.ascontiguousarray(x0, np.float32)
+        qd_meas = np.ascontiguousarray(qd_meas, np.float32)
+        cmd = np.ascontiguousarray(cmd, np.float32)
+        phase = np.ascontiguousarray(phase, np.float32)
+        tau = np.empty((n, 18), np.float32) if tau is None else tau
+        q_set = np.empty((n, 18), np.float32) if q_set is None else q_set
+        qd_set = np.empty((n, 18), np.float32) if qd_set is None else qd_set
+        value = np.empty(n, np.float32) if value is None else value
+        status = np.empty(n, np.int32) if status is None else status
+        self._check(self.lib.mpc_solve_host(self.ctx, n, _ptr(ids), _ptr(x0), _ptr(qd_meas), _ptr(cmd),
+                                            _ptr(phase), _ptr(tau), _ptr(q_set), _ptr(qd_set),
+                                            _ptr(value), _ptr(status)))
+        return dict(tau=tau, q_set=q_set, qd_set=qd_set, value=value, status=status)
+
+    # -- inspection
+    def agent_stats(self, ids):
+        ids = np.ascontiguousarray(ids, np.int32)
+        n = len(ids)
+        it = np.empty(n, np.int32)
+        rf = np.empty(n, np.int32)
+        po = np.empty(n, np.int32)
+        rp = np.empty(n, np.float32)
+        rd = np.empty(n, np.float32)
+        self._check(self.lib.mpc_get_agent_stats(self.ctx, n, _ptr(ids), _ptr(it), _ptr(rf), _ptr(po),
+                                                 _ptr(rp), _ptr(rd)))
+        return dict(iters=it, refactors=rf, polished=po, prim_res=rp, dual_res=rd)
+
+    def export_state(self, agent_id: int, N: int):
+        x = np.empty((N + 1, 30), np.float32)
+        u = np.empty((N, 30), np.float32)
+        w = np.empty((N, 56), np.float32)
+        y = np.empty((N, 56), np.float32)
+        rho = np.empty(1, np.float32)
+        self._check(self.lib.mpc_export_state(self.ctx, int(agent_id), _ptr(x), _ptr(u), _ptr(w),
+                                              _ptr(y), _ptr(rho)))
+        return dict(x=x, u=u, w=w, y=y, rho=float(rho[0]))
+
+    def import_state(self, agent_id: int, st: dict):
+        arrs = [np.ascontiguousarray(st[k], np.float32) for k in ("x", "u", "w", "y")]
+        self._check(self.lib.mpc_import_state(self.ctx, int(agent_id), *[_ptr(a) for a in arrs],
+                                              C.c_float(st["rho"])))
+
+    def stats(self) -> dict:
+        import json
+        buf = C.create_string_buffer(1024)
+        self._check(self.lib.mpc_get_stats(self.ctx, buf, 1024))
+        return json.loads(buf.value.decode())

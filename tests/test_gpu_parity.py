@@ -1,0 +1,218 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Bar (elementwise): |tau_gpu - tau_oracle| <= 1e-4 N m + 1e-3 |tau_oracle|;
+unscaled primal and dual residuals <= 1e-4.  The per-agent FP32-vs-FP64
+torque error is printed (pytest -s shows it).
+"""
+import numpy as np
+import pytest
+
+from helpers import RES_TOL, agents, device_inputs, oracle_view, torque_close
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mpcgpu():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2510_12717_b300 import mpcgpu as m
+    m.load()
+    return m
+
+
+def _run(mpcgpu, model, inp32, ids, form, max_h=20, solver=None, **opts):
+    dev = torch.device("cuda:0")
+    s = solver or mpcgpu.Solver(max_agents=int(np.max(ids)) + 1, max_horizon=max_h, form=form,
+                                stream=torch.cuda.current_stream().cuda_stream, **opts)
+    if solver is None:
+        s.set_models(model, ids)
+    n = len(ids)
+    t = {k: torch.from_numpy(v).to(dev) for k, v in inp32.items()}
+    ids_d = torch.from_numpy(np.asarray(ids, np.int32)).to(dev)
+    tk = s.submit(ids_d, t["x0"], t["qd_meas"], t["cmd"], t["phase"])
+    s.solve(tk)
+    out = dict(tau=torch.empty((n, 18), device=dev), q_set=torch.empty((n, 18), device=dev),
+               qd_set=torch.empty((n, 18), device=dev), value=torch.empty(n, device=dev),
+               status=torch.empty(n, dtype=torch.int32, device=dev))
+    s.get_torques(tk, **out)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["stats"] = s.agent_stats(ids)
+    res["solver"] = s
+    return res
+
+
+def _oracle(model, inp32, processes=None):
+    from oracle.solve import solve_batch
+    m, i = oracle_view(model, inp32)
+    return solve_batch(m, i, processes=processes)
+
+
+def _report(name, got, ref, st):
+    err = np.abs(got - ref)
+    rel = np.linalg.norm(got - ref, axis=1) / np.maximum(np.linalg.norm(ref, axis=1), 1e-12)
+    print(f"\n[{name}] FP32 vs FP64 per agent: max|dtau| {err.max(axis=1).round(6).tolist()}")
+    print(f"[{name}] norm-wise rel err: {rel.round(7).tolist()}")
+    print(f"[{name}] iters {st['iters'].tolist()} refactors {st['refactors'].tolist()} "
+          f"polished {st['polished'].tolist()}")
+
+
+@pytest.mark.parametrize("form", [0, 1], ids=["plain", "fused"])
+def test_small_workload_matches_oracle(mpcgpu, form):
+    ids = np.arange(16)
+    model, inp = agents("small", ids)
+    inp32 = device_inputs(inp)
+    got = _run(mpcgpu, model, inp32, ids, form)
+    ref = _oracle(model, inp32)
+    _report(f"small/{'fused' if form else 'plain'}", got["tau"], ref["tau"], got["stats"])
+    assert (got["status"] == 0).all(), got["status"]
+    assert torque_close(got["tau"], ref["tau"]).all()
+    assert np.allclose(got["q_set"], ref["q_set"], atol=1e-6)
+    assert torque_close(got["qd_set"], ref["qd_set"]).all()
+    assert (got["stats"]["prim_res"] <= RES_TOL).all() and (got["stats"]["dual_res"] <= RES_TOL).all()
+    assert np.allclose(got["value"], ref["V"], rtol=1e-3, atol=1e-4)
+    got["solver"].close()
+
+
+def test_mixed_horizons_and_gaits_match_oracle(mpcgpu):
+    # uneven workload: horizons 5..20, walk/stand/hop/single-stance; a sample
+    # that includes both horizon extremes and every gait
+    from workload import make_agents
+    pool, _ = make_agents("uneven", np.arange(400))
+    pick = []
+    for g in range(5):
+        pick += list(np.nonzero(pool["gait"] == g)[0][:3])
+    pick += list(np.nonzero(pool["N"] == 5)[0][:2]) + list(np.nonzero(pool["N"] == 20)[0][:2])
+    ids = np.array(sorted(set(int(p) for p in pick)))
+    model, inp = agents("uneven", ids)
+    inp32 = device_inputs(inp)
+    slots = np.arange(len(ids))
+    got = _run(mpcgpu, model, inp32, slots, 1)
+    ref = _oracle(model, inp32)
+    _report("uneven/fused", got["tau"], ref["tau"], got["stats"])
+    assert (got["status"] == 0).all(), got["status"]
+    ok = torque_close(got["tau"], ref["tau"])
+    assert ok.all(), np.argwhere(~ok)
+    assert (got["stats"]["prim_res"] <= RES_TOL).all() and (got["stats"]["dual_res"] <= RES_TOL).all()
+    got["solver"].close()
+
+
+def test_plain_and_fused_forms_agree(mpcgpu):
+    ids = np.arange(12)
+    model, inp = agents("uneven", ids)
+    inp32 = device_inputs(inp)
+    a = _run(mpcgpu, model, inp32, ids, 0)
+    b = _run(mpcgpu, model, inp32, ids, 1)
+    assert np.array_equal(a["tau"], b["tau"])
+    assert np.array_equal(a["status"], b["status"])
+    a["solver"].close(); b["solver"].close()
+
+
+def test_alone_equals_in_mix(mpcgpu):
+    # each agent solved alone gives the same result as in a mixed batch
+    ids = np.arange(10)
+    model, inp = agents("uneven", ids)
+    inp32 = device_inputs(inp)
+    mix = _run(mpcgpu, model, inp32, ids, 1)
+    for a in (0, 3, 7):
+        one = {k: v[a:a + 1] for k, v in inp32.items()}
+        sub = {k: v[a:a + 1] for k, v in model.items()}
+        alone = _run(mpcgpu, sub, one, np.array([0]), 1)
+        assert np.array_equal(alone["tau"][0], mix["tau"][a])
+        alone["solver"].close()
+    mix["solver"].close()
+
+
+def test_warm_start_reaches_same_solution(mpcgpu):
+    ids = np.arange(8)
+    model, inp = agents("uniform", ids)
+    inp32 = device_inputs(inp)
+    s = mpcgpu.Solver(max_agents=8, max_horizon=10, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_models(model, ids)
+    cold = _run(mpcgpu, model, inp32, ids, 1, solver=s)
+    warm = _run(mpcgpu, model, inp32, ids, 1, solver=s)     # same inputs, warm started
+    assert torque_close(warm["tau"], cold["tau"]).all()
+    assert warm["stats"]["iters"].sum() <= cold["stats"]["iters"].sum()
+    # next replan: perturbed state, warm start vs the oracle
+    model1, inp1 = agents("uniform", ids, replan=1)
+    inp1_32 = device_inputs(inp1)
+    nxt = _run(mpcgpu, model1, inp1_32, ids, 1, solver=s)
+    ref = _oracle(model1, inp1_32)
+    assert torque_close(nxt["tau"], ref["tau"]).all()
+    s.close()
+
+
+def test_edge_cases_empty_nan_and_order(mpcgpu):
+    ids = np.arange(6)
+    model, inp = agents("small", ids)
+    inp32 = device_inputs(inp)
+    s = mpcgpu.Solver(max_agents=6, max_horizon=10, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_models(model, ids)
+    # empty batch
+    e = torch.empty(0, device="cuda:0")
+    tk = s.submit(torch.empty(0, dtype=torch.int32, device="cuda:0"), e, e, e, e)
+    s.solve(tk)
+    s.get_torques(tk)
+    # NaN in one agent's state: that agent is flagged, the others are unaffected
+    bad = {k: v.copy() for k, v in inp32.items()}
+    bad["x0"][2, 7] = np.nan
+    good = _run(mpcgpu, model, inp32, ids, 1, solver=s)
+    nan = _run(mpcgpu, model, bad, ids, 1, solver=s)
+    assert nan["status"][2] == mpcgpu.AGENT_NAN
+    assert (np.delete(nan["status"], 2) == 0).all()
+    keep = [0, 1, 3, 4, 5]
+    assert torque_close(nan["tau"][keep], good["tau"][keep]).all()
+    # permuted batch order: results follow their agents
+    perm = np.array([4, 1, 5, 0, 3, 2])
+    pinp = {k: v[perm] for k, v in inp32.items()}
+    p = _run(mpcgpu, model, pinp, perm, 1, solver=s)
+    assert torque_close(p["tau"], good["tau"][perm]).all()
+    s.close()
+
+
+def test_host_path_and_state_roundtrip(mpcgpu):
+    ids = np.arange(5)
+    model, inp = agents("small", ids)
+    inp32 = device_inputs(inp)
+    s = mpcgpu.Solver(max_agents=5, max_horizon=10, stream=torch.cuda.current_stream().cuda_stream,
+                      warm_start=0)
+    s.set_models(model, ids)
+    dev = _run(mpcgpu, model, inp32, ids, 1, solver=s)
+    host = s.solve_host(ids, inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+    assert np.array_equal(host["tau"], dev["tau"])
+    st = s.export_state(3, 10)
+    assert np.allclose(st["x"][0], inp32["x0"][3])
+    s.import_state(3, st)
+    st2 = s.export_state(3, 10)
+    for k in ("x", "u", "w", "y"):
+        assert np.array_equal(st[k], st2[k])
+    s.close()
+
+
+def test_full_size_mixed_16k_sampled(mpcgpu):
+    # 16384 mixed-horizon agents in one launch (the benchmark's configuration);
+    # a seeded sample is checked against the oracle, every agent by property
+    from workload import make_agents
+    n = 16384
+    model, inp = make_agents("mixed16k")
+    inp32 = device_inputs(inp)
+    ids = np.arange(n)
+    got = _run(mpcgpu, model, inp32, ids, 1)
+    st = got["stats"]
+    assert (got["status"] != mpcgpu.AGENT_NAN).all()
+    solved = got["status"] == 0
+    print(f"\n[16k] solved {solved.mean():.4f} polished {st['polished'].mean():.4f} "
+          f"iters mean {st['iters'].mean():.1f} max {st['iters'].max()}")
+    assert solved.mean() >= 0.99
+    assert np.isfinite(got["tau"]).all()
+    rng = np.random.default_rng(7)
+    sample = np.sort(rng.choice(n, 24, replace=False))
+    sm = {k: v[sample] for k, v in model.items()}
+    si = {k: v[sample] for k, v in inp32.items()}
+    ref = _oracle(sm, si)
+    ok = torque_close(got["tau"][sample], ref["tau"])
+    _report("16k-sample", got["tau"][sample], ref["tau"], {k: v[sample] for k, v in st.items()})
+    assert ok[solved[sample]].all()
+    got["solver"].close()
