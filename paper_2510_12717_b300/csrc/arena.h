@@ -76,6 +76,7 @@ struct Arena {
   float* xt;              // [A][(maxN+1)*VS] KKT-solve primal (x tilde)
   float* ut;              // [A][maxN*VS]
   float* dv;              // [A][maxN*VS]    feed-forward terms d_k
+  int* act;               // [A][maxN*RS]    polish: active-set code per row
 };
 
 // lin record layout

@@ -92,7 +92,7 @@ static size_t arena_bytes(size_t A, size_t n) {
   f += A * ((n + 1) * VS + n * VS + 3 * n * RS);     // xref uref rlo rhi rcls
   f += A * lin_floats((int)n);
   f += A * (3 * n * MB + 2 * n * 64);                // cK cH cB cE cC
-  f += A * ((n + 1) * VS + 2 * n * VS);              // xt ut dv
+  f += A * ((n + 1) * VS + 2 * n * VS + n * RS);     // xt ut dv act
   f += A * (1 + 30 + 18 + 4 + 1 + 18 * 3 + 2);       // host-path staging
   f += A * (MODEL_F + 2 * SCHED_D + 1);              // model upload staging
   return f * 4;
@@ -181,6 +181,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   AL(a.xt, A * (n + 1) * VS);
   AL(a.ut, A * n * VS);
   AL(a.dv, A * n * VS);
+  AL(a.act, A * n * RS);
   AL(ctx->d_ids, A);
   AL(ctx->d_x0, A * 30);
   AL(ctx->d_qd, A * 18);

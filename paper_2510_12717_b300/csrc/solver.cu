@@ -587,18 +587,28 @@ __device__ int admm_solve(const AgentPtrs& ap, float* sm, int lane, const Solver
 // Per-stage active-set description built by every lane from smem rows.
 struct FootAct { int swing, zero, top, tx, ty; };
 
-__device__ __forceinline__ void stage_active(const AgentPtrs& ap, int k, int* act, int lane) {
-  for (int r = lane; r < NR; r += 32) {
-    const float lo = ap.rlo[k * RS + r], hi = ap.rhi[k * RS + r];
-    const float w = ap.w[k * RS + r], y = ap.y[k * RS + r];
-    int a = 0;
-    if (lo == hi) a = 3;
-    else {
-      if (w - lo < -y) a |= 1;
-      if (hi - w < y) a |= 2;
+// Initial guess of every stage's active set, stored in the agent's act array
+// (code: bit 0 at lower bound, bit 1 at upper bound, 3 = equality row).
+__device__ void init_active(const AgentPtrs& ap, int lane) {
+  for (int k = 0; k < ap.N; ++k) {
+    for (int r = lane; r < NR; r += 32) {
+      const float lo = ap.rlo[k * RS + r], hi = ap.rhi[k * RS + r];
+      const float w = ap.w[k * RS + r], y = ap.y[k * RS + r];
+      int a = 0;
+      if (lo == hi) a = 3;
+      else {
+        if (w - lo < -y) a |= 1;
+        if (hi - w < y) a |= 2;
+      }
+      ap.act[k * RS + r] = a;
     }
-    act[r] = a;
   }
+  __syncwarp();
+}
+
+// stage k's active-set codes into shared memory
+__device__ __forceinline__ void stage_active(const AgentPtrs& ap, int k, int* act, int lane) {
+  for (int r = lane; r < NR; r += 32) act[r] = ap.act[k * RS + r];
   __syncwarp();
 }
 
@@ -853,8 +863,12 @@ __device__ bool polish_solve(const AgentPtrs& ap, float* sm, int lane) {
 // Optimality check of the polished point (xt, ut): primal feasibility of
 // every row, and KKT conditions of the guessed active set (stationarity in
 // the free directions, right sign of the multipliers of the active rows),
-// with the dynamics multipliers from the costate recursion.
-__device__ Res polish_check(const AgentPtrs& ap, float* sm, int lane) {
+// with the dynamics multipliers from the costate recursion.  When `fix` is
+// set the active set is corrected for a next attempt: rows the point
+// violates are added, active rows whose multiplier has the wrong sign are
+// dropped; *changed reports whether anything changed.
+__device__ Res polish_check(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, bool fix,
+                            int* changed) {
   const int N = ap.N;
   const float* md = ap.mdl;
   const float dt = md[M_DT], mu = md[M_MU];
@@ -862,65 +876,89 @@ __device__ Res polish_check(const AgentPtrs& ap, float* sm, int lane) {
   float* vec = sm + W_VEC;
   float* vU = vec + V_U * 64; float* vXN = vec + V_XN * 64; float* vM = vec + V_S * 64;
   float* vG = vec + V_G * 64;
-  int* act = reinterpret_cast<int*>(vec + V_LO * 64);
   const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
   const float twoR = lane < 30 ? 2.f * dt * md[M_R + lane] : 0.f;
   const float* xs = ap.xt;
   const float* us = ap.ut;
   float rp = 0.f, ps = 0.f, rd = 0.f, ds = 0.f;
+  int chg = 0;
+  // scales first (they set the tolerances)
+  float m = lane < 30 ? twoQ * (xs[N * VS + lane] - ap.xref[N * VS + lane]) : 0.f;
   for (int k = 0; k < N; ++k) {
+    if (lane < 30) {
+      ds = fmaxf(ds, fmaxf(fabsf(twoR * us[k * VS + lane]), fabsf(twoR * ap.uref[k * VS + lane])));
+      ds = fmaxf(ds, fmaxf(fabsf(twoQ * xs[(k + 1) * VS + lane]), fabsf(twoQ * ap.xref[(k + 1) * VS + lane])));
+    }
     vU[lane] = us[k * VS + lane];
     vXN[lane] = xs[(k + 1) * VS + lane];
     __syncwarp();
-    for (int r = lane; r < NR; r += 32) {
-      const float v = crow(vU, vXN, r, mu);
-      const float lo = ap.rlo[k * RS + r], hi = ap.rhi[k * RS + r];
-      rp = fmaxf(rp, fmaxf(fmaxf(lo - v, v - hi), 0.f));
-      if (ap.rcls[k * RS + r] > 0.f) ps = fmaxf(ps, fabsf(v));
-    }
+    for (int r = lane; r < NR; r += 32)
+      if (ap.rcls[k * RS + r] > 0.f) ps = fmaxf(ps, fabsf(crow(vU, vXN, r, mu)));
     __syncwarp();
   }
-  float m = lane < 30 ? twoQ * (xs[N * VS + lane] - ap.xref[N * VS + lane]) : 0.f;
+  ps = warp_max(ps);
+  ds = warp_max(ds);
+  const float tol_p = prm.eps_abs + prm.eps_rel * ps;
+  const float tol_d = prm.eps_abs + prm.eps_rel * ds;
+  // dual conditions, costate backward
+  int* act = reinterpret_cast<int*>(vec + V_LO * 64);
   for (int k = N - 1; k >= 0; --k) {
     const float* dA = ap.lin + L_STAGE + k * 64;
     stage_active(ap, k, act, lane);
     vM[lane] = m;
     __syncwarp();
     float g = 0.f;
-    if (lane < 30) {
+    if (lane < 30)
       g = twoR * (us[k * VS + lane] - ap.uref[k * VS + lane]) + (lane < NC ? wmv<true>(Bm, vM, lane) : dt * m);
-      ds = fmaxf(ds, fmaxf(fabsf(twoR * us[k * VS + lane]), fabsf(twoR * ap.uref[k * VS + lane])));
-      ds = fmaxf(ds, fmaxf(fabsf(twoQ * xs[(k + 1) * VS + lane]), fabsf(twoQ * ap.xref[(k + 1) * VS + lane])));
-    }
     vG[lane] = g;
     __syncwarp();
-    // joint rates: lane i in 12..29
+    int* ak = ap.act + k * RS;
+    // joint rates: lane i in 12..29 (row i + 8); y = -g
     if (lane >= 12 && lane < 30) {
       const int a = act[lane + 8];
-      if (a & 1) rd = fmaxf(rd, fmaxf(-g, 0.f));        // y = -g <= 0 at a lower bound
-      else if (a & 2) rd = fmaxf(rd, fmaxf(g, 0.f));    // y = -g >= 0 at an upper bound
+      float bad = 0.f;
+      if (a & 1) bad = fmaxf(-g, 0.f);         // needs y <= 0 at a lower bound
+      else if (a & 2) bad = fmaxf(g, 0.f);     // needs y >= 0 at an upper bound
       else rd = fmaxf(rd, fabsf(g));
+      rd = fmaxf(rd, bad);
+      if (fix && bad > tol_d) { ak[lane + 8] = 0; chg = 1; }
     }
     // feet: lane f in 0..1
     if (lane < 2) {
-      const int f = lane, b = 6 * f;
+      const int f = lane, b = 6 * f, p = 12 + 4 * f;
       const FootAct fa = foot_act(act, f);
       const float gx = vG[b], gy = vG[b + 1], gz = vG[b + 2];
       if (!fa.swing) {
         for (int c = 3; c < 6; ++c) rd = fmaxf(rd, fabsf(vG[b + c]));   // free moments
         if (fa.zero) {
           // -g in the normal cone of the pyramid at 0: g . ray >= 0 on its 4 rays
+          float worst = 0.f;
           for (int sx = -1; sx <= 1; sx += 2)
             for (int sy = -1; sy <= 1; sy += 2)
-              rd = fmaxf(rd, fmaxf(-(sx * mu * gx + sy * mu * gy + gz), 0.f));
+              worst = fmaxf(worst, -(sx * mu * gx + sy * mu * gy + gz));
+          rd = fmaxf(rd, worst);
+          if (fix && worst > tol_d) {
+            ak[b + 2] &= ~1;
+            if ((act[p] & 2) && (act[p + 1] & 2)) { ak[p] = 0; ak[p + 1] = 0; }
+            if ((act[p + 2] & 2) && (act[p + 3] & 2)) { ak[p + 2] = 0; ak[p + 3] = 0; }
+            chg = 1;
+          }
         } else {
           const float ypx = fa.tx ? -fa.tx * gx : 0.f;
           const float ypy = fa.ty ? -fa.ty * gy : 0.f;
-          if (fa.tx) rd = fmaxf(rd, fmaxf(-ypx, 0.f)); else rd = fmaxf(rd, fabsf(gx));
-          if (fa.ty) rd = fmaxf(rd, fmaxf(-ypy, 0.f)); else rd = fmaxf(rd, fabsf(gy));
-          const float rz = gz - mu * (ypx + ypy);   // = -y_top when f_z is at its upper bound
-          if (fa.top) rd = fmaxf(rd, fmaxf(rz, 0.f));
-          else rd = fmaxf(rd, fabsf(rz));
+          if (fa.tx) {
+            rd = fmaxf(rd, fmaxf(-ypx, 0.f));
+            if (fix && -ypx > tol_d) { ak[fa.tx > 0 ? p : p + 1] = 0; chg = 1; }
+          } else rd = fmaxf(rd, fabsf(gx));
+          if (fa.ty) {
+            rd = fmaxf(rd, fmaxf(-ypy, 0.f));
+            if (fix && -ypy > tol_d) { ak[fa.ty > 0 ? p + 2 : p + 3] = 0; chg = 1; }
+          } else rd = fmaxf(rd, fabsf(gy));
+          const float rz = gz - mu * (ypx + ypy);   // = -y_top when f_z sits at its upper bound
+          if (fa.top) {
+            rd = fmaxf(rd, fmaxf(rz, 0.f));
+            if (fix && rz > tol_d) { ak[b + 2] &= ~2; chg = 1; }
+          } else rd = fmaxf(rd, fabsf(rz));
         }
       }
     }
@@ -930,9 +968,50 @@ __device__ Res polish_check(const AgentPtrs& ap, float* sm, int lane) {
     __syncwarp();
     m = mn;
   }
+  // primal feasibility of every row (after the dual pass, so that the dual
+  // conditions are read on the active set the point was solved with)
+  for (int k = 0; k < N; ++k) {
+    vU[lane] = us[k * VS + lane];
+    vXN[lane] = xs[(k + 1) * VS + lane];
+    __syncwarp();
+    for (int r = lane; r < NR; r += 32) {
+      const float v = crow(vU, vXN, r, mu);
+      const float lo = ap.rlo[k * RS + r], hi = ap.rhi[k * RS + r];
+      const float viol = fmaxf(fmaxf(lo - v, v - hi), 0.f);
+      rp = fmaxf(rp, viol);
+      if (fix && viol > tol_p && ap.act[k * RS + r] == 0) {
+        ap.act[k * RS + r] = (v < lo) ? 1 : 2;
+        chg = 1;
+      }
+    }
+    __syncwarp();
+  }
   Res out;
-  out.rp = warp_max(rp); out.ps = warp_max(ps); out.rd = warp_max(rd); out.ds = warp_max(ds);
+  out.rp = warp_max(rp); out.ps = ps; out.rd = warp_max(rd); out.ds = ds;
+  if (changed) *changed = warp_or(chg);
   return out;
+}
+
+// Polish with active-set correction: up to four attempts; returns true and
+// leaves the polished point in (x, u) when one passes its check.
+__device__ bool polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Res* res) {
+  init_active(ap, lane);
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    if (!polish_solve(ap, sm, lane)) return false;
+    int changed = 0;
+    const Res pr = polish_check(ap, sm, lane, prm, true, &changed);
+    const bool ok = isfinite(pr.rp) && isfinite(pr.rd) && pr.rp <= prm.eps_abs + prm.eps_rel * pr.ps &&
+                    pr.rd <= prm.eps_abs + prm.eps_rel * pr.ds;
+    if (ok) {
+      for (int k = 1; k <= ap.N; ++k) ap.x[k * VS + lane] = ap.xt[k * VS + lane];
+      for (int k = 0; k < ap.N; ++k) ap.u[k * VS + lane] = ap.ut[k * VS + lane];
+      __syncwarp();
+      *res = pr;
+      return true;
+    }
+    if (!changed) return false;
+  }
+  return false;
 }
 
 // ============================================================ torque map (A7)
@@ -1008,17 +1087,11 @@ __device__ void solve_agent(const AgentPtrs& ap, float* sm, int lane, const Solv
   int status = admm_solve(ap, sm, lane, prm, factored, &iters, &refac, &r);
   int polished = 0;
   if (status != MPC_AGENT_NAN_ && prm.polish) {
-    if (polish_solve(ap, sm, lane)) {
-      const Res pr = polish_check(ap, sm, lane);
-      const float tol_p = prm.eps_abs + prm.eps_rel * pr.ps;
-      const float tol_d = prm.eps_abs + prm.eps_rel * pr.ds;
-      if (isfinite(pr.rp) && isfinite(pr.rd) && pr.rp <= tol_p && pr.rd <= tol_d) {
-        polished = 1;
-        for (int k = 1; k <= ap.N; ++k) ap.x[k * VS + lane] = ap.xt[k * VS + lane];
-        for (int k = 0; k < ap.N; ++k) ap.u[k * VS + lane] = ap.ut[k * VS + lane];
-        r.rp = pr.rp; r.rd = pr.rd;
-        status = MPC_AGENT_SOLVED_;
-      }
+    Res pr;
+    if (polish(ap, sm, lane, prm, &pr)) {
+      polished = 1;
+      r.rp = pr.rp; r.rd = pr.rd;
+      status = MPC_AGENT_SOLVED_;
     }
   }
   __syncwarp();
@@ -1105,21 +1178,12 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) mpc_k_polish(Arena a, Ba
   const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
   if (ap.st[T_STATUS] == MPC_AGENT_NAN_ || !prm.polish) return;
   load_lin(ap, sm, lane);
-  if (!polish_solve(ap, sm, lane)) return;
-  const Res pr = polish_check(ap, sm, lane);
-  // tolerances relative to the polished point's own scales
-  const float tol_p = prm.eps_abs + prm.eps_rel * pr.ps;
-  const float tol_d = prm.eps_abs + prm.eps_rel * pr.ds;
-  if (isfinite(pr.rp) && isfinite(pr.rd) && pr.rp <= tol_p && pr.rd <= tol_d) {
-    for (int k = 1; k <= ap.N; ++k) ap.x[k * VS + lane] = ap.xt[k * VS + lane];
-    for (int k = 0; k < ap.N; ++k) ap.u[k * VS + lane] = ap.ut[k * VS + lane];
-    __syncwarp();
-    if (lane == 0) {
-      ap.st[T_STATUS] = MPC_AGENT_SOLVED_;
-      ap.st[T_POLISHED] = 1;
-      ap.out[O_PRIM] = pr.rp;
-      ap.out[O_DUAL] = pr.rd;
-    }
+  Res pr;
+  if (polish(ap, sm, lane, prm, &pr) && lane == 0) {
+    ap.st[T_STATUS] = MPC_AGENT_SOLVED_;
+    ap.st[T_POLISHED] = 1;
+    ap.out[O_PRIM] = pr.rp;
+    ap.out[O_DUAL] = pr.rd;
   }
 }
 

@@ -45,6 +45,7 @@ struct AgentPtrs {
   float *x, *u, *w, *y, *rho;
   int* warm;
   float *inp, *xref, *uref, *rlo, *rhi, *rcls, *lin, *cK, *cH, *cE, *cB, *cC, *xt, *ut, *dv;
+  int* act;
   float* out;
   int* st;
 };
@@ -76,6 +77,7 @@ __device__ __forceinline__ AgentPtrs agent_ptrs(const Arena& a, int s) {
   p.xt = a.xt + (size_t)s * (n + 1) * VS;
   p.ut = a.ut + (size_t)s * n * VS;
   p.dv = a.dv + (size_t)s * n * VS;
+  p.act = a.act + (size_t)s * n * RS;
   p.out = a.out + (size_t)s * OUT_F;
   p.st = a.stat + (size_t)s * ST_I;
   return p;

@@ -44,10 +44,17 @@ def _run(mpcgpu, model, inp32, ids, form, max_h=20, solver=None, **opts):
     return res
 
 
+_ORACLE_CACHE = {}
+
+
 def _oracle(model, inp32, processes=None):
+    """Oracle solve of the same inputs (cached by content within the session)."""
     from oracle.solve import solve_batch
-    m, i = oracle_view(model, inp32)
-    return solve_batch(m, i, processes=processes)
+    key = hash(tuple(np.asarray(v).tobytes() for v in (inp32["x0"], inp32["phase"], model["mass"], model["N"])))
+    if key not in _ORACLE_CACHE:
+        m, i = oracle_view(model, inp32)
+        _ORACLE_CACHE[key] = solve_batch(m, i, processes=processes)
+    return _ORACLE_CACHE[key]
 
 
 def _report(name, got, ref, st):
