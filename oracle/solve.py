@@ -40,8 +40,11 @@ def _worker(args):
             out["y"], r.converged, r.iters, out["extras"]["stance"])
 
 
+_THREAD_VARS = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+
+
 def _init_worker():
-    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    for var in _THREAD_VARS:
         os.environ[var] = "1"
     try:
         from threadpoolctl import threadpool_limits
@@ -65,8 +68,18 @@ def solve_batch(model: dict, inputs: dict, idx=None, processes: int | None = Non
         import multiprocessing as mp
         n = processes or len(os.sched_getaffinity(0))
         ctx = mp.get_context("spawn")
-        with ctx.Pool(n, initializer=_init_worker) as pool:
-            res = pool.map(_worker, jobs, chunksize=1)
+        # workers start with one BLAS thread each (set before they import numpy)
+        saved = {v: os.environ.get(v) for v in _THREAD_VARS}
+        os.environ.update({v: "1" for v in _THREAD_VARS})
+        try:
+            with ctx.Pool(n, initializer=_init_worker) as pool:
+                res = pool.map(_worker, jobs, chunksize=1)
+        finally:
+            for v, old in saved.items():
+                if old is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = old
     return dict(
         tau=np.stack([r[0] for r in res]), q_set=np.stack([r[1] for r in res]),
         qd_set=np.stack([r[2] for r in res]), V=np.array([r[3] for r in res]),
