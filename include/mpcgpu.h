@@ -195,6 +195,32 @@ mpc_status mpc_import_state(mpc_ctx* ctx, int32_t agent_id, const float* x_host,
                             const float* u_host, const float* w_host, const float* y_host,
                             float rho);
 
+/* Allocation-free solve, for callers that cannot allocate device memory
+ * when they need a solve: code inside a CUDA stream capture (cudaMalloc
+ * cannot be captured), simulator plugins that may only use buffers handed to
+ * them, or processes whose device allocator belongs to another framework.
+ * The paper has no counterpart; it is a deployment convenience.
+ *
+ * Solves n <= 64 agents of horizon N <= 20 (models_host[n], host memory) in
+ * one cold-started fused pass with the default options of
+ * mpc_default_config(), on `stream` (a cudaStream_t; NULL = default stream).
+ * Inputs x0, qd_meas, cmd, phase and outputs tau, q_set, qd_set, value,
+ * agent_status are device buffers with the layouts above (outputs may be
+ * NULL).  All workspace lives in one static device array of about 12 MB that
+ * every GPU loading this library holds until the process exits; no call
+ * allocates or frees device memory.
+ *   - The first call on a device resolves the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the one array, which keeps the previous call's
+ *     contents (warm-start markers are cleared each call): calls that may
+ *     overlap on the GPU, from any thread or stream, race.
+ * Returns MPC_ERR_INVALID for n > 64, a horizon > 20, an invalid model or a
+ * NULL input; MPC_ERR_CUDA when a runtime call fails. */
+mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_host, const float* x0,
+                            const float* qd_meas, const float* cmd, const float* phase,
+                            float* tau, float* q_set, float* qd_set, float* value,
+                            int32_t* agent_status, void* stream);
+
 /* JSON summary of the context (sizes, arenas, counters) into buf. */
 mpc_status mpc_get_stats(mpc_ctx* ctx, char* buf, size_t cap);
 

@@ -73,6 +73,7 @@ SIGNATURES = {
     "mpc_get_agent_stats": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P]),
     "mpc_export_state": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P]),
     "mpc_import_state": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_float]),
+    "mpc_solve_static": (C.c_int, [C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "mpc_get_stats": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
     "mpc_last_error": (C.c_char_p, [_P]),
 }
@@ -119,6 +120,24 @@ def pack_models(model: dict, idx=None) -> np.ndarray:
     for name in MODEL_DTYPE.names:
         out[name] = np.asarray(model[name])[idx]
     return out
+
+
+STATIC_MAX_AGENTS = 64
+STATIC_MAX_HORIZON = 20
+
+
+def solve_static(model: dict, x0, qd_meas, cmd, phase, *, tau=None, q_set=None, qd_set=None,
+                 value=None, status=None, stream=None, idx=None) -> int:
+    """mpc_solve_static: allocation-free cold solve of up to 64 agents.
+
+    For callers that cannot allocate device memory at solve time.  Inputs and
+    outputs are caller-owned device tensors; returns the mpc_status code.
+    """
+    lib = load()
+    recs = pack_models(model, idx)
+    return lib.mpc_solve_static(len(recs), recs.ctypes.data, _ptr(x0), _ptr(qd_meas), _ptr(cmd),
+                                _ptr(phase), _ptr(tau), _ptr(q_set), _ptr(qd_set), _ptr(value),
+                                _ptr(status), stream)
 
 
 class Solver:
