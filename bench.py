@@ -37,6 +37,10 @@ WORKLOAD = "mixed16k"
 REPLANS = 4          # distinct pre-generated replan inputs, cycled
 FP32_LANES = 128     # FP32 FMA lanes per SM (B300)
 N_SM = 148
+# DRAM bytes per agent of the fused kernel from the last ncu capture of this
+# kernel version (profiles/mpc_k_fused_mixed16k_1024agents.md: 180.9 MB for
+# 1024 agents); None once the kernel has changed since that capture.
+TRAFFIC_BYTES_PER_AGENT = 180.935e6 / 1024
 
 
 def parse():
@@ -267,7 +271,8 @@ def run_ours(args):
         "latency_budget_ms": 10.0,
         "plain": plain,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": None if TRAFFIC_BYTES_PER_AGENT is None else TRAFFIC_BYTES_PER_AGENT * n,
                      "kernel": "mpc_k_fused", "flops_per_launch": float(fl),
                      "peak_basis": f"148 SM x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz (derived)"},
         "cpu_baseline": cpu,
