@@ -40,7 +40,7 @@ N_SM = 148
 # DRAM bytes per agent of the fused kernel from the last ncu capture of this
 # kernel version (profiles/mpc_k_fused_mixed16k_1024agents.md: 180.9 MB for
 # 1024 agents); None once the kernel has changed since that capture.
-TRAFFIC_BYTES_PER_AGENT = 180.935e6 / 1024
+TRAFFIC_BYTES_PER_AGENT = None
 
 
 def parse():
@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--agents", type=int, default=0, help="override agent count (0 = workload's)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--variant", type=int, default=1, help="kernel variant (register cap), 1 or 2")
     return ap.parse_args()
 
 
@@ -159,7 +160,7 @@ def run_ours(args):
 
     def make_solver(form):
         s = mpcgpu.Solver(max_agents=n, max_horizon=int(Nh.max()), form=form, device=local,
-                          stream=stream.cuda_stream)
+                          stream=stream.cuda_stream, variant=args.variant)
         s.set_models(model, slots)
         return s
 
@@ -265,7 +266,7 @@ def run_ours(args):
         "config": {"workload": f"{args.workload}: {n} agents per GPU, horizon N~U{{5..20}} (mean "
                                f"{Nh.mean():.2f}), gaits walk/stand/hop/single-stance, warm-started "
                                f"replans with perturbed state", "agents_per_gpu": n,
-                   "form": "fused", "precision": "fp32",
+                   "form": "fused", "precision": "fp32", "variant": args.variant,
                    "l2": "per-agent working set (~1.6 GB) >> L2; no flush"},
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "latency_budget_ms": 10.0,

@@ -62,7 +62,8 @@ typedef enum {
   MPC_AGENT_MAX_ITER = 1,      /* iteration cap reached (or fixed-N_QP mode) */
   MPC_AGENT_PRIMAL_INFEAS = 2,
   MPC_AGENT_DUAL_INFEAS = 3,
-  MPC_AGENT_NAN = 4            /* non-finite input or iterate; outputs zeroed */
+  MPC_AGENT_NAN = 4,           /* non-finite input or iterate; outputs zeroed */
+  MPC_AGENT_TIMEOUT = 5        /* a bounded device wait gave up; outputs zeroed */
 } mpc_agent_status;
 
 typedef enum { MPC_FP32 = 0, MPC_TF32 = 1, MPC_BF16 = 2, MPC_FP64 = 3 } mpc_precision;
@@ -76,8 +77,8 @@ typedef enum {
 
 /* Solver and context options.  mpc_default_config() fills the defaults:
  * rho0 0.1, sigma 1e-6, alpha 1.6, eps_abs = eps_rel = 1e-5, max_iter 4000,
- * fixed_iters 0, check_every 10, adaptive_rho 1, polish 1, form FUSED,
- * precision FP32, max_horizon 20.  OSQP's parameters (Stellato et al. 2020,
+ * fixed_iters 0, check_every 10, adaptive_rho 1, polish 1, warm_start 1,
+ * form FUSED, precision FP32, max_horizon 20, variant 1.  OSQP's parameters (Stellato et al. 2020,
  * Sec. 3.2, to which the paper defers after Eq. (backsolve_2)). */
 typedef struct mpc_config {
   int device;                 /* CUDA device ordinal */
@@ -95,6 +96,8 @@ typedef struct mpc_config {
   int adaptive_rho;           /* OSQP rho update (refactor when off by 5x) */
   int polish;                 /* OSQP-style active-set polish after ADMM */
   int warm_start;             /* start from the agent's previous solution */
+  int variant;                /* kernel build: 1 = 2 resident blocks/SM (no register
+                                 spills), 2 = 3 blocks/SM (more warps, some spills) */
 } mpc_config;
 
 /* One agent's model (host memory, float64; stored as float32 on the device,

@@ -25,6 +25,9 @@ constexpr int NR = 56;      // inequality rows per stage
 constexpr int RS = 64;      // stride of per-stage row arrays
 constexpr int VS = 32;      // stride of per-stage lane vectors
 constexpr int MAXN = 32;
+constexpr int R24 = 24;     // row stride of the dense R24 blocks
+constexpr int BLK = 528;    // floats of one R24 block (22 rows x 24)
+constexpr int CB_F = 648;   // polish, per stage: compact B_hat (136) + dense column-major B_hat (512)
 
 // float model record (MODEL_F floats per agent)
 enum : int {
@@ -67,21 +70,25 @@ struct Arena {
   float* rhi;             // [A][maxN*RS]
   float* rcls;            // [A][maxN*RS] rho multiplier per row: 0 free, 1 ineq, 1e3 eq
   float* lin;             // [A][LIN_F]  A_base, B, per-stage dA (3x10) and c
-  float* cK;              // [A][maxN*MB] Riccati gains K_k
-  float* cH;              // [A][maxN*MB] inverse Schur blocks H_uu^-1
+  float* cK;              // [A][maxN*BLK] Riccati gains K_k (R24)
+  float* cH;              // [A][maxN*BLK] inverse Schur blocks H_uu^-1 (R24)
   float* cE;              // [A][maxN*64] e_k = P_{k+1} c_k (lanes 0-21), arm gain (22-29),
                           //   arm e (32-39), arm H_uu^-1 (54-61)
-  float* cB;              // [A][maxN*MB] polish: per-stage reduced B
+  float* cB;              // [A][maxN*CB_F] polish: per-stage reduced B (compact + dense)
   float* cC;              // [A][maxN*64] polish: reduced c (0-29), reduced linear cost (32-61)
   float* xt;              // [A][(maxN+1)*VS] KKT-solve primal (x tilde)
   float* ut;              // [A][maxN*VS]
   float* dv;              // [A][maxN*VS]    feed-forward terms d_k
   int* act;               // [A][maxN*RS]    polish: active-set code per row
+  int* order;             // [A] work queue of the persistent kernel: batch rows, longest first
+  int* counter;           // [1] next queue position
 };
 
-// lin record layout
-__host__ __device__ inline int lin_floats(int maxN) { return 2 * MB + maxN * (2 * VS); }
-enum : int { L_ABASE = 0, L_B = MB, L_STAGE = 2 * MB };   // stage k: dA at L_STAGE + k*64 (30 used), c at +32
+// lin record layout: dense A_base and B (column-major, stride 23), their
+// compact columns (22 x 6 values, padded to 136), then per stage k the leg
+// coupling block dA_k (3x10 at +0) and the affine term c_k (at +32)
+enum : int { L_ABASE = 0, L_B = MB, L_AV = 2 * MB, L_BV = 2 * MB + 136, L_STAGE = 2 * MB + 272 };
+__host__ __device__ constexpr int lin_floats(int maxN) { return L_STAGE + maxN * 64; }
 
 struct Batch {
   int n;
@@ -90,6 +97,8 @@ struct Batch {
   const float* qd;        // [n][18]
   const float* cmd;       // [n][4]
   const float* phase;     // [n]
+  const int* order;       // [n] processing order of the rows (NULL: row order)
+  int* counter;           // work-queue counter, zero at launch (NULL: static assignment)
 };
 
 struct SolverParams {

@@ -91,8 +91,8 @@ static size_t arena_bytes(size_t A, size_t n) {
   f += A * IN_F;
   f += A * ((n + 1) * VS + n * VS + 3 * n * RS);     // xref uref rlo rhi rcls
   f += A * lin_floats((int)n);
-  f += A * (3 * n * MB + 2 * n * 64);                // cK cH cB cE cC
-  f += A * ((n + 1) * VS + 2 * n * VS + n * RS);     // xt ut dv act
+  f += A * (2 * n * BLK + n * CB_F + 2 * n * 64);    // cK cH cB cE cC
+  f += A * ((n + 1) * VS + 2 * n * VS + n * RS + 1); // xt ut dv act order
   f += A * (1 + 30 + 18 + 4 + 1 + 18 * 3 + 2);       // host-path staging
   f += A * (MODEL_F + 2 * SCHED_D + 1);              // model upload staging
   return f * 4;
@@ -121,6 +121,7 @@ mpc_status mpc_default_config(mpc_config* cfg) {
   cfg->adaptive_rho = 1;
   cfg->polish = 1;
   cfg->warm_start = 1;
+  cfg->variant = 1;
   return MPC_OK;
 }
 
@@ -134,7 +135,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   if (cfg->form != MPC_FORM_PLAIN && cfg->form != MPC_FORM_FUSED) return MPC_ERR_INVALID;
   if (!(cfg->rho0 > 0.f) || !(cfg->sigma > 0.f) || !(cfg->alpha > 0.f && cfg->alpha < 2.f) ||
       !(cfg->eps_abs >= 0.f) || !(cfg->eps_rel >= 0.f) || cfg->max_iter <= 0 || cfg->fixed_iters < 0 ||
-      cfg->check_every <= 0)
+      cfg->check_every <= 0 || cfg->variant < 1 || cfg->variant > 2)
     return MPC_ERR_INVALID;
   const size_t A = (size_t)cfg->max_agents, n = (size_t)cfg->max_horizon;
   if (cfg->hbm_budget_bytes && arena_bytes(A, n) > cfg->hbm_budget_bytes) return MPC_ERR_BUDGET;
@@ -173,15 +174,17 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   AL(a.rhi, A * n * RS);
   AL(a.rcls, A * n * RS);
   AL(a.lin, A * (size_t)lin_floats((int)n));
-  AL(a.cK, A * n * MB);
-  AL(a.cH, A * n * MB);
+  AL(a.cK, A * n * BLK);
+  AL(a.cH, A * n * BLK);
   AL(a.cE, A * n * 64);
-  AL(a.cB, A * n * MB);
+  AL(a.cB, A * n * CB_F);
   AL(a.cC, A * n * 64);
   AL(a.xt, A * (n + 1) * VS);
   AL(a.ut, A * n * VS);
   AL(a.dv, A * n * VS);
   AL(a.act, A * n * RS);
+  AL(a.order, A);
+  AL(a.counter, 4);
   AL(ctx->d_ids, A);
   AL(ctx->d_x0, A * 30);
   AL(ctx->d_qd, A * 18);
@@ -352,7 +355,7 @@ mpc_status mpc_submit(mpc_ctx* ctx, int32_t n, const int32_t* ids, const float* 
     if (tk.state == 0) {
       tk.id = ctx->next_ticket++;
       tk.state = 1;
-      tk.b = mpc::Batch{n, ids, x0, qd, cmd, phase};
+      tk.b = mpc::Batch{n, ids, x0, qd, cmd, phase, nullptr, nullptr};
       *ticket = tk.id;
       return MPC_OK;
     }
@@ -381,7 +384,8 @@ mpc_status mpc_solve(mpc_ctx* ctx, uint64_t ticket) {
   if (tk->state != 1) return fail(ctx, MPC_ERR_STATE, "solve: ticket already solved");
   CK(cudaSetDevice(ctx->cfg.device));
   int launches = 0;
-  cudaError_t e = mpc::launch_solve(ctx->ar, tk->b, params_of(ctx->cfg), ctx->cfg.form, 0, ctx->stream, &launches);
+  cudaError_t e = mpc::launch_solve(ctx->ar, tk->b, params_of(ctx->cfg), ctx->cfg.form, 0, ctx->stream, &launches,
+                                     ctx->cfg.variant);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "solve: kernel launch");
   ctx->launches += launches;
   ctx->solves += 1;

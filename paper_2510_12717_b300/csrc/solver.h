@@ -12,14 +12,20 @@ constexpr int WARPS_PER_BLOCK = 4;
 constexpr int MPC_AGENT_SOLVED_ = 0;
 constexpr int MPC_AGENT_MAX_ITER_ = 1;
 constexpr int MPC_AGENT_NAN_ = 4;
+constexpr int MPC_AGENT_TIMEOUT_ = 5;
 
 size_t smem_bytes_per_block();
 
 // Enqueue the whole hot path for a batch.  form 0 = plain (five step
-// kernels), 1 = fused (one kernel; grid_fused > 0 caps its grid).
+// kernels), 1 = fused (one kernel; grid_fused > 0 caps its grid).  variant:
+// register cap of the solver kernels, 1 = 2 blocks/SM, 2 = 3 blocks/SM.
 // *launches is incremented by the number of kernels enqueued.
 cudaError_t launch_solve(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
-                         cudaStream_t st, int* launches);
+                         cudaStream_t st, int* launches, int variant);
+
+template <int MINB>
+cudaError_t launch_variant(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
+                           cudaStream_t st, int* launches);
 
 cudaError_t launch_gather(const Arena& a, int n, const int* ids, float* tau, float* qset, float* qdset,
                           float* value, int* status, cudaStream_t st);

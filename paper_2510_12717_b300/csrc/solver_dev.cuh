@@ -1,10 +1,17 @@
 // Device code of the batched MPC solver: one warp solves one agent.
 //
 // Lane i (< 30) owns index i of the state x and the input u (layout in
-// arena.h).  Lanes 0-21 carry the coupled base+leg block, whose stage
-// matrices are dense 22x22 blocks kept column-major with stride LD = 23 in
-// shared memory (an odd stride makes both row and column walks bank-conflict
-// free); lanes 22-29 carry the eight decoupled arm joints as scalars.
+// arena.h).  Lanes 0-21 carry the coupled base+leg block; lanes 22-29 the
+// eight decoupled arm joints as scalar problems.
+//
+// Dense 22x22 blocks (Riccati P, H_uu^-1, H_ux, K) are row-major with stride
+// 24 ("R24"): element (i, j) at i*24 + j.  A lane reading M(k, lane) walks
+// consecutive banks, and a row M(k, 0..23) is 16-byte aligned so it can be
+// broadcast with float4 loads.  The stage matrices A_k and B are sparse with
+// a fixed pattern (the model's block structure); they are kept as compact
+// columns (at most 6 nonzeros per column, values in shared memory, row
+// indices known at compile time), plus one dense column-major copy (stride
+// 23) of A_base and B for the row-oriented products of the forward rollout.
 //
 // Paper mapping (Alg. 1):
 //   f_init/f_param    -> setup_agent()   contact schedule, references, bounds,
@@ -12,7 +19,7 @@
 //   f_KKT             -> setup_agent()   linearisation (analytic Jacobians)
 //                        factor()        per-stage KKT blocks (assembly)
 //   cuDSS_fac         -> factor()        backward Riccati recursion
-//   cuDSS_solve       -> sweep()         backward/forward linear sweeps
+//   cuDSS_solve       -> sweep           backward/forward linear sweeps
 //   f_ADMM            -> admm_*()        relaxation, projection, dual update,
 //                                        residuals, rho update
 //   line search       -> alpha = 1 (the solution is the final iterate)
@@ -20,6 +27,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <math.h>
+#include <stdint.h>
 #include "arena.h"
 
 namespace mpc {
@@ -28,15 +36,20 @@ constexpr float GRAV = 9.81f;
 constexpr unsigned FULL = 0xffffffffu;
 
 // ---------------------------------------------------------------- smem map
-// per-warp shared workspace (floats)
+// per-warp shared workspace (floats); R24 blocks are BLK floats
 enum : int {
-  W_ABASE = 0, W_B = MB, W_P = 2 * MB, W_AK = 3 * MB, W_PA = 4 * MB, W_PB = 5 * MB,
-  W_H = 6 * MB, W_X = 7 * MB, W_K = 8 * MB, W_VEC = 9 * MB, NVEC = 16,
-  W_FLOATS = 9 * MB + NVEC * 64
+  S_P = 0, S_H = BLK, S_X = 2 * BLK, S_K = 3 * BLK,     // factor blocks / sweep double buffers
+  S_AB = 4 * BLK,                                        // dense A_base, column-major LD = 23
+  S_B = S_AB + 512,                                      // dense B (or B_hat), column-major LD = 23
+  S_AV = S_B + 512,                                      // compact A_k columns: 22 x 6
+  S_BV = S_AV + 136,                                     // compact B columns: 22 x 6
+  S_VEC = S_BV + 136,                                    // 12 vectors of 64
+  S_BAR = S_VEC + 12 * 64,                               // 2 mbarriers (16 bytes)
+  W_FLOATS = S_BAR + 4
 };
-// vector slots inside W_VEC (64 floats each)
-enum : int { V_S = 0, V_H = 1, V_X = 2, V_U = 3, V_XN = 4, V_ROW = 5, V_ROW2 = 6,
-             V_T = 7, V_G = 8, V_MISC = 9, V_FLAGS = 10, V_LO = 11, V_HI = 12, V_CLS = 13 };
+enum : int { V_S = 0, V_H = 1, V_X = 2, V_U = 3, V_XN = 4, V_ROW = 5, V_T = 6, V_G = 7,
+             V_C = 8, V_FLAGS = 9, V_ACT = 10, V_D = 11 };
+constexpr int LDD = 23;   // stride of the dense column-major copies
 
 struct AgentPtrs {
   const float* mdl;
@@ -69,10 +82,10 @@ __device__ __forceinline__ AgentPtrs agent_ptrs(const Arena& a, int s) {
   p.rhi = a.rhi + (size_t)s * n * RS;
   p.rcls = a.rcls + (size_t)s * n * RS;
   p.lin = a.lin + (size_t)s * lin_floats(n);
-  p.cK = a.cK + (size_t)s * n * MB;
-  p.cH = a.cH + (size_t)s * n * MB;
+  p.cK = a.cK + (size_t)s * n * BLK;
+  p.cH = a.cH + (size_t)s * n * BLK;
   p.cE = a.cE + (size_t)s * n * 64;
-  p.cB = a.cB + (size_t)s * n * MB;
+  p.cB = a.cB + (size_t)s * n * CB_F;
   p.cC = a.cC + (size_t)s * n * 64;
   p.xt = a.xt + (size_t)s * (n + 1) * VS;
   p.ut = a.ut + (size_t)s * n * VS;
@@ -96,84 +109,159 @@ __device__ __forceinline__ float warp_sum(float v) {
 }
 __device__ __forceinline__ int warp_or(int v) { return __any_sync(FULL, v); }
 
-// ------------------------------------------------- dense 22x22 warp algebra
-// Block element (i, j) sits at j*LD + i.  Lanes >= NC compute on a clamped
-// index and never store.
+// ------------------------------------------------- sparsity of A_k and B
+// Compact column j holds the nonzero rows of column j, at most 6.
+//   A = I + dt f_x:  p <- v, Theta <- Theta (pitch, yaw columns), Theta <- w,
+//                    w <- w (gyroscopic), w <- leg joints (contact dependent)
+//   B = dt f_u:      v, w <- foot forces; w <- foot moments; q_leg <- qdot_leg
+// (polish's B_hat = B G keeps the same pattern: G mixes forces within a foot)
+__host__ __device__ constexpr int acnt(int j) { return j < 4 ? 1 : j < 6 ? 3 : j < 9 ? 2 : j < 12 ? 6 : 4; }
+__host__ __device__ constexpr int arow(int j, int t) {
+  return j < 4 ? j : j < 6 ? 3 + t : j < 9 ? (t == 0 ? j : j - 6) : j < 12 ? (t < 3 ? 3 + t : 6 + t)
+                                                                          : (t == 0 ? j : 8 + t);
+}
+__host__ __device__ constexpr int bcnt(int j) { return j < 12 ? ((j % 6) < 3 ? 6 : 3) : 1; }
+__host__ __device__ constexpr int brow(int j, int t) {
+  return j < 12 ? ((j % 6) < 3 ? 6 + t : 9 + t) : j;
+}
 
-// C = op(A) op(B) (+ Cadd).  C must not alias A or B; Cadd may alias C.
-template <bool TA, bool TB>
-__device__ __forceinline__ void wgemm(float* C, const float* A, const float* B,
-                                      const float* Cadd, float alpha, int lane) {
+// ------------------------------------------------- dense R24 warp algebra
+// C = alpha * A^T B (+ Cadd):  lane i computes row i of C.  A(k, i) is read by
+// the lane (consecutive banks), B(k, 0..21) is broadcast with float4 loads.
+// C may alias Cadd but not A or B.
+__device__ __forceinline__ void r24_gemm_tn(float* C, const float* A, const float* B, const float* Cadd,
+                                            float alpha, int lane) {
+  // two passes of 12 columns keep the accumulators at 12 registers; the two
+  // padding columns (22, 23) of C are written as zero (row-vector products
+  // read them)
   const int i = lane < NC ? lane : NC - 1;
-  float acc[NC];
+  float4 out[6];
 #pragma unroll
-  for (int j = 0; j < NC; ++j) acc[j] = 0.f;
+  for (int half = 0; half < 2; ++half) {
+    float acc[12];
+#pragma unroll
+    for (int j = 0; j < 12; ++j) acc[j] = 0.f;
 #pragma unroll 2
-  for (int k = 0; k < NC; ++k) {
-    const float a = TA ? A[i * LD + k] : A[k * LD + i];
+    for (int k = 0; k < NC; ++k) {
+      const float a = A[k * R24 + i];
+      const float4* b4 = reinterpret_cast<const float4*>(B + k * R24 + 12 * half);
 #pragma unroll
-    for (int j = 0; j < NC; ++j) {
-      const float b = TB ? B[k * LD + j] : B[j * LD + k];
-      acc[j] = fmaf(a, b, acc[j]);
+      for (int m = 0; m < 3; ++m) {
+        const float4 b = b4[m];
+        acc[4 * m + 0] = fmaf(a, b.x, acc[4 * m + 0]);
+        acc[4 * m + 1] = fmaf(a, b.y, acc[4 * m + 1]);
+        acc[4 * m + 2] = fmaf(a, b.z, acc[4 * m + 2]);
+        acc[4 * m + 3] = fmaf(a, b.w, acc[4 * m + 3]);
+      }
     }
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+      out[3 * half + m] = make_float4(alpha * acc[4 * m], alpha * acc[4 * m + 1], alpha * acc[4 * m + 2],
+                                      alpha * acc[4 * m + 3]);
   }
+  out[5].z = 0.f;
+  out[5].w = 0.f;
   __syncwarp();
   if (lane < NC) {
+    float4* c4 = reinterpret_cast<float4*>(C + i * R24);
+    const float4* d4 = reinterpret_cast<const float4*>(Cadd + i * R24);
 #pragma unroll
-    for (int j = 0; j < NC; ++j) {
-      float v = alpha * acc[j];
-      if (Cadd) v += Cadd[j * LD + i];
-      C[j * LD + i] = v;
+    for (int m = 0; m < 6; ++m) {
+      float4 v = out[m];
+      if (Cadd) {
+        const float4 d = d4[m];
+        v.x += d.x; v.y += d.y;
+        if (m < 5) { v.z += d.z; v.w += d.w; }   // columns 22, 23 stay zero
+      }
+      c4[m] = v;
     }
   }
   __syncwarp();
 }
 
-// y_i = sum_j op(M)(i, j) v_j for the lane's row i (< NC)
-template <bool TM>
-__device__ __forceinline__ float wmv(const float* M, const float* v, int lane) {
+// y_i = sum_j M(j, i) v_j  (M^T v; for symmetric M this is M v)
+__device__ __forceinline__ float r24_mtv(const float* M, const float* v, int lane) {
   const int i = lane < NC ? lane : NC - 1;
   float a0 = 0.f, a1 = 0.f;
 #pragma unroll
   for (int j = 0; j < NC; j += 2) {
-    a0 = fmaf(TM ? M[i * LD + j] : M[j * LD + i], v[j], a0);
-    a1 = fmaf(TM ? M[i * LD + j + 1] : M[(j + 1) * LD + i], v[j + 1], a1);
+    a0 = fmaf(M[j * R24 + i], v[j], a0);
+    a1 = fmaf(M[(j + 1) * R24 + i], v[j + 1], a1);
+  }
+  return a0 + a1;
+}
+// y_i = sum_j M(i, j) v_j  (row of the lane, float4 loads)
+__device__ __forceinline__ float r24_mv(const float* M, const float* v, int lane) {
+  const int i = lane < NC ? lane : NC - 1;
+  const float4* m4 = reinterpret_cast<const float4*>(M + i * R24);
+  const float4* v4 = reinterpret_cast<const float4*>(v);
+  float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+  for (int m = 0; m < 6; ++m) {
+    const float4 a = m4[m], b = v4[m];
+    a0 = fmaf(a.x, b.x, a0); a1 = fmaf(a.y, b.y, a1);
+    a0 = fmaf(a.z, b.z, a0); a1 = fmaf(a.w, b.w, a1);
   }
   return a0 + a1;
 }
 
-// In-place inverse of a symmetric positive definite block by Gauss-Jordan
+// In-place inverse of a symmetric positive definite R24 block by Gauss-Jordan
 // elimination without pivoting; lane j updates column j.
-__device__ __forceinline__ void winv(float* H, int lane) {
+__device__ __forceinline__ void r24_inv(float* H, int lane) {
   const int j = lane < NC ? lane : NC - 1;
   for (int p = 0; p < NC; ++p) {
     float col[NC];
 #pragma unroll
-    for (int i = 0; i < NC; ++i) col[i] = H[p * LD + i];
-    const float rowp = H[j * LD + p];
+    for (int i = 0; i < NC; ++i) col[i] = H[i * R24 + p];
+    const float rowp = H[p * R24 + j];
     const float inv = 1.f / col[p];
     __syncwarp();
     if (lane < NC) {
       if (j == p) {
 #pragma unroll
-        for (int i = 0; i < NC; ++i) H[j * LD + i] = (i == p) ? inv : -col[i] * inv;
+        for (int i = 0; i < NC; ++i) H[i * R24 + j] = (i == p) ? inv : -col[i] * inv;
       } else {
         const float rp = rowp * inv;
 #pragma unroll
-        for (int i = 0; i < NC; ++i)
-          H[j * LD + i] = (i == p) ? rp : fmaf(-col[i], rp, H[j * LD + i]);
+        for (int i = 0; i < NC; ++i) H[i * R24 + j] = (i == p) ? rp : fmaf(-col[i], rp, H[i * R24 + j]);
       }
     }
     __syncwarp();
   }
 }
 
-// copy a 22x22 block (MB floats) between memories, whole warp
-__device__ __forceinline__ void wcopy_block(float* dst, const float* src, int lane) {
-  const float4* s4 = reinterpret_cast<const float4*>(src);
-  float4* d4 = reinterpret_cast<float4*>(dst);
+// dense column-major (LDD) mat-vec, lane row i: sum_j M(i, j) v_j
+__device__ __forceinline__ float cm_mv(const float* M, const float* v, int lane) {
+  const int i = lane < NC ? lane : NC - 1;
+  float a0 = 0.f, a1 = 0.f;
 #pragma unroll
-  for (int t = lane; t < MB / 4; t += 32) d4[t] = s4[t];
+  for (int j = 0; j < NC; j += 2) {
+    a0 = fmaf(M[j * LDD + i], v[j], a0);
+    a1 = fmaf(M[(j + 1) * LDD + i], v[j + 1], a1);
+  }
+  return a0 + a1;
+}
+
+// compact-column transposed products for the lane's own column i:
+// (A^T v)_i = sum_t A(arow(i,t), i) v[arow(i,t)]; runtime lane, so the
+// pattern is read from per-lane registers filled by load_pattern().
+struct LanePat { int ar[6], br[6]; };
+__device__ __forceinline__ LanePat lane_pattern(int lane) {
+  LanePat p;
+  const int j = lane < NC ? lane : 0;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    p.ar[t] = t < acnt(j) ? arow(j, t) : 0;
+    p.br[t] = t < bcnt(j) ? brow(j, t) : 0;
+  }
+  return p;
+}
+__device__ __forceinline__ float cc_tv(const float* val, const int* rows, const float* v, int lane) {
+  const int j = lane < NC ? lane : 0;
+  float a = 0.f;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) a = fmaf(val[j * 6 + t], v[rows[t]], a);
+  return a;
 }
 
 // ----------------------------------------------------------- row algebra
@@ -192,10 +280,6 @@ __device__ __forceinline__ float cuT(const float* v, int i, float mu) {
     return r;
   }
   return i < 30 ? v[i + 8] : 0.f;
-}
-// (C_x^T v)_i for x index i
-__device__ __forceinline__ float cxT(const float* v, int i) {
-  return (i >= 12 && i < 30) ? v[i + 26] : 0.f;
 }
 // row value r of C_u u + C_x xn
 __device__ __forceinline__ float crow(const float* u, const float* xn, int r, float mu) {
@@ -229,6 +313,46 @@ __device__ __forceinline__ M3 mul3(const M3& a, const M3& b) {
 __device__ __forceinline__ M3 skew3(float x, float y, float z) {
   M3 s = {{0.f, -z, y, z, 0.f, -x, -y, x, 0.f}};
   return s;
+}
+
+// ------------------------------------------------- TMA bulk copies (1D)
+// cp.async.bulk global -> shared, completion counted on an mbarrier.  Waits
+// are bounded: after kSpinLimit polls the wait gives up and reports it.
+constexpr int kSpinLimit = 1 << 22;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+// returns false if the phase did not complete within the spin limit
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+  uint32_t done = 0;
+  for (int it = 0; it < kSpinLimit; ++it) {
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
 }
 
 }  // namespace mpc

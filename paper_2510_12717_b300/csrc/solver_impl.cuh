@@ -1,0 +1,1458 @@
+// Kernels of the batched MPC solver (sm_103a).  One warp per agent.
+// Included by one translation unit per kernel variant (solver_v*.cu).
+//
+// Two launch forms of the same device steps:
+//   plain : mpc_k_setup -> mpc_k_factor -> mpc_k_admm -> mpc_k_polish -> mpc_k_torque,
+//           one launch per step, all intermediates in the global arenas;
+//   fused : mpc_k_fused runs every step of an agent in one warp, keeping the
+//           constant stage matrices in shared memory between steps.
+// Both run the same sequence: ADMM with residual checks, rho updates and an
+// early polish attempt once the residuals are within 100x of the tolerance;
+// a final polish after ADMM if none was accepted; the torque map.
+#pragma once
+#include "solver_dev.cuh"
+#include "solver.h"
+
+namespace mpc {
+namespace {   // everything but launch_variant is private to the variant's translation unit
+
+// ============================================================ small helpers
+// diagonal of the x_k block of the ADMM KKT matrix (k >= 1): 2 dt Q + sigma
+// + rho on the joint-box row of stage k-1
+__device__ __forceinline__ float qt_x(const AgentPtrs& ap, int k, int i, float rho, float sigma) {
+  const float* md = ap.mdl;
+  float v = 2.f * md[M_DT] * md[M_Q + i] + sigma;
+  if (i >= 12 && i < 30) v += rho * ap.rcls[(k - 1) * RS + i + 26];
+  return v;
+}
+
+// A_k x for the coupled block, lane row: dense A_base (column-major) plus
+// the contact-dependent block dA_k (rows 9-11 x columns 12-21)
+__device__ __forceinline__ float ak_mv(const float* Ab, const float* dA, const float* v, int lane) {
+  float r = cm_mv(Ab, v, lane);
+  if (lane >= 9 && lane < 12) {
+    const float* row = dA + (lane - 9) * 10;
+#pragma unroll
+    for (int c = 0; c < 10; ++c) r = fmaf(row[c], v[12 + c], r);
+  }
+  return r;
+}
+
+// compact A values of stage k: the leg-joint columns take dA_k
+__device__ __forceinline__ void set_stage_A(float* sm, const float* dA, int lane) {
+  if (lane >= 12 && lane < NC) {
+    float* av = sm + S_AV + lane * 6;
+#pragma unroll
+    for (int t = 1; t < 4; ++t) av[t] = dA[(t - 1) * 10 + (lane - 12)];
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void copy_n(float* dst, const float* src, int n4, int lane) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+  float4* d4 = reinterpret_cast<float4*>(dst);
+  for (int t = lane; t < n4; t += 32) d4[t] = s4[t];
+}
+__device__ __forceinline__ void copy_blk(float* dst, const float* src, int lane) { copy_n(dst, src, BLK / 4, lane); }
+// ============================================================ setup (A1, A2)
+// Contact schedule, references, bounds (f_param), analytic linearisation
+// about x0 and u_ref (f_KKT Jacobians), warm or cold start (f_init).
+// Returns false (agent marked NaN) when an input is not finite.
+__device__ __noinline__ bool setup_agent(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm) {
+  const int N = ap.N;
+  const float* md = ap.mdl;
+  float* vec = sm + S_VEC;
+  float* xbar = vec + V_X * 64;
+  int* flags = reinterpret_cast<int*>(vec + V_FLAGS * 64);
+
+  const float xi = lane < 30 ? ap.inp[I_X0 + lane] : 0.f;
+  bool bad = lane < 30 && !isfinite(xi);
+  if (lane < 18) bad |= !isfinite(ap.inp[I_QD + lane]);
+  if (lane < 5) bad |= !isfinite(ap.inp[I_CMD + lane]);
+  if (warp_or(bad)) return false;
+  xbar[lane] = xi;
+
+  // contact schedule (double precision, no contraction): lane k -> stage k
+  if (lane < N) {
+    const double step = __ddiv_rn(ap.sch[S_DT], ap.sch[S_PERIOD]);
+    double ph = __dadd_rn((double)ap.inp[I_PHASE], __dmul_rn((double)lane, step));
+    ph = __dsub_rn(ph, floor(ph));
+    int f = 0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      double s = __dadd_rn(ph, ap.sch[S_OFF + i]);
+      s = __dsub_rn(s, floor(s));
+      if (s < ap.sch[S_DUTY + i]) f |= 1 << i;
+    }
+    flags[lane] = f;
+  }
+  __syncwarp();
+
+  const float fzmax = md[M_FZMAX], qdmax = md[M_QDMAX], qlim = md[M_QLIM];
+  // stage bounds: lane k writes the 56 rows of stage k
+  if (lane < N) {
+    const int f = flags[lane];
+    float* lo = ap.rlo + lane * RS;
+    float* hi = ap.rhi + lane * RS;
+    float* cl = ap.rcls + lane * RS;
+    for (int i = 0; i < 2; ++i) {
+      const int b = 6 * i, p = 12 + 4 * i;
+      const bool stance = (f >> i) & 1;
+      for (int c = 0; c < 6; ++c) {
+        if (stance) {
+          const bool z = (c == 2);
+          lo[b + c] = z ? 0.f : -INFINITY;
+          hi[b + c] = z ? fzmax : INFINITY;
+          cl[b + c] = z ? 1.f : 0.f;
+        } else {
+          lo[b + c] = 0.f;
+          hi[b + c] = 0.f;
+          cl[b + c] = 1000.f;
+        }
+      }
+      for (int t = 0; t < 4; ++t) {
+        lo[p + t] = -INFINITY;
+        hi[p + t] = stance ? 0.f : INFINITY;
+        cl[p + t] = stance ? 1.f : 0.f;
+      }
+    }
+    for (int j = 0; j < 18; ++j) {
+      lo[20 + j] = -qdmax; hi[20 + j] = qdmax; cl[20 + j] = 1.f;
+      lo[38 + j] = -qlim;  hi[38 + j] = qlim;  cl[38 + j] = 1.f;
+    }
+  }
+
+  // references: desired trajectory (Eqs. des_traj_1..5) and force split
+  const float dt = md[M_DT];
+  const float ch = ap.inp[I_CMD], cvx = ap.inp[I_CMD + 1], cvy = ap.inp[I_CMD + 2], cwz = ap.inp[I_CMD + 3];
+  for (int k = 0; k <= N; ++k) {
+    const float yaw = xbar[5] + ((float)k * dt) * cwz;
+    float v = 0.f;
+    if (lane == 2) v = ch;
+    else if (lane == 5) v = yaw;
+    else if (lane == 6) v = cosf(yaw) * cvx - sinf(yaw) * cvy;
+    else if (lane == 7) v = sinf(yaw) * cvx + cosf(yaw) * cvy;
+    else if (lane == 11) v = cwz;
+    else if (lane >= 12 && lane < 30) v = md[M_QNOM + lane - 12];
+    ap.xref[k * VS + lane] = v;
+  }
+  const float weight = md[M_MASS] * GRAV;
+  for (int k = 0; k < N; ++k) {
+    const int f = flags[k];
+    const float share = weight / (float)__popc(f);
+    float v = 0.f;
+    if (lane == 2 && (f & 1)) v = share;
+    if (lane == 8 && (f & 2)) v = share;
+    ap.uref[k * VS + lane] = v;
+  }
+
+  // ---- linearisation about (x0, u_ref_k): analytic Jacobians, forward Euler
+  const float roll = xbar[3], pitch = xbar[4], yaw0 = xbar[5];
+  const float cr = cosf(roll), sr = sinf(roll), cp = cosf(pitch), sp = sinf(pitch);
+  const float cy = cosf(yaw0), sy = sinf(yaw0);
+  const M3 R = {{cy * cp, cy * sp * sr - sy * cr, cy * sp * cr + sy * sr,
+                 sy * cp, sy * sp * sr + cy * cr, sy * sp * cr - cy * sr,
+                 -sp, cp * sr, cp * cr}};
+  const float I0 = md[M_INERTIA], I1 = md[M_INERTIA + 1], I2 = md[M_INERTIA + 2];
+  M3 Iw, Iwi;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      Iw.m[3 * r + c] = m3(R, r, 0) * I0 * m3(R, c, 0) + m3(R, r, 1) * I1 * m3(R, c, 1) + m3(R, r, 2) * I2 * m3(R, c, 2);
+      Iwi.m[3 * r + c] = m3(R, r, 0) / I0 * m3(R, c, 0) + m3(R, r, 1) / I1 * m3(R, c, 1) + m3(R, r, 2) / I2 * m3(R, c, 2);
+    }
+  const float w0 = xbar[9], w1 = xbar[10], w2 = xbar[11];
+  const float ic = 1.f / cp, tp = sp * ic;
+  const M3 Einv = {{cy * ic, sy * ic, 0.f, -sy, cy, 0.f, cy * tp, sy * tp, 1.f}};
+  const float ea = cy * w0 + sy * w1, eb = -sy * w0 + cy * w1;
+  // d(E^-1 w)/dTheta, columns (roll, pitch, yaw)
+  const M3 dE = {{0.f, ea * sp * ic * ic, eb * ic, 0.f, 0.f, -ea, 0.f, ea * ic * ic, tp * eb}};
+  const float Iww0 = Iw.m[0] * w0 + Iw.m[1] * w1 + Iw.m[2] * w2;
+  const float Iww1 = Iw.m[3] * w0 + Iw.m[4] * w1 + Iw.m[5] * w2;
+  const float Iww2 = Iw.m[6] * w0 + Iw.m[7] * w1 + Iw.m[8] * w2;
+  // gyroscopic Jacobian: I_w^-1 (-[w]x I_w + [I_w w]x)
+  M3 sw = skew3(w0, w1, w2), sIw = skew3(Iww0, Iww1, Iww2);
+  M3 swI = mul3(sw, Iw);
+  M3 gin;
+#pragma unroll
+  for (int t = 0; t < 9; ++t) gin.m[t] = sIw.m[t] - swI.m[t];
+  const M3 gyro = mul3(Iwi, gin);
+  // foot levers r_i(q) = lever_i + J_r,i (q_leg,i - q_nom,leg,i)
+  float rl[2][3];
+#pragma unroll
+  for (int f = 0; f < 2; ++f)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      float v = md[M_LEVER + 3 * f + c];
+      for (int j = 0; j < 5; ++j)
+        v += md[M_JLEG + 30 * f + 5 * c + j] * (xbar[12 + 5 * f + j] - md[M_QNOM + 5 * f + j]);
+      rl[f][c] = v;
+    }
+  const float invm = md[M_INVM];
+
+  // A_base = I + dt f_x (without the contact-dependent leg coupling) and
+  // B = dt f_u, dense column-major: lane j fills column j
+  float* Ab = sm + S_AB;
+  float* Bm = sm + S_B;
+  if (lane < NC) {
+    const int j = lane;
+    for (int i = 0; i < NC; ++i) {
+      float a = (i == j) ? 1.f : 0.f;
+      if (i < 3 && j == i + 6) a += dt;
+      if (i >= 3 && i < 6 && j >= 3 && j < 6) a += dt * m3(dE, i - 3, j - 3);
+      if (i >= 3 && i < 6 && j >= 9 && j < 12) a += dt * m3(Einv, i - 3, j - 9);
+      if (i >= 9 && i < 12 && j >= 9 && j < 12) a += dt * m3(gyro, i - 9, j - 9);
+      Ab[j * LDD + i] = a;
+      float b = 0.f;
+      if (i >= 6 && i < 9 && (j == i - 6 || j == i)) b = dt * invm;
+      if (i >= 9 && i < 12 && j < 12) {
+        const int f = j / 6, c = j - 6 * f, r = i - 9;
+        if (c < 3) {
+          // I_w^-1 [r_f]x, column c
+          const M3 S = skew3(rl[f][0], rl[f][1], rl[f][2]);
+          b = dt * (m3(Iwi, r, 0) * m3(S, 0, c) + m3(Iwi, r, 1) * m3(S, 1, c) + m3(Iwi, r, 2) * m3(S, 2, c));
+        } else {
+          b = dt * m3(Iwi, r, c - 3);
+        }
+      }
+      if (i >= 12 && j == i) b = dt;
+      Bm[j * LDD + i] = b;
+    }
+  }
+  __syncwarp();
+  // compact columns of A_base and B
+  if (lane < NC) {
+    const int j = lane;
+    for (int t = 0; t < 6; ++t) {
+      sm[S_AV + j * 6 + t] = t < acnt(j) ? Ab[j * LDD + arow(j, t)] : 0.f;
+      sm[S_BV + j * 6 + t] = t < bcnt(j) ? Bm[j * LDD + brow(j, t)] : 0.f;
+    }
+  }
+  __syncwarp();
+  // stash for the separate-kernel form and the factor's reloads
+  copy_n(ap.lin + L_ABASE, Ab, 2 * MB / 4, lane);
+  copy_n(ap.lin + L_AV, sm + S_AV, 272 / 4, lane);
+
+  // per stage: dA_k = dt dw/dq_leg (depends on the stance forces of u_ref_k)
+  // and c_k = x0 + dt f(x0, u_ref_k) - A_k x0 - B u_ref_k
+  for (int k = 0; k < N; ++k) {
+    float* st = ap.lin + L_STAGE + k * 64;
+    const float FL = ap.uref[k * VS + 2], FR = ap.uref[k * VS + 8];
+    if (lane < 30) {
+      const int r = lane / 10, col = lane - 10 * r, f = col / 5, j = col - 5 * f;
+      const float F = f ? FR : FL;
+      const float jr0 = md[M_JLEG + 30 * f + 0 * 5 + j], jr1 = md[M_JLEG + 30 * f + 1 * 5 + j];
+      st[lane] = dt * F * (m3(Iwi, r, 0) * jr1 - m3(Iwi, r, 1) * jr0);
+    }
+    __syncwarp();
+    if (lane < NC) {
+      const int i = lane;
+      float f0 = 0.f;
+      if (i < 3) f0 = xbar[6 + i];
+      else if (i < 6) f0 = m3(Einv, i - 3, 0) * w0 + m3(Einv, i - 3, 1) * w1 + m3(Einv, i - 3, 2) * w2;
+      else if (i < 9) f0 = (i == 8) ? (FL + FR) * invm - GRAV : 0.f;
+      else if (i < 12) {
+        // I_w^-1 (r_L x f_L + r_R x f_R - w x I_w w) with f = (0, 0, F)
+        const float t0 = rl[0][1] * FL + rl[1][1] * FR - (w1 * Iww2 - w2 * Iww1);
+        const float t1 = -rl[0][0] * FL - rl[1][0] * FR - (w2 * Iww0 - w0 * Iww2);
+        const float t2 = -(w0 * Iww1 - w1 * Iww0);
+        const int r = i - 9;
+        f0 = m3(Iwi, r, 0) * t0 + m3(Iwi, r, 1) * t1 + m3(Iwi, r, 2) * t2;
+      }
+      const float Ax = ak_mv(Ab, st, xbar, lane);
+      const float Bu = Bm[2 * LDD + i] * FL + Bm[8 * LDD + i] * FR;
+      st[32 + i] = xbar[i] + dt * f0 - Ax - Bu;
+    }
+    __syncwarp();
+  }
+
+  // warm or cold start (f_init: the current pose repeated over the horizon,
+  // everything else zero; duals zero)
+  const bool warm = prm.warm_start && (*ap.warm == N);
+  if (!warm) {
+    for (int k = 0; k <= N; ++k) {
+      float v = 0.f;
+      if (lane < 6) v = xbar[lane];
+      else if (lane >= 12 && lane < 30) v = md[M_QNOM + lane - 12];
+      ap.x[k * VS + lane] = v;
+    }
+    for (int k = 0; k < N; ++k) ap.u[k * VS + lane] = 0.f;
+    __syncwarp();
+    for (int k = 0; k < N; ++k) {
+      for (int r = lane; r < NR; r += 32) {
+        const float v = (r >= 38) ? md[M_QNOM + r - 38] : 0.f;
+        ap.w[k * RS + r] = fminf(fmaxf(v, ap.rlo[k * RS + r]), ap.rhi[k * RS + r]);
+        ap.y[k * RS + r] = 0.f;
+      }
+    }
+    if (lane == 0) *ap.rho = prm.rho0;
+  }
+  ap.x[lane] = xbar[lane];
+  __syncwarp();
+  return true;
+}
+
+// load the constant stage matrices (dense A_base, B and their compact
+// columns) of the agent into smem
+__device__ __forceinline__ void load_lin(const AgentPtrs& ap, float* sm, int lane) {
+  copy_n(sm + S_AB, ap.lin + L_ABASE, 2 * MB / 4, lane);
+  copy_n(sm + S_AV, ap.lin + L_AV, 272 / 4, lane);
+  __syncwarp();
+}
+
+// ============================================================ factor (A3, A4)
+// Backward Riccati recursion on the stage blocks of the KKT system of the
+// ADMM x-update (P + sigma I + rho C^T C, dynamics as exact constraints).
+// Per stage, lane j forms column j of P A_k and P B from the compact columns
+// (at most 6 terms each), then column j of
+//   H_uu = R_t + B^T (P B),  H_ux = B^T (P A),  T = A^T (P A)
+// with compile-time sparsity; H_uu is inverted (Gauss-Jordan), K = -H_uu^-1 H_ux
+// and P <- T + H_ux^T K + diag(Q_t).  Caches per stage: K_k, H_uu,k^-1 (R24),
+// e_k = P_{k+1} c_k, and the arm lanes' scalar gain, inverse and e.
+// The polish step runs the same recursion on its reduced problem.
+struct StageIn {
+  const float* c;     // affine term c_k of the coupled lanes (smem vector)
+  float rt_diag;      // this lane's diagonal of R_t
+  float rt_off[3];    // force lanes: R_t(row b+r, j) of the foot block; arm lanes: [0] = B, [1] = c
+  float qt;           // this lane's diagonal of Q_t for x_k (k >= 1)
+};
+
+__device__ __forceinline__ void factor_stage(const AgentPtrs& ap, float* sm, int lane, int k,
+                                             const StageIn& in, float* Pa, const LanePat& pat) {
+  float* P = sm + S_P; float* H = sm + S_H; float* X = sm + S_X; float* K = sm + S_K;
+  const float* av = sm + S_AV;
+  const float* bv = sm + S_BV;
+  const int j = lane < NC ? lane : NC - 1;
+  // e = P c (before P is overwritten)
+  const float e = r24_mtv(P, in.c, lane);
+  // lane j: column j of P B, then H(:, j) = B^T (P B)(:, j) (H, X are not
+  // read by other lanes before the next barrier, so they are written at once)
+  {
+    float pb[NC];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) pb[i] = 0.f;
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      const float b = bv[j * 6 + t];
+      const int rb = pat.br[t];
+#pragma unroll
+      for (int i = 0; i < NC; ++i) pb[i] = fmaf(P[i * R24 + rb], b, pb[i]);
+    }
+    if (lane < NC) {
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        float h = 0.f;
+#pragma unroll
+        for (int t = 0; t < 6; ++t)
+          if (t < bcnt(i)) h = fmaf(bv[i * 6 + t], pb[brow(i, t)], h);
+        H[i * R24 + j] = h;
+      }
+    }
+  }
+  // column j of P A_k, then X(:, j) = B^T (P A)(:, j) and T(:, j) = A^T (P A)(:, j)
+  float pa[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) pa[i] = 0.f;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) {
+    const float a = av[j * 6 + t];
+    const int ra = pat.ar[t];
+#pragma unroll
+    for (int i = 0; i < NC; ++i) pa[i] = fmaf(P[i * R24 + ra], a, pa[i]);
+  }
+  if (lane < NC) {
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      float x = 0.f;
+#pragma unroll
+      for (int t = 0; t < 6; ++t)
+        if (t < bcnt(i)) x = fmaf(bv[i * 6 + t], pa[brow(i, t)], x);
+      X[i * R24 + j] = x;
+    }
+  }
+  __syncwarp();   // every lane has read P: T may overwrite it
+  if (lane < NC) {
+#pragma unroll
+    for (int i = 0; i < NC; ++i) {
+      float tt = 0.f;
+#pragma unroll
+      for (int t = 0; t < 6; ++t)
+        if (t < acnt(i)) tt = fmaf(av[i * 6 + t], pa[arow(i, t)], tt);
+      P[i * R24 + j] = tt;
+    }
+    // + R_t column j: its diagonal and, for a force lane, its foot block
+    H[j * R24 + j] += in.rt_diag;
+    if (j < 12 && (j % 6) < 3) {
+      const int b = (j / 6) * 6;
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+        if (b + r != j) H[(b + r) * R24 + j] += in.rt_off[r];
+    }
+  }
+  __syncwarp();
+  r24_inv(H, lane);
+  r24_gemm_tn(K, H, X, nullptr, -1.f, lane);     // K = -H_uu^-1 H_ux (H_uu^-1 symmetric)
+  copy_blk(ap.cK + (size_t)k * BLK, K, lane);
+  copy_blk(ap.cH + (size_t)k * BLK, H, lane);
+  float* ce = ap.cE + k * 64;
+  if (lane < NC) ce[lane] = e;
+  // arm lanes: scalar Riccati, A = 1
+  if (lane >= NC && lane < 30) {
+    const float Bh = in.rt_off[0];
+    const float Huu = in.rt_diag + Bh * Bh * (*Pa);
+    const float Hux = Bh * (*Pa);
+    const float Hi = 1.f / Huu;
+    const float Ka = -Hi * Hux;
+    ce[lane] = Ka;
+    ce[32 + lane] = Hi;
+    ce[32 + lane - NC] = (*Pa) * in.rt_off[1];   // e of the arm lane
+    if (k >= 1) *Pa = in.qt + *Pa + Hux * Ka;
+  }
+  if (k >= 1) {
+    r24_gemm_tn(P, X, K, P, 1.f, lane);          // P = A^T P A + H_ux^T K
+    float t[NC];
+    if (lane < NC) {
+#pragma unroll
+      for (int i = 0; i < NC; ++i) t[i] = 0.5f * (P[i * R24 + j] + P[j * R24 + i]);
+    }
+    __syncwarp();
+    if (lane < NC) {
+#pragma unroll
+      for (int i = 0; i < NC; ++i) P[i * R24 + j] = t[i];
+      P[j * R24 + j] += in.qt;
+    }
+  }
+  __syncwarp();
+}
+
+// ADMM stage inputs: R_t = 2 dt R + sigma I + rho C_u^T diag(cls) C_u
+__device__ __forceinline__ StageIn admm_stage_in(const AgentPtrs& ap, int k, float rho, float sigma,
+                                                 float* cvec, int lane) {
+  const float* md = ap.mdl;
+  const float dt = md[M_DT], mu = md[M_MU];
+  const float* rc = ap.rcls + k * RS;
+  StageIn in;
+  in.c = cvec;
+  in.rt_off[0] = in.rt_off[1] = in.rt_off[2] = 0.f;
+  in.rt_diag = 0.f;
+  in.qt = (k >= 1 && lane < 30) ? qt_x(ap, k, lane, rho, sigma) : 0.f;
+  if (lane < NC) {
+    const int j = lane;
+    const int row = j < 12 ? j : j + 8;
+    float d = 2.f * dt * md[M_R + j] + sigma + rho * rc[row];
+    if (j < 12 && (j % 6) < 3) {
+      const int f = j / 6, c = j - 6 * f, p = 12 + 4 * f;
+      const float r0 = rho * rc[p], r1 = rho * rc[p + 1], r2 = rho * rc[p + 2], r3 = rho * rc[p + 3];
+      if (c == 0) { d += r0 + r1; in.rt_off[2] = mu * (r1 - r0); }
+      if (c == 1) { d += r2 + r3; in.rt_off[2] = mu * (r3 - r2); }
+      if (c == 2) {
+        d += mu * mu * (r0 + r1 + r2 + r3);
+        in.rt_off[0] = mu * (r1 - r0);
+        in.rt_off[1] = mu * (r3 - r2);
+      }
+    }
+    in.rt_diag = d;
+    cvec[lane] = ap.lin[L_STAGE + k * 64 + 32 + lane];
+  } else if (lane < 30) {
+    in.rt_diag = 2.f * dt * md[M_R + lane] + sigma + rho * rc[lane + 8];
+    in.rt_off[0] = dt;     // arm B
+    in.rt_off[1] = 0.f;    // arm c
+  }
+  __syncwarp();
+  return in;
+}
+
+__device__ __noinline__ void factor_admm(const AgentPtrs& ap, float* sm, int lane, float rho, float sigma, const LanePat& pat) {
+  const int N = ap.N;
+  float* P = sm + S_P;
+  float* cvec = sm + S_VEC + V_C * 64;
+  const int j = lane < NC ? lane : NC - 1;
+  copy_n(sm + S_BV, ap.lin + L_BV, 136 / 4, lane);   // compact B of the ADMM problem
+  if (lane < NC) {
+    for (int i = 0; i < NC; ++i) P[i * R24 + j] = 0.f;
+    P[j * R24 + j] = qt_x(ap, N, j, rho, sigma);
+  }
+  float Pa = (lane >= NC && lane < 30) ? qt_x(ap, N, lane, rho, sigma) : 0.f;
+  __syncwarp();
+  for (int k = N - 1; k >= 0; --k) {
+    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
+    const StageIn in = admm_stage_in(ap, k, rho, sigma, cvec, lane);
+    factor_stage(ap, sm, lane, k, in, &Pa, pat);
+  }
+  // the caches were written with generic stores and are read back through
+  // the async (TMA) proxy
+  fence_proxy_async();
+  __syncwarp();
+}
+
+// ============================================================ ADMM iteration (A5)
+// One OSQP iteration with the equality-constrained KKT solve done by the
+// cached Riccati factors (backward linear sweep + forward rollout), then
+// relaxation, projection onto [lo, hi] and the dual update, stage by stage.
+// The per-stage blocks K_k, H_uu,k^-1 are prefetched one stage ahead into two
+// shared-memory buffers with TMA bulk copies (completion on an mbarrier).
+struct Pipe {
+  uint64_t* bar;
+  uint32_t ph[2];
+  int timeout;
+};
+
+__device__ __forceinline__ void pipe_init(Pipe& pp, float* sm, int lane) {
+  pp.bar = reinterpret_cast<uint64_t*>(sm + S_BAR);
+  pp.ph[0] = pp.ph[1] = 0;
+  pp.timeout = 0;
+  if (lane == 0) {
+    mbar_init(pp.bar, 1);
+    mbar_init(pp.bar + 1, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+}
+__device__ __forceinline__ void pipe_issue(Pipe& pp, int b, float* dstK, const float* srcK, float* dstH,
+                                           const float* srcH, int lane) {
+  if (lane == 0) {
+    fence_proxy_async();
+    const uint32_t bytes = (uint32_t)(BLK * sizeof(float));
+    mbar_expect_tx(pp.bar + b, dstH ? 2 * bytes : bytes);
+    tma_load_1d(dstK, srcK, bytes, pp.bar + b);
+    if (dstH) tma_load_1d(dstH, srcH, bytes, pp.bar + b);
+  }
+}
+__device__ __forceinline__ void pipe_wait(Pipe& pp, int b) {
+  if (!mbar_wait(pp.bar + b, pp.ph[b])) pp.timeout = 1;
+  pp.ph[b] ^= 1u;
+}
+
+__device__ void admm_iteration(const AgentPtrs& ap, float* sm, int lane, float rho, const SolverParams& prm,
+                               Pipe& pp, const LanePat& pat) {
+  const int N = ap.N;
+  const float* md = ap.mdl;
+  const float dt = md[M_DT], mu = md[M_MU], sigma = prm.sigma, alpha = prm.alpha;
+  float* Ab = sm + S_AB; float* Bm = sm + S_B;
+  float* const K0 = sm + S_P; float* const K1 = sm + S_X;
+  float* const H0 = sm + S_H; float* const H1 = sm + S_K;
+  float* vec = sm + S_VEC;
+  float* vS = vec + V_S * 64; float* vH = vec + V_H * 64; float* vX = vec + V_X * 64;
+  float* vU = vec + V_U * 64; float* vXN = vec + V_XN * 64; float* vR = vec + V_ROW * 64;
+  const bool arm = lane >= NC && lane < 30;
+  const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
+  const float twoR = lane < 30 ? 2.f * dt * md[M_R + lane] : 0.f;
+
+  // linear term of x_k (k >= 1): -2dt Q xr_k - sigma x_k - C_x^T (rho w - y) of stage k-1
+  auto qlin = [&](int k) -> float {
+    float v = -twoQ * ap.xref[k * VS + lane] - sigma * ap.x[k * VS + lane];
+    if (lane >= 12 && lane < 30) {
+      const int r = lane + 26;
+      v -= rho * ap.rcls[(k - 1) * RS + r] * ap.w[(k - 1) * RS + r] - ap.y[(k - 1) * RS + r];
+    }
+    return v;
+  };
+  // ---- backward sweep: p_k, d_k
+  pipe_issue(pp, 0, K0, ap.cK + (size_t)(N - 1) * BLK, H0, ap.cH + (size_t)(N - 1) * BLK, lane);
+  float p = lane < 30 ? qlin(N) : 0.f;
+  for (int k = N - 1; k >= 0; --k) {
+    const int b = (N - 1 - k) & 1;
+    float* const Kc = b ? K1 : K0;
+    float* const Hc = b ? H1 : H0;
+    if (k >= 1)
+      pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k - 1) * BLK, b ? H0 : H1, ap.cH + (size_t)(k - 1) * BLK,
+                 lane);
+    const float* ce = ap.cE + k * 64;
+    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
+    for (int r = lane; r < NR; r += 32)
+      vR[r] = rho * ap.rcls[k * RS + r] * ap.w[k * RS + r] - ap.y[k * RS + r];
+    const float s = (lane < NC ? ce[lane] : 0.f) + p;
+    vS[lane] = s;
+    __syncwarp();
+    float h = 0.f;
+    if (lane < 30) {
+      const float rlin = -twoR * ap.uref[k * VS + lane] - sigma * ap.u[k * VS + lane] - cuT(vR, lane, mu);
+      h = rlin + (lane < NC ? cc_tv(sm + S_BV, pat.br, vS, lane) : dt * s);
+    }
+    vH[lane] = h;
+    float pn = 0.f;
+    if (k >= 1 && lane < 30) pn = qlin(k) + (lane < NC ? cc_tv(sm + S_AV, pat.ar, vS, lane) : s);
+    pipe_wait(pp, b);
+    __syncwarp();
+    float d = 0.f;
+    if (lane < NC) d = -r24_mtv(Hc, vH, lane);
+    else if (arm) d = -ce[32 + lane] * h;
+    ap.dv[k * VS + lane] = d;
+    if (k >= 1) {
+      if (lane < NC) pn += r24_mtv(Kc, vH, lane);
+      else if (arm) pn += ce[lane] * h;
+      p = pn;
+    }
+    __syncwarp();
+  }
+
+  // ---- forward rollout + per-stage relaxation / projection / dual update
+  float x = lane < 30 ? ap.x[lane] : 0.f;   // x_0 = x0
+  pipe_issue(pp, 0, K0, ap.cK, nullptr, nullptr, lane);
+  for (int k = 0; k < N; ++k) {
+    const int b = k & 1;
+    float* const Kc = b ? K1 : K0;
+    if (k + 1 < N) pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k + 1) * BLK, nullptr, nullptr, lane);
+    const float* ce = ap.cE + k * 64;
+    const float* dA = ap.lin + L_STAGE + k * 64;
+    vX[lane] = x;
+    const float dk = ap.dv[k * VS + lane];
+    pipe_wait(pp, b);
+    __syncwarp();
+    float u = 0.f;
+    if (lane < NC) u = r24_mv(Kc, vX, lane) + dk;
+    else if (arm) u = ce[lane] * x + dk;
+    vU[lane] = u;
+    __syncwarp();
+    float xn = 0.f;
+    if (lane < NC) xn = ak_mv(Ab, dA, vX, lane) + cm_mv(Bm, vU, lane) + dA[32 + lane];
+    else if (arm) xn = x + dt * u;
+    vXN[lane] = xn;
+    ap.xt[(k + 1) * VS + lane] = xn;
+    ap.ut[k * VS + lane] = u;
+    __syncwarp();
+    for (int r = lane; r < NR; r += 32) {
+      const float zt = crow(vU, vXN, r, mu);
+      const float wo = ap.w[k * RS + r], yo = ap.y[k * RS + r];
+      const float wh = alpha * zt + (1.f - alpha) * wo;
+      const float rr = rho * ap.rcls[k * RS + r];
+      float wn, yn;
+      if (rr > 0.f) {
+        wn = fminf(fmaxf(wh + yo / rr, ap.rlo[k * RS + r]), ap.rhi[k * RS + r]);
+        yn = yo + rr * (wh - wn);
+      } else {
+        wn = wh;
+        yn = 0.f;
+      }
+      ap.w[k * RS + r] = wn;
+      ap.y[k * RS + r] = yn;
+    }
+    if (lane < 30) {
+      ap.u[k * VS + lane] = alpha * u + (1.f - alpha) * ap.u[k * VS + lane];
+      ap.x[(k + 1) * VS + lane] = alpha * xn + (1.f - alpha) * ap.x[(k + 1) * VS + lane];
+    }
+    x = xn;
+    __syncwarp();
+  }
+}
+
+// ============================================================ residuals (A5 vii)
+// Unscaled OSQP residuals of the current iterate: primal |C z - w|_inf over
+// constrained rows; dual = stationarity in u after choosing the dynamics
+// multipliers that make stationarity in x exact (costate recursion).
+struct Res { float rp, rd, ps, ds; };
+
+__device__ __noinline__ Res admm_residuals(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat) {
+  const int N = ap.N;
+  const float* md = ap.mdl;
+  const float dt = md[M_DT], mu = md[M_MU];
+  float* vec = sm + S_VEC;
+  float* vU = vec + V_U * 64; float* vXN = vec + V_XN * 64; float* vM = vec + V_S * 64;
+  float* vY = vec + V_ROW * 64;
+  const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
+  const float twoR = lane < 30 ? 2.f * dt * md[M_R + lane] : 0.f;
+  const float* xs = ap.x;
+  const float* us = ap.u;
+  const float* ys = ap.y;
+  float rp = 0.f, ps = 0.f, rd = 0.f, ds = 0.f;
+  for (int k = 0; k < N; ++k) {
+    vU[lane] = us[k * VS + lane];
+    vXN[lane] = xs[(k + 1) * VS + lane];
+    __syncwarp();
+    for (int r = lane; r < NR; r += 32) {
+      if (ap.rcls[k * RS + r] > 0.f) {
+        const float v = crow(vU, vXN, r, mu);
+        const float w = ap.w[k * RS + r];
+        rp = fmaxf(rp, fabsf(v - w));
+        ps = fmaxf(ps, fmaxf(fabsf(v), fabsf(w)));
+      }
+    }
+    __syncwarp();
+  }
+  auto gx = [&](int k) -> float {   // 2dt Q (x_k - xr_k) + C_x^T y_{k-1}
+    float g = twoQ * (xs[k * VS + lane] - ap.xref[k * VS + lane]);
+    if (lane >= 12 && lane < 30) g += ys[(k - 1) * RS + lane + 26];
+    return g;
+  };
+  float m = lane < 30 ? gx(N) : 0.f;
+  for (int k = N - 1; k >= 0; --k) {
+    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
+    vM[lane] = m;
+    for (int r = lane; r < NR; r += 32) vY[r] = ys[k * RS + r];
+    __syncwarp();
+    float mn = 0.f;
+    if (lane < 30) {
+      const float cty = cuT(vY, lane, mu);
+      const float gu = twoR * (us[k * VS + lane] - ap.uref[k * VS + lane]) + cty;
+      const float ru = gu + (lane < NC ? cc_tv(sm + S_BV, pat.br, vM, lane) : dt * m);
+      rd = fmaxf(rd, fabsf(ru));
+      ds = fmaxf(ds, fmaxf(fabsf(twoR * us[k * VS + lane]), fabsf(twoR * ap.uref[k * VS + lane])));
+      ds = fmaxf(ds, fmaxf(fabsf(cty), fabsf(twoQ * xs[(k + 1) * VS + lane])));
+      ds = fmaxf(ds, fabsf(twoQ * ap.xref[(k + 1) * VS + lane]));
+      if (lane >= 12) ds = fmaxf(ds, fabsf(vY[lane + 26]));
+      if (k >= 1) mn = gx(k) + (lane < NC ? cc_tv(sm + S_AV, pat.ar, vM, lane) : m);
+    }
+    __syncwarp();
+    m = mn;
+  }
+  Res out;
+  out.rp = warp_max(rp); out.ps = warp_max(ps); out.rd = warp_max(rd); out.ds = warp_max(ds);
+  return out;
+}
+
+// ============================================================ polish
+// OSQP's solution polishing: active set from (w, y) (row at its lower bound
+// when w - lo < -y, at its upper bound when hi - w < y).  Active rows are
+// eliminated exactly: u_k = G_k v_k + t_k, and the reduced equality-
+// constrained LQ problem is solved by one more Riccati factor + sweep.
+// Joint-box (state) rows are not handled: if one is active the polish is
+// skipped.  Active-set codes: bit 0 lower, bit 1 upper, 3 = equality row.
+struct FootAct { int swing, zero, top, tx, ty; };
+
+__device__ void init_active(const AgentPtrs& ap, int lane) {
+  for (int k = 0; k < ap.N; ++k) {
+    for (int r = lane; r < NR; r += 32) {
+      const float lo = ap.rlo[k * RS + r], hi = ap.rhi[k * RS + r];
+      const float w = ap.w[k * RS + r], y = ap.y[k * RS + r];
+      int a = 0;
+      if (lo == hi) a = 3;
+      else {
+        if (w - lo < -y) a |= 1;
+        if (hi - w < y) a |= 2;
+      }
+      ap.act[k * RS + r] = a;
+    }
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ void stage_active(const AgentPtrs& ap, int k, int* act, int lane) {
+  __syncwarp();
+  for (int r = lane; r < NR; r += 32) act[r] = ap.act[k * RS + r];
+  __syncwarp();
+}
+
+__device__ __forceinline__ FootAct foot_act(const int* act, int f) {
+  FootAct fa;
+  const int b = 6 * f, p = 12 + 4 * f;
+  fa.swing = act[b + 2] == 3;
+  const bool up0 = act[p] & 2, up1 = act[p + 1] & 2, up2 = act[p + 2] & 2, up3 = act[p + 3] & 2;
+  fa.zero = !fa.swing && ((act[b + 2] & 1) || (up0 && up1) || (up2 && up3));
+  fa.top = !fa.swing && !fa.zero && (act[b + 2] & 2);
+  fa.tx = up0 ? 1 : (up1 ? -1 : 0);
+  fa.ty = up2 ? 1 : (up3 ? -1 : 0);
+  return fa;
+}
+
+// The elimination of stage k for input i (< 30).  Force inputs:
+// u_i = sum_c gf[c] v_{b+c} + t (row of the foot's 3x3 block G_f); other
+// inputs: u_i = g v_i + t with g in {0, 1}.
+struct Elim { float g, t, gf[3]; };
+
+__device__ __forceinline__ Elim lane_elim(const AgentPtrs& ap, int k, const int* act, int i, float mu) {
+  Elim e;
+  e.g = 1.f; e.t = 0.f; e.gf[0] = e.gf[1] = e.gf[2] = 0.f;
+  if (i < 12) {
+    const int f = i / 6, c = i - 6 * f, b = 6 * f;
+    const FootAct fa = foot_act(act, f);
+    if (fa.swing || fa.zero) { e.g = 0.f; return e; }
+    if (c >= 3) return e;                                   // free moment
+    e.g = 0.f;
+    if (fa.top) {
+      const float F = ap.rhi[k * RS + b + 2];
+      if (c == 2) e.t = F;
+      else {
+        const int tt = c == 0 ? fa.tx : fa.ty;
+        if (tt) e.t = tt * mu * F;
+        else e.gf[c] = 1.f;
+      }
+    } else {
+      if (c == 2) e.gf[2] = 1.f;
+      else {
+        const int tt = c == 0 ? fa.tx : fa.ty;
+        if (tt) e.gf[2] = tt * mu;
+        else e.gf[c] = 1.f;
+      }
+    }
+    return e;
+  }
+  if (i < 30) {
+    const int r = i + 8;
+    const int a = act[r];
+    if (a & 1) { e.g = 0.f; e.t = ap.rlo[k * RS + r]; }
+    else if (a & 2) { e.g = 0.f; e.t = ap.rhi[k * RS + r]; }
+  }
+  return e;
+}
+
+// Per-stage inputs of the polish factor: compact B_hat = B G (into smem, and
+// to global with a dense column-major copy for the sweep), R_hat = G^T D G
+// plus 1 on eliminated inputs, c_hat = c + B t, r_hat = G^T D (t - u_ref).
+__device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const int* act, float* cvec, int lane) {
+  const float* md = ap.mdl;
+  const float dt = md[M_DT], mu = md[M_MU];
+  const float* bbase = ap.lin + L_BV;
+  float* vec = sm + S_VEC;
+  float* gfv = vec + V_T * 64;       // rows of G_f, 3 per force input (indexed 3*i)
+  float* gv = vec + V_G * 64;        // g per input
+  float* tv = vec + V_D * 64;        // t per input
+  float* vD2 = vec + V_H * 64;       // D (t - u_ref)
+  const Elim el = lane_elim(ap, k, act, lane, mu);
+  const float Dj = lane < 30 ? 2.f * dt * md[M_R + lane] : 0.f;
+  if (lane < 30) {
+    gv[lane] = el.g;
+    tv[lane] = el.t;
+    vD2[lane] = Dj * (el.t - ap.uref[k * VS + lane]);
+    if (lane < 12) { gfv[lane * 3] = el.gf[0]; gfv[lane * 3 + 1] = el.gf[1]; gfv[lane * 3 + 2] = el.gf[2]; }
+  } else {
+    tv[lane] = 0.f;
+  }
+  __syncwarp();
+  StageIn in;
+  in.c = cvec;
+  in.rt_off[0] = in.rt_off[1] = in.rt_off[2] = 0.f;
+  in.rt_diag = 0.f;
+  in.qt = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
+  float* cc = ap.cC + k * 64;
+  float* gB = ap.cB + (size_t)k * CB_F;
+  if (lane < NC) {
+    const int j = lane;
+    const bool fj = j < 12 && (j % 6) < 3;
+    const int b = (j / 6) * 6, c = j - b;
+    float bh[6];
+#pragma unroll
+    for (int t = 0; t < 6; ++t) {
+      if (fj)
+        bh[t] = bbase[(b + 0) * 6 + t] * gfv[(b + 0) * 3 + c] + bbase[(b + 1) * 6 + t] * gfv[(b + 1) * 3 + c] +
+                bbase[(b + 2) * 6 + t] * gfv[(b + 2) * 3 + c];
+      else
+        bh[t] = bbase[j * 6 + t] * gv[j];
+    }
+    if (fj) {
+      float d = 0.f, alive = 0.f;
+      for (int l = 0; l < 3; ++l) {
+        const float g = gfv[(b + l) * 3 + c];
+        const float Dl = 2.f * dt * md[M_R + b + l];
+        d += g * Dl * g;
+        alive = fmaxf(alive, g != 0.f ? 1.f : 0.f);
+        for (int r = 0; r < 3; ++r) in.rt_off[r] += gfv[(b + l) * 3 + r] * Dl * g;
+      }
+      in.rt_diag = d + (1.f - alive);
+    } else {
+      in.rt_diag = gv[j] * Dj * gv[j] + (1.f - gv[j]);
+    }
+#pragma unroll
+    for (int t = 0; t < 6; ++t) { sm[S_BV + j * 6 + t] = bh[t]; gB[j * 6 + t] = bh[t]; }
+    float* dn = gB + 136 + j * LDD;
+    for (int i = 0; i < NC; ++i) dn[i] = 0.f;
+#pragma unroll
+    for (int t = 0; t < 6; ++t)
+      if (t < bcnt(j)) dn[brow(j, t)] = bh[t];
+    // c_hat and r_hat
+    const float chat = ap.lin[L_STAGE + k * 64 + 32 + j] + cm_mv(sm + S_B, tv, lane);
+    cvec[j] = chat;
+    cc[j] = chat;
+    cc[32 + j] = fj ? gfv[(b + 0) * 3 + c] * vD2[b] + gfv[(b + 1) * 3 + c] * vD2[b + 1] +
+                          gfv[(b + 2) * 3 + c] * vD2[b + 2]
+                    : gv[j] * vD2[j];
+  } else if (lane < 30) {
+    const float alive = el.g;
+    in.rt_diag = alive * Dj + (1.f - alive);
+    in.rt_off[0] = alive * dt;                  // arm B_hat
+    in.rt_off[1] = (1.f - alive) * dt * el.t;   // arm c_hat
+    cc[lane] = in.rt_off[1];
+    cc[32 + lane] = alive * vD2[lane];
+  }
+  __syncwarp();
+  return in;
+}
+
+// Factor and solve the reduced problem; the polished primal goes to xt/ut.
+// Overwrites the Riccati caches (the caller refactors if ADMM continues).
+__device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat) {
+  const int N = ap.N;
+  const float* md = ap.mdl;
+  const float dt = md[M_DT], mu = md[M_MU];
+  float* P = sm + S_P; float* H = sm + S_H; float* X = sm + S_X; float* K = sm + S_K;
+  float* vec = sm + S_VEC;
+  float* cvec = vec + V_C * 64;
+  int* act = reinterpret_cast<int*>(vec + V_ACT * 64);
+  const int j = lane < NC ? lane : NC - 1;
+  const bool arm = lane >= NC && lane < 30;
+  const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
+
+  // state (joint-box) rows active anywhere -> no polish
+  int qact = 0;
+  for (int k = 0; k < N; ++k)
+    for (int r = 38 + lane; r < NR; r += 32) qact |= ap.act[k * RS + r] != 0;
+  if (warp_or(qact)) return false;
+
+  // ---- factor of the reduced problem (cost 2dt Q, 2dt R; no sigma, no rho)
+  if (lane < NC) {
+    for (int i = 0; i < NC; ++i) P[i * R24 + j] = 0.f;
+    P[j * R24 + j] = 2.f * dt * md[M_Q + j];
+  }
+  float Pa = arm ? twoQ : 0.f;
+  __syncwarp();
+  for (int k = N - 1; k >= 0; --k) {
+    stage_active(ap, k, act, lane);
+    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
+    const StageIn in = polish_stage_in(ap, sm, k, act, cvec, lane);
+    factor_stage(ap, sm, lane, k, in, &Pa, pat);
+  }
+
+  // ---- backward sweep of the reduced problem
+  float* vS = vec + V_S * 64; float* vH = vec + V_H * 64; float* vX = vec + V_X * 64;
+  float* vV = vec + V_U * 64;
+  float p = lane < 30 ? -twoQ * ap.xref[N * VS + lane] : 0.f;
+  for (int k = N - 1; k >= 0; --k) {
+    const float* ce = ap.cE + k * 64;
+    const float* cc = ap.cC + k * 64;
+    const float* gB = ap.cB + (size_t)k * CB_F;
+    stage_active(ap, k, act, lane);
+    const Elim el = lane_elim(ap, k, act, lane, mu);
+    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
+    copy_blk(K, ap.cK + (size_t)k * BLK, lane);
+    copy_blk(H, ap.cH + (size_t)k * BLK, lane);
+    copy_n(sm + S_BV, gB, 136 / 4, lane);
+    const float s = p + (lane < NC ? ce[lane] : (arm ? ce[32 + lane - NC] : 0.f));
+    vS[lane] = s;
+    __syncwarp();
+    float h = 0.f;
+    if (lane < NC) h = cc[32 + lane] + cc_tv(sm + S_BV, pat.br, vS, lane);
+    else if (arm) h = cc[32 + lane] + el.g * dt * s;
+    vH[lane] = h;
+    __syncwarp();
+    float d = 0.f;
+    if (lane < NC) d = -r24_mtv(H, vH, lane);
+    else if (arm) d = -ce[32 + lane] * h;
+    ap.dv[k * VS + lane] = d;
+    if (k >= 1) {
+      const float ql = lane < 30 ? -twoQ * ap.xref[k * VS + lane] : 0.f;
+      if (lane < NC) p = ql + cc_tv(sm + S_AV, pat.ar, vS, lane) + r24_mtv(K, vH, lane);
+      else if (arm) p = ql + s + ce[lane] * h;
+    }
+    __syncwarp();
+  }
+  // ---- forward rollout, u = G v + t
+  float x = lane < 30 ? ap.x[lane] : 0.f;
+  for (int k = 0; k < N; ++k) {
+    const float* ce = ap.cE + k * 64;
+    const float* cc = ap.cC + k * 64;
+    const float* dA = ap.lin + L_STAGE + k * 64;
+    stage_active(ap, k, act, lane);
+    const Elim el = lane_elim(ap, k, act, lane, mu);
+    copy_blk(K, ap.cK + (size_t)k * BLK, lane);
+    copy_n(X, ap.cB + (size_t)k * CB_F + 136, MB / 4, lane);     // dense B_hat
+    vX[lane] = x;
+    __syncwarp();
+    float v = 0.f;
+    if (lane < NC) v = r24_mv(K, vX, lane) + ap.dv[k * VS + lane];
+    else if (arm) v = ce[lane] * x + ap.dv[k * VS + lane];
+    vV[lane] = v;
+    __syncwarp();
+    float xn = 0.f, u = 0.f;
+    if (lane < NC) {
+      xn = ak_mv(sm + S_AB, dA, vX, lane) + cm_mv(X, vV, lane) + cc[lane];
+      if (lane < 12 && (lane % 6) < 3) {
+        const int b = (lane / 6) * 6;
+        u = el.gf[0] * vV[b] + el.gf[1] * vV[b + 1] + el.gf[2] * vV[b + 2] + el.t;
+      } else {
+        u = el.g * v + el.t;
+      }
+    } else if (arm) {
+      xn = x + el.g * dt * v + cc[lane];
+      u = el.g * v + el.t;
+    }
+    ap.xt[(k + 1) * VS + lane] = xn;
+    ap.ut[k * VS + lane] = u;
+    x = xn;
+    __syncwarp();
+  }
+  // restore the compact B of the ADMM problem
+  copy_n(sm + S_BV, ap.lin + L_BV, 136 / 4, lane);
+  __syncwarp();
+  return true;
+}
+
+// Optimality check of the polished point (xt, ut): KKT conditions of the
+// guessed active set (stationarity in the free directions, right sign of the
+// multipliers of the active rows, dynamics multipliers from the costate
+// recursion), then primal feasibility of every row.  With `fix` the active
+// set is corrected for a next attempt: active rows whose multiplier has the
+// wrong sign are dropped, rows the point violates are added; *changed
+// reports whether anything changed.
+__device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, bool fix,
+                            int* changed, const LanePat& pat) {
+  const int N = ap.N;
+  const float* md = ap.mdl;
+  const float dt = md[M_DT], mu = md[M_MU];
+  float* vec = sm + S_VEC;
+  float* vU = vec + V_U * 64; float* vXN = vec + V_XN * 64; float* vM = vec + V_S * 64;
+  float* vG = vec + V_G * 64;
+  int* act = reinterpret_cast<int*>(vec + V_ACT * 64);
+  const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
+  const float twoR = lane < 30 ? 2.f * dt * md[M_R + lane] : 0.f;
+  const float* xs = ap.xt;
+  const float* us = ap.ut;
+  float rp = 0.f, ps = 0.f, rd = 0.f, ds = 0.f;
+  int chg = 0;
+  // scales (they set the tolerances)
+  for (int k = 0; k < N; ++k) {
+    if (lane < 30) {
+      ds = fmaxf(ds, fmaxf(fabsf(twoR * us[k * VS + lane]), fabsf(twoR * ap.uref[k * VS + lane])));
+      ds = fmaxf(ds, fmaxf(fabsf(twoQ * xs[(k + 1) * VS + lane]), fabsf(twoQ * ap.xref[(k + 1) * VS + lane])));
+    }
+    vU[lane] = us[k * VS + lane];
+    vXN[lane] = xs[(k + 1) * VS + lane];
+    __syncwarp();
+    for (int r = lane; r < NR; r += 32)
+      if (ap.rcls[k * RS + r] > 0.f) ps = fmaxf(ps, fabsf(crow(vU, vXN, r, mu)));
+    __syncwarp();
+  }
+  ps = warp_max(ps);
+  ds = warp_max(ds);
+  const float tol_p = prm.eps_abs + prm.eps_rel * ps;
+  const float tol_d = prm.eps_abs + prm.eps_rel * ds;
+  // dual conditions, costate backward
+  float m = lane < 30 ? twoQ * (xs[N * VS + lane] - ap.xref[N * VS + lane]) : 0.f;
+  for (int k = N - 1; k >= 0; --k) {
+    stage_active(ap, k, act, lane);
+    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
+    vM[lane] = m;
+    __syncwarp();
+    float g = 0.f;
+    if (lane < 30)
+      g = twoR * (us[k * VS + lane] - ap.uref[k * VS + lane]) +
+          (lane < NC ? cc_tv(sm + S_BV, pat.br, vM, lane) : dt * m);
+    vG[lane] = g;
+    __syncwarp();
+    int* ak = ap.act + k * RS;
+    // joint rates: input i in 12..29 (row i + 8); multiplier y = -g
+    if (lane >= 12 && lane < 30) {
+      const int a = act[lane + 8];
+      float bad = 0.f;
+      if (a & 1) bad = fmaxf(-g, 0.f);         // needs y <= 0 at a lower bound
+      else if (a & 2) bad = fmaxf(g, 0.f);     // needs y >= 0 at an upper bound
+      else rd = fmaxf(rd, fabsf(g));
+      rd = fmaxf(rd, bad);
+      if (fix && bad > tol_d) { ak[lane + 8] = 0; chg = 1; }
+    }
+    // feet: lane f in 0..1
+    if (lane < 2) {
+      const int f = lane, b = 6 * f, p = 12 + 4 * f;
+      const FootAct fa = foot_act(act, f);
+      const float gx = vG[b], gy = vG[b + 1], gz = vG[b + 2];
+      if (!fa.swing) {
+        for (int c = 3; c < 6; ++c) rd = fmaxf(rd, fabsf(vG[b + c]));   // free moments
+        if (fa.zero) {
+          // -g in the normal cone of the pyramid at 0: g . ray >= 0 on its 4 rays
+          float worst = 0.f;
+          for (int sx = -1; sx <= 1; sx += 2)
+            for (int sy = -1; sy <= 1; sy += 2) worst = fmaxf(worst, -(sx * mu * gx + sy * mu * gy + gz));
+          rd = fmaxf(rd, worst);
+          if (fix && worst > tol_d) {
+            ak[b + 2] &= ~1;
+            if ((act[p] & 2) && (act[p + 1] & 2)) { ak[p] = 0; ak[p + 1] = 0; }
+            if ((act[p + 2] & 2) && (act[p + 3] & 2)) { ak[p + 2] = 0; ak[p + 3] = 0; }
+            chg = 1;
+          }
+        } else {
+          const float ypx = fa.tx ? -fa.tx * gx : 0.f;
+          const float ypy = fa.ty ? -fa.ty * gy : 0.f;
+          if (fa.tx) {
+            rd = fmaxf(rd, fmaxf(-ypx, 0.f));
+            if (fix && -ypx > tol_d) { ak[fa.tx > 0 ? p : p + 1] = 0; chg = 1; }
+          } else {
+            rd = fmaxf(rd, fabsf(gx));
+          }
+          if (fa.ty) {
+            rd = fmaxf(rd, fmaxf(-ypy, 0.f));
+            if (fix && -ypy > tol_d) { ak[fa.ty > 0 ? p + 2 : p + 3] = 0; chg = 1; }
+          } else {
+            rd = fmaxf(rd, fabsf(gy));
+          }
+          const float rz = gz - mu * (ypx + ypy);   // = -y_top when f_z sits at its upper bound
+          if (fa.top) {
+            rd = fmaxf(rd, fmaxf(rz, 0.f));
+            if (fix && rz > tol_d) { ak[b + 2] &= ~2; chg = 1; }
+          } else {
+            rd = fmaxf(rd, fabsf(rz));
+          }
+        }
+      }
+    }
+    float mn = 0.f;
+    if (k >= 1 && lane < 30)
+      mn = twoQ * (xs[k * VS + lane] - ap.xref[k * VS + lane]) +
+           (lane < NC ? cc_tv(sm + S_AV, pat.ar, vM, lane) : m);
+    __syncwarp();
+    m = mn;
+  }
+  // primal feasibility of every row (after the dual pass, so that the dual
+  // conditions are read on the active set the point was solved with)
+  for (int k = 0; k < N; ++k) {
+    vU[lane] = us[k * VS + lane];
+    vXN[lane] = xs[(k + 1) * VS + lane];
+    __syncwarp();
+    for (int r = lane; r < NR; r += 32) {
+      const float v = crow(vU, vXN, r, mu);
+      const float lo = ap.rlo[k * RS + r], hi = ap.rhi[k * RS + r];
+      const float viol = fmaxf(fmaxf(lo - v, v - hi), 0.f);
+      rp = fmaxf(rp, viol);
+      if (fix && viol > tol_p && ap.act[k * RS + r] == 0) {
+        ap.act[k * RS + r] = (v < lo) ? 1 : 2;
+        chg = 1;
+      }
+    }
+    __syncwarp();
+  }
+  Res out;
+  out.rp = warp_max(rp); out.ps = ps; out.rd = warp_max(rd); out.ds = ds;
+  if (changed) *changed = warp_or(chg);
+  return out;
+}
+
+// Polish with active-set correction: up to four attempts; true when one
+// passes its check, with the polished point copied into (x, u).
+__device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Res* res,
+                       const LanePat& pat) {
+  init_active(ap, lane);
+  for (int attempt = 0; attempt < 4; ++attempt) {
+    if (!polish_solve(ap, sm, lane, pat)) return false;
+    int changed = 0;
+    const Res pr = polish_check(ap, sm, lane, prm, true, &changed, pat);
+    const bool ok = isfinite(pr.rp) && isfinite(pr.rd) && pr.rp <= prm.eps_abs + prm.eps_rel * pr.ps &&
+                    pr.rd <= prm.eps_abs + prm.eps_rel * pr.ds;
+    if (ok) {
+      for (int k = 1; k <= ap.N; ++k) ap.x[k * VS + lane] = ap.xt[k * VS + lane];
+      for (int k = 0; k < ap.N; ++k) ap.u[k * VS + lane] = ap.ut[k * VS + lane];
+      __syncwarp();
+      *res = pr;
+      return true;
+    }
+    if (!changed) return false;
+  }
+  return false;
+}
+
+// ============================================================ ADMM driver (A5, A6)
+// Iterations with a residual check every check_every; OSQP's rho update
+// (refactor when the ratio is off by 5x); one early polish attempt once both
+// residuals are within 100x of the tolerance.  Returns the agent status.
+struct Outcome { int status, iters, refac, polished; Res r; };
+
+__device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, bool factored,
+                              Pipe& pp, const LanePat& pat) {
+  float rho = *ap.rho;
+  if (!factored) factor_admm(ap, sm, lane, rho, prm.sigma, pat);
+  Outcome o;
+  o.status = MPC_AGENT_MAX_ITER_; o.iters = 0; o.refac = 0; o.polished = 0;
+  o.r.rp = o.r.rd = o.r.ps = o.r.ds = 0.f;
+  const bool fixed = prm.fixed_iters > 0;
+  const int max_it = fixed ? prm.fixed_iters : prm.max_iter;
+  bool tried_early = false;
+  int it = 0;
+  for (it = 1; it <= max_it; ++it) {
+    admm_iteration(ap, sm, lane, rho, prm, pp, pat);
+    if (warp_or(pp.timeout)) { o.status = MPC_AGENT_TIMEOUT_; break; }
+    const bool check = (!fixed && (it % prm.check_every == 0)) || it == max_it;
+    if (!check) continue;
+    o.r = admm_residuals(ap, sm, lane, pat);
+    if (!(isfinite(o.r.rp) && isfinite(o.r.rd))) { o.status = MPC_AGENT_NAN_; break; }
+    if (fixed) break;
+    const float tol_p = prm.eps_abs + prm.eps_rel * o.r.ps;
+    const float tol_d = prm.eps_abs + prm.eps_rel * o.r.ds;
+    if (o.r.rp <= tol_p && o.r.rd <= tol_d) { o.status = MPC_AGENT_SOLVED_; break; }
+    if (prm.polish && !tried_early && o.r.rp <= 100.f * tol_p && o.r.rd <= 100.f * tol_d) {
+      tried_early = true;
+      Res pr;
+      if (polish(ap, sm, lane, prm, &pr, pat)) {
+        o.polished = 1;
+        o.status = MPC_AGENT_SOLVED_;
+        o.r.rp = pr.rp; o.r.rd = pr.rd;
+        break;
+      }
+      factor_admm(ap, sm, lane, rho, prm.sigma, pat);   // the polish overwrote the caches
+      ++o.refac;
+    }
+    if (prm.adaptive_rho && it < max_it) {
+      const float num = o.r.rp / fmaxf(o.r.ps, 1e-30f);
+      const float den = o.r.rd / fmaxf(o.r.ds, 1e-30f);
+      float rn = rho * sqrtf(num / fmaxf(den, 1e-30f));
+      rn = fminf(fmaxf(rn, 1e-6f), 1e6f);
+      if (rn > 5.f * rho || rn < 0.2f * rho) {
+        rho = rn;
+        factor_admm(ap, sm, lane, rho, prm.sigma, pat);
+        ++o.refac;
+      }
+    }
+  }
+  o.iters = it > max_it ? max_it : it;
+  if (lane == 0) *ap.rho = rho;
+  return o;
+}
+
+// ============================================================ torque map (A7)
+// q_MPC = x0.q; qdot_MPC = u_0.qdot; qddot = (u_1.qdot - u_0.qdot)/dt;
+// tau = K_p (q_MPC - q) + K_d (qdot_MPC - qdot) + M qddot + h - J_leg^T W
+// (Eqs. rnea, mpc_torque); value = QP objective at the solution.
+__device__ __noinline__ void torque_map(const AgentPtrs& ap, int lane) {
+  const int N = ap.N;
+  const float* md = ap.mdl;
+  const float dt = md[M_DT];
+  if (lane < 18) {
+    const int j = lane;
+    const float q = ap.inp[I_X0 + 12 + j];
+    const float qd0 = ap.u[12 + j];
+    const float qd1 = ap.u[VS + 12 + j];
+    float tau = md[M_KP + j] * (q - q) + md[M_KD + j] * (qd0 - ap.inp[I_QD + j]) +
+                md[M_MJ + j] * ((qd1 - qd0) / dt) + md[M_HJ + j];
+    if (j < 10) {
+      const int f = j / 5, jj = j - 5 * f;
+      for (int r = 0; r < 6; ++r) tau -= md[M_JLEG + 30 * f + 5 * r + jj] * ap.u[6 * f + r];
+    }
+    ap.out[O_TAU + j] = tau;
+    ap.out[O_QSET + j] = q;
+    ap.out[O_QDSET + j] = qd0;
+  }
+  float v = 0.f;
+  if (lane < 30) {
+    const float q = md[M_Q + lane], r = md[M_R + lane];
+    for (int k = 0; k <= N; ++k) {
+      const float e = ap.x[k * VS + lane] - ap.xref[k * VS + lane];
+      v = fmaf(dt * q * e, e, v);
+    }
+    for (int k = 0; k < N; ++k) {
+      const float e = ap.u[k * VS + lane] - ap.uref[k * VS + lane];
+      v = fmaf(dt * r * e, e, v);
+    }
+  }
+  v = warp_sum(v);
+  if (lane == 0) ap.out[O_V] = v;
+}
+
+__device__ void mark_status_only(const AgentPtrs& ap, int lane, int status) {
+  if (lane < 18) { ap.out[O_TAU + lane] = 0.f; ap.out[O_QSET + lane] = 0.f; ap.out[O_QDSET + lane] = 0.f; }
+  if (lane == 0) {
+    ap.out[O_V] = 0.f;
+    ap.st[T_STATUS] = status;
+    ap.st[T_ITERS] = 0; ap.st[T_REFAC] = 0; ap.st[T_POLISHED] = 0;
+    *ap.warm = 0;
+  }
+  __syncwarp();
+}
+
+// copy the batch row's inputs into the agent's input record
+__device__ __forceinline__ void load_inputs(const Batch& b, int row, const AgentPtrs& ap, int lane) {
+  if (lane < 30) ap.inp[I_X0 + lane] = b.x0[(size_t)row * 30 + lane];
+  if (lane < 18) ap.inp[I_QD + lane] = b.qd[(size_t)row * 18 + lane];
+  if (lane < 4) ap.inp[I_CMD + lane] = b.cmd[(size_t)row * 4 + lane];
+  if (lane == 0) ap.inp[I_PHASE] = b.phase[row];
+  __syncwarp();
+}
+
+__device__ void write_outcome(const AgentPtrs& ap, int lane, const Outcome& o) {
+  __syncwarp();
+  if (lane == 0) {
+    ap.st[T_STATUS] = o.status;
+    ap.st[T_ITERS] = o.iters;
+    ap.st[T_REFAC] = o.refac;
+    ap.st[T_POLISHED] = o.polished;
+    ap.out[O_PRIM] = o.r.rp;
+    ap.out[O_DUAL] = o.r.rd;
+    *ap.warm = (o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) ? 0 : ap.N;
+  }
+  __syncwarp();
+}
+
+// final polish when ADMM ended without an accepted one
+__device__ void final_polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Outcome& o,
+                             const LanePat& pat) {
+  if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) return;
+  Res pr;
+  if (polish(ap, sm, lane, prm, &pr, pat)) {
+    o.polished = 1;
+    o.status = MPC_AGENT_SOLVED_;
+    o.r.rp = pr.rp; o.r.rd = pr.rd;
+  }
+}
+
+// ============================================================ kernels
+extern __shared__ __align__(16) float g_smem[];
+
+// a batch row names a live slot (admitted by mpc_set_models, in range)
+__device__ __forceinline__ bool valid_slot(const Arena& a, const Batch& b, int row) {
+  const int s = b.ids[row];
+  return s >= 0 && s < a.max_agents && a.horizon[s] >= 2 && a.horizon[s] <= a.maxN;
+}
+__device__ __forceinline__ float* warp_smem() { return g_smem + (threadIdx.x >> 5) * W_FLOATS; }
+
+template <int MINB>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_fused(Arena a, Batch b, SolverParams prm) {
+  // persistent: each warp takes the next batch row from the work queue
+  // (longest expected solve first) until the queue is empty
+  const int lane = threadIdx.x & 31;
+  float* sm = warp_smem();
+  const LanePat pat = lane_pattern(lane);
+  Pipe pp;
+  pipe_init(pp, sm, lane);
+  int static_row = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  const int nw = gridDim.x * WARPS_PER_BLOCK;
+  for (;;) {
+    int idx;
+    if (b.counter) {
+      idx = 0;
+      if (lane == 0) idx = atomicAdd(b.counter, 1);
+      idx = __shfl_sync(FULL, idx, 0);
+    } else {
+      idx = static_row;
+      static_row += nw;
+    }
+    if (idx >= b.n) break;
+    const int row = b.order ? b.order[idx] : idx;
+    if (!valid_slot(a, b, row)) continue;
+    const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
+    load_inputs(b, row, ap, lane);
+    if (!setup_agent(ap, sm, lane, prm)) { mark_status_only(ap, lane, MPC_AGENT_NAN_); continue; }
+    Outcome o = admm_solve(ap, sm, lane, prm, false, pp, pat);
+    final_polish(ap, sm, lane, prm, o, pat);
+    write_outcome(ap, lane, o);
+    torque_map(ap, lane);
+    __syncwarp();
+  }
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_setup(Arena a, Batch b, SolverParams prm) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  if (row >= b.n || !valid_slot(a, b, row)) return;
+  float* sm = warp_smem();
+  const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
+  load_inputs(b, row, ap, lane);
+  if (!setup_agent(ap, sm, lane, prm)) mark_status_only(ap, lane, MPC_AGENT_NAN_);
+  else if (lane == 0) ap.st[T_STATUS] = MPC_AGENT_MAX_ITER_;
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_factor(Arena a, Batch b, SolverParams prm) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  if (row >= b.n || !valid_slot(a, b, row)) return;
+  float* sm = warp_smem();
+  const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
+  if (ap.st[T_STATUS] == MPC_AGENT_NAN_) return;
+  load_lin(ap, sm, lane);
+  factor_admm(ap, sm, lane, *ap.rho, prm.sigma, lane_pattern(lane));
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_admm(Arena a, Batch b, SolverParams prm) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  if (row >= b.n || !valid_slot(a, b, row)) return;
+  float* sm = warp_smem();
+  const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
+  if (ap.st[T_STATUS] == MPC_AGENT_NAN_) return;
+  load_lin(ap, sm, lane);
+  const LanePat pat = lane_pattern(lane);
+  Pipe pp;
+  pipe_init(pp, sm, lane);
+  const Outcome o = admm_solve(ap, sm, lane, prm, true, pp, pat);
+  write_outcome(ap, lane, o);
+}
+
+template <int MINB>
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_polish(Arena a, Batch b, SolverParams prm) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  if (row >= b.n || !valid_slot(a, b, row)) return;
+  float* sm = warp_smem();
+  const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
+  Outcome o;
+  o.status = ap.st[T_STATUS];
+  o.iters = ap.st[T_ITERS];
+  o.refac = ap.st[T_REFAC];
+  o.polished = ap.st[T_POLISHED];
+  o.r.rp = ap.out[O_PRIM];
+  o.r.rd = ap.out[O_DUAL];
+  o.r.ps = o.r.ds = 0.f;
+  if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) return;
+  load_lin(ap, sm, lane);
+  copy_n(sm + S_BV, ap.lin + L_BV, 136 / 4, lane);
+  __syncwarp();
+  final_polish(ap, sm, lane, prm, o, lane_pattern(lane));
+  if (o.polished) write_outcome(ap, lane, o);
+}
+
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) mpc_k_torque(Arena a, Batch b) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  if (row >= b.n || !valid_slot(a, b, row)) return;
+  const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
+  const int st = ap.st[T_STATUS];
+  if (st == MPC_AGENT_NAN_ || st == MPC_AGENT_TIMEOUT_) return;
+  torque_map(ap, lane);
+}
+
+}  // namespace
+
+// ============================================================ variant launcher
+// Kernel variants: the minimum resident blocks per SM given to the compiler
+// (register cap).  One translation unit instantiates one variant.
+template <int MINB>
+cudaError_t configure_smem() {
+  const int bytes = (int)smem_bytes_per_block();
+  void (*ks[])(Arena, Batch, SolverParams) = {mpc_k_fused<MINB>, mpc_k_setup<MINB>, mpc_k_factor<MINB>,
+                                              mpc_k_admm<MINB>, mpc_k_polish<MINB>};
+  for (auto k : ks) {
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+template <int MINB>
+cudaError_t launch_variant(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
+                           cudaStream_t st, int* launches) {
+  static int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e = configure_smem<MINB>();
+    if (e != cudaSuccess) return e;
+    configured = dev;
+  }
+  if (b.n <= 0) return cudaSuccess;
+  const size_t smem = smem_bytes_per_block();
+  const int blocks = (b.n + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+  const dim3 thr(WARPS_PER_BLOCK * 32);
+  if (form == 1) {
+    // resident grid: SMs x blocks per SM (the persistent warps drain the queue)
+    static int resident = 0, resident_dev = -1;
+    if (resident_dev != dev) {
+      int nsm = 0, per_sm = 0;
+      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mpc_k_fused<MINB>, WARPS_PER_BLOCK * 32, smem);
+      resident = nsm * (per_sm > 0 ? per_sm : 1);
+      resident_dev = dev;
+    }
+    int g = b.counter ? resident : blocks;
+    if (grid_fused > 0 && grid_fused < g) g = grid_fused;
+    if (g > blocks) g = blocks;
+    mpc_k_fused<MINB><<<g, thr, smem, st>>>(a, b, prm);
+    if (launches) *launches += 1;
+  } else {
+    mpc_k_setup<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
+    mpc_k_factor<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
+    mpc_k_admm<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
+    mpc_k_polish<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
+    mpc_k_torque<<<blocks, thr, 0, st>>>(a, b);
+    if (launches) *launches += 5;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace mpc

@@ -26,7 +26,7 @@ constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct Layout {
   size_t model, sched, horizon, ids, xs, us, ws, ys, rho, warm, out, stat, inp, xref, uref, rlo, rhi,
-      rcls, lin, cK, cH, cE, cB, cC, xt, ut, dv, act, total;
+      rcls, lin, cK, cH, cE, cB, cC, xt, ut, dv, act, order, counter, total;
 };
 
 constexpr Layout make_layout(size_t A, size_t n) {
@@ -52,16 +52,18 @@ constexpr Layout make_layout(size_t A, size_t n) {
   L.rlo = take(A * n * RS * 4);
   L.rhi = take(A * n * RS * 4);
   L.rcls = take(A * n * RS * 4);
-  L.lin = take(A * (2 * MB + n * 2 * VS) * 4);
-  L.cK = take(A * n * MB * 4);
-  L.cH = take(A * n * MB * 4);
+  L.lin = take(A * (size_t)lin_floats((int)n) * 4);
+  L.cK = take(A * n * BLK * 4);
+  L.cH = take(A * n * BLK * 4);
   L.cE = take(A * n * 64 * 4);
-  L.cB = take(A * n * MB * 4);
+  L.cB = take(A * n * CB_F * 4);
   L.cC = take(A * n * 64 * 4);
   L.xt = take(A * (n + 1) * VS * 4);
   L.ut = take(A * n * VS * 4);
   L.dv = take(A * n * VS * 4);
   L.act = take(A * n * RS * 4);
+  L.order = take(A * 4);
+  L.counter = take(16);
   L.total = o;
   return L;
 }
@@ -196,6 +198,8 @@ extern "C" mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_
   a.ut = at<float>(b, kL.ut);
   a.dv = at<float>(b, kL.dv);
   a.act = at<int>(b, kL.act);
+  a.order = at<int>(b, kL.order);
+  a.counter = at<int>(b, kL.counter);
   int* d_ids = at<int>(b, kL.ids);
 
   // models, horizons and the slot list; the whole horizon array is rewritten
@@ -217,8 +221,8 @@ extern "C" mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_
   prm.eps_rel = c.eps_rel; prm.max_iter = c.max_iter; prm.fixed_iters = c.fixed_iters;
   prm.check_every = c.check_every; prm.adaptive_rho = c.adaptive_rho; prm.polish = c.polish;
   prm.warm_start = 0;
-  mpc::Batch bt{n, d_ids, x0, qd_meas, cmd, phase};
-  if (mpc::launch_solve(a, bt, prm, MPC_FORM_FUSED, 0, st, nullptr) != cudaSuccess) return MPC_ERR_CUDA;
+  mpc::Batch bt{n, d_ids, x0, qd_meas, cmd, phase, nullptr, nullptr};
+  if (mpc::launch_solve(a, bt, prm, MPC_FORM_FUSED, 0, st, nullptr, c.variant) != cudaSuccess) return MPC_ERR_CUDA;
   if (mpc::launch_gather(a, n, d_ids, tau, q_set, qd_set, value, agent_status, st) != cudaSuccess)
     return MPC_ERR_CUDA;
   return MPC_OK;

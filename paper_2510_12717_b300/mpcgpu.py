@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libmpcgpu.so")
 
 MPC_OK, MPC_ERR_INVALID, MPC_ERR_BUDGET, MPC_ERR_CUDA = 0, 1, 2, 3
 MPC_ERR_NOT_READY, MPC_ERR_TIMEOUT, MPC_ERR_STATE = 4, 5, 6
-AGENT_SOLVED, AGENT_MAX_ITER, AGENT_PRIMAL_INFEAS, AGENT_DUAL_INFEAS, AGENT_NAN = 0, 1, 2, 3, 4
+AGENT_SOLVED, AGENT_MAX_ITER, AGENT_PRIMAL_INFEAS, AGENT_DUAL_INFEAS, AGENT_NAN, AGENT_TIMEOUT = 0, 1, 2, 3, 4, 5
 FORM_PLAIN, FORM_FUSED = 0, 1
 FP32, TF32, BF16, FP64 = 0, 1, 2, 3
 
@@ -32,7 +32,7 @@ class MpcConfig(C.Structure):
         ("form", C.c_int), ("rho0", C.c_float), ("sigma", C.c_float), ("alpha", C.c_float),
         ("eps_abs", C.c_float), ("eps_rel", C.c_float), ("max_iter", C.c_int),
         ("fixed_iters", C.c_int), ("check_every", C.c_int), ("adaptive_rho", C.c_int),
-        ("polish", C.c_int), ("warm_start", C.c_int),
+        ("polish", C.c_int), ("warm_start", C.c_int), ("variant", C.c_int),
     ]
 
 
