@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--variant", type=int, default=1, help="kernel variant (register cap), 1 or 2")
+    ap.add_argument("--check-every", type=int, default=10)
+    ap.add_argument("--early-polish", type=float, default=100.0)
     return ap.parse_args()
 
 
@@ -160,7 +162,8 @@ def run_ours(args):
 
     def make_solver(form):
         s = mpcgpu.Solver(max_agents=n, max_horizon=int(Nh.max()), form=form, device=local,
-                          stream=stream.cuda_stream, variant=args.variant)
+                          stream=stream.cuda_stream, variant=args.variant,
+                          check_every=args.check_every, early_polish=args.early_polish)
         s.set_models(model, slots)
         return s
 
@@ -267,6 +270,7 @@ def run_ours(args):
                                f"{Nh.mean():.2f}), gaits walk/stand/hop/single-stance, warm-started "
                                f"replans with perturbed state", "agents_per_gpu": n,
                    "form": "fused", "precision": "fp32", "variant": args.variant,
+                   "check_every": args.check_every, "early_polish": args.early_polish,
                    "l2": "per-agent working set (~1.6 GB) >> L2; no flush"},
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "latency_budget_ms": 10.0,

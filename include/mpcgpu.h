@@ -78,7 +78,7 @@ typedef enum {
 /* Solver and context options.  mpc_default_config() fills the defaults:
  * rho0 0.1, sigma 1e-6, alpha 1.6, eps_abs = eps_rel = 1e-5, max_iter 4000,
  * fixed_iters 0, check_every 10, adaptive_rho 1, polish 1, warm_start 1,
- * form FUSED, precision FP32, max_horizon 20, variant 1.  OSQP's parameters (Stellato et al. 2020,
+ * form FUSED, precision FP32, max_horizon 20, variant 1, early_polish 100.  OSQP's parameters (Stellato et al. 2020,
  * Sec. 3.2, to which the paper defers after Eq. (backsolve_2)). */
 typedef struct mpc_config {
   int device;                 /* CUDA device ordinal */
@@ -98,6 +98,8 @@ typedef struct mpc_config {
   int warm_start;             /* start from the agent's previous solution */
   int variant;                /* kernel build: 1 = 2 resident blocks/SM (no register
                                  spills), 2 = 3 blocks/SM (more warps, some spills) */
+  float early_polish;         /* try the polish once both residuals are within this
+                                 factor of the tolerance (0 = only after ADMM) */
 } mpc_config;
 
 /* One agent's model (host memory, float64; stored as float32 on the device,

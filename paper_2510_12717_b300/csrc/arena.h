@@ -102,7 +102,7 @@ struct Batch {
 };
 
 struct SolverParams {
-  float rho0, sigma, alpha, eps_abs, eps_rel;
+  float rho0, sigma, alpha, eps_abs, eps_rel, early_polish;
   int max_iter, fixed_iters, check_every, adaptive_rho, polish, warm_start;
 };
 

@@ -122,6 +122,7 @@ mpc_status mpc_default_config(mpc_config* cfg) {
   cfg->polish = 1;
   cfg->warm_start = 1;
   cfg->variant = 1;
+  cfg->early_polish = 100.f;
   return MPC_OK;
 }
 
@@ -135,7 +136,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   if (cfg->form != MPC_FORM_PLAIN && cfg->form != MPC_FORM_FUSED) return MPC_ERR_INVALID;
   if (!(cfg->rho0 > 0.f) || !(cfg->sigma > 0.f) || !(cfg->alpha > 0.f && cfg->alpha < 2.f) ||
       !(cfg->eps_abs >= 0.f) || !(cfg->eps_rel >= 0.f) || cfg->max_iter <= 0 || cfg->fixed_iters < 0 ||
-      cfg->check_every <= 0 || cfg->variant < 1 || cfg->variant > 2)
+      cfg->check_every <= 0 || cfg->variant < 1 || cfg->variant > 2 || !(cfg->early_polish >= 0.f))
     return MPC_ERR_INVALID;
   const size_t A = (size_t)cfg->max_agents, n = (size_t)cfg->max_horizon;
   if (cfg->hbm_budget_bytes && arena_bytes(A, n) > cfg->hbm_budget_bytes) return MPC_ERR_BUDGET;
@@ -372,6 +373,7 @@ static Ticket* find_ticket(mpc_ctx* ctx, uint64_t id) {
 static mpc::SolverParams params_of(const mpc_config& c) {
   mpc::SolverParams p;
   p.rho0 = c.rho0; p.sigma = c.sigma; p.alpha = c.alpha; p.eps_abs = c.eps_abs; p.eps_rel = c.eps_rel;
+  p.early_polish = c.early_polish;
   p.max_iter = c.max_iter; p.fixed_iters = c.fixed_iters; p.check_every = c.check_every;
   p.adaptive_rho = c.adaptive_rho; p.polish = c.polish; p.warm_start = c.warm_start;
   return p;

@@ -7,7 +7,7 @@
 //   fused : mpc_k_fused runs every step of an agent in one warp, keeping the
 //           constant stage matrices in shared memory between steps.
 // Both run the same sequence: ADMM with residual checks, rho updates and an
-// early polish attempt once the residuals are within 100x of the tolerance;
+// early polish attempt once the residuals are within early_polish x the tolerance;
 // a final polish after ADMM if none was accepted; the torque map.
 #pragma once
 #include "solver_dev.cuh"
@@ -42,6 +42,7 @@ __device__ __forceinline__ float ak_mv(const float* Ab, const float* dA, const f
 __device__ __forceinline__ void set_stage_A(float* sm, const float* dA, int lane) {
   if (lane >= 12 && lane < NC) {
     float* av = sm + S_AV + lane * 6;
+    av[0] = 1.f;   // identity entry (the polish may zero it for a stage)
 #pragma unroll
     for (int t = 1; t < 4; ++t) av[t] = dA[(t - 1) * 10 + (lane - 12)];
   }
@@ -397,17 +398,17 @@ __device__ __forceinline__ void factor_stage(const AgentPtrs& ap, float* sm, int
   copy_blk(ap.cH + (size_t)k * BLK, H, lane);
   float* ce = ap.cE + k * 64;
   if (lane < NC) ce[lane] = e;
-  // arm lanes: scalar Riccati, A = 1
+  // arm lanes: scalar Riccati with A = rt_off[2], B = rt_off[0], c = rt_off[1]
   if (lane >= NC && lane < 30) {
-    const float Bh = in.rt_off[0];
+    const float Bh = in.rt_off[0], Aa = in.rt_off[2];
     const float Huu = in.rt_diag + Bh * Bh * (*Pa);
-    const float Hux = Bh * (*Pa);
+    const float Hux = Bh * (*Pa) * Aa;
     const float Hi = 1.f / Huu;
     const float Ka = -Hi * Hux;
     ce[lane] = Ka;
     ce[32 + lane] = Hi;
     ce[32 + lane - NC] = (*Pa) * in.rt_off[1];   // e of the arm lane
-    if (k >= 1) *Pa = in.qt + *Pa + Hux * Ka;
+    if (k >= 1) *Pa = in.qt + Aa * Aa * (*Pa) + Hux * Ka;
   }
   if (k >= 1) {
     r24_gemm_tn(P, X, K, P, 1.f, lane);          // P = A^T P A + H_ux^T K
@@ -458,6 +459,7 @@ __device__ __forceinline__ StageIn admm_stage_in(const AgentPtrs& ap, int k, flo
     in.rt_diag = 2.f * dt * md[M_R + lane] + sigma + rho * rc[lane + 8];
     in.rt_off[0] = dt;     // arm B
     in.rt_off[1] = 0.f;    // arm c
+    in.rt_off[2] = 1.f;    // arm A
   }
   __syncwarp();
   return in;
@@ -747,12 +749,16 @@ __device__ __forceinline__ FootAct foot_act(const int* act, int f) {
 
 // The elimination of stage k for input i (< 30).  Force inputs:
 // u_i = sum_c gf[c] v_{b+c} + t (row of the foot's 3x3 block G_f); other
-// inputs: u_i = g v_i + t with g in {0, 1}.
-struct Elim { float g, t, gf[3]; };
+// inputs: u_i = g v_i + t + phi x_i with g in {0, 1}.  A joint rate whose
+// joint-box row (on x_{k+1}) is active is fixed by q_{k+1} = q_k + dt qdot_k
+// = b:  qdot_k = (b - q_k)/dt, i.e. t = b/dt, phi = -1/dt (qbox = 1).
+// conflict = 1 when the rate box and the joint box of the same joint are
+// both active at one stage (not handled: the polish is abandoned).
+struct Elim { float g, t, phi, gf[3]; int qbox, conflict; };
 
 __device__ __forceinline__ Elim lane_elim(const AgentPtrs& ap, int k, const int* act, int i, float mu) {
   Elim e;
-  e.g = 1.f; e.t = 0.f; e.gf[0] = e.gf[1] = e.gf[2] = 0.f;
+  e.g = 1.f; e.t = 0.f; e.phi = 0.f; e.gf[0] = e.gf[1] = e.gf[2] = 0.f; e.qbox = 0; e.conflict = 0;
   if (i < 12) {
     const int f = i / 6, c = i - 6 * f, b = 6 * f;
     const FootAct fa = foot_act(act, f);
@@ -778,10 +784,19 @@ __device__ __forceinline__ Elim lane_elim(const AgentPtrs& ap, int k, const int*
     return e;
   }
   if (i < 30) {
-    const int r = i + 8;
-    const int a = act[r];
+    const int r = i + 8, rq = i + 26;
+    const int a = act[r], aq = act[rq];
     if (a & 1) { e.g = 0.f; e.t = ap.rlo[k * RS + r]; }
     else if (a & 2) { e.g = 0.f; e.t = ap.rhi[k * RS + r]; }
+    if (aq) {
+      if (a) { e.conflict = 1; return e; }
+      const float dt = ap.mdl[M_DT];
+      const float bnd = (aq & 1) ? ap.rlo[k * RS + rq] : ap.rhi[k * RS + rq];
+      e.g = 0.f;
+      e.t = bnd / dt;
+      e.phi = -1.f / dt;
+      e.qbox = 1;
+    }
   }
   return e;
 }
@@ -813,7 +828,11 @@ __device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const 
   in.c = cvec;
   in.rt_off[0] = in.rt_off[1] = in.rt_off[2] = 0.f;
   in.rt_diag = 0.f;
-  in.qt = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
+  // state cost of x_k; an eliminated joint rate moves its cost dt R u^2 onto
+  // x_k:  (R/dt) (x_i - b)^2
+  in.qt = lane < 30 ? 2.f * dt * md[M_Q + lane] + (el.qbox ? 2.f * md[M_R + lane] / dt : 0.f) : 0.f;
+  // A_hat = A + B Phi: the eliminated joint's identity entry vanishes
+  if (el.qbox && lane >= 12 && lane < NC) sm[S_AV + lane * 6] = 0.f;
   float* cc = ap.cC + k * 64;
   float* gB = ap.cB + (size_t)k * CB_F;
   if (lane < NC) {
@@ -861,6 +880,7 @@ __device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const 
     in.rt_diag = alive * Dj + (1.f - alive);
     in.rt_off[0] = alive * dt;                  // arm B_hat
     in.rt_off[1] = (1.f - alive) * dt * el.t;   // arm c_hat
+    in.rt_off[2] = el.qbox ? 0.f : 1.f;         // arm A_hat
     cc[lane] = in.rt_off[1];
     cc[32 + lane] = alive * vD2[lane];
   }
@@ -882,11 +902,11 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
   const bool arm = lane >= NC && lane < 30;
   const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
 
-  // state (joint-box) rows active anywhere -> no polish
-  int qact = 0;
+  // a joint whose rate box and joint box are both active at one stage -> no polish
+  int conflict = 0;
   for (int k = 0; k < N; ++k)
-    for (int r = 38 + lane; r < NR; r += 32) qact |= ap.act[k * RS + r] != 0;
-  if (warp_or(qact)) return false;
+    for (int j = lane; j < 18; j += 32) conflict |= (ap.act[k * RS + 20 + j] != 0) && (ap.act[k * RS + 38 + j] != 0);
+  if (warp_or(conflict)) return false;
 
   // ---- factor of the reduced problem (cost 2dt Q, 2dt R; no sigma, no rho)
   if (lane < NC) {
@@ -913,6 +933,7 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
     stage_active(ap, k, act, lane);
     const Elim el = lane_elim(ap, k, act, lane, mu);
     set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
+    if (el.qbox && lane >= 12 && lane < NC) sm[S_AV + lane * 6] = 0.f;
     copy_blk(K, ap.cK + (size_t)k * BLK, lane);
     copy_blk(H, ap.cH + (size_t)k * BLK, lane);
     copy_n(sm + S_BV, gB, 136 / 4, lane);
@@ -929,9 +950,11 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
     else if (arm) d = -ce[32 + lane] * h;
     ap.dv[k * VS + lane] = d;
     if (k >= 1) {
-      const float ql = lane < 30 ? -twoQ * ap.xref[k * VS + lane] : 0.f;
+      // linear cost of x_k (with the moved cost of an eliminated joint rate)
+      float ql = lane < 30 ? -twoQ * ap.xref[k * VS + lane] : 0.f;
+      if (el.qbox) ql -= 2.f * md[M_R + lane] * el.t;
       if (lane < NC) p = ql + cc_tv(sm + S_AV, pat.ar, vS, lane) + r24_mtv(K, vH, lane);
-      else if (arm) p = ql + s + ce[lane] * h;
+      else if (arm) p = ql + (el.qbox ? 0.f : s) + ce[lane] * h;
     }
     __syncwarp();
   }
@@ -954,16 +977,16 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
     __syncwarp();
     float xn = 0.f, u = 0.f;
     if (lane < NC) {
-      xn = ak_mv(sm + S_AB, dA, vX, lane) + cm_mv(X, vV, lane) + cc[lane];
+      xn = el.qbox ? cc[lane] : ak_mv(sm + S_AB, dA, vX, lane) + cm_mv(X, vV, lane) + cc[lane];
       if (lane < 12 && (lane % 6) < 3) {
         const int b = (lane / 6) * 6;
         u = el.gf[0] * vV[b] + el.gf[1] * vV[b + 1] + el.gf[2] * vV[b + 2] + el.t;
       } else {
-        u = el.g * v + el.t;
+        u = el.g * v + el.t + el.phi * x;
       }
     } else if (arm) {
-      xn = x + el.g * dt * v + cc[lane];
-      u = el.g * v + el.t;
+      xn = (el.qbox ? 0.f : x) + el.g * dt * v + cc[lane];
+      u = el.g * v + el.t + el.phi * x;
     }
     ap.xt[(k + 1) * VS + lane] = xn;
     ap.ut[k * VS + lane] = u;
@@ -1029,15 +1052,28 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
     vG[lane] = g;
     __syncwarp();
     int* ak = ap.act + k * RS;
-    // joint rates: input i in 12..29 (row i + 8); multiplier y = -g
+    // joint rates: input i in 12..29 (row i + 8); multiplier y = -g.  With
+    // the joint box of stage k active (row i + 26, on x_{k+1}), the rate is
+    // eliminated: its stationarity 2dt R u + dt (m + y_q) = 0 gives the
+    // joint-box multiplier y_q, and the costate takes it (m <- m + y_q).
     if (lane >= 12 && lane < 30) {
-      const int a = act[lane + 8];
+      const int a = act[lane + 8], aq = act[lane + 26];
       float bad = 0.f;
-      if (a & 1) bad = fmaxf(-g, 0.f);         // needs y <= 0 at a lower bound
-      else if (a & 2) bad = fmaxf(g, 0.f);     // needs y >= 0 at an upper bound
-      else rd = fmaxf(rd, fabsf(g));
+      if (aq) {
+        const float yq = -2.f * md[M_R + lane] * us[k * VS + lane] - m;
+        if (aq & 1) bad = fmaxf(yq, 0.f);          // lower bound: y_q <= 0
+        else bad = fmaxf(-yq, 0.f);                // upper bound: y_q >= 0
+        m += yq;
+        if (fix && bad > tol_d) { ak[lane + 26] = 0; chg = 1; }
+      } else if (a & 1) {
+        bad = fmaxf(-g, 0.f);                      // needs y <= 0 at a lower bound
+      } else if (a & 2) {
+        bad = fmaxf(g, 0.f);                       // needs y >= 0 at an upper bound
+      } else {
+        rd = fmaxf(rd, fabsf(g));
+      }
       rd = fmaxf(rd, bad);
-      if (fix && bad > tol_d) { ak[lane + 8] = 0; chg = 1; }
+      if (fix && !aq && bad > tol_d) { ak[lane + 8] = 0; chg = 1; }
     }
     // feet: lane f in 0..1
     if (lane < 2) {
@@ -1083,6 +1119,9 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
         }
       }
     }
+    __syncwarp();
+    vM[lane] = m;          // costate with the joint-box multipliers of stage k
+    __syncwarp();
     float mn = 0.f;
     if (k >= 1 && lane < 30)
       mn = twoQ * (xs[k * VS + lane] - ap.xref[k * VS + lane]) +
@@ -1140,7 +1179,7 @@ __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, co
 // ============================================================ ADMM driver (A5, A6)
 // Iterations with a residual check every check_every; OSQP's rho update
 // (refactor when the ratio is off by 5x); one early polish attempt once both
-// residuals are within 100x of the tolerance.  Returns the agent status.
+// residuals are within early_polish x the tolerance.  Returns the agent status.
 struct Outcome { int status, iters, refac, polished; Res r; };
 
 __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, bool factored,
@@ -1165,7 +1204,8 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
     const float tol_p = prm.eps_abs + prm.eps_rel * o.r.ps;
     const float tol_d = prm.eps_abs + prm.eps_rel * o.r.ds;
     if (o.r.rp <= tol_p && o.r.rd <= tol_d) { o.status = MPC_AGENT_SOLVED_; break; }
-    if (prm.polish && !tried_early && o.r.rp <= 100.f * tol_p && o.r.rd <= 100.f * tol_d) {
+    if (prm.polish && prm.early_polish > 0.f && !tried_early && o.r.rp <= prm.early_polish * tol_p &&
+        o.r.rd <= prm.early_polish * tol_d) {
       tried_early = true;
       Res pr;
       if (polish(ap, sm, lane, prm, &pr, pat)) {

@@ -218,7 +218,7 @@ extern "C" mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_
   mpc_default_config(&c);
   mpc::SolverParams prm;
   prm.rho0 = c.rho0; prm.sigma = c.sigma; prm.alpha = c.alpha; prm.eps_abs = c.eps_abs;
-  prm.eps_rel = c.eps_rel; prm.max_iter = c.max_iter; prm.fixed_iters = c.fixed_iters;
+  prm.eps_rel = c.eps_rel; prm.early_polish = c.early_polish; prm.max_iter = c.max_iter; prm.fixed_iters = c.fixed_iters;
   prm.check_every = c.check_every; prm.adaptive_rho = c.adaptive_rho; prm.polish = c.polish;
   prm.warm_start = 0;
   mpc::Batch bt{n, d_ids, x0, qd_meas, cmd, phase, nullptr, nullptr};
