@@ -78,7 +78,8 @@ typedef enum {
 /* Solver and context options.  mpc_default_config() fills the defaults:
  * rho0 0.1, sigma 1e-6, alpha 1.6, eps_abs = eps_rel = 1e-5, max_iter 4000,
  * fixed_iters 0, check_every 10, adaptive_rho 1, polish 1, warm_start 1,
- * form FUSED, precision FP32, max_horizon 20, variant 1, early_polish 100.  OSQP's parameters (Stellato et al. 2020,
+ * form FUSED, precision FP32, max_horizon 20, variant 1, early_polish 100,
+ * graph 0.  OSQP's parameters (Stellato et al. 2020,
  * Sec. 3.2, to which the paper defers after Eq. (backsolve_2)). */
 typedef struct mpc_config {
   int device;                 /* CUDA device ordinal */
@@ -100,6 +101,9 @@ typedef struct mpc_config {
                                  spills), 2 = 3 blocks/SM (more warps, some spills) */
   float early_polish;         /* try the polish once both residuals are within this
                                  factor of the tolerance (0 = only after ADMM) */
+  int graph;                  /* 1: the fused solve is captured as a CUDA graph the
+                                 first time a batch (buffers, ticket slot, stream)
+                                 is solved and replayed afterwards */
 } mpc_config;
 
 /* One agent's model (host memory, float64; stored as float32 on the device,
@@ -156,11 +160,28 @@ mpc_status mpc_submit(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids,
                       const float* x0, const float* qd_meas, const float* cmd,
                       const float* phase, uint64_t* ticket);
 
-/* Enqueue the whole hot path (Alg. 1) for the ticket's agents on the stream:
+/* Enqueue the whole hot path (Alg. 1) for the ticket's agents on the
+ * context's stream:
  * schedule/references/bounds, linearisation, assembly, Riccati factor, ADMM
  * iterations with residual checks and rho updates, polish, torque map, and
  * the write-back of each agent's warm start. */
 mpc_status mpc_solve(mpc_ctx* ctx, uint64_t ticket);
+
+/* mpc_solve on a caller-chosen stream (a cudaStream_t; NULL = legacy default
+ * stream).  Batches solved concurrently on different streams must not share
+ * an agent: their per-agent state would race.  Each ticket has its own work
+ * queue, so concurrent tickets are otherwise independent.  The ticket's
+ * results are gathered on the same stream by mpc_get_torques. */
+mpc_status mpc_solve_on(mpc_ctx* ctx, uint64_t ticket, void* stream);
+
+/* Pick the kernel variant, residual-check period and early-polish threshold
+ * (the batching form's tunables) by timing every candidate on the ticket's
+ * batch (`repeats` timed solves each, after one untimed solve) on the
+ * context's stream.  Among the candidates that solve the most agents the
+ * fastest wins and is stored in the context's configuration.  The batch's
+ * agents are solved repeatedly (their warm starts advance); the ticket stays
+ * submitted.  report (may be NULL) receives a JSON summary.  Synchronous. */
+mpc_status mpc_autotune(mpc_ctx* ctx, uint64_t ticket, int32_t repeats, char* report, size_t cap);
 
 /* Enqueue a gather of the ticket's results into caller buffers (any may be
  * NULL): tau, q_set, qd_set [n][18], value[n] = QP objective at the

@@ -21,7 +21,20 @@ struct Ticket {
   uint64_t id = 0;
   int state = 0;   // 0 free, 1 submitted, 2 solved
   mpc::Batch b{};
+  cudaStream_t stream = nullptr;   // stream the ticket was solved on
 };
+
+// a captured solve (graph mode): replayed while the batch buffers, the
+// ticket slot and the stream are the same
+struct GraphEntry {
+  int n = -1, slot = -1;
+  const void* ptrs[5] = {};
+  cudaStream_t stream = nullptr;
+  int variant = 0, check_every = 0;
+  float early_polish = 0.f;
+  cudaGraphExec_t exec = nullptr;
+};
+constexpr int kMaxGraphs = 16;
 
 }  // namespace
 
@@ -46,8 +59,13 @@ struct mpc_ctx {
   float* d_mstage = nullptr;
   double* d_sstage = nullptr;
   int* d_hstage = nullptr;
+  int* qorder = nullptr;             // per-ticket work-queue buffers [kMaxTickets][A]
+  int* qcount = nullptr;             // per-ticket queue counters [kMaxTickets][8]
+  GraphEntry graphs[kMaxGraphs];
+  int graph_next = 0;
   long long launches = 0;
   long long solves = 0;
+  long long graph_replays = 0;
   std::string err = "ok";
 };
 
@@ -95,6 +113,7 @@ static size_t arena_bytes(size_t A, size_t n) {
   f += A * ((n + 1) * VS + 2 * n * VS + n * RS + 1); // xt ut dv act order
   f += A * (1 + 30 + 18 + 4 + 1 + 18 * 3 + 2);       // host-path staging
   f += A * (MODEL_F + 2 * SCHED_D + 1);              // model upload staging
+  f += A * kMaxTickets + kMaxTickets * 8;            // per-ticket work queues
   return f * 4;
 }
 
@@ -123,6 +142,7 @@ mpc_status mpc_default_config(mpc_config* cfg) {
   cfg->warm_start = 1;
   cfg->variant = 1;
   cfg->early_polish = 100.f;
+  cfg->graph = 0;
   return MPC_OK;
 }
 
@@ -136,6 +156,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   if (cfg->form != MPC_FORM_PLAIN && cfg->form != MPC_FORM_FUSED) return MPC_ERR_INVALID;
   if (!(cfg->rho0 > 0.f) || !(cfg->sigma > 0.f) || !(cfg->alpha > 0.f && cfg->alpha < 2.f) ||
       !(cfg->eps_abs >= 0.f) || !(cfg->eps_rel >= 0.f) || cfg->max_iter <= 0 || cfg->fixed_iters < 0 ||
+      cfg->graph < 0 || cfg->graph > 1 ||
       cfg->check_every <= 0 || cfg->variant < 1 || cfg->variant > 2 || !(cfg->early_polish >= 0.f))
     return MPC_ERR_INVALID;
   const size_t A = (size_t)cfg->max_agents, n = (size_t)cfg->max_horizon;
@@ -199,6 +220,8 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   AL(ctx->d_mstage, A * MODEL_F);
   AL(ctx->d_sstage, A * SCHED_D);
   AL(ctx->d_hstage, A);
+  AL(ctx->qorder, (size_t)kMaxTickets * A);
+  AL(ctx->qcount, (size_t)kMaxTickets * 8);
 #undef AL
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -216,6 +239,9 @@ mpc_status mpc_destroy(mpc_ctx* ctx) {
   if (!ctx) return MPC_ERR_INVALID;
   cudaSetDevice(ctx->cfg.device);
   cudaStreamSynchronize(ctx->stream);
+  cudaDeviceSynchronize();
+  for (auto& g : ctx->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   for (void* p : ctx->allocs) cudaFree(p);
   delete ctx;
   return MPC_OK;
@@ -356,7 +382,8 @@ mpc_status mpc_submit(mpc_ctx* ctx, int32_t n, const int32_t* ids, const float* 
     if (tk.state == 0) {
       tk.id = ctx->next_ticket++;
       tk.state = 1;
-      tk.b = mpc::Batch{n, ids, x0, qd, cmd, phase, nullptr, nullptr};
+      tk.b = mpc::Batch{n, ids, x0, qd, cmd, phase, ctx->qorder + (size_t)t * ctx->cfg.max_agents,
+                        ctx->qcount + (size_t)t * 8};
       *ticket = tk.id;
       return MPC_OK;
     }
@@ -379,21 +406,72 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   return p;
 }
 
-mpc_status mpc_solve(mpc_ctx* ctx, uint64_t ticket) {
+static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
+  int launches = 0;
+  const mpc::SolverParams prm = params_of(ctx->cfg);
+  const int form = ctx->cfg.form;
+  if (!ctx->cfg.graph || form != MPC_FORM_FUSED) {
+    cudaError_t e = mpc::launch_solve(ctx->ar, tk->b, prm, form, 0, st, &launches, ctx->cfg.variant);
+    ctx->launches += launches;
+    return e;
+  }
+  const int slot = (int)(tk - ctx->tickets);
+  const void* ptrs[5] = {tk->b.ids, tk->b.x0, tk->b.qd, tk->b.cmd, tk->b.phase};
+  for (auto& g : ctx->graphs) {
+    if (g.exec && g.n == tk->b.n && g.slot == slot && g.stream == st && g.variant == ctx->cfg.variant &&
+        g.check_every == ctx->cfg.check_every && g.early_polish == ctx->cfg.early_polish &&
+        !memcmp(g.ptrs, ptrs, sizeof(ptrs))) {
+      ctx->graph_replays += 1;
+      ctx->launches += 2;   // the order and fused kernels of the graph
+      return cudaGraphLaunch(g.exec, st);
+    }
+  }
+  // first time: one-time set-up outside the capture, then capture the solve
+  cudaError_t e = mpc::launch_solve(ctx->ar, mpc::Batch{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                                        nullptr},
+                                    prm, form, 0, st, nullptr, ctx->cfg.variant);
+  if (e != cudaSuccess) return e;
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  e = mpc::launch_solve(ctx->ar, tk->b, prm, form, 0, st, &launches, ctx->cfg.variant);
+  cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+  if (e != cudaSuccess) return e;
+  if (e2 != cudaSuccess) return e2;
+  GraphEntry& g = ctx->graphs[ctx->graph_next];
+  ctx->graph_next = (ctx->graph_next + 1) % kMaxGraphs;
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  g = GraphEntry{};
+  e = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) { g.exec = nullptr; return e; }
+  g.n = tk->b.n;
+  g.slot = slot;
+  memcpy(g.ptrs, ptrs, sizeof(ptrs));
+  g.stream = st;
+  g.variant = ctx->cfg.variant;
+  g.check_every = ctx->cfg.check_every;
+  g.early_polish = ctx->cfg.early_polish;
+  ctx->launches += launches;
+  return cudaGraphLaunch(g.exec, st);
+}
+
+mpc_status mpc_solve_on(mpc_ctx* ctx, uint64_t ticket, void* stream) {
   if (!ctx) return MPC_ERR_INVALID;
   Ticket* tk = find_ticket(ctx, ticket);
   if (!tk) return fail(ctx, MPC_ERR_NOT_READY, "solve: unknown ticket");
   if (tk->state != 1) return fail(ctx, MPC_ERR_STATE, "solve: ticket already solved");
   CK(cudaSetDevice(ctx->cfg.device));
-  int launches = 0;
-  cudaError_t e = mpc::launch_solve(ctx->ar, tk->b, params_of(ctx->cfg), ctx->cfg.form, 0, ctx->stream, &launches,
-                                     ctx->cfg.variant);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = enqueue_solve(ctx, tk, st);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "solve: kernel launch");
-  ctx->launches += launches;
   ctx->solves += 1;
   tk->state = 2;
+  tk->stream = st;
   return MPC_OK;
 }
+
+mpc_status mpc_solve(mpc_ctx* ctx, uint64_t ticket) { return mpc_solve_on(ctx, ticket, ctx ? ctx->stream : nullptr); }
 
 mpc_status mpc_get_torques(mpc_ctx* ctx, uint64_t ticket, float* tau, float* q_set, float* qd_set, float* value,
                            int32_t* agent_status) {
@@ -403,7 +481,7 @@ mpc_status mpc_get_torques(mpc_ctx* ctx, uint64_t ticket, float* tau, float* q_s
   if (tk->state != 2) return fail(ctx, MPC_ERR_NOT_READY, "get_torques: ticket not solved");
   CK(cudaSetDevice(ctx->cfg.device));
   cudaError_t e = mpc::launch_gather(ctx->ar, tk->b.n, tk->b.ids, tau, q_set, qd_set, value, agent_status,
-                                     ctx->stream);
+                                     tk->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "get_torques: gather");
   ctx->launches += 1;
   tk->state = 0;
@@ -518,17 +596,89 @@ mpc_status mpc_import_state(mpc_ctx* ctx, int32_t id, const float* x, const floa
   return MPC_OK;
 }
 
+mpc_status mpc_autotune(mpc_ctx* ctx, uint64_t ticket, int32_t repeats, char* report, size_t cap) {
+  if (!ctx) return MPC_ERR_INVALID;
+  Ticket* tk = find_ticket(ctx, ticket);
+  if (!tk) return fail(ctx, MPC_ERR_NOT_READY, "autotune: unknown ticket");
+  if (tk->state != 1) return fail(ctx, MPC_ERR_STATE, "autotune: ticket already solved");
+  if (repeats < 1) repeats = 1;
+  CK(cudaSetDevice(ctx->cfg.device));
+  const mpc_config saved = ctx->cfg;
+  struct Cand { int variant, check_every; float early; float ms; float solved; };
+  std::vector<Cand> cands;
+  for (int v = 1; v <= 2; ++v)
+    for (int c : {5, 10})
+      for (float ep : {30.f, 100.f, 1000.f}) cands.push_back(Cand{v, c, ep, 0.f, 0.f});
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  std::vector<int> st(tk->b.n);
+  int* d_st = ctx->d_status;
+  int best = -1;
+  for (size_t i = 0; i < cands.size(); ++i) {
+    ctx->cfg.variant = cands[i].variant;
+    ctx->cfg.check_every = cands[i].check_every;
+    ctx->cfg.early_polish = cands[i].early;
+    ctx->cfg.graph = 0;
+    const mpc::SolverParams prm = params_of(ctx->cfg);
+    int launches = 0;
+    // one untimed pass (warm starts from this candidate), then timed passes
+    CK(mpc::launch_solve(ctx->ar, tk->b, prm, ctx->cfg.form, 0, ctx->stream, &launches, ctx->cfg.variant));
+    CK(cudaEventRecord(e0, ctx->stream));
+    for (int r = 0; r < repeats; ++r)
+      CK(mpc::launch_solve(ctx->ar, tk->b, prm, ctx->cfg.form, 0, ctx->stream, &launches, ctx->cfg.variant));
+    CK(cudaEventRecord(e1, ctx->stream));
+    CK(mpc::launch_gather(ctx->ar, tk->b.n, tk->b.ids, nullptr, nullptr, nullptr, nullptr, d_st, ctx->stream));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaMemcpy(st.data(), d_st, sizeof(int) * tk->b.n, cudaMemcpyDeviceToHost));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    int ok = 0;
+    for (int v : st) ok += (v == MPC_AGENT_SOLVED);
+    cands[i].ms = ms / repeats;
+    cands[i].solved = tk->b.n ? (float)ok / tk->b.n : 1.f;
+    ctx->launches += launches;
+  }
+  // fastest among the candidates that solve as many agents as the best one
+  float best_solved = 0.f;
+  for (auto& c : cands) best_solved = c.solved > best_solved ? c.solved : best_solved;
+  for (size_t i = 0; i < cands.size(); ++i)
+    if (cands[i].solved >= best_solved && (best < 0 || cands[i].ms < cands[best].ms)) best = (int)i;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->cfg = saved;
+  ctx->cfg.variant = cands[best].variant;
+  ctx->cfg.check_every = cands[best].check_every;
+  ctx->cfg.early_polish = cands[best].early;
+  if (report && cap) {
+    std::string js = "{\"chosen\": {\"variant\": " + std::to_string(cands[best].variant) +
+                     ", \"check_every\": " + std::to_string(cands[best].check_every) +
+                     ", \"early_polish\": " + std::to_string(cands[best].early) + "}, \"candidates\": [";
+    for (size_t i = 0; i < cands.size(); ++i) {
+      char b[200];
+      snprintf(b, sizeof(b), "%s{\"variant\": %d, \"check_every\": %d, \"early_polish\": %g, \"ms\": %.4f, \"solved\": %.5f}",
+               i ? ", " : "", cands[i].variant, cands[i].check_every, cands[i].early, cands[i].ms, cands[i].solved);
+      js += b;
+    }
+    js += "]}";
+    snprintf(report, cap, "%s", js.c_str());
+  }
+  return MPC_OK;
+}
+
 mpc_status mpc_get_stats(mpc_ctx* ctx, char* buf, size_t cap) {
   if (!ctx || !buf || cap == 0) return MPC_ERR_INVALID;
   int live = 0;
   for (int h : ctx->live) live += h != 0;
   snprintf(buf, cap,
            "{\"max_agents\": %d, \"max_horizon\": %d, \"live_agents\": %d, \"arena_bytes\": %zu, "
-           "\"form\": \"%s\", \"kernel_launches\": %lld, \"solves\": %lld, \"smem_per_block\": %zu, "
-           "\"warps_per_block\": %d}",
+           "\"form\": \"%s\", \"kernel_launches\": %lld, \"solves\": %lld, \"graph_replays\": %lld, "
+           "\"smem_per_block\": %zu, \"warps_per_block\": %d, \"variant\": %d, \"check_every\": %d, "
+           "\"early_polish\": %g, \"graph\": %d}",
            ctx->cfg.max_agents, ctx->cfg.max_horizon, live, ctx->bytes,
-           ctx->cfg.form == MPC_FORM_FUSED ? "fused" : "plain", ctx->launches, ctx->solves,
-           mpc::smem_bytes_per_block(), mpc::WARPS_PER_BLOCK);
+           ctx->cfg.form == MPC_FORM_FUSED ? "fused" : "plain", ctx->launches, ctx->solves, ctx->graph_replays,
+           mpc::smem_bytes_per_block(), mpc::WARPS_PER_BLOCK, ctx->cfg.variant, ctx->cfg.check_every,
+           (double)ctx->cfg.early_polish, ctx->cfg.graph);
   return MPC_OK;
 }
 

@@ -40,16 +40,20 @@ __global__ void __launch_bounds__(1024) mpc_k_order(Arena a, Batch b, int* order
 
 cudaError_t launch_solve(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
                          cudaStream_t st, int* launches, int variant) {
+  // queue buffers: the batch's own (one per ticket, so batches on different
+  // streams do not share them) or the arena's
+  int* ord = b.order ? const_cast<int*>(b.order) : a.order;
+  int* cnt = b.counter ? b.counter : a.counter;
   Batch bb = b;
   bb.order = nullptr;
   bb.counter = nullptr;
-  if (form == 1 && b.n > 0 && a.order && a.counter && b.n <= a.max_agents) {
-    mpc_k_order<<<1, 1024, 0, st>>>(a, Batch{b.n, b.ids, b.x0, b.qd, b.cmd, b.phase, nullptr, a.counter}, a.order);
+  if (form == 1 && b.n > 0 && ord && cnt && b.n <= a.max_agents) {
+    mpc_k_order<<<1, 1024, 0, st>>>(a, Batch{b.n, b.ids, b.x0, b.qd, b.cmd, b.phase, nullptr, cnt}, ord);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (launches) *launches += 1;
-    bb.order = a.order;
-    bb.counter = a.counter;
+    bb.order = ord;
+    bb.counter = cnt;
   }
   if (variant == 2) return launch_variant<3>(a, bb, prm, form, grid_fused, st, launches);
   return launch_variant<2>(a, bb, prm, form, grid_fused, st, launches);

@@ -1457,28 +1457,26 @@ cudaError_t configure_smem() {
 template <int MINB>
 cudaError_t launch_variant(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
                            cudaStream_t st, int* launches) {
-  static int configured = -1;
+  // one-time set-up per device (also done before any stream capture by a
+  // call with n = 0): smem opt-in and the resident grid of the persistent kernel
+  static int configured = -1, resident = 0;
   int dev = 0;
   cudaGetDevice(&dev);
+  const size_t smem = smem_bytes_per_block();
   if (configured != dev) {
     cudaError_t e = configure_smem<MINB>();
     if (e != cudaSuccess) return e;
+    int nsm = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mpc_k_fused<MINB>, WARPS_PER_BLOCK * 32, smem);
+    resident = nsm * (per_sm > 0 ? per_sm : 1);
     configured = dev;
   }
   if (b.n <= 0) return cudaSuccess;
-  const size_t smem = smem_bytes_per_block();
   const int blocks = (b.n + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
   const dim3 thr(WARPS_PER_BLOCK * 32);
   if (form == 1) {
-    // resident grid: SMs x blocks per SM (the persistent warps drain the queue)
-    static int resident = 0, resident_dev = -1;
-    if (resident_dev != dev) {
-      int nsm = 0, per_sm = 0;
-      cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mpc_k_fused<MINB>, WARPS_PER_BLOCK * 32, smem);
-      resident = nsm * (per_sm > 0 ? per_sm : 1);
-      resident_dev = dev;
-    }
+    // resident grid: the persistent warps drain the work queue
     int g = b.counter ? resident : blocks;
     if (grid_fused > 0 && grid_fused < g) g = grid_fused;
     if (g > blocks) g = blocks;

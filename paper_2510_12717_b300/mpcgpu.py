@@ -33,7 +33,7 @@ class MpcConfig(C.Structure):
         ("eps_abs", C.c_float), ("eps_rel", C.c_float), ("max_iter", C.c_int),
         ("fixed_iters", C.c_int), ("check_every", C.c_int), ("adaptive_rho", C.c_int),
         ("polish", C.c_int), ("warm_start", C.c_int), ("variant", C.c_int),
-        ("early_polish", C.c_float),
+        ("early_polish", C.c_float), ("graph", C.c_int),
     ]
 
 
@@ -69,6 +69,8 @@ SIGNATURES = {
     "mpc_release_agent": (C.c_int, [_P, C.c_int32]),
     "mpc_submit": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _U64P]),
     "mpc_solve": (C.c_int, [_P, C.c_uint64]),
+    "mpc_solve_on": (C.c_int, [_P, C.c_uint64, _P]),
+    "mpc_autotune": (C.c_int, [_P, C.c_uint64, C.c_int32, C.c_char_p, C.c_size_t]),
     "mpc_get_torques": (C.c_int, [_P, C.c_uint64, _P, _P, _P, _P, _P]),
     "mpc_solve_host": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "mpc_get_agent_stats": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P]),
@@ -199,8 +201,19 @@ class Solver:
                                         _ptr(cmd), _ptr(phase), C.byref(t)))
         return t.value
 
-    def solve(self, ticket: int):
-        self._check(self.lib.mpc_solve(self.ctx, C.c_uint64(ticket)))
+    def solve(self, ticket: int, stream=None):
+        """mpc_solve (context stream) or mpc_solve_on (stream: a cudaStream_t handle)."""
+        if stream is None:
+            self._check(self.lib.mpc_solve(self.ctx, C.c_uint64(ticket)))
+        else:
+            self._check(self.lib.mpc_solve_on(self.ctx, C.c_uint64(ticket), stream))
+
+    def autotune(self, ticket: int, repeats: int = 2) -> dict:
+        """mpc_autotune: time the tunables on the ticket's batch, keep the fastest."""
+        import json
+        buf = C.create_string_buffer(8192)
+        self._check(self.lib.mpc_autotune(self.ctx, C.c_uint64(ticket), repeats, buf, 8192))
+        return json.loads(buf.value.decode())
 
     def get_torques(self, ticket: int, tau=None, q_set=None, qd_set=None, value=None, status=None):
         self._check(self.lib.mpc_get_torques(self.ctx, C.c_uint64(ticket), _ptr(tau), _ptr(q_set),
