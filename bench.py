@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--variant", type=int, default=1, help="kernel variant (register cap), 1 or 2")
     ap.add_argument("--check-every", type=int, default=10)
     ap.add_argument("--early-polish", type=float, default=100.0)
+    ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner in the warm-up")
+    ap.add_argument("--no-graph", action="store_true", help="launch without CUDA-graph replay")
+    ap.add_argument("--serve-seconds", type=float, default=0.5, help="serving run length (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=0.5, help="request rate, x 16384 agents at 100 Hz")
     return ap.parse_args()
 
 
@@ -161,9 +165,11 @@ def run_ours(args):
     Nh = model["N"].astype(np.int64)
 
     def make_solver(form):
+        chosen = form == mpcgpu.FORM_FUSED
         s = mpcgpu.Solver(max_agents=n, max_horizon=int(Nh.max()), form=form, device=local,
                           stream=stream.cuda_stream, variant=args.variant,
-                          check_every=args.check_every, early_polish=args.early_polish)
+                          check_every=args.check_every, early_polish=args.early_polish,
+                          graph=int(chosen and not args.no_graph))
         s.set_models(model, slots)
         return s
 
@@ -189,8 +195,18 @@ def run_ours(args):
             ev[1].record(stream)
         s.get_torques(tk, **out)
 
+    tune_report = None
+
     def timed(form, K, W):
+        nonlocal tune_report
         s = make_solver(form)
+        if form == mpcgpu.FORM_FUSED and not args.no_autotune:
+            # the autotuner runs on the first replan's batch (part of the warm-up)
+            x = d_in[0]
+            tk = s.submit(d_ids, x["x0"], x["qd_meas"], x["cmd"], x["phase"])
+            tune_report = s.autotune(tk, repeats=1)
+            s.solve(tk)
+            s.get_torques(tk, **out)
         for i in range(W):
             step(s, i)
         barrier()
@@ -259,6 +275,10 @@ def run_ours(args):
         plain = {"value": world * n * K2 / (tp / 1e3), "ms_per_step": tp / K2,
                  "p50_ms": float(np.percentile(perp, 50)), "gpu_launches_per_step": lp // K2}
 
+    serving = None
+    if args.serve_seconds > 0:
+        serving = run_serving(args, model, replans, n)
+
     if rank != 0:
         return
     cpu = None if args.no_cpu else cpu_baseline(args.workload, budget_s=20.0)
@@ -269,12 +289,15 @@ def run_ours(args):
         "config": {"workload": f"{args.workload}: {n} agents per GPU, horizon N~U{{5..20}} (mean "
                                f"{Nh.mean():.2f}), gaits walk/stand/hop/single-stance, warm-started "
                                f"replans with perturbed state", "agents_per_gpu": n,
-                   "form": "fused", "precision": "fp32", "variant": args.variant,
-                   "check_every": args.check_every, "early_polish": args.early_polish,
+                   "form": "fused (persistent, work queue)", "precision": "fp32",
+                   "graph": not args.no_graph,
+                   "tuned": tune_report["chosen"] if tune_report else
+                   {"variant": args.variant, "check_every": args.check_every, "early_polish": args.early_polish},
                    "l2": "per-agent working set (~1.6 GB) >> L2; no flush"},
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "latency_budget_ms": 10.0,
         "plain": plain,
+        "serving": serving,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": None if TRAFFIC_BYTES_PER_AGENT is None else TRAFFIC_BYTES_PER_AGENT * n,
@@ -290,6 +313,19 @@ def run_ours(args):
                    "prim_res_max": float(st["prim_res"].max()), "dual_res_max": float(st["dual_res"].max())},
     }
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ serving
+def run_serving(args, model, replans, n):
+    """Continuous batching under a Poisson request stream (16384-agent pool)."""
+    from paper_2510_12717_b300.serve import ServingEngine
+    rate = args.serve_rate * 16384 * 100.0
+    eng = ServingEngine(model, replans, pool=n, streams=2, hbm_budget_bytes=8 << 30)
+    st = eng.run(rate=rate, duration=args.serve_seconds, churn_every=100, churn_frac=0.05)
+    eng.close()
+    st["rate_x_16384_at_100hz"] = args.serve_rate
+    st["note"] = "requests of one agent coalesce (newest state wins); 2 streams; churn 5% every 100 batches"
+    return st
 
 
 # ------------------------------------------------------------------ CPU oracle

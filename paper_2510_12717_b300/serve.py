@@ -1,0 +1,215 @@
+"""Continuous-batching serving loop over the C ABI (one GPU).
+
+Requests for agent replans arrive as a Poisson stream.  Agents are slots of
+one solver context (admitted under an HBM budget at creation); each keeps its
+warm start and factor caches resident on the device.  A request waits in a
+per-agent pending set: later requests of the same agent coalesce into it (the
+newest state wins).  Whenever one of the streams is free, all pending agents
+that are not already in flight (up to max_batch) form the next batch, which
+is copied from pinned memory, solved on that stream (mpc_solve_on) and read
+back, overlapping with the batch on the other stream.  Every `churn_every`
+batches a fraction of the live agents leaves and as many new agents join.
+
+Latency of a request = completion time of the batch that answered it minus
+its arrival time (time since the run started, on the host clock).
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import mpcgpu
+
+
+class ServingEngine:
+    def __init__(self, model: dict, replans: list, *, pool: int, streams: int = 2, max_batch: int = 0,
+                 hbm_budget_bytes: int = 8 << 30, device: int = 0, **solver_opts):
+        """model: SoA agent models (workload.make_agents layout) of every agent
+        that may ever join (live + reserve); replans: list of per-agent input
+        dicts (x0, qd_meas, cmd, phase) cycled through as request states.
+        pool: number of slots (live agents at a time)."""
+        import torch
+        self.torch = torch
+        self.dev = torch.device("cuda", device)
+        self.model = model
+        self.replans = replans
+        self.total = len(model["mass"])
+        self.pool = pool
+        self.max_batch = max_batch or pool
+        self.solver = mpcgpu.Solver(max_agents=pool, max_horizon=int(np.max(model["N"])), device=device,
+                                    stream=torch.cuda.current_stream(self.dev).cuda_stream,
+                                    hbm_budget_bytes=hbm_budget_bytes, **solver_opts)
+        # slot s holds agent slot_agent[s]
+        self.slot_agent = np.arange(pool)
+        self.reserve = list(range(pool, self.total))
+        self.solver.set_models(model, np.arange(pool, dtype=np.int32), idx=self.slot_agent)
+        self.streams = [torch.cuda.Stream(self.dev) for _ in range(streams)]
+        mb = self.max_batch
+        pin = dict(pin_memory=True)
+        self.h_in = [dict(ids=torch.empty(mb, dtype=torch.int32, **pin), x0=torch.empty((mb, 30), **pin),
+                          qd=torch.empty((mb, 18), **pin), cmd=torch.empty((mb, 4), **pin),
+                          ph=torch.empty(mb, **pin)) for _ in streams_range(streams)]
+        self.d_in = [dict(ids=torch.empty(mb, dtype=torch.int32, device=self.dev),
+                          x0=torch.empty((mb, 30), device=self.dev), qd=torch.empty((mb, 18), device=self.dev),
+                          cmd=torch.empty((mb, 4), device=self.dev), ph=torch.empty(mb, device=self.dev))
+                     for _ in streams_range(streams)]
+        self.d_out = [dict(tau=torch.empty((mb, 18), device=self.dev),
+                           st=torch.empty(mb, dtype=torch.int32, device=self.dev)) for _ in streams_range(streams)]
+        self.h_out = [dict(tau=torch.empty((mb, 18), **pin), st=torch.empty(mb, dtype=torch.int32, **pin))
+                      for _ in streams_range(streams)]
+
+    def close(self):
+        self.solver.close()
+
+    # ---------------------------------------------------------------- churn
+    def churn(self, frac: float, rng):
+        """A fraction of the live agents leaves; as many reserve agents join."""
+        k = int(round(frac * self.pool))
+        if k == 0 or len(self.reserve) < k:
+            return 0
+        slots = np.sort(rng.choice(self.pool, k, replace=False))
+        for s in slots:
+            self.solver.release(int(s))
+            self.reserve.append(int(self.slot_agent[s]))
+        new = [self.reserve.pop(0) for _ in range(k)]
+        self.slot_agent[slots] = new
+        self.solver.set_models(self.model, slots.astype(np.int32), idx=np.asarray(new))
+        return k
+
+    # ---------------------------------------------------------------- run
+    def run(self, rate: float, duration: float, *, seed: int = 0, churn_every: int = 100,
+            churn_frac: float = 0.05, warmup_batches: int = 2):
+        """Serve a Poisson stream of `rate` requests/s for `duration` seconds
+        of arrivals.  Returns latency and throughput statistics."""
+        torch = self.torch
+        rng = np.random.default_rng(seed)
+        n_req = rng.poisson(rate * duration)
+        t_arr = np.sort(rng.uniform(0.0, duration, n_req))
+        slot_req = rng.integers(0, self.pool, n_req)
+        # per-slot request lists (arrival order) for latency bookkeeping
+        order = np.argsort(slot_req, kind="stable")
+        starts = np.searchsorted(slot_req[order], np.arange(self.pool + 1))
+        times_by_slot = t_arr[order]
+        arrived = np.zeros(self.pool, dtype=np.int64)     # requests arrived so far, per slot
+        served = np.zeros(self.pool, dtype=np.int64)      # requests answered, per slot
+        in_flight = np.zeros(self.pool, dtype=bool)
+        replan_idx = np.zeros(self.pool, dtype=np.int64)
+        lat = []
+        batches = 0
+        solves = 0
+        sizes = []
+        busy = [None] * len(self.streams)
+        next_req = 0
+        # warm the solver (models resident, first factorisations) before the clock starts
+        self.bad_status = 0
+        for _ in range(warmup_batches):
+            for lo in range(0, self.pool, self.max_batch):
+                self._solve_sync(np.arange(lo, min(lo + self.max_batch, self.pool)), replan_idx)
+        t0 = time.perf_counter()
+        while True:
+            now = time.perf_counter() - t0
+            # arrivals
+            hi = np.searchsorted(t_arr, now, side="right")
+            if hi > next_req:
+                np.add.at(arrived, slot_req[next_req:hi], 1)
+                next_req = hi
+            # completions
+            for si, b in enumerate(busy):
+                if b is not None and b["event"].query():
+                    t_done = time.perf_counter() - t0
+                    sl, cover = b["slots"], b["cover"]
+                    self.bad_status += int(np.count_nonzero(self.h_out[si]["st"].numpy()[:len(sl)] != 0))
+                    lat.append(self._latencies(times_by_slot, starts, served, sl, cover, t_done))
+                    served[sl] = cover
+                    in_flight[sl] = False
+                    solves += len(sl)
+                    busy[si] = None
+            # new batches on free streams
+            for si in range(len(self.streams)):
+                if busy[si] is not None:
+                    continue
+                ready = np.nonzero((arrived > served) & ~in_flight)[0]
+                if len(ready) == 0:
+                    continue
+                sl = ready[:self.max_batch]
+                busy[si] = self._launch(si, sl, replan_idx)
+                busy[si]["cover"] = arrived[sl].copy()
+                in_flight[sl] = True
+                replan_idx[sl] += 1
+                batches += 1
+                sizes.append(len(sl))
+                if churn_every and batches % churn_every == 0:
+                    # leave/join between batches: wait for the device, then swap
+                    torch.cuda.synchronize(self.dev)
+                    for sj, bj in enumerate(busy):
+                        if bj is not None:
+                            t_done = time.perf_counter() - t0
+                            self.bad_status += int(np.count_nonzero(self.h_out[sj]["st"].numpy()[:len(bj["slots"])] != 0))
+                            lat.append(self._latencies(times_by_slot, starts, served, bj["slots"], bj["cover"], t_done))
+                            served[bj["slots"]] = bj["cover"]
+                            in_flight[bj["slots"]] = False
+                            solves += len(bj["slots"])
+                            busy[sj] = None
+                    self.churn(churn_frac, rng)
+            if next_req >= n_req and all(b is None for b in busy) and not np.any(arrived > served):
+                break
+            if now > duration * 20 + 60:
+                break
+        wall = time.perf_counter() - t0
+        lat = np.concatenate(lat) if lat else np.zeros(0)
+        return dict(requests=int(n_req), rate=rate, duration=duration, wall_s=wall, solves=int(solves),
+                    not_solved=int(self.bad_status),
+                    solves_per_s=solves / wall, batches=batches, mean_batch=float(np.mean(sizes)) if sizes else 0.0,
+                    p50_ms=float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
+                    p99_ms=float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
+                    coalesced_frac=1.0 - solves / max(n_req, 1))
+
+    @staticmethod
+    def _latencies(times_by_slot, starts, served, sl, cover, t_done):
+        # requests [served, cover) of each slot in the batch are answered now
+        cnt = cover - served[sl]
+        if cnt.sum() == 0:
+            return np.zeros(0)
+        first = starts[sl] + served[sl]
+        idx = np.repeat(first - np.cumsum(cnt) + cnt, cnt) + np.arange(cnt.sum())
+        return t_done - times_by_slot[idx]
+
+    def _fill(self, si, sl, replan_idx):
+        h = self.h_in[si]
+        n = len(sl)
+        agents = self.slot_agent[sl]
+        ids_np = h["ids"].numpy()
+        ids_np[:n] = sl
+        for key, dst in (("x0", "x0"), ("qd_meas", "qd"), ("cmd", "cmd"), ("phase", "ph")):
+            out = h[dst].numpy()
+            for r in range(len(self.replans)):
+                m = (replan_idx[sl] % len(self.replans)) == r
+                if m.any():
+                    out[:n][m] = self.replans[r][key][agents[m]]
+        return n
+
+    def _launch(self, si, sl, replan_idx):
+        torch = self.torch
+        n = self._fill(si, sl, replan_idx)
+        st = self.streams[si]
+        d, h, do, ho = self.d_in[si], self.h_in[si], self.d_out[si], self.h_out[si]
+        with torch.cuda.stream(st):
+            for k in ("ids", "x0", "qd", "cmd", "ph"):
+                d[k][:n].copy_(h[k][:n], non_blocking=True)
+            tk = self.solver.submit(d["ids"][:n], d["x0"][:n], d["qd"][:n], d["cmd"][:n], d["ph"][:n])
+            self.solver.solve(tk, stream=st.cuda_stream)
+            self.solver.get_torques(tk, tau=do["tau"][:n], status=do["st"][:n])
+            ho["tau"][:n].copy_(do["tau"][:n], non_blocking=True)
+            ho["st"][:n].copy_(do["st"][:n], non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(st)
+        return dict(slots=sl, event=ev)
+
+    def _solve_sync(self, sl, replan_idx):
+        b = self._launch(0, sl, replan_idx)
+        b["event"].synchronize()
+
+
+def streams_range(n):
+    return range(n)
