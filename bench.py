@@ -160,7 +160,8 @@ def run_ours(args):
 
     ids, model, replans = make_workload(args.workload, args.agents, rank, world)
     n = len(ids)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)          # non-default stream: graph capture needs one
+    torch.cuda.set_stream(stream)
     slots = np.arange(n, dtype=np.int32)
     Nh = model["N"].astype(np.int64)
 

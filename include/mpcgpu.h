@@ -103,7 +103,8 @@ typedef struct mpc_config {
                                  factor of the tolerance (0 = only after ADMM) */
   int graph;                  /* 1: the fused solve is captured as a CUDA graph the
                                  first time a batch (buffers, ticket slot, stream)
-                                 is solved and replayed afterwards */
+                                 is solved and replayed afterwards (only on a
+                                 non-default stream; direct launches otherwise) */
 } mpc_config;
 
 /* One agent's model (host memory, float64; stored as float32 on the device,
@@ -155,7 +156,9 @@ mpc_status mpc_release_agent(mpc_ctx* ctx, int32_t agent_id);
 
 /* Register one replan batch of n agents (device buffers, layouts above).
  * Nothing runs yet; the buffers must stay valid until mpc_solve has been
- * enqueued.  *ticket identifies the batch.  At most 64 tickets are pending. */
+ * enqueued.  *ticket identifies the batch.  At most 64 tickets are pending
+ * (a ticket's slot is reused only after its solve and gather have completed
+ * on the device); MPC_ERR_STATE when none is free. */
 mpc_status mpc_submit(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids,
                       const float* x0, const float* qd_meas, const float* cmd,
                       const float* phase, uint64_t* ticket);

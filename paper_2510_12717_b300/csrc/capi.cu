@@ -22,12 +22,17 @@ struct Ticket {
   int state = 0;   // 0 free, 1 submitted, 2 solved
   mpc::Batch b{};
   cudaStream_t stream = nullptr;   // stream the ticket was solved on
+  // the slot's work-queue buffers are in use until this event (recorded after
+  // the gather) has completed: a free slot is reused only then
+  cudaEvent_t done = nullptr;
+  bool pending = false;
 };
 
-// a captured solve (graph mode): replayed while the batch buffers, the
-// ticket slot and the stream are the same
+// a captured solve (graph mode): replayed while the batch buffers and the
+// stream are the same.  Each entry owns its work-queue buffers (replays of
+// one entry are ordered on its stream).
 struct GraphEntry {
-  int n = -1, slot = -1;
+  int n = -1;
   const void* ptrs[5] = {};
   cudaStream_t stream = nullptr;
   int variant = 0, check_every = 0;
@@ -63,6 +68,8 @@ struct mpc_ctx {
   int* qcount = nullptr;             // per-ticket queue counters [kMaxTickets][8]
   GraphEntry graphs[kMaxGraphs];
   int graph_next = 0;
+  int* gorder = nullptr;             // per-graph work-queue buffers [kMaxGraphs][A]
+  int* gcount = nullptr;             // per-graph queue counters [kMaxGraphs][8]
   long long launches = 0;
   long long solves = 0;
   long long graph_replays = 0;
@@ -113,7 +120,7 @@ static size_t arena_bytes(size_t A, size_t n) {
   f += A * ((n + 1) * VS + 2 * n * VS + n * RS + 1); // xt ut dv act order
   f += A * (1 + 30 + 18 + 4 + 1 + 18 * 3 + 2);       // host-path staging
   f += A * (MODEL_F + 2 * SCHED_D + 1);              // model upload staging
-  f += A * kMaxTickets + kMaxTickets * 8;            // per-ticket work queues
+  f += A * (kMaxTickets + kMaxGraphs) + (kMaxTickets + kMaxGraphs) * 8;   // work queues
   return f * 4;
 }
 
@@ -222,6 +229,8 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   AL(ctx->d_hstage, A);
   AL(ctx->qorder, (size_t)kMaxTickets * A);
   AL(ctx->qcount, (size_t)kMaxTickets * 8);
+  AL(ctx->gorder, (size_t)kMaxGraphs * A);
+  AL(ctx->gcount, (size_t)kMaxGraphs * 8);
 #undef AL
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -242,6 +251,8 @@ mpc_status mpc_destroy(mpc_ctx* ctx) {
   cudaDeviceSynchronize();
   for (auto& g : ctx->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
+  for (auto& t : ctx->tickets)
+    if (t.done) cudaEventDestroy(t.done);
   for (void* p : ctx->allocs) cudaFree(p);
   delete ctx;
   return MPC_OK;
@@ -379,6 +390,12 @@ mpc_status mpc_submit(mpc_ctx* ctx, int32_t n, const int32_t* ids, const float* 
   if (n > 0 && (!ids || !x0 || !qd || !cmd || !phase)) return fail(ctx, MPC_ERR_INVALID, "submit: NULL buffer");
   for (int t = 0; t < kMaxTickets; ++t) {
     Ticket& tk = ctx->tickets[t];
+    if (tk.state == 0 && tk.pending) {
+      const cudaError_t q = cudaEventQuery(tk.done);
+      if (q == cudaErrorNotReady) continue;        // its kernels may still read the slot
+      if (q != cudaSuccess) return cuda_fail(ctx, q, "submit: ticket event");
+      tk.pending = false;
+    }
     if (tk.state == 0) {
       tk.id = ctx->next_ticket++;
       tk.state = 1;
@@ -410,15 +427,17 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
   int launches = 0;
   const mpc::SolverParams prm = params_of(ctx->cfg);
   const int form = ctx->cfg.form;
-  if (!ctx->cfg.graph || form != MPC_FORM_FUSED) {
+  // graph capture needs a non-default stream; on the legacy stream the
+  // solve is launched directly
+  if (!ctx->cfg.graph || form != MPC_FORM_FUSED || st == nullptr || st == cudaStreamLegacy) {
     cudaError_t e = mpc::launch_solve(ctx->ar, tk->b, prm, form, 0, st, &launches, ctx->cfg.variant);
     ctx->launches += launches;
     return e;
   }
-  const int slot = (int)(tk - ctx->tickets);
   const void* ptrs[5] = {tk->b.ids, tk->b.x0, tk->b.qd, tk->b.cmd, tk->b.phase};
-  for (auto& g : ctx->graphs) {
-    if (g.exec && g.n == tk->b.n && g.slot == slot && g.stream == st && g.variant == ctx->cfg.variant &&
+  for (int gi = 0; gi < kMaxGraphs; ++gi) {
+    GraphEntry& g = ctx->graphs[gi];
+    if (g.exec && g.n == tk->b.n && g.stream == st && g.variant == ctx->cfg.variant &&
         g.check_every == ctx->cfg.check_every && g.early_polish == ctx->cfg.early_polish &&
         !memcmp(g.ptrs, ptrs, sizeof(ptrs))) {
       ctx->graph_replays += 1;
@@ -427,26 +446,34 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
     }
   }
   // first time: one-time set-up outside the capture, then capture the solve
+  // with this entry's own queue buffers
   cudaError_t e = mpc::launch_solve(ctx->ar, mpc::Batch{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                         nullptr},
                                     prm, form, 0, st, nullptr, ctx->cfg.variant);
   if (e != cudaSuccess) return e;
+  const int gi = ctx->graph_next;
+  ctx->graph_next = (ctx->graph_next + 1) % kMaxGraphs;
+  GraphEntry& g = ctx->graphs[gi];
+  if (g.exec) {
+    // the evicted entry's queue buffers may still be read by a replay in flight
+    cudaStreamSynchronize(g.stream);
+    cudaGraphExecDestroy(g.exec);
+  }
+  g = GraphEntry{};
+  mpc::Batch b = tk->b;
+  b.order = ctx->gorder + (size_t)gi * ctx->cfg.max_agents;
+  b.counter = ctx->gcount + (size_t)gi * 8;
   cudaGraph_t graph = nullptr;
   e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  e = mpc::launch_solve(ctx->ar, tk->b, prm, form, 0, st, &launches, ctx->cfg.variant);
+  e = mpc::launch_solve(ctx->ar, b, prm, form, 0, st, &launches, ctx->cfg.variant);
   cudaError_t e2 = cudaStreamEndCapture(st, &graph);
   if (e != cudaSuccess) return e;
   if (e2 != cudaSuccess) return e2;
-  GraphEntry& g = ctx->graphs[ctx->graph_next];
-  ctx->graph_next = (ctx->graph_next + 1) % kMaxGraphs;
-  if (g.exec) cudaGraphExecDestroy(g.exec);
-  g = GraphEntry{};
   e = cudaGraphInstantiate(&g.exec, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) { g.exec = nullptr; return e; }
   g.n = tk->b.n;
-  g.slot = slot;
   memcpy(g.ptrs, ptrs, sizeof(ptrs));
   g.stream = st;
   g.variant = ctx->cfg.variant;
@@ -484,6 +511,9 @@ mpc_status mpc_get_torques(mpc_ctx* ctx, uint64_t ticket, float* tau, float* q_s
                                      tk->stream);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "get_torques: gather");
   ctx->launches += 1;
+  if (!tk->done) CK(cudaEventCreateWithFlags(&tk->done, cudaEventDisableTiming));
+  CK(cudaEventRecord(tk->done, tk->stream));
+  tk->pending = true;
   tk->state = 0;
   return MPC_OK;
 }

@@ -1178,8 +1178,8 @@ __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, co
 
 // ============================================================ ADMM driver (A5, A6)
 // Iterations with a residual check every check_every; OSQP's rho update
-// (refactor when the ratio is off by 5x); one early polish attempt once both
-// residuals are within early_polish x the tolerance.  Returns the agent status.
+// (refactor when the ratio is off by 5x); polish attempts once both residuals
+// are within early_polish x the tolerance.  Returns the agent status.
 struct Outcome { int status, iters, refac, polished; Res r; };
 
 __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, bool factored,
@@ -1191,7 +1191,11 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
   o.r.rp = o.r.rd = o.r.ps = o.r.ds = 0.f;
   const bool fixed = prm.fixed_iters > 0;
   const int max_it = fixed ? prm.fixed_iters : prm.max_iter;
-  bool tried_early = false;
+  // polish attempts: the first once both residuals are within early_polish x
+  // the tolerance, then again every 100 iterations while they stay there (the
+  // active-set guess improves as ADMM proceeds; in FP32 ADMM can plateau just
+  // above the tolerance), at most 8 attempts
+  int polish_tries = 0, next_polish_it = 0;
   int it = 0;
   for (it = 1; it <= max_it; ++it) {
     admm_iteration(ap, sm, lane, rho, prm, pp, pat);
@@ -1204,9 +1208,10 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
     const float tol_p = prm.eps_abs + prm.eps_rel * o.r.ps;
     const float tol_d = prm.eps_abs + prm.eps_rel * o.r.ds;
     if (o.r.rp <= tol_p && o.r.rd <= tol_d) { o.status = MPC_AGENT_SOLVED_; break; }
-    if (prm.polish && prm.early_polish > 0.f && !tried_early && o.r.rp <= prm.early_polish * tol_p &&
-        o.r.rd <= prm.early_polish * tol_d) {
-      tried_early = true;
+    if (prm.polish && prm.early_polish > 0.f && polish_tries < 8 && it >= next_polish_it &&
+        o.r.rp <= prm.early_polish * tol_p && o.r.rd <= prm.early_polish * tol_d) {
+      ++polish_tries;
+      next_polish_it = it + 100;
       Res pr;
       if (polish(ap, sm, lane, prm, &pr, pat)) {
         o.polished = 1;

@@ -103,6 +103,8 @@ class ServingEngine:
         next_req = 0
         # warm the solver (models resident, first factorisations) before the clock starts
         self.bad_status = 0
+        self.status_counts = {}
+        self.batch_log = []
         for _ in range(warmup_batches):
             for lo in range(0, self.pool, self.max_batch):
                 self._solve_sync(np.arange(lo, min(lo + self.max_batch, self.pool)), replan_idx)
@@ -119,7 +121,11 @@ class ServingEngine:
                 if b is not None and b["event"].query():
                     t_done = time.perf_counter() - t0
                     sl, cover = b["slots"], b["cover"]
-                    self.bad_status += int(np.count_nonzero(self.h_out[si]["st"].numpy()[:len(sl)] != 0))
+                    stv = self.h_out[si]["st"].numpy()[:len(sl)]
+                    self.bad_status += int(np.count_nonzero(stv != 0))
+                    for v in np.unique(stv):
+                        self.status_counts[int(v)] = self.status_counts.get(int(v), 0) + int(np.count_nonzero(stv == v))
+                    self.batch_log.append((len(sl), t_done - b["t_start"]))
                     lat.append(self._latencies(times_by_slot, starts, served, sl, cover, t_done))
                     served[sl] = cover
                     in_flight[sl] = False
@@ -135,6 +141,7 @@ class ServingEngine:
                 sl = ready[:self.max_batch]
                 busy[si] = self._launch(si, sl, replan_idx)
                 busy[si]["cover"] = arrived[sl].copy()
+                busy[si]["t_start"] = time.perf_counter() - t0
                 in_flight[sl] = True
                 replan_idx[sl] += 1
                 batches += 1

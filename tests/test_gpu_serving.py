@@ -21,7 +21,7 @@ def test_serving_loop_runs_and_solves_everything():
     eng = ServingEngine(model, reps, pool=pool, streams=2, max_batch=256)
     st = eng.run(rate=40000.0, duration=0.25, churn_every=4, churn_frac=0.05)
     eng.close()
-    print("\n[serving]", st)
+    print("\n[serving]", st, "statuses", eng.status_counts)
     assert st["not_solved"] == 0
     assert st["solves"] > 0 and st["batches"] >= 4
     assert st["p50_ms"] is not None and st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"]

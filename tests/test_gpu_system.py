@@ -36,13 +36,16 @@ def test_graph_replay_is_bitwise_equal(mpcgpu):
     model, inp = agents("uneven", ids)
     t = _dev(device_inputs(inp))
     ids_d = torch.from_numpy(ids.astype(np.int32)).cuda()
-    cs = torch.cuda.current_stream().cuda_stream
-    ref = mpcgpu.Solver(max_agents=64, max_horizon=20, stream=cs, warm_start=0)
-    ref.set_models(model, ids)
-    tau0, st0 = _solve(ref, ids_d, t, 64)
-    g = mpcgpu.Solver(max_agents=64, max_horizon=20, stream=cs, warm_start=0, graph=1)
-    g.set_models(model, ids)
-    outs = [_solve(g, ids_d, t, 64) for _ in range(3)]    # capture, then two replays
+    side = torch.cuda.Stream()          # graphs are captured on a non-default stream
+    torch.cuda.synchronize()
+    with torch.cuda.stream(side):
+        cs = side.cuda_stream
+        ref = mpcgpu.Solver(max_agents=64, max_horizon=20, stream=cs, warm_start=0)
+        ref.set_models(model, ids)
+        tau0, st0 = _solve(ref, ids_d, t, 64)
+        g = mpcgpu.Solver(max_agents=64, max_horizon=20, stream=cs, warm_start=0, graph=1)
+        g.set_models(model, ids)
+        outs = [_solve(g, ids_d, t, 64) for _ in range(3)]    # capture, then two replays
     torch.cuda.synchronize()
     assert g.stats()["graph_replays"] == 2
     for tau, st in outs:
