@@ -38,9 +38,9 @@ REPLANS = 4          # distinct pre-generated replan inputs, cycled
 FP32_LANES = 128     # FP32 FMA lanes per SM (B300)
 N_SM = 148
 # DRAM bytes per agent of the fused kernel from the last ncu capture of this
-# kernel version (profiles/mpc_k_fused_mixed16k_1024agents.md: 180.9 MB for
-# 1024 agents); None once the kernel has changed since that capture.
-TRAFFIC_BYTES_PER_AGENT = None
+# kernel version (profiles/mpc_k_fused_mixed16k_2048agents.md: 1.866 GB for
+# 2048 agents, tuned configuration); None once the kernel has changed since.
+TRAFFIC_BYTES_PER_AGENT = (1.306290e9 + 0.559540e9) / 2048
 
 
 def parse():
