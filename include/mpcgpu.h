@@ -79,7 +79,7 @@ typedef enum {
  * rho0 0.1, sigma 1e-6, alpha 1.6, eps_abs = eps_rel = 1e-5, max_iter 4000,
  * fixed_iters 0, check_every 10, adaptive_rho 1, polish 1, warm_start 1,
  * form FUSED, precision FP32, max_horizon 20, variant 1, early_polish 100,
- * graph 0.  OSQP's parameters (Stellato et al. 2020,
+ * graph 0, warm_polish 1.  OSQP's parameters (Stellato et al. 2020,
  * Sec. 3.2, to which the paper defers after Eq. (backsolve_2)). */
 typedef struct mpc_config {
   int device;                 /* CUDA device ordinal */
@@ -105,6 +105,9 @@ typedef struct mpc_config {
                                  first time a batch (buffers, ticket slot, stream)
                                  is solved and replayed afterwards (only on a
                                  non-default stream; direct launches otherwise) */
+  int warm_polish;            /* 1: on a warm start, first polish from the previous
+                                 replan's final active set; ADMM runs only if that
+                                 fails its KKT check */
 } mpc_config;
 
 /* One agent's model (host memory, float64; stored as float32 on the device,
@@ -205,8 +208,9 @@ mpc_status mpc_solve_host(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host
 
 /* Per-agent solver statistics of the last solve of each agent, copied to
  * host arrays (any may be NULL): ADMM iterations, refactorisations, polish
- * accepted (0/1), final unscaled primal and dual residuals (inf-norms).
- * Synchronises the stream. */
+ * accepted (0 no, 1 after ADMM, 2 from the warm active set without ADMM),
+ * final unscaled primal and dual residuals (inf-norms).  Synchronises the
+ * stream. */
 mpc_status mpc_get_agent_stats(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host,
                                int32_t* iters_host, int32_t* refactors_host,
                                int32_t* polished_host, float* prim_res_host,

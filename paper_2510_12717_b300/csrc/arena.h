@@ -43,7 +43,7 @@ enum : int { I_X0 = 0, I_QD = 32, I_CMD = 50, I_PHASE = 54, IN_F = 64 };
 // per-agent output record (OUT_F floats)
 enum : int { O_TAU = 0, O_QSET = 18, O_QDSET = 36, O_V = 54, O_PRIM = 55, O_DUAL = 56, OUT_F = 64 };
 // per-agent integer record (ST_I ints)
-enum : int { T_STATUS = 0, T_ITERS = 1, T_REFAC = 2, T_POLISHED = 3, T_N = 4, ST_I = 8 };
+enum : int { T_STATUS = 0, T_ITERS = 1, T_REFAC = 2, T_POLISHED = 3, T_N = 4, T_WARM = 5, T_FIRST = 6, ST_I = 8 };
 
 struct Arena {
   int max_agents;
@@ -103,7 +103,7 @@ struct Batch {
 
 struct SolverParams {
   float rho0, sigma, alpha, eps_abs, eps_rel, early_polish;
-  int max_iter, fixed_iters, check_every, adaptive_rho, polish, warm_start;
+  int max_iter, fixed_iters, check_every, adaptive_rho, polish, warm_start, warm_polish;
 };
 
 }  // namespace mpc

@@ -150,6 +150,7 @@ mpc_status mpc_default_config(mpc_config* cfg) {
   cfg->variant = 1;
   cfg->early_polish = 100.f;
   cfg->graph = 0;
+  cfg->warm_polish = 1;
   return MPC_OK;
 }
 
@@ -420,6 +421,7 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   p.early_polish = c.early_polish;
   p.max_iter = c.max_iter; p.fixed_iters = c.fixed_iters; p.check_every = c.check_every;
   p.adaptive_rho = c.adaptive_rho; p.polish = c.polish; p.warm_start = c.warm_start;
+  p.warm_polish = c.warm_polish;
   return p;
 }
 
@@ -564,7 +566,7 @@ mpc_status mpc_get_agent_stats(mpc_ctx* ctx, int32_t n, const int32_t* ids, int3
     const float* o = &out[(size_t)ids[i] * mpc::OUT_F];
     if (iters) iters[i] = s[mpc::T_ITERS];
     if (refactors) refactors[i] = s[mpc::T_REFAC];
-    if (polished) polished[i] = s[mpc::T_POLISHED];
+    if (polished) polished[i] = s[mpc::T_POLISHED] ? (s[mpc::T_FIRST] ? 2 : 1) : 0;
     if (prim) prim[i] = o[mpc::O_PRIM];
     if (dual) dual[i] = o[mpc::O_DUAL];
   }

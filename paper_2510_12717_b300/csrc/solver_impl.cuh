@@ -271,6 +271,7 @@ __device__ __noinline__ bool setup_agent(const AgentPtrs& ap, float* sm, int lan
   // warm or cold start (f_init: the current pose repeated over the horizon,
   // everything else zero; duals zero)
   const bool warm = prm.warm_start && (*ap.warm == N);
+  if (lane == 0) ap.st[T_WARM] = warm ? 1 : 0;
   if (!warm) {
     for (int k = 0; k <= N; ++k) {
       float v = 0.f;
@@ -1155,9 +1156,30 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
 
 // Polish with active-set correction: up to four attempts; true when one
 // passes its check, with the polished point copied into (x, u).
+// Initial guess from the agent's previous final active set (kept per slot):
+// rows that became equalities (a foot switched to swing) are active, rows
+// that stopped being equalities start inactive, the rest keep their code.
+__device__ void init_active_prev(const AgentPtrs& ap, int lane) {
+  for (int k = 0; k < ap.N; ++k) {
+    for (int r = lane; r < NR; r += 32) {
+      const float lo = ap.rlo[k * RS + r], hi = ap.rhi[k * RS + r];
+      int a = ap.act[k * RS + r];
+      if (lo == hi) a = 3;
+      else if (a == 3) a = 0;
+      else {
+        if (!isfinite(lo)) a &= ~1;
+        if (!isfinite(hi)) a &= ~2;
+      }
+      ap.act[k * RS + r] = a;
+    }
+  }
+  __syncwarp();
+}
+
 __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Res* res,
-                       const LanePat& pat) {
-  init_active(ap, lane);
+                       const LanePat& pat, bool from_prev = false) {
+  if (from_prev) init_active_prev(ap, lane);
+  else init_active(ap, lane);
   for (int attempt = 0; attempt < 4; ++attempt) {
     if (!polish_solve(ap, sm, lane, pat)) return false;
     int changed = 0;
@@ -1185,10 +1207,25 @@ struct Outcome { int status, iters, refac, polished; Res r; };
 __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, bool factored,
                               Pipe& pp, const LanePat& pat) {
   float rho = *ap.rho;
-  if (!factored) factor_admm(ap, sm, lane, rho, prm.sigma, pat);
   Outcome o;
   o.status = MPC_AGENT_MAX_ITER_; o.iters = 0; o.refac = 0; o.polished = 0;
   o.r.rp = o.r.rd = o.r.ps = o.r.ds = 0.f;
+  // warm start: the previous replan's final active set is usually still
+  // right; a polish from it that passes the KKT check is the optimum, with no
+  // ADMM factorisation and no iteration
+  if (lane == 0) ap.st[T_FIRST] = 0;
+  if (prm.polish && prm.warm_polish && ap.st[T_WARM] && prm.fixed_iters == 0) {
+    Res pr;
+    if (polish(ap, sm, lane, prm, &pr, pat, true)) {
+      o.polished = 1;
+      o.status = MPC_AGENT_SOLVED_;
+      o.r.rp = pr.rp; o.r.rd = pr.rd;
+      if (lane == 0) ap.st[T_FIRST] = 1;
+      return o;
+    }
+    factored = false;   // the polish overwrote the caches
+  }
+  if (!factored) factor_admm(ap, sm, lane, rho, prm.sigma, pat);
   const bool fixed = prm.fixed_iters > 0;
   const int max_it = fixed ? prm.fixed_iters : prm.max_iter;
   // polish attempts: the first once both residuals are within early_polish x

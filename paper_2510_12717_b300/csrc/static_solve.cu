@@ -221,6 +221,7 @@ extern "C" mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_
   prm.eps_rel = c.eps_rel; prm.early_polish = c.early_polish; prm.max_iter = c.max_iter; prm.fixed_iters = c.fixed_iters;
   prm.check_every = c.check_every; prm.adaptive_rho = c.adaptive_rho; prm.polish = c.polish;
   prm.warm_start = 0;
+  prm.warm_polish = 0;
   mpc::Batch bt{n, d_ids, x0, qd_meas, cmd, phase, nullptr, nullptr};
   if (mpc::launch_solve(a, bt, prm, MPC_FORM_FUSED, 0, st, nullptr, c.variant) != cudaSuccess) return MPC_ERR_CUDA;
   if (mpc::launch_gather(a, n, d_ids, tau, q_set, qd_set, value, agent_status, st) != cudaSuccess)

@@ -33,7 +33,7 @@ class MpcConfig(C.Structure):
         ("eps_abs", C.c_float), ("eps_rel", C.c_float), ("max_iter", C.c_int),
         ("fixed_iters", C.c_int), ("check_every", C.c_int), ("adaptive_rho", C.c_int),
         ("polish", C.c_int), ("warm_start", C.c_int), ("variant", C.c_int),
-        ("early_polish", C.c_float), ("graph", C.c_int),
+        ("early_polish", C.c_float), ("graph", C.c_int), ("warm_polish", C.c_int),
     ]
 
 
