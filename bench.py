@@ -8,8 +8,12 @@ updates, polish, torque map, warm-start write-back (paper Alg. 1).
 Default workload "mixed16k": 16384 agents, horizon N ~ U{5..20}, gaits
 walk/stand/hop/single-stance, FP32, warm-started from the previous replan,
 inputs of each replan perturbed (state += N(0, 0.02), phase += 0.02).  The
-per-agent state touched every step (about 1.6 GB of warm starts, factor
-caches and scratch) is far larger than L2, so no explicit flush is needed.
+replans run forward in time: every step (warm-up, timed and end-to-end)
+solves the next replan of one monotone sequence, as a 100 Hz controller
+does.  A cold solve (no warm start, as for an agent that just joined) is
+timed on its own.  The per-agent state touched every step (warm starts,
+factor caches and scratch, about 1 GB) is far larger than L2, so no explicit
+flush is needed.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -34,19 +38,18 @@ sys.path.insert(0, ROOT)
 METRIC = "agent MPC solves/s and p50/p99 latency vs 10 ms @16384 agents, chosen vs plain"
 UNIT = "agent-solves/s"
 WORKLOAD = "mixed16k"
-REPLANS = 4          # distinct pre-generated replan inputs, cycled
 FP32_LANES = 128     # FP32 FMA lanes per SM (B300)
 N_SM = 148
 # DRAM bytes per agent of the fused kernel from the last ncu capture of this
 # kernel version (profiles/mpc_k_fused_mixed16k_2048agents.md: 1.866 GB for
 # 2048 agents, tuned configuration); None once the kernel has changed since.
-TRAFFIC_BYTES_PER_AGENT = (1.306290e9 + 0.559540e9) / 2048
+TRAFFIC_BYTES_PER_AGENT = None
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
@@ -71,14 +74,15 @@ def dist_env():
 
 
 # ------------------------------------------------------------------ inputs
-def make_workload(name, n_agents, rank, world):
+def make_workload(name, n_agents, rank, world, n_replans):
+    """Agents of this rank and `n_replans` consecutive replans of them."""
     from workload import make_agents, perturb_inputs, workload_spec
     spec = workload_spec(name)
     n = n_agents or spec["n_agents"]
     ids = np.arange(rank * n, (rank + 1) * n)      # weak scaling: each rank its own agents
     model, inp = make_agents(name, ids)
     replans = [inp]
-    for r in range(1, REPLANS):
+    for r in range(1, n_replans):
         replans.append(perturb_inputs(name, replans[-1], ids, r))
     replans = [{k: np.ascontiguousarray(v, np.float32) for k, v in x.items()} for x in replans]
     return ids, model, replans
@@ -160,7 +164,18 @@ def run_ours(args):
     g.build()
     from paper_2510_12717_b300 import mpcgpu
 
-    ids, model, replans = make_workload(args.workload, args.agents, rank, world)
+    # replan 0: autotune (cold); 1..W: warm-up; W+1..W+K: timed; then the
+    # end-to-end run's 2 warm-up and K timed replans
+    W, K = args.warmup, args.steps
+    n_rep = 1 + W + K + 2 + K
+    if args.serve_seconds > 0:
+        # the serving run walks each agent forward through the same sequence:
+        # enough replans that no agent wraps around to replan 0
+        from workload import workload_spec
+        n_agents = args.agents or workload_spec(args.workload)["n_agents"]
+        per_agent = args.serve_rate * 16384 * 100.0 * args.serve_seconds / n_agents
+        n_rep = max(n_rep, 2 + int(np.ceil(1.25 * per_agent)))
+    ids, model, replans = make_workload(args.workload, args.agents, rank, world, n_rep)
     n = len(ids)
     stream = torch.cuda.Stream(dev)          # non-default stream: graph capture needs one
     torch.cuda.set_stream(stream)
@@ -189,7 +204,7 @@ def run_ours(args):
             dist.barrier()
 
     def step(s, i, ev=None):
-        x = d_in[i % REPLANS]
+        x = d_in[i]
         tk = s.submit(d_ids, x["x0"], x["qd_meas"], x["cmd"], x["phase"])
         if ev is not None:
             ev[0].record(stream)
@@ -211,7 +226,7 @@ def run_ours(args):
             s.solve(tk)
             s.get_torques(tk, **out)
         for i in range(W):
-            step(s, i)
+            step(s, 1 + i)
         barrier()
         l0 = s.stats()["kernel_launches"]
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
@@ -221,7 +236,7 @@ def run_ours(args):
             barrier()
             t0.record(stream)
             for i in range(K):
-                step(s, W + i, evs[i])
+                step(s, 1 + W + i, evs[i])
             t1.record(stream)
             barrier()
         total_ms = t0.elapsed_time(t1)
@@ -254,21 +269,47 @@ def run_ours(args):
                 [("tau", (n, 18), _t.float32), ("q_set", (n, 18), _t.float32),
                  ("qd_set", (n, 18), _t.float32), ("value", (n,), _t.float32), ("status", (n,), _t.int32)]}
     ids_pin = _t.from_numpy(slots).pin_memory().numpy()
+    e0 = 1 + W + K
     for i in range(2):
-        x = pin[i % REPLANS]
+        x = pin[e0 + i]
         s.solve_host(ids_pin, x["x0"], x["qd_meas"], x["cmd"], x["phase"], **res_host)
     barrier()
+    e2e_per = []
     h0 = time.perf_counter()
     for i in range(args.steps):
-        x = pin[i % REPLANS]
+        x = pin[e0 + 2 + i]
+        hs = time.perf_counter()
         s.solve_host(ids_pin, x["x0"], x["qd_meas"], x["cmd"], x["phase"], **res_host)
+        e2e_per.append(round(1e3 * (time.perf_counter() - hs), 3))
     barrier()
     e2e_s = time.perf_counter() - h0
     e2e = {"value": world * n * args.steps / e2e_s, "unit": UNIT,
            "h2d_bytes_per_step": int(n * (4 + 4 * (30 + 18 + 4 + 1))),
            "d2h_bytes_per_step": int(n * (4 * (18 * 3 + 1) + 4)),
-           "ms_per_step": 1e3 * e2e_s / args.steps}
+           "ms_per_step": 1e3 * e2e_s / args.steps, "per_step_ms": e2e_per}
     s.close()
+
+    # a cold solve (fresh state, no warm start): the tuned configuration, the
+    # first replan, one launch timed with events
+    cfg = tune_report["chosen"] if tune_report else \
+        {"variant": args.variant, "check_every": args.check_every, "early_polish": args.early_polish}
+    sc = mpcgpu.Solver(max_agents=n, max_horizon=int(Nh.max()), form=mpcgpu.FORM_FUSED, device=local,
+                       stream=stream.cuda_stream, variant=cfg["variant"], check_every=cfg["check_every"],
+                       early_polish=cfg["early_polish"], graph=0)
+    sc.set_models(model, slots)
+    barrier()
+    c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    x = d_in[0]
+    tk = sc.submit(d_ids, x["x0"], x["qd_meas"], x["cmd"], x["phase"])
+    c0.record(stream)
+    sc.solve(tk)
+    c1.record(stream)
+    sc.get_torques(tk, **out)
+    barrier()
+    sct = sc.agent_stats(slots)
+    cold = {"ms": c0.elapsed_time(c1), "solved_frac": float((out["status"].cpu().numpy() == 0).mean()),
+            "iters_mean": float(sct["iters"].mean()), "iters_max": int(sct["iters"].max())}
+    sc.close()
 
     plain = None
     if not args.no_plain:
@@ -296,9 +337,10 @@ def run_ours(args):
                    "graph": not args.no_graph,
                    "tuned": tune_report["chosen"] if tune_report else
                    {"variant": args.variant, "check_every": args.check_every, "early_polish": args.early_polish},
-                   "l2": "per-agent working set (~1.6 GB) >> L2; no flush"},
+                   "replans": "monotone sequence, 100 Hz (phase += 0.02 per replan)",
+                   "l2": "per-agent working set (~1 GB) >> L2; no flush"},
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
-        "latency_budget_ms": 10.0,
+        "latency_budget_ms": 10.0, "per_step_ms": [round(v, 3) for v in per], "cold_solve": cold,
         "plain": plain,
         "serving": serving,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -314,7 +356,9 @@ def run_ours(args):
                    "iters_mean": float(st["iters"].mean()), "iters_p99": float(np.percentile(st["iters"], 99)),
                    "polished_from_warm_set": float((st["polished"] == 2).mean()),
                    "refactors_mean": float(st["refactors"].mean()),
-                   "prim_res_max": float(st["prim_res"].max()), "dual_res_max": float(st["dual_res"].max())},
+                   "prim_res_max": float(st["prim_res"].max()), "dual_res_max": float(st["dual_res"].max()),
+                   "prim_scaled_max": float(st["prim_scaled"].max()),
+                   "dual_scaled_max": float(st["dual_scaled"].max())},
     }
     print(json.dumps(line), flush=True)
 

@@ -209,12 +209,16 @@ mpc_status mpc_solve_host(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host
 /* Per-agent solver statistics of the last solve of each agent, copied to
  * host arrays (any may be NULL): ADMM iterations, refactorisations, polish
  * accepted (0 no, 1 after ADMM, 2 from the warm active set without ADMM),
- * final unscaled primal and dual residuals (inf-norms).  Synchronises the
- * stream. */
+ * final unscaled primal and dual residuals (inf-norms), and the scaled
+ * residuals: the largest primal row violation / stationarity component over
+ * its own tolerance eps_abs + eps_rel * (magnitude of that row's or
+ * component's terms), the convergence measure (<= 1 converged).
+ * Synchronises the stream. */
 mpc_status mpc_get_agent_stats(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host,
                                int32_t* iters_host, int32_t* refactors_host,
                                int32_t* polished_host, float* prim_res_host,
-                               float* dual_res_host);
+                               float* dual_res_host, float* prim_scaled_host,
+                               float* dual_scaled_host);
 
 /* Checkpoint / inspection of one agent's solver state (host buffers):
  * x[(N+1)][30], u[N][30] = last primal solution (after polish, if accepted),

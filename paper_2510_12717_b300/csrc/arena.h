@@ -27,7 +27,6 @@ constexpr int VS = 32;      // stride of per-stage lane vectors
 constexpr int MAXN = 32;
 constexpr int R24 = 24;     // row stride of the dense R24 blocks
 constexpr int BLK = 528;    // floats of one R24 block (22 rows x 24)
-constexpr int CB_F = 648;   // polish, per stage: compact B_hat (136) + dense column-major B_hat (512)
 
 // float model record (MODEL_F floats per agent)
 enum : int {
@@ -41,7 +40,10 @@ enum : int { S_DT = 0, S_PERIOD = 1, S_DUTY = 2, S_OFF = 4, SCHED_D = 8 };
 // per-agent input record (IN_F floats): x0, qd_meas, cmd, phase
 enum : int { I_X0 = 0, I_QD = 32, I_CMD = 50, I_PHASE = 54, IN_F = 64 };
 // per-agent output record (OUT_F floats)
-enum : int { O_TAU = 0, O_QSET = 18, O_QDSET = 36, O_V = 54, O_PRIM = 55, O_DUAL = 56, OUT_F = 64 };
+// O_PRIM/O_DUAL: residual inf-norms; O_PRIM_N/O_DUAL_N: largest component over
+// its own tolerance (<= 1 converged)
+enum : int { O_TAU = 0, O_QSET = 18, O_QDSET = 36, O_V = 54, O_PRIM = 55, O_DUAL = 56, O_PRIM_N = 57,
+             O_DUAL_N = 58, OUT_F = 64 };
 // per-agent integer record (ST_I ints)
 enum : int { T_STATUS = 0, T_ITERS = 1, T_REFAC = 2, T_POLISHED = 3, T_N = 4, T_WARM = 5, T_FIRST = 6, ST_I = 8 };
 
@@ -74,8 +76,6 @@ struct Arena {
   float* cH;              // [A][maxN*BLK] inverse Schur blocks H_uu^-1 (R24)
   float* cE;              // [A][maxN*64] e_k = P_{k+1} c_k (lanes 0-21), arm gain (22-29),
                           //   arm e (32-39), arm H_uu^-1 (54-61)
-  float* cB;              // [A][maxN*CB_F] polish: per-stage reduced B (compact + dense)
-  float* cC;              // [A][maxN*64] polish: reduced c (0-29), reduced linear cost (32-61)
   float* xt;              // [A][(maxN+1)*VS] KKT-solve primal (x tilde)
   float* ut;              // [A][maxN*VS]
   float* dv;              // [A][maxN*VS]    feed-forward terms d_k

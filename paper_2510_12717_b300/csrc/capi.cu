@@ -116,7 +116,7 @@ static size_t arena_bytes(size_t A, size_t n) {
   f += A * IN_F;
   f += A * ((n + 1) * VS + n * VS + 3 * n * RS);     // xref uref rlo rhi rcls
   f += A * lin_floats((int)n);
-  f += A * (2 * n * BLK + n * CB_F + 2 * n * 64);    // cK cH cB cE cC
+  f += A * (2 * n * BLK + n * 64);                   // cK cH cE
   f += A * ((n + 1) * VS + 2 * n * VS + n * RS + 1); // xt ut dv act order
   f += A * (1 + 30 + 18 + 4 + 1 + 18 * 3 + 2);       // host-path staging
   f += A * (MODEL_F + 2 * SCHED_D + 1);              // model upload staging
@@ -207,8 +207,6 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   AL(a.cK, A * n * BLK);
   AL(a.cH, A * n * BLK);
   AL(a.cE, A * n * 64);
-  AL(a.cB, A * n * CB_F);
-  AL(a.cC, A * n * 64);
   AL(a.xt, A * (n + 1) * VS);
   AL(a.ut, A * n * VS);
   AL(a.dv, A * n * VS);
@@ -550,7 +548,7 @@ mpc_status mpc_solve_host(mpc_ctx* ctx, int32_t n, const int32_t* ids, const flo
 }
 
 mpc_status mpc_get_agent_stats(mpc_ctx* ctx, int32_t n, const int32_t* ids, int32_t* iters, int32_t* refactors,
-                               int32_t* polished, float* prim, float* dual) {
+                               int32_t* polished, float* prim, float* dual, float* prim_n, float* dual_n) {
   if (!ctx) return MPC_ERR_INVALID;
   if (n < 0 || (n > 0 && !ids)) return fail(ctx, MPC_ERR_INVALID, "get_agent_stats: bad arguments");
   CK(cudaSetDevice(ctx->cfg.device));
@@ -569,6 +567,8 @@ mpc_status mpc_get_agent_stats(mpc_ctx* ctx, int32_t n, const int32_t* ids, int3
     if (polished) polished[i] = s[mpc::T_POLISHED] ? (s[mpc::T_FIRST] ? 2 : 1) : 0;
     if (prim) prim[i] = o[mpc::O_PRIM];
     if (dual) dual[i] = o[mpc::O_DUAL];
+    if (prim_n) prim_n[i] = o[mpc::O_PRIM_N];
+    if (dual_n) dual_n[i] = o[mpc::O_DUAL_N];
   }
   return MPC_OK;
 }

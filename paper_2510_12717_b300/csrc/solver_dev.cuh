@@ -57,7 +57,7 @@ struct AgentPtrs {
   int N;
   float *x, *u, *w, *y, *rho;
   int* warm;
-  float *inp, *xref, *uref, *rlo, *rhi, *rcls, *lin, *cK, *cH, *cE, *cB, *cC, *xt, *ut, *dv;
+  float *inp, *xref, *uref, *rlo, *rhi, *rcls, *lin, *cK, *cH, *cE, *xt, *ut, *dv;
   int* act;
   float* out;
   int* st;
@@ -85,8 +85,6 @@ __device__ __forceinline__ AgentPtrs agent_ptrs(const Arena& a, int s) {
   p.cK = a.cK + (size_t)s * n * BLK;
   p.cH = a.cH + (size_t)s * n * BLK;
   p.cE = a.cE + (size_t)s * n * 64;
-  p.cB = a.cB + (size_t)s * n * CB_F;
-  p.cC = a.cC + (size_t)s * n * 64;
   p.xt = a.xt + (size_t)s * (n + 1) * VS;
   p.ut = a.ut + (size_t)s * n * VS;
   p.dv = a.dv + (size_t)s * n * VS;
@@ -206,28 +204,59 @@ __device__ __forceinline__ float r24_mv(const float* M, const float* v, int lane
 }
 
 // In-place inverse of a symmetric positive definite R24 block by Gauss-Jordan
-// elimination without pivoting; lane j updates column j.
-__device__ __forceinline__ void r24_inv(float* H, int lane) {
+// elimination without pivoting, in the symmetric (sweep) form: lane j keeps
+// column j in registers.  Pivoting on p maps M to M' with
+//   M'_pp = 1/M_pp,  M'_pj = M_pj/M_pp,  M'_ip = -M_ip/M_pp,
+//   M'_ij = M_ij - M_ip M_pj/M_pp,
+// so after pivots 0..p-1 the entries with exactly one index among the pivoted
+// ones are antisymmetric and the rest symmetric: the pivot column p is row p
+// with the sign of rows i < p flipped.  Row p is one register per lane, so a
+// pivot costs one shared-memory vector (double buffered in sc, 2 x 32 floats,
+// 16-byte aligned) and one warp barrier.  Pivot p writes row p+1 into the
+// other buffer, which every lane finished reading at pivot p-1.
+__device__ __forceinline__ void r24_inv(float* H, float* sc, int lane) {
   const int j = lane < NC ? lane : NC - 1;
+  float h[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) h[i] = H[i * R24 + j];
+  sc[lane] = h[0];
+#pragma unroll
   for (int p = 0; p < NC; ++p) {
-    float col[NC];
-#pragma unroll
-    for (int i = 0; i < NC; ++i) col[i] = H[i * R24 + p];
-    const float rowp = H[p * R24 + j];
-    const float inv = 1.f / col[p];
     __syncwarp();
-    if (lane < NC) {
-      if (j == p) {
+    float v[24];
+    const float4* b4 = reinterpret_cast<const float4*>(sc + (p & 1) * 32);
 #pragma unroll
-        for (int i = 0; i < NC; ++i) H[i * R24 + j] = (i == p) ? inv : -col[i] * inv;
-      } else {
-        const float rp = rowp * inv;
-#pragma unroll
-        for (int i = 0; i < NC; ++i) H[i * R24 + j] = (i == p) ? rp : fmaf(-col[i], rp, H[i * R24 + j]);
-      }
+    for (int q = 0; q < 6; ++q) {
+      const float4 t = b4[q];
+      v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
     }
-    __syncwarp();
+    // the pivot of an SPD block is positive and well away from 0: the fast
+    // reciprocal (2 ulp) is ample
+    const float inv = __fdividef(1.f, v[p]);
+    float* nxt = sc + ((p + 1) & 1) * 32;   // row p+1 goes out first (the next pivot waits on it)
+    if (j == p) {
+      if (p + 1 < NC) { h[p + 1] = -h[p + 1] * inv; nxt[lane] = h[p + 1]; }
+#pragma unroll
+      for (int i = 0; i < NC; ++i)
+        if (i != p && i != p + 1) h[i] = -h[i] * inv;
+      h[p] = inv;
+    } else {
+      const float rp = h[p] * inv;
+      if (p + 1 < NC) { h[p + 1] = fmaf(-v[p + 1], rp, h[p + 1]); nxt[lane] = h[p + 1]; }
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        if (i == p || i == p + 1) continue;
+        const float ci = i < p ? -v[i] : v[i];   // M_ip
+        h[i] = fmaf(-ci, rp, h[i]);
+      }
+      h[p] = rp;
+    }
   }
+  if (lane < NC) {
+#pragma unroll
+    for (int i = 0; i < NC; ++i) H[i * R24 + j] = h[i];
+  }
+  __syncwarp();
 }
 
 // dense column-major (LDD) mat-vec, lane row i: sum_j M(i, j) v_j

@@ -316,12 +316,19 @@ __device__ __forceinline__ void load_lin(const AgentPtrs& ap, float* sm, int lan
 struct StageIn {
   const float* c;     // affine term c_k of the coupled lanes (smem vector)
   float rt_diag;      // this lane's diagonal of R_t
-  float rt_off[3];    // force lanes: R_t(row b+r, j) of the foot block; arm lanes: [0] = B, [1] = c
+  float rt_off[3];    // force lanes: R_t(row b+r, j) of the foot block; arm lanes: [0] = B, [1] = c, [2] = A
   float qt;           // this lane's diagonal of Q_t for x_k (k >= 1)
+  float rh;           // polish: this lane's linear cost of the reduced input
 };
+// per-lane results of one factor stage: e (coupled: (P_{k+1} c_k)_i; arm:
+// P_{k+1} c), and for arm lanes the scalar gain and inverse
+struct StageOut { float e, Ka, Hi; };
 
-__device__ __forceinline__ void factor_stage(const AgentPtrs& ap, float* sm, int lane, int k,
-                                             const StageIn& in, float* Pa, const LanePat& pat) {
+__device__ __forceinline__ StageOut factor_stage(const AgentPtrs& ap, float* sm, int lane, int k,
+                                                 const StageIn& in, float* Pa, const LanePat& pat,
+                                                 bool store_h = true) {
+  StageOut so;
+  so.e = so.Ka = so.Hi = 0.f;
   float* P = sm + S_P; float* H = sm + S_H; float* X = sm + S_X; float* K = sm + S_K;
   const float* av = sm + S_AV;
   const float* bv = sm + S_BV;
@@ -393,12 +400,13 @@ __device__ __forceinline__ void factor_stage(const AgentPtrs& ap, float* sm, int
     }
   }
   __syncwarp();
-  r24_inv(H, lane);
+  r24_inv(H, sm + S_VEC + V_S * 64, lane);   // V_S is free during a factor stage
   r24_gemm_tn(K, H, X, nullptr, -1.f, lane);     // K = -H_uu^-1 H_ux (H_uu^-1 symmetric)
   copy_blk(ap.cK + (size_t)k * BLK, K, lane);
-  copy_blk(ap.cH + (size_t)k * BLK, H, lane);
+  if (store_h) copy_blk(ap.cH + (size_t)k * BLK, H, lane);
   float* ce = ap.cE + k * 64;
   if (lane < NC) ce[lane] = e;
+  so.e = e;
   // arm lanes: scalar Riccati with A = rt_off[2], B = rt_off[0], c = rt_off[1]
   if (lane >= NC && lane < 30) {
     const float Bh = in.rt_off[0], Aa = in.rt_off[2];
@@ -409,6 +417,9 @@ __device__ __forceinline__ void factor_stage(const AgentPtrs& ap, float* sm, int
     ce[lane] = Ka;
     ce[32 + lane] = Hi;
     ce[32 + lane - NC] = (*Pa) * in.rt_off[1];   // e of the arm lane
+    so.e = (*Pa) * in.rt_off[1];
+    so.Ka = Ka;
+    so.Hi = Hi;
     if (k >= 1) *Pa = in.qt + Aa * Aa * (*Pa) + Hux * Ka;
   }
   if (k >= 1) {
@@ -426,6 +437,7 @@ __device__ __forceinline__ void factor_stage(const AgentPtrs& ap, float* sm, int
     }
   }
   __syncwarp();
+  return so;
 }
 
 // ADMM stage inputs: R_t = 2 dt R + sigma I + rho C_u^T diag(cls) C_u
@@ -438,6 +450,7 @@ __device__ __forceinline__ StageIn admm_stage_in(const AgentPtrs& ap, int k, flo
   in.c = cvec;
   in.rt_off[0] = in.rt_off[1] = in.rt_off[2] = 0.f;
   in.rt_diag = 0.f;
+  in.rh = 0.f;
   in.qt = (k >= 1 && lane < 30) ? qt_x(ap, k, lane, rho, sigma) : 0.f;
   if (lane < NC) {
     const int j = lane;
@@ -644,9 +657,21 @@ __device__ void admm_iteration(const AgentPtrs& ap, float* sm, int lane, float r
 // Unscaled OSQP residuals of the current iterate: primal |C z - w|_inf over
 // constrained rows; dual = stationarity in u after choosing the dynamics
 // multipliers that make stationarity in x exact (costate recursion).
-struct Res { float rp, rd, ps, ds; };
+// Residuals: rp, rd the inf-norms of the primal and dual residuals; ps, ds
+// the global scales (for the rho update); pn, dn the largest residual
+// component over its own tolerance eps_abs + eps_rel * (magnitude of the
+// terms of that row or stationarity component), the convergence measure
+// (<= 1 converged): the components differ by orders of magnitude (forces vs
+// joint rates), and one global scale would let the small ones go unchecked.
+struct Res { float rp, rd, ps, ds, pn, dn; };
+// A polished point must also pass every row and component at kScaledAccept
+// times its own tolerance: FP32 rounding of a correct polish stays below ~5
+// there, while an active row whose multiplier has the wrong sign (a wrong
+// active set that the global scales let through) lands at 10^2 and above.
+constexpr float kScaledAccept = 10.f;
 
-__device__ __noinline__ Res admm_residuals(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat) {
+__device__ __noinline__ Res admm_residuals(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm,
+                                           const LanePat& pat) {
   const int N = ap.N;
   const float* md = ap.mdl;
   const float dt = md[M_DT], mu = md[M_MU];
@@ -658,7 +683,8 @@ __device__ __noinline__ Res admm_residuals(const AgentPtrs& ap, float* sm, int l
   const float* xs = ap.x;
   const float* us = ap.u;
   const float* ys = ap.y;
-  float rp = 0.f, ps = 0.f, rd = 0.f, ds = 0.f;
+  const float ea = prm.eps_abs, er = prm.eps_rel;
+  float rp = 0.f, ps = 0.f, rd = 0.f, ds = 0.f, pn = 0.f, dn = 0.f;
   for (int k = 0; k < N; ++k) {
     vU[lane] = us[k * VS + lane];
     vXN[lane] = xs[(k + 1) * VS + lane];
@@ -667,8 +693,10 @@ __device__ __noinline__ Res admm_residuals(const AgentPtrs& ap, float* sm, int l
       if (ap.rcls[k * RS + r] > 0.f) {
         const float v = crow(vU, vXN, r, mu);
         const float w = ap.w[k * RS + r];
+        const float sc = fmaxf(fabsf(v), fabsf(w));
         rp = fmaxf(rp, fabsf(v - w));
-        ps = fmaxf(ps, fmaxf(fabsf(v), fabsf(w)));
+        ps = fmaxf(ps, sc);
+        pn = fmaxf(pn, fabsf(v - w) / (ea + er * sc));
       }
     }
     __syncwarp();
@@ -688,8 +716,12 @@ __device__ __noinline__ Res admm_residuals(const AgentPtrs& ap, float* sm, int l
     if (lane < 30) {
       const float cty = cuT(vY, lane, mu);
       const float gu = twoR * (us[k * VS + lane] - ap.uref[k * VS + lane]) + cty;
-      const float ru = gu + (lane < NC ? cc_tv(sm + S_BV, pat.br, vM, lane) : dt * m);
+      const float btm = lane < NC ? cc_tv(sm + S_BV, pat.br, vM, lane) : dt * m;
+      const float ru = gu + btm;
       rd = fmaxf(rd, fabsf(ru));
+      const float su = fmaxf(fmaxf(fabsf(twoR * us[k * VS + lane]), fabsf(twoR * ap.uref[k * VS + lane])),
+                             fmaxf(fabsf(cty), fabsf(btm)));
+      dn = fmaxf(dn, fabsf(ru) / (ea + er * su));
       ds = fmaxf(ds, fmaxf(fabsf(twoR * us[k * VS + lane]), fabsf(twoR * ap.uref[k * VS + lane])));
       ds = fmaxf(ds, fmaxf(fabsf(cty), fabsf(twoQ * xs[(k + 1) * VS + lane])));
       ds = fmaxf(ds, fabsf(twoQ * ap.xref[(k + 1) * VS + lane]));
@@ -701,6 +733,7 @@ __device__ __noinline__ Res admm_residuals(const AgentPtrs& ap, float* sm, int l
   }
   Res out;
   out.rp = warp_max(rp); out.ps = warp_max(ps); out.rd = warp_max(rd); out.ds = warp_max(ds);
+  out.pn = warp_max(pn); out.dn = warp_max(dn);
   return out;
 }
 
@@ -709,8 +742,11 @@ __device__ __noinline__ Res admm_residuals(const AgentPtrs& ap, float* sm, int l
 // when w - lo < -y, at its upper bound when hi - w < y).  Active rows are
 // eliminated exactly: u_k = G_k v_k + t_k, and the reduced equality-
 // constrained LQ problem is solved by one more Riccati factor + sweep.
-// Joint-box (state) rows are not handled: if one is active the polish is
-// skipped.  Active-set codes: bit 0 lower, bit 1 upper, 3 = equality row.
+// An active joint-box row (on x_{k+1}) eliminates the joint rate of stage k
+// through q_{k+1} = q_k + dt qd_k; a joint with both its rate row and its
+// joint-box row active at one stage keeps only one of them (a degenerate
+// optimum that needs both is left to ADMM).
+// Active-set codes: bit 0 lower, bit 1 upper, 3 = equality row.
 struct FootAct { int swing, zero, top, tx, ty; };
 
 __device__ void init_active(const AgentPtrs& ap, int lane) {
@@ -802,19 +838,20 @@ __device__ __forceinline__ Elim lane_elim(const AgentPtrs& ap, int k, const int*
   return e;
 }
 
-// Per-stage inputs of the polish factor: compact B_hat = B G (into smem, and
-// to global with a dense column-major copy for the sweep), R_hat = G^T D G
-// plus 1 on eliminated inputs, c_hat = c + B t, r_hat = G^T D (t - u_ref).
-__device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const int* act, float* cvec, int lane) {
+// Per-stage inputs of the polish factor: compact B_hat = B G (into smem),
+// R_hat = G^T D G plus 1 on eliminated inputs, c_hat = c + B t (into cvec),
+// r_hat = G^T D (t - u_ref) (per lane), Q_t of x_k with the moved cost of an
+// eliminated joint rate, A_hat (identity entry of an eliminated joint).
+__device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const int* act, float* cvec,
+                                   const Elim& el, int lane) {
   const float* md = ap.mdl;
-  const float dt = md[M_DT], mu = md[M_MU];
+  const float dt = md[M_DT];
   const float* bbase = ap.lin + L_BV;
   float* vec = sm + S_VEC;
   float* gfv = vec + V_T * 64;       // rows of G_f, 3 per force input (indexed 3*i)
   float* gv = vec + V_G * 64;        // g per input
   float* tv = vec + V_D * 64;        // t per input
   float* vD2 = vec + V_H * 64;       // D (t - u_ref)
-  const Elim el = lane_elim(ap, k, act, lane, mu);
   const float Dj = lane < 30 ? 2.f * dt * md[M_R + lane] : 0.f;
   if (lane < 30) {
     gv[lane] = el.g;
@@ -829,25 +866,25 @@ __device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const 
   in.c = cvec;
   in.rt_off[0] = in.rt_off[1] = in.rt_off[2] = 0.f;
   in.rt_diag = 0.f;
+  in.rh = 0.f;
   // state cost of x_k; an eliminated joint rate moves its cost dt R u^2 onto
   // x_k:  (R/dt) (x_i - b)^2
   in.qt = lane < 30 ? 2.f * dt * md[M_Q + lane] + (el.qbox ? 2.f * md[M_R + lane] / dt : 0.f) : 0.f;
   // A_hat = A + B Phi: the eliminated joint's identity entry vanishes
   if (el.qbox && lane >= 12 && lane < NC) sm[S_AV + lane * 6] = 0.f;
-  float* cc = ap.cC + k * 64;
-  float* gB = ap.cB + (size_t)k * CB_F;
   if (lane < NC) {
     const int j = lane;
     const bool fj = j < 12 && (j % 6) < 3;
     const int b = (j / 6) * 6, c = j - b;
-    float bh[6];
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
+      float v;
       if (fj)
-        bh[t] = bbase[(b + 0) * 6 + t] * gfv[(b + 0) * 3 + c] + bbase[(b + 1) * 6 + t] * gfv[(b + 1) * 3 + c] +
-                bbase[(b + 2) * 6 + t] * gfv[(b + 2) * 3 + c];
+        v = bbase[(b + 0) * 6 + t] * gfv[(b + 0) * 3 + c] + bbase[(b + 1) * 6 + t] * gfv[(b + 1) * 3 + c] +
+            bbase[(b + 2) * 6 + t] * gfv[(b + 2) * 3 + c];
       else
-        bh[t] = bbase[j * 6 + t] * gv[j];
+        v = bbase[j * 6 + t] * gv[j];
+      sm[S_BV + j * 6 + t] = v;
     }
     if (fj) {
       float d = 0.f, alive = 0.f;
@@ -859,237 +896,260 @@ __device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const 
         for (int r = 0; r < 3; ++r) in.rt_off[r] += gfv[(b + l) * 3 + r] * Dl * g;
       }
       in.rt_diag = d + (1.f - alive);
+      in.rh = gfv[(b + 0) * 3 + c] * vD2[b] + gfv[(b + 1) * 3 + c] * vD2[b + 1] + gfv[(b + 2) * 3 + c] * vD2[b + 2];
     } else {
       in.rt_diag = gv[j] * Dj * gv[j] + (1.f - gv[j]);
+      in.rh = gv[j] * vD2[j];
     }
-#pragma unroll
-    for (int t = 0; t < 6; ++t) { sm[S_BV + j * 6 + t] = bh[t]; gB[j * 6 + t] = bh[t]; }
-    float* dn = gB + 136 + j * LDD;
-    for (int i = 0; i < NC; ++i) dn[i] = 0.f;
-#pragma unroll
-    for (int t = 0; t < 6; ++t)
-      if (t < bcnt(j)) dn[brow(j, t)] = bh[t];
-    // c_hat and r_hat
-    const float chat = ap.lin[L_STAGE + k * 64 + 32 + j] + cm_mv(sm + S_B, tv, lane);
-    cvec[j] = chat;
-    cc[j] = chat;
-    cc[32 + j] = fj ? gfv[(b + 0) * 3 + c] * vD2[b] + gfv[(b + 1) * 3 + c] * vD2[b + 1] +
-                          gfv[(b + 2) * 3 + c] * vD2[b + 2]
-                    : gv[j] * vD2[j];
+    cvec[j] = ap.lin[L_STAGE + k * 64 + 32 + j] + cm_mv(sm + S_B, tv, lane);   // c_hat
   } else if (lane < 30) {
     const float alive = el.g;
     in.rt_diag = alive * Dj + (1.f - alive);
     in.rt_off[0] = alive * dt;                  // arm B_hat
     in.rt_off[1] = (1.f - alive) * dt * el.t;   // arm c_hat
     in.rt_off[2] = el.qbox ? 0.f : 1.f;         // arm A_hat
-    cc[lane] = in.rt_off[1];
-    cc[32 + lane] = alive * vD2[lane];
+    in.rh = alive * vD2[lane];
   }
   __syncwarp();
   return in;
 }
 
-// Factor and solve the reduced problem; the polished primal goes to xt/ut.
-// Overwrites the Riccati caches (the caller refactors if ADMM continues).
-__device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat) {
+// Factor and solve the reduced problem in one backward pass (the linear
+// recursion rides along with the Riccati recursion, since the reduced problem
+// is solved once), then roll forward with u = G v + t + Phi x through the
+// original dynamics.  The polished primal goes to xt/ut.  Overwrites the
+// Riccati caches (the caller refactors if ADMM continues).
+__device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat, Pipe& pp) {
   const int N = ap.N;
   const float* md = ap.mdl;
   const float dt = md[M_DT], mu = md[M_MU];
-  float* P = sm + S_P; float* H = sm + S_H; float* X = sm + S_X; float* K = sm + S_K;
+  float* P = sm + S_P; float* H = sm + S_H; float* K = sm + S_K;
   float* vec = sm + S_VEC;
   float* cvec = vec + V_C * 64;
   int* act = reinterpret_cast<int*>(vec + V_ACT * 64);
+  float* vS = vec + V_S * 64; float* vH = vec + V_H * 64; float* vX = vec + V_X * 64;
+  float* vV = vec + V_U * 64; float* vU = vec + V_XN * 64;
   const int j = lane < NC ? lane : NC - 1;
   const bool arm = lane >= NC && lane < 30;
   const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
 
-  // a joint whose rate box and joint box are both active at one stage -> no polish
-  int conflict = 0;
+  // a joint whose rate row and joint-box row are both marked active at one
+  // stage (the guess usually marks a joint-box row that the optimum only
+  // nearly touches): keep the row with the larger multiplier estimate; the
+  // check and its corrections settle the rest
   for (int k = 0; k < N; ++k)
-    for (int j = lane; j < 18; j += 32) conflict |= (ap.act[k * RS + 20 + j] != 0) && (ap.act[k * RS + 38 + j] != 0);
-  if (warp_or(conflict)) return false;
+    for (int jj = lane; jj < 18; jj += 32) {
+      int* a = ap.act + k * RS;
+      if (a[20 + jj] != 0 && a[38 + jj] != 0) {
+        if (fabsf(ap.y[k * RS + 38 + jj]) >= fabsf(ap.y[k * RS + 20 + jj])) a[20 + jj] = 0;
+        else a[38 + jj] = 0;
+      }
+    }
+  __syncwarp();
 
-  // ---- factor of the reduced problem (cost 2dt Q, 2dt R; no sigma, no rho)
+  // ---- backward: Riccati factor of the reduced problem (cost 2dt Q, 2dt R;
+  // no sigma, no rho) and its linear recursion
   if (lane < NC) {
     for (int i = 0; i < NC; ++i) P[i * R24 + j] = 0.f;
     P[j * R24 + j] = 2.f * dt * md[M_Q + j];
   }
   float Pa = arm ? twoQ : 0.f;
+  float p = lane < 30 ? -twoQ * ap.xref[N * VS + lane] : 0.f;
   __syncwarp();
   for (int k = N - 1; k >= 0; --k) {
     stage_active(ap, k, act, lane);
     set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
-    const StageIn in = polish_stage_in(ap, sm, k, act, cvec, lane);
-    factor_stage(ap, sm, lane, k, in, &Pa, pat);
-  }
-
-  // ---- backward sweep of the reduced problem
-  float* vS = vec + V_S * 64; float* vH = vec + V_H * 64; float* vX = vec + V_X * 64;
-  float* vV = vec + V_U * 64;
-  float p = lane < 30 ? -twoQ * ap.xref[N * VS + lane] : 0.f;
-  for (int k = N - 1; k >= 0; --k) {
-    const float* ce = ap.cE + k * 64;
-    const float* cc = ap.cC + k * 64;
-    const float* gB = ap.cB + (size_t)k * CB_F;
-    stage_active(ap, k, act, lane);
     const Elim el = lane_elim(ap, k, act, lane, mu);
-    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
-    if (el.qbox && lane >= 12 && lane < NC) sm[S_AV + lane * 6] = 0.f;
-    copy_blk(K, ap.cK + (size_t)k * BLK, lane);
-    copy_blk(H, ap.cH + (size_t)k * BLK, lane);
-    copy_n(sm + S_BV, gB, 136 / 4, lane);
-    const float s = p + (lane < NC ? ce[lane] : (arm ? ce[32 + lane - NC] : 0.f));
+    const StageIn in = polish_stage_in(ap, sm, k, act, cvec, el, lane);
+    const StageOut so = factor_stage(ap, sm, lane, k, in, &Pa, pat, false);
+    // H (= H_uu^-1) and K of stage k are still in smem
+    const float s = p + so.e;
     vS[lane] = s;
     __syncwarp();
     float h = 0.f;
-    if (lane < NC) h = cc[32 + lane] + cc_tv(sm + S_BV, pat.br, vS, lane);
-    else if (arm) h = cc[32 + lane] + el.g * dt * s;
+    if (lane < NC) h = in.rh + cc_tv(sm + S_BV, pat.br, vS, lane);
+    else if (arm) h = in.rh + el.g * dt * s;
     vH[lane] = h;
     __syncwarp();
     float d = 0.f;
     if (lane < NC) d = -r24_mtv(H, vH, lane);
-    else if (arm) d = -ce[32 + lane] * h;
+    else if (arm) d = -so.Hi * h;
     ap.dv[k * VS + lane] = d;
     if (k >= 1) {
       // linear cost of x_k (with the moved cost of an eliminated joint rate)
       float ql = lane < 30 ? -twoQ * ap.xref[k * VS + lane] : 0.f;
       if (el.qbox) ql -= 2.f * md[M_R + lane] * el.t;
       if (lane < NC) p = ql + cc_tv(sm + S_AV, pat.ar, vS, lane) + r24_mtv(K, vH, lane);
-      else if (arm) p = ql + (el.qbox ? 0.f : s) + ce[lane] * h;
+      else if (arm) p = ql + (el.qbox ? 0.f : s) + so.Ka * h;
     }
     __syncwarp();
   }
-  // ---- forward rollout, u = G v + t
+  // restore the compact B of the original problem
+  copy_n(sm + S_BV, ap.lin + L_BV, 136 / 4, lane);
+  fence_proxy_async();   // K_k were written with generic stores; the rollout reads them by TMA
+  __syncwarp();
+
+  // ---- forward rollout: v = K x + d, u = G v + t + Phi x, x+ = A x + B u + c
+  float* const K0 = sm + S_P; float* const K1 = sm + S_X;
   float x = lane < 30 ? ap.x[lane] : 0.f;
+  pipe_issue(pp, 0, K0, ap.cK, nullptr, nullptr, lane);
   for (int k = 0; k < N; ++k) {
+    const int b = k & 1;
+    float* const Kc = b ? K1 : K0;
+    if (k + 1 < N) pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k + 1) * BLK, nullptr, nullptr, lane);
     const float* ce = ap.cE + k * 64;
-    const float* cc = ap.cC + k * 64;
     const float* dA = ap.lin + L_STAGE + k * 64;
     stage_active(ap, k, act, lane);
     const Elim el = lane_elim(ap, k, act, lane, mu);
-    copy_blk(K, ap.cK + (size_t)k * BLK, lane);
-    copy_n(X, ap.cB + (size_t)k * CB_F + 136, MB / 4, lane);     // dense B_hat
     vX[lane] = x;
+    const float dk = ap.dv[k * VS + lane];
+    pipe_wait(pp, b);
     __syncwarp();
     float v = 0.f;
-    if (lane < NC) v = r24_mv(K, vX, lane) + ap.dv[k * VS + lane];
-    else if (arm) v = ce[lane] * x + ap.dv[k * VS + lane];
+    if (lane < NC) v = r24_mv(Kc, vX, lane) + dk;
+    else if (arm) v = ce[lane] * x + dk;
     vV[lane] = v;
     __syncwarp();
-    float xn = 0.f, u = 0.f;
-    if (lane < NC) {
-      xn = el.qbox ? cc[lane] : ak_mv(sm + S_AB, dA, vX, lane) + cm_mv(X, vV, lane) + cc[lane];
-      if (lane < 12 && (lane % 6) < 3) {
-        const int b = (lane / 6) * 6;
-        u = el.gf[0] * vV[b] + el.gf[1] * vV[b + 1] + el.gf[2] * vV[b + 2] + el.t;
-      } else {
-        u = el.g * v + el.t + el.phi * x;
-      }
-    } else if (arm) {
-      xn = (el.qbox ? 0.f : x) + el.g * dt * v + cc[lane];
+    float u = 0.f;
+    if (lane < 12 && (lane % 6) < 3) {
+      const int bb = (lane / 6) * 6;
+      u = el.gf[0] * vV[bb] + el.gf[1] * vV[bb + 1] + el.gf[2] * vV[bb + 2] + el.t;
+    } else if (lane < 30) {
       u = el.g * v + el.t + el.phi * x;
     }
+    vU[lane] = u;
+    __syncwarp();
+    float xn = 0.f;
+    if (lane < NC) xn = ak_mv(sm + S_AB, dA, vX, lane) + cm_mv(sm + S_B, vU, lane) + dA[32 + lane];
+    else if (arm) xn = x + dt * u;
     ap.xt[(k + 1) * VS + lane] = xn;
     ap.ut[k * VS + lane] = u;
     x = xn;
     __syncwarp();
   }
-  // restore the compact B of the ADMM problem
-  copy_n(sm + S_BV, ap.lin + L_BV, 136 / 4, lane);
-  __syncwarp();
-  return true;
+  return !warp_or(pp.timeout);
 }
 
-// Optimality check of the polished point (xt, ut): KKT conditions of the
-// guessed active set (stationarity in the free directions, right sign of the
-// multipliers of the active rows, dynamics multipliers from the costate
-// recursion), then primal feasibility of every row.  With `fix` the active
-// set is corrected for a next attempt: active rows whose multiplier has the
-// wrong sign are dropped, rows the point violates are added; *changed
-// reports whether anything changed.
-__device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, bool fix,
-                            int* changed, const LanePat& pat) {
+// Optimality check of the polished point (xt, ut), one backward pass: KKT
+// conditions of the guessed active set (stationarity in the free directions,
+// right sign of the multipliers of the active rows, dynamics multipliers from
+// the costate recursion) and primal feasibility of every row, each measured
+// against its own tolerance (see Res).  With FIX (after a failed check) the
+// active set is corrected for a next attempt: active rows whose multiplier
+// has the wrong sign by more than tol_d are dropped, rows the point violates
+// by more than tol_p are added (the two touch disjoint rows; the stage's
+// conditions are read from the copy in act taken before either), and
+// *changed reports whether anything changed.  The thresholds are the tighter
+// of the failed check's global tolerances (tol_p, tol_d) and kScaledAccept
+// times the row's or component's own tolerance.
+template <bool FIX>
+__device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm,
+                                         int* changed, const LanePat& pat, float tol_p = 0.f,
+                                         float tol_d = 0.f) {
   const int N = ap.N;
   const float* md = ap.mdl;
   const float dt = md[M_DT], mu = md[M_MU];
+  const float ea = prm.eps_abs, er = prm.eps_rel;
   float* vec = sm + S_VEC;
   float* vU = vec + V_U * 64; float* vXN = vec + V_XN * 64; float* vM = vec + V_S * 64;
-  float* vG = vec + V_G * 64;
+  float* vG = vec + V_G * 64; float* vT = vec + V_T * 64;
   int* act = reinterpret_cast<int*>(vec + V_ACT * 64);
   const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
   const float twoR = lane < 30 ? 2.f * dt * md[M_R + lane] : 0.f;
   const float* xs = ap.xt;
   const float* us = ap.ut;
-  float rp = 0.f, ps = 0.f, rd = 0.f, ds = 0.f;
+  float rp = 0.f, ps = 0.f, rd = 0.f, ds = 0.f, pn = 0.f, dn = 0.f;
   int chg = 0;
-  // scales (they set the tolerances)
-  for (int k = 0; k < N; ++k) {
-    if (lane < 30) {
-      ds = fmaxf(ds, fmaxf(fabsf(twoR * us[k * VS + lane]), fabsf(twoR * ap.uref[k * VS + lane])));
-      ds = fmaxf(ds, fmaxf(fabsf(twoQ * xs[(k + 1) * VS + lane]), fabsf(twoQ * ap.xref[(k + 1) * VS + lane])));
-    }
-    vU[lane] = us[k * VS + lane];
-    vXN[lane] = xs[(k + 1) * VS + lane];
-    __syncwarp();
-    for (int r = lane; r < NR; r += 32)
-      if (ap.rcls[k * RS + r] > 0.f) ps = fmaxf(ps, fabsf(crow(vU, vXN, r, mu)));
-    __syncwarp();
-  }
-  ps = warp_max(ps);
-  ds = warp_max(ds);
-  const float tol_p = prm.eps_abs + prm.eps_rel * ps;
-  const float tol_d = prm.eps_abs + prm.eps_rel * ds;
-  // dual conditions, costate backward
   float m = lane < 30 ? twoQ * (xs[N * VS + lane] - ap.xref[N * VS + lane]) : 0.f;
   for (int k = N - 1; k >= 0; --k) {
     stage_active(ap, k, act, lane);
     set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
     vM[lane] = m;
-    __syncwarp();
-    float g = 0.f;
-    if (lane < 30)
-      g = twoR * (us[k * VS + lane] - ap.uref[k * VS + lane]) +
-          (lane < NC ? cc_tv(sm + S_BV, pat.br, vM, lane) : dt * m);
-    vG[lane] = g;
+    vU[lane] = us[k * VS + lane];
+    vXN[lane] = xs[(k + 1) * VS + lane];
     __syncwarp();
     int* ak = ap.act + k * RS;
+    // primal feasibility of the rows of stage k
+    for (int r = lane; r < NR; r += 32) {
+      const float v = crow(vU, vXN, r, mu);
+      const float lo = ap.rlo[k * RS + r], hi = ap.rhi[k * RS + r];
+      if (ap.rcls[k * RS + r] > 0.f) ps = fmaxf(ps, fabsf(v));
+      const float viol = fmaxf(fmaxf(lo - v, v - hi), 0.f);
+      float sc = fabsf(v);
+      if (isfinite(lo)) sc = fmaxf(sc, fabsf(lo));
+      if (isfinite(hi)) sc = fmaxf(sc, fabsf(hi));
+      const float tp = ea + er * sc;
+      rp = fmaxf(rp, viol);
+      pn = fmaxf(pn, viol / tp);
+      if (FIX && viol > fminf(tol_p, kScaledAccept * tp) && act[r] == 0) {
+        ak[r] = (v < lo) ? 1 : 2;
+        chg = 1;
+        // a joint's rate row and joint-box row are not kept active together
+        // (the polish would drop one again): the row that enters displaces
+        // the other one of the same joint and stage
+        if (r >= 38 && act[r - 18] != 0) ak[r - 18] = 0;
+        else if (r >= 20 && r < 38 && act[r + 18] != 0) ak[r + 18] = 0;
+      }
+    }
+    // stationarity of the inputs without their row multipliers, and its tolerance
+    float g = 0.f, td = 1.f;
+    if (lane < 30) {
+      const float u = us[k * VS + lane], ur = ap.uref[k * VS + lane];
+      const float btm = lane < NC ? cc_tv(sm + S_BV, pat.br, vM, lane) : dt * m;
+      g = twoR * (u - ur) + btm;
+      td = ea + er * fmaxf(fmaxf(fabsf(twoR * u), fabsf(twoR * ur)), fabsf(btm));
+      ds = fmaxf(ds, fmaxf(fabsf(twoR * u), fabsf(twoR * ur)));
+      ds = fmaxf(ds, fmaxf(fabsf(twoQ * xs[(k + 1) * VS + lane]), fabsf(twoQ * ap.xref[(k + 1) * VS + lane])));
+    }
+    vG[lane] = g;
+    vT[lane] = td;
+    __syncwarp();
     // joint rates: input i in 12..29 (row i + 8); multiplier y = -g.  With
     // the joint box of stage k active (row i + 26, on x_{k+1}), the rate is
     // eliminated: its stationarity 2dt R u + dt (m + y_q) = 0 gives the
     // joint-box multiplier y_q, and the costate takes it (m <- m + y_q).
     if (lane >= 12 && lane < 30) {
       const int a = act[lane + 8], aq = act[lane + 26];
-      float bad = 0.f;
+      float bad = 0.f, tol = td;
       if (aq) {
-        const float yq = -2.f * md[M_R + lane] * us[k * VS + lane] - m;
+        const float tu = -2.f * md[M_R + lane] * us[k * VS + lane];
+        const float yq = tu - m;
+        tol = ea + er * fmaxf(fabsf(tu), fabsf(m));
         if (aq & 1) bad = fmaxf(yq, 0.f);          // lower bound: y_q <= 0
         else bad = fmaxf(-yq, 0.f);                // upper bound: y_q >= 0
         m += yq;
-        if (fix && bad > tol_d) { ak[lane + 26] = 0; chg = 1; }
+        if (FIX && bad > fminf(tol_d, kScaledAccept * tol)) { ak[lane + 26] = 0; chg = 1; }
       } else if (a & 1) {
         bad = fmaxf(-g, 0.f);                      // needs y <= 0 at a lower bound
       } else if (a & 2) {
         bad = fmaxf(g, 0.f);                       // needs y >= 0 at an upper bound
       } else {
-        rd = fmaxf(rd, fabsf(g));
+        bad = fabsf(g);
       }
       rd = fmaxf(rd, bad);
-      if (fix && !aq && bad > tol_d) { ak[lane + 8] = 0; chg = 1; }
+      dn = fmaxf(dn, bad / tol);
+      if (FIX && !aq && a && bad > fminf(tol_d, kScaledAccept * tol)) { ak[lane + 8] = 0; chg = 1; }
     }
     // feet: lane f in 0..1
     if (lane < 2) {
       const int f = lane, b = 6 * f, p = 12 + 4 * f;
       const FootAct fa = foot_act(act, f);
       const float gx = vG[b], gy = vG[b + 1], gz = vG[b + 2];
+      const float tf = fmaxf(fmaxf(vT[b], vT[b + 1]), vT[b + 2]);
+      const float thr = fminf(tol_d, kScaledAccept * tf);
       if (!fa.swing) {
-        for (int c = 3; c < 6; ++c) rd = fmaxf(rd, fabsf(vG[b + c]));   // free moments
+        for (int c = 3; c < 6; ++c) {                                  // free moments
+          rd = fmaxf(rd, fabsf(vG[b + c]));
+          dn = fmaxf(dn, fabsf(vG[b + c]) / vT[b + c]);
+        }
         if (fa.zero) {
           // -g in the normal cone of the pyramid at 0: g . ray >= 0 on its 4 rays
           float worst = 0.f;
           for (int sx = -1; sx <= 1; sx += 2)
             for (int sy = -1; sy <= 1; sy += 2) worst = fmaxf(worst, -(sx * mu * gx + sy * mu * gy + gz));
           rd = fmaxf(rd, worst);
-          if (fix && worst > tol_d) {
+          dn = fmaxf(dn, worst / tf);
+          if (FIX && worst > thr) {
             ak[b + 2] &= ~1;
             if ((act[p] & 2) && (act[p + 1] & 2)) { ak[p] = 0; ak[p + 1] = 0; }
             if ((act[p + 2] & 2) && (act[p + 3] & 2)) { ak[p + 2] = 0; ak[p + 3] = 0; }
@@ -1100,22 +1160,28 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
           const float ypy = fa.ty ? -fa.ty * gy : 0.f;
           if (fa.tx) {
             rd = fmaxf(rd, fmaxf(-ypx, 0.f));
-            if (fix && -ypx > tol_d) { ak[fa.tx > 0 ? p : p + 1] = 0; chg = 1; }
+            dn = fmaxf(dn, fmaxf(-ypx, 0.f) / tf);
+            if (FIX && -ypx > thr) { ak[fa.tx > 0 ? p : p + 1] = 0; chg = 1; }
           } else {
             rd = fmaxf(rd, fabsf(gx));
+            dn = fmaxf(dn, fabsf(gx) / vT[b]);
           }
           if (fa.ty) {
             rd = fmaxf(rd, fmaxf(-ypy, 0.f));
-            if (fix && -ypy > tol_d) { ak[fa.ty > 0 ? p + 2 : p + 3] = 0; chg = 1; }
+            dn = fmaxf(dn, fmaxf(-ypy, 0.f) / tf);
+            if (FIX && -ypy > thr) { ak[fa.ty > 0 ? p + 2 : p + 3] = 0; chg = 1; }
           } else {
             rd = fmaxf(rd, fabsf(gy));
+            dn = fmaxf(dn, fabsf(gy) / vT[b + 1]);
           }
           const float rz = gz - mu * (ypx + ypy);   // = -y_top when f_z sits at its upper bound
           if (fa.top) {
             rd = fmaxf(rd, fmaxf(rz, 0.f));
-            if (fix && rz > tol_d) { ak[b + 2] &= ~2; chg = 1; }
+            dn = fmaxf(dn, fmaxf(rz, 0.f) / tf);
+            if (FIX && rz > thr) { ak[b + 2] &= ~2; chg = 1; }
           } else {
             rd = fmaxf(rd, fabsf(rz));
+            dn = fmaxf(dn, fabsf(rz) / tf);
           }
         }
       }
@@ -1130,32 +1196,15 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
     __syncwarp();
     m = mn;
   }
-  // primal feasibility of every row (after the dual pass, so that the dual
-  // conditions are read on the active set the point was solved with)
-  for (int k = 0; k < N; ++k) {
-    vU[lane] = us[k * VS + lane];
-    vXN[lane] = xs[(k + 1) * VS + lane];
-    __syncwarp();
-    for (int r = lane; r < NR; r += 32) {
-      const float v = crow(vU, vXN, r, mu);
-      const float lo = ap.rlo[k * RS + r], hi = ap.rhi[k * RS + r];
-      const float viol = fmaxf(fmaxf(lo - v, v - hi), 0.f);
-      rp = fmaxf(rp, viol);
-      if (fix && viol > tol_p && ap.act[k * RS + r] == 0) {
-        ap.act[k * RS + r] = (v < lo) ? 1 : 2;
-        chg = 1;
-      }
-    }
-    __syncwarp();
-  }
   Res out;
-  out.rp = warp_max(rp); out.ps = ps; out.rd = warp_max(rd); out.ds = ds;
+  out.rp = warp_max(rp); out.ps = warp_max(ps); out.rd = warp_max(rd); out.ds = warp_max(ds);
+  out.pn = warp_max(pn); out.dn = warp_max(dn);
   if (changed) *changed = warp_or(chg);
   return out;
 }
 
-// Polish with active-set correction: up to four attempts; true when one
-// passes its check, with the polished point copied into (x, u).
+// Polish with active-set correction: up to four attempts (eight from the
+// previous replan's active set); true when one passes its check, with the polished point copied into (x, u).
 // Initial guess from the agent's previous final active set (kept per slot):
 // rows that became equalities (a foot switched to swing) are active, rows
 // that stopped being equalities start inactive, the rest keep their code.
@@ -1177,15 +1226,19 @@ __device__ void init_active_prev(const AgentPtrs& ap, int lane) {
 }
 
 __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Res* res,
-                       const LanePat& pat, bool from_prev = false) {
+                       const LanePat& pat, Pipe& pp, bool from_prev = false) {
   if (from_prev) init_active_prev(ap, lane);
   else init_active(ap, lane);
-  for (int attempt = 0; attempt < 4; ++attempt) {
-    if (!polish_solve(ap, sm, lane, pat)) return false;
-    int changed = 0;
-    const Res pr = polish_check(ap, sm, lane, prm, true, &changed, pat);
-    const bool ok = isfinite(pr.rp) && isfinite(pr.rd) && pr.rp <= prm.eps_abs + prm.eps_rel * pr.ps &&
-                    pr.rd <= prm.eps_abs + prm.eps_rel * pr.ds;
+  // from the previous replan's active set more corrections pay: the
+  // alternative is an ADMM solve
+  const int attempts = from_prev ? 8 : 4;
+  for (int attempt = 0; attempt < attempts; ++attempt) {
+    if (!polish_solve(ap, sm, lane, pat, pp)) return false;
+    const Res pr = polish_check<false>(ap, sm, lane, prm, nullptr, pat);
+    const float tol_p = prm.eps_abs + prm.eps_rel * pr.ps;
+    const float tol_d = prm.eps_abs + prm.eps_rel * pr.ds;
+    const bool ok = isfinite(pr.rp) && isfinite(pr.rd) && pr.rp <= tol_p && pr.rd <= tol_d &&
+                    pr.pn <= kScaledAccept && pr.dn <= kScaledAccept;
     if (ok) {
       for (int k = 1; k <= ap.N; ++k) ap.x[k * VS + lane] = ap.xt[k * VS + lane];
       for (int k = 0; k < ap.N; ++k) ap.u[k * VS + lane] = ap.ut[k * VS + lane];
@@ -1193,9 +1246,100 @@ __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, co
       *res = pr;
       return true;
     }
+    if (attempt + 1 == attempts) break;
+    int changed = 0;
+    polish_check<true>(ap, sm, lane, prm, &changed, pat, tol_p, tol_d);
     if (!changed) return false;
   }
   return false;
+}
+
+// ADMM warm start after a failed polish from the previous active set: the
+// last polished point (xt, ut) with the row values w = clip(C z) and the row
+// multipliers y of its active set (read from the same costate recursion and
+// stationarity conditions as the optimality check, projected onto the sign
+// each bound allows).  The (x, u, w, y) kept per agent are otherwise those of
+// the last replan that ran ADMM, however many replans ago that was.
+__device__ __noinline__ void polish_warm_start(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat) {
+  const int N = ap.N;
+  const float* md = ap.mdl;
+  const float dt = md[M_DT], mu = md[M_MU];
+  float* vec = sm + S_VEC;
+  float* vU = vec + V_U * 64; float* vXN = vec + V_XN * 64; float* vM = vec + V_S * 64;
+  float* vG = vec + V_G * 64;
+  int* act = reinterpret_cast<int*>(vec + V_ACT * 64);
+  const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
+  const float twoR = lane < 30 ? 2.f * dt * md[M_R + lane] : 0.f;
+  const float* xs = ap.xt;
+  const float* us = ap.ut;
+  float m = lane < 30 ? twoQ * (xs[N * VS + lane] - ap.xref[N * VS + lane]) : 0.f;
+  for (int k = N - 1; k >= 0; --k) {
+    stage_active(ap, k, act, lane);
+    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
+    vM[lane] = m;
+    vU[lane] = us[k * VS + lane];
+    vXN[lane] = xs[(k + 1) * VS + lane];
+    __syncwarp();
+    float g = 0.f;
+    if (lane < 30)
+      g = twoR * (us[k * VS + lane] - ap.uref[k * VS + lane]) +
+          (lane < NC ? cc_tv(sm + S_BV, pat.br, vM, lane) : dt * m);
+    vG[lane] = g;
+    __syncwarp();
+    float* yk = ap.y + k * RS;
+    float* wk = ap.w + k * RS;
+    // joint rate rows (20..37) and joint-box rows (38..55)
+    if (lane >= 12 && lane < 30) {
+      const int a = act[lane + 8], aq = act[lane + 26];
+      float yr = 0.f, yq = 0.f;
+      if (aq) {
+        const float v = -2.f * md[M_R + lane] * us[k * VS + lane] - m;
+        m += v;
+        yq = (aq & 1) ? fminf(v, 0.f) : fmaxf(v, 0.f);
+      } else if (a & 1) {
+        yr = fminf(-g, 0.f);
+      } else if (a & 2) {
+        yr = fmaxf(-g, 0.f);
+      }
+      yk[lane + 8] = yr;
+      yk[lane + 26] = yq;
+    }
+    // wrench rows (0..11) and friction-pyramid rows (12..19) of foot f
+    if (lane < 2) {
+      const int f = lane, b = 6 * f, p = 12 + 4 * f;
+      const FootAct fa = foot_act(act, f);
+      const float gx = vG[b], gy = vG[b + 1], gz = vG[b + 2];
+      float yw[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, yp[4] = {0.f, 0.f, 0.f, 0.f};
+      if (fa.swing) {
+        for (int c = 0; c < 6; ++c) yw[c] = -vG[b + c];    // equality rows
+      } else if (fa.zero) {
+        yp[0] = fmaxf(-gx, 0.f); yp[1] = fmaxf(gx, 0.f);
+        yp[2] = fmaxf(-gy, 0.f); yp[3] = fmaxf(gy, 0.f);
+        yw[2] = fminf(-gz + mu * (yp[0] + yp[1] + yp[2] + yp[3]), 0.f);
+      } else {
+        if (fa.tx) yp[fa.tx > 0 ? 0 : 1] = fmaxf(-fa.tx * gx, 0.f);
+        if (fa.ty) yp[fa.ty > 0 ? 2 : 3] = fmaxf(-fa.ty * gy, 0.f);
+        const float rz = gz - mu * (yp[0] + yp[1] + yp[2] + yp[3]);
+        if (fa.top) yw[2] = fmaxf(-rz, 0.f);
+      }
+      for (int c = 0; c < 6; ++c) yk[b + c] = yw[c];
+      for (int t = 0; t < 4; ++t) yk[p + t] = yp[t];
+    }
+    for (int r = lane; r < NR; r += 32)
+      wk[r] = fminf(fmaxf(crow(vU, vXN, r, mu), ap.rlo[k * RS + r]), ap.rhi[k * RS + r]);
+    __syncwarp();
+    vM[lane] = m;
+    __syncwarp();
+    float mn = 0.f;
+    if (k >= 1 && lane < 30)
+      mn = twoQ * (xs[k * VS + lane] - ap.xref[k * VS + lane]) +
+           (lane < NC ? cc_tv(sm + S_AV, pat.ar, vM, lane) : m);
+    __syncwarp();
+    m = mn;
+  }
+  for (int k = 1; k <= N; ++k) ap.x[k * VS + lane] = xs[k * VS + lane];
+  for (int k = 0; k < N; ++k) ap.u[k * VS + lane] = us[k * VS + lane];
+  __syncwarp();
 }
 
 // ============================================================ ADMM driver (A5, A6)
@@ -1209,21 +1353,22 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
   float rho = *ap.rho;
   Outcome o;
   o.status = MPC_AGENT_MAX_ITER_; o.iters = 0; o.refac = 0; o.polished = 0;
-  o.r.rp = o.r.rd = o.r.ps = o.r.ds = 0.f;
+  o.r.rp = o.r.rd = o.r.ps = o.r.ds = o.r.pn = o.r.dn = 0.f;
   // warm start: the previous replan's final active set is usually still
   // right; a polish from it that passes the KKT check is the optimum, with no
   // ADMM factorisation and no iteration
   if (lane == 0) ap.st[T_FIRST] = 0;
   if (prm.polish && prm.warm_polish && ap.st[T_WARM] && prm.fixed_iters == 0) {
     Res pr;
-    if (polish(ap, sm, lane, prm, &pr, pat, true)) {
+    if (polish(ap, sm, lane, prm, &pr, pat, pp, true)) {
       o.polished = 1;
       o.status = MPC_AGENT_SOLVED_;
-      o.r.rp = pr.rp; o.r.rd = pr.rd;
+      o.r = pr;
       if (lane == 0) ap.st[T_FIRST] = 1;
       return o;
     }
     factored = false;   // the polish overwrote the caches
+    polish_warm_start(ap, sm, lane, pat);
   }
   if (!factored) factor_admm(ap, sm, lane, rho, prm.sigma, pat);
   const bool fixed = prm.fixed_iters > 0;
@@ -1231,7 +1376,10 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
   // polish attempts: the first once both residuals are within early_polish x
   // the tolerance, then again every 100 iterations while they stay there (the
   // active-set guess improves as ADMM proceeds; in FP32 ADMM can plateau just
-  // above the tolerance), at most 8 attempts
+  // above the tolerance).  The spacing doubles every second attempt, so the
+  // attempts cost a bounded share of the iterations; it starts at 20
+  // iterations for a warm-started agent (close to its optimum), 100 cold.
+  const int polish_every = ap.st[T_WARM] ? 20 : 100;
   int polish_tries = 0, next_polish_it = 0;
   int it = 0;
   for (it = 1; it <= max_it; ++it) {
@@ -1239,21 +1387,26 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
     if (warp_or(pp.timeout)) { o.status = MPC_AGENT_TIMEOUT_; break; }
     const bool check = (!fixed && (it % prm.check_every == 0)) || it == max_it;
     if (!check) continue;
-    o.r = admm_residuals(ap, sm, lane, pat);
+    o.r = admm_residuals(ap, sm, lane, prm, pat);
     if (!(isfinite(o.r.rp) && isfinite(o.r.rd))) { o.status = MPC_AGENT_NAN_; break; }
     if (fixed) break;
+    // OSQP's stopping rule (global scales), and every row and component
+    // within kScaledAccept times its own tolerance, as a polish must be
     const float tol_p = prm.eps_abs + prm.eps_rel * o.r.ps;
     const float tol_d = prm.eps_abs + prm.eps_rel * o.r.ds;
-    if (o.r.rp <= tol_p && o.r.rd <= tol_d) { o.status = MPC_AGENT_SOLVED_; break; }
-    if (prm.polish && prm.early_polish > 0.f && polish_tries < 8 && it >= next_polish_it &&
+    if (o.r.rp <= tol_p && o.r.rd <= tol_d && o.r.pn <= kScaledAccept && o.r.dn <= kScaledAccept) {
+      o.status = MPC_AGENT_SOLVED_;
+      break;
+    }
+    if (prm.polish && prm.early_polish > 0.f && polish_tries < 24 && it >= next_polish_it &&
         o.r.rp <= prm.early_polish * tol_p && o.r.rd <= prm.early_polish * tol_d) {
       ++polish_tries;
-      next_polish_it = it + 100;
+      next_polish_it = it + (polish_every << (polish_tries >> 1));
       Res pr;
-      if (polish(ap, sm, lane, prm, &pr, pat)) {
+      if (polish(ap, sm, lane, prm, &pr, pat, pp)) {
         o.polished = 1;
         o.status = MPC_AGENT_SOLVED_;
-        o.r.rp = pr.rp; o.r.rd = pr.rd;
+        o.r = pr;
         break;
       }
       factor_admm(ap, sm, lane, rho, prm.sigma, pat);   // the polish overwrote the caches
@@ -1344,6 +1497,8 @@ __device__ void write_outcome(const AgentPtrs& ap, int lane, const Outcome& o) {
     ap.st[T_POLISHED] = o.polished;
     ap.out[O_PRIM] = o.r.rp;
     ap.out[O_DUAL] = o.r.rd;
+    ap.out[O_PRIM_N] = o.r.pn;
+    ap.out[O_DUAL_N] = o.r.dn;
     *ap.warm = (o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) ? 0 : ap.N;
   }
   __syncwarp();
@@ -1351,13 +1506,13 @@ __device__ void write_outcome(const AgentPtrs& ap, int lane, const Outcome& o) {
 
 // final polish when ADMM ended without an accepted one
 __device__ void final_polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Outcome& o,
-                             const LanePat& pat) {
+                             const LanePat& pat, Pipe& pp) {
   if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) return;
   Res pr;
-  if (polish(ap, sm, lane, prm, &pr, pat)) {
+  if (polish(ap, sm, lane, prm, &pr, pat, pp)) {
     o.polished = 1;
     o.status = MPC_AGENT_SOLVED_;
-    o.r.rp = pr.rp; o.r.rd = pr.rd;
+    o.r = pr;
   }
 }
 
@@ -1399,7 +1554,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_fused(Arena 
     load_inputs(b, row, ap, lane);
     if (!setup_agent(ap, sm, lane, prm)) { mark_status_only(ap, lane, MPC_AGENT_NAN_); continue; }
     Outcome o = admm_solve(ap, sm, lane, prm, false, pp, pat);
-    final_polish(ap, sm, lane, prm, o, pat);
+    final_polish(ap, sm, lane, prm, o, pat, pp);
     write_outcome(ap, lane, o);
     torque_map(ap, lane);
     __syncwarp();
@@ -1460,12 +1615,15 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_polish(Arena
   o.polished = ap.st[T_POLISHED];
   o.r.rp = ap.out[O_PRIM];
   o.r.rd = ap.out[O_DUAL];
+  o.r.pn = ap.out[O_PRIM_N];
+  o.r.dn = ap.out[O_DUAL_N];
   o.r.ps = o.r.ds = 0.f;
   if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) return;
   load_lin(ap, sm, lane);
   copy_n(sm + S_BV, ap.lin + L_BV, 136 / 4, lane);
-  __syncwarp();
-  final_polish(ap, sm, lane, prm, o, lane_pattern(lane));
+  Pipe pp;
+  pipe_init(pp, sm, lane);
+  final_polish(ap, sm, lane, prm, o, lane_pattern(lane), pp);
   if (o.polished) write_outcome(ap, lane, o);
 }
 

@@ -73,7 +73,7 @@ SIGNATURES = {
     "mpc_autotune": (C.c_int, [_P, C.c_uint64, C.c_int32, C.c_char_p, C.c_size_t]),
     "mpc_get_torques": (C.c_int, [_P, C.c_uint64, _P, _P, _P, _P, _P]),
     "mpc_solve_host": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
-    "mpc_get_agent_stats": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P]),
+    "mpc_get_agent_stats": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "mpc_export_state": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P]),
     "mpc_import_state": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_float]),
     "mpc_solve_static": (C.c_int, [C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -247,9 +247,12 @@ class Solver:
         po = np.empty(n, np.int32)
         rp = np.empty(n, np.float32)
         rd = np.empty(n, np.float32)
+        pn = np.empty(n, np.float32)
+        dn = np.empty(n, np.float32)
         self._check(self.lib.mpc_get_agent_stats(self.ctx, n, _ptr(ids), _ptr(it), _ptr(rf), _ptr(po),
-                                                 _ptr(rp), _ptr(rd)))
-        return dict(iters=it, refactors=rf, polished=po, prim_res=rp, dual_res=rd)
+                                                 _ptr(rp), _ptr(rd), _ptr(pn), _ptr(dn)))
+        return dict(iters=it, refactors=rf, polished=po, prim_res=rp, dual_res=rd, prim_scaled=pn,
+                    dual_scaled=dn)
 
     def export_state(self, agent_id: int, N: int):
         x = np.empty((N + 1, 30), np.float32)
