@@ -74,6 +74,7 @@ struct Arena {
   float* lin;             // [A][LIN_F]  A_base, B, per-stage dA (3x10) and c
   float* cK;              // [A][maxN*BLK] Riccati gains K_k (R24)
   float* cH;              // [A][maxN*BLK] inverse Schur blocks H_uu^-1 (R24)
+  float* cEl;             // [A][maxN*128] polish: per-stage elimination of each input (float4 per lane)
   float* cE;              // [A][maxN*64] e_k = P_{k+1} c_k (lanes 0-21), arm gain (22-29),
                           //   arm e (32-39), arm H_uu^-1 (54-61)
   float* xt;              // [A][(maxN+1)*VS] KKT-solve primal (x tilde)

@@ -116,7 +116,7 @@ static size_t arena_bytes(size_t A, size_t n) {
   f += A * IN_F;
   f += A * ((n + 1) * VS + n * VS + 3 * n * RS);     // xref uref rlo rhi rcls
   f += A * lin_floats((int)n);
-  f += A * (2 * n * BLK + n * 64);                   // cK cH cE
+  f += A * (2 * n * BLK + n * 64 + n * 128);         // cK cH cE cEl
   f += A * ((n + 1) * VS + 2 * n * VS + n * RS + 1); // xt ut dv act order
   f += A * (1 + 30 + 18 + 4 + 1 + 18 * 3 + 2);       // host-path staging
   f += A * (MODEL_F + 2 * SCHED_D + 1);              // model upload staging
@@ -207,6 +207,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   AL(a.cK, A * n * BLK);
   AL(a.cH, A * n * BLK);
   AL(a.cE, A * n * 64);
+  AL(a.cEl, A * n * 128);
   AL(a.xt, A * (n + 1) * VS);
   AL(a.ut, A * n * VS);
   AL(a.dv, A * n * VS);

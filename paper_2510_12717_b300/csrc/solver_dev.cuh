@@ -57,7 +57,7 @@ struct AgentPtrs {
   int N;
   float *x, *u, *w, *y, *rho;
   int* warm;
-  float *inp, *xref, *uref, *rlo, *rhi, *rcls, *lin, *cK, *cH, *cE, *xt, *ut, *dv;
+  float *inp, *xref, *uref, *rlo, *rhi, *rcls, *lin, *cK, *cH, *cE, *cEl, *xt, *ut, *dv;
   int* act;
   float* out;
   int* st;
@@ -85,6 +85,7 @@ __device__ __forceinline__ AgentPtrs agent_ptrs(const Arena& a, int s) {
   p.cK = a.cK + (size_t)s * n * BLK;
   p.cH = a.cH + (size_t)s * n * BLK;
   p.cE = a.cE + (size_t)s * n * 64;
+  p.cEl = a.cEl + (size_t)s * n * 128;
   p.xt = a.xt + (size_t)s * (n + 1) * VS;
   p.ut = a.ut + (size_t)s * n * VS;
   p.dv = a.dv + (size_t)s * n * VS;

@@ -789,13 +789,20 @@ __device__ __forceinline__ FootAct foot_act(const int* act, int f) {
 // inputs: u_i = g v_i + t + phi x_i with g in {0, 1}.  A joint rate whose
 // joint-box row (on x_{k+1}) is active is fixed by q_{k+1} = q_k + dt qdot_k
 // = b:  qdot_k = (b - q_k)/dt, i.e. t = b/dt, phi = -1/dt (qbox = 1).
-// conflict = 1 when the rate box and the joint box of the same joint are
-// both active at one stage (not handled: the polish is abandoned).
-struct Elim { float g, t, phi, gf[3]; int qbox, conflict; };
+// When the rate row is active as well (a degenerate optimum: the joint rides
+// its rate bound onto its limit), the rate keeps its bound t_r and the pair
+// fixes q_k = b - dt t_r instead: a constraint on x_k carried to stage k-1,
+// where it eliminates that stage's joint rate in the same way (or, if that
+// rate is at its bound too, is carried further).  carry_in: the constraint
+// on q_{k+1} carried from stage k+1; carry_out: the one passed to stage k-1.
+struct Carry { int on; float b; };
+struct Elim { float g, t, phi, gf[3]; int qbox; Carry carry_out; };
 
-__device__ __forceinline__ Elim lane_elim(const AgentPtrs& ap, int k, const int* act, int i, float mu) {
+__device__ __forceinline__ Elim lane_elim(const AgentPtrs& ap, int k, const int* act, int i, float mu,
+                                          Carry carry_in) {
   Elim e;
-  e.g = 1.f; e.t = 0.f; e.phi = 0.f; e.gf[0] = e.gf[1] = e.gf[2] = 0.f; e.qbox = 0; e.conflict = 0;
+  e.g = 1.f; e.t = 0.f; e.phi = 0.f; e.gf[0] = e.gf[1] = e.gf[2] = 0.f; e.qbox = 0;
+  e.carry_out.on = 0; e.carry_out.b = 0.f;
   if (i < 12) {
     const int f = i / 6, c = i - 6 * f, b = 6 * f;
     const FootAct fa = foot_act(act, f);
@@ -823,14 +830,17 @@ __device__ __forceinline__ Elim lane_elim(const AgentPtrs& ap, int k, const int*
   if (i < 30) {
     const int r = i + 8, rq = i + 26;
     const int a = act[r], aq = act[rq];
-    if (a & 1) { e.g = 0.f; e.t = ap.rlo[k * RS + r]; }
-    else if (a & 2) { e.g = 0.f; e.t = ap.rhi[k * RS + r]; }
-    if (aq) {
-      if (a) { e.conflict = 1; return e; }
-      const float dt = ap.mdl[M_DT];
-      const float bnd = (aq & 1) ? ap.rlo[k * RS + rq] : ap.rhi[k * RS + rq];
+    int eq = carry_in.on;
+    float eb = carry_in.b;
+    if (!eq && aq) { eq = 1; eb = (aq & 1) ? ap.rlo[k * RS + rq] : ap.rhi[k * RS + rq]; }
+    const float dt = ap.mdl[M_DT];
+    if (a) {
       e.g = 0.f;
-      e.t = bnd / dt;
+      e.t = (a & 1) ? ap.rlo[k * RS + r] : ap.rhi[k * RS + r];
+      if (eq) { e.carry_out.on = 1; e.carry_out.b = eb - dt * e.t; }
+    } else if (eq) {
+      e.g = 0.f;
+      e.t = eb / dt;
       e.phi = -1.f / dt;
       e.qbox = 1;
     }
@@ -933,20 +943,6 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
   const bool arm = lane >= NC && lane < 30;
   const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
 
-  // a joint whose rate row and joint-box row are both marked active at one
-  // stage (the guess usually marks a joint-box row that the optimum only
-  // nearly touches): keep the row with the larger multiplier estimate; the
-  // check and its corrections settle the rest
-  for (int k = 0; k < N; ++k)
-    for (int jj = lane; jj < 18; jj += 32) {
-      int* a = ap.act + k * RS;
-      if (a[20 + jj] != 0 && a[38 + jj] != 0) {
-        if (fabsf(ap.y[k * RS + 38 + jj]) >= fabsf(ap.y[k * RS + 20 + jj])) a[20 + jj] = 0;
-        else a[38 + jj] = 0;
-      }
-    }
-  __syncwarp();
-
   // ---- backward: Riccati factor of the reduced problem (cost 2dt Q, 2dt R;
   // no sigma, no rho) and its linear recursion
   if (lane < NC) {
@@ -955,11 +951,20 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
   }
   float Pa = arm ? twoQ : 0.f;
   float p = lane < 30 ? -twoQ * ap.xref[N * VS + lane] : 0.f;
+  Carry carry = {0, 0.f};
   __syncwarp();
   for (int k = N - 1; k >= 0; --k) {
     stage_active(ap, k, act, lane);
     set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
-    const Elim el = lane_elim(ap, k, act, lane, mu);
+    const Elim el = lane_elim(ap, k, act, lane, mu, carry);
+    carry = el.carry_out;
+    // the stage's elimination, for the forward pass: (g | G_f row 0, G_f row
+    // 1, G_f row 2 | phi, t)
+    {
+      const bool fl = lane < 12 && (lane % 6) < 3;
+      reinterpret_cast<float4*>(ap.cEl + k * 128)[lane] =
+          make_float4(fl ? el.gf[0] : el.g, el.gf[1], fl ? el.gf[2] : el.phi, el.t);
+    }
     const StageIn in = polish_stage_in(ap, sm, k, act, cvec, el, lane);
     const StageOut so = factor_stage(ap, sm, lane, k, in, &Pa, pat, false);
     // H (= H_uu^-1) and K of stage k are still in smem
@@ -999,8 +1004,7 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
     if (k + 1 < N) pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k + 1) * BLK, nullptr, nullptr, lane);
     const float* ce = ap.cE + k * 64;
     const float* dA = ap.lin + L_STAGE + k * 64;
-    stage_active(ap, k, act, lane);
-    const Elim el = lane_elim(ap, k, act, lane, mu);
+    const float4 el = reinterpret_cast<const float4*>(ap.cEl + k * 128)[lane];
     vX[lane] = x;
     const float dk = ap.dv[k * VS + lane];
     pipe_wait(pp, b);
@@ -1013,9 +1017,9 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
     float u = 0.f;
     if (lane < 12 && (lane % 6) < 3) {
       const int bb = (lane / 6) * 6;
-      u = el.gf[0] * vV[bb] + el.gf[1] * vV[bb + 1] + el.gf[2] * vV[bb + 2] + el.t;
+      u = el.x * vV[bb] + el.y * vV[bb + 1] + el.z * vV[bb + 2] + el.w;
     } else if (lane < 30) {
-      u = el.g * v + el.t + el.phi * x;
+      u = el.x * v + el.w + el.z * x;
     }
     vU[lane] = u;
     __syncwarp();
@@ -1037,9 +1041,11 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
 // against its own tolerance (see Res).  With FIX (after a failed check) the
 // active set is corrected for a next attempt: active rows whose multiplier
 // has the wrong sign by more than tol_d are dropped, rows the point violates
-// by more than tol_p are added (the two touch disjoint rows; the stage's
-// conditions are read from the copy in act taken before either), and
-// *changed reports whether anything changed.  The thresholds are the tighter
+// by more than tol_p are added; a chain of rate-bound stages under a joint
+// limit that reaches the given q_0 over-determines q and loses its last rate
+// row if the limit is overshot, else the limit row.  Dual and primal
+// corrections touch disjoint rows; the stage's conditions are read from the
+// copy in act taken before either.  *changed reports whether anything changed.  The thresholds are the tighter
 // of the failed check's global tolerances (tol_p, tol_d) and kScaledAccept
 // times the row's or component's own tolerance.
 template <bool FIX>
@@ -1061,6 +1067,14 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
   float rp = 0.f, ps = 0.f, rd = 0.f, ds = 0.f, pn = 0.f, dn = 0.f;
   int chg = 0;
   float m = lane < 30 ? twoQ * (xs[N * VS + lane] - ap.xref[N * VS + lane]) : 0.f;
+  // a chain of stages kc..ke whose joint rate sits at its bound while the
+  // joint limit of stage ke is active (see Elim): the limit's multiplier is
+  // nu, the multiplier nu' of the constraint carried to stage kc-1, and each
+  // rate row's is its own stationarity value minus dt nu; ch_up / ch_lo hold
+  // the least / greatest of those values over the chain's rate rows at an
+  // upper / lower bound, ch_tol the largest tolerance among them
+  int ch_on = 0, ch_ke = 0, ch_side = 0, ch_over = 0;
+  float ch_up = 0.f, ch_lo = 0.f, ch_tol = 0.f;
   for (int k = N - 1; k >= 0; --k) {
     stage_active(ap, k, act, lane);
     set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
@@ -1084,11 +1098,6 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
       if (FIX && viol > fminf(tol_p, kScaledAccept * tp) && act[r] == 0) {
         ak[r] = (v < lo) ? 1 : 2;
         chg = 1;
-        // a joint's rate row and joint-box row are not kept active together
-        // (the polish would drop one again): the row that enters displaces
-        // the other one of the same joint and stage
-        if (r >= 38 && act[r - 18] != 0) ak[r - 18] = 0;
-        else if (r >= 20 && r < 38 && act[r + 18] != 0) ak[r + 18] = 0;
       }
     }
     // stationarity of the inputs without their row multipliers, and its tolerance
@@ -1110,25 +1119,56 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
     // joint-box multiplier y_q, and the costate takes it (m <- m + y_q).
     if (lane >= 12 && lane < 30) {
       const int a = act[lane + 8], aq = act[lane + 26];
-      float bad = 0.f, tol = td;
-      if (aq) {
+      // chain end: the joint limit's multiplier nu and the chain's rate rows
+      auto close_chain = [&](float nu, float tol_nu) {
+        const float bq = (ch_side & 1) ? fmaxf(nu, 0.f) : fmaxf(-nu, 0.f);
+        const float br = fmaxf(fmaxf(dt * nu - ch_up, 0.f), fmaxf(ch_lo - dt * nu, 0.f));
+        rd = fmaxf(rd, fmaxf(bq, br));
+        dn = fmaxf(dn, fmaxf(bq / tol_nu, br / ch_tol));
+        if (FIX && bq > fminf(tol_d, kScaledAccept * tol_nu)) { ap.act[ch_ke * RS + lane + 26] = 0; chg = 1; }
+        if (FIX && br > fminf(tol_d, kScaledAccept * ch_tol)) { ap.act[ch_ke * RS + lane + 8] = 0; chg = 1; }
+        ch_on = 0;
+      };
+      if (a && (ch_on || aq)) {
+        // rate at its bound under a joint limit (own, or carried): the chain
+        // goes on to stage k-1; the rate's own stationarity value is -g
+        if (!ch_on) {
+          ch_on = 1; ch_ke = k; ch_side = aq; ch_up = 3.0e38f; ch_lo = -3.0e38f; ch_tol = 0.f;
+          const float qn = vXN[lane];                       // q_{k+1} of this joint
+          ch_over = (aq & 1) ? (qn < ap.rlo[k * RS + lane + 26]) : (qn > ap.rhi[k * RS + lane + 26]);
+        }
+        if (a & 2) ch_up = fminf(ch_up, -g);
+        else ch_lo = fmaxf(ch_lo, -g);
+        ch_tol = fmaxf(ch_tol, td);
+        if (k == 0) {
+          // q_0 is given: nothing carries the limit further, the chain
+          // over-determines q_{ke+1}
+          if (FIX) { ap.act[ch_ke * RS + lane + (ch_over ? 8 : 26)] = 0; chg = 1; }
+          close_chain(0.f, td);
+        }
+      } else if (ch_on || aq) {
+        // joint rate eliminated by the joint limit (own, or carried to here)
         const float tu = -2.f * md[M_R + lane] * us[k * VS + lane];
         const float yq = tu - m;
-        tol = ea + er * fmaxf(fabsf(tu), fabsf(m));
-        if (aq & 1) bad = fmaxf(yq, 0.f);          // lower bound: y_q <= 0
-        else bad = fmaxf(-yq, 0.f);                // upper bound: y_q >= 0
+        const float tol = ea + er * fmaxf(fabsf(tu), fabsf(m));
+        if (ch_on) {
+          close_chain(yq, tol);
+        } else {
+          const float bad = (aq & 1) ? fmaxf(yq, 0.f) : fmaxf(-yq, 0.f);   // lower: y_q <= 0; upper: >= 0
+          rd = fmaxf(rd, bad);
+          dn = fmaxf(dn, bad / tol);
+          if (FIX && bad > fminf(tol_d, kScaledAccept * tol)) { ak[lane + 26] = 0; chg = 1; }
+        }
         m += yq;
-        if (FIX && bad > fminf(tol_d, kScaledAccept * tol)) { ak[lane + 26] = 0; chg = 1; }
-      } else if (a & 1) {
-        bad = fmaxf(-g, 0.f);                      // needs y <= 0 at a lower bound
-      } else if (a & 2) {
-        bad = fmaxf(g, 0.f);                       // needs y >= 0 at an upper bound
       } else {
-        bad = fabsf(g);
+        float bad;
+        if (a & 1) bad = fmaxf(-g, 0.f);           // needs y <= 0 at a lower bound
+        else if (a & 2) bad = fmaxf(g, 0.f);       // needs y >= 0 at an upper bound
+        else bad = fabsf(g);
+        rd = fmaxf(rd, bad);
+        dn = fmaxf(dn, bad / td);
+        if (FIX && a && bad > fminf(tol_d, kScaledAccept * td)) { ak[lane + 8] = 0; chg = 1; }
       }
-      rd = fmaxf(rd, bad);
-      dn = fmaxf(dn, bad / tol);
-      if (FIX && !aq && a && bad > fminf(tol_d, kScaledAccept * tol)) { ak[lane + 8] = 0; chg = 1; }
     }
     // feet: lane f in 0..1
     if (lane < 2) {
@@ -1273,6 +1313,7 @@ __device__ __noinline__ void polish_warm_start(const AgentPtrs& ap, float* sm, i
   const float* xs = ap.xt;
   const float* us = ap.ut;
   float m = lane < 30 ? twoQ * (xs[N * VS + lane] - ap.xref[N * VS + lane]) : 0.f;
+  int ch_on = 0, ch_ke = 0, ch_side = 0;   // open chain of rate-bound stages under a joint limit
   for (int k = N - 1; k >= 0; --k) {
     stage_active(ap, k, act, lane);
     set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
@@ -1288,21 +1329,39 @@ __device__ __noinline__ void polish_warm_start(const AgentPtrs& ap, float* sm, i
     __syncwarp();
     float* yk = ap.y + k * RS;
     float* wk = ap.w + k * RS;
-    // joint rate rows (20..37) and joint-box rows (38..55)
+    // joint rate rows (20..37) and joint-box rows (38..55); a chain's
+    // multipliers as in the optimality check: the limit takes nu, each rate
+    // row its own value minus dt nu
     if (lane >= 12 && lane < 30) {
       const int a = act[lane + 8], aq = act[lane + 26];
-      float yr = 0.f, yq = 0.f;
-      if (aq) {
+      auto close_chain = [&](float nu, int k0) {
+        for (int i = k0; i <= ch_ke; ++i) {
+          const int ai = ap.act[i * RS + lane + 8];
+          const float v = ap.y[i * RS + lane + 8] - dt * nu;
+          ap.y[i * RS + lane + 8] = (ai & 1) ? fminf(v, 0.f) : fmaxf(v, 0.f);
+        }
+        ap.y[ch_ke * RS + lane + 26] = (ch_side & 1) ? fminf(nu, 0.f) : fmaxf(nu, 0.f);
+        ch_on = 0;
+      };
+      if (a && (ch_on || aq)) {
+        if (!ch_on) { ch_on = 1; ch_ke = k; ch_side = aq; }
+        yk[lane + 8] = -g;
+        yk[lane + 26] = 0.f;
+        if (k == 0) close_chain(0.f, 0);
+      } else if (ch_on || aq) {
         const float v = -2.f * md[M_R + lane] * us[k * VS + lane] - m;
         m += v;
-        yq = (aq & 1) ? fminf(v, 0.f) : fmaxf(v, 0.f);
-      } else if (a & 1) {
-        yr = fminf(-g, 0.f);
-      } else if (a & 2) {
-        yr = fmaxf(-g, 0.f);
+        yk[lane + 8] = 0.f;
+        if (ch_on) {
+          yk[lane + 26] = 0.f;
+          close_chain(v, k + 1);
+        } else {
+          yk[lane + 26] = (aq & 1) ? fminf(v, 0.f) : fmaxf(v, 0.f);
+        }
+      } else {
+        yk[lane + 8] = (a & 1) ? fminf(-g, 0.f) : ((a & 2) ? fmaxf(-g, 0.f) : 0.f);
+        yk[lane + 26] = 0.f;
       }
-      yk[lane + 8] = yr;
-      yk[lane + 26] = yq;
     }
     // wrench rows (0..11) and friction-pyramid rows (12..19) of foot f
     if (lane < 2) {

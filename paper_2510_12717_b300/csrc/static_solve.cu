@@ -26,7 +26,7 @@ constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct Layout {
   size_t model, sched, horizon, ids, xs, us, ws, ys, rho, warm, out, stat, inp, xref, uref, rlo, rhi,
-      rcls, lin, cK, cH, cE, xt, ut, dv, act, order, counter, total;
+      rcls, lin, cK, cH, cE, cEl, xt, ut, dv, act, order, counter, total;
 };
 
 constexpr Layout make_layout(size_t A, size_t n) {
@@ -56,6 +56,7 @@ constexpr Layout make_layout(size_t A, size_t n) {
   L.cK = take(A * n * BLK * 4);
   L.cH = take(A * n * BLK * 4);
   L.cE = take(A * n * 64 * 4);
+  L.cEl = take(A * n * 128 * 4);
   L.xt = take(A * (n + 1) * VS * 4);
   L.ut = take(A * n * VS * 4);
   L.dv = take(A * n * VS * 4);
@@ -190,6 +191,7 @@ extern "C" mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_
   a.cK = at<float>(b, kL.cK);
   a.cH = at<float>(b, kL.cH);
   a.cE = at<float>(b, kL.cE);
+  a.cEl = at<float>(b, kL.cEl);
   a.xt = at<float>(b, kL.xt);
   a.ut = at<float>(b, kL.ut);
   a.dv = at<float>(b, kL.dv);
