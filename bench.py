@@ -41,10 +41,9 @@ WORKLOAD = "mixed16k"
 FP32_LANES = 128     # FP32 FMA lanes per SM (B300)
 N_SM = 148
 # DRAM bytes per agent of the fused kernel from the last ncu capture of this
-# kernel version (profiles/mpc_k_fused_mixed16k_2048agents.md: 70.67 MB read
-# + 136.34 MB written for a warm replan of 2048 agents); None once the kernel
-# has changed since.
-TRAFFIC_BYTES_PER_AGENT = (70.666496e6 + 136.340992e6) / 2048
+# kernel version (profiles/mpc_k_fused_mixed16k_2048agents.md); None once the
+# kernel has changed since.
+TRAFFIC_BYTES_PER_AGENT = (86.018048e6 + 155.169024e6) / 2048
 
 
 def parse():
