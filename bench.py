@@ -62,7 +62,8 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner in the warm-up")
     ap.add_argument("--no-graph", action="store_true", help="launch without CUDA-graph replay")
     ap.add_argument("--serve-seconds", type=float, default=0.5, help="serving run length (0 = skip)")
-    ap.add_argument("--serve-rate", type=float, default=0.5, help="request rate, x 16384 agents at 100 Hz")
+    ap.add_argument("--serve-rate", default="0.5,1,2",
+                    help="request rates, comma-separated, x 16384 agents at 100 Hz")
     return ap.parse_args()
 
 
@@ -167,27 +168,20 @@ def run_ours(args):
     # replan 0: autotune (cold); 1..W: warm-up; W+1..W+K: timed; then the
     # end-to-end run's 2 warm-up and K timed replans
     W, K = args.warmup, args.steps
-    n_rep = 1 + W + K + 2 + K
-    if args.serve_seconds > 0:
-        # the serving run walks each agent forward through the same sequence:
-        # enough replans that no agent wraps around to replan 0
-        from workload import workload_spec
-        n_agents = args.agents or workload_spec(args.workload)["n_agents"]
-        per_agent = args.serve_rate * 16384 * 100.0 * args.serve_seconds / n_agents
-        n_rep = max(n_rep, 2 + int(np.ceil(1.25 * per_agent)))
-    ids, model, replans = make_workload(args.workload, args.agents, rank, world, n_rep)
+    ids, model, replans = make_workload(args.workload, args.agents, rank, world, 1 + W + K + 2 + K)
     n = len(ids)
     stream = torch.cuda.Stream(dev)          # non-default stream: graph capture needs one
     torch.cuda.set_stream(stream)
     slots = np.arange(n, dtype=np.int32)
     Nh = model["N"].astype(np.int64)
 
-    def make_solver(form):
+    def make_solver(form, **opts):
         chosen = form == mpcgpu.FORM_FUSED
+        kw = dict(variant=args.variant, check_every=args.check_every, early_polish=args.early_polish,
+                  graph=int(chosen and not args.no_graph))
+        kw.update(opts)
         s = mpcgpu.Solver(max_agents=n, max_horizon=int(Nh.max()), form=form, device=local,
-                          stream=stream.cuda_stream, variant=args.variant,
-                          check_every=args.check_every, early_polish=args.early_polish,
-                          graph=int(chosen and not args.no_graph))
+                          stream=stream.cuda_stream, **kw)
         s.set_models(model, slots)
         return s
 
@@ -215,10 +209,10 @@ def run_ours(args):
 
     tune_report = None
 
-    def timed(form, K, W):
+    def timed(form, K, W, tune=True, **opts):
         nonlocal tune_report
-        s = make_solver(form)
-        if form == mpcgpu.FORM_FUSED and not args.no_autotune:
+        s = make_solver(form, **opts)
+        if form == mpcgpu.FORM_FUSED and tune and not args.no_autotune:
             # the autotuner runs on the first replan's batch (part of the warm-up)
             x = d_in[0]
             tk = s.submit(d_ids, x["x0"], x["qd_meas"], x["cmd"], x["phase"])
@@ -311,6 +305,19 @@ def run_ours(args):
             "iters_mean": float(sct["iters"].mean()), "iters_max": int(sct["iters"].max())}
     sc.close()
 
+    # the paper's own mode: a fixed number of ADMM iterations (N_QP = 25) per
+    # replan, no polish, warm-started; speed only (not an exact optimum)
+    paper_mode = None
+    if not args.no_plain:
+        K3 = min(args.steps, 5)
+        sp, tp, perp, lp, stp, _, _ = timed(mpcgpu.FORM_FUSED, K3, args.warmup, tune=False,
+                                            variant=cfg["variant"], fixed_iters=25, polish=0, warm_polish=0)
+        sp.close()
+        paper_mode = {"value": world * n * K3 / (tp / 1e3), "ms_per_step": tp / K3,
+                      "p50_ms": float(np.percentile(perp, 50)), "admm_iters": 25, "polish": False,
+                      "note": "fixed N_QP = 25 ADMM iterations per replan, warm-started, no polish (the paper's "
+                              "mode; speed only, not converged)"}
+
     plain = None
     if not args.no_plain:
         K2 = min(args.steps, 3)
@@ -342,6 +349,7 @@ def run_ours(args):
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "latency_budget_ms": 10.0, "per_step_ms": [round(v, 3) for v in per], "cold_solve": cold,
         "plain": plain,
+        "paper_mode_fixed25": paper_mode,
         "serving": serving,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
@@ -365,15 +373,20 @@ def run_ours(args):
 
 # ------------------------------------------------------------------ serving
 def run_serving(args, model, replans, n):
-    """Continuous batching under a Poisson request stream (16384-agent pool)."""
+    """Continuous batching under a Poisson request stream (16384-agent pool),
+    at each requested rate; each agent's state walks forward one 10 ms step
+    per request from the workload's first replan."""
     from paper_2510_12717_b300.serve import ServingEngine
-    rate = args.serve_rate * 16384 * 100.0
-    eng = ServingEngine(model, replans, pool=n, streams=2, hbm_budget_bytes=8 << 30)
-    st = eng.run(rate=rate, duration=args.serve_seconds, churn_every=100, churn_frac=0.05)
-    eng.close()
-    st["rate_x_16384_at_100hz"] = args.serve_rate
-    st["note"] = "requests of one agent coalesce (newest state wins); 2 streams; churn 5% every 100 batches"
-    return st
+    out = {}
+    for f in [float(v) for v in str(args.serve_rate).split(",") if v.strip()]:
+        eng = ServingEngine(model, replans[0], pool=n, streams=2, hbm_budget_bytes=8 << 30, seed=7)
+        st = eng.run(rate=f * 16384 * 100.0, duration=args.serve_seconds, churn_every=100, churn_frac=0.05)
+        eng.close()
+        st["rate_x_16384_at_100hz"] = f
+        out[f"{f:g}x"] = st
+    out["note"] = ("requests of one agent coalesce (newest state wins); 2 streams; churn 5% every 100 batches; "
+                   "rates x 1.6384 M requests/s")
+    return out
 
 
 # ------------------------------------------------------------------ CPU oracle

@@ -10,6 +10,11 @@ is copied from pinned memory, solved on that stream (mpc_solve_on) and read
 back, overlapping with the batch on the other stream.  Every `churn_every`
 batches a fraction of the live agents leaves and as many new agents join.
 
+Request states: each agent walks forward in time from its initial inputs;
+a request is one 10 ms environment step (gait phase += phase_step, state +=
+N(0, step_sigma)), so a batch answering s coalesced requests of an agent
+solves its state s steps on from its previous solve.
+
 Latency of a request = completion time of the batch that answered it minus
 its arrival time (time since the run started, on the host clock).
 """
@@ -23,17 +28,22 @@ from . import mpcgpu
 
 
 class ServingEngine:
-    def __init__(self, model: dict, replans: list, *, pool: int, streams: int = 2, max_batch: int = 0,
-                 hbm_budget_bytes: int = 8 << 30, device: int = 0, **solver_opts):
+    def __init__(self, model: dict, inputs, *, pool: int, streams: int = 2, max_batch: int = 0,
+                 hbm_budget_bytes: int = 8 << 30, device: int = 0, step_sigma: float = 0.02,
+                 phase_step: float = 0.02, seed: int = 0, **solver_opts):
         """model: SoA agent models (workload.make_agents layout) of every agent
-        that may ever join (live + reserve); replans: list of per-agent input
-        dicts (x0, qd_meas, cmd, phase) cycled through as request states.
+        that may ever join (live + reserve); inputs: their initial per-agent
+        input dict (x0, qd_meas, cmd, phase), or a list whose first entry is.
         pool: number of slots (live agents at a time)."""
         import torch
         self.torch = torch
         self.dev = torch.device("cuda", device)
         self.model = model
-        self.replans = replans
+        if isinstance(inputs, (list, tuple)):
+            inputs = inputs[0]
+        self.state = {k: np.array(v, dtype=np.float32, copy=True) for k, v in inputs.items()}
+        self.step_sigma, self.phase_step = step_sigma, phase_step
+        self.walk_rng = np.random.default_rng(seed)
         self.total = len(model["mass"])
         self.pool = pool
         self.max_batch = max_batch or pool
@@ -94,7 +104,6 @@ class ServingEngine:
         arrived = np.zeros(self.pool, dtype=np.int64)     # requests arrived so far, per slot
         served = np.zeros(self.pool, dtype=np.int64)      # requests answered, per slot
         in_flight = np.zeros(self.pool, dtype=bool)
-        replan_idx = np.zeros(self.pool, dtype=np.int64)
         lat = []
         batches = 0
         solves = 0
@@ -107,7 +116,8 @@ class ServingEngine:
         self.batch_log = []
         for _ in range(warmup_batches):
             for lo in range(0, self.pool, self.max_batch):
-                self._solve_sync(np.arange(lo, min(lo + self.max_batch, self.pool)), replan_idx)
+                sl = np.arange(lo, min(lo + self.max_batch, self.pool))
+                self._solve_sync(sl, np.ones(len(sl), dtype=np.int64))
         t0 = time.perf_counter()
         while True:
             now = time.perf_counter() - t0
@@ -139,11 +149,10 @@ class ServingEngine:
                 if len(ready) == 0:
                     continue
                 sl = ready[:self.max_batch]
-                busy[si] = self._launch(si, sl, replan_idx)
+                busy[si] = self._launch(si, sl, arrived[sl] - served[sl])
                 busy[si]["cover"] = arrived[sl].copy()
                 busy[si]["t_start"] = time.perf_counter() - t0
                 in_flight[sl] = True
-                replan_idx[sl] += 1
                 batches += 1
                 sizes.append(len(sl))
                 if churn_every and batches % churn_every == 0:
@@ -182,23 +191,31 @@ class ServingEngine:
         idx = np.repeat(first - np.cumsum(cnt) + cnt, cnt) + np.arange(cnt.sum())
         return t_done - times_by_slot[idx]
 
-    def _fill(self, si, sl, replan_idx):
+    def _advance(self, agents, steps):
+        """Walk the agents' states `steps` environment steps forward."""
+        st = self.state
+        s = np.asarray(steps, dtype=np.float32)
+        st["x0"][agents] += (self.step_sigma * np.sqrt(s))[:, None] * \
+            self.walk_rng.standard_normal((len(agents), st["x0"].shape[1]), dtype=np.float32)
+        st["qd_meas"][agents] = 0.1 * self.walk_rng.standard_normal((len(agents), st["qd_meas"].shape[1]),
+                                                                    dtype=np.float32)
+        st["cmd"][agents, 0] = st["x0"][agents, 2]
+        ph = st["phase"][agents] + self.phase_step * s
+        st["phase"][agents] = ph - np.floor(ph)
+
+    def _fill(self, si, sl, steps):
         h = self.h_in[si]
         n = len(sl)
         agents = self.slot_agent[sl]
-        ids_np = h["ids"].numpy()
-        ids_np[:n] = sl
+        self._advance(agents, steps)
+        h["ids"].numpy()[:n] = sl
         for key, dst in (("x0", "x0"), ("qd_meas", "qd"), ("cmd", "cmd"), ("phase", "ph")):
-            out = h[dst].numpy()
-            for r in range(len(self.replans)):
-                m = (replan_idx[sl] % len(self.replans)) == r
-                if m.any():
-                    out[:n][m] = self.replans[r][key][agents[m]]
+            h[dst].numpy()[:n] = self.state[key][agents]
         return n
 
-    def _launch(self, si, sl, replan_idx):
+    def _launch(self, si, sl, steps):
         torch = self.torch
-        n = self._fill(si, sl, replan_idx)
+        n = self._fill(si, sl, steps)
         st = self.streams[si]
         d, h, do, ho = self.d_in[si], self.h_in[si], self.d_out[si], self.h_out[si]
         with torch.cuda.stream(st):
@@ -213,8 +230,8 @@ class ServingEngine:
             ev.record(st)
         return dict(slots=sl, event=ev)
 
-    def _solve_sync(self, sl, replan_idx):
-        b = self._launch(0, sl, replan_idx)
+    def _solve_sync(self, sl, steps):
+        b = self._launch(0, sl, steps)
         b["event"].synchronize()
 
 
