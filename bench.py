@@ -61,6 +61,10 @@ def parse():
     ap.add_argument("--early-polish", type=float, default=100.0)
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner in the warm-up")
     ap.add_argument("--no-graph", action="store_true", help="launch without CUDA-graph replay")
+    ap.add_argument("--precision", type=int, default=0, help="factor precision: 0 FP32, 1 TF32, 2 BF16, 3 FP64")
+    ap.add_argument("--refine", type=int, default=-1, help="refinement steps per polish (-1: library default)")
+    ap.add_argument("--no-precision", action="store_true", help="skip the per-precision speed/accuracy report")
+    ap.add_argument("--precision-agents", type=int, default=48, help="agents per workload sample, precision report")
     ap.add_argument("--serve-seconds", type=float, default=0.5, help="serving run length (0 = skip)")
     ap.add_argument("--serve-rate", default="0.5,1,2",
                     help="request rates, comma-separated, x 16384 agents at 100 Hz")
@@ -178,7 +182,7 @@ def run_ours(args):
     def make_solver(form, **opts):
         chosen = form == mpcgpu.FORM_FUSED
         kw = dict(variant=args.variant, check_every=args.check_every, early_polish=args.early_polish,
-                  graph=int(chosen and not args.no_graph))
+                  graph=int(chosen and not args.no_graph), precision=args.precision, refine_steps=args.refine)
         kw.update(opts)
         s = mpcgpu.Solver(max_agents=n, max_horizon=int(Nh.max()), form=form, device=local,
                           stream=stream.cuda_stream, **kw)
@@ -318,6 +322,10 @@ def run_ours(args):
                       "note": "fixed N_QP = 25 ADMM iterations per replan, warm-started, no polish (the paper's "
                               "mode; speed only, not converged)"}
 
+    precision = None
+    if not args.no_precision:
+        precision = precision_report(args, timed, cfg, n, world, mpcgpu)
+
     plain = None
     if not args.no_plain:
         K2 = min(args.steps, 3)
@@ -350,6 +358,7 @@ def run_ours(args):
         "latency_budget_ms": 10.0, "per_step_ms": [round(v, 3) for v in per], "cold_solve": cold,
         "plain": plain,
         "paper_mode_fixed25": paper_mode,
+        "precision": precision,
         "serving": serving,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
@@ -369,6 +378,74 @@ def run_ours(args):
                    "dual_scaled_max": float(st["dual_scaled"].max())},
     }
     print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ precision
+PREC_NAMES = {0: "FP32", 1: "TF32", 2: "BF16", 3: "FP64-Schur"}
+
+
+def precision_report(args, timed, cfg, n, world, mpcgpu):
+    """Per factor precision: replan time on the full workload, and on seeded
+    samples of the regular and the ill-conditioned (Q, R in [1e-4, 1e4])
+    workloads, a cold and a warm replan each: the solver's own residuals and
+    the torques' deviation from an FP32 solve with two refinement steps.  (The
+    comparison with the FP64 oracle is in tests/test_gpu_precision.py.)"""
+    import torch
+    from workload import make_agents, perturb_inputs
+    K = min(args.steps, 5)
+    na = args.precision_agents
+    stream = torch.cuda.current_stream().cuda_stream
+    ids_all = np.arange(na, dtype=np.int32)
+
+    def sample_solve(model, inps, prec, refine):
+        sv = mpcgpu.Solver(max_agents=na, max_horizon=int(model["N"].max()), stream=stream,
+                           precision=prec, refine_steps=refine)
+        sv.set_models(model, ids_all)
+        res = []
+        for x in inps:
+            r = sv.solve_host(ids_all, x["x0"], x["qd_meas"], x["cmd"], x["phase"])
+            res.append((r, sv.agent_stats(ids_all)))
+        sv.close()
+        return res
+
+    samples = {}
+    for wl in ("mixed16k", "mixed16k_ill"):
+        ids = np.sort(np.random.default_rng(5).choice(16384, na, replace=False))
+        model, inp = make_agents(wl, ids)
+        inps = [inp, perturb_inputs(wl, inp, ids, 1)]
+        inps = [{k: np.ascontiguousarray(v, np.float32) for k, v in x.items()} for x in inps]
+        samples[wl] = (model, inps, [r["tau"] for r, _ in sample_solve(model, inps, 0, 2)])
+    out = {}
+    for prec in (0, 1, 2, 3):
+        s, tp, perp, _, _, _, _ = timed(mpcgpu.FORM_FUSED, K, args.warmup, tune=False, variant=cfg["variant"],
+                                       check_every=cfg["check_every"], early_polish=cfg["early_polish"],
+                                       precision=prec, refine_steps=-1)
+        s.close()
+        entry = {"value": world * n * K / (tp / 1e3), "ms_per_step": tp / K,
+                 "p50_ms": float(np.percentile(perp, 50)), "samples": {}}
+        for wl, (model, inps, taus_ref) in samples.items():
+            acc = []
+            for replan, ((r, st), tref) in enumerate(zip(sample_solve(model, inps, prec, -1), taus_ref)):
+                tau = r["tau"]
+                fin = np.isfinite(tau).all(axis=1)
+                dev = np.where(fin[:, None], np.abs(tau - tref) / (1e-4 + 1e-3 * np.abs(tref)), np.inf)
+                rel = np.linalg.norm(np.nan_to_num(tau - tref, nan=1e9), axis=1) / \
+                    np.maximum(np.linalg.norm(tref, axis=1), 1e-9)
+                acc.append({"replan": "cold" if replan == 0 else "warm", "agents": na,
+                            "solved": float((r["status"] == 0).mean()),
+                            "polished": float((st["polished"] > 0).mean()),
+                            "iters_mean": float(st["iters"].mean()), "iters_max": int(st["iters"].max()),
+                            "prim_res_max": float(np.max(st["prim_res"])), "dual_res_max": float(np.max(st["dual_res"])),
+                            "prim_scaled_max": float(np.max(st["prim_scaled"])),
+                            "dual_scaled_max": float(np.max(st["dual_scaled"])),
+                            "within_torque_tol_of_fp32_refined": float((dev.max(axis=1) <= 1.0).mean()),
+                            "median_rel_dev": float(np.median(rel)), "max_rel_dev": float(np.max(rel))})
+            entry["samples"][wl] = acc
+        out[PREC_NAMES[prec]] = entry
+    out["note"] = ("factor precision; refinement automatic (1 step on a polish after ADMM, and on the warm-start "
+                   "polish for TF32/BF16); deviations against FP32 with 2 refinement steps, torque tolerance "
+                   "1e-4 N m + 1e-3 |tau|; oracle comparison in tests/test_gpu_precision.py")
+    return out
 
 
 # ------------------------------------------------------------------ serving

@@ -79,7 +79,7 @@ typedef enum {
  * rho0 0.1, sigma 1e-6, alpha 1.6, eps_abs = eps_rel = 1e-5, max_iter 4000,
  * fixed_iters 0, check_every 10, adaptive_rho 1, polish 1, warm_start 1,
  * form FUSED, precision FP32, max_horizon 20, variant 1, early_polish 100,
- * graph 0, warm_polish 1.  OSQP's parameters (Stellato et al. 2020,
+ * graph 0, warm_polish 1, refine_steps -1.  OSQP's parameters (Stellato et al. 2020,
  * Sec. 3.2, to which the paper defers after Eq. (backsolve_2)). */
 typedef struct mpc_config {
   int device;                 /* CUDA device ordinal */
@@ -87,7 +87,11 @@ typedef struct mpc_config {
   int max_agents;             /* agent ids are 0 .. max_agents-1 */
   int max_horizon;            /* largest N any agent may use (<= MPC_MAX_HORIZON) */
   size_t hbm_budget_bytes;    /* cap on all device arenas; 0 = no cap */
-  int precision;              /* mpc_precision; only MPC_FP32 is implemented */
+  int precision;              /* mpc_precision of the Riccati factor (the rest is FP32):
+                                 FP32; TF32 / BF16 = the two dense stage-block
+                                 products (K = -H_uu^-1 H_ux and H_ux^T K) on the
+                                 tensor cores (mma.sync), FP32 accumulation; FP64 =
+                                 the stage Schur complement H_uu inverted in FP64 */
   int form;                   /* mpc_form: separate step kernels or one fused kernel */
   float rho0, sigma, alpha;   /* ADMM step size, proximal weight, relaxation */
   float eps_abs, eps_rel;     /* OSQP-style stopping tolerances */
@@ -108,6 +112,10 @@ typedef struct mpc_config {
   int warm_polish;            /* 1: on a warm start, first polish from the previous
                                  replan's final active set; ADMM runs only if that
                                  fails its KKT check */
+  int refine_steps;           /* iterative-refinement steps on each polish solve
+                                 (0..4); -1 = automatic: 1 on a polish after ADMM
+                                 iterations, and on the warm-start polish 1 for
+                                 TF32 / BF16, 0 for FP32 / FP64 */
 } mpc_config;
 
 /* One agent's model (host memory, float64; stored as float32 on the device,

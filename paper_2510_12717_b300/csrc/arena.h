@@ -75,6 +75,7 @@ struct Arena {
   float* cK;              // [A][maxN*BLK] Riccati gains K_k (R24)
   float* cH;              // [A][maxN*BLK] inverse Schur blocks H_uu^-1 (R24)
   float* cEl;             // [A][maxN*128] polish: per-stage elimination of each input (float4 per lane)
+  float* cD;              // [A][maxN*VS]  polish refinement: feed-forward terms of the correction
   float* cE;              // [A][maxN*64] e_k = P_{k+1} c_k (lanes 0-21), arm gain (22-29),
                           //   arm e (32-39), arm H_uu^-1 (54-61)
   float* xt;              // [A][(maxN+1)*VS] KKT-solve primal (x tilde)
@@ -105,6 +106,9 @@ struct Batch {
 struct SolverParams {
   float rho0, sigma, alpha, eps_abs, eps_rel, early_polish;
   int max_iter, fixed_iters, check_every, adaptive_rho, polish, warm_start, warm_polish;
+  int precision;   // factor precision: PREC_FP32 / PREC_TF32 / PREC_BF16 / PREC_FP64
+  int refine;      // iterative-refinement steps on a polish from the previous active set
+  int refine_admm; // ... and on a polish that follows ADMM iterations
 };
 
 }  // namespace mpc

@@ -116,7 +116,7 @@ static size_t arena_bytes(size_t A, size_t n) {
   f += A * IN_F;
   f += A * ((n + 1) * VS + n * VS + 3 * n * RS);     // xref uref rlo rhi rcls
   f += A * lin_floats((int)n);
-  f += A * (2 * n * BLK + n * 64 + n * 128);         // cK cH cE cEl
+  f += A * (2 * n * BLK + n * 64 + n * 128 + n * VS); // cK cH cE cEl cD
   f += A * ((n + 1) * VS + 2 * n * VS + n * RS + 1); // xt ut dv act order
   f += A * (1 + 30 + 18 + 4 + 1 + 18 * 3 + 2);       // host-path staging
   f += A * (MODEL_F + 2 * SCHED_D + 1);              // model upload staging
@@ -151,6 +151,7 @@ mpc_status mpc_default_config(mpc_config* cfg) {
   cfg->early_polish = 100.f;
   cfg->graph = 0;
   cfg->warm_polish = 1;
+  cfg->refine_steps = -1;
   return MPC_OK;
 }
 
@@ -160,7 +161,8 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   if (!cfg) return MPC_ERR_INVALID;
   if (cfg->max_agents <= 0 || cfg->max_horizon < 2 || cfg->max_horizon > MPC_MAX_HORIZON)
     return MPC_ERR_INVALID;
-  if (cfg->precision != MPC_FP32) return MPC_ERR_INVALID;
+  if (cfg->precision < MPC_FP32 || cfg->precision > MPC_FP64) return MPC_ERR_INVALID;
+  if (cfg->refine_steps < -1 || cfg->refine_steps > 4) return MPC_ERR_INVALID;
   if (cfg->form != MPC_FORM_PLAIN && cfg->form != MPC_FORM_FUSED) return MPC_ERR_INVALID;
   if (!(cfg->rho0 > 0.f) || !(cfg->sigma > 0.f) || !(cfg->alpha > 0.f && cfg->alpha < 2.f) ||
       !(cfg->eps_abs >= 0.f) || !(cfg->eps_rel >= 0.f) || cfg->max_iter <= 0 || cfg->fixed_iters < 0 ||
@@ -208,6 +210,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   AL(a.cH, A * n * BLK);
   AL(a.cE, A * n * 64);
   AL(a.cEl, A * n * 128);
+  AL(a.cD, A * n * VS);
   AL(a.xt, A * (n + 1) * VS);
   AL(a.ut, A * n * VS);
   AL(a.dv, A * n * VS);
@@ -421,6 +424,13 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   p.max_iter = c.max_iter; p.fixed_iters = c.fixed_iters; p.check_every = c.check_every;
   p.adaptive_rho = c.adaptive_rho; p.polish = c.polish; p.warm_start = c.warm_start;
   p.warm_polish = c.warm_polish;
+  p.precision = c.precision;
+  // automatic: one step where the factor is TF32 / BF16; otherwise one on a
+  // polish after ADMM (a cold or fallback solve, where it is cheap next to the
+  // iterations) and none on the warm-start polish
+  const bool low = c.precision == MPC_TF32 || c.precision == MPC_BF16;
+  p.refine = c.refine_steps >= 0 ? c.refine_steps : (low ? 1 : 0);
+  p.refine_admm = c.refine_steps >= 0 ? c.refine_steps : 1;
   return p;
 }
 

@@ -57,7 +57,7 @@ struct AgentPtrs {
   int N;
   float *x, *u, *w, *y, *rho;
   int* warm;
-  float *inp, *xref, *uref, *rlo, *rhi, *rcls, *lin, *cK, *cH, *cE, *cEl, *xt, *ut, *dv;
+  float *inp, *xref, *uref, *rlo, *rhi, *rcls, *lin, *cK, *cH, *cE, *cEl, *cD, *xt, *ut, *dv;
   int* act;
   float* out;
   int* st;
@@ -86,6 +86,7 @@ __device__ __forceinline__ AgentPtrs agent_ptrs(const Arena& a, int s) {
   p.cH = a.cH + (size_t)s * n * BLK;
   p.cE = a.cE + (size_t)s * n * 64;
   p.cEl = a.cEl + (size_t)s * n * 128;
+  p.cD = a.cD + (size_t)s * n * VS;
   p.xt = a.xt + (size_t)s * (n + 1) * VS;
   p.ut = a.ut + (size_t)s * n * VS;
   p.dv = a.dv + (size_t)s * n * VS;
@@ -257,6 +258,157 @@ __device__ __forceinline__ void r24_inv(float* H, float* sc, int lane) {
 #pragma unroll
     for (int i = 0; i < NC; ++i) H[i * R24 + j] = h[i];
   }
+  __syncwarp();
+}
+
+// The same inverse with the sweep in FP64 (the stage Schur complement where
+// conditioning needs it); H in and out stays FP32.  sc: 2 x 32 doubles
+// (16-byte aligned).  A pivot reads the row back element by element, so the
+// row is not held in registers twice.
+static __device__ __noinline__ void r24_inv_f64(float* H, double* sc, int lane) {
+  const int j = lane < NC ? lane : NC - 1;
+  double h[NC];
+#pragma unroll
+  for (int i = 0; i < NC; ++i) h[i] = (double)H[i * R24 + j];
+  sc[lane] = h[0];
+#pragma unroll
+  for (int p = 0; p < NC; ++p) {
+    __syncwarp();
+    const double* v = sc + (p & 1) * 32;
+    const double inv = 1.0 / v[p];
+    double* nxt = sc + ((p + 1) & 1) * 32;
+    if (j == p) {
+      if (p + 1 < NC) { h[p + 1] = -h[p + 1] * inv; nxt[lane] = h[p + 1]; }
+#pragma unroll
+      for (int i = 0; i < NC; ++i)
+        if (i != p && i != p + 1) h[i] = -h[i] * inv;
+      h[p] = inv;
+    } else {
+      const double rp = h[p] * inv;
+      if (p + 1 < NC) { h[p + 1] = fma(-v[p + 1], rp, h[p + 1]); nxt[lane] = h[p + 1]; }
+#pragma unroll
+      for (int i = 0; i < NC; ++i) {
+        if (i == p || i == p + 1) continue;
+        const double ci = i < p ? -v[i] : v[i];
+        h[i] = fma(-ci, rp, h[i]);
+      }
+      h[p] = rp;
+    }
+  }
+  if (lane < NC) {
+#pragma unroll
+    for (int i = 0; i < NC; ++i) H[i * R24 + j] = (float)h[i];
+  }
+  __syncwarp();
+}
+
+// ------------------------------------------------- tensor-core R24 products
+// C = alpha * A^T B (+ Cadd) for the 22 x 22 blocks on the warp's tensor
+// cores (mma.sync), FP32 accumulation: M = 22 padded to 32 (two m16 tiles),
+// N = 22 padded to 24 (three n8 tiles), K = 22 padded to 24 (TF32, k8) or 32
+// (BF16, k16).  Padding reads as zero; the padding columns of C are written
+// as zero.  Fragment layouts (PTX ISA, mma.m16n8k8 .tf32 / m16n8k16 .bf16):
+// g = lane / 4, t = lane % 4;  C: (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1).
+enum : int { PREC_FP32 = 0, PREC_TF32 = 1, PREC_BF16 = 2, PREC_FP64 = 3 };
+
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  uint32_t r;
+  asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(r) : "f"(hi), "f"(lo));
+  return r;
+}
+// A^T(m, k) = A[k][m] and B(k, n) with the 22 x 22 bounds applied
+__device__ __forceinline__ float r24_at(const float* A, int k, int m) {
+  return (k < NC && m < NC) ? A[k * R24 + m] : 0.f;
+}
+
+template <int P>
+__device__ __noinline__ void r24_gemm_tn_mma(float* C, const float* A, const float* B, const float* Cadd,
+                                             float alpha, int lane) {
+  const int g = lane >> 2, t = lane & 3;
+  float acc[2][3][4];
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 3; ++ni)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[mi][ni][c] = 0.f;
+  if (P == PREC_TF32) {
+#pragma unroll
+    for (int k0 = 0; k0 < 24; k0 += 8) {
+      uint32_t a[2][4], b[3][2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int m = 16 * mi + g;
+        a[mi][0] = to_tf32(r24_at(A, k0 + t, m));
+        a[mi][1] = to_tf32(r24_at(A, k0 + t, m + 8));
+        a[mi][2] = to_tf32(r24_at(A, k0 + t + 4, m));
+        a[mi][3] = to_tf32(r24_at(A, k0 + t + 4, m + 8));
+      }
+#pragma unroll
+      for (int ni = 0; ni < 3; ++ni) {
+        const int n = 8 * ni + g;
+        b[ni][0] = to_tf32(r24_at(B, k0 + t, n));
+        b[ni][1] = to_tf32(r24_at(B, k0 + t + 4, n));
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 3; ++ni)
+          asm volatile(
+              "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};"
+              : "+f"(acc[mi][ni][0]), "+f"(acc[mi][ni][1]), "+f"(acc[mi][ni][2]), "+f"(acc[mi][ni][3])
+              : "r"(a[mi][0]), "r"(a[mi][1]), "r"(a[mi][2]), "r"(a[mi][3]), "r"(b[ni][0]), "r"(b[ni][1]));
+    }
+  } else {
+#pragma unroll
+    for (int k0 = 0; k0 < 32; k0 += 16) {
+      uint32_t a[2][4], b[3][2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int m = 16 * mi + g;
+        a[mi][0] = pack_bf16(r24_at(A, k0 + 2 * t, m), r24_at(A, k0 + 2 * t + 1, m));
+        a[mi][1] = pack_bf16(r24_at(A, k0 + 2 * t, m + 8), r24_at(A, k0 + 2 * t + 1, m + 8));
+        a[mi][2] = pack_bf16(r24_at(A, k0 + 2 * t + 8, m), r24_at(A, k0 + 2 * t + 9, m));
+        a[mi][3] = pack_bf16(r24_at(A, k0 + 2 * t + 8, m + 8), r24_at(A, k0 + 2 * t + 9, m + 8));
+      }
+#pragma unroll
+      for (int ni = 0; ni < 3; ++ni) {
+        const int n = 8 * ni + g;
+        b[ni][0] = pack_bf16(r24_at(B, k0 + 2 * t, n), r24_at(B, k0 + 2 * t + 1, n));
+        b[ni][1] = pack_bf16(r24_at(B, k0 + 2 * t + 8, n), r24_at(B, k0 + 2 * t + 9, n));
+      }
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 3; ++ni)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};"
+              : "+f"(acc[mi][ni][0]), "+f"(acc[mi][ni][1]), "+f"(acc[mi][ni][2]), "+f"(acc[mi][ni][3])
+              : "r"(a[mi][0]), "r"(a[mi][1]), "r"(a[mi][2]), "r"(a[mi][3]), "r"(b[ni][0]), "r"(b[ni][1]));
+    }
+  }
+  __syncwarp();
+#pragma unroll
+  for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+    for (int ni = 0; ni < 3; ++ni)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int row = 16 * mi + g + ((c & 2) ? 8 : 0);
+        const int col = 8 * ni + 2 * t + (c & 1);
+        if (row < NC) {
+          float v = 0.f;
+          if (col < NC) v = alpha * acc[mi][ni][c] + (Cadd ? Cadd[row * R24 + col] : 0.f);
+          C[row * R24 + col] = v;
+        }
+      }
   __syncwarp();
 }
 

@@ -325,7 +325,7 @@ struct StageIn {
 struct StageOut { float e, Ka, Hi; };
 
 __device__ __forceinline__ StageOut factor_stage(const AgentPtrs& ap, float* sm, int lane, int k,
-                                                 const StageIn& in, float* Pa, const LanePat& pat,
+                                                 const StageIn& in, float* Pa, const LanePat& pat, int prec,
                                                  bool store_h = true) {
   StageOut so;
   so.e = so.Ka = so.Hi = 0.f;
@@ -400,8 +400,13 @@ __device__ __forceinline__ StageOut factor_stage(const AgentPtrs& ap, float* sm,
     }
   }
   __syncwarp();
-  r24_inv(H, sm + S_VEC + V_S * 64, lane);   // V_S is free during a factor stage
-  r24_gemm_tn(K, H, X, nullptr, -1.f, lane);     // K = -H_uu^-1 H_ux (H_uu^-1 symmetric)
+  // V_S (and V_H) are free during a factor stage
+  if (prec == PREC_FP64) r24_inv_f64(H, reinterpret_cast<double*>(sm + S_VEC + V_S * 64), lane);
+  else r24_inv(H, sm + S_VEC + V_S * 64, lane);
+  // K = -H_uu^-1 H_ux (H_uu^-1 symmetric)
+  if (prec == PREC_TF32) r24_gemm_tn_mma<PREC_TF32>(K, H, X, nullptr, -1.f, lane);
+  else if (prec == PREC_BF16) r24_gemm_tn_mma<PREC_BF16>(K, H, X, nullptr, -1.f, lane);
+  else r24_gemm_tn(K, H, X, nullptr, -1.f, lane);
   copy_blk(ap.cK + (size_t)k * BLK, K, lane);
   if (store_h) copy_blk(ap.cH + (size_t)k * BLK, H, lane);
   float* ce = ap.cE + k * 64;
@@ -423,7 +428,10 @@ __device__ __forceinline__ StageOut factor_stage(const AgentPtrs& ap, float* sm,
     if (k >= 1) *Pa = in.qt + Aa * Aa * (*Pa) + Hux * Ka;
   }
   if (k >= 1) {
-    r24_gemm_tn(P, X, K, P, 1.f, lane);          // P = A^T P A + H_ux^T K
+    // P = A^T P A + H_ux^T K
+    if (prec == PREC_TF32) r24_gemm_tn_mma<PREC_TF32>(P, X, K, P, 1.f, lane);
+    else if (prec == PREC_BF16) r24_gemm_tn_mma<PREC_BF16>(P, X, K, P, 1.f, lane);
+    else r24_gemm_tn(P, X, K, P, 1.f, lane);
     float t[NC];
     if (lane < NC) {
 #pragma unroll
@@ -479,7 +487,8 @@ __device__ __forceinline__ StageIn admm_stage_in(const AgentPtrs& ap, int k, flo
   return in;
 }
 
-__device__ __noinline__ void factor_admm(const AgentPtrs& ap, float* sm, int lane, float rho, float sigma, const LanePat& pat) {
+__device__ __noinline__ void factor_admm(const AgentPtrs& ap, float* sm, int lane, float rho, float sigma,
+                                        const LanePat& pat, int prec) {
   const int N = ap.N;
   float* P = sm + S_P;
   float* cvec = sm + S_VEC + V_C * 64;
@@ -494,7 +503,7 @@ __device__ __noinline__ void factor_admm(const AgentPtrs& ap, float* sm, int lan
   for (int k = N - 1; k >= 0; --k) {
     set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
     const StageIn in = admm_stage_in(ap, k, rho, sigma, cvec, lane);
-    factor_stage(ap, sm, lane, k, in, &Pa, pat);
+    factor_stage(ap, sm, lane, k, in, &Pa, pat, prec);
   }
   // the caches were written with generic stores and are read back through
   // the async (TMA) proxy
@@ -924,12 +933,152 @@ __device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const 
   return in;
 }
 
+// Polish forward pass: v = K x + d, u = G v + t + Phi x, x+ = A x + B u + c
+// with the recorded eliminations; a refinement pass re-rolls from the
+// previous pass: v = v_old + K (x - x_old) + d' with the correction's
+// feed-forward d'.  v is kept (dv) for the next pass.
+__device__ __noinline__ void polish_rollout(const AgentPtrs& ap, float* sm, int lane, Pipe& pp, bool refine) {
+  const int N = ap.N;
+  const float dt = ap.mdl[M_DT];
+  float* vec = sm + S_VEC;
+  float* vX = vec + V_X * 64; float* vV = vec + V_U * 64; float* vU = vec + V_XN * 64;
+  const bool arm = lane >= NC && lane < 30;
+  float* const K0 = sm + S_P; float* const K1 = sm + S_X;
+    float x = lane < 30 ? ap.x[lane] : 0.f;
+    float xo = x;                                  // previous pass's x_k (x_0 is fixed)
+    pipe_issue(pp, 0, K0, ap.cK, nullptr, nullptr, lane);
+    for (int k = 0; k < N; ++k) {
+      const int b = k & 1;
+      float* const Kc = b ? K1 : K0;
+      if (k + 1 < N) pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k + 1) * BLK, nullptr, nullptr, lane);
+      const float* ce = ap.cE + k * 64;
+      const float* dA = ap.lin + L_STAGE + k * 64;
+      const float4 el = reinterpret_cast<const float4*>(ap.cEl + k * 128)[lane];
+      vX[lane] = refine ? x - xo : x;
+      const float base = refine ? ap.dv[k * VS + lane] + ap.cD[k * VS + lane] : ap.dv[k * VS + lane];
+      const float xo_next = refine ? ap.xt[(k + 1) * VS + lane] : 0.f;
+      pipe_wait(pp, b);
+      __syncwarp();
+      float v = 0.f;
+      if (lane < NC) v = r24_mv(Kc, vX, lane) + base;
+      else if (arm) v = ce[lane] * vX[lane] + base;
+      vV[lane] = v;
+      ap.dv[k * VS + lane] = v;
+      __syncwarp();
+      float u = 0.f;
+      if (lane < 12 && (lane % 6) < 3) {
+        const int bb = (lane / 6) * 6;
+        u = el.x * vV[bb] + el.y * vV[bb + 1] + el.z * vV[bb + 2] + el.w;
+      } else if (lane < 30) {
+        u = el.x * v + el.w + el.z * x;
+      }
+      vU[lane] = u;
+      vX[lane] = x;
+      __syncwarp();
+      float xn = 0.f;
+      if (lane < NC) xn = ak_mv(sm + S_AB, dA, vX, lane) + cm_mv(sm + S_B, vU, lane) + dA[32 + lane];
+      else if (arm) xn = x + dt * u;
+      ap.xt[(k + 1) * VS + lane] = xn;
+      ap.ut[k * VS + lane] = u;
+      x = xn;
+      xo = xo_next;
+      __syncwarp();
+    }
+}
+
+// One iterative-refinement step of the polish solve: the residual of the
+// reduced problem's v-stationarity, R_hat v + r_hat + B_hat^T lam_{k+1}, with
+// the costate lam that makes its x-stationarity exact, is the linear term of a
+// correction solved with the same factors (K_k, H_uu,k^-1); the rollout then
+// applies it through the exact dynamics.
+__device__ __noinline__ void polish_refine(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat, Pipe& pp) {
+  const int N = ap.N;
+  const float* md = ap.mdl;
+  const float dt = md[M_DT], mu = md[M_MU];
+  float* vec = sm + S_VEC;
+  float* cvec = vec + V_C * 64;
+  int* act = reinterpret_cast<int*>(vec + V_ACT * 64);
+  float* vS = vec + V_S * 64; float* vH = vec + V_H * 64; float* vV = vec + V_U * 64;
+  const bool arm = lane >= NC && lane < 30;
+  const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
+  float* const K0 = sm + S_P; float* const K1 = sm + S_X;
+  float* const H0 = sm + S_H; float* const H1 = sm + S_K;
+  float* vR = vec + V_ROW * 64;
+  float lam = lane < 30 ? twoQ * (ap.xt[N * VS + lane] - ap.xref[N * VS + lane]) : 0.f;
+  float pc = 0.f;
+  Carry carry2 = {0, 0.f};
+  pipe_issue(pp, 0, K0, ap.cK + (size_t)(N - 1) * BLK, H0, ap.cH + (size_t)(N - 1) * BLK, lane);
+  for (int k = N - 1; k >= 0; --k) {
+    const int b = (N - 1 - k) & 1;
+    float* const Kc = b ? K1 : K0;
+    float* const Hc = b ? H1 : H0;
+    if (k >= 1)
+      pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k - 1) * BLK, b ? H0 : H1,
+                 ap.cH + (size_t)(k - 1) * BLK, lane);
+    stage_active(ap, k, act, lane);
+    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
+    const Elim el = lane_elim(ap, k, act, lane, mu, carry2);
+    carry2 = el.carry_out;
+    const StageIn in = polish_stage_in(ap, sm, k, act, cvec, el, lane);
+    const float v = ap.dv[k * VS + lane];
+    vV[lane] = v;
+    vS[lane] = lam;
+    vR[lane] = pc;
+    __syncwarp();
+    float rv = 0.f, h = 0.f;
+    if (lane < 12 && (lane % 6) < 3) {
+      const int bb = (lane / 6) * 6, c = lane - bb;
+      rv = in.rt_diag * v;
+#pragma unroll
+      for (int r3 = 0; r3 < 3; ++r3)
+        if (r3 != c) rv = fmaf(in.rt_off[r3], vV[bb + r3], rv);
+    } else if (lane < 30) {
+      rv = in.rt_diag * v;
+    }
+    if (lane < NC) {
+      rv += in.rh + cc_tv(sm + S_BV, pat.br, vS, lane);
+      h = rv + cc_tv(sm + S_BV, pat.br, vR, lane);
+    } else if (arm) {
+      rv += in.rh + in.rt_off[0] * lam;
+      h = rv + in.rt_off[0] * pc;
+    }
+    vH[lane] = h;
+    float lamn = 0.f, pcn = 0.f;
+    if (k >= 1 && lane < 30) {
+      float ql = -twoQ * ap.xref[k * VS + lane];
+      if (el.qbox) ql -= 2.f * md[M_R + lane] * el.t;
+      lamn = in.qt * ap.xt[k * VS + lane] + ql +
+             (lane < NC ? cc_tv(sm + S_AV, pat.ar, vS, lane) : (el.qbox ? 0.f : lam));
+      pcn = lane < NC ? cc_tv(sm + S_AV, pat.ar, vR, lane) : (el.qbox ? 0.f : pc);
+    }
+    const float* ce = ap.cE + k * 64;
+    pipe_wait(pp, b);
+    __syncwarp();
+    float d = 0.f;
+    if (lane < NC) d = -r24_mtv(Hc, vH, lane);
+    else if (arm) d = -ce[32 + lane] * h;
+    ap.cD[k * VS + lane] = d;
+    if (k >= 1) {
+      if (lane < NC) pcn += r24_mtv(Kc, vH, lane);
+      else if (arm) pcn += ce[lane] * h;
+    }
+    lam = lamn;
+    pc = pcn;
+    __syncwarp();
+  }
+  copy_n(sm + S_BV, ap.lin + L_BV, 136 / 4, lane);
+  __syncwarp();
+  
+  polish_rollout(ap, sm, lane, pp, true);
+}
+
 // Factor and solve the reduced problem in one backward pass (the linear
 // recursion rides along with the Riccati recursion, since the reduced problem
 // is solved once), then roll forward with u = G v + t + Phi x through the
 // original dynamics.  The polished primal goes to xt/ut.  Overwrites the
 // Riccati caches (the caller refactors if ADMM continues).
-__device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat, Pipe& pp) {
+__device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat, Pipe& pp,
+                                          const SolverParams& prm, int nref) {
   const int N = ap.N;
   const float* md = ap.mdl;
   const float dt = md[M_DT], mu = md[M_MU];
@@ -937,8 +1086,7 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
   float* vec = sm + S_VEC;
   float* cvec = vec + V_C * 64;
   int* act = reinterpret_cast<int*>(vec + V_ACT * 64);
-  float* vS = vec + V_S * 64; float* vH = vec + V_H * 64; float* vX = vec + V_X * 64;
-  float* vV = vec + V_U * 64; float* vU = vec + V_XN * 64;
+  float* vS = vec + V_S * 64; float* vH = vec + V_H * 64;
   const int j = lane < NC ? lane : NC - 1;
   const bool arm = lane >= NC && lane < 30;
   const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
@@ -966,7 +1114,7 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
           make_float4(fl ? el.gf[0] : el.g, el.gf[1], fl ? el.gf[2] : el.phi, el.t);
     }
     const StageIn in = polish_stage_in(ap, sm, k, act, cvec, el, lane);
-    const StageOut so = factor_stage(ap, sm, lane, k, in, &Pa, pat, false);
+    const StageOut so = factor_stage(ap, sm, lane, k, in, &Pa, pat, prm.precision, nref > 0);
     // H (= H_uu^-1) and K of stage k are still in smem
     const float s = p + so.e;
     vS[lane] = s;
@@ -994,43 +1142,8 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
   fence_proxy_async();   // K_k were written with generic stores; the rollout reads them by TMA
   __syncwarp();
 
-  // ---- forward rollout: v = K x + d, u = G v + t + Phi x, x+ = A x + B u + c
-  float* const K0 = sm + S_P; float* const K1 = sm + S_X;
-  float x = lane < 30 ? ap.x[lane] : 0.f;
-  pipe_issue(pp, 0, K0, ap.cK, nullptr, nullptr, lane);
-  for (int k = 0; k < N; ++k) {
-    const int b = k & 1;
-    float* const Kc = b ? K1 : K0;
-    if (k + 1 < N) pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k + 1) * BLK, nullptr, nullptr, lane);
-    const float* ce = ap.cE + k * 64;
-    const float* dA = ap.lin + L_STAGE + k * 64;
-    const float4 el = reinterpret_cast<const float4*>(ap.cEl + k * 128)[lane];
-    vX[lane] = x;
-    const float dk = ap.dv[k * VS + lane];
-    pipe_wait(pp, b);
-    __syncwarp();
-    float v = 0.f;
-    if (lane < NC) v = r24_mv(Kc, vX, lane) + dk;
-    else if (arm) v = ce[lane] * x + dk;
-    vV[lane] = v;
-    __syncwarp();
-    float u = 0.f;
-    if (lane < 12 && (lane % 6) < 3) {
-      const int bb = (lane / 6) * 6;
-      u = el.x * vV[bb] + el.y * vV[bb + 1] + el.z * vV[bb + 2] + el.w;
-    } else if (lane < 30) {
-      u = el.x * v + el.w + el.z * x;
-    }
-    vU[lane] = u;
-    __syncwarp();
-    float xn = 0.f;
-    if (lane < NC) xn = ak_mv(sm + S_AB, dA, vX, lane) + cm_mv(sm + S_B, vU, lane) + dA[32 + lane];
-    else if (arm) xn = x + dt * u;
-    ap.xt[(k + 1) * VS + lane] = xn;
-    ap.ut[k * VS + lane] = u;
-    x = xn;
-    __syncwarp();
-  }
+  polish_rollout(ap, sm, lane, pp, false);
+  for (int rs = 0; rs < nref; ++rs) polish_refine(ap, sm, lane, pat, pp);
   return !warp_or(pp.timeout);
 }
 
@@ -1273,7 +1386,7 @@ __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, co
   // alternative is an ADMM solve
   const int attempts = from_prev ? 8 : 4;
   for (int attempt = 0; attempt < attempts; ++attempt) {
-    if (!polish_solve(ap, sm, lane, pat, pp)) return false;
+    if (!polish_solve(ap, sm, lane, pat, pp, prm, from_prev ? prm.refine : prm.refine_admm)) return false;
     const Res pr = polish_check<false>(ap, sm, lane, prm, nullptr, pat);
     const float tol_p = prm.eps_abs + prm.eps_rel * pr.ps;
     const float tol_d = prm.eps_abs + prm.eps_rel * pr.ds;
@@ -1429,7 +1542,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
     factored = false;   // the polish overwrote the caches
     polish_warm_start(ap, sm, lane, pat);
   }
-  if (!factored) factor_admm(ap, sm, lane, rho, prm.sigma, pat);
+  if (!factored) factor_admm(ap, sm, lane, rho, prm.sigma, pat, prm.precision);
   const bool fixed = prm.fixed_iters > 0;
   const int max_it = fixed ? prm.fixed_iters : prm.max_iter;
   // polish attempts: the first once both residuals are within early_polish x
@@ -1468,7 +1581,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
         o.r = pr;
         break;
       }
-      factor_admm(ap, sm, lane, rho, prm.sigma, pat);   // the polish overwrote the caches
+      factor_admm(ap, sm, lane, rho, prm.sigma, pat, prm.precision);   // the polish overwrote the caches
       ++o.refac;
     }
     if (prm.adaptive_rho && it < max_it) {
@@ -1478,7 +1591,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
       rn = fminf(fmaxf(rn, 1e-6f), 1e6f);
       if (rn > 5.f * rho || rn < 0.2f * rho) {
         rho = rn;
-        factor_admm(ap, sm, lane, rho, prm.sigma, pat);
+        factor_admm(ap, sm, lane, rho, prm.sigma, pat, prm.precision);
         ++o.refac;
       }
     }
@@ -1641,7 +1754,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_factor(Arena
   const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
   if (ap.st[T_STATUS] == MPC_AGENT_NAN_) return;
   load_lin(ap, sm, lane);
-  factor_admm(ap, sm, lane, *ap.rho, prm.sigma, lane_pattern(lane));
+  factor_admm(ap, sm, lane, *ap.rho, prm.sigma, lane_pattern(lane), prm.precision);
 }
 
 template <int MINB>

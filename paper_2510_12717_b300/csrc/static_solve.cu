@@ -26,7 +26,7 @@ constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct Layout {
   size_t model, sched, horizon, ids, xs, us, ws, ys, rho, warm, out, stat, inp, xref, uref, rlo, rhi,
-      rcls, lin, cK, cH, cE, cEl, xt, ut, dv, act, order, counter, total;
+      rcls, lin, cK, cH, cE, cEl, cD, xt, ut, dv, act, order, counter, total;
 };
 
 constexpr Layout make_layout(size_t A, size_t n) {
@@ -57,6 +57,7 @@ constexpr Layout make_layout(size_t A, size_t n) {
   L.cH = take(A * n * BLK * 4);
   L.cE = take(A * n * 64 * 4);
   L.cEl = take(A * n * 128 * 4);
+  L.cD = take(A * n * VS * 4);
   L.xt = take(A * (n + 1) * VS * 4);
   L.ut = take(A * n * VS * 4);
   L.dv = take(A * n * VS * 4);
@@ -192,6 +193,7 @@ extern "C" mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_
   a.cH = at<float>(b, kL.cH);
   a.cE = at<float>(b, kL.cE);
   a.cEl = at<float>(b, kL.cEl);
+  a.cD = at<float>(b, kL.cD);
   a.xt = at<float>(b, kL.xt);
   a.ut = at<float>(b, kL.ut);
   a.dv = at<float>(b, kL.dv);
@@ -220,6 +222,9 @@ extern "C" mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_
   prm.check_every = c.check_every; prm.adaptive_rho = c.adaptive_rho; prm.polish = c.polish;
   prm.warm_start = 0;
   prm.warm_polish = 0;
+  prm.precision = c.precision;
+  prm.refine = 0;
+  prm.refine_admm = 1;
   mpc::Batch bt{n, d_ids, x0, qd_meas, cmd, phase, nullptr, nullptr};
   if (mpc::launch_solve(a, bt, prm, MPC_FORM_FUSED, 0, st, nullptr, c.variant) != cudaSuccess) return MPC_ERR_CUDA;
   if (mpc::launch_gather(a, n, d_ids, tau, q_set, qd_set, value, agent_status, st) != cudaSuccess)

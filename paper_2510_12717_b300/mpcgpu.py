@@ -34,6 +34,7 @@ class MpcConfig(C.Structure):
         ("fixed_iters", C.c_int), ("check_every", C.c_int), ("adaptive_rho", C.c_int),
         ("polish", C.c_int), ("warm_start", C.c_int), ("variant", C.c_int),
         ("early_polish", C.c_float), ("graph", C.c_int), ("warm_polish", C.c_int),
+        ("refine_steps", C.c_int),
     ]
 
 

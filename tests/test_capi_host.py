@@ -59,8 +59,12 @@ def test_default_config_and_argument_errors(lib):
     bad.max_horizon = 99
     assert lib.mpc_create(C.byref(bad), C.byref(h)) == mpcgpu.MPC_ERR_INVALID
     bad.max_horizon = 20
-    bad.precision = mpcgpu.BF16       # not built yet: rejected, not silently run in FP32
+    bad.precision = 7                 # not a precision
     assert lib.mpc_create(C.byref(bad), C.byref(h)) == mpcgpu.MPC_ERR_INVALID
+    bad.precision = mpcgpu.BF16
+    bad.refine_steps = 9              # out of range
+    assert lib.mpc_create(C.byref(bad), C.byref(h)) == mpcgpu.MPC_ERR_INVALID
+    bad.refine_steps = -1
     bad.precision = mpcgpu.FP32
     bad.hbm_budget_bytes = 1024       # far below what 16 agents need
     assert lib.mpc_create(C.byref(bad), C.byref(h)) == mpcgpu.MPC_ERR_BUDGET
