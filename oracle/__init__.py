@@ -18,6 +18,8 @@ Sec. III-B Eq. (kkt_system); Sec. III-C Alg. 1, Eqs. (rnea), (mpc_torque)):
              solve of that QP (the exact optimum the GPU's ADMM converges to)
   torque.py  first-stage solution -> joint torques (Eqs. rnea, mpc_torque)
   solve.py   the whole per-agent pipeline, and a process pool over agents
+  policy.py  residual policy (Sec. IV: observation, 3 x 256 ELU MLP, leg
+             actions) and joint-torque blending (Eq. joint-torque)
   lqr.py     closed-form affine finite-horizon LQR (a pin for the IPM)
   activeset.py brute-force active-set enumeration on toy QPs (a pin)
   kkt.py     KKT stationarity / feasibility / complementarity checks (a pin)

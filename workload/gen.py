@@ -195,3 +195,21 @@ def take_agents(d: dict, idx) -> dict:
     """Select a subset of agents (rows) from a model or inputs dict."""
     idx = np.asarray(idx)
     return {k: np.ascontiguousarray(v[idx]) for k, v in d.items()}
+
+
+# ---------------------------------------------------------------- residual policy
+POLICY_OBS, POLICY_HIDDEN, POLICY_ACT = 54, 256, 10
+
+
+def make_policy(seed: int = 2510_12717 + 100) -> dict:
+    """Random weights of the residual MLP 54 -> 256 -> 256 -> 256 -> 10 (the
+    trained weights are not available): W_l ~ N(0, 1/fan_in) stored [in][out],
+    b_l ~ N(0, 0.01), FP32.  Random draws only."""
+    g = np.random.Generator(np.random.Philox(key=splitmix64(seed)))
+    dims = [POLICY_OBS, POLICY_HIDDEN, POLICY_HIDDEN, POLICY_HIDDEN, POLICY_ACT]
+    out = {}
+    for layer in range(4):
+        fan_in, fan_out = dims[layer], dims[layer + 1]
+        out[f"W{layer + 1}"] = (g.standard_normal((fan_in, fan_out)) / np.sqrt(fan_in)).astype(np.float32)
+        out[f"b{layer + 1}"] = (0.01 * g.standard_normal(fan_out)).astype(np.float32)
+    return out
