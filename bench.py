@@ -40,6 +40,21 @@ UNIT = "agent-solves/s"
 WORKLOAD = "mixed16k"
 FP32_LANES = 128     # FP32 FMA lanes per SM (B300)
 N_SM = 148
+
+
+def _measured_bf16_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        for k in ("bf16_tflops", "bf16_dense_tflops"):
+            if k in d:
+                return float(d[k])
+    except Exception:
+        pass
+    return 1800.0   # fallback figure for one B300
+
+
+BF16_PEAK_TFLOPS = _measured_bf16_peak()
 # DRAM bytes per agent of the fused kernel from the last ncu capture of this
 # kernel version (profiles/mpc_k_fused_mixed16k_2048agents.md); None once the
 # kernel has changed since.
@@ -64,6 +79,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=0, help="factor precision: 0 FP32, 1 TF32, 2 BF16, 3 FP64")
     ap.add_argument("--refine", type=int, default=-1, help="refinement steps per polish (-1: library default)")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-precision speed/accuracy report")
+    ap.add_argument("--no-policy", action="store_true", help="skip the residual-policy measurement")
     ap.add_argument("--precision-agents", type=int, default=48, help="agents per workload sample, precision report")
     ap.add_argument("--serve-seconds", type=float, default=0.5, help="serving run length (0 = skip)")
     ap.add_argument("--serve-rate", default="0.5,1,2",
@@ -172,7 +188,7 @@ def run_ours(args):
     # replan 0: autotune (cold); 1..W: warm-up; W+1..W+K: timed; then the
     # end-to-end run's 2 warm-up and K timed replans
     W, K = args.warmup, args.steps
-    ids, model, replans = make_workload(args.workload, args.agents, rank, world, 1 + W + K + 2 + K)
+    ids, model, replans = make_workload(args.workload, args.agents, rank, world, 1 + W + K + 2 + K + K)
     n = len(ids)
     stream = torch.cuda.Stream(dev)          # non-default stream: graph capture needs one
     torch.cuda.set_stream(stream)
@@ -285,6 +301,39 @@ def run_ours(args):
            "h2d_bytes_per_step": int(n * (4 + 4 * (30 + 18 + 4 + 1))),
            "d2h_bytes_per_step": int(n * (4 * (18 * 3 + 1) + 4)),
            "ms_per_step": 1e3 * e2e_s / args.steps, "per_step_ms": e2e_per}
+    # residual policy + blend (paper Sec. IV) after each replan: the policy
+    # kernel timed with events on the stream, over the next K replans
+    policy = None
+    if not args.no_policy:
+        from workload import make_policy
+        s.set_policy(make_policy(), 0.1)
+        tau_b = torch.empty((n, 18), device=dev)
+        act_b = torch.empty((n, 10), device=dev)
+        p0 = 1 + W + K + 2 + K
+        pev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        sev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        barrier()
+        for i in range(K):
+            x = d_in[p0 + i]
+            tk = s.submit(d_ids, x["x0"], x["qd_meas"], x["cmd"], x["phase"])
+            sev[i][0].record(stream)
+            s.solve(tk)
+            sev[i][1].record(stream)
+            pev[i][0].record(stream)
+            s.policy_torques(tk, tau=tau_b, action=act_b)
+            pev[i][1].record(stream)
+            s.get_torques(tk, **out)
+        barrier()
+        pol_ms = float(np.mean([a.elapsed_time(b) for a, b in pev]))
+        step_ms = float(np.mean([a.elapsed_time(b) for a, b in sev]))
+        macs = 54 * 256 + 2 * 256 * 256 + 256 * 10
+        pflops = 2.0 * macs * n
+        policy = {"kernel_ms": pol_ms, "solve_ms_same_replans": step_ms,
+                  "tflops": pflops / (pol_ms / 1e3) / 1e12, "flops_per_launch": pflops,
+                  "peak_bf16_tflops": BF16_PEAK_TFLOPS,
+                  "frac_of_bf16_peak": pflops / (pol_ms / 1e3) / 1e12 / BF16_PEAK_TFLOPS,
+                  "note": "MLP 54-256-256-256-10 (ELU) on mma.sync bf16 tensor cores + joint-torque blend "
+                          "(lambda 0.1), random weights; peak = measured cuBLAS bf16 burst"}
     s.close()
 
     # a cold solve (fresh state, no warm start): the tuned configuration, the
@@ -359,6 +408,7 @@ def run_ours(args):
         "plain": plain,
         "paper_mode_fixed25": paper_mode,
         "precision": precision,
+        "residual_policy": policy,
         "serving": serving,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,

@@ -269,6 +269,33 @@ mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_host, const
 /* JSON summary of the context (sizes, arenas, counters) into buf. */
 mpc_status mpc_get_stats(mpc_ctx* ctx, char* buf, size_t cap);
 
+/* Residual policy and joint-torque blending after the MPC (paper Sec. IV,
+ * "Residual Architecture" and "Blending Strategy", Eq. (joint-torque)).
+ * mpc_set_policy uploads the MLP 54 -> 256 -> 256 -> 256 -> 10 (ELU hidden
+ * layers): host FP32 weights W_l stored [in][out] row-major (W1 54 x 256,
+ * W2 and W3 256 x 256, W4 256 x 10) and biases b_l; the device keeps the
+ * weights in bfloat16 (round to nearest even) and the biases in FP32.
+ * blend_lambda is the blending factor lambda (0.1 in the paper).  May be
+ * called again to replace the weights.  Errors: MPC_ERR_INVALID for a NULL
+ * pointer or a non-finite lambda. */
+mpc_status mpc_set_policy(mpc_ctx* ctx, const float* W1, const float* b1, const float* W2,
+                          const float* b2, const float* W3, const float* b3, const float* W4,
+                          const float* b4, float blend_lambda);
+
+/* Evaluate the policy for a solved ticket and blend its actions into the MPC
+ * torques; call between mpc_solve and mpc_get_torques (which releases the
+ * ticket).  Per agent (batch row order): the observation
+ * o = [p, theta, q_j, omega, v, qdot_j, phi, V_MPC] in R^54, with qdot_j the
+ * measured joint velocity and phi = (phase, sin and cos of 2 pi (phase +
+ * offset_i) for both feet); the actions a in R^10 (leg joints 0-9); the
+ * torques tau = tau_MPC + lambda (K_p (a + q_nom - q) - K_d qdot) on the legs
+ * and tau_MPC on the arms.  Each layer runs on the tensor cores with
+ * bfloat16 inputs and FP32 accumulation.  Outputs (device, either may be
+ * NULL): tau [n][18], action [n][10].  Enqueued on the ticket's stream.
+ * Errors: MPC_ERR_STATE if no policy is set, MPC_ERR_NOT_READY for an
+ * unknown or unsolved ticket. */
+mpc_status mpc_policy_torques(mpc_ctx* ctx, uint64_t ticket, float* tau_dev, float* action_dev);
+
 /* One-line description of the last error on this context (never NULL). */
 const char* mpc_last_error(mpc_ctx* ctx);
 

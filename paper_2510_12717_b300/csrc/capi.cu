@@ -10,6 +10,7 @@
 
 #include "mpcgpu.h"
 #include "solver.h"
+#include "policy.h"
 
 using mpc::Arena;
 
@@ -73,6 +74,9 @@ struct mpc_ctx {
   long long launches = 0;
   long long solves = 0;
   long long graph_replays = 0;
+  // residual policy (mpc_set_policy): bfloat16 weights, FP32 biases
+  mpc::PolicyDev pol{};
+  bool has_policy = false;
   std::string err = "ok";
 };
 
@@ -731,3 +735,74 @@ const char* mpc_last_error(mpc_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------ residual policy
+// round to the nearest bfloat16, ties to even (the bit pattern of a float32)
+static uint16_t bf16_bits(float f) {
+  uint32_t u;
+  memcpy(&u, &f, 4);
+  if ((u & 0x7F800000u) == 0x7F800000u) return (uint16_t)(u >> 16);   // inf / nan pass through
+  u += 0x7FFFu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+// W [in][out] (host, FP32) -> [out_pad][in_pad] bfloat16, zero padding
+static std::vector<uint16_t> transpose_bf16(const float* W, int in, int out, int in_pad, int out_pad) {
+  std::vector<uint16_t> t((size_t)in_pad * out_pad, 0);
+  for (int i = 0; i < in; ++i)
+    for (int o = 0; o < out; ++o) t[(size_t)o * in_pad + i] = bf16_bits(W[(size_t)i * out + o]);
+  return t;
+}
+
+mpc_status mpc_set_policy(mpc_ctx* ctx, const float* W1, const float* b1, const float* W2, const float* b2,
+                          const float* W3, const float* b3, const float* W4, const float* b4, float blend_lambda) {
+  using namespace mpc;
+  if (!ctx) return MPC_ERR_INVALID;
+  if (!W1 || !b1 || !W2 || !b2 || !W3 || !b3 || !W4 || !b4) return fail(ctx, MPC_ERR_INVALID, "set_policy: NULL");
+  if (!isfinite(blend_lambda)) return fail(ctx, MPC_ERR_INVALID, "set_policy: lambda not finite");
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const std::vector<uint16_t> w[4] = {transpose_bf16(W1, POL_OBS, POL_HID, POL_K1, POL_HID),
+                                      transpose_bf16(W2, POL_HID, POL_HID, POL_HID, POL_HID),
+                                      transpose_bf16(W3, POL_HID, POL_HID, POL_HID, POL_HID),
+                                      transpose_bf16(W4, POL_HID, POL_ACT, POL_HID, POL_N4)};
+  std::vector<float> b4p(POL_N4, 0.f);
+  for (int i = 0; i < POL_ACT; ++i) b4p[i] = b4[i];
+  const float* b[4] = {b1, b2, b3, b4p.data()};
+  const int bn[4] = {POL_HID, POL_HID, POL_HID, POL_N4};
+  if (!ctx->has_policy) {
+    void* p = nullptr;
+    size_t total = 0;
+    for (int l = 0; l < 4; ++l) total += w[l].size() * 2 + (size_t)bn[l] * 4;
+    CK(cudaMalloc(&p, total));
+    ctx->allocs.push_back(p);
+    ctx->bytes += total;
+    uint8_t* q = static_cast<uint8_t*>(p);
+    const __nv_bfloat16** W[4] = {&ctx->pol.W1, &ctx->pol.W2, &ctx->pol.W3, &ctx->pol.W4};
+    const float** B[4] = {&ctx->pol.b1, &ctx->pol.b2, &ctx->pol.b3, &ctx->pol.b4};
+    for (int l = 0; l < 4; ++l) { *W[l] = reinterpret_cast<const __nv_bfloat16*>(q); q += w[l].size() * 2; }
+    for (int l = 0; l < 4; ++l) { *B[l] = reinterpret_cast<const float*>(q); q += (size_t)bn[l] * 4; }
+  }
+  const void* Wd[4] = {ctx->pol.W1, ctx->pol.W2, ctx->pol.W3, ctx->pol.W4};
+  const void* Bd[4] = {ctx->pol.b1, ctx->pol.b2, ctx->pol.b3, ctx->pol.b4};
+  for (int l = 0; l < 4; ++l) {
+    CK(cudaMemcpy(const_cast<void*>(Wd[l]), w[l].data(), w[l].size() * 2, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(const_cast<void*>(Bd[l]), b[l], (size_t)bn[l] * 4, cudaMemcpyHostToDevice));
+  }
+  ctx->pol.lambda = blend_lambda;
+  ctx->has_policy = true;
+  return MPC_OK;
+}
+
+mpc_status mpc_policy_torques(mpc_ctx* ctx, uint64_t ticket, float* tau, float* action) {
+  if (!ctx) return MPC_ERR_INVALID;
+  if (!ctx->has_policy) return fail(ctx, MPC_ERR_STATE, "policy_torques: no policy set");
+  Ticket* tk = find_ticket(ctx, ticket);
+  if (!tk) return fail(ctx, MPC_ERR_NOT_READY, "policy_torques: unknown ticket");
+  if (tk->state != 2) return fail(ctx, MPC_ERR_NOT_READY, "policy_torques: ticket not solved");
+  CK(cudaSetDevice(ctx->cfg.device));
+  cudaError_t e = mpc::launch_policy(ctx->ar, tk->b.n, tk->b.ids, ctx->pol, tau, action, tk->stream);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "policy_torques");
+  ctx->launches += 1;
+  return MPC_OK;
+}

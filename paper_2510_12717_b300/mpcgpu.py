@@ -80,6 +80,8 @@ SIGNATURES = {
     "mpc_solve_static": (C.c_int, [C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "mpc_get_stats": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
     "mpc_last_error": (C.c_char_p, [_P]),
+    "mpc_set_policy": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_float]),
+    "mpc_policy_torques": (C.c_int, [_P, C.c_uint64, _P, _P]),
 }
 
 _lib = None
@@ -219,6 +221,21 @@ class Solver:
     def get_torques(self, ticket: int, tau=None, q_set=None, qd_set=None, value=None, status=None):
         self._check(self.lib.mpc_get_torques(self.ctx, C.c_uint64(ticket), _ptr(tau), _ptr(q_set),
                                              _ptr(qd_set), _ptr(value), _ptr(status)))
+
+    # -- residual policy (paper Sec. IV) blended into the MPC torques
+    def set_policy(self, weights: dict, blend_lambda: float = 0.1):
+        """weights: W1..W4 ([in][out]) and b1..b4 as FP32 arrays
+        (workload.make_policy layout)."""
+        arrs = []
+        for l in (1, 2, 3, 4):
+            arrs.append(np.ascontiguousarray(weights[f"W{l}"], np.float32))
+            arrs.append(np.ascontiguousarray(weights[f"b{l}"], np.float32))
+        self._keep_policy = arrs
+        self._check(self.lib.mpc_set_policy(self.ctx, *[_ptr(a) for a in arrs], C.c_float(blend_lambda)))
+
+    def policy_torques(self, ticket: int, tau=None, action=None):
+        """Enqueue the policy for a solved ticket (before get_torques)."""
+        self._check(self.lib.mpc_policy_torques(self.ctx, C.c_uint64(ticket), _ptr(tau), _ptr(action)))
 
     # -- host-buffer path (numpy in, numpy out)
     def solve_host(self, ids, x0, qd_meas, cmd, phase, *, tau=None, q_set=None, qd_set=None,
