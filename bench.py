@@ -94,13 +94,32 @@ def dist_env():
     return rank, world, local
 
 
+def shard_ids(n, rank, world):
+    """Weak scaling: rank r owns agents [r n, (r + 1) n); every agent's QP is
+    independent, so there is no exchange on the data path."""
+    return np.arange(rank * n, (rank + 1) * n)
+
+
+def job_throughput(n, steps, local_ms, world, device=None):
+    """(whole-job agent-solves/s, job ms) from this rank's timed region: the
+    job takes as long as its slowest rank (max over ranks)."""
+    total_ms = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return world * n * steps / (total_ms / 1e3), total_ms
+
+
 # ------------------------------------------------------------------ inputs
 def make_workload(name, n_agents, rank, world, n_replans):
     """Agents of this rank and `n_replans` consecutive replans of them."""
     from workload import make_agents, perturb_inputs, workload_spec
     spec = workload_spec(name)
     n = n_agents or spec["n_agents"]
-    ids = np.arange(rank * n, (rank + 1) * n)      # weak scaling: each rank its own agents
+    ids = shard_ids(n, rank, world)
     model, inp = make_agents(name, ids)
     replans = [inp]
     for r in range(1, n_replans):
@@ -261,13 +280,8 @@ def run_ours(args):
         return s, total_ms, per, launches, st, status, clk.summary()
 
     s, total_ms, per, launches, st, status, clocks = timed(mpcgpu.FORM_FUSED, args.steps, args.warmup)
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    value, total_ms = job_throughput(n, args.steps, total_ms, world, dev)
     ms_step = total_ms / args.steps
-    value = world * n * args.steps / (total_ms / 1e3)
 
     # roofline of the dominant kernel (the fused solve kernel, one launch per step)
     fl = flops_per_agent(Nh, st["iters"], st["refactors"], st["polished"]).sum()
