@@ -861,11 +861,13 @@ __device__ __forceinline__ Elim lane_elim(const AgentPtrs& ap, int k, const int*
 // R_hat = G^T D G plus 1 on eliminated inputs, c_hat = c + B t (into cvec),
 // r_hat = G^T D (t - u_ref) (per lane), Q_t of x_k with the moved cost of an
 // eliminated joint rate, A_hat (identity entry of an eliminated joint).
-__device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const int* act, float* cvec,
-                                   const Elim& el, int lane) {
+// uref: this lane's u_ref,k; c_k: this lane's c_k (lanes < 22)
+__device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, float* cvec, const Elim& el, int lane,
+                                   const LanePat& pat, float uref, float c_k) {
   const float* md = ap.mdl;
   const float dt = md[M_DT];
-  const float* bbase = ap.lin + L_BV;
+  const float* Bd = sm + S_B;        // dense B (column-major, LDD): compact entry t of column j is
+                                     // B(brow(j, t), j); the three force columns of a foot share rows
   float* vec = sm + S_VEC;
   float* gfv = vec + V_T * 64;       // rows of G_f, 3 per force input (indexed 3*i)
   float* gv = vec + V_G * 64;        // g per input
@@ -875,7 +877,7 @@ __device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const 
   if (lane < 30) {
     gv[lane] = el.g;
     tv[lane] = el.t;
-    vD2[lane] = Dj * (el.t - ap.uref[k * VS + lane]);
+    vD2[lane] = Dj * (el.t - uref);
     if (lane < 12) { gfv[lane * 3] = el.gf[0]; gfv[lane * 3 + 1] = el.gf[1]; gfv[lane * 3 + 2] = el.gf[2]; }
   } else {
     tv[lane] = 0.f;
@@ -898,11 +900,13 @@ __device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const 
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
       float v;
+      // padding entries (t >= bcnt) read row 0 of B, which is zero (p has no input)
+      const int rb = pat.br[t];
       if (fj)
-        v = bbase[(b + 0) * 6 + t] * gfv[(b + 0) * 3 + c] + bbase[(b + 1) * 6 + t] * gfv[(b + 1) * 3 + c] +
-            bbase[(b + 2) * 6 + t] * gfv[(b + 2) * 3 + c];
+        v = Bd[(b + 0) * LDD + rb] * gfv[(b + 0) * 3 + c] + Bd[(b + 1) * LDD + rb] * gfv[(b + 1) * 3 + c] +
+            Bd[(b + 2) * LDD + rb] * gfv[(b + 2) * 3 + c];
       else
-        v = bbase[j * 6 + t] * gv[j];
+        v = Bd[j * LDD + rb] * gv[j];
       sm[S_BV + j * 6 + t] = v;
     }
     if (fj) {
@@ -920,7 +924,7 @@ __device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, int k, const 
       in.rt_diag = gv[j] * Dj * gv[j] + (1.f - gv[j]);
       in.rh = gv[j] * vD2[j];
     }
-    cvec[j] = ap.lin[L_STAGE + k * 64 + 32 + j] + cm_mv(sm + S_B, tv, lane);   // c_hat
+    cvec[j] = c_k + cm_mv(sm + S_B, tv, lane);   // c_hat
   } else if (lane < 30) {
     const float alive = el.g;
     in.rt_diag = alive * Dj + (1.f - alive);
@@ -1019,7 +1023,8 @@ __device__ __noinline__ void polish_refine(const AgentPtrs& ap, float* sm, int l
     set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
     const Elim el = lane_elim(ap, k, act, lane, mu, carry2);
     carry2 = el.carry_out;
-    const StageIn in = polish_stage_in(ap, sm, k, act, cvec, el, lane);
+    const StageIn in = polish_stage_in(ap, sm, cvec, el, lane, pat, ap.uref[k * VS + lane],
+                                       lane < NC ? ap.lin[L_STAGE + k * 64 + 32 + lane] : 0.f);
     const float v = ap.dv[k * VS + lane];
     vV[lane] = v;
     vS[lane] = lam;
@@ -1113,7 +1118,8 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
       reinterpret_cast<float4*>(ap.cEl + k * 128)[lane] =
           make_float4(fl ? el.gf[0] : el.g, el.gf[1], fl ? el.gf[2] : el.phi, el.t);
     }
-    const StageIn in = polish_stage_in(ap, sm, k, act, cvec, el, lane);
+    const StageIn in = polish_stage_in(ap, sm, cvec, el, lane, pat, ap.uref[k * VS + lane],
+                                       lane < NC ? ap.lin[L_STAGE + k * 64 + 32 + lane] : 0.f);
     const StageOut so = factor_stage(ap, sm, lane, k, in, &Pa, pat, prm.precision, nref > 0);
     // H (= H_uu^-1) and K of stage k are still in smem
     const float s = p + so.e;
