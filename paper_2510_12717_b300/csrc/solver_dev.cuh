@@ -310,6 +310,9 @@ static __device__ __noinline__ void r24_inv_f64(float* H, double* sc, int lane) 
 // as zero.  Fragment layouts (PTX ISA, mma.m16n8k8 .tf32 / m16n8k16 .bf16):
 // g = lane / 4, t = lane % 4;  C: (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1).
 enum : int { PREC_FP32 = 0, PREC_TF32 = 1, PREC_BF16 = 2, PREC_FP64 = 3 };
+// kernel specialisation: PREC_FP32 compiles the FP32 factor only; PREC_ANY
+// reads the precision at run time
+constexpr int PREC_ANY = -1;
 
 __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;

@@ -324,9 +324,11 @@ struct StageIn {
 // P_{k+1} c), and for arm lanes the scalar gain and inverse
 struct StageOut { float e, Ka, Hi; };
 
+template <int PREC>
 __device__ __forceinline__ StageOut factor_stage(const AgentPtrs& ap, float* sm, int lane, int k,
-                                                 const StageIn& in, float* Pa, const LanePat& pat, int prec,
+                                                 const StageIn& in, float* Pa, const LanePat& pat, int prec_rt,
                                                  bool store_h = true) {
+  const int prec = PREC >= 0 ? PREC : prec_rt;
   StageOut so;
   so.e = so.Ka = so.Hi = 0.f;
   float* P = sm + S_P; float* H = sm + S_H; float* X = sm + S_X; float* K = sm + S_K;
@@ -487,6 +489,7 @@ __device__ __forceinline__ StageIn admm_stage_in(const AgentPtrs& ap, int k, flo
   return in;
 }
 
+template <int PREC>
 __device__ __noinline__ void factor_admm(const AgentPtrs& ap, float* sm, int lane, float rho, float sigma,
                                         const LanePat& pat, int prec) {
   const int N = ap.N;
@@ -503,7 +506,7 @@ __device__ __noinline__ void factor_admm(const AgentPtrs& ap, float* sm, int lan
   for (int k = N - 1; k >= 0; --k) {
     set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
     const StageIn in = admm_stage_in(ap, k, rho, sigma, cvec, lane);
-    factor_stage(ap, sm, lane, k, in, &Pa, pat, prec);
+    factor_stage<PREC>(ap, sm, lane, k, in, &Pa, pat, prec);
   }
   // the caches were written with generic stores and are read back through
   // the async (TMA) proxy
@@ -1082,6 +1085,7 @@ __device__ __noinline__ void polish_refine(const AgentPtrs& ap, float* sm, int l
 // is solved once), then roll forward with u = G v + t + Phi x through the
 // original dynamics.  The polished primal goes to xt/ut.  Overwrites the
 // Riccati caches (the caller refactors if ADMM continues).
+template <int PREC>
 __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat, Pipe& pp,
                                           const SolverParams& prm, int nref) {
   const int N = ap.N;
@@ -1120,7 +1124,7 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
     }
     const StageIn in = polish_stage_in(ap, sm, cvec, el, lane, pat, ap.uref[k * VS + lane],
                                        lane < NC ? ap.lin[L_STAGE + k * 64 + 32 + lane] : 0.f);
-    const StageOut so = factor_stage(ap, sm, lane, k, in, &Pa, pat, prm.precision, nref > 0);
+    const StageOut so = factor_stage<PREC>(ap, sm, lane, k, in, &Pa, pat, prm.precision, nref > 0);
     // H (= H_uu^-1) and K of stage k are still in smem
     const float s = p + so.e;
     vS[lane] = s;
@@ -1384,6 +1388,7 @@ __device__ void init_active_prev(const AgentPtrs& ap, int lane) {
   __syncwarp();
 }
 
+template <int PREC>
 __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Res* res,
                        const LanePat& pat, Pipe& pp, bool from_prev = false) {
   if (from_prev) init_active_prev(ap, lane);
@@ -1392,7 +1397,7 @@ __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, co
   // alternative is an ADMM solve
   const int attempts = from_prev ? 8 : 4;
   for (int attempt = 0; attempt < attempts; ++attempt) {
-    if (!polish_solve(ap, sm, lane, pat, pp, prm, from_prev ? prm.refine : prm.refine_admm)) return false;
+    if (!polish_solve<PREC>(ap, sm, lane, pat, pp, prm, from_prev ? prm.refine : prm.refine_admm)) return false;
     const Res pr = polish_check<false>(ap, sm, lane, prm, nullptr, pat);
     const float tol_p = prm.eps_abs + prm.eps_rel * pr.ps;
     const float tol_d = prm.eps_abs + prm.eps_rel * pr.ds;
@@ -1526,6 +1531,7 @@ __device__ __noinline__ void polish_warm_start(const AgentPtrs& ap, float* sm, i
 // are within early_polish x the tolerance.  Returns the agent status.
 struct Outcome { int status, iters, refac, polished; Res r; };
 
+template <int PREC>
 __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, bool factored,
                               Pipe& pp, const LanePat& pat) {
   float rho = *ap.rho;
@@ -1538,7 +1544,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
   if (lane == 0) ap.st[T_FIRST] = 0;
   if (prm.polish && prm.warm_polish && ap.st[T_WARM] && prm.fixed_iters == 0) {
     Res pr;
-    if (polish(ap, sm, lane, prm, &pr, pat, pp, true)) {
+    if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, true)) {
       o.polished = 1;
       o.status = MPC_AGENT_SOLVED_;
       o.r = pr;
@@ -1548,7 +1554,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
     factored = false;   // the polish overwrote the caches
     polish_warm_start(ap, sm, lane, pat);
   }
-  if (!factored) factor_admm(ap, sm, lane, rho, prm.sigma, pat, prm.precision);
+  if (!factored) factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, prm.precision);
   const bool fixed = prm.fixed_iters > 0;
   const int max_it = fixed ? prm.fixed_iters : prm.max_iter;
   // polish attempts: the first once both residuals are within early_polish x
@@ -1581,13 +1587,13 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
       ++polish_tries;
       next_polish_it = it + (polish_every << (polish_tries >> 1));
       Res pr;
-      if (polish(ap, sm, lane, prm, &pr, pat, pp)) {
+      if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp)) {
         o.polished = 1;
         o.status = MPC_AGENT_SOLVED_;
         o.r = pr;
         break;
       }
-      factor_admm(ap, sm, lane, rho, prm.sigma, pat, prm.precision);   // the polish overwrote the caches
+      factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, prm.precision);   // the polish overwrote the caches
       ++o.refac;
     }
     if (prm.adaptive_rho && it < max_it) {
@@ -1597,7 +1603,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
       rn = fminf(fmaxf(rn, 1e-6f), 1e6f);
       if (rn > 5.f * rho || rn < 0.2f * rho) {
         rho = rn;
-        factor_admm(ap, sm, lane, rho, prm.sigma, pat, prm.precision);
+        factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, prm.precision);
         ++o.refac;
       }
     }
@@ -1683,11 +1689,12 @@ __device__ void write_outcome(const AgentPtrs& ap, int lane, const Outcome& o) {
 }
 
 // final polish when ADMM ended without an accepted one
+template <int PREC>
 __device__ void final_polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Outcome& o,
                              const LanePat& pat, Pipe& pp) {
   if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) return;
   Res pr;
-  if (polish(ap, sm, lane, prm, &pr, pat, pp)) {
+  if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp)) {
     o.polished = 1;
     o.status = MPC_AGENT_SOLVED_;
     o.r = pr;
@@ -1704,7 +1711,7 @@ __device__ __forceinline__ bool valid_slot(const Arena& a, const Batch& b, int r
 }
 __device__ __forceinline__ float* warp_smem() { return g_smem + (threadIdx.x >> 5) * W_FLOATS; }
 
-template <int MINB>
+template <int MINB, int PREC>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_fused(Arena a, Batch b, SolverParams prm) {
   // persistent: each warp takes the next batch row from the work queue
   // (longest expected solve first) until the queue is empty
@@ -1731,8 +1738,8 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_fused(Arena 
     const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
     load_inputs(b, row, ap, lane);
     if (!setup_agent(ap, sm, lane, prm)) { mark_status_only(ap, lane, MPC_AGENT_NAN_); continue; }
-    Outcome o = admm_solve(ap, sm, lane, prm, false, pp, pat);
-    final_polish(ap, sm, lane, prm, o, pat, pp);
+    Outcome o = admm_solve<PREC>(ap, sm, lane, prm, false, pp, pat);
+    final_polish<PREC>(ap, sm, lane, prm, o, pat, pp);
     write_outcome(ap, lane, o);
     torque_map(ap, lane);
     __syncwarp();
@@ -1751,7 +1758,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_setup(Arena 
   else if (lane == 0) ap.st[T_STATUS] = MPC_AGENT_MAX_ITER_;
 }
 
-template <int MINB>
+template <int MINB, int PREC>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_factor(Arena a, Batch b, SolverParams prm) {
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
@@ -1760,10 +1767,10 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_factor(Arena
   const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
   if (ap.st[T_STATUS] == MPC_AGENT_NAN_) return;
   load_lin(ap, sm, lane);
-  factor_admm(ap, sm, lane, *ap.rho, prm.sigma, lane_pattern(lane), prm.precision);
+  factor_admm<PREC>(ap, sm, lane, *ap.rho, prm.sigma, lane_pattern(lane), prm.precision);
 }
 
-template <int MINB>
+template <int MINB, int PREC>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_admm(Arena a, Batch b, SolverParams prm) {
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
@@ -1775,11 +1782,11 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_admm(Arena a
   const LanePat pat = lane_pattern(lane);
   Pipe pp;
   pipe_init(pp, sm, lane);
-  const Outcome o = admm_solve(ap, sm, lane, prm, true, pp, pat);
+  const Outcome o = admm_solve<PREC>(ap, sm, lane, prm, true, pp, pat);
   write_outcome(ap, lane, o);
 }
 
-template <int MINB>
+template <int MINB, int PREC>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_polish(Arena a, Batch b, SolverParams prm) {
   const int lane = threadIdx.x & 31;
   const int row = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
@@ -1801,7 +1808,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_polish(Arena
   copy_n(sm + S_BV, ap.lin + L_BV, 136 / 4, lane);
   Pipe pp;
   pipe_init(pp, sm, lane);
-  final_polish(ap, sm, lane, prm, o, lane_pattern(lane), pp);
+  final_polish<PREC>(ap, sm, lane, prm, o, lane_pattern(lane), pp);
   if (o.polished) write_outcome(ap, lane, o);
 }
 
@@ -1818,13 +1825,12 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) mpc_k_torque(Arena a, Ba
 }  // namespace
 
 // ============================================================ variant launcher
-// Kernel variants: the minimum resident blocks per SM given to the compiler
-// (register cap).  One translation unit instantiates one variant.
-template <int MINB>
+// One translation unit instantiates one register-cap variant.
+template <int MINB, int PREC>
 cudaError_t configure_smem() {
   const int bytes = (int)smem_bytes_per_block();
-  void (*ks[])(Arena, Batch, SolverParams) = {mpc_k_fused<MINB>, mpc_k_setup<MINB>, mpc_k_factor<MINB>,
-                                              mpc_k_admm<MINB>, mpc_k_polish<MINB>};
+  void (*ks[])(Arena, Batch, SolverParams) = {mpc_k_fused<MINB, PREC>, mpc_k_setup<MINB>, mpc_k_factor<MINB, PREC>,
+                                              mpc_k_admm<MINB, PREC>, mpc_k_polish<MINB, PREC>};
   for (auto k : ks) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e != cudaSuccess) return e;
@@ -1832,9 +1838,9 @@ cudaError_t configure_smem() {
   return cudaSuccess;
 }
 
-template <int MINB>
-cudaError_t launch_variant(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
-                           cudaStream_t st, int* launches) {
+template <int MINB, int PREC>
+cudaError_t launch_prec(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
+                        cudaStream_t st, int* launches) {
   // one-time set-up per device (also done before any stream capture by a
   // call with n = 0): smem opt-in and the resident grid of the persistent kernel
   static int configured = -1, resident = 0;
@@ -1842,11 +1848,11 @@ cudaError_t launch_variant(const Arena& a, const Batch& b, const SolverParams& p
   cudaGetDevice(&dev);
   const size_t smem = smem_bytes_per_block();
   if (configured != dev) {
-    cudaError_t e = configure_smem<MINB>();
+    cudaError_t e = configure_smem<MINB, PREC>();
     if (e != cudaSuccess) return e;
     int nsm = 0, per_sm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mpc_k_fused<MINB>, WARPS_PER_BLOCK * 32, smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mpc_k_fused<MINB, PREC>, WARPS_PER_BLOCK * 32, smem);
     resident = nsm * (per_sm > 0 ? per_sm : 1);
     configured = dev;
   }
@@ -1858,17 +1864,27 @@ cudaError_t launch_variant(const Arena& a, const Batch& b, const SolverParams& p
     int g = b.counter ? resident : blocks;
     if (grid_fused > 0 && grid_fused < g) g = grid_fused;
     if (g > blocks) g = blocks;
-    mpc_k_fused<MINB><<<g, thr, smem, st>>>(a, b, prm);
+    mpc_k_fused<MINB, PREC><<<g, thr, smem, st>>>(a, b, prm);
     if (launches) *launches += 1;
   } else {
     mpc_k_setup<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
-    mpc_k_factor<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
-    mpc_k_admm<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
-    mpc_k_polish<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
+    mpc_k_factor<MINB, PREC><<<blocks, thr, smem, st>>>(a, b, prm);
+    mpc_k_admm<MINB, PREC><<<blocks, thr, smem, st>>>(a, b, prm);
+    mpc_k_polish<MINB, PREC><<<blocks, thr, smem, st>>>(a, b, prm);
     mpc_k_torque<<<blocks, thr, 0, st>>>(a, b);
     if (launches) *launches += 5;
   }
   return cudaGetLastError();
+}
+
+// Kernel variants: the minimum resident blocks per SM given to the compiler
+// (register cap), each in two builds: the FP32 factor only, or the factor
+// precision read at run time (TF32 / BF16 / FP64 paths).
+template <int MINB>
+cudaError_t launch_variant(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
+                           cudaStream_t st, int* launches) {
+  if (prm.precision == PREC_FP32) return launch_prec<MINB, PREC_FP32>(a, b, prm, form, grid_fused, st, launches);
+  return launch_prec<MINB, PREC_ANY>(a, b, prm, form, grid_fused, st, launches);
 }
 
 }  // namespace mpc
