@@ -109,9 +109,10 @@ typedef struct mpc_config {
                                  first time a batch (buffers, ticket slot, stream)
                                  is solved and replayed afterwards (only on a
                                  non-default stream; direct launches otherwise) */
-  int warm_polish;            /* 1: on a warm start, first polish from the previous
-                                 replan's final active set; ADMM runs only if that
-                                 fails its KKT check */
+  int warm_polish;            /* 1: polish first, from the previous replan's final
+                                 active set (warm start) or from the equality rows
+                                 alone (cold agent); ADMM runs only if that fails
+                                 its KKT check */
   int refine_steps;           /* iterative-refinement steps on each polish solve
                                  (0..4); -1 = automatic: 1 on a polish after ADMM
                                  iterations, and on the warm-start polish 1 for
@@ -216,7 +217,7 @@ mpc_status mpc_solve_host(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host
 
 /* Per-agent solver statistics of the last solve of each agent, copied to
  * host arrays (any may be NULL): ADMM iterations, refactorisations, polish
- * accepted (0 no, 1 after ADMM, 2 from the warm active set without ADMM),
+ * accepted (0 no, 1 after ADMM, 2 by the polish first, without ADMM),
  * final unscaled primal and dual residuals (inf-norms), and the scaled
  * residuals: the largest primal row violation / stationarity component over
  * its own tolerance eps_abs + eps_rel * (magnitude of that row's or

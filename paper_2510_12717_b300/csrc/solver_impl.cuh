@@ -1366,8 +1366,8 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
   return out;
 }
 
-// Polish with active-set correction: up to four attempts (eight from the
-// previous replan's active set); true when one passes its check, with the polished point copied into (x, u).
+// Polish with active-set correction: up to four attempts (eight before any
+// ADMM iteration); true when one passes its check, with the polished point copied into (x, u).
 // Initial guess from the agent's previous final active set (kept per slot):
 // rows that became equalities (a foot switched to swing) are active, rows
 // that stopped being equalities start inactive, the rest keep their code.
@@ -1388,16 +1388,30 @@ __device__ void init_active_prev(const AgentPtrs& ap, int lane) {
   __syncwarp();
 }
 
+// A cold agent's first guess: only the equality rows (swing-foot wrenches).
+__device__ void init_active_min(const AgentPtrs& ap, int lane) {
+  for (int k = 0; k < ap.N; ++k)
+    for (int r = lane; r < NR; r += 32)
+      ap.act[k * RS + r] = ap.rlo[k * RS + r] == ap.rhi[k * RS + r] ? 3 : 0;
+  __syncwarp();
+}
+
+// guess: POLISH_ADMM from ADMM's (w, y); POLISH_PREV the previous replan's
+// final active set; POLISH_MIN the equality rows alone (cold agent)
+enum : int { POLISH_ADMM = 0, POLISH_PREV = 1, POLISH_MIN = 2 };
+
 template <int PREC>
 __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Res* res,
-                       const LanePat& pat, Pipe& pp, bool from_prev = false) {
-  if (from_prev) init_active_prev(ap, lane);
+                       const LanePat& pat, Pipe& pp, int guess = POLISH_ADMM) {
+  if (guess == POLISH_PREV) init_active_prev(ap, lane);
+  else if (guess == POLISH_MIN) init_active_min(ap, lane);
   else init_active(ap, lane);
-  // from the previous replan's active set more corrections pay: the
-  // alternative is an ADMM solve
-  const int attempts = from_prev ? 8 : 4;
+  // before any ADMM iteration more corrections pay: the alternative is an
+  // ADMM solve
+  const int attempts = guess == POLISH_ADMM ? 4 : 8;
+  const int nref = guess == POLISH_PREV ? prm.refine : prm.refine_admm;
   for (int attempt = 0; attempt < attempts; ++attempt) {
-    if (!polish_solve<PREC>(ap, sm, lane, pat, pp, prm, from_prev ? prm.refine : prm.refine_admm)) return false;
+    if (!polish_solve<PREC>(ap, sm, lane, pat, pp, prm, nref)) return false;
     const Res pr = polish_check<false>(ap, sm, lane, prm, nullptr, pat);
     const float tol_p = prm.eps_abs + prm.eps_rel * pr.ps;
     const float tol_d = prm.eps_abs + prm.eps_rel * pr.ds;
@@ -1538,13 +1552,14 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
   Outcome o;
   o.status = MPC_AGENT_MAX_ITER_; o.iters = 0; o.refac = 0; o.polished = 0;
   o.r.rp = o.r.rd = o.r.ps = o.r.ds = o.r.pn = o.r.dn = 0.f;
-  // warm start: the previous replan's final active set is usually still
-  // right; a polish from it that passes the KKT check is the optimum, with no
-  // ADMM factorisation and no iteration
+  // polish first: a warm start's previous final active set is usually still
+  // right, and a cold agent's optimum has few active rows; a polish from that
+  // guess (with its corrections) that passes the KKT check is the optimum,
+  // with no ADMM factorisation and no iteration
   if (lane == 0) ap.st[T_FIRST] = 0;
-  if (prm.polish && prm.warm_polish && ap.st[T_WARM] && prm.fixed_iters == 0) {
+  if (prm.polish && prm.warm_polish && prm.fixed_iters == 0) {
     Res pr;
-    if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, true)) {
+    if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, ap.st[T_WARM] ? POLISH_PREV : POLISH_MIN)) {
       o.polished = 1;
       o.status = MPC_AGENT_SOLVED_;
       o.r = pr;
