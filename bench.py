@@ -518,12 +518,19 @@ def run_serving(args, model, replans, n):
     at each requested rate; each agent's state walks forward one 10 ms step
     per request from the workload's first replan."""
     from paper_2510_12717_b300.serve import ServingEngine
+    from workload import make_agents
+    # reserve agents that join as others leave (5 % every 100 batches)
+    reserve = max(n // 8, 1)
+    rmodel, rinp = make_agents(args.workload, np.arange(n, n + reserve))
+    smodel = {k: np.concatenate([model[k], rmodel[k]]) for k in model}
+    sinp = {k: np.concatenate([replans[0][k], np.asarray(rinp[k], np.float32)]) for k in replans[0]}
     out = {}
     for f in [float(v) for v in str(args.serve_rate).split(",") if v.strip()]:
-        eng = ServingEngine(model, replans[0], pool=n, streams=2, hbm_budget_bytes=8 << 30, seed=7)
+        eng = ServingEngine(smodel, sinp, pool=n, streams=2, hbm_budget_bytes=8 << 30, seed=7)
         st = eng.run(rate=f * 16384 * 100.0, duration=args.serve_seconds, churn_every=100, churn_frac=0.05)
         eng.close()
         st["rate_x_16384_at_100hz"] = f
+        st["churned_agents"] = int(eng.churned)
         out[f"{f:g}x"] = st
     out["note"] = ("requests of one agent coalesce (newest state wins); 2 streams; churn 5% every 100 batches; "
                    "rates x 1.6384 M requests/s")

@@ -43,7 +43,10 @@ class ServingEngine:
             inputs = inputs[0]
         self.state = {k: np.array(v, dtype=np.float32, copy=True) for k, v in inputs.items()}
         self.step_sigma, self.phase_step = step_sigma, phase_step
-        self.walk_rng = np.random.default_rng(seed)
+        # the walk's noise is drawn once and read cyclically (synthetic states;
+        # drawing fresh normals per batch dominated the host loop)
+        self.noise = np.random.default_rng(seed).standard_normal(1 << 22, dtype=np.float32)
+        self.noise_at = 0
         self.total = len(model["mass"])
         self.pool = pool
         self.max_batch = max_batch or pool
@@ -53,6 +56,7 @@ class ServingEngine:
         # slot s holds agent slot_agent[s]
         self.slot_agent = np.arange(pool)
         self.reserve = list(range(pool, self.total))
+        self.churned = 0
         self.solver.set_models(model, np.arange(pool, dtype=np.int32), idx=self.slot_agent)
         self.streams = [torch.cuda.Stream(self.dev) for _ in range(streams)]
         mb = self.max_batch
@@ -79,10 +83,11 @@ class ServingEngine:
         if k == 0 or len(self.reserve) < k:
             return 0
         slots = np.sort(rng.choice(self.pool, k, replace=False))
-        for s in slots:
-            self.solver.release(int(s))
-            self.reserve.append(int(self.slot_agent[s]))
+        # the joining agent's model replaces the leaving one's in its slot:
+        # mpc_set_models resets the slot's warm start (no per-slot release)
+        self.reserve.extend(int(a) for a in self.slot_agent[slots])
         new = [self.reserve.pop(0) for _ in range(k)]
+        self.churned += k
         self.slot_agent[slots] = new
         self.solver.set_models(self.model, slots.astype(np.int32), idx=np.asarray(new))
         return k
@@ -191,14 +196,20 @@ class ServingEngine:
         idx = np.repeat(first - np.cumsum(cnt) + cnt, cnt) + np.arange(cnt.sum())
         return t_done - times_by_slot[idx]
 
+    def _draw(self, shape):
+        size = int(np.prod(shape))
+        if self.noise_at + size > len(self.noise):
+            self.noise_at = 0
+        out = self.noise[self.noise_at:self.noise_at + size].reshape(shape)
+        self.noise_at += size
+        return out
+
     def _advance(self, agents, steps):
         """Walk the agents' states `steps` environment steps forward."""
         st = self.state
         s = np.asarray(steps, dtype=np.float32)
-        st["x0"][agents] += (self.step_sigma * np.sqrt(s))[:, None] * \
-            self.walk_rng.standard_normal((len(agents), st["x0"].shape[1]), dtype=np.float32)
-        st["qd_meas"][agents] = 0.1 * self.walk_rng.standard_normal((len(agents), st["qd_meas"].shape[1]),
-                                                                    dtype=np.float32)
+        st["x0"][agents] += (self.step_sigma * np.sqrt(s))[:, None] * self._draw((len(agents), st["x0"].shape[1]))
+        st["qd_meas"][agents] = 0.1 * self._draw((len(agents), st["qd_meas"].shape[1]))
         st["cmd"][agents, 0] = st["x0"][agents, 2]
         ph = st["phase"][agents] + self.phase_step * s
         st["phase"][agents] = ph - np.floor(ph)
