@@ -236,11 +236,18 @@ def run_ours(args):
             import torch.distributed as dist
             dist.barrier()
 
+    # the solver reads its inputs from persistent device buffers that each
+    # replan's state is copied into (as a control loop would), so the
+    # captured graph is replayed; the copy is part of the step
+    cur = {k: torch.empty_like(v) for k, v in d_in[0].items()}
+
     def step(s, i, ev=None):
-        x = d_in[i]
-        tk = s.submit(d_ids, x["x0"], x["qd_meas"], x["cmd"], x["phase"])
         if ev is not None:
             ev[0].record(stream)
+        for k, v in d_in[i].items():
+            cur[k].copy_(v, non_blocking=True)
+        x = cur
+        tk = s.submit(d_ids, x["x0"], x["qd_meas"], x["cmd"], x["phase"])
         s.solve(tk)
         if ev is not None:
             ev[1].record(stream)
@@ -275,11 +282,12 @@ def run_ours(args):
         total_ms = t0.elapsed_time(t1)
         per = [a.elapsed_time(b) for a, b in evs]
         launches = s.stats()["kernel_launches"] - l0
+        graph_replays = s.stats().get("graph_replays", 0)
         st = s.agent_stats(slots)
         status = out["status"].cpu().numpy()
-        return s, total_ms, per, launches, st, status, clk.summary()
+        return s, total_ms, per, launches, st, status, clk.summary(), graph_replays
 
-    s, total_ms, per, launches, st, status, clocks = timed(mpcgpu.FORM_FUSED, args.steps, args.warmup)
+    s, total_ms, per, launches, st, status, clocks, graph_replays = timed(mpcgpu.FORM_FUSED, args.steps, args.warmup)
     value, total_ms = job_throughput(n, args.steps, total_ms, world, dev)
     ms_step = total_ms / args.steps
 
@@ -377,7 +385,7 @@ def run_ours(args):
     paper_mode = None
     if not args.no_plain:
         K3 = min(args.steps, 5)
-        sp, tp, perp, lp, stp, _, _ = timed(mpcgpu.FORM_FUSED, K3, args.warmup, tune=False,
+        sp, tp, perp, lp, stp, _, _, _ = timed(mpcgpu.FORM_FUSED, K3, args.warmup, tune=False,
                                             variant=cfg["variant"], fixed_iters=25, polish=0, warm_polish=0)
         sp.close()
         paper_mode = {"value": world * n * K3 / (tp / 1e3), "ms_per_step": tp / K3,
@@ -392,7 +400,7 @@ def run_ours(args):
     plain = None
     if not args.no_plain:
         K2 = min(args.steps, 3)
-        sp, tp, perp, lp, _, _, _ = timed(mpcgpu.FORM_PLAIN, K2, args.warmup)
+        sp, tp, perp, lp, _, _, _, _ = timed(mpcgpu.FORM_PLAIN, K2, args.warmup)
         sp.close()
         plain = {"value": world * n * K2 / (tp / 1e3), "ms_per_step": tp / K2,
                  "p50_ms": float(np.percentile(perp, 50)), "gpu_launches_per_step": lp // K2}
@@ -412,7 +420,7 @@ def run_ours(args):
                                f"{Nh.mean():.2f}), gaits walk/stand/hop/single-stance, warm-started "
                                f"replans with perturbed state", "agents_per_gpu": n,
                    "form": "fused (persistent, work queue)", "precision": "fp32",
-                   "graph": not args.no_graph,
+                   "graph": not args.no_graph, "graph_replays": int(graph_replays),
                    "tuned": tune_report["chosen"] if tune_report else
                    {"variant": args.variant, "check_every": args.check_every, "early_polish": args.early_polish},
                    "replans": "monotone sequence, 100 Hz (phase += 0.02 per replan)",
@@ -481,7 +489,7 @@ def precision_report(args, timed, cfg, n, world, mpcgpu):
         samples[wl] = (model, inps, [r["tau"] for r, _ in sample_solve(model, inps, 0, 2)])
     out = {}
     for prec in (0, 1, 2, 3):
-        s, tp, perp, _, _, _, _ = timed(mpcgpu.FORM_FUSED, K, args.warmup, tune=False, variant=cfg["variant"],
+        s, tp, perp, _, _, _, _, _ = timed(mpcgpu.FORM_FUSED, K, args.warmup, tune=False, variant=cfg["variant"],
                                        check_every=cfg["check_every"], early_polish=cfg["early_polish"],
                                        precision=prec, refine_steps=-1)
         s.close()

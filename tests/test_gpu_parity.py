@@ -284,3 +284,54 @@ def test_full_size_mixed_16k_sampled(mpcgpu):
     _report("16k-sample", got["tau"][sample], ref["tau"], {k: v[sample] for k, v in st.items()})
     assert ok[solved[sample]].all()
     got["solver"].close()
+
+
+def test_full_size_warm_replans_in_bench_configuration(mpcgpu):
+    # the benchmark's launch configuration: 16384 mixed agents on a side
+    # stream with graph replay, kernel variant 2, replans walked forward;
+    # replan 2 (polish first from the previous active set) checked on a seeded
+    # sample against the oracle, every agent by property
+    from workload import make_agents, perturb_inputs
+    n = 16384
+    ids = np.arange(n)
+    model, inp = make_agents("mixed16k", ids)
+    reps = [inp]
+    for r in (1, 2):
+        reps.append(perturb_inputs("mixed16k", reps[-1], ids, r))
+    dev = torch.device("cuda:0")
+    side = torch.cuda.Stream(dev)
+    s = mpcgpu.Solver(max_agents=n, max_horizon=20, stream=side.cuda_stream, graph=1, variant=2,
+                      check_every=10, early_polish=1000.0)
+    s.set_models(model, ids)
+    d_ids = torch.from_numpy(ids.astype(np.int32)).to(dev)
+    out = dict(tau=torch.empty((n, 18), device=dev), q_set=torch.empty((n, 18), device=dev),
+               qd_set=torch.empty((n, 18), device=dev), value=torch.empty(n, device=dev),
+               status=torch.empty(n, dtype=torch.int32, device=dev))
+    cur = {k: torch.empty(v.shape, dtype=torch.float32, device=dev) for k, v in reps[0].items()}
+    with torch.cuda.stream(side):
+        for x in reps:
+            # each replan's state goes into the same input buffers (graph replay)
+            for k, v in x.items():
+                cur[k].copy_(torch.from_numpy(np.ascontiguousarray(v, np.float32)))
+            tk = s.submit(d_ids, cur["x0"], cur["qd_meas"], cur["cmd"], cur["phase"])
+            s.solve(tk)
+            s.get_torques(tk, **out)
+    torch.cuda.synchronize()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    st = s.agent_stats(ids)
+    stats = s.stats()
+    s.close()
+    assert (got["status"] == 0).all()
+    assert np.isfinite(got["tau"]).all()
+    assert (st["polished"] == 2).mean() >= 0.99          # polish first carried the warm replan
+    assert (st["prim_scaled"] <= 10).all() and (st["dual_scaled"] <= 10).all()
+    assert stats["graph_replays"] >= 1
+    rng = np.random.default_rng(11)
+    sample = np.sort(rng.choice(n, 32, replace=False))
+    inp32 = device_inputs(reps[-1])
+    sm = {k: v[sample] for k, v in model.items()}
+    si = {k: v[sample] for k, v in inp32.items()}
+    ref = _oracle(sm, si)
+    ok = torque_close(got["tau"][sample], ref["tau"])
+    _report("16k-warm-sample", got["tau"][sample], ref["tau"], {k: v[sample] for k, v in st.items()})
+    assert ok.all(), np.argwhere(~ok)
