@@ -147,24 +147,38 @@ def flops_per_agent(N, iters, refac, polished):
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
+    """nvidia-smi sampled every 20 ms; summary() keeps the samples taken
+    between begin() and end() (the timed region)."""
+
     def __init__(self, device_index=0):
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_{os.getpid()}.csv")
         self.dev = device_index
+        self.t_begin = self.t_end = None
 
     def __enter__(self):
         os.makedirs(os.path.dirname(self.path), exist_ok=True)
-        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+        q = ("timestamp,index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={q}",
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "20"],
                                          stdout=self.fh, stderr=subprocess.DEVNULL)
+            # the sampler is running before the timed region starts
+            t = time.time()
+            while time.time() - t < 5.0 and os.path.getsize(self.path) == 0 and self.proc.poll() is None:
+                time.sleep(0.01)
         except Exception:
             self.proc = None
         return self
+
+    def begin(self):
+        self.t_begin = time.time()
+
+    def end(self):
+        self.t_end = time.time()
 
     def __exit__(self, *a):
         if self.proc:
@@ -175,20 +189,48 @@ class ClockSampler:
                 self.proc.kill()
             self.fh.close()
 
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        for fmt in ("%Y/%m/%d %H:%M:%S.%f", "%Y/%m/%d %H:%M:%S"):
+            try:
+                return datetime.datetime.strptime(text.strip(), fmt).timestamp()
+            except ValueError:
+                pass
+        return None
+
     def summary(self):
         try:
-            rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+            rows = [[c.strip() for c in r.split(",")] for r in open(self.path).read().strip().splitlines()
+                    if r.strip()]
         except Exception:
             rows = []
+        rows = [r for r in rows if len(r) >= 10]
         if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        window = "timed region"
+        if self.t_begin is not None and self.t_end is not None:
+            inside = [r for r in rows if (ts := self._stamp(r[0])) is not None
+                      and self.t_begin - 0.025 <= ts <= self.t_end + 0.025]
+            if inside:
+                rows = inside
+            else:
+                mid = 0.5 * (self.t_begin + self.t_end)
+                rows = [min(rows, key=lambda r: abs((self._stamp(r[0]) or 0.0) - mid))]
+                window = "nearest sample to the timed region"
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [v for r in rows if (v := num(r[2])) is not None]
+        mx = [v for r in rows if (v := num(r[3])) is not None]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for r in rows for i in range(4)
-                          if len(r) > 5 + i and r[5 + i].strip().lower() == "active"})
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[6 + i].lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None,
-                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows)}
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons, "samples": len(rows),
+                "window": window}
 
 
 # ------------------------------------------------------------------ ours
@@ -274,11 +316,13 @@ def run_ours(args):
         t1 = torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             barrier()
+            clk.begin()
             t0.record(stream)
             for i in range(K):
                 step(s, 1 + W + i, evs[i])
             t1.record(stream)
             barrier()
+            clk.end()
         total_ms = t0.elapsed_time(t1)
         per = [a.elapsed_time(b) for a, b in evs]
         launches = s.stats()["kernel_launches"] - l0
@@ -358,6 +402,15 @@ def run_ours(args):
                           "(lambda 0.1), random weights; peak = measured cuBLAS bf16 burst"}
     s.close()
 
+    # measured ceilings of the arithmetic units (throughput microbenchmarks in
+    # the library), beside the derived FP32 peak and the cuBLAS bf16 peak
+    alu = {}
+    for name, kind in (("fp32_fma", mpcgpu.PEAK_FP32_FMA), ("fp64_fma", mpcgpu.PEAK_FP64_FMA),
+                       ("tf32_mma_sync", mpcgpu.PEAK_TF32_MMA_SYNC), ("bf16_mma_sync", mpcgpu.PEAK_BF16_MMA_SYNC)):
+        alu[name + "_tflops"] = mpcgpu.measure_peak(kind, stream.cuda_stream)[0]
+    if policy is not None:
+        policy["frac_of_measured_bf16_mma_sync"] = policy["tflops"] / alu["bf16_mma_sync_tflops"]
+
     # a cold solve (fresh state, no warm start): the tuned configuration, the
     # first replan, one launch timed with events
     cfg = tune_report["chosen"] if tune_report else \
@@ -436,7 +489,11 @@ def run_ours(args):
                      "frac": achieved / peak,
                      "traffic": None if TRAFFIC_BYTES_PER_AGENT is None else TRAFFIC_BYTES_PER_AGENT * n,
                      "kernel": "mpc_k_fused", "flops_per_launch": float(fl),
-                     "peak_basis": f"148 SM x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz (derived)"},
+                     "peak_basis": f"148 SM x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz (derived)",
+                     "measured_fp32_fma_tflops": alu["fp32_fma_tflops"],
+                     "frac_of_measured_fp32": achieved / alu["fp32_fma_tflops"]},
+        "measured_alu_peaks": dict(alu, note="library throughput kernels (mpc_measure_peak): independent "
+                                   "FMA chains / back-to-back mma.sync, 64 warps per SM"),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

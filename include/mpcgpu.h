@@ -70,6 +70,14 @@ typedef enum { MPC_FP32 = 0, MPC_TF32 = 1, MPC_BF16 = 2, MPC_FP64 = 3 } mpc_prec
 
 typedef enum { MPC_FORM_PLAIN = 0, MPC_FORM_FUSED = 1 } mpc_form;
 
+/* Unit measured by mpc_measure_peak. */
+typedef enum {
+  MPC_PEAK_FP32_FMA = 0,      /* FP32 fused multiply-add on the CUDA cores */
+  MPC_PEAK_FP64_FMA = 1,      /* FP64 fused multiply-add */
+  MPC_PEAK_TF32_MMA_SYNC = 2, /* mma.sync m16n8k8 TF32, FP32 accumulation */
+  MPC_PEAK_BF16_MMA_SYNC = 3  /* mma.sync m16n8k16 BF16, FP32 accumulation */
+} mpc_peak_kind;
+
 typedef enum {
   MPC_GAIT_WALK = 0, MPC_GAIT_STAND = 1, MPC_GAIT_HOP = 2,
   MPC_GAIT_SINGLE_L = 3, MPC_GAIT_SINGLE_R = 4
@@ -91,7 +99,12 @@ typedef struct mpc_config {
                                  FP32; TF32 / BF16 = the two dense stage-block
                                  products (K = -H_uu^-1 H_ux and H_ux^T K) on the
                                  tensor cores (mma.sync), FP32 accumulation; FP64 =
-                                 the stage Schur complement H_uu inverted in FP64 */
+                                 the stage Schur complement H_uu inverted in FP64.
+                                 With polish first on (polish, warm_polish,
+                                 fixed_iters 0), a TF32 / BF16 agent whose polish
+                                 first fails falls back to FP32 factors for its
+                                 ADMM solve and later polishes; otherwise every
+                                 factor uses the requested precision */
   int form;                   /* mpc_form: separate step kernels or one fused kernel */
   float rho0, sigma, alpha;   /* ADMM step size, proximal weight, relaxation */
   float eps_abs, eps_rel;     /* OSQP-style stopping tolerances */
@@ -296,6 +309,17 @@ mpc_status mpc_set_policy(mpc_ctx* ctx, const float* W1, const float* b1, const 
  * Errors: MPC_ERR_STATE if no policy is set, MPC_ERR_NOT_READY for an
  * unknown or unsolved ticket. */
 mpc_status mpc_policy_torques(mpc_ctx* ctx, uint64_t ticket, float* tau_dev, float* action_dev);
+
+/* Measured arithmetic ceiling of one unit, the denominator of the solver's
+ * roofline: a throughput kernel (64 warps per SM, independent dependency
+ * chains on that unit only) run once to warm up and five times timed with
+ * CUDA events on `stream` (a cudaStream_t, NULL = the legacy default stream)
+ * on the current device.  Outputs (host): tflops = FLOP per launch / mean
+ * launch time (an FMA counts 2 FLOP, an m16n8kK mma 2 x 16 x 8 x K); ms (may
+ * be NULL) = mean launch time in milliseconds.  Synchronises the stream.
+ * Errors: MPC_ERR_INVALID for an unknown kind or a NULL tflops,
+ * MPC_ERR_CUDA for a failed allocation or launch. */
+mpc_status mpc_measure_peak(int32_t kind, void* stream, double* tflops, double* ms);
 
 /* One-line description of the last error on this context (never NULL). */
 const char* mpc_last_error(mpc_ctx* ctx);

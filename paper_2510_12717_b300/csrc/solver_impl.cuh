@@ -1087,7 +1087,7 @@ __device__ __noinline__ void polish_refine(const AgentPtrs& ap, float* sm, int l
 // Riccati caches (the caller refactors if ADMM continues).
 template <int PREC>
 __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat, Pipe& pp,
-                                          const SolverParams& prm, int nref) {
+                                          const SolverParams& prm, int nref, int prec) {
   const int N = ap.N;
   const float* md = ap.mdl;
   const float dt = md[M_DT], mu = md[M_MU];
@@ -1124,7 +1124,7 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
     }
     const StageIn in = polish_stage_in(ap, sm, cvec, el, lane, pat, ap.uref[k * VS + lane],
                                        lane < NC ? ap.lin[L_STAGE + k * 64 + 32 + lane] : 0.f);
-    const StageOut so = factor_stage<PREC>(ap, sm, lane, k, in, &Pa, pat, prm.precision, nref > 0);
+    const StageOut so = factor_stage<PREC>(ap, sm, lane, k, in, &Pa, pat, prec, nref > 0);
     // H (= H_uu^-1) and K of stage k are still in smem
     const float s = p + so.e;
     vS[lane] = s;
@@ -1402,7 +1402,7 @@ enum : int { POLISH_ADMM = 0, POLISH_PREV = 1, POLISH_MIN = 2 };
 
 template <int PREC>
 __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Res* res,
-                       const LanePat& pat, Pipe& pp, int guess = POLISH_ADMM) {
+                       const LanePat& pat, Pipe& pp, int prec, int guess = POLISH_ADMM) {
   if (guess == POLISH_PREV) init_active_prev(ap, lane);
   else if (guess == POLISH_MIN) init_active_min(ap, lane);
   else init_active(ap, lane);
@@ -1411,7 +1411,7 @@ __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, co
   const int attempts = guess == POLISH_ADMM ? 4 : 8;
   const int nref = guess == POLISH_PREV ? prm.refine : prm.refine_admm;
   for (int attempt = 0; attempt < attempts; ++attempt) {
-    if (!polish_solve<PREC>(ap, sm, lane, pat, pp, prm, nref)) return false;
+    if (!polish_solve<PREC>(ap, sm, lane, pat, pp, prm, nref, prec)) return false;
     const Res pr = polish_check<false>(ap, sm, lane, prm, nullptr, pat);
     const float tol_p = prm.eps_abs + prm.eps_rel * pr.ps;
     const float tol_d = prm.eps_abs + prm.eps_rel * pr.ds;
@@ -1543,14 +1543,21 @@ __device__ __noinline__ void polish_warm_start(const AgentPtrs& ap, float* sm, i
 // Iterations with a residual check every check_every; OSQP's rho update
 // (refactor when the ratio is off by 5x); polish attempts once both residuals
 // are within early_polish x the tolerance.  Returns the agent status.
-struct Outcome { int status, iters, refac, polished; Res r; };
+struct Outcome { int status, iters, refac, polished, prec; Res r; };
+
+// Factor precision after a failed polish first: a TF32 or BF16 factor that
+// did not give the optimum at once is not trusted for ADMM (an inexact
+// factor can make ADMM diverge), so the agent's fallback factors in FP32.
+__device__ __forceinline__ int fallback_precision(int p) {
+  return (p == PREC_TF32 || p == PREC_BF16) ? PREC_FP32 : p;
+}
 
 template <int PREC>
 __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, bool factored,
                               Pipe& pp, const LanePat& pat) {
   float rho = *ap.rho;
   Outcome o;
-  o.status = MPC_AGENT_MAX_ITER_; o.iters = 0; o.refac = 0; o.polished = 0;
+  o.status = MPC_AGENT_MAX_ITER_; o.iters = 0; o.refac = 0; o.polished = 0; o.prec = prm.precision;
   o.r.rp = o.r.rd = o.r.ps = o.r.ds = o.r.pn = o.r.dn = 0.f;
   // polish first: a warm start's previous final active set is usually still
   // right, and a cold agent's optimum has few active rows; a polish from that
@@ -1559,7 +1566,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
   if (lane == 0) ap.st[T_FIRST] = 0;
   if (prm.polish && prm.warm_polish && prm.fixed_iters == 0) {
     Res pr;
-    if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, ap.st[T_WARM] ? POLISH_PREV : POLISH_MIN)) {
+    if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, o.prec, ap.st[T_WARM] ? POLISH_PREV : POLISH_MIN)) {
       o.polished = 1;
       o.status = MPC_AGENT_SOLVED_;
       o.r = pr;
@@ -1567,9 +1574,10 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
       return o;
     }
     factored = false;   // the polish overwrote the caches
+    o.prec = fallback_precision(o.prec);
     polish_warm_start(ap, sm, lane, pat);
   }
-  if (!factored) factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, prm.precision);
+  if (!factored) factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, o.prec);
   const bool fixed = prm.fixed_iters > 0;
   const int max_it = fixed ? prm.fixed_iters : prm.max_iter;
   // polish attempts: the first once both residuals are within early_polish x
@@ -1602,13 +1610,13 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
       ++polish_tries;
       next_polish_it = it + (polish_every << (polish_tries >> 1));
       Res pr;
-      if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp)) {
+      if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, o.prec)) {
         o.polished = 1;
         o.status = MPC_AGENT_SOLVED_;
         o.r = pr;
         break;
       }
-      factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, prm.precision);   // the polish overwrote the caches
+      factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, o.prec);   // the polish overwrote the caches
       ++o.refac;
     }
     if (prm.adaptive_rho && it < max_it) {
@@ -1618,7 +1626,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
       rn = fminf(fmaxf(rn, 1e-6f), 1e6f);
       if (rn > 5.f * rho || rn < 0.2f * rho) {
         rho = rn;
-        factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, prm.precision);
+        factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, o.prec);
         ++o.refac;
       }
     }
@@ -1709,7 +1717,7 @@ __device__ void final_polish(const AgentPtrs& ap, float* sm, int lane, const Sol
                              const LanePat& pat, Pipe& pp) {
   if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) return;
   Res pr;
-  if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp)) {
+  if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, o.prec)) {
     o.polished = 1;
     o.status = MPC_AGENT_SOLVED_;
     o.r = pr;
@@ -1818,6 +1826,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_polish(Arena
   o.r.pn = ap.out[O_PRIM_N];
   o.r.dn = ap.out[O_DUAL_N];
   o.r.ps = o.r.ds = 0.f;
+  o.prec = prm.warm_polish && prm.fixed_iters == 0 ? fallback_precision(prm.precision) : prm.precision;
   if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) return;
   load_lin(ap, sm, lane);
   copy_n(sm + S_BV, ap.lin + L_BV, 136 / 4, lane);

@@ -20,6 +20,7 @@ MPC_ERR_NOT_READY, MPC_ERR_TIMEOUT, MPC_ERR_STATE = 4, 5, 6
 AGENT_SOLVED, AGENT_MAX_ITER, AGENT_PRIMAL_INFEAS, AGENT_DUAL_INFEAS, AGENT_NAN, AGENT_TIMEOUT = 0, 1, 2, 3, 4, 5
 FORM_PLAIN, FORM_FUSED = 0, 1
 FP32, TF32, BF16, FP64 = 0, 1, 2, 3
+PEAK_FP32_FMA, PEAK_FP64_FMA, PEAK_TF32_MMA_SYNC, PEAK_BF16_MMA_SYNC = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "MPC_OK", 1: "MPC_ERR_INVALID", 2: "MPC_ERR_BUDGET", 3: "MPC_ERR_CUDA",
                 4: "MPC_ERR_NOT_READY", 5: "MPC_ERR_TIMEOUT", 6: "MPC_ERR_STATE"}
@@ -82,6 +83,7 @@ SIGNATURES = {
     "mpc_last_error": (C.c_char_p, [_P]),
     "mpc_set_policy": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_float]),
     "mpc_policy_torques": (C.c_int, [_P, C.c_uint64, _P, _P]),
+    "mpc_measure_peak": (C.c_int, [C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 }
 
 _lib = None
@@ -144,6 +146,16 @@ def solve_static(model: dict, x0, qd_meas, cmd, phase, *, tau=None, q_set=None, 
     return lib.mpc_solve_static(len(recs), recs.ctypes.data, _ptr(x0), _ptr(qd_meas), _ptr(cmd),
                                 _ptr(phase), _ptr(tau), _ptr(q_set), _ptr(qd_set), _ptr(value),
                                 _ptr(status), stream)
+
+
+def measure_peak(kind: int, stream=None) -> tuple[float, float]:
+    """mpc_measure_peak: (TFLOP/s, ms per launch) of one arithmetic unit."""
+    lib = load()
+    tf, ms = C.c_double(0.0), C.c_double(0.0)
+    st = lib.mpc_measure_peak(kind, stream, C.byref(tf), C.byref(ms))
+    if st != MPC_OK:
+        raise MpcError(st, f"mpc_measure_peak({kind}) failed")
+    return tf.value, ms.value
 
 
 class Solver:

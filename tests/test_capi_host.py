@@ -70,6 +70,9 @@ def test_default_config_and_argument_errors(lib):
     assert lib.mpc_create(C.byref(bad), C.byref(h)) == mpcgpu.MPC_ERR_BUDGET
     assert lib.mpc_destroy(None) == mpcgpu.MPC_ERR_INVALID
     assert lib.mpc_last_error(None) == b"NULL context"
+    tf = C.c_double(0.0)
+    assert lib.mpc_measure_peak(9, None, C.byref(tf), None) == mpcgpu.MPC_ERR_INVALID
+    assert lib.mpc_measure_peak(mpcgpu.PEAK_FP32_FMA, None, None, None) == mpcgpu.MPC_ERR_INVALID
 
 
 def test_pack_models_roundtrip():
