@@ -81,7 +81,7 @@ def parse():
     ap.add_argument("--no-precision", action="store_true", help="skip the per-precision speed/accuracy report")
     ap.add_argument("--no-policy", action="store_true", help="skip the residual-policy measurement")
     ap.add_argument("--precision-agents", type=int, default=48, help="agents per workload sample, precision report")
-    ap.add_argument("--serve-seconds", type=float, default=0.5, help="serving run length (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=1.5, help="serving run length (0 = skip)")
     ap.add_argument("--serve-rate", default="0.5,1,2",
                     help="request rates, comma-separated, x 16384 agents at 100 Hz")
     return ap.parse_args()
@@ -592,12 +592,13 @@ def run_serving(args, model, replans, n):
     out = {}
     for f in [float(v) for v in str(args.serve_rate).split(",") if v.strip()]:
         eng = ServingEngine(smodel, sinp, pool=n, streams=2, hbm_budget_bytes=8 << 30, seed=7)
-        st = eng.run(rate=f * 16384 * 100.0, duration=args.serve_seconds, churn_every=100, churn_frac=0.05)
+        st = eng.run(rate=f * 16384 * 100.0, duration=args.serve_seconds, churn_period=1.0, churn_frac=0.05)
         eng.close()
         st["rate_x_16384_at_100hz"] = f
         st["churned_agents"] = int(eng.churned)
         out[f"{f:g}x"] = st
-    out["note"] = ("requests of one agent coalesce (newest state wins); 2 streams; churn 5% every 100 batches; "
+    out["note"] = ("requests of one agent coalesce (newest state wins); 2 streams; churn: 5% of the agents "
+                   "(between requests) swapped for reserve agents every 1 s = 100 replans at 100 Hz; "
                    "rates x 1.6384 M requests/s")
     return out
 

@@ -58,10 +58,16 @@ typedef enum {
 } mpc_status;
 
 typedef enum {
-  MPC_AGENT_SOLVED = 0,        /* ADMM met its tolerances */
+  MPC_AGENT_SOLVED = 0,        /* ADMM met its tolerances, or a polish passed the KKT check */
   MPC_AGENT_MAX_ITER = 1,      /* iteration cap reached (or fixed-N_QP mode) */
-  MPC_AGENT_PRIMAL_INFEAS = 2,
-  MPC_AGENT_DUAL_INFEAS = 3,
+  MPC_AGENT_PRIMAL_INFEAS = 2, /* no point satisfies the constraints: OSQP's certificate
+                                  (the multiplier change of the last ADMM iteration,
+                                  with the dynamics multipliers from the costate
+                                  recursion) held at a residual check, tolerance
+                                  1e-4 relative; outputs are those of the last
+                                  iterate, and the next replan cold-starts */
+  MPC_AGENT_DUAL_INFEAS = 3,   /* never produced: every row of the cost is bounded
+                                  below on the dynamics (Q, R >= 0, x0 fixed) */
   MPC_AGENT_NAN = 4,           /* non-finite input or iterate; outputs zeroed */
   MPC_AGENT_TIMEOUT = 5        /* a bounded device wait gave up; outputs zeroed */
 } mpc_agent_status;

@@ -23,10 +23,13 @@ Sec. III-B Eq. (kkt_system); Sec. III-C Alg. 1, Eqs. (rnea), (mpc_torque)):
   lqr.py     closed-form affine finite-horizon LQR (a pin for the IPM)
   activeset.py brute-force active-set enumeration on toy QPs (a pin)
   kkt.py     KKT stationarity / feasibility / complementarity checks (a pin)
+  feasibility.py  primal feasibility of the QP's constraint set (an LP by
+             HiGHS), the reference for the solver's infeasibility status
 
 Pins (tests/test_oracle_*.py, all CPU): closed-form LQR when no constraint is
 active, brute-force active sets on toy QPs, KKT invariants on every solve,
 complex-step vs central-difference Jacobians, rigid-body invariants, a
 rotation-derivative check of the Euler-rate map, hand-worked contact
-schedules (tests/golden/), and a hand-computed standing torque.
+schedules (tests/golden/), a hand-computed standing torque, and the
+closed-form joint-reachability bound for the feasibility LP.
 """

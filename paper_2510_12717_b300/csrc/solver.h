@@ -11,6 +11,7 @@ constexpr int WARPS_PER_BLOCK = 4;
 // per-agent status codes (same values as mpc_agent_status in the public header)
 constexpr int MPC_AGENT_SOLVED_ = 0;
 constexpr int MPC_AGENT_MAX_ITER_ = 1;
+constexpr int MPC_AGENT_PRIMAL_INFEAS_ = 2;
 constexpr int MPC_AGENT_NAN_ = 4;
 constexpr int MPC_AGENT_TIMEOUT_ = 5;
 

@@ -552,8 +552,11 @@ __device__ __forceinline__ void pipe_wait(Pipe& pp, int b) {
   pp.ph[b] ^= 1u;
 }
 
+// store_dy: also write the change of the row multipliers, y_new - y_old, to
+// the agent's cEl scratch (free outside a polish), for the primal
+// infeasibility test that follows a residual check
 __device__ void admm_iteration(const AgentPtrs& ap, float* sm, int lane, float rho, const SolverParams& prm,
-                               Pipe& pp, const LanePat& pat) {
+                               Pipe& pp, const LanePat& pat, bool store_dy = false) {
   const int N = ap.N;
   const float* md = ap.mdl;
   const float dt = md[M_DT], mu = md[M_MU], sigma = prm.sigma, alpha = prm.alpha;
@@ -655,6 +658,7 @@ __device__ void admm_iteration(const AgentPtrs& ap, float* sm, int lane, float r
       }
       ap.w[k * RS + r] = wn;
       ap.y[k * RS + r] = yn;
+      if (store_dy) ap.cEl[k * 128 + r] = yn - yo;
     }
     if (lane < 30) {
       ap.u[k * VS + lane] = alpha * u + (1.f - alpha) * ap.u[k * VS + lane];
@@ -747,6 +751,67 @@ __device__ __noinline__ Res admm_residuals(const AgentPtrs& ap, float* sm, int l
   out.rp = warp_max(rp); out.ps = warp_max(ps); out.rd = warp_max(rd); out.ds = warp_max(ds);
   out.pn = warp_max(pn); out.dn = warp_max(dn);
   return out;
+}
+
+// ============================================================ infeasibility (A5 vii)
+// OSQP's primal infeasibility certificate (Stellato et al. 2020, Sec. 3.4;
+// Banjac et al. 2019): when the constraints admit no point, the change of
+// the multipliers over an iteration, dy = y^k - y^(k-1), converges to a
+// Farkas certificate.  Here the dynamics rows are eliminated exactly, so
+// their multipliers nu are not iterated: they are taken from the costate
+// recursion that makes the certificate's x-components vanish,
+// m_N = C_x^T dy_(N-1), m_k = C_x^T dy_(k-1) + A_k^T m_(k+1), nu = -m.  The
+// problem is declared primal infeasible when the u-components nearly vanish,
+// |C_u^T dy_k + B_k^T m_(k+1)|_inf <= eps |dy|_inf, and the support function
+// of the constraint set is negative along dy:
+// hi^T max(dy, 0) + lo^T min(dy, 0) + e^T nu < -eps |dy|_inf, with
+// e^T nu = -(m_0^T x0 + sum_k m_(k+1)^T c_k) and m_0 = A_0^T m_1.
+// Reads dy from cEl (written by the preceding admm_iteration).
+constexpr float kEpsPrimInf = 1e-4f;   // OSQP's default eps_prim_inf
+
+__device__ __noinline__ bool admm_primal_infeasible(const AgentPtrs& ap, float* sm, int lane, const LanePat& pat) {
+  const int N = ap.N;
+  const float* md = ap.mdl;
+  const float dt = md[M_DT], mu = md[M_MU];
+  float* vec = sm + S_VEC;
+  float* vM = vec + V_S * 64;
+  float* vY = vec + V_ROW * 64;
+  const float* dy = ap.cEl;
+  float dyn = 0.f, supp = 0.f;
+  for (int k = 0; k < N; ++k)
+    for (int r = lane; r < NR; r += 32) {
+      const float d = dy[k * 128 + r];
+      if (ap.rcls[k * RS + r] > 0.f && d != 0.f) {
+        dyn = fmaxf(dyn, fabsf(d));
+        supp += d > 0.f ? d * ap.rhi[k * RS + r] : d * ap.rlo[k * RS + r];
+      }
+    }
+  dyn = warp_max(dyn);
+  supp = warp_sum(supp);
+  if (!(dyn > 0.f) || !(supp < INFINITY)) return false;   // no change, or dy leaves an unbounded side
+  float m = (lane >= 12 && lane < 30) ? dy[(N - 1) * 128 + lane + 26] : 0.f;
+  float ru = 0.f, ex = 0.f;
+  for (int k = N - 1; k >= 0; --k) {
+    const float* dA = ap.lin + L_STAGE + k * 64;
+    set_stage_A(sm, dA, lane);
+    vM[lane] = m;
+    for (int r = lane; r < NR; r += 32) vY[r] = dy[k * 128 + r];
+    __syncwarp();
+    float mn = 0.f;
+    if (lane < 30) {
+      const float btm = lane < NC ? cc_tv(sm + S_BV, pat.br, vM, lane) : dt * m;
+      ru = fmaxf(ru, fabsf(cuT(vY, lane, mu) + btm));
+      if (lane < NC) ex += m * dA[32 + lane];                 // m_(k+1)^T c_k
+      const float atm = lane < NC ? cc_tv(sm + S_AV, pat.ar, vM, lane) : m;
+      if (k >= 1) mn = atm + (lane >= 12 ? dy[(k - 1) * 128 + lane + 26] : 0.f);
+      else ex += atm * ap.x[lane];                              // m_0^T x0
+    }
+    __syncwarp();
+    m = mn;
+  }
+  ru = warp_max(ru);
+  ex = warp_sum(ex);
+  return ru <= kEpsPrimInf * dyn && supp - ex < -kEpsPrimInf * dyn;
 }
 
 // ============================================================ polish
@@ -1590,9 +1655,9 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
   int polish_tries = 0, next_polish_it = 0;
   int it = 0;
   for (it = 1; it <= max_it; ++it) {
-    admm_iteration(ap, sm, lane, rho, prm, pp, pat);
-    if (warp_or(pp.timeout)) { o.status = MPC_AGENT_TIMEOUT_; break; }
     const bool check = (!fixed && (it % prm.check_every == 0)) || it == max_it;
+    admm_iteration(ap, sm, lane, rho, prm, pp, pat, check && !fixed);
+    if (warp_or(pp.timeout)) { o.status = MPC_AGENT_TIMEOUT_; break; }
     if (!check) continue;
     o.r = admm_residuals(ap, sm, lane, prm, pat);
     if (!(isfinite(o.r.rp) && isfinite(o.r.rd))) { o.status = MPC_AGENT_NAN_; break; }
@@ -1603,6 +1668,12 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
     const float tol_d = prm.eps_abs + prm.eps_rel * o.r.ds;
     if (o.r.rp <= tol_p && o.r.rd <= tol_d && o.r.pn <= kScaledAccept && o.r.dn <= kScaledAccept) {
       o.status = MPC_AGENT_SOLVED_;
+      break;
+    }
+    // a primal residual that stays above its acceptance level: test the
+    // last iteration's multiplier change for an infeasibility certificate
+    if (o.r.pn > kScaledAccept && admm_primal_infeasible(ap, sm, lane, pat)) {
+      o.status = MPC_AGENT_PRIMAL_INFEAS_;
       break;
     }
     if (prm.polish && prm.early_polish > 0.f && polish_tries < 24 && it >= next_polish_it &&
@@ -1706,7 +1777,8 @@ __device__ void write_outcome(const AgentPtrs& ap, int lane, const Outcome& o) {
     ap.out[O_DUAL] = o.r.rd;
     ap.out[O_PRIM_N] = o.r.pn;
     ap.out[O_DUAL_N] = o.r.dn;
-    *ap.warm = (o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) ? 0 : ap.N;
+    *ap.warm = (o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_ ||
+                o.status == MPC_AGENT_PRIMAL_INFEAS_) ? 0 : ap.N;
   }
   __syncwarp();
 }
@@ -1715,7 +1787,9 @@ __device__ void write_outcome(const AgentPtrs& ap, int lane, const Outcome& o) {
 template <int PREC>
 __device__ void final_polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Outcome& o,
                              const LanePat& pat, Pipe& pp) {
-  if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) return;
+  if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_ ||
+      o.status == MPC_AGENT_PRIMAL_INFEAS_)
+    return;
   Res pr;
   if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, o.prec)) {
     o.polished = 1;
@@ -1827,7 +1901,9 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_polish(Arena
   o.r.dn = ap.out[O_DUAL_N];
   o.r.ps = o.r.ds = 0.f;
   o.prec = prm.warm_polish && prm.fixed_iters == 0 ? fallback_precision(prm.precision) : prm.precision;
-  if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_) return;
+  if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_ ||
+      o.status == MPC_AGENT_PRIMAL_INFEAS_)
+    return;
   load_lin(ap, sm, lane);
   copy_n(sm + S_BV, ap.lin + L_BV, 136 / 4, lane);
   Pipe pp;

@@ -7,13 +7,19 @@ per-agent pending set: later requests of the same agent coalesce into it (the
 newest state wins).  Whenever one of the streams is free, all pending agents
 that are not already in flight (up to max_batch) form the next batch, which
 is copied from pinned memory, solved on that stream (mpc_solve_on) and read
-back, overlapping with the batch on the other stream.  Every `churn_every`
-batches a fraction of the live agents leaves and as many new agents join.
+back, overlapping with the batch on the other stream.  Every `churn_period`
+seconds (1 s = 100 replans of an agent at 100 Hz) a fraction of the live
+agents leaves and as many new agents join: agents between requests (none of
+their batches in flight), so the swap needs no wait for the device.
 
 Request states: each agent walks forward in time from its initial inputs;
-a request is one 10 ms environment step (gait phase += phase_step, state +=
-N(0, step_sigma)), so a batch answering s coalesced requests of an agent
-solves its state s steps on from its previous solve.
+a request is one 10 ms environment step: gait phase += phase_step, and the
+state takes one step of a mean-reverting walk around the agent's initial
+state, x <- x_init + a (x - x_init) + step_sigma N(0, I), as a robot under
+feedback control stays near its reference (a plain random walk drifts past
+the joint limits within a few seconds and makes the QPs infeasible).  A
+batch answering s coalesced requests of an agent solves its state s steps
+on from its previous solve (the s-step transition of the same walk).
 
 Latency of a request = completion time of the batch that answered it minus
 its arrival time (time since the run started, on the host clock).
@@ -30,7 +36,7 @@ from . import mpcgpu
 class ServingEngine:
     def __init__(self, model: dict, inputs, *, pool: int, streams: int = 2, max_batch: int = 0,
                  hbm_budget_bytes: int = 8 << 30, device: int = 0, step_sigma: float = 0.02,
-                 phase_step: float = 0.02, seed: int = 0, **solver_opts):
+                 phase_step: float = 0.02, revert: float = 0.95, seed: int = 0, **solver_opts):
         """model: SoA agent models (workload.make_agents layout) of every agent
         that may ever join (live + reserve); inputs: their initial per-agent
         input dict (x0, qd_meas, cmd, phase), or a list whose first entry is.
@@ -41,12 +47,7 @@ class ServingEngine:
         self.model = model
         if isinstance(inputs, (list, tuple)):
             inputs = inputs[0]
-        self.state = {k: np.array(v, dtype=np.float32, copy=True) for k, v in inputs.items()}
-        self.step_sigma, self.phase_step = step_sigma, phase_step
-        # the walk's noise is drawn once and read cyclically (synthetic states;
-        # drawing fresh normals per batch dominated the host loop)
-        self.noise = np.random.default_rng(seed).standard_normal(1 << 22, dtype=np.float32)
-        self.noise_at = 0
+        self.walk = StateWalk(inputs, step_sigma=step_sigma, phase_step=phase_step, revert=revert, seed=seed)
         self.total = len(model["mass"])
         self.pool = pool
         self.max_batch = max_batch or pool
@@ -77,12 +78,15 @@ class ServingEngine:
         self.solver.close()
 
     # ---------------------------------------------------------------- churn
-    def churn(self, frac: float, rng):
-        """A fraction of the live agents leaves; as many reserve agents join."""
+    def churn(self, frac: float, rng, idle=None):
+        """A fraction of the live agents leaves; as many reserve agents join.
+        idle: mask of the slots that may leave (no batch of theirs in flight)."""
         k = int(round(frac * self.pool))
+        cand = np.arange(self.pool) if idle is None else np.nonzero(idle)[0]
+        k = min(k, len(cand))
         if k == 0 or len(self.reserve) < k:
             return 0
-        slots = np.sort(rng.choice(self.pool, k, replace=False))
+        slots = np.sort(rng.choice(cand, k, replace=False))
         # the joining agent's model replaces the leaving one's in its slot:
         # mpc_set_models resets the slot's warm start (no per-slot release)
         self.reserve.extend(int(a) for a in self.slot_agent[slots])
@@ -93,11 +97,10 @@ class ServingEngine:
         return k
 
     # ---------------------------------------------------------------- run
-    def run(self, rate: float, duration: float, *, seed: int = 0, churn_every: int = 100,
+    def run(self, rate: float, duration: float, *, seed: int = 0, churn_period: float = 1.0,
             churn_frac: float = 0.05, warmup_batches: int = 2):
         """Serve a Poisson stream of `rate` requests/s for `duration` seconds
         of arrivals.  Returns latency and throughput statistics."""
-        torch = self.torch
         rng = np.random.default_rng(seed)
         n_req = rng.poisson(rate * duration)
         t_arr = np.sort(rng.uniform(0.0, duration, n_req))
@@ -123,6 +126,7 @@ class ServingEngine:
             for lo in range(0, self.pool, self.max_batch):
                 sl = np.arange(lo, min(lo + self.max_batch, self.pool))
                 self._solve_sync(sl, np.ones(len(sl), dtype=np.int64))
+        next_churn = churn_period if churn_period and churn_period > 0 else float("inf")
         t0 = time.perf_counter()
         while True:
             now = time.perf_counter() - t0
@@ -140,7 +144,7 @@ class ServingEngine:
                     self.bad_status += int(np.count_nonzero(stv != 0))
                     for v in np.unique(stv):
                         self.status_counts[int(v)] = self.status_counts.get(int(v), 0) + int(np.count_nonzero(stv == v))
-                    self.batch_log.append((len(sl), t_done - b["t_start"]))
+                    self.batch_log.append((len(sl), t_done - b["t_start"], b["t_start"]))
                     lat.append(self._latencies(times_by_slot, starts, served, sl, cover, t_done))
                     served[sl] = cover
                     in_flight[sl] = False
@@ -160,19 +164,11 @@ class ServingEngine:
                 in_flight[sl] = True
                 batches += 1
                 sizes.append(len(sl))
-                if churn_every and batches % churn_every == 0:
-                    # leave/join between batches: wait for the device, then swap
-                    torch.cuda.synchronize(self.dev)
-                    for sj, bj in enumerate(busy):
-                        if bj is not None:
-                            t_done = time.perf_counter() - t0
-                            self.bad_status += int(np.count_nonzero(self.h_out[sj]["st"].numpy()[:len(bj["slots"])] != 0))
-                            lat.append(self._latencies(times_by_slot, starts, served, bj["slots"], bj["cover"], t_done))
-                            served[bj["slots"]] = bj["cover"]
-                            in_flight[bj["slots"]] = False
-                            solves += len(bj["slots"])
-                            busy[sj] = None
-                    self.churn(churn_frac, rng)
+            if now >= next_churn:
+                # leave/join: slots with no batch in flight are swapped (the
+                # model upload is ordered before any later batch of theirs)
+                self.churn(churn_frac, rng, idle=~in_flight)
+                next_churn += churn_period
             if next_req >= n_req and all(b is None for b in busy) and not np.any(arrived > served):
                 break
             if now > duration * 20 + 60:
@@ -196,32 +192,15 @@ class ServingEngine:
         idx = np.repeat(first - np.cumsum(cnt) + cnt, cnt) + np.arange(cnt.sum())
         return t_done - times_by_slot[idx]
 
-    def _draw(self, shape):
-        size = int(np.prod(shape))
-        if self.noise_at + size > len(self.noise):
-            self.noise_at = 0
-        out = self.noise[self.noise_at:self.noise_at + size].reshape(shape)
-        self.noise_at += size
-        return out
-
-    def _advance(self, agents, steps):
-        """Walk the agents' states `steps` environment steps forward."""
-        st = self.state
-        s = np.asarray(steps, dtype=np.float32)
-        st["x0"][agents] += (self.step_sigma * np.sqrt(s))[:, None] * self._draw((len(agents), st["x0"].shape[1]))
-        st["qd_meas"][agents] = 0.1 * self._draw((len(agents), st["qd_meas"].shape[1]))
-        st["cmd"][agents, 0] = st["x0"][agents, 2]
-        ph = st["phase"][agents] + self.phase_step * s
-        st["phase"][agents] = ph - np.floor(ph)
-
     def _fill(self, si, sl, steps):
         h = self.h_in[si]
         n = len(sl)
-        agents = self.slot_agent[sl]
-        self._advance(agents, steps)
+        x0, qd, cmd, ph = self.walk.advance(self.slot_agent[sl], steps)
         h["ids"].numpy()[:n] = sl
-        for key, dst in (("x0", "x0"), ("qd_meas", "qd"), ("cmd", "cmd"), ("phase", "ph")):
-            h[dst].numpy()[:n] = self.state[key][agents]
+        h["x0"].numpy()[:n] = x0
+        h["qd"].numpy()[:n] = qd
+        h["cmd"].numpy()[:n] = cmd
+        h["ph"].numpy()[:n] = ph
         return n
 
     def _launch(self, si, sl, steps):
@@ -248,3 +227,57 @@ class ServingEngine:
 
 def streams_range(n):
     return range(n)
+
+
+class StateWalk:
+    """Synthetic per-agent request states.  One environment step: phase +=
+    phase_step, x <- x_init + a (x - x_init) + sigma xi (xi ~ N(0, I)),
+    qd_meas ~ 0.1 N(0, I), commanded height = current height (the other
+    command entries stay).  s coalesced steps take the s-step transition:
+    decay a^s, noise scale sigma sqrt((1 - a^2s) / (1 - a^2)).  The noise is
+    drawn once into a pool and read as windows at random offsets (synthetic
+    states; fresh normals per batch dominated the host loop).  Arrays are kept
+    per field and contiguous, so a batch is a few gathers and one scatter."""
+
+    def __init__(self, inputs, *, step_sigma=0.02, phase_step=0.02, revert=0.95, seed=0, pool_size=1 << 22):
+        self.X = np.array(inputs["x0"], dtype=np.float32, copy=True)
+        self.XI = self.X.copy()
+        self.CMD = np.array(inputs["cmd"], dtype=np.float32, copy=True)
+        self.PH = np.array(inputs["phase"], dtype=np.float32, copy=True)
+        self.phase_step = np.float32(phase_step)
+        steps = np.arange(_MAX_STEPS + 1, dtype=np.float64)
+        a = float(revert)
+        var = steps if a == 1.0 else (1.0 - a ** (2.0 * steps)) / (1.0 - a * a)
+        self.decay_tab = (a ** steps).astype(np.float32)
+        self.sdev_tab = (step_sigma * np.sqrt(var)).astype(np.float32)
+        self.rng = np.random.default_rng(seed)
+        self.noise = self.rng.standard_normal(pool_size, dtype=np.float32)
+
+    def draw(self, shape):
+        """A window of the pool at a random offset (a fixed cyclic order would
+        repeat each agent's noise with a fixed period and correlate the walk)."""
+        size = int(np.prod(shape))
+        at = int(self.rng.integers(0, len(self.noise) - size + 1))
+        return self.noise[at:at + size].reshape(shape)
+
+    def advance(self, agents, steps):
+        """Walk the agents' states `steps` environment steps forward; returns
+        (x0, qd_meas, cmd, phase) of the batch, fresh arrays in batch order."""
+        n = len(agents)
+        s = np.minimum(np.asarray(steps, dtype=np.int64), _MAX_STEPS)
+        x = self.X[agents]
+        xi = self.XI[agents]
+        x -= xi
+        x *= self.decay_tab[s][:, None]
+        x += xi
+        x += self.sdev_tab[s][:, None] * self.draw((n, 30))
+        self.X[agents] = x
+        ph = self.PH[agents] + self.phase_step * s.astype(np.float32)
+        ph -= np.floor(ph)
+        self.PH[agents] = ph
+        cmd = self.CMD[agents]
+        cmd[:, 0] = x[:, 2]
+        return x, 0.1 * self.draw((n, 18)), cmd, ph
+
+
+_MAX_STEPS = 1024        # coalesced steps beyond this take this many

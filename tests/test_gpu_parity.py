@@ -335,3 +335,39 @@ def test_full_size_warm_replans_in_bench_configuration(mpcgpu):
     ok = torque_close(got["tau"][sample], ref["tau"])
     _report("16k-warm-sample", got["tau"][sample], ref["tau"], {k: v[sample] for k, v in st.items()})
     assert ok.all(), np.argwhere(~ok)
+
+
+@pytest.mark.parametrize("form", [1, 0], ids=["fused", "plain"])
+def test_primal_infeasible_agents_are_flagged(mpcgpu, form):
+    # a joint started beyond q_lim + dt qd_max cannot reach its box in the
+    # first stage: OSQP's certificate (the multiplier change of an ADMM
+    # iteration) flags the agent long before the iteration cap; the rest of
+    # the batch is solved as usual
+    from oracle import qp as qpmod
+    from oracle.feasibility import is_feasible
+    from oracle.solve import agent_params
+    ids = np.arange(16)
+    model, inp = agents("uneven", ids)
+    bad = [1, 6, 11]
+    for a, j in zip(bad, (3, 9, 15)):
+        inp["x0"][a, 12 + j] = 2.0 if a % 2 else -2.0
+    inp32 = device_inputs(inp)
+    m64, i64 = oracle_view(model, inp32)
+    feas = [is_feasible(qpmod.agent_qp(agent_params(m64, a), i64["x0"][a], i64["cmd"][a],
+                                       float(i64["phase"][a]))[0]) for a in ids]
+    assert [a for a in ids if not feas[a]] == bad
+    s = mpcgpu.Solver(max_agents=16, max_horizon=20, form=form, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_models(model, ids)
+    r = s.solve_host(ids.astype(np.int32), inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+    st = s.agent_stats(ids.astype(np.int32))
+    s.close()
+    print(f"\n[infeasible, form {form}] status {r['status'].tolist()}, iterations of the flagged "
+          f"{st['iters'][bad].tolist()}")
+    assert (r["status"][bad] == mpcgpu.AGENT_PRIMAL_INFEAS).all()
+    assert (st["iters"][bad] < 1000).all()
+    assert np.isfinite(r["tau"]).all()
+    good = np.setdiff1d(ids, bad)
+    assert (r["status"][good] == 0).all()
+    ref = _oracle({k: v[good] for k, v in model.items()}, {k: v[good] for k, v in inp32.items()})
+    ok = torque_close(r["tau"][good], ref["tau"])
+    assert ok.all(), np.argwhere(~ok)

@@ -19,11 +19,12 @@ def test_serving_loop_runs_and_solves_everything():
         reps.append(perturb_inputs("serving", reps[-1], ids, r))
     reps = [{k: np.ascontiguousarray(v, np.float32) for k, v in x.items()} for x in reps]
     eng = ServingEngine(model, reps, pool=pool, streams=2, max_batch=256)
-    st = eng.run(rate=40000.0, duration=0.25, churn_every=4, churn_frac=0.05)
+    st = eng.run(rate=40000.0, duration=0.25, churn_period=0.05, churn_frac=0.05)
     eng.close()
     print("\n[serving]", st, "statuses", eng.status_counts)
     assert st["not_solved"] == 0
     assert st["solves"] > 0 and st["batches"] >= 4
+    assert eng.churned >= 3 * round(0.05 * pool)
     assert st["p50_ms"] is not None and st["p50_ms"] > 0 and st["p99_ms"] >= st["p50_ms"]
 
 

@@ -134,3 +134,41 @@ def test_standing_equilibrium_torque_by_hand():
     assert np.allclose(out["u"][0, [2, 8]], W, atol=1e-8)
     assert np.allclose(out["tau"], tau, atol=1e-8)
     assert abs(out["V"]) < 1e-8
+
+
+def test_feasibility_lp_on_a_textbook_pair():
+    # x <= 0 and x >= 1 (no point), against 0 <= x <= 1 (a segment)
+    from types import SimpleNamespace
+    from oracle.feasibility import is_feasible
+    bad = SimpleNamespace(C=np.array([[1.0], [1.0]]), lo=np.array([-np.inf, 1.0]), hi=np.array([0.0, np.inf]),
+                          E=np.zeros((0, 1)), e=np.zeros(0))
+    ok = SimpleNamespace(C=np.array([[1.0]]), lo=np.array([0.0]), hi=np.array([1.0]),
+                         E=np.zeros((0, 1)), e=np.zeros(0))
+    assert not is_feasible(bad)
+    assert is_feasible(ok)
+
+
+@pytest.mark.parametrize("i,joint,side", [(0, 0, 1.0), (2, 7, -1.0), (5, 17, 1.0)])
+def test_feasibility_lp_matches_the_joint_reachability_bound(i, joint, side):
+    # |q0_j| <= q_lim + dt qd_max is the exact first-stage reachability
+    # condition; the LP over the whole horizon QP must flip at the same place
+    from oracle.feasibility import is_feasible, joint_limits_reachable
+    model, inp = make_agents("uneven", np.arange(8))
+    m = agent_params(model, i)
+    lim = float(m["q_lim"]) + float(m["dt"]) * float(m["qd_max"])
+    for scale, want in ((0.999, True), (1.001, False)):
+        x0 = np.array(inp["x0"][i], float)
+        x0[12 + joint] = side * scale * lim
+        qp, _ = qpmod.agent_qp(m, x0, inp["cmd"][i], float(inp["phase"][i]))
+        assert joint_limits_reachable(m, x0) == want
+        assert is_feasible(qp) == want, (scale, want)
+
+
+@pytest.mark.parametrize("name", ["uneven", "mixed16k"])
+def test_workload_agents_are_feasible(name):
+    from oracle.feasibility import is_feasible
+    model, inp = make_agents(name, np.arange(6))
+    for i in range(6):
+        m = agent_params(model, i)
+        qp, _ = qpmod.agent_qp(m, np.asarray(inp["x0"][i], float), inp["cmd"][i], float(inp["phase"][i]))
+        assert is_feasible(qp)
