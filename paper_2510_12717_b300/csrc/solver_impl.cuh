@@ -237,14 +237,22 @@ __device__ __noinline__ bool setup_agent(const AgentPtrs& ap, float* sm, int lan
 
   // per stage: dA_k = dt dw/dq_leg (depends on the stance forces of u_ref_k)
   // and c_k = x0 + dt f(x0, u_ref_k) - A_k x0 - B u_ref_k
+  // (the stance forces are those of u_ref_k, recomputed from the contact
+  // flags; dA_k is staged in shared memory for the A_k x0 product, so neither
+  // is read back from global memory right after it was written)
+  float* vdA = vec + V_T * 64;
   for (int k = 0; k < N; ++k) {
     float* st = ap.lin + L_STAGE + k * 64;
-    const float FL = ap.uref[k * VS + 2], FR = ap.uref[k * VS + 8];
+    const int fk = flags[k];
+    const float share = weight / (float)__popc(fk);
+    const float FL = (fk & 1) ? share : 0.f, FR = (fk & 2) ? share : 0.f;
     if (lane < 30) {
       const int r = lane / 10, col = lane - 10 * r, f = col / 5, j = col - 5 * f;
       const float F = f ? FR : FL;
       const float jr0 = md[M_JLEG + 30 * f + 0 * 5 + j], jr1 = md[M_JLEG + 30 * f + 1 * 5 + j];
-      st[lane] = dt * F * (m3(Iwi, r, 0) * jr1 - m3(Iwi, r, 1) * jr0);
+      const float v = dt * F * (m3(Iwi, r, 0) * jr1 - m3(Iwi, r, 1) * jr0);
+      st[lane] = v;
+      vdA[lane] = v;
     }
     __syncwarp();
     if (lane < NC) {
@@ -261,7 +269,7 @@ __device__ __noinline__ bool setup_agent(const AgentPtrs& ap, float* sm, int lan
         const int r = i - 9;
         f0 = m3(Iwi, r, 0) * t0 + m3(Iwi, r, 1) * t1 + m3(Iwi, r, 2) * t2;
       }
-      const float Ax = ak_mv(Ab, st, xbar, lane);
+      const float Ax = ak_mv(Ab, vdA, xbar, lane);
       const float Bu = Bm[2 * LDD + i] * FL + Bm[8 * LDD + i] * FR;
       st[32 + i] = xbar[i] + dt * f0 - Ax - Bu;
     }
@@ -566,6 +574,7 @@ __device__ void admm_iteration(const AgentPtrs& ap, float* sm, int lane, float r
   float* vec = sm + S_VEC;
   float* vS = vec + V_S * 64; float* vH = vec + V_H * 64; float* vX = vec + V_X * 64;
   float* vU = vec + V_U * 64; float* vXN = vec + V_XN * 64; float* vR = vec + V_ROW * 64;
+  float* vA = vec + V_D * 64;
   const bool arm = lane >= NC && lane < 30;
   const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
   const float twoR = lane < 30 ? 2.f * dt * md[M_R + lane] : 0.f;
@@ -629,7 +638,10 @@ __device__ void admm_iteration(const AgentPtrs& ap, float* sm, int lane, float r
     const float* dA = ap.lin + L_STAGE + k * 64;
     vX[lane] = x;
     const float dk = ap.dv[k * VS + lane];
+    const float dA0 = dA[lane], dA1 = dA[32 + lane];    // staged in smem with the stage's other loads
     pipe_wait(pp, b);
+    vA[lane] = dA0;
+    vA[32 + lane] = dA1;
     __syncwarp();
     float u = 0.f;
     if (lane < NC) u = r24_mv(Kc, vX, lane) + dk;
@@ -637,7 +649,7 @@ __device__ void admm_iteration(const AgentPtrs& ap, float* sm, int lane, float r
     vU[lane] = u;
     __syncwarp();
     float xn = 0.f;
-    if (lane < NC) xn = ak_mv(Ab, dA, vX, lane) + cm_mv(Bm, vU, lane) + dA[32 + lane];
+    if (lane < NC) xn = ak_mv(Ab, vA, vX, lane) + cm_mv(Bm, vU, lane) + vA[32 + lane];
     else if (arm) xn = x + dt * u;
     vXN[lane] = xn;
     ap.xt[(k + 1) * VS + lane] = xn;
@@ -843,6 +855,54 @@ __device__ void init_active(const AgentPtrs& ap, int lane) {
   __syncwarp();
 }
 
+// One stage's per-lane global inputs of a polish pass, loaded together at
+// the top of the stage: one memory round trip, where loading each where it
+// is used costs one per step (active codes, A_k, bounds, references)
+struct StagePre {
+  int a0, a1;                      // active-set codes of rows lane and lane + 32
+  float dA[3];                     // this lane's entries of the stage-varying A_k block (lanes 12-21)
+  float F;                         // force lanes: upper bound of the foot's normal-force row
+  float lo_r, hi_r, lo_q, hi_q;    // lanes 12-29: bounds of the joint's rate row and joint-box row
+  float uref, ck;                  // u_ref,k and (coupled lanes) the affine term c_k
+};
+__device__ __forceinline__ StagePre stage_pre(const AgentPtrs& ap, int k, int lane) {
+  StagePre p;
+  const int* ak = ap.act + k * RS;
+  const float* lo = ap.rlo + k * RS;
+  const float* hi = ap.rhi + k * RS;
+  const float* dA = ap.lin + L_STAGE + k * 64;
+  p.a0 = ak[lane];
+  p.a1 = lane < NR - 32 ? ak[lane + 32] : 0;
+  const bool aj = lane >= 12 && lane < NC;
+#pragma unroll
+  for (int t = 0; t < 3; ++t) p.dA[t] = aj ? dA[t * 10 + (lane - 12)] : 0.f;
+  p.F = lane < 12 ? hi[(lane / 6) * 6 + 2] : 0.f;
+  const bool jr = lane >= 12 && lane < 30;
+  p.lo_r = jr ? lo[lane + 8] : 0.f;
+  p.hi_r = jr ? hi[lane + 8] : 0.f;
+  p.lo_q = jr ? lo[lane + 26] : 0.f;
+  p.hi_q = jr ? hi[lane + 26] : 0.f;
+  p.uref = ap.uref[k * VS + lane];
+  p.ck = lane < NC ? dA[32 + lane] : 0.f;
+  return p;
+}
+__device__ __forceinline__ void stage_active_pre(const StagePre& p, int* act, int lane) {
+  __syncwarp();
+  act[lane] = p.a0;
+  if (lane < NR - 32) act[lane + 32] = p.a1;
+  __syncwarp();
+}
+__device__ __forceinline__ void set_stage_A_pre(float* sm, const StagePre& p, int lane) {
+  if (lane >= 12 && lane < NC) {
+    float* av = sm + S_AV + lane * 6;
+    av[0] = 1.f;
+    av[1] = p.dA[0];
+    av[2] = p.dA[1];
+    av[3] = p.dA[2];
+  }
+  __syncwarp();
+}
+
 __device__ __forceinline__ void stage_active(const AgentPtrs& ap, int k, int* act, int lane) {
   __syncwarp();
   for (int r = lane; r < NR; r += 32) act[r] = ap.act[k * RS + r];
@@ -875,19 +935,19 @@ __device__ __forceinline__ FootAct foot_act(const int* act, int f) {
 struct Carry { int on; float b; };
 struct Elim { float g, t, phi, gf[3]; int qbox; Carry carry_out; };
 
-__device__ __forceinline__ Elim lane_elim(const AgentPtrs& ap, int k, const int* act, int i, float mu,
-                                          Carry carry_in) {
+__device__ __forceinline__ Elim lane_elim(const AgentPtrs& ap, const StagePre& pre, const int* act, int i,
+                                          float mu, Carry carry_in) {
   Elim e;
   e.g = 1.f; e.t = 0.f; e.phi = 0.f; e.gf[0] = e.gf[1] = e.gf[2] = 0.f; e.qbox = 0;
   e.carry_out.on = 0; e.carry_out.b = 0.f;
   if (i < 12) {
-    const int f = i / 6, c = i - 6 * f, b = 6 * f;
+    const int f = i / 6, c = i - 6 * f;
     const FootAct fa = foot_act(act, f);
     if (fa.swing || fa.zero) { e.g = 0.f; return e; }
     if (c >= 3) return e;                                   // free moment
     e.g = 0.f;
     if (fa.top) {
-      const float F = ap.rhi[k * RS + b + 2];
+      const float F = pre.F;
       if (c == 2) e.t = F;
       else {
         const int tt = c == 0 ? fa.tx : fa.ty;
@@ -909,11 +969,11 @@ __device__ __forceinline__ Elim lane_elim(const AgentPtrs& ap, int k, const int*
     const int a = act[r], aq = act[rq];
     int eq = carry_in.on;
     float eb = carry_in.b;
-    if (!eq && aq) { eq = 1; eb = (aq & 1) ? ap.rlo[k * RS + rq] : ap.rhi[k * RS + rq]; }
+    if (!eq && aq) { eq = 1; eb = (aq & 1) ? pre.lo_q : pre.hi_q; }
     const float dt = ap.mdl[M_DT];
     if (a) {
       e.g = 0.f;
-      e.t = (a & 1) ? ap.rlo[k * RS + r] : ap.rhi[k * RS + r];
+      e.t = (a & 1) ? pre.lo_r : pre.hi_r;
       if (eq) { e.carry_out.on = 1; e.carry_out.b = eb - dt * e.t; }
     } else if (eq) {
       e.g = 0.f;
@@ -1014,6 +1074,7 @@ __device__ __noinline__ void polish_rollout(const AgentPtrs& ap, float* sm, int 
   const float dt = ap.mdl[M_DT];
   float* vec = sm + S_VEC;
   float* vX = vec + V_X * 64; float* vV = vec + V_U * 64; float* vU = vec + V_XN * 64;
+  float* vA = vec + V_D * 64;   // the stage's dA_k block and c_k, staged with the stage's other loads
   const bool arm = lane >= NC && lane < 30;
   float* const K0 = sm + S_P; float* const K1 = sm + S_X;
     float x = lane < 30 ? ap.x[lane] : 0.f;
@@ -1026,10 +1087,13 @@ __device__ __noinline__ void polish_rollout(const AgentPtrs& ap, float* sm, int 
       const float* ce = ap.cE + k * 64;
       const float* dA = ap.lin + L_STAGE + k * 64;
       const float4 el = reinterpret_cast<const float4*>(ap.cEl + k * 128)[lane];
+      const float dA0 = dA[lane], dA1 = dA[32 + lane];
       vX[lane] = refine ? x - xo : x;
       const float base = refine ? ap.dv[k * VS + lane] + ap.cD[k * VS + lane] : ap.dv[k * VS + lane];
       const float xo_next = refine ? ap.xt[(k + 1) * VS + lane] : 0.f;
       pipe_wait(pp, b);
+      vA[lane] = dA0;
+      vA[32 + lane] = dA1;
       __syncwarp();
       float v = 0.f;
       if (lane < NC) v = r24_mv(Kc, vX, lane) + base;
@@ -1048,7 +1112,7 @@ __device__ __noinline__ void polish_rollout(const AgentPtrs& ap, float* sm, int 
       vX[lane] = x;
       __syncwarp();
       float xn = 0.f;
-      if (lane < NC) xn = ak_mv(sm + S_AB, dA, vX, lane) + cm_mv(sm + S_B, vU, lane) + dA[32 + lane];
+      if (lane < NC) xn = ak_mv(sm + S_AB, vA, vX, lane) + cm_mv(sm + S_B, vU, lane) + vA[32 + lane];
       else if (arm) xn = x + dt * u;
       ap.xt[(k + 1) * VS + lane] = xn;
       ap.ut[k * VS + lane] = u;
@@ -1087,12 +1151,12 @@ __device__ __noinline__ void polish_refine(const AgentPtrs& ap, float* sm, int l
     if (k >= 1)
       pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k - 1) * BLK, b ? H0 : H1,
                  ap.cH + (size_t)(k - 1) * BLK, lane);
-    stage_active(ap, k, act, lane);
-    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
-    const Elim el = lane_elim(ap, k, act, lane, mu, carry2);
+    const StagePre pre = stage_pre(ap, k, lane);
+    stage_active_pre(pre, act, lane);
+    set_stage_A_pre(sm, pre, lane);
+    const Elim el = lane_elim(ap, pre, act, lane, mu, carry2);
     carry2 = el.carry_out;
-    const StageIn in = polish_stage_in(ap, sm, cvec, el, lane, pat, ap.uref[k * VS + lane],
-                                       lane < NC ? ap.lin[L_STAGE + k * 64 + 32 + lane] : 0.f);
+    const StageIn in = polish_stage_in(ap, sm, cvec, el, lane, pat, pre.uref, pre.ck);
     const float v = ap.dv[k * VS + lane];
     vV[lane] = v;
     vS[lane] = lam;
@@ -1176,9 +1240,11 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
   Carry carry = {0, 0.f};
   __syncwarp();
   for (int k = N - 1; k >= 0; --k) {
-    stage_active(ap, k, act, lane);
-    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
-    const Elim el = lane_elim(ap, k, act, lane, mu, carry);
+    const StagePre pre = stage_pre(ap, k, lane);
+    const float xr = lane < 30 ? ap.xref[k * VS + lane] : 0.f;   // used after the factor
+    stage_active_pre(pre, act, lane);
+    set_stage_A_pre(sm, pre, lane);
+    const Elim el = lane_elim(ap, pre, act, lane, mu, carry);
     carry = el.carry_out;
     // the stage's elimination, for the forward pass: (g | G_f row 0, G_f row
     // 1, G_f row 2 | phi, t)
@@ -1187,8 +1253,7 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
       reinterpret_cast<float4*>(ap.cEl + k * 128)[lane] =
           make_float4(fl ? el.gf[0] : el.g, el.gf[1], fl ? el.gf[2] : el.phi, el.t);
     }
-    const StageIn in = polish_stage_in(ap, sm, cvec, el, lane, pat, ap.uref[k * VS + lane],
-                                       lane < NC ? ap.lin[L_STAGE + k * 64 + 32 + lane] : 0.f);
+    const StageIn in = polish_stage_in(ap, sm, cvec, el, lane, pat, pre.uref, pre.ck);
     const StageOut so = factor_stage<PREC>(ap, sm, lane, k, in, &Pa, pat, prec, nref > 0);
     // H (= H_uu^-1) and K of stage k are still in smem
     const float s = p + so.e;
@@ -1205,7 +1270,7 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
     ap.dv[k * VS + lane] = d;
     if (k >= 1) {
       // linear cost of x_k (with the moved cost of an eliminated joint rate)
-      float ql = lane < 30 ? -twoQ * ap.xref[k * VS + lane] : 0.f;
+      float ql = -twoQ * xr;
       if (el.qbox) ql -= 2.f * md[M_R + lane] * el.t;
       if (lane < NC) p = ql + cc_tv(sm + S_AV, pat.ar, vS, lane) + r24_mtv(K, vH, lane);
       else if (arm) p = ql + (el.qbox ? 0.f : s) + so.Ka * h;
@@ -1264,18 +1329,35 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
   int ch_on = 0, ch_ke = 0, ch_side = 0, ch_over = 0;
   float ch_up = 0.f, ch_lo = 0.f, ch_tol = 0.f;
   for (int k = N - 1; k >= 0; --k) {
-    stage_active(ap, k, act, lane);
-    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
+    // every global input of stage k, loaded together (one memory round trip)
+    const StagePre pre = stage_pre(ap, k, lane);
+    const float u_k = us[k * VS + lane], x_n = xs[(k + 1) * VS + lane];
+    const float xr_n = ap.xref[(k + 1) * VS + lane];
+    const float x_k = k >= 1 ? xs[k * VS + lane] : 0.f, xr_k = k >= 1 ? ap.xref[k * VS + lane] : 0.f;
+    float rlo[2], rhi[2], rcl[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = lane + 32 * h;
+      const bool in = r < NR;
+      rlo[h] = in ? ap.rlo[k * RS + r] : 0.f;
+      rhi[h] = in ? ap.rhi[k * RS + r] : 0.f;
+      rcl[h] = in ? ap.rcls[k * RS + r] : 0.f;
+    }
+    stage_active_pre(pre, act, lane);
+    set_stage_A_pre(sm, pre, lane);
     vM[lane] = m;
-    vU[lane] = us[k * VS + lane];
-    vXN[lane] = xs[(k + 1) * VS + lane];
+    vU[lane] = u_k;
+    vXN[lane] = x_n;
     __syncwarp();
     int* ak = ap.act + k * RS;
     // primal feasibility of the rows of stage k
-    for (int r = lane; r < NR; r += 32) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = lane + 32 * h;
+      if (r >= NR) break;
       const float v = crow(vU, vXN, r, mu);
-      const float lo = ap.rlo[k * RS + r], hi = ap.rhi[k * RS + r];
-      if (ap.rcls[k * RS + r] > 0.f) ps = fmaxf(ps, fabsf(v));
+      const float lo = rlo[h], hi = rhi[h];
+      if (rcl[h] > 0.f) ps = fmaxf(ps, fabsf(v));
       const float viol = fmaxf(fmaxf(lo - v, v - hi), 0.f);
       float sc = fabsf(v);
       if (isfinite(lo)) sc = fmaxf(sc, fabsf(lo));
@@ -1291,12 +1373,12 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
     // stationarity of the inputs without their row multipliers, and its tolerance
     float g = 0.f, td = 1.f;
     if (lane < 30) {
-      const float u = us[k * VS + lane], ur = ap.uref[k * VS + lane];
+      const float u = u_k, ur = pre.uref;
       const float btm = lane < NC ? cc_tv(sm + S_BV, pat.br, vM, lane) : dt * m;
       g = twoR * (u - ur) + btm;
       td = ea + er * fmaxf(fmaxf(fabsf(twoR * u), fabsf(twoR * ur)), fabsf(btm));
       ds = fmaxf(ds, fmaxf(fabsf(twoR * u), fabsf(twoR * ur)));
-      ds = fmaxf(ds, fmaxf(fabsf(twoQ * xs[(k + 1) * VS + lane]), fabsf(twoQ * ap.xref[(k + 1) * VS + lane])));
+      ds = fmaxf(ds, fmaxf(fabsf(twoQ * x_n), fabsf(twoQ * xr_n)));
     }
     vG[lane] = g;
     vT[lane] = td;
@@ -1323,7 +1405,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
         if (!ch_on) {
           ch_on = 1; ch_ke = k; ch_side = aq; ch_up = 3.0e38f; ch_lo = -3.0e38f; ch_tol = 0.f;
           const float qn = vXN[lane];                       // q_{k+1} of this joint
-          ch_over = (aq & 1) ? (qn < ap.rlo[k * RS + lane + 26]) : (qn > ap.rhi[k * RS + lane + 26]);
+          ch_over = (aq & 1) ? (qn < pre.lo_q) : (qn > pre.hi_q);
         }
         if (a & 2) ch_up = fminf(ch_up, -g);
         else ch_lo = fmaxf(ch_lo, -g);
@@ -1336,7 +1418,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
         }
       } else if (ch_on || aq) {
         // joint rate eliminated by the joint limit (own, or carried to here)
-        const float tu = -2.f * md[M_R + lane] * us[k * VS + lane];
+        const float tu = -2.f * md[M_R + lane] * u_k;
         const float yq = tu - m;
         const float tol = ea + er * fmaxf(fabsf(tu), fabsf(m));
         if (ch_on) {
@@ -1419,7 +1501,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
     __syncwarp();
     float mn = 0.f;
     if (k >= 1 && lane < 30)
-      mn = twoQ * (xs[k * VS + lane] - ap.xref[k * VS + lane]) +
+      mn = twoQ * (x_k - xr_k) +
            (lane < NC ? cc_tv(sm + S_AV, pat.ar, vM, lane) : m);
     __syncwarp();
     m = mn;
