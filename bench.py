@@ -58,7 +58,7 @@ BF16_PEAK_TFLOPS = _measured_bf16_peak()
 # DRAM bytes per agent of the fused kernel from the last ncu capture of this
 # kernel version (profiles/mpc_k_fused_mixed16k_2048agents.md); None once the
 # kernel has changed since.
-TRAFFIC_BYTES_PER_AGENT = (87.755008e6 + 160.629504e6) / 2048
+TRAFFIC_BYTES_PER_AGENT = (89.489920e6 + 161.486336e6) / 2048
 
 
 def parse():
