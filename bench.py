@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--no-policy", action="store_true", help="skip the residual-policy measurement")
     ap.add_argument("--precision-agents", type=int, default=48, help="agents per workload sample, precision report")
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="serving run length (0 = skip)")
+    ap.add_argument("--no-tree", action="store_true",
+                    help="diagonal joint model in the torque map instead of RNEA over a kinematic tree")
     ap.add_argument("--serve-rate", default="0.5,1,2",
                     help="request rates, comma-separated, x 16384 agents at 100 Hz")
     return ap.parse_args()
@@ -114,13 +116,26 @@ def job_throughput(n, steps, local_ms, world, device=None):
 
 
 # ------------------------------------------------------------------ inputs
+TREES = True    # agents carry a kinematic tree: the torque map runs RNEA (Eq. rnea)
+
+
+def make_models(name, ids):
+    """(model, inputs of replan 0) of the given agents; with TREES, the model
+    dict also holds each agent's kinematic tree."""
+    from workload import make_agents, make_trees
+    model, inp = make_agents(name, ids)
+    if TREES:
+        model.update(make_trees(name, ids))
+    return model, inp
+
+
 def make_workload(name, n_agents, rank, world, n_replans):
     """Agents of this rank and `n_replans` consecutive replans of them."""
     from workload import make_agents, perturb_inputs, workload_spec
     spec = workload_spec(name)
     n = n_agents or spec["n_agents"]
     ids = shard_ids(n, rank, world)
-    model, inp = make_agents(name, ids)
+    model, inp = make_models(name, ids)
     replans = [inp]
     for r in range(1, n_replans):
         replans.append(perturb_inputs(name, replans[-1], ids, r))
@@ -477,6 +492,8 @@ def run_ours(args):
                    "tuned": tune_report["chosen"] if tune_report else
                    {"variant": args.variant, "check_every": args.check_every, "early_polish": args.early_polish},
                    "replans": "monotone sequence, 100 Hz (phase += 0.02 per replan)",
+                   "torque_map": "RNEA over a seeded 18-joint kinematic tree per agent" if TREES
+                   else "diagonal joint model",
                    "l2": "per-agent working set (~1 GB) >> L2; no flush"},
         "p50_ms": float(np.percentile(per, 50)), "p99_ms": float(np.percentile(per, 99)),
         "latency_budget_ms": 10.0, "per_step_ms": [round(v, 3) for v in per], "cold_solve": cold,
@@ -540,7 +557,7 @@ def precision_report(args, timed, cfg, n, world, mpcgpu):
     samples = {}
     for wl in ("mixed16k", "mixed16k_ill"):
         ids = np.sort(np.random.default_rng(5).choice(16384, na, replace=False))
-        model, inp = make_agents(wl, ids)
+        model, inp = make_models(wl, ids)
         inps = [inp, perturb_inputs(wl, inp, ids, 1)]
         inps = [{k: np.ascontiguousarray(v, np.float32) for k, v in x.items()} for x in inps]
         samples[wl] = (model, inps, [r["tau"] for r, _ in sample_solve(model, inps, 0, 2)])
@@ -586,7 +603,7 @@ def run_serving(args, model, replans, n):
     from workload import make_agents
     # reserve agents that join as others leave (5 % every 100 batches)
     reserve = max(n // 8, 1)
-    rmodel, rinp = make_agents(args.workload, np.arange(n, n + reserve))
+    rmodel, rinp = make_models(args.workload, np.arange(n, n + reserve))
     smodel = {k: np.concatenate([model[k], rmodel[k]]) for k in model}
     sinp = {k: np.concatenate([replans[0][k], np.asarray(rinp[k], np.float32)]) for k in replans[0]}
     out = {}
@@ -613,7 +630,7 @@ def cpu_baseline(name, budget_s=20.0, seed=11):
     cores = len(os.sched_getaffinity(0))
     rng = np.random.default_rng(seed)
     sample = np.sort(rng.choice(spec["n_agents"], max(cores, 8), replace=False))
-    model, inp = make_agents(name, sample)
+    model, inp = make_models(name, sample)
     t0 = time.perf_counter()
     solve_batch(model, inp, processes=min(cores, len(sample)))
     dt = time.perf_counter() - t0
@@ -635,7 +652,7 @@ def run_reference(args):
     times = []
     for i in range(args.warmup + args.steps):
         sample = np.sort(rng.choice(spec["n_agents"], per_step, replace=False))
-        model, inp = make_agents(args.workload, sample)
+        model, inp = make_models(args.workload, sample)
         t0 = time.perf_counter()
         solve_batch(model, inp, processes=min(cores, per_step))
         if i >= args.warmup:
@@ -656,6 +673,7 @@ def run_reference(args):
 
 if __name__ == "__main__":
     a = parse()
+    TREES = not a.no_tree
     if a.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
     if a.impl == "reference":

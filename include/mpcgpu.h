@@ -160,6 +160,25 @@ typedef struct mpc_agent_model {
   double q_nom[18];         /* nominal joint angles */
 } mpc_agent_model;
 
+/* One agent's kinematic tree for the torque map's inverse dynamics (paper
+ * Sec. III-C, Eq. (rnea): M(q) qddot + h(q, qdot) by the recursive
+ * Newton-Euler algorithm).  Host memory, float64; stored as float32.  18
+ * revolute joints in four chains hanging off the floating base, in the
+ * joint order of the state: 0-4 left leg, 5-9 right leg, 10-13 left arm,
+ * 14-17 right arm; a chain's first joint has the base as parent, every other
+ * joint the previous one.  Joint j turns about axis[j] (a unit vector in its
+ * parent link's frame) at offset[j] from the parent frame's origin (the base
+ * frame's origin is the base position p of the state); link j's frame is the
+ * parent's translated to the joint and rotated by q_j about the axis. */
+typedef struct mpc_tree_model {
+  double axis[18][3];
+  double offset[18][3];     /* m */
+  double mass[18];          /* link mass, kg */
+  double com[18][3];        /* link centre of mass in the link frame, m */
+  double inertia[18][3];    /* diagonal of the link's inertia about its centre of mass
+                               in the link frame, kg m^2 */
+} mpc_tree_model;
+
 typedef struct mpc_ctx mpc_ctx;
 
 /* Fill *cfg with the defaults above (device 0, NULL stream, max_agents 16384). */
@@ -181,6 +200,21 @@ mpc_status mpc_set_models(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host
 
 /* Single-agent form of mpc_set_models. */
 mpc_status mpc_set_model(mpc_ctx* ctx, int32_t agent_id, const mpc_agent_model* model_host);
+
+/* Give agents a kinematic tree (trees_host[n], at agent_ids_host[n]): from
+ * the next solve their torque map computes M(q) qddot + h(q, qdot) of Eq.
+ * (rnea) by the recursive Newton-Euler algorithm over the tree, the floating
+ * base moving as the MPC predicts (orientation and angular velocity of x0,
+ * accelerations (x_1 - x_0)/dt of its twist, gravity 9.81 m/s^2 along -z),
+ * in place of the diagonal joint model M_j qddot_j + h_j; the contact term
+ * -J_leg^T W keeps the model's leg Jacobian.  An agent without a tree, or
+ * whose model was uploaded again since (mpc_set_models clears the tree),
+ * uses the diagonal model.  The QP does not depend on the tree.  Synchronous
+ * with respect to the host buffers.  Errors: MPC_ERR_INVALID for a bad count,
+ * an id out of range, a NULL buffer, a non-finite value, an axis that is not
+ * a unit vector (|norm - 1| > 1e-6), a negative mass or inertia. */
+mpc_status mpc_set_trees(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host,
+                         const mpc_tree_model* trees_host);
 
 /* Remove an agent: its slot no longer accepts submissions. */
 mpc_status mpc_release_agent(mpc_ctx* ctx, int32_t agent_id);

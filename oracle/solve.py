@@ -27,7 +27,7 @@ def solve_agent(m: dict, x0, cmd, phase, qd_meas, *, tol_mu=1e-13, tol_res=1e-11
     N = qp.N
     u = np.stack([qp.u(r.z, k) for k in range(N)])
     x = np.vstack([x0[None, :]] + [qp.x(r.z, k)[None, :] for k in range(1, N + 1)])
-    tau, q_set, qd_set = torque.torque_map(m, x0, qd_meas, u[0], u[1])
+    tau, q_set, qd_set = torque.torque_map(m, x0, qd_meas, u[0], u[1], x1=x[1])
     return dict(tau=tau, q_set=q_set, qd_set=qd_set, V=qp.objective(r.z),
                 x=x, u=u, y=r.y.reshape(N, 56), ipm=r, qp=qp, extras=ex)
 

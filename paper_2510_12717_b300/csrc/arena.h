@@ -28,13 +28,21 @@ constexpr int MAXN = 32;
 constexpr int R24 = 24;     // row stride of the dense R24 blocks
 constexpr int BLK = 528;    // floats of one R24 block (22 rows x 24)
 
-// float model record (MODEL_F floats per agent)
+// float model record (MODEL_F floats per agent).  M_TREE_ON != 0 marks an
+// agent whose torque map runs the recursive Newton-Euler algorithm over its
+// kinematic tree, stored from M_TREE on: per joint j (TREE_J floats at
+// M_TREE + TREE_J j) the axis (3, parent frame), the joint's offset from the
+// parent frame's origin (3), the link mass, its centre of mass (3, link
+// frame) and the diagonal of its inertia about the centre of mass (3).
+// Uploading a model clears both (mpc_set_models writes the whole record).
 enum : int {
   M_MASS = 0, M_INVM = 1, M_INERTIA = 2, M_LEVER = 5, M_JLEG = 11,   // J_leg[f][r][j] at 11 + 30f + 5r + j
   M_MJ = 71, M_HJ = 89, M_KP = 107, M_KD = 125, M_Q = 143, M_R = 173,
   M_MU = 203, M_FZMAX = 204, M_QDMAX = 205, M_QLIM = 206, M_DT = 207,
-  M_QNOM = 208, MODEL_F = 256
+  M_QNOM = 208, M_TREE_ON = 226, M_TREE = 256, MODEL_F = 512
 };
+enum : int { TREE_J = 13, TREE_F = 18 * TREE_J, TA_AXIS = 0, TA_OFF = 3, TA_MASS = 6, TA_COM = 7, TA_INER = 10 };
+static_assert(M_TREE + TREE_F <= MODEL_F, "tree record exceeds the model record");
 // double schedule record (SCHED_D doubles per agent)
 enum : int { S_DT = 0, S_PERIOD = 1, S_DUTY = 2, S_OFF = 4, SCHED_D = 8 };
 // per-agent input record (IN_F floats): x0, qd_meas, cmd, phase

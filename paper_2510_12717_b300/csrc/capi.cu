@@ -2,6 +2,7 @@
 // Declarations and argument conventions: include/mpcgpu.h.
 #include <cuda_runtime.h>
 #include <math.h>
+#include <cmath>
 #include <stdio.h>
 #include <string.h>
 
@@ -326,6 +327,15 @@ static void pack_model(const mpc_agent_model& m, float* f, double* s) {
 
 }  // extern "C"
 
+// scatter packed kinematic trees into their agents' model records and mark them
+__global__ void mpc_k_scatter_trees(int n, const int* ids, const float* tf, float* model) {
+  const int row = blockIdx.x;
+  if (row >= n) return;
+  float* rec = model + (size_t)ids[row] * mpc::MODEL_F;
+  for (int t = threadIdx.x; t < mpc::TREE_F; t += blockDim.x) rec[mpc::M_TREE + t] = tf[(size_t)row * mpc::TREE_F + t];
+  if (threadIdx.x == 0) rec[mpc::M_TREE_ON] = 1.f;
+}
+
 // scatter packed models into their slots, clear warm starts
 __global__ void mpc_k_scatter_models(int n, const int* ids, const float* mf, const double* ms, const int* hz,
                                      float* model, double* sched, int* horizon, int* warm) {
@@ -370,6 +380,54 @@ mpc_status mpc_set_models(mpc_ctx* ctx, int32_t n, const int32_t* ids, const mpc
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < n; ++i) ctx->live[ids[i]] = hz[i];
+  return MPC_OK;
+}
+
+static const char* check_tree(const mpc_tree_model& t) {
+  for (int j = 0; j < 18; ++j) {
+    double nn = 0.0;
+    for (int c = 0; c < 3; ++c) {
+      if (!std::isfinite(t.axis[j][c]) || !std::isfinite(t.offset[j][c]) || !std::isfinite(t.com[j][c]) ||
+          !std::isfinite(t.inertia[j][c]))
+        return "non-finite tree value";
+      if (t.inertia[j][c] < 0.0) return "negative link inertia";
+      nn += t.axis[j][c] * t.axis[j][c];
+    }
+    if (std::fabs(std::sqrt(nn) - 1.0) > 1e-6) return "joint axis is not a unit vector";
+    if (!std::isfinite(t.mass[j]) || t.mass[j] < 0.0) return "bad link mass";
+  }
+  return nullptr;
+}
+
+mpc_status mpc_set_trees(mpc_ctx* ctx, int32_t n, const int32_t* ids, const mpc_tree_model* trees) {
+  if (!ctx) return MPC_ERR_INVALID;
+  if (n < 0 || n > ctx->cfg.max_agents || (n > 0 && (!ids || !trees)))
+    return fail(ctx, MPC_ERR_INVALID, "set_trees: bad count or NULL buffer");
+  if (n == 0) return MPC_OK;
+  using namespace mpc;
+  std::vector<float> tf((size_t)n * TREE_F);
+  for (int i = 0; i < n; ++i) {
+    if (ids[i] < 0 || ids[i] >= ctx->cfg.max_agents) return fail(ctx, MPC_ERR_INVALID, "set_trees: agent id out of range");
+    const char* why = check_tree(trees[i]);
+    if (why) return fail(ctx, MPC_ERR_INVALID, std::string("set_trees: ") + why);
+    float* f = &tf[(size_t)i * TREE_F];
+    for (int j = 0; j < 18; ++j) {
+      float* J = f + j * TREE_J;
+      for (int c = 0; c < 3; ++c) {
+        J[TA_AXIS + c] = (float)trees[i].axis[j][c];
+        J[TA_OFF + c] = (float)trees[i].offset[j][c];
+        J[TA_COM + c] = (float)trees[i].com[j][c];
+        J[TA_INER + c] = (float)trees[i].inertia[j][c];
+      }
+      J[TA_MASS] = (float)trees[i].mass[j];
+    }
+  }
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaMemcpyAsync(ctx->d_ids, ids, sizeof(int) * n, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaMemcpyAsync(ctx->d_mstage, tf.data(), sizeof(float) * tf.size(), cudaMemcpyHostToDevice, ctx->stream));
+  mpc_k_scatter_trees<<<n, 128, 0, ctx->stream>>>(n, ctx->d_ids, ctx->d_mstage, ctx->model);
+  CK(cudaGetLastError());
+  CK(cudaStreamSynchronize(ctx->stream));
   return MPC_OK;
 }
 

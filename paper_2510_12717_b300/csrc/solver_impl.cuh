@@ -1791,19 +1791,131 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
 
 // ============================================================ torque map (A7)
 // q_MPC = x0.q; qdot_MPC = u_0.qdot; qddot = (u_1.qdot - u_0.qdot)/dt;
-// tau = K_p (q_MPC - q) + K_d (qdot_MPC - qdot) + M qddot + h - J_leg^T W
-// (Eqs. rnea, mpc_torque); value = QP objective at the solution.
+// tau = K_p (q_MPC - q) + K_d (qdot_MPC - qdot) + [M qddot + h] - J_leg^T W
+// (Eqs. rnea, mpc_torque); value = QP objective at the solution.  M qddot + h
+// comes from the recursive Newton-Euler algorithm over the agent's kinematic
+// tree when it has one, else from the diagonal joint model M_j qddot_j + h_j.
+
+// 3-vector helpers of the Newton-Euler recursion
+struct V3 { float x, y, z; };
+__device__ __forceinline__ V3 v3(float x, float y, float z) { V3 r; r.x = x; r.y = y; r.z = z; return r; }
+__device__ __forceinline__ V3 operator+(V3 a, V3 b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ V3 operator*(float s, V3 a) { return v3(s * a.x, s * a.y, s * a.z); }
+__device__ __forceinline__ V3 cross(V3 a, V3 b) {
+  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ float dot(V3 a, V3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3 mv3(const M3& R, V3 a) {
+  return v3(R.m[0] * a.x + R.m[1] * a.y + R.m[2] * a.z, R.m[3] * a.x + R.m[4] * a.y + R.m[5] * a.z,
+            R.m[6] * a.x + R.m[7] * a.y + R.m[8] * a.z);
+}
+__device__ __forceinline__ V3 mtv3(const M3& R, V3 a) {   // R^T a
+  return v3(R.m[0] * a.x + R.m[3] * a.y + R.m[6] * a.z, R.m[1] * a.x + R.m[4] * a.y + R.m[7] * a.z,
+            R.m[2] * a.x + R.m[5] * a.y + R.m[8] * a.z);
+}
+__device__ __forceinline__ V3 ld3(const float* p) { return v3(p[0], p[1], p[2]); }
+
+// Inverse dynamics of one chain of the tree (joints j0 .. j0+len-1, the
+// first hanging off the base) by the recursive Newton-Euler algorithm in
+// world coordinates (Luh, Walker and Paul 1980; Featherstone 2008, Ch. 5):
+// outward, each link's rotation, angular velocity and acceleration, the
+// acceleration of its joint origin and of its centre of mass; inward, the
+// force and moment each link transmits to its parent, the joint torque being
+// the moment's component along the joint axis.  The base's motion is given:
+// rotation Rb, angular velocity wb, angular acceleration dwb and linear
+// acceleration ab of its origin, gravity folded into ab as an upward
+// acceleration.  tau[t] receives the torque of joint j0 + t.
+__device__ __noinline__ void chain_rnea(const float* tr, int j0, int len, const M3& Rb, V3 wb, V3 dwb, V3 ab,
+                                        const float* q, const float* qd, const float* qdd, float* tau) {
+  V3 z[5], d[5], rc[5], F[5], Nm[5];
+  M3 R = Rb;
+  V3 w = wb, al = dwb, acc = ab;
+  for (int t = 0; t < len; ++t) {
+    const float* J = tr + (j0 + t) * TREE_J;
+    const V3 ax = ld3(J + TA_AXIS);
+    d[t] = mv3(R, ld3(J + TA_OFF));                    // parent origin -> joint origin
+    acc = acc + cross(al, d[t]) + cross(w, cross(w, d[t]));
+    z[t] = mv3(R, ax);
+    const V3 wj = qd[t] * z[t];
+    al = al + qdd[t] * z[t] + cross(w, wj);
+    w = w + wj;
+    // R <- R Rot(ax, q): Rodrigues
+    const float c = cosf(q[t]), s = sinf(q[t]), k = 1.f - c;
+    M3 Rj;
+    Rj.m[0] = c + k * ax.x * ax.x;         Rj.m[1] = k * ax.x * ax.y - s * ax.z; Rj.m[2] = k * ax.x * ax.z + s * ax.y;
+    Rj.m[3] = k * ax.y * ax.x + s * ax.z;  Rj.m[4] = c + k * ax.y * ax.y;        Rj.m[5] = k * ax.y * ax.z - s * ax.x;
+    Rj.m[6] = k * ax.z * ax.x - s * ax.y;  Rj.m[7] = k * ax.z * ax.y + s * ax.x; Rj.m[8] = c + k * ax.z * ax.z;
+    R = mul3(R, Rj);
+    const float m = J[TA_MASS];
+    rc[t] = mv3(R, ld3(J + TA_COM));                   // joint origin -> centre of mass
+    const V3 ac = acc + cross(al, rc[t]) + cross(w, cross(w, rc[t]));
+    F[t] = m * ac;
+    // N = I_w al + w x (I_w w), I_w = R diag(I) R^T
+    const V3 Id = ld3(J + TA_INER);
+    const V3 bl = mtv3(R, al), bw = mtv3(R, w);
+    const V3 Ial = mv3(R, v3(Id.x * bl.x, Id.y * bl.y, Id.z * bl.z));
+    const V3 Iw = mv3(R, v3(Id.x * bw.x, Id.y * bw.y, Id.z * bw.z));
+    Nm[t] = Ial + cross(w, Iw);
+  }
+  V3 f = v3(0.f, 0.f, 0.f), n = v3(0.f, 0.f, 0.f);
+  for (int t = len - 1; t >= 0; --t) {
+    // moment about joint t's origin: its own link's, plus the child's
+    // (transmitted from the child's joint origin, d[t+1] away)
+    V3 nt = Nm[t] + cross(rc[t], F[t]) + n;
+    if (t + 1 < len) nt = nt + cross(d[t + 1], f);
+    f = F[t] + f;
+    n = nt;
+    tau[t] = dot(z[t], nt);
+  }
+}
+
 __device__ __noinline__ void torque_map(const AgentPtrs& ap, int lane) {
   const int N = ap.N;
   const float* md = ap.mdl;
   const float dt = md[M_DT];
+  // M qddot + h of joint `lane` (lanes 0-17)
+  float inv = 0.f;
+  if (md[M_TREE_ON] != 0.f) {
+    // lane c < 4 runs chain c (left leg, right leg, left arm, right arm); the
+    // base moves as the MPC predicts: orientation and angular velocity of x0,
+    // accelerations (x_1 - x_0)/dt of the twist
+    float tl[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (lane < 4) {
+      const int j0 = lane < 2 ? 5 * lane : 10 + 4 * (lane - 2), len = lane < 2 ? 5 : 4;
+      const float* x0 = ap.inp + I_X0;
+      const float* x1 = ap.x + VS;
+      const float cr = cosf(x0[3]), sr = sinf(x0[3]), cp = cosf(x0[4]), sp = sinf(x0[4]);
+      const float cy = cosf(x0[5]), sy = sinf(x0[5]);
+      const M3 Rb = {{cy * cp, cy * sp * sr - sy * cr, cy * sp * cr + sy * sr,
+                      sy * cp, sy * sp * sr + cy * cr, sy * sp * cr - cy * sr,
+                      -sp, cp * sr, cp * cr}};
+      const float idt = 1.f / dt;
+      const V3 wb = v3(x0[9], x0[10], x0[11]);
+      const V3 dwb = v3((x1[9] - x0[9]) * idt, (x1[10] - x0[10]) * idt, (x1[11] - x0[11]) * idt);
+      const V3 ab = v3((x1[6] - x0[6]) * idt, (x1[7] - x0[7]) * idt, (x1[8] - x0[8]) * idt + GRAV);
+      float q[5], qd[5], qdd[5];
+      for (int t = 0; t < len; ++t) {
+        q[t] = x0[12 + j0 + t];
+        qd[t] = ap.u[12 + j0 + t];
+        qdd[t] = (ap.u[VS + 12 + j0 + t] - qd[t]) * idt;
+      }
+      chain_rnea(md + M_TREE, j0, len, Rb, wb, dwb, ab, q, qd, qdd, tl);
+    }
+    const int c = lane < 10 ? lane / 5 : (lane < 14 ? 2 : 3);
+    const int t = lane < 10 ? lane % 5 : (lane < 14 ? lane - 10 : lane - 14);
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+      const float v = __shfl_sync(FULL, tl[i], c);
+      if (i == t) inv = v;
+    }
+  } else if (lane < 18) {
+    inv = md[M_MJ + lane] * ((ap.u[VS + 12 + lane] - ap.u[12 + lane]) / dt) + md[M_HJ + lane];
+  }
   if (lane < 18) {
     const int j = lane;
     const float q = ap.inp[I_X0 + 12 + j];
     const float qd0 = ap.u[12 + j];
-    const float qd1 = ap.u[VS + 12 + j];
-    float tau = md[M_KP + j] * (q - q) + md[M_KD + j] * (qd0 - ap.inp[I_QD + j]) +
-                md[M_MJ + j] * ((qd1 - qd0) / dt) + md[M_HJ + j];
+    float tau = md[M_KP + j] * (q - q) + md[M_KD + j] * (qd0 - ap.inp[I_QD + j]) + inv;
     if (j < 10) {
       const int f = j / 5, jj = j - 5 * f;
       for (int r = 0; r < 6; ++r) tau -= md[M_JLEG + 30 * f + 5 * r + jj] * ap.u[6 * f + r];

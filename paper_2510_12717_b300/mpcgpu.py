@@ -60,6 +60,31 @@ MODEL_DTYPE = np.dtype([
     ("offset", "f8", 2), ("q_nom", "f8", 18),
 ], align=True)
 
+class MpcTreeModel(C.Structure):
+    _fields_ = [
+        ("axis", (C.c_double * 3) * 18), ("offset", (C.c_double * 3) * 18), ("mass", C.c_double * 18),
+        ("com", (C.c_double * 3) * 18), ("inertia", (C.c_double * 3) * 18),
+    ]
+
+
+# numpy mirror of mpc_tree_model; field name -> key of the model dict (workload.make_trees)
+TREE_DTYPE = np.dtype([("axis", "f8", (18, 3)), ("offset", "f8", (18, 3)), ("mass", "f8", 18),
+                       ("com", "f8", (18, 3)), ("inertia", "f8", (18, 3))], align=True)
+TREE_KEYS = {"axis": "tree_axis", "offset": "tree_offset", "mass": "tree_mass", "com": "tree_com",
+             "inertia": "tree_inertia"}
+
+
+def pack_trees(trees: dict, idx=None) -> np.ndarray:
+    """Tree arrays (tree_axis, tree_offset, tree_mass, tree_com, tree_inertia)
+    -> mpc_tree_model array."""
+    B = len(trees["tree_mass"])
+    idx = np.arange(B) if idx is None else np.asarray(idx)
+    out = np.zeros(len(idx), dtype=TREE_DTYPE)
+    for name, key in TREE_KEYS.items():
+        out[name] = np.asarray(trees[key])[idx]
+    return out
+
+
 # every function the header declares: name -> (restype, argtypes)
 _P, _I32P, _U64P = C.c_void_p, C.c_void_p, C.POINTER(C.c_uint64)
 SIGNATURES = {
@@ -83,6 +108,7 @@ SIGNATURES = {
     "mpc_last_error": (C.c_char_p, [_P]),
     "mpc_set_policy": (C.c_int, [_P, _P, _P, _P, _P, _P, _P, _P, _P, C.c_float]),
     "mpc_policy_torques": (C.c_int, [_P, C.c_uint64, _P, _P]),
+    "mpc_set_trees": (C.c_int, [_P, C.c_int32, _P, _P]),
     "mpc_measure_peak": (C.c_int, [C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
 }
 
@@ -201,10 +227,21 @@ class Solver:
 
     # -- models
     def set_models(self, model: dict, agent_ids, idx=None):
+        """mpc_set_models; when the model dict also holds kinematic trees
+        (tree_* keys, workload.make_trees), mpc_set_trees for the same agents."""
         recs = pack_models(model, idx)
         ids = np.ascontiguousarray(agent_ids, dtype=np.int32)
         assert len(ids) == len(recs)
         self._check(self.lib.mpc_set_models(self.ctx, len(ids), _ptr(ids), recs.ctypes.data))
+        if "tree_axis" in model:
+            self.set_trees(model, ids, idx)
+
+    def set_trees(self, trees: dict, agent_ids, idx=None):
+        """mpc_set_trees: kinematic trees for the agents' torque maps."""
+        recs = pack_trees(trees, idx)
+        ids = np.ascontiguousarray(agent_ids, dtype=np.int32)
+        assert len(ids) == len(recs)
+        self._check(self.lib.mpc_set_trees(self.ctx, len(ids), _ptr(ids), recs.ctypes.data))
 
     def release(self, agent_id: int):
         self._check(self.lib.mpc_release_agent(self.ctx, int(agent_id)))

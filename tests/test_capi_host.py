@@ -43,6 +43,19 @@ def test_struct_layouts_match(lib):
     assert mpcgpu.MODEL_DTYPE.itemsize == C.sizeof(mpcgpu.MpcAgentModel)
     for name in mpcgpu.MODEL_DTYPE.names:
         assert mpcgpu.MODEL_DTYPE.fields[name][1] == getattr(mpcgpu.MpcAgentModel, name).offset, name
+    assert mpcgpu.TREE_DTYPE.itemsize == C.sizeof(mpcgpu.MpcTreeModel)
+    for name in mpcgpu.TREE_DTYPE.names:
+        assert mpcgpu.TREE_DTYPE.fields[name][1] == getattr(mpcgpu.MpcTreeModel, name).offset, name
+
+
+def test_pack_trees_roundtrip():
+    from paper_2510_12717_b300 import mpcgpu
+    from workload import make_trees
+    t = make_trees("small", np.arange(3))
+    recs = mpcgpu.pack_trees(t, [2, 0])
+    np.testing.assert_array_equal(recs["axis"][0], t["tree_axis"][2])
+    np.testing.assert_array_equal(recs["inertia"][1], t["tree_inertia"][0])
+    assert np.allclose(np.linalg.norm(recs["axis"], axis=-1), 1.0)
 
 
 def test_default_config_and_argument_errors(lib):
@@ -70,6 +83,7 @@ def test_default_config_and_argument_errors(lib):
     assert lib.mpc_create(C.byref(bad), C.byref(h)) == mpcgpu.MPC_ERR_BUDGET
     assert lib.mpc_destroy(None) == mpcgpu.MPC_ERR_INVALID
     assert lib.mpc_last_error(None) == b"NULL context"
+    assert lib.mpc_set_trees(None, 0, None, None) == mpcgpu.MPC_ERR_INVALID
     tf = C.c_double(0.0)
     assert lib.mpc_measure_peak(9, None, C.byref(tf), None) == mpcgpu.MPC_ERR_INVALID
     assert lib.mpc_measure_peak(mpcgpu.PEAK_FP32_FMA, None, None, None) == mpcgpu.MPC_ERR_INVALID

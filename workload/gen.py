@@ -213,3 +213,66 @@ def make_policy(seed: int = 2510_12717 + 100) -> dict:
         out[f"W{layer + 1}"] = (g.standard_normal((fan_in, fan_out)) / np.sqrt(fan_in)).astype(np.float32)
         out[f"b{layer + 1}"] = (0.01 * g.standard_normal(fan_out)).astype(np.float32)
     return out
+
+
+# ---------------------------------------------------------------- kinematic trees
+# 18 revolute joints in four chains hanging off the floating base: (first
+# joint, length) of the left leg, right leg, left arm, right arm.  A chain's
+# first joint has the base as parent, every other joint the previous one.
+TREE_CHAINS = ((0, 5), (5, 5), (10, 4), (14, 4))
+_TREE_STREAM = 1 << 20
+_LEG_AXES = ((0.0, 0.0, 1.0), (1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 1.0, 0.0), (0.0, 1.0, 0.0))
+_ARM_AXES = ((0.0, 1.0, 0.0), (1.0, 0.0, 0.0), (0.0, 0.0, 1.0), (0.0, 1.0, 0.0))
+
+
+def make_trees(name: str, agent_ids=None) -> dict:
+    """Seeded synthetic kinematic trees, one per agent (the robot's model
+    files are not available).  Per joint j: axis (unit vector in its parent
+    link's frame, a hip/knee/ankle or shoulder/elbow pattern tilted by up to
+    0.1 per component), offset of the joint from the parent frame's origin
+    (legs: hip at (0, +-0.1, -0.1), thigh and shank 0.3-0.4 m; arms: shoulder
+    at (0, +-0.2, 0.3), upper arm 0.2-0.3 m), link mass (legs 0.5-5 kg, arms
+    0.5-1.5 kg), centre of mass in the link frame, and the diagonal of the
+    link's rotational inertia about its centre of mass.  Random draws only."""
+    spec = workload_spec(name)
+    if agent_ids is None:
+        agent_ids = np.arange(spec["n_agents"])
+    agent_ids = np.asarray(agent_ids, dtype=np.int64)
+    B = len(agent_ids)
+    axis = np.zeros((B, NJ, 3))
+    offset = np.zeros((B, NJ, 3))
+    mass = np.zeros((B, NJ))
+    com = np.zeros((B, NJ, 3))
+    inertia = np.zeros((B, NJ, 3))
+    seed = SEED_BASE + spec["idx"]
+    leg_mass = ((1.0, 2.0), (1.0, 2.0), (3.0, 5.0), (2.0, 4.0), (0.5, 1.0))
+    for a, aid in enumerate(agent_ids):
+        g = agent_rng(seed, int(aid), stream=_TREE_STREAM)
+        for c, (j0, length) in enumerate(TREE_CHAINS):
+            side = 1.0 if c % 2 == 0 else -1.0
+            leg = c < 2
+            for t in range(length):
+                j = j0 + t
+                ax = np.array(_LEG_AXES[t] if leg else _ARM_AXES[t]) + g.uniform(-0.1, 0.1, 3)
+                axis[a, j] = ax / np.linalg.norm(ax)
+                if leg:
+                    if t == 0:
+                        offset[a, j] = (g.uniform(-0.02, 0.02), side * g.uniform(0.08, 0.12), g.uniform(-0.12, -0.08))
+                    elif t < 3:
+                        offset[a, j] = (0.0, 0.0, -g.uniform(0.03, 0.06))
+                    else:
+                        offset[a, j] = (0.0, 0.0, -g.uniform(0.3, 0.4))
+                    mass[a, j] = g.uniform(*leg_mass[t])
+                    com[a, j] = (g.uniform(-0.02, 0.02), g.uniform(-0.02, 0.02), -g.uniform(0.02, 0.2))
+                    inertia[a, j] = g.uniform(0.002, 0.05, 3)
+                else:
+                    if t == 0:
+                        offset[a, j] = (g.uniform(-0.02, 0.02), side * g.uniform(0.18, 0.22), g.uniform(0.25, 0.35))
+                    elif t < 3:
+                        offset[a, j] = (0.0, side * g.uniform(0.0, 0.03), -g.uniform(0.02, 0.05))
+                    else:
+                        offset[a, j] = (0.0, 0.0, -g.uniform(0.2, 0.3))
+                    mass[a, j] = g.uniform(0.5, 1.5)
+                    com[a, j] = (g.uniform(-0.02, 0.02), g.uniform(-0.02, 0.02), -g.uniform(0.02, 0.15))
+                    inertia[a, j] = g.uniform(0.001, 0.02, 3)
+    return dict(tree_axis=axis, tree_offset=offset, tree_mass=mass, tree_com=com, tree_inertia=inertia)
