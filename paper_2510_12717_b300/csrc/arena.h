@@ -117,6 +117,8 @@ struct SolverParams {
   int precision;   // factor precision: PREC_FP32 / PREC_TF32 / PREC_BF16 / PREC_FP64
   int refine;      // iterative-refinement steps on a polish from the previous active set
   int refine_admm; // ... and on a polish that follows ADMM iterations
+  int trees;       // 1: some agent has a kinematic tree; mpc_k_rnea runs after the solve
+  int split;       // fused form: 1 = set-up and torque map as kernels of their own
 };
 
 }  // namespace mpc

@@ -37,7 +37,7 @@ struct GraphEntry {
   int n = -1;
   const void* ptrs[5] = {};
   cudaStream_t stream = nullptr;
-  int variant = 0, check_every = 0;
+  int variant = 0, check_every = 0, trees = 0;
   float early_polish = 0.f;
   cudaGraphExec_t exec = nullptr;
 };
@@ -78,6 +78,7 @@ struct mpc_ctx {
   // residual policy (mpc_set_policy): bfloat16 weights, FP32 biases
   mpc::PolicyDev pol{};
   bool has_policy = false;
+  bool has_trees = false;            // some agent was given a kinematic tree (mpc_set_trees)
   std::string err = "ok";
 };
 
@@ -428,6 +429,7 @@ mpc_status mpc_set_trees(mpc_ctx* ctx, int32_t n, const int32_t* ids, const mpc_
   mpc_k_scatter_trees<<<n, 128, 0, ctx->stream>>>(n, ctx->d_ids, ctx->d_mstage, ctx->model);
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->stream));
+  ctx->has_trees = true;
   return MPC_OK;
 }
 
@@ -493,12 +495,15 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   const bool low = c.precision == MPC_TF32 || c.precision == MPC_BF16;
   p.refine = c.refine_steps >= 0 ? c.refine_steps : (low ? 1 : 0);
   p.refine_admm = c.refine_steps >= 0 ? c.refine_steps : 1;
+  p.trees = 0;
+  p.split = 1;
   return p;
 }
 
 static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
   int launches = 0;
-  const mpc::SolverParams prm = params_of(ctx->cfg);
+  mpc::SolverParams prm = params_of(ctx->cfg);
+  prm.trees = ctx->has_trees ? 1 : 0;
   const int form = ctx->cfg.form;
   // graph capture needs a non-default stream; on the legacy stream the
   // solve is launched directly
@@ -512,9 +517,9 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
     GraphEntry& g = ctx->graphs[gi];
     if (g.exec && g.n == tk->b.n && g.stream == st && g.variant == ctx->cfg.variant &&
         g.check_every == ctx->cfg.check_every && g.early_polish == ctx->cfg.early_polish &&
-        !memcmp(g.ptrs, ptrs, sizeof(ptrs))) {
+        g.trees == prm.trees && !memcmp(g.ptrs, ptrs, sizeof(ptrs))) {
       ctx->graph_replays += 1;
-      ctx->launches += 2;   // the order and fused kernels of the graph
+      ctx->launches += 2 + prm.trees;   // the order and fused kernels of the graph (+ the RNEA kernel)
       return cudaGraphLaunch(g.exec, st);
     }
   }
@@ -552,6 +557,7 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
   g.variant = ctx->cfg.variant;
   g.check_every = ctx->cfg.check_every;
   g.early_polish = ctx->cfg.early_polish;
+  g.trees = prm.trees;
   ctx->launches += launches;
   return cudaGraphLaunch(g.exec, st);
 }
@@ -725,7 +731,8 @@ mpc_status mpc_autotune(mpc_ctx* ctx, uint64_t ticket, int32_t repeats, char* re
     ctx->cfg.check_every = cands[i].check_every;
     ctx->cfg.early_polish = cands[i].early;
     ctx->cfg.graph = 0;
-    const mpc::SolverParams prm = params_of(ctx->cfg);
+    mpc::SolverParams prm = params_of(ctx->cfg);
+    prm.trees = ctx->has_trees ? 1 : 0;
     int launches = 0;
     // one untimed pass (warm starts from this candidate), then timed passes
     CK(mpc::launch_solve(ctx->ar, tk->b, prm, ctx->cfg.form, 0, ctx->stream, &launches, ctx->cfg.variant));

@@ -1794,7 +1794,10 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
 // tau = K_p (q_MPC - q) + K_d (qdot_MPC - qdot) + [M qddot + h] - J_leg^T W
 // (Eqs. rnea, mpc_torque); value = QP objective at the solution.  M qddot + h
 // comes from the recursive Newton-Euler algorithm over the agent's kinematic
-// tree when it has one, else from the diagonal joint model M_j qddot_j + h_j.
+// tree when it has one (mpc_k_rnea, a kernel of its own after the solve: run
+// once per agent inside the persistent kernel its code was always cold in the
+// instruction cache, 5x its cost alone), else from the diagonal joint model
+// M_j qddot_j + h_j.
 
 // 3-vector helpers of the Newton-Euler recursion
 struct V3 { float x, y, z; };
@@ -1827,9 +1830,12 @@ __device__ __forceinline__ V3 ld3(const float* p) { return v3(p[0], p[1], p[2]);
 // acceleration.  tau[t] receives the torque of joint j0 + t.
 __device__ __noinline__ void chain_rnea(const float* tr, int j0, int len, const M3& Rb, V3 wb, V3 dwb, V3 ab,
                                         const float* q, const float* qd, const float* qdd, float* tau) {
+  // compact loops (not unrolled): this runs once per agent, and unrolled
+  // straight-line code here costs more in instruction fetch than in arithmetic
   V3 z[5], d[5], rc[5], F[5], Nm[5];
   M3 R = Rb;
   V3 w = wb, al = dwb, acc = ab;
+#pragma unroll 1
   for (int t = 0; t < len; ++t) {
     const float* J = tr + (j0 + t) * TREE_J;
     const V3 ax = ld3(J + TA_AXIS);
@@ -1839,13 +1845,25 @@ __device__ __noinline__ void chain_rnea(const float* tr, int j0, int len, const 
     const V3 wj = qd[t] * z[t];
     al = al + qdd[t] * z[t] + cross(w, wj);
     w = w + wj;
-    // R <- R Rot(ax, q): Rodrigues
-    const float c = cosf(q[t]), s = sinf(q[t]), k = 1.f - c;
-    M3 Rj;
-    Rj.m[0] = c + k * ax.x * ax.x;         Rj.m[1] = k * ax.x * ax.y - s * ax.z; Rj.m[2] = k * ax.x * ax.z + s * ax.y;
-    Rj.m[3] = k * ax.y * ax.x + s * ax.z;  Rj.m[4] = c + k * ax.y * ax.y;        Rj.m[5] = k * ax.y * ax.z - s * ax.x;
-    Rj.m[6] = k * ax.z * ax.x - s * ax.y;  Rj.m[7] = k * ax.z * ax.y + s * ax.x; Rj.m[8] = c + k * ax.z * ax.z;
-    R = mul3(R, Rj);
+    // R <- R Rot(ax, q) (Rodrigues): column c of the product is R (Rot e_c)
+    float s, c;
+    sincosf(q[t], &s, &c);
+    const float k = 1.f - c;
+    M3 Rn;
+#pragma unroll 1
+    for (int col = 0; col < 3; ++col) {
+      const float e0 = col == 0, e1 = col == 1, e2 = col == 2;
+      // Rot e = c e + s (ax x e) + k (ax . e) ax
+      const float ad = ax.x * e0 + ax.y * e1 + ax.z * e2;
+      const V3 rcol = v3(c * e0 + s * (ax.y * e2 - ax.z * e1) + k * ad * ax.x,
+                         c * e1 + s * (ax.z * e0 - ax.x * e2) + k * ad * ax.y,
+                         c * e2 + s * (ax.x * e1 - ax.y * e0) + k * ad * ax.z);
+      const V3 o = mv3(R, rcol);
+      Rn.m[col] = o.x;
+      Rn.m[3 + col] = o.y;
+      Rn.m[6 + col] = o.z;
+    }
+    R = Rn;
     const float m = J[TA_MASS];
     rc[t] = mv3(R, ld3(J + TA_COM));                   // joint origin -> centre of mass
     const V3 ac = acc + cross(al, rc[t]) + cross(w, cross(w, rc[t]));
@@ -1857,14 +1875,15 @@ __device__ __noinline__ void chain_rnea(const float* tr, int j0, int len, const 
     const V3 Iw = mv3(R, v3(Id.x * bw.x, Id.y * bw.y, Id.z * bw.z));
     Nm[t] = Ial + cross(w, Iw);
   }
-  V3 f = v3(0.f, 0.f, 0.f), n = v3(0.f, 0.f, 0.f);
+  V3 f = v3(0.f, 0.f, 0.f), n = v3(0.f, 0.f, 0.f), dn = v3(0.f, 0.f, 0.f);
+#pragma unroll 1
   for (int t = len - 1; t >= 0; --t) {
     // moment about joint t's origin: its own link's, plus the child's
-    // (transmitted from the child's joint origin, d[t+1] away)
-    V3 nt = Nm[t] + cross(rc[t], F[t]) + n;
-    if (t + 1 < len) nt = nt + cross(d[t + 1], f);
+    // (transmitted from the child's joint origin, dn = d[t+1] away)
+    const V3 nt = Nm[t] + cross(rc[t], F[t]) + n + cross(dn, f);
     f = F[t] + f;
     n = nt;
+    dn = d[t];
     tau[t] = dot(z[t], nt);
   }
 }
@@ -1873,41 +1892,11 @@ __device__ __noinline__ void torque_map(const AgentPtrs& ap, int lane) {
   const int N = ap.N;
   const float* md = ap.mdl;
   const float dt = md[M_DT];
-  // M qddot + h of joint `lane` (lanes 0-17)
+  // M qddot + h of joint `lane` (lanes 0-17): the diagonal joint model, or,
+  // for an agent with a kinematic tree, nothing here: mpc_k_rnea adds the
+  // tree's inverse dynamics after the solve
   float inv = 0.f;
   if (md[M_TREE_ON] != 0.f) {
-    // lane c < 4 runs chain c (left leg, right leg, left arm, right arm); the
-    // base moves as the MPC predicts: orientation and angular velocity of x0,
-    // accelerations (x_1 - x_0)/dt of the twist
-    float tl[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-    if (lane < 4) {
-      const int j0 = lane < 2 ? 5 * lane : 10 + 4 * (lane - 2), len = lane < 2 ? 5 : 4;
-      const float* x0 = ap.inp + I_X0;
-      const float* x1 = ap.x + VS;
-      const float cr = cosf(x0[3]), sr = sinf(x0[3]), cp = cosf(x0[4]), sp = sinf(x0[4]);
-      const float cy = cosf(x0[5]), sy = sinf(x0[5]);
-      const M3 Rb = {{cy * cp, cy * sp * sr - sy * cr, cy * sp * cr + sy * sr,
-                      sy * cp, sy * sp * sr + cy * cr, sy * sp * cr - cy * sr,
-                      -sp, cp * sr, cp * cr}};
-      const float idt = 1.f / dt;
-      const V3 wb = v3(x0[9], x0[10], x0[11]);
-      const V3 dwb = v3((x1[9] - x0[9]) * idt, (x1[10] - x0[10]) * idt, (x1[11] - x0[11]) * idt);
-      const V3 ab = v3((x1[6] - x0[6]) * idt, (x1[7] - x0[7]) * idt, (x1[8] - x0[8]) * idt + GRAV);
-      float q[5], qd[5], qdd[5];
-      for (int t = 0; t < len; ++t) {
-        q[t] = x0[12 + j0 + t];
-        qd[t] = ap.u[12 + j0 + t];
-        qdd[t] = (ap.u[VS + 12 + j0 + t] - qd[t]) * idt;
-      }
-      chain_rnea(md + M_TREE, j0, len, Rb, wb, dwb, ab, q, qd, qdd, tl);
-    }
-    const int c = lane < 10 ? lane / 5 : (lane < 14 ? 2 : 3);
-    const int t = lane < 10 ? lane % 5 : (lane < 14 ? lane - 10 : lane - 14);
-#pragma unroll
-    for (int i = 0; i < 5; ++i) {
-      const float v = __shfl_sync(FULL, tl[i], c);
-      if (i == t) inv = v;
-    }
   } else if (lane < 18) {
     inv = md[M_MJ + lane] * ((ap.u[VS + 12 + lane] - ap.u[12 + lane]) / dt) + md[M_HJ + lane];
   }
@@ -2027,12 +2016,18 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_fused(Arena 
     const int row = b.order ? b.order[idx] : idx;
     if (!valid_slot(a, b, row)) continue;
     const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
-    load_inputs(b, row, ap, lane);
-    if (!setup_agent(ap, sm, lane, prm)) { mark_status_only(ap, lane, MPC_AGENT_NAN_); continue; }
+    if (prm.split) {
+      // set up by mpc_k_setup (the torque map follows in mpc_k_torque)
+      if (ap.st[T_STATUS] == MPC_AGENT_NAN_) continue;
+      load_lin(ap, sm, lane);
+    } else {
+      load_inputs(b, row, ap, lane);
+      if (!setup_agent(ap, sm, lane, prm)) { mark_status_only(ap, lane, MPC_AGENT_NAN_); continue; }
+    }
     Outcome o = admm_solve<PREC>(ap, sm, lane, prm, false, pp, pat);
     final_polish<PREC>(ap, sm, lane, prm, o, pat, pp);
     write_outcome(ap, lane, o);
-    torque_map(ap, lane);
+    if (!prm.split) torque_map(ap, lane);
     __syncwarp();
   }
 }
@@ -2112,7 +2107,12 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) mpc_k_torque(Arena a, Ba
   if (row >= b.n || !valid_slot(a, b, row)) return;
   const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
   const int st = ap.st[T_STATUS];
-  if (st == MPC_AGENT_NAN_ || st == MPC_AGENT_TIMEOUT_) return;
+  if (st == MPC_AGENT_NAN_ || st == MPC_AGENT_TIMEOUT_) {
+    // a failed solve leaves no torques: zeroed outputs, as the status says
+    if (lane < 18) { ap.out[O_TAU + lane] = 0.f; ap.out[O_QSET + lane] = 0.f; ap.out[O_QDSET + lane] = 0.f; }
+    if (lane == 0) ap.out[O_V] = 0.f;
+    return;
+  }
   torque_map(ap, lane);
 }
 
@@ -2120,6 +2120,43 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) mpc_k_torque(Arena a, Ba
 
 // ============================================================ variant launcher
 // One translation unit instantiates one register-cap variant.
+// Inverse dynamics of the agents' kinematic trees (Eq. rnea), added to the
+// torques of the solve: four threads per agent, one per chain (left leg,
+// right leg, left arm, right arm); the base moves as the MPC predicts
+// (orientation and angular velocity of x0, accelerations (x_1 - x_0)/dt of
+// its twist).  Agents without a tree, or whose solve failed (non-finite or
+// timed out), are left alone.
+static __global__ void __launch_bounds__(128) mpc_k_rnea(Arena a, Batch b) {
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = gt >> 2, c = gt & 3;
+  if (row >= b.n || !valid_slot(a, b, row)) return;
+  const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
+  const float* md = ap.mdl;
+  if (md[M_TREE_ON] == 0.f) return;
+  const int status = ap.st[T_STATUS];
+  if (status == MPC_AGENT_NAN_ || status == MPC_AGENT_TIMEOUT_) return;
+  const int j0 = c < 2 ? 5 * c : 10 + 4 * (c - 2), len = c < 2 ? 5 : 4;
+  const float dt = md[M_DT], idt = 1.f / dt;
+  const float* x0 = ap.inp + I_X0;
+  const float* x1 = ap.x + VS;
+  const float cr = cosf(x0[3]), sr = sinf(x0[3]), cp = cosf(x0[4]), sp = sinf(x0[4]);
+  const float cy = cosf(x0[5]), sy = sinf(x0[5]);
+  const M3 Rb = {{cy * cp, cy * sp * sr - sy * cr, cy * sp * cr + sy * sr,
+                  sy * cp, sy * sp * sr + cy * cr, sy * sp * cr - cy * sr,
+                  -sp, cp * sr, cp * cr}};
+  const V3 wb = v3(x0[9], x0[10], x0[11]);
+  const V3 dwb = v3((x1[9] - x0[9]) * idt, (x1[10] - x0[10]) * idt, (x1[11] - x0[11]) * idt);
+  const V3 ab = v3((x1[6] - x0[6]) * idt, (x1[7] - x0[7]) * idt, (x1[8] - x0[8]) * idt + GRAV);
+  float q[5], qd[5], qdd[5], tl[5];
+  for (int t = 0; t < len; ++t) {
+    q[t] = x0[12 + j0 + t];
+    qd[t] = ap.u[12 + j0 + t];
+    qdd[t] = (ap.u[VS + 12 + j0 + t] - qd[t]) * idt;
+  }
+  chain_rnea(md + M_TREE, j0, len, Rb, wb, dwb, ab, q, qd, qdd, tl);
+  for (int t = 0; t < len; ++t) ap.out[O_TAU + j0 + t] += tl[t];
+}
+
 template <int MINB, int PREC>
 cudaError_t configure_smem() {
   const int bytes = (int)smem_bytes_per_block();
@@ -2154,12 +2191,23 @@ cudaError_t launch_prec(const Arena& a, const Batch& b, const SolverParams& prm,
   const int blocks = (b.n + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
   const dim3 thr(WARPS_PER_BLOCK * 32);
   if (form == 1) {
-    // resident grid: the persistent warps drain the work queue
+    // resident grid: the persistent warps drain the work queue.  Split:
+    // the once-per-agent set-up and torque map run as kernels of their own
+    // around it, where every warp runs the same code (inside the persistent
+    // kernel that code was cold in the instruction cache for each agent)
     int g = b.counter ? resident : blocks;
     if (grid_fused > 0 && grid_fused < g) g = grid_fused;
     if (g > blocks) g = blocks;
+    if (prm.split) {
+      mpc_k_setup<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
+      if (launches) *launches += 1;
+    }
     mpc_k_fused<MINB, PREC><<<g, thr, smem, st>>>(a, b, prm);
     if (launches) *launches += 1;
+    if (prm.split) {
+      mpc_k_torque<<<blocks, thr, 0, st>>>(a, b);
+      if (launches) *launches += 1;
+    }
   } else {
     mpc_k_setup<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
     mpc_k_factor<MINB, PREC><<<blocks, thr, smem, st>>>(a, b, prm);
@@ -2167,6 +2215,10 @@ cudaError_t launch_prec(const Arena& a, const Batch& b, const SolverParams& prm,
     mpc_k_polish<MINB, PREC><<<blocks, thr, smem, st>>>(a, b, prm);
     mpc_k_torque<<<blocks, thr, 0, st>>>(a, b);
     if (launches) *launches += 5;
+  }
+  if (prm.trees) {
+    mpc_k_rnea<<<(b.n * 4 + 127) / 128, 128, 0, st>>>(a, b);
+    if (launches) *launches += 1;
   }
   return cudaGetLastError();
 }
