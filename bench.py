@@ -55,10 +55,11 @@ def _measured_bf16_peak():
 
 
 BF16_PEAK_TFLOPS = _measured_bf16_peak()
-# DRAM bytes per agent of the fused kernel from the last ncu capture of this
-# kernel version (profiles/mpc_k_fused_mixed16k_2048agents.md); None once the
-# kernel has changed since.
-TRAFFIC_BYTES_PER_AGENT = (89.489920e6 + 161.486336e6) / 2048
+# DRAM bytes per agent of one solve step (order, set-up, persistent solve,
+# torque and RNEA kernels) from the last ncu capture of this kernel version
+# (profiles/mpc_k_fused_mixed16k_2048agents.md); None once the kernels have
+# changed since.
+TRAFFIC_BYTES_PER_AGENT = (134.55e6 + 113.94e6) / 2048
 
 
 def parse():
@@ -505,7 +506,9 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": None if TRAFFIC_BYTES_PER_AGENT is None else TRAFFIC_BYTES_PER_AGENT * n,
-                     "kernel": "mpc_k_fused", "flops_per_launch": float(fl),
+                     "kernel": "solve step: mpc_k_setup + mpc_k_fused (persistent, 86 % of the step's device "
+                               "time) + mpc_k_torque + mpc_k_rnea, timed as one graph replay",
+                     "flops_per_launch": float(fl),
                      "peak_basis": f"148 SM x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz (derived)",
                      "measured_fp32_fma_tflops": alu["fp32_fma_tflops"],
                      "frac_of_measured_fp32": achieved / alu["fp32_fma_tflops"]},
