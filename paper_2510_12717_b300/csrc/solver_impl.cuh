@@ -90,53 +90,72 @@ __device__ __noinline__ bool setup_agent(const AgentPtrs& ap, float* sm, int lan
   __syncwarp();
 
   const float fzmax = md[M_FZMAX], qdmax = md[M_QDMAX], qlim = md[M_QLIM];
-  // stage bounds: lane k writes the 56 rows of stage k
-  if (lane < N) {
-    const int f = flags[lane];
-    float* lo = ap.rlo + lane * RS;
-    float* hi = ap.rhi + lane * RS;
-    float* cl = ap.rcls + lane * RS;
-    for (int i = 0; i < 2; ++i) {
-      const int b = 6 * i, p = 12 + 4 * i;
-      const bool stance = (f >> i) & 1;
-      for (int c = 0; c < 6; ++c) {
-        if (stance) {
-          const bool z = (c == 2);
-          lo[b + c] = z ? 0.f : -INFINITY;
-          hi[b + c] = z ? fzmax : INFINITY;
-          cl[b + c] = z ? 1.f : 0.f;
+  // stage bounds: per stage, lane r writes rows r and r + 32 (coalesced)
+  for (int k = 0; k < N; ++k) {
+    const int f = flags[k];
+    float* lo = ap.rlo + k * RS;
+    float* hi = ap.rhi + k * RS;
+    float* cl = ap.rcls + k * RS;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int r = lane + 32 * h;
+      if (r >= NR) break;
+      float l, u, c;
+      if (r < 12) {                                 // foot wrench boxes
+        const int i = r / 6, cc = r - 6 * i;
+        if ((f >> i) & 1) {
+          const bool z = (cc == 2);
+          l = z ? 0.f : -INFINITY; u = z ? fzmax : INFINITY; c = z ? 1.f : 0.f;
         } else {
-          lo[b + c] = 0.f;
-          hi[b + c] = 0.f;
-          cl[b + c] = 1000.f;
+          l = 0.f; u = 0.f; c = 1000.f;
         }
+      } else if (r < 20) {                          // friction pyramids
+        const bool stance = (f >> ((r - 12) / 4)) & 1;
+        l = -INFINITY; u = stance ? 0.f : INFINITY; c = stance ? 1.f : 0.f;
+      } else if (r < 38) {                          // joint rates
+        l = -qdmax; u = qdmax; c = 1.f;
+      } else {                                      // joint positions (on x_{k+1})
+        l = -qlim; u = qlim; c = 1.f;
       }
-      for (int t = 0; t < 4; ++t) {
-        lo[p + t] = -INFINITY;
-        hi[p + t] = stance ? 0.f : INFINITY;
-        cl[p + t] = stance ? 1.f : 0.f;
-      }
-    }
-    for (int j = 0; j < 18; ++j) {
-      lo[20 + j] = -qdmax; hi[20 + j] = qdmax; cl[20 + j] = 1.f;
-      lo[38 + j] = -qlim;  hi[38 + j] = qlim;  cl[38 + j] = 1.f;
+      lo[r] = l;
+      hi[r] = u;
+      cl[r] = c;
     }
   }
 
   // references: desired trajectory (Eqs. des_traj_1..5) and force split
   const float dt = md[M_DT];
   const float ch = ap.inp[I_CMD], cvx = ap.inp[I_CMD + 1], cvy = ap.inp[I_CMD + 2], cwz = ap.inp[I_CMD + 3];
+  // yaw_k and its cosine and sine for every stage k = 0..N at once (lane k,
+  // lane 0 also k = 32)
+  float* vyaw = vec + V_T * 64;
+  float* vcos = vec + V_G * 64;
+  float* vsin = vec + V_D * 64;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int k = lane + 32 * h;
+    if (k <= N) {
+      const float yaw = xbar[5] + ((float)k * dt) * cwz;
+      float sy, cy;
+      sincosf(yaw, &sy, &cy);
+      vyaw[k] = yaw;
+      vcos[k] = cy;
+      vsin[k] = sy;
+    }
+  }
+  __syncwarp();
+  const float qn = (lane >= 12 && lane < 30) ? md[M_QNOM + lane - 12] : 0.f;
   for (int k = 0; k <= N; ++k) {
-    const float yaw = xbar[5] + ((float)k * dt) * cwz;
     float v = 0.f;
     if (lane == 2) v = ch;
-    else if (lane == 5) v = yaw;
-    else if (lane == 6) v = cosf(yaw) * cvx - sinf(yaw) * cvy;
-    else if (lane == 7) v = sinf(yaw) * cvx + cosf(yaw) * cvy;
+    else if (lane == 5) v = vyaw[k];
+    else if (lane == 6) v = vcos[k] * cvx - vsin[k] * cvy;
+    else if (lane == 7) v = vsin[k] * cvx + vcos[k] * cvy;
     else if (lane == 11) v = cwz;
-    else if (lane >= 12 && lane < 30) v = md[M_QNOM + lane - 12];
+    else if (lane >= 12 && lane < 30) v = qn;
     ap.xref[k * VS + lane] = v;
   }
+  __syncwarp();
   const float weight = md[M_MASS] * GRAV;
   for (int k = 0; k < N; ++k) {
     const int f = flags[k];
@@ -240,38 +259,56 @@ __device__ __noinline__ bool setup_agent(const AgentPtrs& ap, float* sm, int lan
   // (the stance forces are those of u_ref_k, recomputed from the contact
   // flags; dA_k is staged in shared memory for the A_k x0 product, so neither
   // is read back from global memory right after it was written)
+  // stage-independent parts, once: the dA_k entry of lane (r, col) per unit
+  // stance force, A_base x0, and f(x0, u) = f0c + f0L F_L + f0R F_R
   float* vdA = vec + V_T * 64;
+  float gdA = 0.f;
+  int fsel = 0;
+  if (lane < 30) {
+    const int r = lane / 10, col = lane - 10 * r, f = col / 5, j = col - 5 * f;
+    const float jr0 = md[M_JLEG + 30 * f + 0 * 5 + j], jr1 = md[M_JLEG + 30 * f + 1 * 5 + j];
+    gdA = dt * (m3(Iwi, r, 0) * jr1 - m3(Iwi, r, 1) * jr0);
+    fsel = f;
+  }
+  float Abx = 0.f, f0c = 0.f, f0L = 0.f, f0R = 0.f, BuL = 0.f, BuR = 0.f;
+  if (lane < NC) {
+    const int i = lane;
+    Abx = cm_mv(Ab, xbar, lane);
+    if (i < 3) f0c = xbar[6 + i];
+    else if (i < 6) f0c = m3(Einv, i - 3, 0) * w0 + m3(Einv, i - 3, 1) * w1 + m3(Einv, i - 3, 2) * w2;
+    else if (i == 8) { f0c = -GRAV; f0L = invm; f0R = invm; }
+    else if (i >= 9 && i < 12) {
+      // I_w^-1 (r_L x f_L + r_R x f_R - w x I_w w) with f = (0, 0, F)
+      const int r = i - 9;
+      const float g0 = w1 * Iww2 - w2 * Iww1, g1 = w2 * Iww0 - w0 * Iww2, g2 = w0 * Iww1 - w1 * Iww0;
+      f0c = -(m3(Iwi, r, 0) * g0 + m3(Iwi, r, 1) * g1 + m3(Iwi, r, 2) * g2);
+      f0L = m3(Iwi, r, 0) * rl[0][1] - m3(Iwi, r, 1) * rl[0][0];
+      f0R = m3(Iwi, r, 0) * rl[1][1] - m3(Iwi, r, 1) * rl[1][0];
+    }
+    BuL = Bm[2 * LDD + i];
+    BuR = Bm[8 * LDD + i];
+  }
   for (int k = 0; k < N; ++k) {
     float* st = ap.lin + L_STAGE + k * 64;
     const int fk = flags[k];
     const float share = weight / (float)__popc(fk);
     const float FL = (fk & 1) ? share : 0.f, FR = (fk & 2) ? share : 0.f;
     if (lane < 30) {
-      const int r = lane / 10, col = lane - 10 * r, f = col / 5, j = col - 5 * f;
-      const float F = f ? FR : FL;
-      const float jr0 = md[M_JLEG + 30 * f + 0 * 5 + j], jr1 = md[M_JLEG + 30 * f + 1 * 5 + j];
-      const float v = dt * F * (m3(Iwi, r, 0) * jr1 - m3(Iwi, r, 1) * jr0);
+      const float v = (fsel ? FR : FL) * gdA;
       st[lane] = v;
       vdA[lane] = v;
     }
     __syncwarp();
     if (lane < NC) {
       const int i = lane;
-      float f0 = 0.f;
-      if (i < 3) f0 = xbar[6 + i];
-      else if (i < 6) f0 = m3(Einv, i - 3, 0) * w0 + m3(Einv, i - 3, 1) * w1 + m3(Einv, i - 3, 2) * w2;
-      else if (i < 9) f0 = (i == 8) ? (FL + FR) * invm - GRAV : 0.f;
-      else if (i < 12) {
-        // I_w^-1 (r_L x f_L + r_R x f_R - w x I_w w) with f = (0, 0, F)
-        const float t0 = rl[0][1] * FL + rl[1][1] * FR - (w1 * Iww2 - w2 * Iww1);
-        const float t1 = -rl[0][0] * FL - rl[1][0] * FR - (w2 * Iww0 - w0 * Iww2);
-        const float t2 = -(w0 * Iww1 - w1 * Iww0);
-        const int r = i - 9;
-        f0 = m3(Iwi, r, 0) * t0 + m3(Iwi, r, 1) * t1 + m3(Iwi, r, 2) * t2;
+      float Ax = Abx;
+      if (i >= 9 && i < 12) {
+        const float* row = vdA + (i - 9) * 10;
+#pragma unroll
+        for (int c = 0; c < 10; ++c) Ax = fmaf(row[c], xbar[12 + c], Ax);
       }
-      const float Ax = ak_mv(Ab, vdA, xbar, lane);
-      const float Bu = Bm[2 * LDD + i] * FL + Bm[8 * LDD + i] * FR;
-      st[32 + i] = xbar[i] + dt * f0 - Ax - Bu;
+      const float f0 = f0c + f0L * FL + f0R * FR;
+      st[32 + i] = xbar[i] + dt * f0 - Ax - (BuL * FL + BuR * FR);
     }
     __syncwarp();
   }
