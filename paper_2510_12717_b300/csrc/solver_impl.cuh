@@ -2081,6 +2081,23 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_setup(Arena 
   else if (lane == 0) ap.st[T_STATUS] = MPC_AGENT_MAX_ITER_;
 }
 
+// Set-up of the fused form: the same per-agent work as mpc_k_setup, with a
+// per-warp shared-memory window that starts at S_AB (set-up never touches the
+// factor blocks below it): half the shared memory per warp, so about 20
+// warps per SM instead of the solve kernels' 12 hide its memory latency
+constexpr int W_SETUP = W_FLOATS - S_AB;
+__global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) mpc_k_setup_lean(Arena a, Batch b, SolverParams prm) {
+  const int lane = threadIdx.x & 31;
+  const int row = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
+  if (row >= b.n || !valid_slot(a, b, row)) return;
+  // offsets from S_AB on land in this warp's window; nothing below S_AB is addressed
+  float* sm = g_smem + (threadIdx.x >> 5) * W_SETUP - S_AB;
+  const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
+  load_inputs(b, row, ap, lane);
+  if (!setup_agent(ap, sm, lane, prm)) mark_status_only(ap, lane, MPC_AGENT_NAN_);
+  else if (lane == 0) ap.st[T_STATUS] = MPC_AGENT_MAX_ITER_;
+}
+
 template <int MINB, int PREC>
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_factor(Arena a, Batch b, SolverParams prm) {
   const int lane = threadIdx.x & 31;
@@ -2236,7 +2253,7 @@ cudaError_t launch_prec(const Arena& a, const Batch& b, const SolverParams& prm,
     if (grid_fused > 0 && grid_fused < g) g = grid_fused;
     if (g > blocks) g = blocks;
     if (prm.split) {
-      mpc_k_setup<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
+      mpc_k_setup_lean<<<blocks, thr, WARPS_PER_BLOCK * W_SETUP * sizeof(float), st>>>(a, b, prm);
       if (launches) *launches += 1;
     }
     mpc_k_fused<MINB, PREC><<<g, thr, smem, st>>>(a, b, prm);
