@@ -205,58 +205,64 @@ __device__ __forceinline__ float r24_mv(const float* M, const float* v, int lane
   return a0 + a1;
 }
 
-// In-place inverse of a symmetric positive definite R24 block by Gauss-Jordan
-// elimination without pivoting, in the symmetric (sweep) form: lane j keeps
-// column j in registers.  Pivoting on p maps M to M' with
-//   M'_pp = 1/M_pp,  M'_pj = M_pj/M_pp,  M'_ip = -M_ip/M_pp,
-//   M'_ij = M_ij - M_ip M_pj/M_pp,
-// so after pivots 0..p-1 the entries with exactly one index among the pivoted
-// ones are antisymmetric and the rest symmetric: the pivot column p is row p
-// with the sign of rows i < p flipped.  Row p is one register per lane, so a
-// pivot costs one shared-memory vector (double buffered in sc, 2 x 32 floats,
-// 16-byte aligned) and one warp barrier.  Pivot p writes row p+1 into the
-// other buffer, which every lane finished reading at pivot p-1.
+// In-place inverse of a symmetric positive definite R24 block by the sweep
+// operator (Goodnight 1979) on 2 x 2 pivot blocks: sweeping the index pair
+// S = {k, k+1} with B = M_SS maps
+//   M_SS <- -B^-1,  M_iS <- M_iS B^-1,  M_Sj <- B^-1 M_Sj,
+//   M_ij <- M_ij - M_iS B^-1 M_Sj   (i, j outside S),
+// keeps M symmetric, and equals sweeping k and then k+1 one at a time; after
+// all eleven pairs M holds -M^-1.  Lane j keeps column j in registers; the
+// columns k and k+1 every lane needs are, by symmetry, the rows k and k+1 of
+// the lanes' own columns: one shared-memory write per lane and row, double
+// buffered in sc (2 buffers x 2 rows x 32 floats, 16-byte aligned), and one
+// warp barrier per pair.  A pair writes the next pair's rows first, into the
+// other buffer, which every lane finished reading at the pair before.
 __device__ __forceinline__ void r24_inv(float* H, float* sc, int lane) {
   const int j = lane < NC ? lane : NC - 1;
   float h[NC];
 #pragma unroll
   for (int i = 0; i < NC; ++i) h[i] = H[i * R24 + j];
   sc[lane] = h[0];
+  sc[32 + lane] = h[1];
 #pragma unroll
-  for (int p = 0; p < NC; ++p) {
+  for (int r = 0; r < NC / 2; ++r) {
+    const int k = 2 * r;
     __syncwarp();
-    float v[24];
-    const float4* b4 = reinterpret_cast<const float4*>(sc + (p & 1) * 32);
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const float4 t = b4[q];
-      v[4 * q] = t.x; v[4 * q + 1] = t.y; v[4 * q + 2] = t.z; v[4 * q + 3] = t.w;
+    const float* V0 = sc + (r & 1) * 64;   // column k
+    const float* V1 = V0 + 32;             // column k + 1
+    const float a = V0[k], b = V0[k + 1], c = V1[k + 1];
+    // the pivot block of an SPD matrix is SPD, its determinant well away from
+    // 0: the fast reciprocal (2 ulp) is ample
+    const float id = __fdividef(1.f, fmaf(a, c, -b * b));
+    const bool s0 = j == k, s1 = j == k + 1, in = s0 || s1;
+    // lanes outside S: y = B^-1 M_Sj; lanes in S: their new entries are
+    // M_iS B^-1 e_j (their old column is dropped: keep = 0)
+    float y0 = id * fmaf(c, h[k], -b * h[k + 1]);
+    float y1 = id * fmaf(a, h[k + 1], -b * h[k]);
+    if (s0) { y0 = -id * c; y1 = id * b; }
+    if (s1) { y0 = id * b; y1 = -id * a; }
+    const float keep = in ? 0.f : 1.f;
+    // the next pair's rows first
+    if (r + 1 < NC / 2) {
+      float* N0 = sc + ((r + 1) & 1) * 64;
+      h[k + 2] = fmaf(-V0[k + 2], y0, fmaf(-V1[k + 2], y1, keep * h[k + 2]));
+      h[k + 3] = fmaf(-V0[k + 3], y0, fmaf(-V1[k + 3], y1, keep * h[k + 3]));
+      N0[lane] = h[k + 2];
+      N0[32 + lane] = h[k + 3];
     }
-    // the pivot of an SPD block is positive and well away from 0: the fast
-    // reciprocal (2 ulp) is ample
-    const float inv = __fdividef(1.f, v[p]);
-    float* nxt = sc + ((p + 1) & 1) * 32;   // row p+1 goes out first (the next pivot waits on it)
-    if (j == p) {
-      if (p + 1 < NC) { h[p + 1] = -h[p + 1] * inv; nxt[lane] = h[p + 1]; }
 #pragma unroll
-      for (int i = 0; i < NC; ++i)
-        if (i != p && i != p + 1) h[i] = -h[i] * inv;
-      h[p] = inv;
-    } else {
-      const float rp = h[p] * inv;
-      if (p + 1 < NC) { h[p + 1] = fmaf(-v[p + 1], rp, h[p + 1]); nxt[lane] = h[p + 1]; }
-#pragma unroll
-      for (int i = 0; i < NC; ++i) {
-        if (i == p || i == p + 1) continue;
-        const float ci = i < p ? -v[i] : v[i];   // M_ip
-        h[i] = fmaf(-ci, rp, h[i]);
-      }
-      h[p] = rp;
+    for (int i = 0; i < NC; ++i) {
+      if (i == k || i == k + 1 || i == k + 2 || i == k + 3) continue;
+      h[i] = fmaf(-V0[i], y0, fmaf(-V1[i], y1, keep * h[i]));
     }
+    // M_SS <- -B^-1 on the lanes in S, M_Sj <- B^-1 M_Sj elsewhere
+    if (s0) { h[k] = -id * c; h[k + 1] = id * b; }
+    else if (s1) { h[k] = id * b; h[k + 1] = -id * a; }
+    else { h[k] = y0; h[k + 1] = y1; }
   }
   if (lane < NC) {
 #pragma unroll
-    for (int i = 0; i < NC; ++i) H[i * R24 + j] = h[i];
+    for (int i = 0; i < NC; ++i) H[i * R24 + j] = -h[i];
   }
   __syncwarp();
 }

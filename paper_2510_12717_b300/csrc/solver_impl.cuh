@@ -354,7 +354,7 @@ __device__ __forceinline__ void load_lin(const AgentPtrs& ap, float* sm, int lan
 // Per stage, lane j forms column j of P A_k and P B from the compact columns
 // (at most 6 terms each), then column j of
 //   H_uu = R_t + B^T (P B),  H_ux = B^T (P A),  T = A^T (P A)
-// with compile-time sparsity; H_uu is inverted (Gauss-Jordan), K = -H_uu^-1 H_ux
+// with compile-time sparsity; H_uu is inverted (2 x 2-block sweep), K = -H_uu^-1 H_ux
 // and P <- T + H_ux^T K + diag(Q_t).  Caches per stage: K_k, H_uu,k^-1 (R24),
 // e_k = P_{k+1} c_k, and the arm lanes' scalar gain, inverse and e.
 // The polish step runs the same recursion on its reduced problem.
