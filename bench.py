@@ -59,7 +59,7 @@ BF16_PEAK_TFLOPS = _measured_bf16_peak()
 # torque and RNEA kernels) from the last ncu capture of this kernel version
 # (profiles/mpc_k_fused_mixed16k_2048agents.md); None once the kernels have
 # changed since.
-TRAFFIC_BYTES_PER_AGENT = (134.55e6 + 113.94e6) / 2048
+TRAFFIC_BYTES_PER_AGENT = (132.46e6 + 113.74e6) / 2048
 
 
 def parse():
@@ -506,8 +506,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": None if TRAFFIC_BYTES_PER_AGENT is None else TRAFFIC_BYTES_PER_AGENT * n,
-                     "kernel": "solve step: mpc_k_setup + mpc_k_fused (persistent, 86 % of the step's device "
-                               "time) + mpc_k_torque + mpc_k_rnea, timed as one graph replay",
+                     "kernel": "solve step: mpc_k_setup_lean + mpc_k_fused (persistent, 92 % of the step's "
+                               "device time) + mpc_k_torque + mpc_k_rnea, timed as one graph replay",
                      "flops_per_launch": float(fl),
                      "peak_basis": f"148 SM x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz (derived)",
                      "measured_fp32_fma_tflops": alu["fp32_fma_tflops"],

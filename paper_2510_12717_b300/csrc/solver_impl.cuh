@@ -383,9 +383,7 @@ __device__ __forceinline__ StageOut factor_stage(const AgentPtrs& ap, float* sm,
   // e = P c (before P is overwritten)
   const float e = r24_mtv(P, in.c, lane);
   // lane j: column j of P B, then H(:, j) = B^T (P B)(:, j) (H, X are not
-  // read by other lanes before the next barrier, so they are written at once).
-  // P is exactly symmetric (symmetrised every stage), so column rb of P is
-  // read as row rb: float4 loads
+  // read by other lanes before the next barrier, so they are written at once)
   {
     float pb[NC];
 #pragma unroll
@@ -393,15 +391,9 @@ __device__ __forceinline__ StageOut factor_stage(const AgentPtrs& ap, float* sm,
 #pragma unroll
     for (int t = 0; t < 6; ++t) {
       const float b = bv[j * 6 + t];
-      const float4* row = reinterpret_cast<const float4*>(P + pat.br[t] * R24);
+      const int rb = pat.br[t];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        const float4 v = row[q];
-        pb[4 * q] = fmaf(v.x, b, pb[4 * q]);
-        pb[4 * q + 1] = fmaf(v.y, b, pb[4 * q + 1]);
-        if (4 * q + 2 < NC) pb[4 * q + 2] = fmaf(v.z, b, pb[4 * q + 2]);
-        if (4 * q + 3 < NC) pb[4 * q + 3] = fmaf(v.w, b, pb[4 * q + 3]);
-      }
+      for (int i = 0; i < NC; ++i) pb[i] = fmaf(P[i * R24 + rb], b, pb[i]);
     }
     if (lane < NC) {
 #pragma unroll
@@ -421,15 +413,9 @@ __device__ __forceinline__ StageOut factor_stage(const AgentPtrs& ap, float* sm,
 #pragma unroll
   for (int t = 0; t < 6; ++t) {
     const float a = av[j * 6 + t];
-    const float4* row = reinterpret_cast<const float4*>(P + pat.ar[t] * R24);
+    const int ra = pat.ar[t];
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const float4 v = row[q];
-      pa[4 * q] = fmaf(v.x, a, pa[4 * q]);
-      pa[4 * q + 1] = fmaf(v.y, a, pa[4 * q + 1]);
-      if (4 * q + 2 < NC) pa[4 * q + 2] = fmaf(v.z, a, pa[4 * q + 2]);
-      if (4 * q + 3 < NC) pa[4 * q + 3] = fmaf(v.w, a, pa[4 * q + 3]);
-    }
+    for (int i = 0; i < NC; ++i) pa[i] = fmaf(P[i * R24 + ra], a, pa[i]);
   }
   if (lane < NC) {
 #pragma unroll
