@@ -111,7 +111,11 @@ typedef struct mpc_config {
                                  first fails falls back to FP32 factors for its
                                  ADMM solve and later polishes; otherwise every
                                  factor uses the requested precision */
-  int form;                   /* mpc_form: separate step kernels or one fused kernel */
+  int form;                   /* mpc_form: PLAIN = one kernel per step (set-up, factor,
+                                 ADMM, polish, torque map; static grids); FUSED = a
+                                 set-up kernel, one persistent kernel that solves
+                                 every agent (polish first, ADMM fallback, polish) over
+                                 a longest-first work queue, and a torque-map kernel */
   float rho0, sigma, alpha;   /* ADMM step size, proximal weight, relaxation */
   float eps_abs, eps_rel;     /* OSQP-style stopping tolerances */
   int max_iter;               /* iteration cap */
