@@ -28,6 +28,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -168,7 +169,7 @@ class ClockSampler:
 
     def __init__(self, device_index=0):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"bench_clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"mpc_bench_clocks_{os.getpid()}.csv")
         self.dev = device_index
         self.t_begin = self.t_end = None
 
