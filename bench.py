@@ -60,7 +60,7 @@ BF16_PEAK_TFLOPS = _measured_bf16_peak()
 # torque and RNEA kernels) from the last ncu capture of this kernel version
 # (profiles/mpc_k_fused_mixed16k_2048agents.md); None once the kernels have
 # changed since.
-TRAFFIC_BYTES_PER_AGENT = (132.46e6 + 113.74e6) / 2048
+TRAFFIC_BYTES_PER_AGENT = (133.16e6 + 116.05e6) / 2048
 
 
 def parse():
