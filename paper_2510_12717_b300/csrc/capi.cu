@@ -38,6 +38,7 @@ struct GraphEntry {
   const void* ptrs[5] = {};
   cudaStream_t stream = nullptr;
   int variant = 0, check_every = 0, trees = 0;
+  int kernels = 0;                  // kernels the captured graph launches
   float early_polish = 0.f;
   cudaGraphExec_t exec = nullptr;
 };
@@ -519,7 +520,7 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
         g.check_every == ctx->cfg.check_every && g.early_polish == ctx->cfg.early_polish &&
         g.trees == prm.trees && !memcmp(g.ptrs, ptrs, sizeof(ptrs))) {
       ctx->graph_replays += 1;
-      ctx->launches += 2 + prm.trees;   // the order and fused kernels of the graph (+ the RNEA kernel)
+      ctx->launches += g.kernels;       // the kernels recorded in the graph
       return cudaGraphLaunch(g.exec, st);
     }
   }
@@ -558,6 +559,7 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
   g.check_every = ctx->cfg.check_every;
   g.early_polish = ctx->cfg.early_polish;
   g.trees = prm.trees;
+  g.kernels = launches;
   ctx->launches += launches;
   return cudaGraphLaunch(g.exec, st);
 }

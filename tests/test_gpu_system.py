@@ -42,12 +42,18 @@ def test_graph_replay_is_bitwise_equal(mpcgpu):
         cs = side.cuda_stream
         ref = mpcgpu.Solver(max_agents=64, max_horizon=20, stream=cs, warm_start=0)
         ref.set_models(model, ids)
+        r0 = ref.stats()["kernel_launches"]
         tau0, st0 = _solve(ref, ids_d, t, 64)
+        per_solve = ref.stats()["kernel_launches"] - r0
         g = mpcgpu.Solver(max_agents=64, max_horizon=20, stream=cs, warm_start=0, graph=1)
         g.set_models(model, ids)
-        outs = [_solve(g, ids_d, t, 64) for _ in range(3)]    # capture, then two replays
+        outs = [_solve(g, ids_d, t, 64) for _ in range(2)]    # capture, then a replay
+        l0 = g.stats()["kernel_launches"]
+        outs.append(_solve(g, ids_d, t, 64))                  # a second replay
+        replay_launches = g.stats()["kernel_launches"] - l0
     torch.cuda.synchronize()
     assert g.stats()["graph_replays"] == 2
+    assert replay_launches == per_solve >= 4   # the replay counts every kernel the graph holds
     for tau, st in outs:
         assert torch.equal(tau, tau0) and torch.equal(st, st0)
     ref.close(); g.close()
