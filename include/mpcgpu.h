@@ -309,7 +309,7 @@ mpc_status mpc_import_state(mpc_ctx* ctx, int32_t agent_id, const float* x_host,
  * mpc_default_config(), on `stream` (a cudaStream_t; NULL = default stream).
  * Inputs x0, qd_meas, cmd, phase and outputs tau, q_set, qd_set, value,
  * agent_status are device buffers with the layouts above (outputs may be
- * NULL).  All workspace lives in one static device array of about 12 MB that
+ * NULL).  All workspace lives in one static device array of about 11 MB that
  * every GPU loading this library holds until the process exits; no call
  * allocates or frees device memory.
  *   - The first call on a device resolves the array's device address (with
