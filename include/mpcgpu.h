@@ -324,7 +324,11 @@ mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_host, const
                             float* tau, float* q_set, float* qd_set, float* value,
                             int32_t* agent_status, void* stream);
 
-/* JSON summary of the context (sizes, arenas, counters) into buf. */
+/* JSON summary of the context (sizes, arenas, counters) into buf, and
+ * "polish_attempts": a histogram over the live agents of their last solve's
+ * accepted polish, entry a = agents whose polish took a reduced KKT solves
+ * (the first guess and its corrections), entry 0 = no polish accepted (the
+ * iteration count of the active-set method).  Synchronises the stream. */
 mpc_status mpc_get_stats(mpc_ctx* ctx, char* buf, size_t cap);
 
 /* Residual policy and joint-torque blending after the MPC (paper Sec. IV,

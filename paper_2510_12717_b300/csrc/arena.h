@@ -53,7 +53,9 @@ enum : int { I_X0 = 0, I_QD = 32, I_CMD = 50, I_PHASE = 54, IN_F = 64 };
 enum : int { O_TAU = 0, O_QSET = 18, O_QDSET = 36, O_V = 54, O_PRIM = 55, O_DUAL = 56, O_PRIM_N = 57,
              O_DUAL_N = 58, OUT_F = 64 };
 // per-agent integer record (ST_I ints)
-enum : int { T_STATUS = 0, T_ITERS = 1, T_REFAC = 2, T_POLISHED = 3, T_N = 4, T_WARM = 5, T_FIRST = 6, ST_I = 8 };
+// T_ATTEMPTS: solves of the accepted polish (first + corrections; 0 = none accepted)
+enum : int { T_STATUS = 0, T_ITERS = 1, T_REFAC = 2, T_POLISHED = 3, T_N = 4, T_WARM = 5, T_FIRST = 6,
+             T_ATTEMPTS = 7, ST_I = 8 };
 
 struct Arena {
   int max_agents;

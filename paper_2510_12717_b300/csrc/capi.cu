@@ -784,15 +784,30 @@ mpc_status mpc_get_stats(mpc_ctx* ctx, char* buf, size_t cap) {
   if (!ctx || !buf || cap == 0) return MPC_ERR_INVALID;
   int live = 0;
   for (int h : ctx->live) live += h != 0;
+  // polish attempts of the live agents' last solves: [0] none accepted, [a] a solves
+  long long hist[9] = {0};
+  {
+    std::vector<int> st((size_t)ctx->cfg.max_agents * mpc::ST_I);
+    CK(cudaSetDevice(ctx->cfg.device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpy(st.data(), ctx->ar.stat, sizeof(int) * st.size(), cudaMemcpyDeviceToHost));
+    for (int a = 0; a < ctx->cfg.max_agents; ++a) {
+      if (!ctx->live[a]) continue;
+      const int t = st[(size_t)a * mpc::ST_I + mpc::T_ATTEMPTS];
+      hist[t >= 0 && t <= 8 ? t : 0] += 1;
+    }
+  }
   snprintf(buf, cap,
            "{\"max_agents\": %d, \"max_horizon\": %d, \"live_agents\": %d, \"arena_bytes\": %zu, "
            "\"form\": \"%s\", \"kernel_launches\": %lld, \"solves\": %lld, \"graph_replays\": %lld, "
            "\"smem_per_block\": %zu, \"warps_per_block\": %d, \"variant\": %d, \"check_every\": %d, "
-           "\"early_polish\": %g, \"graph\": %d}",
+           "\"early_polish\": %g, \"graph\": %d, "
+           "\"polish_attempts\": [%lld, %lld, %lld, %lld, %lld, %lld, %lld, %lld, %lld]}",
            ctx->cfg.max_agents, ctx->cfg.max_horizon, live, ctx->bytes,
            ctx->cfg.form == MPC_FORM_FUSED ? "fused" : "plain", ctx->launches, ctx->solves, ctx->graph_replays,
            mpc::smem_bytes_per_block(), mpc::WARPS_PER_BLOCK, ctx->cfg.variant, ctx->cfg.check_every,
-           (double)ctx->cfg.early_polish, ctx->cfg.graph);
+           (double)ctx->cfg.early_polish, ctx->cfg.graph, hist[0], hist[1], hist[2], hist[3], hist[4], hist[5],
+           hist[6], hist[7], hist[8]);
   return MPC_OK;
 }
 

@@ -1604,6 +1604,7 @@ __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, co
     if (ok) {
       for (int k = 1; k <= ap.N; ++k) ap.x[k * VS + lane] = ap.xt[k * VS + lane];
       for (int k = 0; k < ap.N; ++k) ap.u[k * VS + lane] = ap.ut[k * VS + lane];
+      if (lane == 0) ap.st[T_ATTEMPTS] = attempt + 1;
       __syncwarp();
       *res = pr;
       return true;
@@ -1747,7 +1748,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
   // right, and a cold agent's optimum has few active rows; a polish from that
   // guess (with its corrections) that passes the KKT check is the optimum,
   // with no ADMM factorisation and no iteration
-  if (lane == 0) ap.st[T_FIRST] = 0;
+  if (lane == 0) { ap.st[T_FIRST] = 0; ap.st[T_ATTEMPTS] = 0; }
   if (prm.polish && prm.warm_polish && prm.fixed_iters == 0) {
     Res pr;
     if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, o.prec, ap.st[T_WARM] ? POLISH_PREV : POLISH_MIN)) {

@@ -338,6 +338,6 @@ class Solver:
 
     def stats(self) -> dict:
         import json
-        buf = C.create_string_buffer(1024)
-        self._check(self.lib.mpc_get_stats(self.ctx, buf, 1024))
+        buf = C.create_string_buffer(4096)
+        self._check(self.lib.mpc_get_stats(self.ctx, buf, 4096))
         return json.loads(buf.value.decode())

@@ -113,3 +113,23 @@ def test_autotune_picks_a_solving_configuration(mpcgpu):
     r = ref.solve_host(ids, inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
     assert torque_close(tau.cpu().numpy(), r["tau"]).all()
     s.close(); ref.close()
+
+
+def test_polish_attempt_histogram(mpcgpu):
+    # the context's histogram of accepted-polish solve counts covers every
+    # live agent, agrees with the per-agent outcome, and most warm agents
+    # need one solve
+    ids = np.arange(64)
+    model, _ = agents("uneven", ids)
+    s = mpcgpu.Solver(max_agents=64, max_horizon=20, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_models(model, ids)
+    for replan in (0, 1):
+        _, inp = agents("uneven", ids, replan=replan)
+        inp32 = device_inputs(inp)
+        s.solve_host(ids.astype(np.int32), inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+        hist = s.stats()["polish_attempts"]
+        st = s.agent_stats(ids.astype(np.int32))
+        assert len(hist) == 9 and sum(hist) == 64
+        assert hist[0] == int((st["polished"] == 0).sum())
+    assert hist[1] >= 0.75 * 64
+    s.close()
