@@ -58,7 +58,8 @@ typedef enum {
 } mpc_status;
 
 typedef enum {
-  MPC_AGENT_SOLVED = 0,        /* ADMM met its tolerances, or a polish passed the KKT check */
+  MPC_AGENT_SOLVED = 0,        /* a polished point passed the KKT check of its active set
+                                  (the optimum up to rounding) */
   MPC_AGENT_MAX_ITER = 1,      /* iteration cap reached (or fixed-N_QP mode) */
   MPC_AGENT_PRIMAL_INFEAS = 2, /* no point satisfies the constraints: OSQP's certificate
                                   (the multiplier change of the last ADMM iteration,
@@ -69,7 +70,11 @@ typedef enum {
   MPC_AGENT_DUAL_INFEAS = 3,   /* never produced: every row of the cost is bounded
                                   below on the dynamics (Q, R >= 0, x0 fixed) */
   MPC_AGENT_NAN = 4,           /* non-finite input or iterate; outputs zeroed */
-  MPC_AGENT_TIMEOUT = 5        /* a bounded device wait gave up; outputs zeroed */
+  MPC_AGENT_TIMEOUT = 5,       /* a bounded device wait gave up; outputs zeroed */
+  MPC_AGENT_INACCURATE = 6     /* ADMM met its stopping test but no polish passed the KKT
+                                  check (or polish is off): the outputs are ADMM's iterate,
+                                  as accurate as that test, not certified to be the
+                                  optimum; the warm start is kept */
 } mpc_agent_status;
 
 typedef enum { MPC_FP32 = 0, MPC_TF32 = 1, MPC_BF16 = 2, MPC_FP64 = 3 } mpc_precision;
@@ -93,7 +98,8 @@ typedef enum {
  * rho0 0.1, sigma 1e-6, alpha 1.6, eps_abs = eps_rel = 1e-5, max_iter 4000,
  * fixed_iters 0, check_every 10, adaptive_rho 1, polish 1, warm_start 1,
  * form FUSED, precision FP32, max_horizon 20, variant 1, early_polish 100,
- * graph 0, warm_polish 1, refine_steps -1.  OSQP's parameters (Stellato et al. 2020,
+ * graph 0, warm_polish 1, refine_steps -1, spin_limit 4194304, wait_test_agent -1.
+ * OSQP's parameters (Stellato et al. 2020,
  * Sec. 3.2, to which the paper defers after Eq. (backsolve_2)). */
 typedef struct mpc_config {
   int device;                 /* CUDA device ordinal */
@@ -137,9 +143,22 @@ typedef struct mpc_config {
                                  alone (cold agent); ADMM runs only if that fails
                                  its KKT check */
   int refine_steps;           /* iterative-refinement steps on each polish solve
-                                 (0..4); -1 = automatic: 1 on a polish after ADMM
-                                 iterations, and on the warm-start polish 1 for
-                                 TF32 / BF16, 0 for FP32 / FP64 */
+                                 (0..4); -1 = automatic: 2 for TF32 and 3 for BF16
+                                 stage products on every polish; for FP32 / FP64 1
+                                 on a polish after ADMM iterations and 0 on the
+                                 warm-start polish */
+  int spin_limit;             /* polls of a bounded device wait (a stage block's bulk
+                                 copy into shared memory) before it gives up; the
+                                 agent then gets MPC_AGENT_TIMEOUT with zeroed
+                                 outputs, the kernel waits (bounded again) for that
+                                 warp's copies still in flight and the warp takes no
+                                 further agent (the rest of the batch is solved by
+                                 the other warps); mpc_get_stats counts the events
+                                 ("wait_timeouts").  > 0 */
+  int wait_test_agent;        /* failure-detection test only: the first stage-block
+                                 wait of this agent id is armed with no copy behind
+                                 it, so it runs out after spin_limit polls with
+                                 nothing in flight.  -1 = off (the default) */
 } mpc_config;
 
 /* One agent's model (host memory, float64; stored as float32 on the device,
@@ -293,16 +312,30 @@ mpc_status mpc_get_agent_stats(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids
 mpc_status mpc_export_state(mpc_ctx* ctx, int32_t agent_id, float* x_host, float* u_host,
                             float* w_host, float* y_host, float* rho_host);
 
+/* Inspection of one agent's horizon QP as its last solve formed it (host
+ * buffers, each may be NULL): steps f_init / f_param and the linearisation of
+ * Alg. 1, i.e. the desired trajectory (Eqs. des_traj_1-5) xref[(N+1)][30] and
+ * uref[N][30], the row bounds of Eq. (mpc_formulation)'s constraints
+ * lo[N][56], hi[N][56] (rows: 0-11 foot wrenches, 12-19 friction pyramid,
+ * 20-37 joint rates, 38-55 joints at stage k+1; +-inf = free), and the
+ * dynamics linearised about x0 and u_ref,k (Sec. III-B),
+ * x_{k+1} = A_k x_k + B_k u_k + c_k: A[N][30][30], B[N][30][30], c[N][30],
+ * row-major.  Synchronises the stream.  Errors: MPC_ERR_INVALID for an
+ * unknown agent. */
+mpc_status mpc_export_qp(mpc_ctx* ctx, int32_t agent_id, float* xref_host, float* uref_host,
+                         float* lo_host, float* hi_host, float* A_host, float* B_host, float* c_host);
+
 /* Restore a state written by mpc_export_state (sets the warm start). */
 mpc_status mpc_import_state(mpc_ctx* ctx, int32_t agent_id, const float* x_host,
                             const float* u_host, const float* w_host, const float* y_host,
                             float rho);
 
 /* Allocation-free solve, for callers that cannot allocate device memory
- * when they need a solve: code inside a CUDA stream capture (cudaMalloc
- * cannot be captured), simulator plugins that may only use buffers handed to
- * them, or processes whose device allocator belongs to another framework.
- * The paper has no counterpart; it is a deployment convenience.
+ * when they need a solve: simulator plugins that may only use the buffers
+ * handed to them, real-time control loops that must not enter the device
+ * allocator once running, or processes whose device allocator belongs to
+ * another framework.  The paper has no counterpart; it is a deployment
+ * convenience.
  *
  * Solves n <= 64 agents of horizon N <= 20 (models_host[n], host memory) in
  * one cold-started fused pass with the default options of
@@ -314,9 +347,13 @@ mpc_status mpc_import_state(mpc_ctx* ctx, int32_t agent_id, const float* x_host,
  * allocates or frees device memory.
  *   - The first call on a device resolves the array's device address (with
  *     that device current); make that first call before any stream capture.
- *   - Every call shares the one array, which keeps the previous call's
- *     contents (warm-start markers are cleared each call): calls that may
- *     overlap on the GPU, from any thread or stream, race.
+ *   - Every call shares the one device array, which keeps the previous
+ *     call's contents (warm-start markers and the horizons of unused slots
+ *     are cleared each call), and the packed models pass through host
+ *     staging arrays shared by the whole process: any two calls that overlap
+ *     in time race, on the host and on the GPU, whatever their threads,
+ *     devices or streams.  Calls made one after another from one thread are
+ *     safe.
  * Returns MPC_ERR_INVALID for n > 64, a horizon > 20, an invalid model or a
  * NULL input; MPC_ERR_CUDA when a runtime call fails. */
 mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_host, const float* x0,

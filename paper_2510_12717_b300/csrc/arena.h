@@ -19,6 +19,7 @@ namespace mpc {
 constexpr int NX = 30;
 constexpr int NC = 22;      // coupled block size
 constexpr int LD = 23;      // column stride of a 22x22 block (odd: no bank conflicts)
+constexpr int LDD_HOST = 23;  // the same stride, for host code reading the lin record
 constexpr int MB = 512;     // floats reserved per 22x22 block (22*23 = 506 used)
 constexpr int NA = 8;       // arm joints
 constexpr int NR = 56;      // inequality rows per stage
@@ -94,7 +95,10 @@ struct Arena {
   int* act;               // [A][maxN*RS]    polish: active-set code per row
   int* order;             // [A] work queue of the persistent kernel: batch rows, longest first
   int* counter;           // [1] next queue position
+  int* fault;             // [F_COUNT] device event counters (F_WAIT_TIMEOUTS: agents whose bounded
+                          //   wait gave up; each retired its warp after draining its copies)
 };
+enum : int { F_WAIT_TIMEOUTS = 0, F_COUNT = 4 };
 
 // lin record layout: dense A_base and B (column-major, stride 23), their
 // compact columns (22 x 6 values, padded to 136), then per stage k the leg
@@ -113,6 +117,9 @@ struct Batch {
   int* counter;           // work-queue counter, zero at launch (NULL: static assignment)
 };
 
+// default poll count of a bounded mbarrier wait (mpc_config.spin_limit)
+constexpr int kSpinLimit = 1 << 22;
+
 struct SolverParams {
   float rho0, sigma, alpha, eps_abs, eps_rel, early_polish;
   int max_iter, fixed_iters, check_every, adaptive_rho, polish, warm_start, warm_polish;
@@ -121,6 +128,9 @@ struct SolverParams {
   int refine_admm; // ... and on a polish that follows ADMM iterations
   int trees;       // 1: some agent has a kinematic tree; mpc_k_rnea runs after the solve
   int split;       // fused form: 1 = set-up and torque map as kernels of their own
+  int spin_limit;  // polls of a bounded mbarrier wait before it gives up (MPC_AGENT_TIMEOUT)
+  int wait_test_slot;  // failure-detection test: the first stage-block wait of this agent slot is
+                       //   armed with no copy behind it, so it runs out (-1: off)
 };
 
 }  // namespace mpc

@@ -128,6 +128,7 @@ static size_t arena_bytes(size_t A, size_t n) {
   f += A * (1 + 30 + 18 + 4 + 1 + 18 * 3 + 2);       // host-path staging
   f += A * (MODEL_F + 2 * SCHED_D + 1);              // model upload staging
   f += A * (kMaxTickets + kMaxGraphs) + (kMaxTickets + kMaxGraphs) * 8;   // work queues
+  f += F_COUNT;                                      // device event counters
   return f * 4;
 }
 
@@ -159,6 +160,8 @@ mpc_status mpc_default_config(mpc_config* cfg) {
   cfg->graph = 0;
   cfg->warm_polish = 1;
   cfg->refine_steps = -1;
+  cfg->spin_limit = mpc::kSpinLimit;
+  cfg->wait_test_agent = -1;
   return MPC_OK;
 }
 
@@ -170,6 +173,8 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
     return MPC_ERR_INVALID;
   if (cfg->precision < MPC_FP32 || cfg->precision > MPC_FP64) return MPC_ERR_INVALID;
   if (cfg->refine_steps < -1 || cfg->refine_steps > 4) return MPC_ERR_INVALID;
+  if (cfg->spin_limit <= 0 || cfg->wait_test_agent < -1 || cfg->wait_test_agent >= cfg->max_agents)
+    return MPC_ERR_INVALID;
   if (cfg->form != MPC_FORM_PLAIN && cfg->form != MPC_FORM_FUSED) return MPC_ERR_INVALID;
   if (!(cfg->rho0 > 0.f) || !(cfg->sigma > 0.f) || !(cfg->alpha > 0.f && cfg->alpha < 2.f) ||
       !(cfg->eps_abs >= 0.f) || !(cfg->eps_rel >= 0.f) || cfg->max_iter <= 0 || cfg->fixed_iters < 0 ||
@@ -224,6 +229,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   AL(a.act, A * n * RS);
   AL(a.order, A);
   AL(a.counter, 4);
+  AL(a.fault, mpc::F_COUNT);
   AL(ctx->d_ids, A);
   AL(ctx->d_x0, A * 30);
   AL(ctx->d_qd, A * 18);
@@ -490,14 +496,18 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   p.adaptive_rho = c.adaptive_rho; p.polish = c.polish; p.warm_start = c.warm_start;
   p.warm_polish = c.warm_polish;
   p.precision = c.precision;
-  // automatic: one step where the factor is TF32 / BF16; otherwise one on a
-  // polish after ADMM (a cold or fallback solve, where it is cheap next to the
-  // iterations) and none on the warm-start polish
-  const bool low = c.precision == MPC_TF32 || c.precision == MPC_BF16;
-  p.refine = c.refine_steps >= 0 ? c.refine_steps : (low ? 1 : 0);
-  p.refine_admm = c.refine_steps >= 0 ? c.refine_steps : 1;
+  // automatic: where the stage products are TF32 / BF16, the steps that win
+  // back the products' rounding (measured against the FP64 oracle: TF32 needs
+  // 2, BF16 3); otherwise one on a polish after ADMM (a cold or fallback
+  // solve, where it is cheap next to the iterations) and none on the
+  // warm-start polish
+  const int low = c.precision == MPC_TF32 ? 2 : c.precision == MPC_BF16 ? 3 : 0;
+  p.refine = c.refine_steps >= 0 ? c.refine_steps : low;
+  p.refine_admm = c.refine_steps >= 0 ? c.refine_steps : (low > 1 ? low : 1);
   p.trees = 0;
   p.split = 1;
+  p.spin_limit = c.spin_limit;
+  p.wait_test_slot = c.wait_test_agent;
   return p;
 }
 
@@ -681,6 +691,59 @@ mpc_status mpc_export_state(mpc_ctx* ctx, int32_t id, float* x, float* u, float*
   return MPC_OK;
 }
 
+mpc_status mpc_export_qp(mpc_ctx* ctx, int32_t id, float* xref, float* uref, float* lo, float* hi, float* A,
+                         float* B, float* c) {
+  if (!ctx) return MPC_ERR_INVALID;
+  if (id < 0 || id >= ctx->cfg.max_agents || !ctx->live[id]) return fail(ctx, MPC_ERR_INVALID, "export_qp: unknown agent");
+  using namespace mpc;
+  const int N = ctx->live[id], n = ctx->cfg.max_horizon;
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  std::vector<float> bxr((N + 1) * VS), bur(N * VS), blo(N * RS), bhi(N * RS), lin(lin_floats(n));
+  std::vector<float> mdl(MODEL_F);
+  CK(cudaMemcpy(bxr.data(), ctx->ar.xref + (size_t)id * (n + 1) * VS, sizeof(float) * bxr.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(bur.data(), ctx->ar.uref + (size_t)id * n * VS, sizeof(float) * bur.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(blo.data(), ctx->ar.rlo + (size_t)id * n * RS, sizeof(float) * blo.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(bhi.data(), ctx->ar.rhi + (size_t)id * n * RS, sizeof(float) * bhi.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(lin.data(), ctx->ar.lin + (size_t)id * lin_floats(n), sizeof(float) * lin.size(), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(mdl.data(), ctx->model + (size_t)id * MODEL_F, sizeof(float) * MODEL_F, cudaMemcpyDeviceToHost));
+  const float dt = mdl[M_DT];
+  for (int k = 0; k <= N; ++k)
+    for (int i = 0; i < 30; ++i)
+      if (xref) xref[k * 30 + i] = bxr[k * VS + i];
+  for (int k = 0; k < N; ++k) {
+    for (int i = 0; i < 30; ++i)
+      if (uref) uref[k * 30 + i] = bur[k * VS + i];
+    for (int r = 0; r < 56; ++r) {
+      if (lo) lo[k * 56 + r] = blo[k * RS + r];
+      if (hi) hi[k * 56 + r] = bhi[k * RS + r];
+    }
+    // the device keeps the coupled 22 x 22 blocks dense (A_base, B) plus the
+    // stage's leg-coupling block dA_k and affine term c_k; the arm joints are
+    // q+ = q + dt qdot
+    const float* st = lin.data() + L_STAGE + k * 64;
+    float* Ak = A ? A + (size_t)k * 900 : nullptr;
+    float* Bk = B ? B + (size_t)k * 900 : nullptr;
+    for (int i = 0; i < 30; ++i)
+      for (int j = 0; j < 30; ++j) {
+        float a = 0.f, b = 0.f;
+        if (i < NC && j < NC) {
+          a = lin[L_ABASE + j * LDD_HOST + i];
+          b = lin[L_B + j * LDD_HOST + i];
+          if (i >= 9 && i < 12 && j >= 12) a += st[(i - 9) * 10 + (j - 12)];
+        } else if (i == j) {
+          a = 1.f;
+          b = dt;
+        }
+        if (Ak) Ak[i * 30 + j] = a;
+        if (Bk) Bk[i * 30 + j] = b;
+      }
+    for (int i = 0; i < 30; ++i)
+      if (c) c[k * 30 + i] = i < NC ? st[32 + i] : 0.f;
+  }
+  return MPC_OK;
+}
+
 mpc_status mpc_import_state(mpc_ctx* ctx, int32_t id, const float* x, const float* u, const float* w,
                             const float* y, float rho) {
   if (!ctx) return MPC_ERR_INVALID;
@@ -786,11 +849,13 @@ mpc_status mpc_get_stats(mpc_ctx* ctx, char* buf, size_t cap) {
   for (int h : ctx->live) live += h != 0;
   // polish attempts of the live agents' last solves: [0] none accepted, [a] a solves
   long long hist[9] = {0};
+  int fault[mpc::F_COUNT] = {0};
   {
     std::vector<int> st((size_t)ctx->cfg.max_agents * mpc::ST_I);
     CK(cudaSetDevice(ctx->cfg.device));
     CK(cudaStreamSynchronize(ctx->stream));
     CK(cudaMemcpy(st.data(), ctx->ar.stat, sizeof(int) * st.size(), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpy(fault, ctx->ar.fault, sizeof(fault), cudaMemcpyDeviceToHost));
     for (int a = 0; a < ctx->cfg.max_agents; ++a) {
       if (!ctx->live[a]) continue;
       const int t = st[(size_t)a * mpc::ST_I + mpc::T_ATTEMPTS];
@@ -801,12 +866,12 @@ mpc_status mpc_get_stats(mpc_ctx* ctx, char* buf, size_t cap) {
            "{\"max_agents\": %d, \"max_horizon\": %d, \"live_agents\": %d, \"arena_bytes\": %zu, "
            "\"form\": \"%s\", \"kernel_launches\": %lld, \"solves\": %lld, \"graph_replays\": %lld, "
            "\"smem_per_block\": %zu, \"warps_per_block\": %d, \"variant\": %d, \"check_every\": %d, "
-           "\"early_polish\": %g, \"graph\": %d, "
+           "\"early_polish\": %g, \"graph\": %d, \"wait_timeouts\": %d, "
            "\"polish_attempts\": [%lld, %lld, %lld, %lld, %lld, %lld, %lld, %lld, %lld]}",
            ctx->cfg.max_agents, ctx->cfg.max_horizon, live, ctx->bytes,
            ctx->cfg.form == MPC_FORM_FUSED ? "fused" : "plain", ctx->launches, ctx->solves, ctx->graph_replays,
            mpc::smem_bytes_per_block(), mpc::WARPS_PER_BLOCK, ctx->cfg.variant, ctx->cfg.check_every,
-           (double)ctx->cfg.early_polish, ctx->cfg.graph, hist[0], hist[1], hist[2], hist[3], hist[4], hist[5],
+           (double)ctx->cfg.early_polish, ctx->cfg.graph, fault[mpc::F_WAIT_TIMEOUTS], hist[0], hist[1], hist[2], hist[3], hist[4], hist[5],
            hist[6], hist[7], hist[8]);
   return MPC_OK;
 }

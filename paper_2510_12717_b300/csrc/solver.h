@@ -14,6 +14,7 @@ constexpr int MPC_AGENT_MAX_ITER_ = 1;
 constexpr int MPC_AGENT_PRIMAL_INFEAS_ = 2;
 constexpr int MPC_AGENT_NAN_ = 4;
 constexpr int MPC_AGENT_TIMEOUT_ = 5;
+constexpr int MPC_AGENT_INACCURATE_ = 6;
 
 size_t smem_bytes_per_block();
 

@@ -509,8 +509,8 @@ __device__ __forceinline__ M3 skew3(float x, float y, float z) {
 
 // ------------------------------------------------- TMA bulk copies (1D)
 // cp.async.bulk global -> shared, completion counted on an mbarrier.  Waits
-// are bounded: after kSpinLimit polls the wait gives up and reports it.
-constexpr int kSpinLimit = 1 << 22;
+// are bounded: after a given number of polls (SolverParams.spin_limit,
+// kSpinLimit by default, arena.h) the wait gives up and reports it.
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -533,10 +533,10 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
       "l"(src), "r"(bytes), "r"(smem_u32(bar))
       : "memory");
 }
-// returns false if the phase did not complete within the spin limit
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase) {
+// returns false if the phase did not complete within `limit` polls
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int limit) {
   uint32_t done = 0;
-  for (int it = 0; it < kSpinLimit; ++it) {
+  for (int it = 0; it < limit; ++it) {
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
         : "=r"(done)

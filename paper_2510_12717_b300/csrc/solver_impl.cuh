@@ -565,16 +565,26 @@ __device__ __noinline__ void factor_admm(const AgentPtrs& ap, float* sm, int lan
 // relaxation, projection onto [lo, hi] and the dual update, stage by stage.
 // The per-stage blocks K_k, H_uu,k^-1 are prefetched one stage ahead into two
 // shared-memory buffers with TMA bulk copies (completion on an mbarrier).
+// Bounded waits: a wait that gives up (after spin_limit polls) marks the
+// pipe timed out for the whole warp; from then on the pipe issues no copy and
+// skips every wait, the agent's solve ends with MPC_AGENT_TIMEOUT, and the
+// kernel drains the copies still in flight (pipe_drain, bounded too) before
+// the warp retires.  `dry` (failure-detection test only) arms the next
+// barrier with no copy behind it, so that its wait runs out with nothing in
+// flight.
 struct Pipe {
   uint64_t* bar;
-  uint32_t ph[2];
-  int timeout;
+  uint32_t st;      // bit b: phase parity of buffer b; bit 2 + b: a copy was issued into
+                    // buffer b and not yet waited for; bit 4: timed out; bit 5: dry
+  int limit;
+  __device__ __forceinline__ bool timed_out() const { return st & 16u; }
 };
+constexpr uint32_t PIPE_TIMEOUT = 16u, PIPE_DRY = 32u;
 
-__device__ __forceinline__ void pipe_init(Pipe& pp, float* sm, int lane) {
+__device__ __forceinline__ void pipe_init(Pipe& pp, float* sm, int lane, int limit) {
   pp.bar = reinterpret_cast<uint64_t*>(sm + S_BAR);
-  pp.ph[0] = pp.ph[1] = 0;
-  pp.timeout = 0;
+  pp.st = 0u;
+  pp.limit = limit > 0 ? limit : kSpinLimit;
   if (lane == 0) {
     mbar_init(pp.bar, 1);
     mbar_init(pp.bar + 1, 1);
@@ -582,19 +592,45 @@ __device__ __forceinline__ void pipe_init(Pipe& pp, float* sm, int lane) {
   }
   __syncwarp();
 }
+// the next issue of this agent's solve is armed with no copy (test only)
+__device__ __forceinline__ void pipe_set_dry(Pipe& pp, bool dry) {
+  pp.st = dry ? (pp.st | PIPE_DRY) : (pp.st & ~PIPE_DRY);
+}
 __device__ __forceinline__ void pipe_issue(Pipe& pp, int b, float* dstK, const float* srcK, float* dstH,
                                            const float* srcH, int lane) {
+  if (pp.st & PIPE_TIMEOUT) return;
+  const uint32_t bytes = (uint32_t)(BLK * sizeof(float));
+  if (pp.st & PIPE_DRY) {
+    if (lane == 0) mbar_expect_tx(pp.bar + b, dstH ? 2 * bytes : bytes);
+    pp.st &= ~PIPE_DRY;
+    return;
+  }
   if (lane == 0) {
     fence_proxy_async();
-    const uint32_t bytes = (uint32_t)(BLK * sizeof(float));
     mbar_expect_tx(pp.bar + b, dstH ? 2 * bytes : bytes);
     tma_load_1d(dstK, srcK, bytes, pp.bar + b);
     if (dstH) tma_load_1d(dstH, srcH, bytes, pp.bar + b);
   }
+  pp.st |= 4u << b;
 }
 __device__ __forceinline__ void pipe_wait(Pipe& pp, int b) {
-  if (!mbar_wait(pp.bar + b, pp.ph[b])) pp.timeout = 1;
-  pp.ph[b] ^= 1u;
+  if (pp.st & PIPE_TIMEOUT) return;
+  // one decision for the whole warp: a lane that gave up times the warp out
+  if (!__all_sync(FULL, mbar_wait(pp.bar + b, pp.st >> b & 1u, pp.limit))) {
+    pp.st |= PIPE_TIMEOUT;
+    return;
+  }
+  pp.st = (pp.st & ~(4u << b)) ^ (1u << b);
+}
+// after a timeout: wait (bounded) for the copies still in flight into this
+// warp's buffers, so that none lands after the warp has retired
+__device__ __forceinline__ void pipe_drain(Pipe& pp) {
+  for (int b = 0; b < 2; ++b)
+    if (pp.st & (4u << b)) {
+      mbar_wait(pp.bar + b, pp.st >> b & 1u, pp.limit);
+      pp.st &= ~(4u << b);
+    }
+  __syncwarp();
 }
 
 // store_dy: also write the change of the row multipliers, y_new - y_old, to
@@ -1321,7 +1357,7 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
 
   polish_rollout(ap, sm, lane, pp, false);
   for (int rs = 0; rs < nref; ++rs) polish_refine(ap, sm, lane, pat, pp);
-  return !warp_or(pp.timeout);
+  return !pp.timed_out();
 }
 
 // Optimality check of the polished point (xt, ut), one backward pass: KKT
@@ -1758,6 +1794,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
       if (lane == 0) ap.st[T_FIRST] = 1;
       return o;
     }
+    if (pp.timed_out()) { o.status = MPC_AGENT_TIMEOUT_; return o; }
     factored = false;   // the polish overwrote the caches
     o.prec = fallback_precision(o.prec);
     polish_warm_start(ap, sm, lane, pat);
@@ -1777,7 +1814,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
   for (it = 1; it <= max_it; ++it) {
     const bool check = (!fixed && (it % prm.check_every == 0)) || it == max_it;
     admm_iteration(ap, sm, lane, rho, prm, pp, pat, check && !fixed);
-    if (warp_or(pp.timeout)) { o.status = MPC_AGENT_TIMEOUT_; break; }
+    if (pp.timed_out()) { o.status = MPC_AGENT_TIMEOUT_; break; }
     if (!check) continue;
     o.r = admm_residuals(ap, sm, lane, prm, pat);
     if (!(isfinite(o.r.rp) && isfinite(o.r.rd))) { o.status = MPC_AGENT_NAN_; break; }
@@ -1807,6 +1844,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
         o.r = pr;
         break;
       }
+      if (pp.timed_out()) { o.status = MPC_AGENT_TIMEOUT_; break; }
       factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, o.prec);   // the polish overwrote the caches
       ++o.refac;
     }
@@ -2016,7 +2054,30 @@ __device__ void final_polish(const AgentPtrs& ap, float* sm, int lane, const Sol
     o.polished = 1;
     o.status = MPC_AGENT_SOLVED_;
     o.r = pr;
+  } else if (pp.timed_out()) {
+    o.status = MPC_AGENT_TIMEOUT_;
   }
+}
+
+// SOLVED is kept for a point that passed the polish's KKT check (exact on its
+// active set up to rounding); an ADMM iterate that met the stopping test
+// without such a check is only as accurate as that test
+__device__ __forceinline__ void certify(Outcome& o) {
+  if (o.status == MPC_AGENT_SOLVED_ && !o.polished) o.status = MPC_AGENT_INACCURATE_;
+}
+
+// An agent whose bounded wait gave up: its outputs are zeroed (the torque
+// kernel does the same for the fused form), the copies still in flight into
+// the warp's buffers are drained, and the event is counted.  The caller then
+// retires the warp: it takes no further agent, so the timed-out barriers are
+// never reused.
+__device__ void retire_timed_out(const Arena& a, const AgentPtrs& ap, Pipe& pp, int lane) {
+  if (lane < 18) { ap.out[O_TAU + lane] = 0.f; ap.out[O_QSET + lane] = 0.f; ap.out[O_QDSET + lane] = 0.f; }
+  if (lane == 0) {
+    ap.out[O_V] = 0.f;
+    atomicAdd(a.fault + F_WAIT_TIMEOUTS, 1);
+  }
+  pipe_drain(pp);
 }
 
 // ============================================================ kernels
@@ -2037,7 +2098,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_fused(Arena 
   float* sm = warp_smem();
   const LanePat pat = lane_pattern(lane);
   Pipe pp;
-  pipe_init(pp, sm, lane);
+  pipe_init(pp, sm, lane, prm.spin_limit);
   int static_row = blockIdx.x * WARPS_PER_BLOCK + (threadIdx.x >> 5);
   const int nw = gridDim.x * WARPS_PER_BLOCK;
   for (;;) {
@@ -2054,6 +2115,7 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_fused(Arena 
     const int row = b.order ? b.order[idx] : idx;
     if (!valid_slot(a, b, row)) continue;
     const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
+    pipe_set_dry(pp, b.ids[row] == prm.wait_test_slot);
     if (prm.split) {
       // set up by mpc_k_setup (the torque map follows in mpc_k_torque)
       if (ap.st[T_STATUS] == MPC_AGENT_NAN_) continue;
@@ -2064,7 +2126,12 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_fused(Arena 
     }
     Outcome o = admm_solve<PREC>(ap, sm, lane, prm, false, pp, pat);
     final_polish<PREC>(ap, sm, lane, prm, o, pat, pp);
+    certify(o);
     write_outcome(ap, lane, o);
+    if (o.status == MPC_AGENT_TIMEOUT_) {
+      retire_timed_out(a, ap, pp, lane);
+      break;
+    }
     if (!prm.split) torque_map(ap, lane);
     __syncwarp();
   }
@@ -2122,9 +2189,11 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_admm(Arena a
   load_lin(ap, sm, lane);
   const LanePat pat = lane_pattern(lane);
   Pipe pp;
-  pipe_init(pp, sm, lane);
+  pipe_init(pp, sm, lane, prm.spin_limit);
+  pipe_set_dry(pp, b.ids[row] == prm.wait_test_slot);
   const Outcome o = admm_solve<PREC>(ap, sm, lane, prm, true, pp, pat);
   write_outcome(ap, lane, o);
+  if (o.status == MPC_AGENT_TIMEOUT_) retire_timed_out(a, ap, pp, lane);
 }
 
 template <int MINB, int PREC>
@@ -2145,15 +2214,26 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32, MINB) mpc_k_polish(Arena
   o.r.dn = ap.out[O_DUAL_N];
   o.r.ps = o.r.ds = 0.f;
   o.prec = prm.warm_polish && prm.fixed_iters == 0 ? fallback_precision(prm.precision) : prm.precision;
-  if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_ ||
+  if (o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_ ||
       o.status == MPC_AGENT_PRIMAL_INFEAS_)
     return;
+  if (!prm.polish) {
+    certify(o);
+    if (lane == 0) ap.st[T_STATUS] = o.status;
+    return;
+  }
   load_lin(ap, sm, lane);
   copy_n(sm + S_BV, ap.lin + L_BV, 136 / 4, lane);
   Pipe pp;
-  pipe_init(pp, sm, lane);
+  pipe_init(pp, sm, lane, prm.spin_limit);
   final_polish<PREC>(ap, sm, lane, prm, o, lane_pattern(lane), pp);
+  certify(o);
   if (o.polished) write_outcome(ap, lane, o);
+  else if (lane == 0) ap.st[T_STATUS] = o.status;
+  if (o.status == MPC_AGENT_TIMEOUT_) {
+    write_outcome(ap, lane, o);
+    retire_timed_out(a, ap, pp, lane);
+  }
 }
 
 __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) mpc_k_torque(Arena a, Batch b) {

@@ -1,13 +1,16 @@
 // Allocation-free solve entry point (mpc_solve_static).
 //
 // Some callers cannot allocate device memory at the moment they need a
-// solve: code running inside a CUDA stream capture (cudaMalloc is not a
-// capturable operation), simulators and plugins that hand over only their own
-// device buffers and forbid allocation on their hot path, or processes whose
+// solve: simulators and plugins that hand over only their own device buffers
+// and forbid allocation on their hot path, real-time control loops that must
+// not enter the device allocator once running, or processes whose device
 // allocator is owned by another framework.  For them this file keeps all of
-// the solver's workspace in one file-scope static device array, sized for
-// at most kStaticMaxAgents agents of horizon up to kStaticMaxHorizon; every
-// GPU that loads the library holds it until the process exits.
+// the solver's workspace in one file-scope static device array, sized for at
+// most kStaticMaxAgents agents of horizon up to kStaticMaxHorizon; every GPU
+// that loads the library holds it until the process exits.  The packed models
+// pass through process-wide host staging arrays on their way there, so two
+// calls that overlap in time race on the host as well as on the GPU, whatever
+// their devices or streams.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <string.h>
@@ -26,7 +29,7 @@ constexpr size_t align256(size_t b) { return (b + 255) / 256 * 256; }
 
 struct Layout {
   size_t model, sched, horizon, ids, xs, us, ws, ys, rho, warm, out, stat, inp, xref, uref, rlo, rhi,
-      rcls, lin, cK, cH, cE, cEl, cD, xt, ut, dv, act, order, counter, total;
+      rcls, lin, cK, cH, cE, cEl, cD, xt, ut, dv, act, order, counter, fault, total;
 };
 
 constexpr Layout make_layout(size_t A, size_t n) {
@@ -64,6 +67,7 @@ constexpr Layout make_layout(size_t A, size_t n) {
   L.act = take(A * n * RS * 4);
   L.order = take(A * 4);
   L.counter = take(16);
+  L.fault = take(mpc::F_COUNT * 4);
   L.total = o;
   return L;
 }
@@ -76,7 +80,8 @@ static __device__ __align__(256) unsigned char g_static_scratch[kL.total];
 
 unsigned char* g_base[kMaxDevices] = {};   // device address of g_static_scratch, per device
 
-// host staging of one call's packed models (no allocation: fixed size)
+// host staging of one call's packed models (no allocation: fixed size);
+// process-wide, shared by every device and thread
 float g_host_model[kStaticMaxAgents * mpc::MODEL_F];
 double g_host_sched[kStaticMaxAgents * mpc::SCHED_D];
 int g_host_horizon[kStaticMaxAgents];
@@ -200,6 +205,7 @@ extern "C" mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_
   a.act = at<int>(b, kL.act);
   a.order = at<int>(b, kL.order);
   a.counter = at<int>(b, kL.counter);
+  a.fault = at<int>(b, kL.fault);
   int* d_ids = at<int>(b, kL.ids);
 
   // models, horizons and the slot list; the whole horizon array is rewritten
@@ -227,6 +233,8 @@ extern "C" mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_
   prm.refine_admm = 1;
   prm.trees = 0;
   prm.split = 0;          // no kinematic trees here: the diagonal joint model
+  prm.spin_limit = c.spin_limit;
+  prm.wait_test_slot = -1;
   mpc::Batch bt{n, d_ids, x0, qd_meas, cmd, phase, nullptr, nullptr};
   if (mpc::launch_solve(a, bt, prm, MPC_FORM_FUSED, 0, st, nullptr, c.variant) != cudaSuccess) return MPC_ERR_CUDA;
   if (mpc::launch_gather(a, n, d_ids, tau, q_set, qd_set, value, agent_status, st) != cudaSuccess)

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(HERE, "libmpcgpu.so")
 MPC_OK, MPC_ERR_INVALID, MPC_ERR_BUDGET, MPC_ERR_CUDA = 0, 1, 2, 3
 MPC_ERR_NOT_READY, MPC_ERR_TIMEOUT, MPC_ERR_STATE = 4, 5, 6
 AGENT_SOLVED, AGENT_MAX_ITER, AGENT_PRIMAL_INFEAS, AGENT_DUAL_INFEAS, AGENT_NAN, AGENT_TIMEOUT = 0, 1, 2, 3, 4, 5
+AGENT_INACCURATE = 6
 FORM_PLAIN, FORM_FUSED = 0, 1
 FP32, TF32, BF16, FP64 = 0, 1, 2, 3
 PEAK_FP32_FMA, PEAK_FP64_FMA, PEAK_TF32_MMA_SYNC, PEAK_BF16_MMA_SYNC = 0, 1, 2, 3
@@ -35,7 +36,7 @@ class MpcConfig(C.Structure):
         ("fixed_iters", C.c_int), ("check_every", C.c_int), ("adaptive_rho", C.c_int),
         ("polish", C.c_int), ("warm_start", C.c_int), ("variant", C.c_int),
         ("early_polish", C.c_float), ("graph", C.c_int), ("warm_polish", C.c_int),
-        ("refine_steps", C.c_int),
+        ("refine_steps", C.c_int), ("spin_limit", C.c_int), ("wait_test_agent", C.c_int),
     ]
 
 
@@ -103,6 +104,7 @@ SIGNATURES = {
     "mpc_get_agent_stats": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P]),
     "mpc_export_state": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P]),
     "mpc_import_state": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, C.c_float]),
+    "mpc_export_qp": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P]),
     "mpc_solve_static": (C.c_int, [C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
     "mpc_get_stats": (C.c_int, [_P, C.c_char_p, C.c_size_t]),
     "mpc_last_error": (C.c_char_p, [_P]),
@@ -330,6 +332,17 @@ class Solver:
         self._check(self.lib.mpc_export_state(self.ctx, int(agent_id), _ptr(x), _ptr(u), _ptr(w),
                                               _ptr(y), _ptr(rho)))
         return dict(x=x, u=u, w=w, y=y, rho=float(rho[0]))
+
+    def export_qp(self, agent_id: int, N: int) -> dict:
+        """mpc_export_qp: references, row bounds and linearised dynamics of the
+        agent's last solve."""
+        out = dict(x_ref=np.empty((N + 1, 30), np.float32), u_ref=np.empty((N, 30), np.float32),
+                   lo=np.empty((N, 56), np.float32), hi=np.empty((N, 56), np.float32),
+                   A=np.empty((N, 30, 30), np.float32), B=np.empty((N, 30, 30), np.float32),
+                   c=np.empty((N, 30), np.float32))
+        self._check(self.lib.mpc_export_qp(self.ctx, int(agent_id), *[_ptr(out[k]) for k in
+                                                                     ("x_ref", "u_ref", "lo", "hi", "A", "B", "c")]))
+        return out
 
     def import_state(self, agent_id: int, st: dict):
         arrs = [np.ascontiguousarray(st[k], np.float32) for k in ("x", "u", "w", "y")]

@@ -198,18 +198,37 @@ def test_warm_fallback_after_large_change_matches_oracle(mpcgpu):
     print(f"\n[joints near limits] ADMM fallbacks: {int(fell_back.sum())} of {len(ids)}, "
           f"iterations mean {st['iters'][fell_back].mean() if fell_back.any() else 0:.1f}")
     assert fell_back.sum() >= 2
-    assert (r["status"] == 0).all()
-    # a polished result is the optimum of its active set; an agent whose
-    # optimum holds one joint at both its rate bound and its joint limit at
-    # one stage is not polished (that elimination is not supported) and keeps
-    # the ADMM point, accurate to the solver's stopping tolerance only
-    pol = st["polished"] > 0
+    # every agent (including those whose optimum rides a joint rate bound onto
+    # its limit) ends polished: the KKT-checked optimum, held to the full bar
+    assert (r["status"] == 0).all(), r["status"]
+    assert (st["polished"] > 0).all()
     ok = torque_close(r["tau"], ref["tau"])
-    assert ok[pol].all(), np.argwhere(~ok & pol[:, None])
-    assert pol.mean() >= 0.9
-    loose = np.isclose(r["tau"], ref["tau"], rtol=1e-2, atol=1e-1)
-    assert loose.all(), np.argwhere(~loose)
+    assert ok.all(), np.argwhere(~ok)
     s.close()
+
+
+def test_rho_update_refactors_and_matches_oracle(mpcgpu):
+    # ADMM started far from its adapted step size (rho0 = 1e-3), with the
+    # polish only after ADMM: OSQP's rule must raise rho and refactor the
+    # Riccati blocks (A6) for most agents before the iterate converges (an
+    # agent whose residual ratio never leaves the 5x band keeps rho0); every
+    # polished result is the FP64 optimum
+    ids = np.arange(24)
+    model, inp = agents("uneven", ids)
+    inp32 = device_inputs(inp)
+    s = mpcgpu.Solver(max_agents=24, max_horizon=20, stream=torch.cuda.current_stream().cuda_stream,
+                      rho0=1e-3, warm_polish=0, early_polish=0.0)
+    s.set_models(model, ids)
+    r = s.solve_host(ids, inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+    st = s.agent_stats(ids)
+    s.close()
+    ref = _oracle(model, inp32)
+    print(f"\n[rho update] refactors {st['refactors'].tolist()} iterations {st['iters'].tolist()}")
+    assert (st["refactors"] > 0).mean() >= 0.5 and st["refactors"].sum() >= 12
+    assert (r["status"] == 0).all(), r["status"]
+    assert (st["polished"] > 0).all()
+    ok = torque_close(r["tau"], ref["tau"])
+    assert ok.all(), np.argwhere(~ok)
 
 
 def test_edge_cases_empty_nan_and_order(mpcgpu):
@@ -273,16 +292,17 @@ def test_full_size_mixed_16k_sampled(mpcgpu):
     solved = got["status"] == 0
     print(f"\n[16k] solved {solved.mean():.4f} polished {st['polished'].mean():.4f} "
           f"iters mean {st['iters'].mean():.1f} max {st['iters'].max()}")
-    assert solved.mean() >= 0.99
+    assert solved.mean() >= 0.999
     assert np.isfinite(got["tau"]).all()
     rng = np.random.default_rng(7)
     sample = np.sort(rng.choice(n, 24, replace=False))
+    assert (got["status"][sample] == 0).all(), got["status"][sample]
     sm = {k: v[sample] for k, v in model.items()}
     si = {k: v[sample] for k, v in inp32.items()}
     ref = _oracle(sm, si)
     ok = torque_close(got["tau"][sample], ref["tau"])
     _report("16k-sample", got["tau"][sample], ref["tau"], {k: v[sample] for k, v in st.items()})
-    assert ok[solved[sample]].all()
+    assert ok.all(), np.argwhere(~ok)
     got["solver"].close()
 
 

@@ -60,20 +60,17 @@ def test_fp32_and_fp64_factor_match_oracle(mpcgpu, precision, refine):
 
 
 @pytest.mark.parametrize("precision", [1, 2], ids=["tf32", "bf16"])
-def test_tensor_core_factor_runs_and_reports_accuracy(mpcgpu, precision):
-    # TF32 / BF16 stage products with one refinement step: reported, not
-    # required to meet the FP64 torque tolerance on every agent; every agent
-    # is solved (one whose polish first fails falls back to FP32 factors)
+def test_tensor_core_factor_with_refinement_matches_oracle(mpcgpu, precision):
+    # TF32 / BF16 stage products, their rounding won back by the automatic
+    # refinement steps (2 for TF32, 3 for BF16): every agent solved and within
+    # the FP64 torque tolerance; the norm-wise error is printed per replan
     model, inps, refs = _case("uneven", 32)
     for replan, ((r, st), ref) in enumerate(zip(_solve(mpcgpu, model, inps, precision, -1), refs)):
-        assert np.isfinite(r["tau"]).all()
         assert (r["status"] == 0).all(), np.argwhere(r["status"] != 0)
-        ok = torque_close(r["tau"], ref["tau"]).all(axis=1)
         rel = np.linalg.norm(r["tau"] - ref["tau"], axis=1) / np.maximum(np.linalg.norm(ref["tau"], axis=1), 1e-9)
-        print(f"\n[precision {precision} replan {replan}] within tolerance {ok.mean():.3f}, "
-              f"median rel err {np.median(rel):.2e}, max {rel.max():.2e}")
-        assert ok.mean() >= 0.75
-        assert np.median(rel) < 1e-4
+        print(f"\n[precision {precision} replan {replan}] median rel err {np.median(rel):.2e}, max {rel.max():.2e}")
+        ok = torque_close(r["tau"], ref["tau"])
+        assert ok.all(), np.argwhere(~ok)
 
 
 def test_tensor_core_products_track_fp32(mpcgpu):
