@@ -44,8 +44,8 @@ enum : int {
   S_AV = S_B + 512,                                      // compact A_k columns: 22 x 6
   S_BV = S_AV + 136,                                     // compact B columns: 22 x 6
   S_VEC = S_BV + 136,                                    // 12 vectors of 64
-  S_BAR = S_VEC + 12 * 64,                               // 2 mbarriers (16 bytes)
-  W_FLOATS = S_BAR + 4
+  S_BAR = S_VEC + 12 * 64,                               // 4 mbarriers (32 bytes)
+  W_FLOATS = S_BAR + 8
 };
 enum : int { V_S = 0, V_H = 1, V_X = 2, V_U = 3, V_XN = 4, V_ROW = 5, V_T = 6, V_G = 7,
              V_C = 8, V_FLAGS = 9, V_ACT = 10, V_D = 11 };
@@ -190,6 +190,21 @@ __device__ __forceinline__ float r24_mtv(const float* M, const float* v, int lan
     a1 = fmaf(M[(j + 1) * R24 + i], v[j + 1], a1);
   }
   return a0 + a1;
+}
+// (M1^T v)_i and (M2^T v)_i in one pass: four independent sums, each matrix's
+// in the order of r24_mtv (same results, half the dependent chain)
+__device__ __forceinline__ float2 r24_mtv2(const float* M1, const float* M2, const float* v, int lane) {
+  const int i = lane < NC ? lane : NC - 1;
+  float a0 = 0.f, a1 = 0.f, b0 = 0.f, b1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < NC; j += 2) {
+    const float v0 = v[j], v1 = v[j + 1];
+    a0 = fmaf(M1[j * R24 + i], v0, a0);
+    a1 = fmaf(M1[(j + 1) * R24 + i], v1, a1);
+    b0 = fmaf(M2[j * R24 + i], v0, b0);
+    b1 = fmaf(M2[(j + 1) * R24 + i], v1, b1);
+  }
+  return make_float2(a0 + a1, b0 + b1);
 }
 // y_i = sum_j M(i, j) v_j  (row of the lane, float4 loads)
 __device__ __forceinline__ float r24_mv(const float* M, const float* v, int lane) {
@@ -431,6 +446,25 @@ __device__ __forceinline__ float cm_mv(const float* M, const float* v, int lane)
     a0 = fmaf(M[j * LDD + i], v[j], a0);
     a1 = fmaf(M[(j + 1) * LDD + i], v[j + 1], a1);
   }
+  return a0 + a1;
+}
+
+// the same product for a matrix with the sparsity of A_base and B (rows 0-11
+// have their nonzeros in columns 0-11, rows 12-21 only on the diagonal):
+// the structural zeros are skipped, the nonzero terms accumulate in the same
+// two sums (even / odd columns) in the same order, so the result equals
+// cm_mv's
+__device__ __forceinline__ float cm_mv_s(const float* M, const float* v, int lane) {
+  const int i = lane < NC ? lane : NC - 1;
+  float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 12; j += 2) {
+    a0 = fmaf(M[j * LDD + i], v[j], a0);
+    a1 = fmaf(M[(j + 1) * LDD + i], v[j + 1], a1);
+  }
+  const float m = i >= 12 ? M[i * LDD + i] : 0.f;
+  if (i & 1) a1 = fmaf(m, v[i], a1);
+  else a0 = fmaf(m, v[i], a0);
   return a0 + a1;
 }
 

@@ -29,7 +29,7 @@ __device__ __forceinline__ float qt_x(const AgentPtrs& ap, int k, int i, float r
 // A_k x for the coupled block, lane row: dense A_base (column-major) plus
 // the contact-dependent block dA_k (rows 9-11 x columns 12-21)
 __device__ __forceinline__ float ak_mv(const float* Ab, const float* dA, const float* v, int lane) {
-  float r = cm_mv(Ab, v, lane);
+  float r = cm_mv_s(Ab, v, lane);
   if (lane >= 9 && lane < 12) {
     const float* row = dA + (lane - 9) * 10;
 #pragma unroll
@@ -573,21 +573,22 @@ __device__ __noinline__ void factor_admm(const AgentPtrs& ap, float* sm, int lan
 // barrier with no copy behind it, so that its wait runs out with nothing in
 // flight.
 struct Pipe {
-  uint64_t* bar;
-  uint32_t st;      // bit b: phase parity of buffer b; bit 2 + b: a copy was issued into
-                    // buffer b and not yet waited for; bit 4: timed out; bit 5: dry
+  uint64_t* bar;    // kPipeBufs mbarriers, one per shared-memory buffer
+  uint32_t st;      // bit b: phase parity of buffer b; bit 8 + b: a copy was issued into
+                    // buffer b and not yet waited for; bit 16: timed out; bit 17: dry
   int limit;
-  __device__ __forceinline__ bool timed_out() const { return st & 16u; }
+  __device__ __forceinline__ bool timed_out() const { return st & PIPE_TIMEOUT_BIT; }
+  static constexpr uint32_t PIPE_TIMEOUT_BIT = 1u << 16;
 };
-constexpr uint32_t PIPE_TIMEOUT = 16u, PIPE_DRY = 32u;
+constexpr int kPipeBufs = 4;
+constexpr uint32_t PIPE_TIMEOUT = Pipe::PIPE_TIMEOUT_BIT, PIPE_DRY = 1u << 17;
 
 __device__ __forceinline__ void pipe_init(Pipe& pp, float* sm, int lane, int limit) {
   pp.bar = reinterpret_cast<uint64_t*>(sm + S_BAR);
   pp.st = 0u;
   pp.limit = limit > 0 ? limit : kSpinLimit;
   if (lane == 0) {
-    mbar_init(pp.bar, 1);
-    mbar_init(pp.bar + 1, 1);
+    for (int b = 0; b < kPipeBufs; ++b) mbar_init(pp.bar + b, 1);
     fence_mbar_init();
   }
   __syncwarp();
@@ -605,13 +606,14 @@ __device__ __forceinline__ void pipe_issue(Pipe& pp, int b, float* dstK, const f
     pp.st &= ~PIPE_DRY;
     return;
   }
+  // no proxy fence here: every writer of the caches (factor_admm,
+  // polish_solve) fences once after its stores, before the first copy
   if (lane == 0) {
-    fence_proxy_async();
     mbar_expect_tx(pp.bar + b, dstH ? 2 * bytes : bytes);
     tma_load_1d(dstK, srcK, bytes, pp.bar + b);
     if (dstH) tma_load_1d(dstH, srcH, bytes, pp.bar + b);
   }
-  pp.st |= 4u << b;
+  pp.st |= 256u << b;
 }
 __device__ __forceinline__ void pipe_wait(Pipe& pp, int b) {
   if (pp.st & PIPE_TIMEOUT) return;
@@ -620,26 +622,61 @@ __device__ __forceinline__ void pipe_wait(Pipe& pp, int b) {
     pp.st |= PIPE_TIMEOUT;
     return;
   }
-  pp.st = (pp.st & ~(4u << b)) ^ (1u << b);
+  pp.st = (pp.st & ~(256u << b)) ^ (1u << b);
 }
 // after a timeout: wait (bounded) for the copies still in flight into this
 // warp's buffers, so that none lands after the warp has retired
 __device__ __forceinline__ void pipe_drain(Pipe& pp) {
-  for (int b = 0; b < 2; ++b)
-    if (pp.st & (4u << b)) {
+  for (int b = 0; b < kPipeBufs; ++b)
+    if (pp.st & (256u << b)) {
       mbar_wait(pp.bar + b, pp.st >> b & 1u, pp.limit);
-      pp.st &= ~(4u << b);
+      pp.st &= ~(256u << b);
     }
   __syncwarp();
 }
+// The four R24 buffers of a pass that reads only K_k (forward rollouts):
+// stage k in buffer k mod 4, copied three stages ahead
+__device__ __forceinline__ float* kslot(float* sm, int b) {
+  return sm + (b == 0 ? S_P : b == 1 ? S_X : b == 2 ? S_H : S_K);
+}
+
+// Per-lane global inputs of one stage of the ADMM sweeps.  Each stage's are
+// loaded while the previous stage computes (one stage ahead), so a stage
+// waits on memory once, for the TMA copy of its blocks, instead of once per
+// step that uses a global value.
+struct BwdPre {
+  float rc0, w0, y0, rc1, w1, y1;   // rows lane and lane + 32 of stage k
+  float xr, xk;                     // x_ref,k and x_k (linear term of x_k)
+  float rq, wq, yq;                 // joint-box row lane + 26 of stage k - 1 (lanes 12-29)
+  float ur, uk;                     // u_ref,k and u_k
+  float e, e2;                      // cE_k[lane], cE_k[32 + lane]
+  float a[3];                       // lanes 12-21: dA_k entries of the lane's compact A column
+};
+struct FwdPre {
+  float dk, a0, a1, e;              // d_k, dA_k[lane], dA_k[32 + lane] (c_k), arm gain
+  float w0, y0, rc0, lo0, hi0;      // row lane of stage k
+  float w1, y1, rc1, lo1, hi1;      // row lane + 32
+  float uo, xo;                     // u_k and x_{k+1} of the last iterate (relaxation)
+};
 
 // store_dy: also write the change of the row multipliers, y_new - y_old, to
 // the agent's cEl scratch (free outside a polish), for the primal
 // infeasibility test that follows a residual check
-__device__ void admm_iteration(const AgentPtrs& ap, float* sm, int lane, float rho, const SolverParams& prm,
-                               Pipe& pp, const LanePat& pat, bool store_dy = false) {
+__device__ __noinline__ void admm_iteration(const AgentPtrs& ap, float* sm, int lane, float rho,
+                                            const SolverParams& prm, Pipe& pp, const LanePat& pat,
+                                            bool store_dy = false) {
+  // the agent's arrays in registers (a reference to the caller's struct
+  // would be re-read after every store)
   const int N = ap.N;
-  const float* md = ap.mdl;
+  const float* __restrict__ md = ap.mdl;
+  float* __restrict__ X = ap.x; float* __restrict__ U = ap.u;
+  float* __restrict__ Wr = ap.w; float* __restrict__ Yr = ap.y;
+  const float* __restrict__ XR = ap.xref; const float* __restrict__ UR = ap.uref;
+  const float* __restrict__ LO = ap.rlo; const float* __restrict__ HI = ap.rhi;
+  const float* __restrict__ RC = ap.rcls; const float* __restrict__ LIN = ap.lin + L_STAGE;
+  const float* __restrict__ CE = ap.cE; float* __restrict__ DV = ap.dv;
+  float* __restrict__ XT = ap.xt; float* __restrict__ UT = ap.ut; float* __restrict__ EL = ap.cEl;
+  const float* CK = ap.cK; const float* CH = ap.cH;
   const float dt = md[M_DT], mu = md[M_MU], sigma = prm.sigma, alpha = prm.alpha;
   float* Ab = sm + S_AB; float* Bm = sm + S_B;
   float* const K0 = sm + S_P; float* const K1 = sm + S_X;
@@ -649,105 +686,198 @@ __device__ void admm_iteration(const AgentPtrs& ap, float* sm, int lane, float r
   float* vU = vec + V_U * 64; float* vXN = vec + V_XN * 64; float* vR = vec + V_ROW * 64;
   float* vA = vec + V_D * 64;
   const bool arm = lane >= NC && lane < 30;
+  const bool jl = lane >= 12 && lane < 30;      // joint lanes (rate row lane + 8, box row lane + 26)
+  const bool r1 = lane < NR - 32;               // the lane owns a second row
   const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
   const float twoR = lane < 30 ? 2.f * dt * md[M_R + lane] : 0.f;
-
-  // linear term of x_k (k >= 1): -2dt Q xr_k - sigma x_k - C_x^T (rho w - y) of stage k-1
-  auto qlin = [&](int k) -> float {
-    float v = -twoQ * ap.xref[k * VS + lane] - sigma * ap.x[k * VS + lane];
-    if (lane >= 12 && lane < 30) {
-      const int r = lane + 26;
-      v -= rho * ap.rcls[(k - 1) * RS + r] * ap.w[(k - 1) * RS + r] - ap.y[(k - 1) * RS + r];
+  // The row algebra of the lane without branches on its index (the lanes of
+  // a warp would otherwise run each case in turn), as index and coefficient
+  // tables built once per call:
+  //  (C_u^T v)_lane = v[t0] + ta (((ts[0] v[tj[0]] + ts[1] v[tj[1]]) + ts[2] v[tj[2]]) + ts[3] v[tj[3]]),
+  //  the sums in the order of cuT; index 56 of the row vector is held at zero;
+  //  row lane (+ 32 q) of C_u u + C_x x_{k+1} = fmaf(cs1[q], z[ci1[q]], cs0[q] z[ci0[q]])
+  //  over z = [u (64) | x_{k+1} (64)], the terms in the order of crow; z[30] = u_30 = 0.
+  int t0 = 56, tj[4] = {56, 56, 56, 56};
+  float ta = 0.f, ts[4] = {0.f, 0.f, 0.f, 0.f};
+  if (lane < 12) {
+    const int f = lane / 6, c = lane - 6 * f, pp0 = 12 + 4 * f;
+    t0 = lane;
+    if (c == 0) { ta = 1.f; tj[0] = pp0; tj[1] = pp0 + 1; ts[0] = 1.f; ts[1] = -1.f; }
+    if (c == 1) { ta = 1.f; tj[0] = pp0 + 2; tj[1] = pp0 + 3; ts[0] = 1.f; ts[1] = -1.f; }
+    if (c == 2) {
+      ta = -mu;
+#pragma unroll
+      for (int t = 0; t < 4; ++t) { tj[t] = pp0 + t; ts[t] = 1.f; }
     }
+  } else if (lane < 30) {
+    t0 = lane + 8;
+  }
+  int ci0[2], ci1[2];
+  float cs0[2], cs1[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const int r = lane + 32 * q;
+    ci0[q] = 30; ci1[q] = 30; cs0[q] = 0.f; cs1[q] = 0.f;
+    if (r < 12) { ci0[q] = r; cs0[q] = 1.f; }
+    else if (r < 20) {
+      const int f = (r - 12) >> 2, t = (r - 12) & 3, bb = 6 * f;
+      ci0[q] = bb + (t >> 1); cs0[q] = (t & 1) ? -1.f : 1.f;
+      ci1[q] = bb + 2; cs1[q] = -mu;
+    } else if (r < 38) { ci0[q] = r - 8; cs0[q] = 1.f; }
+    else if (r < NR) { ci0[q] = 64 + r - 26; cs0[q] = 1.f; }
+  }
+  if (lane >= NR - 32) vR[lane + 32] = 0.f;   // rows 56-63: the zero of the tables
+  auto cuT_t = [&](const float* v) -> float {
+    const float S = fmaf(ts[3], v[tj[3]], fmaf(ts[2], v[tj[2]], fmaf(ts[1], v[tj[1]], ts[0] * v[tj[0]])));
+    return fmaf(ta, S, v[t0]);
+  };
+  auto crow_t = [&](const float* z, int q) -> float { return fmaf(cs1[q], z[ci1[q]], cs0[q] * z[ci0[q]]); };
+
+  auto load_bwd = [&](int k) {
+    BwdPre q;
+    const int o = k * RS;
+    q.rc0 = RC[o + lane]; q.w0 = Wr[o + lane]; q.y0 = Yr[o + lane];
+    q.rc1 = r1 ? RC[o + lane + 32] : 0.f; q.w1 = r1 ? Wr[o + lane + 32] : 0.f; q.y1 = r1 ? Yr[o + lane + 32] : 0.f;
+    q.xr = XR[k * VS + lane]; q.xk = X[k * VS + lane];
+    const bool hq = jl && k >= 1;
+    q.rq = hq ? RC[o - RS + lane + 26] : 0.f;
+    q.wq = hq ? Wr[o - RS + lane + 26] : 0.f;
+    q.yq = hq ? Yr[o - RS + lane + 26] : 0.f;
+    q.ur = UR[k * VS + lane]; q.uk = U[k * VS + lane];
+    q.e = CE[k * 64 + lane]; q.e2 = CE[k * 64 + 32 + lane];
+    const bool aj = lane >= 12 && lane < NC;
+#pragma unroll
+    for (int t = 0; t < 3; ++t) q.a[t] = aj ? LIN[k * 64 + t * 10 + (lane - 12)] : 0.f;
+    return q;
+  };
+  auto load_fwd = [&](int k) {
+    FwdPre q;
+    const int o = k * RS;
+    q.dk = DV[k * VS + lane];
+    q.a0 = LIN[k * 64 + lane]; q.a1 = LIN[k * 64 + 32 + lane];
+    q.e = CE[k * 64 + lane];
+    q.w0 = Wr[o + lane]; q.y0 = Yr[o + lane]; q.rc0 = RC[o + lane]; q.lo0 = LO[o + lane]; q.hi0 = HI[o + lane];
+    q.w1 = r1 ? Wr[o + lane + 32] : 0.f; q.y1 = r1 ? Yr[o + lane + 32] : 0.f;
+    q.rc1 = r1 ? RC[o + lane + 32] : 0.f; q.lo1 = r1 ? LO[o + lane + 32] : 0.f;
+    q.hi1 = r1 ? HI[o + lane + 32] : 0.f;
+    q.uo = U[k * VS + lane]; q.xo = X[(k + 1) * VS + lane];
+    return q;
+  };
+  // linear term of x_k (k >= 1): -2dt Q xr_k - sigma x_k - C_x^T (rho w - y) of stage k-1
+  auto qlin = [&](const BwdPre& q) -> float {
+    float v = -twoQ * q.xr - sigma * q.xk;
+    if (jl) v -= rho * q.rq * q.wq - q.yq;
     return v;
   };
+
   // ---- backward sweep: p_k, d_k
-  pipe_issue(pp, 0, K0, ap.cK + (size_t)(N - 1) * BLK, H0, ap.cH + (size_t)(N - 1) * BLK, lane);
-  float p = lane < 30 ? qlin(N) : 0.f;
+  pipe_issue(pp, 0, K0, CK + (size_t)(N - 1) * BLK, H0, CH + (size_t)(N - 1) * BLK, lane);
+  float p = 0.f;
+  {
+    // x_N's linear term: its joint-box row is row lane + 26 of stage N - 1
+    const bool hq = jl;
+    const float xr = XR[N * VS + lane], xk = X[N * VS + lane];
+    const float rq = hq ? RC[(N - 1) * RS + lane + 26] : 0.f;
+    const float wq = hq ? Wr[(N - 1) * RS + lane + 26] : 0.f;
+    const float yq = hq ? Yr[(N - 1) * RS + lane + 26] : 0.f;
+    float v = -twoQ * xr - sigma * xk;
+    if (jl) v -= rho * rq * wq - yq;
+    p = lane < 30 ? v : 0.f;
+  }
+  BwdPre cur = load_bwd(N - 1);
   for (int k = N - 1; k >= 0; --k) {
     const int b = (N - 1 - k) & 1;
     float* const Kc = b ? K1 : K0;
     float* const Hc = b ? H1 : H0;
     if (k >= 1)
-      pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k - 1) * BLK, b ? H0 : H1, ap.cH + (size_t)(k - 1) * BLK,
-                 lane);
-    const float* ce = ap.cE + k * 64;
-    set_stage_A(sm, ap.lin + L_STAGE + k * 64, lane);
-    for (int r = lane; r < NR; r += 32)
-      vR[r] = rho * ap.rcls[k * RS + r] * ap.w[k * RS + r] - ap.y[k * RS + r];
-    const float s = (lane < NC ? ce[lane] : 0.f) + p;
+      pipe_issue(pp, b ^ 1, b ? K0 : K1, CK + (size_t)(k - 1) * BLK, b ? H0 : H1, CH + (size_t)(k - 1) * BLK, lane);
+    const BwdPre q = cur;
+    if (k >= 1) cur = load_bwd(k - 1);
+    if (lane >= 12 && lane < NC) {
+      float* av = sm + S_AV + lane * 6;
+      av[0] = 1.f;
+      av[1] = q.a[0];
+      av[2] = q.a[1];
+      av[3] = q.a[2];
+    }
+    __syncwarp();
+    vR[lane] = rho * q.rc0 * q.w0 - q.y0;
+    if (r1) vR[lane + 32] = rho * q.rc1 * q.w1 - q.y1;
+    const float s = (lane < NC ? q.e : 0.f) + p;
     vS[lane] = s;
     __syncwarp();
     float h = 0.f;
     if (lane < 30) {
-      const float rlin = -twoR * ap.uref[k * VS + lane] - sigma * ap.u[k * VS + lane] - cuT(vR, lane, mu);
+      const float rlin = -twoR * q.ur - sigma * q.uk - cuT_t(vR);
       h = rlin + (lane < NC ? cc_tv(sm + S_BV, pat.br, vS, lane) : dt * s);
     }
     vH[lane] = h;
     float pn = 0.f;
-    if (k >= 1 && lane < 30) pn = qlin(k) + (lane < NC ? cc_tv(sm + S_AV, pat.ar, vS, lane) : s);
+    if (k >= 1 && lane < 30) pn = qlin(q) + (lane < NC ? cc_tv(sm + S_AV, pat.ar, vS, lane) : s);
     pipe_wait(pp, b);
     __syncwarp();
+    // d_k = -H_uu^-1 h and K_k^T h in one pass over the two blocks
+    const float2 hk = r24_mtv2(Hc, Kc, vH, lane);
     float d = 0.f;
-    if (lane < NC) d = -r24_mtv(Hc, vH, lane);
-    else if (arm) d = -ce[32 + lane] * h;
-    ap.dv[k * VS + lane] = d;
+    if (lane < NC) d = -hk.x;
+    else if (arm) d = -q.e2 * h;
+    DV[k * VS + lane] = d;
     if (k >= 1) {
-      if (lane < NC) pn += r24_mtv(Kc, vH, lane);
-      else if (arm) pn += ce[lane] * h;
+      if (lane < NC) pn += hk.y;
+      else if (arm) pn += q.e * h;
       p = pn;
     }
     __syncwarp();
   }
 
   // ---- forward rollout + per-stage relaxation / projection / dual update
-  float x = lane < 30 ? ap.x[lane] : 0.f;   // x_0 = x0
-  pipe_issue(pp, 0, K0, ap.cK, nullptr, nullptr, lane);
+  float x = lane < 30 ? X[lane] : 0.f;   // x_0 = x0
+  for (int k = 0; k < 3 && k < N; ++k) pipe_issue(pp, k, kslot(sm, k), CK + (size_t)k * BLK, nullptr, nullptr, lane);
+  FwdPre fc = load_fwd(0);
+  auto row_update = [&](int k, int r, float zt, float wo, float yo, float rc, float lo, float hi) {
+    const float wh = alpha * zt + (1.f - alpha) * wo;
+    const float rr = rho * rc;
+    float wn, yn;
+    if (rr > 0.f) {
+      wn = fminf(fmaxf(wh + yo / rr, lo), hi);
+      yn = yo + rr * (wh - wn);
+    } else {
+      wn = wh;
+      yn = 0.f;
+    }
+    Wr[k * RS + r] = wn;
+    Yr[k * RS + r] = yn;
+    if (store_dy) EL[k * 128 + r] = yn - yo;
+  };
   for (int k = 0; k < N; ++k) {
-    const int b = k & 1;
-    float* const Kc = b ? K1 : K0;
-    if (k + 1 < N) pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k + 1) * BLK, nullptr, nullptr, lane);
-    const float* ce = ap.cE + k * 64;
-    const float* dA = ap.lin + L_STAGE + k * 64;
+    const int b = k & 3;
+    float* const Kc = kslot(sm, b);
+    // stage k + 3 into the buffer stage k - 1 used (free since its last barrier)
+    if (k + 3 < N) pipe_issue(pp, (k + 3) & 3, kslot(sm, (k + 3) & 3), CK + (size_t)(k + 3) * BLK, nullptr, nullptr, lane);
+    const FwdPre q = fc;
+    if (k + 1 < N) fc = load_fwd(k + 1);
     vX[lane] = x;
-    const float dk = ap.dv[k * VS + lane];
-    const float dA0 = dA[lane], dA1 = dA[32 + lane];    // staged in smem with the stage's other loads
     pipe_wait(pp, b);
-    vA[lane] = dA0;
-    vA[32 + lane] = dA1;
+    vA[lane] = q.a0;
+    vA[32 + lane] = q.a1;
     __syncwarp();
     float u = 0.f;
-    if (lane < NC) u = r24_mv(Kc, vX, lane) + dk;
-    else if (arm) u = ce[lane] * x + dk;
+    if (lane < NC) u = r24_mv(Kc, vX, lane) + q.dk;
+    else if (arm) u = q.e * x + q.dk;
     vU[lane] = u;
     __syncwarp();
     float xn = 0.f;
-    if (lane < NC) xn = ak_mv(Ab, vA, vX, lane) + cm_mv(Bm, vU, lane) + vA[32 + lane];
+    if (lane < NC) xn = ak_mv(Ab, vA, vX, lane) + cm_mv_s(Bm, vU, lane) + vA[32 + lane];
     else if (arm) xn = x + dt * u;
     vXN[lane] = xn;
-    ap.xt[(k + 1) * VS + lane] = xn;
-    ap.ut[k * VS + lane] = u;
+    XT[(k + 1) * VS + lane] = xn;
+    UT[k * VS + lane] = u;
     __syncwarp();
-    for (int r = lane; r < NR; r += 32) {
-      const float zt = crow(vU, vXN, r, mu);
-      const float wo = ap.w[k * RS + r], yo = ap.y[k * RS + r];
-      const float wh = alpha * zt + (1.f - alpha) * wo;
-      const float rr = rho * ap.rcls[k * RS + r];
-      float wn, yn;
-      if (rr > 0.f) {
-        wn = fminf(fmaxf(wh + yo / rr, ap.rlo[k * RS + r]), ap.rhi[k * RS + r]);
-        yn = yo + rr * (wh - wn);
-      } else {
-        wn = wh;
-        yn = 0.f;
-      }
-      ap.w[k * RS + r] = wn;
-      ap.y[k * RS + r] = yn;
-      if (store_dy) ap.cEl[k * 128 + r] = yn - yo;
-    }
+    row_update(k, lane, crow_t(vU, 0), q.w0, q.y0, q.rc0, q.lo0, q.hi0);
+    if (r1) row_update(k, lane + 32, crow_t(vU, 1), q.w1, q.y1, q.rc1, q.lo1, q.hi1);
     if (lane < 30) {
-      ap.u[k * VS + lane] = alpha * u + (1.f - alpha) * ap.u[k * VS + lane];
-      ap.x[(k + 1) * VS + lane] = alpha * xn + (1.f - alpha) * ap.x[(k + 1) * VS + lane];
+      U[k * VS + lane] = alpha * u + (1.f - alpha) * q.uo;
+      X[(k + 1) * VS + lane] = alpha * xn + (1.f - alpha) * q.xo;
     }
     x = xn;
     __syncwarp();
@@ -1125,7 +1255,7 @@ __device__ StageIn polish_stage_in(const AgentPtrs& ap, float* sm, float* cvec, 
       in.rt_diag = gv[j] * Dj * gv[j] + (1.f - gv[j]);
       in.rh = gv[j] * vD2[j];
     }
-    cvec[j] = c_k + cm_mv(sm + S_B, tv, lane);   // c_hat
+    cvec[j] = c_k + cm_mv_s(sm + S_B, tv, lane);   // c_hat
   } else if (lane < 30) {
     const float alive = el.g;
     in.rt_diag = alive * Dj + (1.f - alive);
@@ -1149,14 +1279,15 @@ __device__ __noinline__ void polish_rollout(const AgentPtrs& ap, float* sm, int 
   float* vX = vec + V_X * 64; float* vV = vec + V_U * 64; float* vU = vec + V_XN * 64;
   float* vA = vec + V_D * 64;   // the stage's dA_k block and c_k, staged with the stage's other loads
   const bool arm = lane >= NC && lane < 30;
-  float* const K0 = sm + S_P; float* const K1 = sm + S_X;
     float x = lane < 30 ? ap.x[lane] : 0.f;
     float xo = x;                                  // previous pass's x_k (x_0 is fixed)
-    pipe_issue(pp, 0, K0, ap.cK, nullptr, nullptr, lane);
+    for (int k = 0; k < 3 && k < N; ++k)
+      pipe_issue(pp, k, kslot(sm, k), ap.cK + (size_t)k * BLK, nullptr, nullptr, lane);
     for (int k = 0; k < N; ++k) {
-      const int b = k & 1;
-      float* const Kc = b ? K1 : K0;
-      if (k + 1 < N) pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k + 1) * BLK, nullptr, nullptr, lane);
+      const int b = k & 3;
+      float* const Kc = kslot(sm, b);
+      if (k + 3 < N)
+        pipe_issue(pp, (k + 3) & 3, kslot(sm, (k + 3) & 3), ap.cK + (size_t)(k + 3) * BLK, nullptr, nullptr, lane);
       const float* ce = ap.cE + k * 64;
       const float* dA = ap.lin + L_STAGE + k * 64;
       const float4 el = reinterpret_cast<const float4*>(ap.cEl + k * 128)[lane];
@@ -1185,7 +1316,7 @@ __device__ __noinline__ void polish_rollout(const AgentPtrs& ap, float* sm, int 
       vX[lane] = x;
       __syncwarp();
       float xn = 0.f;
-      if (lane < NC) xn = ak_mv(sm + S_AB, vA, vX, lane) + cm_mv(sm + S_B, vU, lane) + vA[32 + lane];
+      if (lane < NC) xn = ak_mv(sm + S_AB, vA, vX, lane) + cm_mv_s(sm + S_B, vU, lane) + vA[32 + lane];
       else if (arm) xn = x + dt * u;
       ap.xt[(k + 1) * VS + lane] = xn;
       ap.ut[k * VS + lane] = u;
