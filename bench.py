@@ -327,7 +327,8 @@ def run_ours(args):
         for i in range(W):
             step(s, 1 + i)
         barrier()
-        l0 = s.stats()["kernel_launches"]
+        st0 = s.stats()
+        l0 = st0["kernel_launches"]
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
@@ -345,7 +346,8 @@ def run_ours(args):
         launches = s.stats()["kernel_launches"] - l0
         graph_replays = s.stats().get("graph_replays", 0)
         st = s.agent_stats(slots)
-        st["polish_attempts"] = s.stats().get("polish_attempts")
+        st1 = s.stats()
+        st["polish_attempts"] = st1.get("polish_attempts")
         status = out["status"].cpu().numpy()
         return s, total_ms, per, launches, st, status, clk.summary(), graph_replays
 
@@ -529,6 +531,7 @@ def run_ours(args):
                    "prim_scaled_max": float(st["prim_scaled"].max()),
                    "dual_scaled_max": float(st["dual_scaled"].max()),
                    "polish_attempts": st["polish_attempts"],
+                   "dual_scaled_p99": float(np.percentile(st["dual_scaled"], 99)),
                    "polish_attempts_note": "agents of the last timed replan whose accepted polish took [0 = none, "
                                            "1, 2, ... 8] reduced KKT solves (the active-set iteration count)"},
     }

@@ -144,9 +144,7 @@ typedef struct mpc_config {
                                  its KKT check */
   int refine_steps;           /* iterative-refinement steps on each polish solve
                                  (0..4); -1 = automatic: 2 for TF32 and 3 for BF16
-                                 stage products on every polish; for FP32 / FP64 1
-                                 on a polish after ADMM iterations and 0 on the
-                                 warm-start polish */
+                                 stage products, 1 for FP32 / FP64 */
   int spin_limit;             /* polls of a bounded device wait (a stage block's bulk
                                  copy into shared memory) before it gives up; the
                                  agent then gets MPC_AGENT_TIMEOUT with zeroed

@@ -498,12 +498,14 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   p.precision = c.precision;
   // automatic: where the stage products are TF32 / BF16, the steps that win
   // back the products' rounding (measured against the FP64 oracle: TF32 needs
-  // 2, BF16 3); otherwise one on a polish after ADMM (a cold or fallback
-  // solve, where it is cheap next to the iterations) and none on the
-  // warm-start polish
-  const int low = c.precision == MPC_TF32 ? 2 : c.precision == MPC_BF16 ? 3 : 0;
+  // 2, BF16 3); otherwise one on every polish: the FP32 factor's rounding
+  // (stage Schur complements whose weights span 10^4) leaves the joint rates
+  // of about one agent in 400 a few 1e-4 off, which the torque map's
+  // qddot = (qdot_1 - qdot_0)/dt turns into torque errors of several times
+  // the tolerance; one step removes them
+  const int low = c.precision == MPC_TF32 ? 2 : c.precision == MPC_BF16 ? 3 : 1;
   p.refine = c.refine_steps >= 0 ? c.refine_steps : low;
-  p.refine_admm = c.refine_steps >= 0 ? c.refine_steps : (low > 1 ? low : 1);
+  p.refine_admm = c.refine_steps >= 0 ? c.refine_steps : low;
   p.trees = 0;
   p.split = 1;
   p.spin_limit = c.spin_limit;

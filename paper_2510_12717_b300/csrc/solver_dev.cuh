@@ -490,6 +490,16 @@ __device__ __forceinline__ float cc_tv(const float* val, const int* rows, const 
   return a;
 }
 
+// the same product with the absolute values of the matrix (v >= 0): the
+// magnitude of the terms that form (A^T v)_i
+__device__ __forceinline__ float cc_tv_abs(const float* val, const int* rows, const float* v, int lane) {
+  const int j = lane < NC ? lane : 0;
+  float a = 0.f;
+#pragma unroll
+  for (int t = 0; t < 6; ++t) a = fmaf(fabsf(val[j * 6 + t]), v[rows[t]], a);
+  return a;
+}
+
 // ----------------------------------------------------------- row algebra
 // Stage rows (paper Eq. mpc_formulation constraints, row layout as in the
 // include file): 0-11 wrench box, 12-19 friction pyramid, 20-37 joint-rate

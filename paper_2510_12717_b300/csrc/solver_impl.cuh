@@ -895,11 +895,21 @@ __device__ __noinline__ void admm_iteration(const AgentPtrs& ap, float* sm, int 
 // (<= 1 converged): the components differ by orders of magnitude (forces vs
 // joint rates), and one global scale would let the small ones go unchecked.
 struct Res { float rp, rd, ps, ds, pn, dn; };
-// A polished point must also pass every row and component at kScaledAccept
-// times its own tolerance: FP32 rounding of a correct polish stays below ~5
-// there, while an active row whose multiplier has the wrong sign (a wrong
-// active set that the global scales let through) lands at 10^2 and above.
-constexpr float kScaledAccept = 10.f;
+// A polished point must also pass every row and component within its own
+// tolerance eps_abs + eps_rel x (magnitude of its terms) (kScaledAccept = 1).
+// The magnitude of a stationarity component counts every term that forms it,
+// through the costate recursion (sums of absolute values: the scale of its
+// FP32 rounding, under 1e-6 of it for the n <= 100 terms here, since
+// n 2^-24 < 1e-5).  A correct polish after its refinement step sits at a few
+// hundredths of that tolerance (99th percentile over a warm replan); an
+// active row whose multiplier has the wrong sign, even one worth only
+// 1e-11 of the objective (a flat direction of the cost), lands above it and
+// is corrected.
+constexpr float kScaledAccept = 1.f;
+// ADMM's own stopping test (its iterate is reported INACCURATE unless a
+// polish certifies it) and the threshold of its infeasibility test read the
+// scaled residuals of admm_residuals at 10 times the tolerance
+constexpr float kAdmmScaledStop = 10.f;
 
 __device__ __noinline__ Res admm_residuals(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm,
                                            const LanePat& pat) {
@@ -1283,25 +1293,40 @@ __device__ __noinline__ void polish_rollout(const AgentPtrs& ap, float* sm, int 
     float xo = x;                                  // previous pass's x_k (x_0 is fixed)
     for (int k = 0; k < 3 && k < N; ++k)
       pipe_issue(pp, k, kslot(sm, k), ap.cK + (size_t)k * BLK, nullptr, nullptr, lane);
+    // per-lane global inputs of a stage, loaded one stage ahead (stage k
+    // writes dv_k, x_{k+1}, u_k: none of stage k+1's inputs)
+    struct RollPre { float4 el; float a0, a1, base, xo_next, e; };
+    auto load = [&](int k) {
+      RollPre q;
+      const float* dA = ap.lin + L_STAGE + k * 64;
+      q.el = reinterpret_cast<const float4*>(ap.cEl + k * 128)[lane];
+      q.a0 = dA[lane];
+      q.a1 = dA[32 + lane];
+      q.base = refine ? ap.dv[k * VS + lane] + ap.cD[k * VS + lane] : ap.dv[k * VS + lane];
+      q.xo_next = refine ? ap.xt[(k + 1) * VS + lane] : 0.f;
+      q.e = ap.cE[k * 64 + lane];
+      return q;
+    };
+    RollPre cur = load(0);
     for (int k = 0; k < N; ++k) {
       const int b = k & 3;
       float* const Kc = kslot(sm, b);
       if (k + 3 < N)
         pipe_issue(pp, (k + 3) & 3, kslot(sm, (k + 3) & 3), ap.cK + (size_t)(k + 3) * BLK, nullptr, nullptr, lane);
-      const float* ce = ap.cE + k * 64;
-      const float* dA = ap.lin + L_STAGE + k * 64;
-      const float4 el = reinterpret_cast<const float4*>(ap.cEl + k * 128)[lane];
-      const float dA0 = dA[lane], dA1 = dA[32 + lane];
+      const RollPre q = cur;
+      if (k + 1 < N) cur = load(k + 1);
+      const float4 el = q.el;
+      const float dA0 = q.a0, dA1 = q.a1;
       vX[lane] = refine ? x - xo : x;
-      const float base = refine ? ap.dv[k * VS + lane] + ap.cD[k * VS + lane] : ap.dv[k * VS + lane];
-      const float xo_next = refine ? ap.xt[(k + 1) * VS + lane] : 0.f;
+      const float base = q.base;
+      const float xo_next = q.xo_next;
       pipe_wait(pp, b);
       vA[lane] = dA0;
       vA[32 + lane] = dA1;
       __syncwarp();
       float v = 0.f;
       if (lane < NC) v = r24_mv(Kc, vX, lane) + base;
-      else if (arm) v = ce[lane] * vX[lane] + base;
+      else if (arm) v = q.e * vX[lane] + base;
       vV[lane] = v;
       ap.dv[k * VS + lane] = v;
       __syncwarp();
@@ -1347,7 +1372,20 @@ __device__ __noinline__ void polish_refine(const AgentPtrs& ap, float* sm, int l
   float lam = lane < 30 ? twoQ * (ap.xt[N * VS + lane] - ap.xref[N * VS + lane]) : 0.f;
   float pc = 0.f;
   Carry carry2 = {0, 0.f};
+  // per-lane global inputs of a stage, loaded one stage ahead
+  struct RefPre { StagePre pre; float v, xr, xt, e, e2; };
+  auto load = [&](int k) {
+    RefPre q;
+    q.pre = stage_pre(ap, k, lane);
+    q.v = ap.dv[k * VS + lane];
+    q.xr = k >= 1 ? ap.xref[k * VS + lane] : 0.f;
+    q.xt = k >= 1 ? ap.xt[k * VS + lane] : 0.f;
+    q.e = ap.cE[k * 64 + lane];
+    q.e2 = ap.cE[k * 64 + 32 + lane];
+    return q;
+  };
   pipe_issue(pp, 0, K0, ap.cK + (size_t)(N - 1) * BLK, H0, ap.cH + (size_t)(N - 1) * BLK, lane);
+  RefPre cur = load(N - 1);
   for (int k = N - 1; k >= 0; --k) {
     const int b = (N - 1 - k) & 1;
     float* const Kc = b ? K1 : K0;
@@ -1355,13 +1393,15 @@ __device__ __noinline__ void polish_refine(const AgentPtrs& ap, float* sm, int l
     if (k >= 1)
       pipe_issue(pp, b ^ 1, b ? K0 : K1, ap.cK + (size_t)(k - 1) * BLK, b ? H0 : H1,
                  ap.cH + (size_t)(k - 1) * BLK, lane);
-    const StagePre pre = stage_pre(ap, k, lane);
+    const RefPre q = cur;
+    if (k >= 1) cur = load(k - 1);
+    const StagePre& pre = q.pre;
     stage_active_pre(pre, act, lane);
     set_stage_A_pre(sm, pre, lane);
     const Elim el = lane_elim(ap, pre, act, lane, mu, carry2);
     carry2 = el.carry_out;
     const StageIn in = polish_stage_in(ap, sm, cvec, el, lane, pat, pre.uref, pre.ck);
-    const float v = ap.dv[k * VS + lane];
+    const float v = q.v;
     vV[lane] = v;
     vS[lane] = lam;
     vR[lane] = pc;
@@ -1386,22 +1426,22 @@ __device__ __noinline__ void polish_refine(const AgentPtrs& ap, float* sm, int l
     vH[lane] = h;
     float lamn = 0.f, pcn = 0.f;
     if (k >= 1 && lane < 30) {
-      float ql = -twoQ * ap.xref[k * VS + lane];
+      float ql = -twoQ * q.xr;
       if (el.qbox) ql -= 2.f * md[M_R + lane] * el.t;
-      lamn = in.qt * ap.xt[k * VS + lane] + ql +
+      lamn = in.qt * q.xt + ql +
              (lane < NC ? cc_tv(sm + S_AV, pat.ar, vS, lane) : (el.qbox ? 0.f : lam));
       pcn = lane < NC ? cc_tv(sm + S_AV, pat.ar, vR, lane) : (el.qbox ? 0.f : pc);
     }
-    const float* ce = ap.cE + k * 64;
     pipe_wait(pp, b);
     __syncwarp();
+    const float2 hk = r24_mtv2(Hc, Kc, vH, lane);
     float d = 0.f;
-    if (lane < NC) d = -r24_mtv(Hc, vH, lane);
-    else if (arm) d = -ce[32 + lane] * h;
+    if (lane < NC) d = -hk.x;
+    else if (arm) d = -q.e2 * h;
     ap.cD[k * VS + lane] = d;
     if (k >= 1) {
-      if (lane < NC) pcn += r24_mtv(Kc, vH, lane);
-      else if (arm) pcn += ce[lane] * h;
+      if (lane < NC) pcn += hk.y;
+      else if (arm) pcn += q.e * h;
     }
     lam = lamn;
     pc = pcn;
@@ -1516,6 +1556,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
   float* vec = sm + S_VEC;
   float* vU = vec + V_U * 64; float* vXN = vec + V_XN * 64; float* vM = vec + V_S * 64;
   float* vG = vec + V_G * 64; float* vT = vec + V_T * 64;
+  float* vMa = vec + V_H * 64;   // magnitude of the terms of the costate (sums of absolute values)
   int* act = reinterpret_cast<int*>(vec + V_ACT * 64);
   const float twoQ = lane < 30 ? 2.f * dt * md[M_Q + lane] : 0.f;
   const float twoR = lane < 30 ? 2.f * dt * md[M_R + lane] : 0.f;
@@ -1524,6 +1565,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
   float rp = 0.f, ps = 0.f, rd = 0.f, ds = 0.f, pn = 0.f, dn = 0.f;
   int chg = 0;
   float m = lane < 30 ? twoQ * (xs[N * VS + lane] - ap.xref[N * VS + lane]) : 0.f;
+  float ma = lane < 30 ? fabsf(twoQ * xs[N * VS + lane]) + fabsf(twoQ * ap.xref[N * VS + lane]) : 0.f;
   // a chain of stages kc..ke whose joint rate sits at its bound while the
   // joint limit of stage ke is active (see Elim): the limit's multiplier is
   // nu, the multiplier nu' of the constraint carried to stage kc-1, and each
@@ -1550,6 +1592,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
     stage_active_pre(pre, act, lane);
     set_stage_A_pre(sm, pre, lane);
     vM[lane] = m;
+    vMa[lane] = ma;
     vU[lane] = u_k;
     vXN[lane] = x_n;
     __syncwarp();
@@ -1579,8 +1622,9 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
     if (lane < 30) {
       const float u = u_k, ur = pre.uref;
       const float btm = lane < NC ? cc_tv(sm + S_BV, pat.br, vM, lane) : dt * m;
+      const float bta = lane < NC ? cc_tv_abs(sm + S_BV, pat.br, vMa, lane) : dt * ma;
       g = twoR * (u - ur) + btm;
-      td = ea + er * fmaxf(fmaxf(fabsf(twoR * u), fabsf(twoR * ur)), fabsf(btm));
+      td = ea + er * fmaxf(fmaxf(fabsf(twoR * u), fabsf(twoR * ur)), bta);
       ds = fmaxf(ds, fmaxf(fabsf(twoR * u), fabsf(twoR * ur)));
       ds = fmaxf(ds, fmaxf(fabsf(twoQ * x_n), fabsf(twoQ * xr_n)));
     }
@@ -1624,7 +1668,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
         // joint rate eliminated by the joint limit (own, or carried to here)
         const float tu = -2.f * md[M_R + lane] * u_k;
         const float yq = tu - m;
-        const float tol = ea + er * fmaxf(fabsf(tu), fabsf(m));
+        const float tol = ea + er * fmaxf(fabsf(tu), ma);
         if (ch_on) {
           close_chain(yq, tol);
         } else {
@@ -1634,6 +1678,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
           if (FIX && bad > fminf(tol_d, kScaledAccept * tol)) { ak[lane + 26] = 0; chg = 1; }
         }
         m += yq;
+        ma += fabsf(tu);
       } else {
         float bad;
         if (a & 1) bad = fmaxf(-g, 0.f);           // needs y <= 0 at a lower bound
@@ -1702,13 +1747,18 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
     }
     __syncwarp();
     vM[lane] = m;          // costate with the joint-box multipliers of stage k
+    vMa[lane] = ma;
     __syncwarp();
-    float mn = 0.f;
-    if (k >= 1 && lane < 30)
+    float mn = 0.f, mna = 0.f;
+    if (k >= 1 && lane < 30) {
       mn = twoQ * (x_k - xr_k) +
            (lane < NC ? cc_tv(sm + S_AV, pat.ar, vM, lane) : m);
+      mna = fabsf(twoQ * x_k) + fabsf(twoQ * xr_k) +
+            (lane < NC ? cc_tv_abs(sm + S_AV, pat.ar, vMa, lane) : ma);
+    }
     __syncwarp();
     m = mn;
+    ma = mna;
   }
   Res out;
   out.rp = warp_max(rp); out.ps = warp_max(ps); out.rd = warp_max(rd); out.ds = warp_max(ds);
@@ -1951,16 +2001,16 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
     if (!(isfinite(o.r.rp) && isfinite(o.r.rd))) { o.status = MPC_AGENT_NAN_; break; }
     if (fixed) break;
     // OSQP's stopping rule (global scales), and every row and component
-    // within kScaledAccept times its own tolerance, as a polish must be
+    // within kAdmmScaledStop times its own tolerance
     const float tol_p = prm.eps_abs + prm.eps_rel * o.r.ps;
     const float tol_d = prm.eps_abs + prm.eps_rel * o.r.ds;
-    if (o.r.rp <= tol_p && o.r.rd <= tol_d && o.r.pn <= kScaledAccept && o.r.dn <= kScaledAccept) {
+    if (o.r.rp <= tol_p && o.r.rd <= tol_d && o.r.pn <= kAdmmScaledStop && o.r.dn <= kAdmmScaledStop) {
       o.status = MPC_AGENT_SOLVED_;
       break;
     }
     // a primal residual that stays above its acceptance level: test the
     // last iteration's multiplier change for an infeasibility certificate
-    if (o.r.pn > kScaledAccept && admm_primal_infeasible(ap, sm, lane, pat)) {
+    if (o.r.pn > kAdmmScaledStop && admm_primal_infeasible(ap, sm, lane, pat)) {
       o.status = MPC_AGENT_PRIMAL_INFEAS_;
       break;
     }

@@ -344,7 +344,7 @@ def test_full_size_warm_replans_in_bench_configuration(mpcgpu):
     assert (got["status"] == 0).all()
     assert np.isfinite(got["tau"]).all()
     assert (st["polished"] == 2).mean() >= 0.99          # polish first carried the warm replan
-    assert (st["prim_scaled"] <= 10).all() and (st["dual_scaled"] <= 10).all()
+    assert (st["prim_scaled"] <= 1).all() and (st["dual_scaled"] <= 1).all()   # each row and component within its own tolerance
     assert stats["graph_replays"] >= 1
     rng = np.random.default_rng(11)
     sample = np.sort(rng.choice(n, 32, replace=False))
@@ -355,6 +355,43 @@ def test_full_size_warm_replans_in_bench_configuration(mpcgpu):
     ok = torque_close(got["tau"][sample], ref["tau"])
     _report("16k-warm-sample", got["tau"][sample], ref["tau"], {k: v[sample] for k, v in st.items()})
     assert ok.all(), np.argwhere(~ok)
+
+
+def test_hard_agents_of_the_benchmark_walk_match_oracle(mpcgpu):
+    # agents of the 16384-agent benchmark workload, walked through replans
+    # 0-2 as the benchmark does, among them three that exposed FP32 failure
+    # modes of the warm-start polish on replan 1: agent 68 (the FP32 factor's
+    # rounding leaves a joint rate 1.5e-4 off, which qddot = (qdot_1 -
+    # qdot_0)/dt turns into 9x the torque tolerance: the refinement step
+    # removes it), agent 248 (an active rate row whose multiplier has the
+    # wrong sign but is worth only 1e-11 of the objective: the check at each
+    # component's own tolerance rejects it), agent 998; plus a seeded sample
+    from workload import make_agents, perturb_inputs
+    rng = np.random.default_rng(2510)
+    hard = [68, 248, 998]
+    rest = rng.choice(np.setdiff1d(np.arange(16384), hard), 61, replace=False)
+    agent_ids = np.sort(np.concatenate([hard, rest]))
+    n = len(agent_ids)
+    model, inp = make_agents("mixed16k", agent_ids)
+    seq = [inp]
+    for r in (1, 2):
+        seq.append(perturb_inputs("mixed16k", seq[-1], agent_ids, r))
+    slots = np.arange(n)
+    s = mpcgpu.Solver(max_agents=n, max_horizon=20, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_models(model, slots)
+    for r, x in enumerate(seq):
+        inp32 = device_inputs(x)
+        got = s.solve_host(slots, inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+        st = s.agent_stats(slots)
+        ref = _oracle(model, inp32)
+        ok = torque_close(got["tau"], ref["tau"])
+        ratio = np.abs(got["tau"] - ref["tau"]) / (1e-4 + 1e-3 * np.abs(ref["tau"]))
+        print(f"\n[benchmark walk, replan {r}] worst |dtau| / tolerance {ratio.max():.3f}, "
+              f"dual scaled max {st['dual_scaled'].max():.3f}")
+        assert (got["status"] == 0).all(), got["status"]
+        assert ok.all(), agent_ids[np.nonzero(~ok.all(axis=1))[0]]
+        assert (st["prim_scaled"] <= 1).all() and (st["dual_scaled"] <= 1).all()
+    s.close()
 
 
 @pytest.mark.parametrize("form", [1, 0], ids=["fused", "plain"])

@@ -84,18 +84,70 @@ def test_tensor_core_products_track_fp32(mpcgpu):
         assert np.median(rel) < tol, (precision, np.median(rel))
 
 
-def test_ill_conditioned_accuracy_reported(mpcgpu):
-    # Q, R spread over [1e-4, 1e4]: FP32 loses digits in the factor; one
-    # refinement step keeps most agents within the torque tolerance; the
-    # TF32 / BF16 factors are reported only
+def _gpu_points(mpcgpu, model, inps, precision, refine):
+    """Solve the replans in sequence and export every agent's final primal
+    (x, u) as well as its status and torques."""
+    n = len(model["mass"])
+    ids = np.arange(n, dtype=np.int32)
+    s = mpcgpu.Solver(max_agents=n, max_horizon=int(model["N"].max()),
+                      stream=torch.cuda.current_stream().cuda_stream, precision=precision, refine_steps=refine)
+    s.set_models(model, np.arange(n))
+    out = []
+    for inp32 in inps:
+        r = s.solve_host(ids, inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+        pts = [s.export_state(int(a), int(model["N"][a])) for a in range(n)]
+        out.append((r, pts))
+    s.close()
+    return out
+
+
+def test_ill_conditioned_solutions_are_optimal_to_fp32_resolution(mpcgpu):
+    # Q, R spread over [1e-4, 1e4].  Along a joint whose rate and position
+    # both weigh ~1e-4 the cost is flat (curvature 2 dt 1e-4 = 8e-6, below the
+    # FP32 rounding of the larger cost terms), so points that an FP32 solver
+    # cannot tell apart (objectives equal to a few 1e-8 of the sum of their
+    # terms, both feasible) can differ by rad/s in that joint's rate and by
+    # tenths of a N m in a torque.  What FP32 can meet, and is held here for
+    # every SOLVED agent: the oracle's optimal objective within 1e-6 of the
+    # magnitude of its terms (16 FP32 units in the last place), rows within
+    # 1e-4 of their bounds, the dynamics within 1e-5.  The torque error
+    # against the FP64 optimum is reported; an agent that is not SOLVED
+    # carries a status that says so.
+    from oracle import qp as qpmod
+    from oracle.solve import agent_params
     model, inps, refs = _case("mixed16k_ill", 32)
-    for precision, refine, need in ((0, 1, 0.8), (3, 1, 0.8), (1, -1, None), (2, -1, None)):
-        for replan, ((r, st), ref) in enumerate(zip(_solve(mpcgpu, model, inps, precision, refine), refs)):
-            fin = np.isfinite(r["tau"]).all(axis=1)
-            ok = torque_close(r["tau"], ref["tau"]).all(axis=1) & fin
-            print(f"\n[ill-conditioned precision {precision} refine {refine} replan {replan}] "
-                  f"within tolerance {ok.mean():.3f}, solved {(r['status'] == 0).mean():.3f}, "
-                  f"polished {(st['polished'] > 0).mean():.3f}")
-            if need is not None:
-                assert fin.all()
-                assert ok.mean() >= need
+    n = len(model["mass"])
+    for precision, refine in ((0, 1), (3, 1)):
+        for replan, ((r, pts), ref) in enumerate(zip(_gpu_points(mpcgpu, model, inps, precision, refine), refs)):
+            m64, i64 = oracle_view(model, inps[replan])
+            within = torque_close(r["tau"], ref["tau"]).all(axis=1)
+            solved = r["status"] == 0
+            gaps = []
+            for a in np.nonzero(solved)[0]:
+                qp, _ = qpmod.agent_qp(agent_params(m64, a), i64["x0"][a], i64["cmd"][a], float(i64["phase"][a]))
+                N = qp.N
+                x = pts[a]["x"].astype(np.float64)
+                u = pts[a]["u"].astype(np.float64)
+                z = np.concatenate([np.concatenate([u[k], x[k + 1]]) for k in range(N)])
+                f_gpu = qp.objective(z)
+                f_opt = ref["V"][a]
+                scale = (0.5 * np.abs(z) @ np.abs(qp.P) @ np.abs(z) + np.abs(qp.q) @ np.abs(z) + abs(qp.const))
+                gaps.append(abs(f_gpu - f_opt) / scale)
+                Cz = qp.C @ z
+                lo_v = np.where(np.isfinite(qp.lo), qp.lo - Cz, 0.0)
+                hi_v = np.where(np.isfinite(qp.hi), Cz - qp.hi, 0.0)
+                bnd = np.where(np.isfinite(qp.lo), np.abs(qp.lo), 0.0) + np.where(np.isfinite(qp.hi), np.abs(qp.hi), 0.0)
+                viol = np.maximum(np.maximum(lo_v, hi_v), 0.0) / (1.0 + bnd)
+                assert viol.max() <= 1e-4, (precision, replan, a, viol.max())
+                assert np.abs(qp.E @ z - qp.e).max() <= 1e-5, (precision, replan, a)
+            gaps = np.asarray(gaps)
+            print(f"\n[ill-conditioned precision {precision} replan {replan}] solved {solved.mean():.3f}, "
+                  f"torques within tolerance {within.mean():.3f} (of solved {within[solved].mean():.3f}), "
+                  f"objective gap max {gaps.max():.1e} of its terms, status {np.bincount(r['status'], minlength=7).tolist()}")
+            assert np.isfinite(r["tau"]).all()
+            assert gaps.max() <= 1e-6, (precision, replan, gaps.max())
+            # the ADMM fallback (no equilibration) reaches its iteration cap on a
+            # few of the flattest agents; they are reported, not passed off
+            assert solved.mean() >= 0.9, solved.mean()
+            # every agent that is not SOLVED says why (iteration cap or no KKT-checked point)
+            assert set(np.unique(r["status"][~solved]).tolist()) <= {mpcgpu.AGENT_MAX_ITER, mpcgpu.AGENT_INACCURATE}
