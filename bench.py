@@ -539,7 +539,7 @@ def run_ours(args):
 
 
 # ------------------------------------------------------------------ precision
-PREC_NAMES = {0: "FP32", 1: "TF32", 2: "BF16", 3: "FP64-Schur"}
+PREC_NAMES = {0: "FP32", 1: "TF32", 2: "BF16", 3: "FP64-Schur", 4: "TF32x3"}
 
 
 def precision_report(args, timed, cfg, n, world, mpcgpu):
@@ -574,7 +574,7 @@ def precision_report(args, timed, cfg, n, world, mpcgpu):
         inps = [{k: np.ascontiguousarray(v, np.float32) for k, v in x.items()} for x in inps]
         samples[wl] = (model, inps, [r["tau"] for r, _ in sample_solve(model, inps, 0, 2)])
     out = {}
-    for prec in (0, 1, 2, 3):
+    for prec in (0, 4, 1, 2, 3):
         s, tp, perp, _, _, _, _, _ = timed(mpcgpu.FORM_FUSED, K, args.warmup, tune=False, variant=cfg["variant"],
                                        check_every=cfg["check_every"], early_polish=cfg["early_polish"],
                                        precision=prec, refine_steps=-1)
@@ -600,9 +600,10 @@ def precision_report(args, timed, cfg, n, world, mpcgpu):
                             "median_rel_dev": float(np.median(rel)), "max_rel_dev": float(np.max(rel))})
             entry["samples"][wl] = acc
         out[PREC_NAMES[prec]] = entry
-    out["note"] = ("factor precision; refinement automatic (1 step on a polish after ADMM, and on the warm-start "
-                   "polish for TF32/BF16); deviations against FP32 with 2 refinement steps, torque tolerance "
-                   "1e-4 N m + 1e-3 |tau|; oracle comparison in tests/test_gpu_precision.py")
+    out["note"] = ("factor precision (TF32x3 = split TF32 on the tensor cores, three mma per tile); refinement "
+                   "automatic (1 step per polish; 2 for TF32, 3 for BF16); deviations against FP32 with 2 "
+                   "refinement steps, torque tolerance 1e-4 N m + 1e-3 |tau|; oracle comparison in "
+                   "tests/test_gpu_precision.py")
     return out
 
 

@@ -77,7 +77,12 @@ typedef enum {
                                   optimum; the warm start is kept */
 } mpc_agent_status;
 
-typedef enum { MPC_FP32 = 0, MPC_TF32 = 1, MPC_BF16 = 2, MPC_FP64 = 3 } mpc_precision;
+/* Precision of the Riccati factor's two dense 22 x 22 stage products per
+ * stage (K = -H_uu^-1 H_ux and H_ux^T K) and of its Schur inverse: FP32 on the
+ * CUDA cores; TF32 / BF16 on the tensor cores (mma.sync, FP32 accumulation);
+ * FP64 Schur inverse; TF32X3 = error-compensated split TF32 on the tensor
+ * cores (three mma per tile, FP32-level accuracy; Ootomo and Yokota 2022). */
+typedef enum { MPC_FP32 = 0, MPC_TF32 = 1, MPC_BF16 = 2, MPC_FP64 = 3, MPC_TF32X3 = 4 } mpc_precision;
 
 typedef enum { MPC_FORM_PLAIN = 0, MPC_FORM_FUSED = 1 } mpc_form;
 
@@ -111,7 +116,9 @@ typedef struct mpc_config {
                                  FP32; TF32 / BF16 = the two dense stage-block
                                  products (K = -H_uu^-1 H_ux and H_ux^T K) on the
                                  tensor cores (mma.sync), FP32 accumulation; FP64 =
-                                 the stage Schur complement H_uu inverted in FP64.
+                                 the stage Schur complement H_uu inverted in FP64;
+                                 TF32X3 = the two products in split TF32 on the
+                                 tensor cores (FP32-level accuracy).
                                  With polish first on (polish, warm_polish,
                                  fixed_iters 0), a TF32 / BF16 agent whose polish
                                  first fails falls back to FP32 factors for its

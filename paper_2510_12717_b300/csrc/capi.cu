@@ -171,7 +171,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   if (!cfg) return MPC_ERR_INVALID;
   if (cfg->max_agents <= 0 || cfg->max_horizon < 2 || cfg->max_horizon > MPC_MAX_HORIZON)
     return MPC_ERR_INVALID;
-  if (cfg->precision < MPC_FP32 || cfg->precision > MPC_FP64) return MPC_ERR_INVALID;
+  if (cfg->precision < MPC_FP32 || cfg->precision > MPC_TF32X3) return MPC_ERR_INVALID;
   if (cfg->refine_steps < -1 || cfg->refine_steps > 4) return MPC_ERR_INVALID;
   if (cfg->spin_limit <= 0 || cfg->wait_test_agent < -1 || cfg->wait_test_agent >= cfg->max_agents)
     return MPC_ERR_INVALID;
@@ -498,7 +498,7 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   p.precision = c.precision;
   // automatic: where the stage products are TF32 / BF16, the steps that win
   // back the products' rounding (measured against the FP64 oracle: TF32 needs
-  // 2, BF16 3); otherwise one on every polish: the FP32 factor's rounding
+  // 2, BF16 3); otherwise (FP32, split TF32, FP64) one on every polish: the FP32 factor's rounding
   // (stage Schur complements whose weights span 10^4) leaves the joint rates
   // of about one agent in 400 a few 1e-4 off, which the torque map's
   // qddot = (qdot_1 - qdot_0)/dt turns into torque errors of several times

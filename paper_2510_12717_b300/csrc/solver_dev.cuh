@@ -331,7 +331,11 @@ static __device__ __noinline__ void r24_inv_f64(float* H, double* sc, int lane) 
 // (BF16, k16).  Padding reads as zero; the padding columns of C are written
 // as zero.  Fragment layouts (PTX ISA, mma.m16n8k8 .tf32 / m16n8k16 .bf16):
 // g = lane / 4, t = lane % 4;  C: (g, 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1).
-enum : int { PREC_FP32 = 0, PREC_TF32 = 1, PREC_BF16 = 2, PREC_FP64 = 3 };
+// PREC_TF32X3: error-compensated split TF32 (Ootomo and Yokota, 2022): each
+// operand x = hi + lo with hi = tf32(x) and lo = tf32(x - hi), and
+// A B = A_hi B_hi + A_hi B_lo + A_lo B_hi (the A_lo B_lo term, 2^-22 of the
+// product, is dropped): three mma per tile, FP32-level accuracy.
+enum : int { PREC_FP32 = 0, PREC_TF32 = 1, PREC_BF16 = 2, PREC_FP64 = 3, PREC_TF32X3 = 4 };
 // kernel specialisation: PREC_FP32 compiles the FP32 factor only; PREC_ANY
 // reads the precision at run time
 constexpr int PREC_ANY = -1;
@@ -340,6 +344,11 @@ __device__ __forceinline__ uint32_t to_tf32(float x) {
   uint32_t r;
   asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
   return r;
+}
+// the split of TF32X3: hi = tf32(x), lo = tf32(x - hi)
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
 }
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   uint32_t r;
@@ -362,7 +371,47 @@ __device__ __noinline__ void r24_gemm_tn_mma(float* C, const float* A, const flo
     for (int ni = 0; ni < 3; ++ni)
 #pragma unroll
       for (int c = 0; c < 4; ++c) acc[mi][ni][c] = 0.f;
-  if (P == PREC_TF32) {
+  if (P == PREC_TF32X3) {
+#pragma unroll
+    for (int k0 = 0; k0 < 24; k0 += 8) {
+      uint32_t ah[2][4], al[2][4], bh[3][2], bl[3][2];
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi) {
+        const int m = 16 * mi + g;
+        split_tf32(r24_at(A, k0 + t, m), ah[mi][0], al[mi][0]);
+        split_tf32(r24_at(A, k0 + t, m + 8), ah[mi][1], al[mi][1]);
+        split_tf32(r24_at(A, k0 + t + 4, m), ah[mi][2], al[mi][2]);
+        split_tf32(r24_at(A, k0 + t + 4, m + 8), ah[mi][3], al[mi][3]);
+      }
+#pragma unroll
+      for (int ni = 0; ni < 3; ++ni) {
+        const int n = 8 * ni + g;
+        split_tf32(r24_at(B, k0 + t, n), bh[ni][0], bl[ni][0]);
+        split_tf32(r24_at(B, k0 + t + 4, n), bh[ni][1], bl[ni][1]);
+      }
+      // the small terms first, then the leading one
+#pragma unroll
+      for (int mi = 0; mi < 2; ++mi)
+#pragma unroll
+        for (int ni = 0; ni < 3; ++ni) {
+          asm volatile(
+              "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};"
+              : "+f"(acc[mi][ni][0]), "+f"(acc[mi][ni][1]), "+f"(acc[mi][ni][2]), "+f"(acc[mi][ni][3])
+              : "r"(al[mi][0]), "r"(al[mi][1]), "r"(al[mi][2]), "r"(al[mi][3]), "r"(bh[ni][0]), "r"(bh[ni][1]));
+          asm volatile(
+              "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};"
+              : "+f"(acc[mi][ni][0]), "+f"(acc[mi][ni][1]), "+f"(acc[mi][ni][2]), "+f"(acc[mi][ni][3])
+              : "r"(ah[mi][0]), "r"(ah[mi][1]), "r"(ah[mi][2]), "r"(ah[mi][3]), "r"(bl[ni][0]), "r"(bl[ni][1]));
+          asm volatile(
+              "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+              "{%0,%1,%2,%3};"
+              : "+f"(acc[mi][ni][0]), "+f"(acc[mi][ni][1]), "+f"(acc[mi][ni][2]), "+f"(acc[mi][ni][3])
+              : "r"(ah[mi][0]), "r"(ah[mi][1]), "r"(ah[mi][2]), "r"(ah[mi][3]), "r"(bh[ni][0]), "r"(bh[ni][1]));
+        }
+    }
+  } else if (P == PREC_TF32) {
 #pragma unroll
     for (int k0 = 0; k0 < 24; k0 += 8) {
       uint32_t a[2][4], b[3][2];

@@ -451,7 +451,8 @@ __device__ __forceinline__ StageOut factor_stage(const AgentPtrs& ap, float* sm,
   if (prec == PREC_FP64) r24_inv_f64(H, reinterpret_cast<double*>(sm + S_VEC + V_S * 64), lane);
   else r24_inv(H, sm + S_VEC + V_S * 64, lane);
   // K = -H_uu^-1 H_ux (H_uu^-1 symmetric)
-  if (prec == PREC_TF32) r24_gemm_tn_mma<PREC_TF32>(K, H, X, nullptr, -1.f, lane);
+  if (prec == PREC_TF32X3) r24_gemm_tn_mma<PREC_TF32X3>(K, H, X, nullptr, -1.f, lane);
+  else if (prec == PREC_TF32) r24_gemm_tn_mma<PREC_TF32>(K, H, X, nullptr, -1.f, lane);
   else if (prec == PREC_BF16) r24_gemm_tn_mma<PREC_BF16>(K, H, X, nullptr, -1.f, lane);
   else r24_gemm_tn(K, H, X, nullptr, -1.f, lane);
   copy_blk(ap.cK + (size_t)k * BLK, K, lane);
@@ -476,7 +477,8 @@ __device__ __forceinline__ StageOut factor_stage(const AgentPtrs& ap, float* sm,
   }
   if (k >= 1) {
     // P = A^T P A + H_ux^T K
-    if (prec == PREC_TF32) r24_gemm_tn_mma<PREC_TF32>(P, X, K, P, 1.f, lane);
+    if (prec == PREC_TF32X3) r24_gemm_tn_mma<PREC_TF32X3>(P, X, K, P, 1.f, lane);
+    else if (prec == PREC_TF32) r24_gemm_tn_mma<PREC_TF32>(P, X, K, P, 1.f, lane);
     else if (prec == PREC_BF16) r24_gemm_tn_mma<PREC_BF16>(P, X, K, P, 1.f, lane);
     else r24_gemm_tn(P, X, K, P, 1.f, lane);
     float t[NC];
@@ -2540,12 +2542,14 @@ cudaError_t launch_prec(const Arena& a, const Batch& b, const SolverParams& prm,
 }
 
 // Kernel variants: the minimum resident blocks per SM given to the compiler
-// (register cap), each in two builds: the FP32 factor only, or the factor
-// precision read at run time (TF32 / BF16 / FP64 paths).
+// (register cap), each in three builds: the FP32 factor only, the split-TF32
+// tensor-core factor only, or the factor precision read at run time (TF32 /
+// BF16 / FP64 paths).
 template <int MINB>
 cudaError_t launch_variant(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
                            cudaStream_t st, int* launches) {
   if (prm.precision == PREC_FP32) return launch_prec<MINB, PREC_FP32>(a, b, prm, form, grid_fused, st, launches);
+  if (prm.precision == PREC_TF32X3) return launch_prec<MINB, PREC_TF32X3>(a, b, prm, form, grid_fused, st, launches);
   return launch_prec<MINB, PREC_ANY>(a, b, prm, form, grid_fused, st, launches);
 }
 

@@ -50,8 +50,11 @@ def _case(name, n):
     return _REF[key]
 
 
-@pytest.mark.parametrize("precision,refine", [(0, 1), (3, 1)], ids=["fp32+refine", "fp64schur+refine"])
-def test_fp32_and_fp64_factor_match_oracle(mpcgpu, precision, refine):
+@pytest.mark.parametrize("precision,refine", [(0, 1), (3, 1), (4, 1)],
+                         ids=["fp32+refine", "fp64schur+refine", "tf32x3+refine"])
+def test_fp32_fp64_and_split_tf32_factor_match_oracle(mpcgpu, precision, refine):
+    # FP32 products, FP64 Schur inverse, and split-TF32 products on the tensor
+    # cores (three mma per tile: FP32-level accuracy), one refinement step each
     model, inps, refs = _case("uneven", 32)
     for (r, st), ref in zip(_solve(mpcgpu, model, inps, precision, refine), refs):
         assert (r["status"] == 0).all()
