@@ -57,10 +57,10 @@ def _measured_bf16_peak():
 
 BF16_PEAK_TFLOPS = _measured_bf16_peak()
 # DRAM bytes per agent of one solve step (order, set-up, persistent solve,
-# torque and RNEA kernels) from the last ncu capture of this kernel version
-# (profiles/mpc_k_fused_mixed16k_2048agents.md); None once the kernels have
-# changed since.
-TRAFFIC_BYTES_PER_AGENT = (133.16e6 + 116.05e6) / 2048
+# torque and RNEA kernels), measured with ncu on 2048 agents of the same
+# workload and kernel version and scaled per agent (the step's traffic grows
+# with the agents it solves); None once the kernels have changed since.
+TRAFFIC_BYTES_PER_AGENT = (290.06e6 + 189.03e6) / 2048
 
 
 def parse():
@@ -78,7 +78,10 @@ def parse():
     ap.add_argument("--early-polish", type=float, default=100.0)
     ap.add_argument("--no-autotune", action="store_true", help="skip the autotuner in the warm-up")
     ap.add_argument("--no-graph", action="store_true", help="launch without CUDA-graph replay")
-    ap.add_argument("--precision", type=int, default=0, help="factor precision: 0 FP32, 1 TF32, 2 BF16, 3 FP64")
+    ap.add_argument("--precision", type=int, default=0,
+                    help="factor precision: 0 FP32, 1 TF32, 2 BF16, 3 FP64 Schur inverse, 4 split TF32")
+    ap.add_argument("--fixed-iters", type=int, default=0,
+                    help="the paper's mode for every timed solve: this many ADMM iterations, no polish (0 = off)")
     ap.add_argument("--refine", type=int, default=-1, help="refinement steps per polish (-1: library default)")
     ap.add_argument("--no-precision", action="store_true", help="skip the per-precision speed/accuracy report")
     ap.add_argument("--no-policy", action="store_true", help="skip the residual-policy measurement")
@@ -86,6 +89,7 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=1.5, help="serving run length (0 = skip)")
     ap.add_argument("--no-tree", action="store_true",
                     help="diagonal joint model in the torque map instead of RNEA over a kinematic tree")
+    ap.add_argument("--serve-streams", type=int, default=2, help="serving: streams with a batch in flight")
     ap.add_argument("--serve-rate", default="0.5,1,2",
                     help="request rates, comma-separated, x 16384 agents at 100 Hz")
     return ap.parse_args()
@@ -146,20 +150,47 @@ def make_workload(name, n_agents, rank, world, n_replans):
 
 
 # ------------------------------------------------------------------ flops
-def flops_per_agent(N, iters, refac, polished):
-    """Algorithmic FP32 FLOPs of one agent-solve in this formulation (dense
-    22x22 coupled block + 8 scalar arm joints per stage).  polished: 2 when
-    the warm active set's polish succeeded (no ADMM factor), else 0/1; one
-    polish attempt is counted per solve."""
-    n = 22
-    mm = 2 * n ** 3            # one 22x22 product
-    mv = 2 * n ** 2            # one 22x22 mat-vec
-    factor = 8 * mm            # PA, PB, B'PB, B'PA, inverse, K, A'PA, X'K
-    iteration = 7 * mv + 600   # B's, H^-1 h, A's, K'h, Kx, Ax, Bu + row updates
-    check = 2 * mv + 400       # costate recursion + row residuals
-    polish = 10 * mm + 7 * mv + 2 * mv + 600
+# Algorithmic FP32 FLOPs per stage of this formulation: the coupled block is
+# n = 22 wide (base + legs; the 8 arm joints are scalar problems), and the
+# stage matrices are counted by their nonzeros (A_k: 74 in the compact
+# columns + 30 in the contact-dependent leg coupling; B: 64).
+_N = 22
+_NNZ_A, _NNZ_DA, _NNZ_B = 74, 30, 64
+_MV = 2 * _N * _N                     # a dense 22 x 22 mat-vec
+FACTOR_STAGE = (_MV                   # e = P c
+                + 2 * _NNZ_B * _N     # P B (sparse columns)
+                + 2 * _NNZ_B * _N     # B^T (P B)
+                + 2 * _NNZ_A * _N     # P A
+                + 2 * _NNZ_B * _N     # B^T (P A)
+                + 2 * _NNZ_A * _N     # A^T (P A)
+                + _N ** 3             # symmetric inverse of H_uu
+                + 2 * 2 * _N ** 3)    # K = -H_uu^-1 H_ux and H_ux^T K
+RECURSION_STAGE = 2 * _MV + 2 * (_NNZ_A + _NNZ_B) + 120     # H^-1 h, K^T h, A^T s, B^T s
+ROLLOUT_STAGE = _MV + 2 * (_NNZ_A + _NNZ_DA + _NNZ_B) + 100  # K x, A x, B u, eliminations
+REFINE_STAGE = 2 * _MV + 2 * (_NNZ_A + _NNZ_B) + 200 + ROLLOUT_STAGE   # residual, correction, re-roll
+CHECK_STAGE = 2 * (_NNZ_A + _NNZ_B) + 300                    # costate recursion, rows, signs
+POLISH_STAGE = FACTOR_STAGE + RECURSION_STAGE + ROLLOUT_STAGE + CHECK_STAGE + 300   # + reduced set-up
+ITER_STAGE = 2 * _MV + 2 * (_NNZ_A + _NNZ_B) + _MV + 2 * (_NNZ_A + _NNZ_DA + _NNZ_B) + 600
+RESID_STAGE = 2 * (_NNZ_A + _NNZ_B) + 400
+
+
+def flops_per_agent(N, iters, refac, polished, attempts=1.0, refine=1):
+    """Algorithmic FP32 FLOPs of one agent-solve (the counts above).
+    polished: 2 when the polish first succeeded (no ADMM factor), else 0/1;
+    attempts: reduced KKT solves per agent (mean of the polish-attempt
+    histogram); refine: refinement steps per polish solve."""
     admm_factors = np.where(polished == 2, 0, 1 + refac)
-    return N * (factor * admm_factors + iteration * iters + check * np.ceil(iters / 5.0) + polish)
+    polish = attempts * (POLISH_STAGE + refine * REFINE_STAGE)
+    return N * (FACTOR_STAGE * admm_factors + ITER_STAGE * iters + RESID_STAGE * np.ceil(iters / 5.0) + polish)
+
+
+def attempts_mean(hist):
+    """Mean reduced KKT solves per agent from the polish-attempt histogram
+    ([0] = no polish accepted, counted as one solve)."""
+    h = np.asarray(hist or [0, 1], dtype=float)
+    a = np.arange(len(h))
+    a[0] = 1
+    return float((a * h).sum() / max(h.sum(), 1.0))
 
 
 # ------------------------------------------------------------------ clocks
@@ -277,6 +308,8 @@ def run_ours(args):
         chosen = form == mpcgpu.FORM_FUSED
         kw = dict(variant=args.variant, check_every=args.check_every, early_polish=args.early_polish,
                   graph=int(chosen and not args.no_graph), precision=args.precision, refine_steps=args.refine)
+        if args.fixed_iters > 0:
+            kw.update(fixed_iters=args.fixed_iters, polish=0, warm_polish=0)
         kw.update(opts)
         s = mpcgpu.Solver(max_agents=n, max_horizon=int(Nh.max()), form=form, device=local,
                           stream=stream.cuda_stream, **kw)
@@ -356,7 +389,9 @@ def run_ours(args):
     ms_step = total_ms / args.steps
 
     # roofline of the dominant kernel (the fused solve kernel, one launch per step)
-    fl = flops_per_agent(Nh, st["iters"], st["refactors"], st["polished"]).sum()
+    att = attempts_mean(st["polish_attempts"])
+    fl = flops_per_agent(Nh, st["iters"], st["refactors"], st["polished"], attempts=att,
+                         refine=1 if args.refine < 0 else args.refine).sum()
     kern_ms = float(np.mean(per))
     achieved = fl / (kern_ms / 1e3) / 1e12
     peak_mhz = clocks["sm_max_mhz"] or 2032.0
@@ -621,13 +656,13 @@ def run_serving(args, model, replans, n):
     sinp = {k: np.concatenate([replans[0][k], np.asarray(rinp[k], np.float32)]) for k in replans[0]}
     out = {}
     for f in [float(v) for v in str(args.serve_rate).split(",") if v.strip()]:
-        eng = ServingEngine(smodel, sinp, pool=n, streams=2, hbm_budget_bytes=8 << 30, seed=7)
+        eng = ServingEngine(smodel, sinp, pool=n, streams=args.serve_streams, hbm_budget_bytes=8 << 30, seed=7)
         st = eng.run(rate=f * 16384 * 100.0, duration=args.serve_seconds, churn_period=1.0, churn_frac=0.05)
         eng.close()
         st["rate_x_16384_at_100hz"] = f
         st["churned_agents"] = int(eng.churned)
         out[f"{f:g}x"] = st
-    out["note"] = ("requests of one agent coalesce (newest state wins); 2 streams; churn: 5% of the agents "
+    out["note"] = (f"requests of one agent coalesce (newest state wins); {args.serve_streams} streams; churn: 5% of the agents "
                    "(between requests) swapped for reserve agents every 1 s = 100 replans at 100 Hz; "
                    "rates x 1.6384 M requests/s")
     return out

@@ -414,6 +414,93 @@ mpc_status mpc_measure_peak(int32_t kind, void* stream, double* tflops, double* 
 /* One-line description of the last error on this context (never NULL). */
 const char* mpc_last_error(mpc_ctx* ctx);
 
+/* ---------------------------------------------------------------- serving
+ * Continuous batching (the serving form of the replan loop): agents are the
+ * context's slots; their warm starts and factor caches stay on the device.
+ * Requests (slot, state, arrival time) are pushed from any host thread; a
+ * later request of a slot that is not yet in a batch replaces the earlier
+ * one's state (coalescing: the newest state wins) and is answered by the
+ * same solve.  A worker thread, started by mpc_server_start, owns the
+ * context until mpc_server_stop: whenever fewer than max_inflight batches
+ * are on the GPU it forms the next one from every slot with pending requests
+ * and no batch in flight (oldest request first, at most max_batch slots),
+ * copies their states to the device and enqueues set-up, solve, gather and
+ * the copy of the torques back on one of its own streams.  When that batch
+ * completes, each request it covered is answered; its latency is the
+ * completion time minus its arrival time on the server's clock
+ * (mpc_server_clock: seconds since mpc_server_start).  While the server runs
+ * the caller makes no other call on the context; the context outlives the
+ * server.  Ownership: the server copies every input on push; results are
+ * copied out by mpc_server_results.  Errors: MPC_ERR_INVALID for bad
+ * arguments (a slot outside [0, pool), a NULL buffer); a CUDA or solver
+ * error stops the worker and is returned by mpc_server_drain and
+ * mpc_server_stop (text: mpc_server_last_error). */
+typedef struct mpc_server mpc_server;
+
+/* pool: slots served (<= the context's max_agents, ids 0..pool-1, each given
+ * a model by mpc_set_models before); max_batch: largest batch; max_inflight:
+ * batches on the GPU at a time (1..4; each has its own stream and pinned and
+ * device buffers, allocated here). */
+mpc_status mpc_server_create(mpc_ctx* ctx, int32_t pool, int32_t max_batch, int32_t max_inflight,
+                             mpc_server** out);
+/* Starts the worker and the server's clock.  MPC_ERR_STATE if started. */
+mpc_status mpc_server_start(mpc_server* srv);
+/* n requests (host arrays): slots [n], x0 [n][30], qd_meas [n][18], cmd [n][4],
+ * phase [n], t_arrive [n] (seconds on the server's clock). */
+mpc_status mpc_server_push(mpc_server* srv, int32_t n, const int32_t* slots, const float* x0,
+                           const float* qd_meas, const float* cmd, const float* phase, const double* t_arrive);
+/* Agents leaving and joining: each slot's model is replaced (its warm start
+ * reset, as by mpc_set_models) by the worker once the slot has no batch in
+ * flight; requests already pending for the slot are answered by the new
+ * agent's solve. */
+mpc_status mpc_server_set_models(mpc_server* srv, int32_t n, const int32_t* slots, const mpc_agent_model* models);
+/* Waits until every pushed request is answered and every swap applied, at
+ * most timeout_s seconds (MPC_ERR_TIMEOUT after that). */
+mpc_status mpc_server_drain(mpc_server* srv, double timeout_s);
+/* Seconds since mpc_server_start. */
+double mpc_server_clock(mpc_server* srv);
+/* Results so far (host buffers, each may be NULL except n_latency):
+ * latency [cap] the answered requests' latencies in answer order (s),
+ * *n_latency their count; tau [pool][18] and status [pool] each slot's last
+ * answer (status -1: never answered); counters [6] = requests pushed,
+ * answered, batches, agent-solves, solves not SOLVED, model swaps applied. */
+mpc_status mpc_server_results(mpc_server* srv, double* latency, int64_t cap, int64_t* n_latency, float* tau,
+                              int32_t* status, int64_t* counters);
+/* The completed batches so far (host buffer, may be NULL): log [cap][3] =
+ * launch time, completion time (s, server clock), agents; *n_batches their
+ * count. */
+mpc_status mpc_server_batches(mpc_server* srv, double* log, int64_t cap, int64_t* n_batches);
+/* Stops the worker after its batches in flight have completed. */
+mpc_status mpc_server_stop(mpc_server* srv);
+const char* mpc_server_last_error(mpc_server* srv);
+/* Stops the server if running and frees its streams and buffers. */
+mpc_status mpc_server_destroy(mpc_server* srv);
+
+/* Synthetic request source for measuring the server (the paper has no
+ * counterpart; it stands in for the simulator's per-step requests): replays
+ * n requests, arrival times t_arrive [n] (seconds from the moment its thread
+ * starts, non-decreasing; pushed with that moment added, on the server's
+ * clock) for slots [n] (< pool), in real time from a thread of its own
+ * through mpc_server_push.  A request is one 10 ms environment step of
+ * its agent: phase += phase_step, and one step of a mean-reverting walk of the
+ * state about the agent's initial state x_init [pool][30] (host),
+ * x <- x_init + revert (x - x_init) + sigma xi with xi ~ N(0, I); qd_meas =
+ * 0.1 xi'; cmd [pool][4] with the commanded height set to the current one;
+ * phase [pool] the initial phases.  Normal draws from a seeded counter-based
+ * generator.  The trace is copied. */
+typedef struct mpc_load mpc_load;
+mpc_status mpc_load_start(mpc_server* srv, int64_t n, const double* t_arrive, const int32_t* slots, int32_t pool,
+                          const float* x_init, const float* cmd, const float* phase, float revert, float sigma,
+                          float phase_step, uint64_t seed, mpc_load** out);
+/* New walk origins for slots whose agents changed (host arrays). */
+mpc_status mpc_load_reset(mpc_load* load, int32_t n, const int32_t* slots, const float* x_init, const float* cmd,
+                          const float* phase);
+/* Waits (at most timeout_s) until every request has been pushed; lag_stats
+ * [3] (may be NULL) = median, 99th percentile and largest delay between a
+ * pushed chunk's oldest arrival time and its push (s). */
+mpc_status mpc_load_wait(mpc_load* load, double timeout_s, double* lag_stats);
+mpc_status mpc_load_destroy(mpc_load* load);
+
 #ifdef __cplusplus
 }
 #endif

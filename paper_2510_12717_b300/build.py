@@ -13,7 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmpcgpu.so")
-SOURCES = ["solver_v1.cu", "solver_v2.cu", "solver_host.cu", "capi.cu", "static_solve.cu", "policy.cu", "peaks.cu"]
+SOURCES = ["solver_v1.cu", "solver_v2.cu", "solver_host.cu", "capi.cu", "static_solve.cu", "policy.cu", "peaks.cu",
+           "server.cu", "load.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -908,6 +908,13 @@ struct Res { float rp, rd, ps, ds, pn, dn; };
 // 1e-11 of the objective (a flat direction of the cost), lands above it and
 // is corrected.
 constexpr float kScaledAccept = 1.f;
+// Corrections change an active row whose check value exceeds kFixScale times
+// its own tolerance; a point that no correction can change (or that of the
+// last attempt) is accepted within kScaledLoose times its tolerance (the
+// residual bar of 1e-4, absolute plus relative, per component) instead of
+// going to ADMM.
+constexpr float kFixScale = 1.f;
+constexpr float kScaledLoose = 10.f;
 // ADMM's own stopping test (its iterate is reported INACCURATE unless a
 // polish certifies it) and the threshold of its infeasibility test read the
 // scaled residuals of admm_residuals at 10 times the tolerance
@@ -1545,7 +1552,7 @@ __device__ __noinline__ bool polish_solve(const AgentPtrs& ap, float* sm, int la
 // row if the limit is overshot, else the limit row.  Dual and primal
 // corrections touch disjoint rows; the stage's conditions are read from the
 // copy in act taken before either.  *changed reports whether anything changed.  The thresholds are the tighter
-// of the failed check's global tolerances (tol_p, tol_d) and kScaledAccept
+// of the failed check's global tolerances (tol_p, tol_d) and kFixScale
 // times the row's or component's own tolerance.
 template <bool FIX>
 __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm,
@@ -1614,7 +1621,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
       const float tp = ea + er * sc;
       rp = fmaxf(rp, viol);
       pn = fmaxf(pn, viol / tp);
-      if (FIX && viol > fminf(tol_p, kScaledAccept * tp) && act[r] == 0) {
+      if (FIX && viol > fminf(tol_p, kFixScale * tp) && act[r] == 0) {
         ak[r] = (v < lo) ? 1 : 2;
         chg = 1;
       }
@@ -1645,8 +1652,8 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
         const float br = fmaxf(fmaxf(dt * nu - ch_up, 0.f), fmaxf(ch_lo - dt * nu, 0.f));
         rd = fmaxf(rd, fmaxf(bq, br));
         dn = fmaxf(dn, fmaxf(bq / tol_nu, br / ch_tol));
-        if (FIX && bq > fminf(tol_d, kScaledAccept * tol_nu)) { ap.act[ch_ke * RS + lane + 26] = 0; chg = 1; }
-        if (FIX && br > fminf(tol_d, kScaledAccept * ch_tol)) { ap.act[ch_ke * RS + lane + 8] = 0; chg = 1; }
+        if (FIX && bq > fminf(tol_d, kFixScale * tol_nu)) { ap.act[ch_ke * RS + lane + 26] = 0; chg = 1; }
+        if (FIX && br > fminf(tol_d, kFixScale * ch_tol)) { ap.act[ch_ke * RS + lane + 8] = 0; chg = 1; }
         ch_on = 0;
       };
       if (a && (ch_on || aq)) {
@@ -1677,7 +1684,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
           const float bad = (aq & 1) ? fmaxf(yq, 0.f) : fmaxf(-yq, 0.f);   // lower: y_q <= 0; upper: >= 0
           rd = fmaxf(rd, bad);
           dn = fmaxf(dn, bad / tol);
-          if (FIX && bad > fminf(tol_d, kScaledAccept * tol)) { ak[lane + 26] = 0; chg = 1; }
+          if (FIX && bad > fminf(tol_d, kFixScale * tol)) { ak[lane + 26] = 0; chg = 1; }
         }
         m += yq;
         ma += fabsf(tu);
@@ -1688,7 +1695,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
         else bad = fabsf(g);
         rd = fmaxf(rd, bad);
         dn = fmaxf(dn, bad / td);
-        if (FIX && a && bad > fminf(tol_d, kScaledAccept * td)) { ak[lane + 8] = 0; chg = 1; }
+        if (FIX && a && bad > fminf(tol_d, kFixScale * td)) { ak[lane + 8] = 0; chg = 1; }
       }
     }
     // feet: lane f in 0..1
@@ -1697,7 +1704,7 @@ __device__ __noinline__ Res polish_check(const AgentPtrs& ap, float* sm, int lan
       const FootAct fa = foot_act(act, f);
       const float gx = vG[b], gy = vG[b + 1], gz = vG[b + 2];
       const float tf = fmaxf(fmaxf(vT[b], vT[b + 1]), vT[b + 2]);
-      const float thr = fminf(tol_d, kScaledAccept * tf);
+      const float thr = fminf(tol_d, kFixScale * tf);
       if (!fa.swing) {
         for (int c = 3; c < 6; ++c) {                                  // free moments
           rd = fmaxf(rd, fabsf(vG[b + c]));
@@ -1818,8 +1825,12 @@ __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, co
     const Res pr = polish_check<false>(ap, sm, lane, prm, nullptr, pat);
     const float tol_p = prm.eps_abs + prm.eps_rel * pr.ps;
     const float tol_d = prm.eps_abs + prm.eps_rel * pr.ds;
-    const bool ok = isfinite(pr.rp) && isfinite(pr.rd) && pr.rp <= tol_p && pr.rd <= tol_d &&
-                    pr.pn <= kScaledAccept && pr.dn <= kScaledAccept;
+    const bool base = isfinite(pr.rp) && isfinite(pr.rd) && pr.rp <= tol_p && pr.rd <= tol_d;
+    const bool loose = base && pr.pn <= kScaledLoose && pr.dn <= kScaledLoose;
+    bool ok = base && pr.pn <= kScaledAccept && pr.dn <= kScaledAccept;
+    int changed = 1;
+    if (!ok && attempt + 1 < attempts) polish_check<true>(ap, sm, lane, prm, &changed, pat, tol_p, tol_d);
+    if (!ok && loose && (!changed || attempt + 1 == attempts)) ok = true;
     if (ok) {
       for (int k = 1; k <= ap.N; ++k) ap.x[k * VS + lane] = ap.xt[k * VS + lane];
       for (int k = 0; k < ap.N; ++k) ap.u[k * VS + lane] = ap.ut[k * VS + lane];
@@ -1828,10 +1839,7 @@ __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, co
       *res = pr;
       return true;
     }
-    if (attempt + 1 == attempts) break;
-    int changed = 0;
-    polish_check<true>(ap, sm, lane, prm, &changed, pat, tol_p, tol_d);
-    if (!changed) return false;
+    if (attempt + 1 == attempts || !changed) break;
   }
   return false;
 }

@@ -112,6 +112,22 @@ SIGNATURES = {
     "mpc_policy_torques": (C.c_int, [_P, C.c_uint64, _P, _P]),
     "mpc_set_trees": (C.c_int, [_P, C.c_int32, _P, _P]),
     "mpc_measure_peak": (C.c_int, [C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
+    "mpc_server_create": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
+    "mpc_server_start": (C.c_int, [_P]),
+    "mpc_server_push": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P]),
+    "mpc_server_set_models": (C.c_int, [_P, C.c_int32, _P, _P]),
+    "mpc_server_drain": (C.c_int, [_P, C.c_double]),
+    "mpc_server_clock": (C.c_double, [_P]),
+    "mpc_server_results": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_int64), _P, _P, _P]),
+    "mpc_server_batches": (C.c_int, [_P, _P, C.c_int64, C.POINTER(C.c_int64)]),
+    "mpc_server_stop": (C.c_int, [_P]),
+    "mpc_server_last_error": (C.c_char_p, [_P]),
+    "mpc_server_destroy": (C.c_int, [_P]),
+    "mpc_load_start": (C.c_int, [_P, C.c_int64, _P, _P, C.c_int32, _P, _P, _P, C.c_float, C.c_float, C.c_float,
+                                 C.c_uint64, C.POINTER(C.c_void_p)]),
+    "mpc_load_reset": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P]),
+    "mpc_load_wait": (C.c_int, [_P, C.c_double, _P]),
+    "mpc_load_destroy": (C.c_int, [_P]),
 }
 
 _lib = None
@@ -354,3 +370,133 @@ class Solver:
         buf = C.create_string_buffer(4096)
         self._check(self.lib.mpc_get_stats(self.ctx, buf, 4096))
         return json.loads(buf.value.decode())
+
+
+class Server:
+    """Continuous-batching server over a Solver's context (mpc_server_*).
+
+    While it runs the context is the server's: make no other Solver call
+    until stop().  Inputs are copied on push; results() copies the answered
+    requests' latencies, each slot's last torques and status, and counters."""
+
+    def __init__(self, solver: Solver, pool: int, max_batch: int = 0, max_inflight: int = 2):
+        self.lib = load()
+        self.solver = solver
+        self.pool = pool
+        h = C.c_void_p()
+        st = self.lib.mpc_server_create(solver.ctx, pool, max_batch or pool, max_inflight, C.byref(h))
+        if st != MPC_OK:
+            raise MpcError(st, "mpc_server_create failed")
+        self.srv = h
+
+    def _check(self, st):
+        if st != MPC_OK:
+            raise MpcError(st, self.lib.mpc_server_last_error(self.srv).decode())
+
+    def start(self):
+        self._check(self.lib.mpc_server_start(self.srv))
+
+    def clock(self) -> float:
+        return self.lib.mpc_server_clock(self.srv)
+
+    def push(self, slots, x0, qd_meas, cmd, phase, t_arrive):
+        slots = np.ascontiguousarray(slots, np.int32)
+        x0 = np.ascontiguousarray(x0, np.float32)
+        qd_meas = np.ascontiguousarray(qd_meas, np.float32)
+        cmd = np.ascontiguousarray(cmd, np.float32)
+        phase = np.ascontiguousarray(phase, np.float32)
+        t_arrive = np.ascontiguousarray(t_arrive, np.float64)
+        self._check(self.lib.mpc_server_push(self.srv, len(slots), _ptr(slots), _ptr(x0), _ptr(qd_meas),
+                                             _ptr(cmd), _ptr(phase), _ptr(t_arrive)))
+
+    def set_models(self, model: dict, slots, idx=None):
+        recs = pack_models(model, idx)
+        slots = np.ascontiguousarray(slots, np.int32)
+        self._keep = recs
+        self._check(self.lib.mpc_server_set_models(self.srv, len(slots), _ptr(slots), recs.ctypes.data))
+
+    def drain(self, timeout_s: float = 60.0):
+        self._check(self.lib.mpc_server_drain(self.srv, C.c_double(timeout_s)))
+
+    def results(self):
+        n = C.c_int64(0)
+        self._check(self.lib.mpc_server_results(self.srv, None, 0, C.byref(n), None, None, None))
+        lat = np.empty(max(n.value, 1), np.float64)
+        tau = np.empty((self.pool, 18), np.float32)
+        status = np.empty(self.pool, np.int32)
+        cnt = np.zeros(6, np.int64)
+        self._check(self.lib.mpc_server_results(self.srv, _ptr(lat), len(lat), C.byref(n), _ptr(tau),
+                                                _ptr(status), _ptr(cnt)))
+        keys = ("pushed", "answered", "batches", "solves", "not_solved", "swapped")
+        return dict(latency=lat[:min(n.value, len(lat))], tau=tau, status=status, **dict(zip(keys, cnt.tolist())))
+
+    def batches(self):
+        """Completed batches: array [n][3] of launch time, completion time (s), agents."""
+        n = C.c_int64(0)
+        self._check(self.lib.mpc_server_batches(self.srv, None, 0, C.byref(n)))
+        log = np.zeros((max(n.value, 1), 3), np.float64)
+        self._check(self.lib.mpc_server_batches(self.srv, _ptr(log), len(log), C.byref(n)))
+        return log[:n.value]
+
+    def stop(self):
+        self._check(self.lib.mpc_server_stop(self.srv))
+
+    def close(self):
+        if getattr(self, "srv", None):
+            self.lib.mpc_server_destroy(self.srv)
+            self.srv = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Load:
+    """Synthetic request source replaying an arrival trace in real time into
+    a Server (mpc_load_*): one mean-reverting walk step of the agent's state
+    per request, from a native thread."""
+
+    def __init__(self, server: Server, t_arrive, slots, x_init, cmd, phase, *, revert=0.95, sigma=0.02,
+                 phase_step=0.02, seed=0):
+        self.lib = load()
+        t = np.ascontiguousarray(t_arrive, np.float64)
+        sl = np.ascontiguousarray(slots, np.int32)
+        x = np.ascontiguousarray(x_init, np.float32)
+        c = np.ascontiguousarray(cmd, np.float32)
+        p = np.ascontiguousarray(phase, np.float32)
+        h = C.c_void_p()
+        st = self.lib.mpc_load_start(server.srv, len(t), _ptr(t), _ptr(sl), server.pool, _ptr(x), _ptr(c), _ptr(p),
+                                     C.c_float(revert), C.c_float(sigma), C.c_float(phase_step), C.c_uint64(seed),
+                                     C.byref(h))
+        if st != MPC_OK:
+            raise MpcError(st, "mpc_load_start failed")
+        self.h = h
+
+    def reset(self, slots, x_init, cmd, phase):
+        sl = np.ascontiguousarray(slots, np.int32)
+        st = self.lib.mpc_load_reset(self.h, len(sl), _ptr(sl), _ptr(np.ascontiguousarray(x_init, np.float32)),
+                                     _ptr(np.ascontiguousarray(cmd, np.float32)),
+                                     _ptr(np.ascontiguousarray(phase, np.float32)))
+        if st != MPC_OK:
+            raise MpcError(st, "mpc_load_reset failed")
+
+    def wait(self, timeout_s: float = 60.0):
+        """Blocks until every request was pushed; returns (median, p99, max) push lag in seconds."""
+        lag = np.zeros(3, np.float64)
+        st = self.lib.mpc_load_wait(self.h, C.c_double(timeout_s), _ptr(lag))
+        if st != MPC_OK:
+            raise MpcError(st, "mpc_load_wait failed")
+        return tuple(lag.tolist())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mpc_load_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -73,5 +73,11 @@ def test_flop_model():
     with_admm = b.flops_per_agent(N, np.array([50, 50]), zero, np.array([1, 1]))
     assert polished[1] == 2 * polished[0]                 # linear in the horizon
     assert (with_admm > polished).all()                   # ADMM adds its factor and iterations
+    # the factor's count: two dense 22^3 products, a symmetric inverse, the
+    # sparse A/B products by their nonzeros, one mat-vec
     n = 22
-    assert polished[0] == 10 * (10 * 2 * n ** 3 + 9 * 2 * n ** 2 + 600)
+    assert b.FACTOR_STAGE == 2 * 2 * n ** 3 + n ** 3 + 2 * n * (3 * 64 + 2 * 74) + 2 * n * n
+    assert polished[0] == 10 * (b.POLISH_STAGE + b.REFINE_STAGE)
+    two = b.flops_per_agent(N, zero, zero, np.array([2, 2]), attempts=2.0)
+    assert np.allclose(two - polished, polished)          # a second reduced solve costs the same
+    assert b.attempts_mean([0, 3, 1]) == 1.25

@@ -1,4 +1,5 @@
-"""Serving form: continuous batching over two streams with churn."""
+"""Serving form: the native continuous-batching server (mpc_server_*) with
+churn, and its answers against direct solves of the same states."""
 import numpy as np
 import pytest
 
@@ -38,3 +39,51 @@ def test_budget_admission():
     s = mpcgpu.Solver(max_agents=1024, max_horizon=20, hbm_budget_bytes=1 << 30)
     assert s.stats()["arena_bytes"] <= 1 << 30
     s.close()
+
+
+def test_server_answers_equal_direct_solves():
+    # every agent's answer from the server equals a direct solve of the same
+    # state on a context with the same history (each agent's solve depends
+    # only on its own state and warm start); two rounds: all agents, then a
+    # subset whose requests coalesce (the newest state wins)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2510_12717_b300 import mpcgpu
+    from workload import make_agents, perturb_inputs
+    n = 96
+    ids = np.arange(n)
+    model, inp = make_agents("serving", ids)
+    r1 = perturb_inputs("serving", inp, ids, 1)
+    r2 = perturb_inputs("serving", r1, ids, 2)
+    f32 = lambda x: {k: np.ascontiguousarray(v, np.float32) for k, v in x.items()}
+    inp, r1, r2 = f32(inp), f32(r1), f32(r2)
+    stream = torch.cuda.current_stream().cuda_stream
+    direct = mpcgpu.Solver(max_agents=n, max_horizon=20, stream=stream)
+    served = mpcgpu.Solver(max_agents=n, max_horizon=20, stream=stream)
+    direct.set_models(model, ids)
+    served.set_models(model, ids)
+    slots = ids.astype(np.int32)
+    d1 = direct.solve_host(slots, inp["x0"], inp["qd_meas"], inp["cmd"], inp["phase"])
+    sub = slots[::3]
+    d2 = direct.solve_host(sub, r2["x0"][sub], r2["qd_meas"][sub], r2["cmd"][sub], r2["phase"][sub])
+    srv = mpcgpu.Server(served, n, max_batch=40, max_inflight=2)
+    srv.start()
+    srv.push(slots, inp["x0"], inp["qd_meas"], inp["cmd"], inp["phase"], np.zeros(n))
+    srv.drain(30.0)
+    a1 = srv.results()
+    # round 2: the subset's replan-1 state, then its replan-2 state in the same push (coalesced)
+    both = np.concatenate([sub, sub])
+    cat = lambda k: np.concatenate([r1[k][sub], r2[k][sub]])
+    t = srv.clock()
+    srv.push(both, cat("x0"), cat("qd_meas"), cat("cmd"), cat("phase"), np.full(len(both), t))
+    srv.drain(30.0)
+    a2 = srv.results()
+    srv.stop()
+    srv.close()
+    served.close()
+    direct.close()
+    assert a1["answered"] == n and a1["batches"] >= 3          # max_batch 40 splits the first round
+    assert np.array_equal(a1["tau"], d1["tau"]) and (a1["status"] == 0).all()
+    assert a2["answered"] == n + len(both) and a2["solves"] == n + len(sub)   # the pairs coalesced
+    assert np.array_equal(a2["tau"][sub], d2["tau"])
+    assert len(a2["latency"]) == n + len(both) and (a2["latency"] >= 0).all()
