@@ -478,10 +478,10 @@ mpc_status mpc_server_destroy(mpc_server* srv);
 
 /* Synthetic request source for measuring the server (the paper has no
  * counterpart; it stands in for the simulator's per-step requests): replays
- * n requests, arrival times t_arrive [n] (seconds from the moment its thread
- * starts, non-decreasing; pushed with that moment added, on the server's
- * clock) for slots [n] (< pool), in real time from a thread of its own
- * through mpc_server_push.  A request is one 10 ms environment step of
+ * n requests, arrival times t_arrive [n] (seconds from the end of this
+ * call's set-up, non-decreasing; pushed with that moment added, on the
+ * server's clock) for slots [n] (< pool), in real time from threads of its
+ * own (the slots split between them) through mpc_server_push.  A request is one 10 ms environment step of
  * its agent: phase += phase_step, and one step of a mean-reverting walk of the
  * state about the agent's initial state x_init [pool][30] (host),
  * x <- x_init + revert (x - x_init) + sigma xi with xi ~ N(0, I); qd_meas =
