@@ -516,7 +516,7 @@ def run_ours(args):
 
     serving = None
     if args.serve_seconds > 0:
-        serving = run_serving(args, model, replans, n)
+        serving = run_serving(args, model, replans, n, cfg)
 
     if rank != 0:
         return
@@ -643,7 +643,7 @@ def precision_report(args, timed, cfg, n, world, mpcgpu):
 
 
 # ------------------------------------------------------------------ serving
-def run_serving(args, model, replans, n):
+def run_serving(args, model, replans, n, cfg=None):
     """Continuous batching under a Poisson request stream (16384-agent pool),
     at each requested rate; each agent's state walks forward one 10 ms step
     per request from the workload's first replan."""
@@ -656,13 +656,20 @@ def run_serving(args, model, replans, n):
     sinp = {k: np.concatenate([replans[0][k], np.asarray(rinp[k], np.float32)]) for k in replans[0]}
     out = {}
     for f in [float(v) for v in str(args.serve_rate).split(",") if v.strip()]:
-        eng = ServingEngine(smodel, sinp, pool=n, streams=args.serve_streams, hbm_budget_bytes=8 << 30, seed=7)
+        # an iteration cap sized to the latency budget: an agent whose polish
+        # fails and whose ADMM fallback has not converged after 500 iterations
+        # (about 30 ms of one warp) is answered MAX_ITER instead of holding its
+        # whole batch for up to 4000
+        eng = ServingEngine(smodel, sinp, pool=n, streams=args.serve_streams, hbm_budget_bytes=8 << 30, seed=7,
+                            max_iter=500, **(cfg or {}))
         st = eng.run(rate=f * 16384 * 100.0, duration=args.serve_seconds, churn_period=1.0, churn_frac=0.05)
         eng.close()
         st["rate_x_16384_at_100hz"] = f
         st["churned_agents"] = int(eng.churned)
         out[f"{f:g}x"] = st
-    out["note"] = (f"requests of one agent coalesce (newest state wins); {args.serve_streams} streams; churn: 5% of the agents "
+    out["note"] = (f"native server (mpc_server_*), requests replayed by native threads (mpc_load_*); requests of one "
+                   f"agent coalesce (newest state wins); {args.serve_streams} batches in flight; ADMM cap 500 iterations; "
+                   "churn: 5% of the agents "
                    "(between requests) swapped for reserve agents every 1 s = 100 replans at 100 Hz; "
                    "rates x 1.6384 M requests/s")
     return out

@@ -63,6 +63,7 @@ struct mpc_server {
   std::vector<uint8_t> inflight;
   std::vector<int32_t> ready_order;               // scratch of the worker
   std::vector<std::pair<int32_t, mpc_agent_model>> swaps;
+  double swaps_since = -1.0;                      // queue time of the oldest pending swap
   // results (guarded by mu)
   std::vector<double> latency;
   std::vector<double> batch_log;                   // per batch: launch time, completion time, agents
@@ -193,6 +194,7 @@ void apply_swaps(mpc_server* s) {
       else { ids.push_back(sw.first); models.push_back(sw.second); }
     }
     s->swaps.swap(keep);
+    s->swaps_since = keep.empty() ? -1.0 : now_s(s);
   }
   if (ids.empty()) return;
   const mpc_status r = mpc_set_models(s->ctx, (int32_t)ids.size(), ids.data(), models.data());
@@ -213,7 +215,6 @@ void run_worker(mpc_server* s) {
       else if (q != cudaErrorNotReady) { set_error(s, MPC_ERR_CUDA, cudaGetErrorString(q)); return; }
       else ++busy;
     }
-    apply_swaps(s);
     for (auto& L : s->lanes) {
       if (busy >= s->max_inflight) break;
       if (L.busy) continue;
@@ -221,6 +222,17 @@ void run_worker(mpc_server* s) {
       ++busy;
       work = true;
     }
+    // model swaps wait for the device (their upload queues behind the
+    // batches that hold the SMs): apply them while every lane is busy, when
+    // the worker could launch nothing anyway, when the GPU is idle, or once
+    // the oldest has waited 20 ms
+    bool due = false;
+    {
+      std::lock_guard<std::mutex> g(s->mu);
+      due = !s->swaps.empty() &&
+            (busy >= s->max_inflight || busy == 0 || now_s(s) - s->swaps_since > 0.02);
+    }
+    if (due) apply_swaps(s);
     if (!work) {
       // nothing completed or launched: wait briefly for a push or a completion
       std::unique_lock<std::mutex> lk(s->mu);
@@ -301,10 +313,10 @@ mpc_status mpc_server_push(mpc_server* s, int32_t n, const int32_t* slots, const
 mpc_status mpc_server_set_models(mpc_server* s, int32_t n, const int32_t* slots, const mpc_agent_model* models) {
   if (!s || n < 0 || (n > 0 && (!slots || !models))) return MPC_ERR_INVALID;
   std::lock_guard<std::mutex> g(s->mu);
-  for (int i = 0; i < n; ++i) {
+  for (int i = 0; i < n; ++i)
     if (slots[i] < 0 || slots[i] >= s->pool) return MPC_ERR_INVALID;
-    s->swaps.emplace_back(slots[i], models[i]);
-  }
+  if (s->swaps.empty() && n > 0) s->swaps_since = now_s(s);
+  for (int i = 0; i < n; ++i) s->swaps.emplace_back(slots[i], models[i]);
   return MPC_OK;
 }
 
