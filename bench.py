@@ -516,7 +516,8 @@ def run_ours(args):
 
     serving = None
     if args.serve_seconds > 0:
-        serving = run_serving(args, model, replans, n, cfg)
+        serving = run_serving(args, model, replans, n,
+                              {k: cfg[k] for k in ("variant", "check_every", "early_polish")})
 
     if rank != 0:
         return

@@ -270,13 +270,19 @@ mpc_status mpc_solve(mpc_ctx* ctx, uint64_t ticket);
  * results are gathered on the same stream by mpc_get_torques. */
 mpc_status mpc_solve_on(mpc_ctx* ctx, uint64_t ticket, void* stream);
 
-/* Pick the kernel variant, residual-check period and early-polish threshold
- * (the batching form's tunables) by timing every candidate on the ticket's
- * batch (`repeats` timed solves each, after one untimed solve) on the
- * context's stream.  Among the candidates that solve the most agents the
- * fastest wins and is stored in the context's configuration.  The batch's
- * agents are solved repeatedly (their warm starts advance); the ticket stays
- * submitted.  report (may be NULL) receives a JSON summary.  Synchronous. */
+/* Tune the batching form's launch configuration on the ticket's batch by
+ * timing candidates (`repeats` timed solves each, after one untimed solve) on
+ * the context's stream, in two stages: the kernel shape (variant = register
+ * cap and so resident warps, x the persistent kernel's resident blocks per
+ * SM: all that fit, or fewer agents in flight), then the ADMM schedule
+ * (residual-check period x early-polish threshold) on the best shape.  Among
+ * the candidates that solve the most agents the fastest wins.  The choice is
+ * stored in the context's configuration and in its table of tuned entries,
+ * keyed by (precision, floor(log2 batch size)): every later solve of a batch
+ * with that key uses the entry (with the tuned batch's mean horizon recorded
+ * beside it).  The batch's agents are solved repeatedly (their warm starts
+ * advance); the ticket stays submitted.  report (may be NULL) receives a JSON
+ * summary: the choice, its key, every candidate, the table.  Synchronous. */
 mpc_status mpc_autotune(mpc_ctx* ctx, uint64_t ticket, int32_t repeats, char* report, size_t cap);
 
 /* Enqueue a gather of the ticket's results into caller buffers (any may be

@@ -37,12 +37,24 @@ struct GraphEntry {
   int n = -1;
   const void* ptrs[5] = {};
   cudaStream_t stream = nullptr;
-  int variant = 0, check_every = 0, trees = 0;
+  int variant = 0, check_every = 0, trees = 0, grid = 0;
   int kernels = 0;                  // kernels the captured graph launches
   float early_polish = 0.f;
   cudaGraphExec_t exec = nullptr;
 };
 constexpr int kMaxGraphs = 16;
+
+// A tuned launch configuration, kept per (factor precision, batch-size bin
+// = floor(log2 n)): kernel variant (register cap, resident warps), resident
+// grid of the persistent kernel in blocks per SM (agents in flight; 0 = all
+// that fit), ADMM residual-check interval and early-polish threshold.
+// mean_horizon records the tuned batch's horizon mix.
+struct TuneEntry {
+  int precision = 0, size_bin = 0;
+  int variant = 1, check_every = 10, grid_per_sm = 0;
+  float early_polish = 100.f, ms = 0.f, mean_horizon = 0.f;
+};
+int size_bin(int n) { int b = 0; while ((2 << b) <= n) ++b; return b; }
 
 }  // namespace
 
@@ -76,6 +88,8 @@ struct mpc_ctx {
   long long launches = 0;
   long long solves = 0;
   long long graph_replays = 0;
+  std::vector<TuneEntry> tuned;      // mpc_autotune's choices, used by every later solve of their key
+  int nsm = 0;                       // SMs of the context's device
   // residual policy (mpc_set_policy): bfloat16 weights, FP32 biases
   mpc::PolicyDev pol{};
   bool has_policy = false;
@@ -194,6 +208,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
     return s;
   };
   if (cudaSetDevice(cfg->device) != cudaSuccess) return bail(MPC_ERR_CUDA);
+  cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, cfg->device);
   Arena& a = ctx->ar;
   a.max_agents = (int)A;
   a.maxN = (int)n;
@@ -513,23 +528,38 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   return p;
 }
 
+// the launch configuration of a batch: the tuned entry of its key if there
+// is one, else the context's options
+static const TuneEntry* tuned_for(const mpc_ctx* ctx, int n) {
+  const int bin = size_bin(n);
+  for (const auto& t : ctx->tuned)
+    if (t.precision == ctx->cfg.precision && t.size_bin == bin) return &t;
+  return nullptr;
+}
+
 static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
   int launches = 0;
-  mpc::SolverParams prm = params_of(ctx->cfg);
+  mpc_config cfg = ctx->cfg;
+  int grid = 0;
+  if (const TuneEntry* t = tuned_for(ctx, tk->b.n)) {
+    cfg.variant = t->variant; cfg.check_every = t->check_every; cfg.early_polish = t->early_polish;
+    grid = t->grid_per_sm * ctx->nsm;
+  }
+  mpc::SolverParams prm = params_of(cfg);
   prm.trees = ctx->has_trees ? 1 : 0;
   const int form = ctx->cfg.form;
   // graph capture needs a non-default stream; on the legacy stream the
   // solve is launched directly
   if (!ctx->cfg.graph || form != MPC_FORM_FUSED || st == nullptr || st == cudaStreamLegacy) {
-    cudaError_t e = mpc::launch_solve(ctx->ar, tk->b, prm, form, 0, st, &launches, ctx->cfg.variant);
+    cudaError_t e = mpc::launch_solve(ctx->ar, tk->b, prm, form, grid, st, &launches, cfg.variant);
     ctx->launches += launches;
     return e;
   }
   const void* ptrs[5] = {tk->b.ids, tk->b.x0, tk->b.qd, tk->b.cmd, tk->b.phase};
   for (int gi = 0; gi < kMaxGraphs; ++gi) {
     GraphEntry& g = ctx->graphs[gi];
-    if (g.exec && g.n == tk->b.n && g.stream == st && g.variant == ctx->cfg.variant &&
-        g.check_every == ctx->cfg.check_every && g.early_polish == ctx->cfg.early_polish &&
+    if (g.exec && g.n == tk->b.n && g.stream == st && g.variant == cfg.variant &&
+        g.check_every == cfg.check_every && g.early_polish == cfg.early_polish && g.grid == grid &&
         g.trees == prm.trees && !memcmp(g.ptrs, ptrs, sizeof(ptrs))) {
       ctx->graph_replays += 1;
       ctx->launches += g.kernels;       // the kernels recorded in the graph
@@ -540,7 +570,7 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
   // with this entry's own queue buffers
   cudaError_t e = mpc::launch_solve(ctx->ar, mpc::Batch{0, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
                                                         nullptr},
-                                    prm, form, 0, st, nullptr, ctx->cfg.variant);
+                                    prm, form, 0, st, nullptr, cfg.variant);
   if (e != cudaSuccess) return e;
   const int gi = ctx->graph_next;
   ctx->graph_next = (ctx->graph_next + 1) % kMaxGraphs;
@@ -557,7 +587,7 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
   cudaGraph_t graph = nullptr;
   e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  e = mpc::launch_solve(ctx->ar, b, prm, form, 0, st, &launches, ctx->cfg.variant);
+  e = mpc::launch_solve(ctx->ar, b, prm, form, grid, st, &launches, cfg.variant);
   cudaError_t e2 = cudaStreamEndCapture(st, &graph);
   if (e != cudaSuccess) return e;
   if (e2 != cudaSuccess) return e2;
@@ -567,9 +597,10 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
   g.n = tk->b.n;
   memcpy(g.ptrs, ptrs, sizeof(ptrs));
   g.stream = st;
-  g.variant = ctx->cfg.variant;
-  g.check_every = ctx->cfg.check_every;
-  g.early_polish = ctx->cfg.early_polish;
+  g.variant = cfg.variant;
+  g.check_every = cfg.check_every;
+  g.early_polish = cfg.early_polish;
+  g.grid = grid;
   g.trees = prm.trees;
   g.kernels = launches;
   ctx->launches += launches;
@@ -781,62 +812,105 @@ mpc_status mpc_autotune(mpc_ctx* ctx, uint64_t ticket, int32_t repeats, char* re
   if (tk->state != 1) return fail(ctx, MPC_ERR_STATE, "autotune: ticket already solved");
   if (repeats < 1) repeats = 1;
   CK(cudaSetDevice(ctx->cfg.device));
-  const mpc_config saved = ctx->cfg;
-  struct Cand { int variant, check_every; float early; float ms; float solved; };
-  std::vector<Cand> cands;
-  for (int v = 1; v <= 2; ++v)
-    for (int c : {5, 10})
-      for (float ep : {30.f, 100.f, 1000.f}) cands.push_back(Cand{v, c, ep, 0.f, 0.f});
+  // the batch's horizon mix (host copy of its ids; recorded with the choice)
+  std::vector<int> ids(tk->b.n);
+  if (tk->b.n) CK(cudaMemcpy(ids.data(), tk->b.ids, sizeof(int) * tk->b.n, cudaMemcpyDeviceToHost));
+  double hsum = 0.0;
+  for (int id : ids) hsum += (id >= 0 && id < ctx->cfg.max_agents) ? ctx->live[id] : 0;
+  const float mean_h = tk->b.n ? (float)(hsum / tk->b.n) : 0.f;
+  struct Cand { int variant, grid_per_sm, check_every; float early; float ms; float solved; };
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   std::vector<int> st(tk->b.n);
   int* d_st = ctx->d_status;
-  int best = -1;
-  for (size_t i = 0; i < cands.size(); ++i) {
-    ctx->cfg.variant = cands[i].variant;
-    ctx->cfg.check_every = cands[i].check_every;
-    ctx->cfg.early_polish = cands[i].early;
-    ctx->cfg.graph = 0;
-    mpc::SolverParams prm = params_of(ctx->cfg);
+  auto run = [&](Cand& c) -> cudaError_t {
+    mpc_config cfg = ctx->cfg;
+    cfg.variant = c.variant; cfg.check_every = c.check_every; cfg.early_polish = c.early;
+    mpc::SolverParams prm = params_of(cfg);
     prm.trees = ctx->has_trees ? 1 : 0;
+    const int grid = c.grid_per_sm * ctx->nsm;
     int launches = 0;
     // one untimed pass (warm starts from this candidate), then timed passes
-    CK(mpc::launch_solve(ctx->ar, tk->b, prm, ctx->cfg.form, 0, ctx->stream, &launches, ctx->cfg.variant));
-    CK(cudaEventRecord(e0, ctx->stream));
-    for (int r = 0; r < repeats; ++r)
-      CK(mpc::launch_solve(ctx->ar, tk->b, prm, ctx->cfg.form, 0, ctx->stream, &launches, ctx->cfg.variant));
-    CK(cudaEventRecord(e1, ctx->stream));
-    CK(mpc::launch_gather(ctx->ar, tk->b.n, tk->b.ids, nullptr, nullptr, nullptr, nullptr, d_st, ctx->stream));
-    CK(cudaEventSynchronize(e1));
-    CK(cudaMemcpy(st.data(), d_st, sizeof(int) * tk->b.n, cudaMemcpyDeviceToHost));
+    cudaError_t e = mpc::launch_solve(ctx->ar, tk->b, prm, cfg.form, grid, ctx->stream, &launches, cfg.variant);
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(e0, ctx->stream);
+    for (int r = 0; r < repeats && e == cudaSuccess; ++r)
+      e = mpc::launch_solve(ctx->ar, tk->b, prm, cfg.form, grid, ctx->stream, &launches, cfg.variant);
+    if (e != cudaSuccess) return e;
+    cudaEventRecord(e1, ctx->stream);
+    e = mpc::launch_gather(ctx->ar, tk->b.n, tk->b.ids, nullptr, nullptr, nullptr, nullptr, d_st, ctx->stream);
+    if (e != cudaSuccess) return e;
+    e = cudaEventSynchronize(e1);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpy(st.data(), d_st, sizeof(int) * tk->b.n, cudaMemcpyDeviceToHost);
     float ms = 0.f;
-    CK(cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventElapsedTime(&ms, e0, e1);
     int ok = 0;
     for (int v : st) ok += (v == MPC_AGENT_SOLVED);
-    cands[i].ms = ms / repeats;
-    cands[i].solved = tk->b.n ? (float)ok / tk->b.n : 1.f;
+    c.ms = ms / repeats;
+    c.solved = tk->b.n ? (float)ok / tk->b.n : 1.f;
     ctx->launches += launches;
-  }
+    return e;
+  };
   // fastest among the candidates that solve as many agents as the best one
-  float best_solved = 0.f;
-  for (auto& c : cands) best_solved = c.solved > best_solved ? c.solved : best_solved;
-  for (size_t i = 0; i < cands.size(); ++i)
-    if (cands[i].solved >= best_solved && (best < 0 || cands[i].ms < cands[best].ms)) best = (int)i;
+  auto pick = [](const std::vector<Cand>& cs) {
+    float best_solved = 0.f;
+    for (auto& c : cs) best_solved = c.solved > best_solved ? c.solved : best_solved;
+    int best = 0;
+    for (size_t i = 0; i < cs.size(); ++i)
+      if (cs[i].solved >= best_solved && (cs[best].solved < best_solved || cs[i].ms < cs[best].ms)) best = (int)i;
+    return best;
+  };
+  // stage 1: register cap (resident warps) x agents in flight (resident
+  // blocks per SM: all that fit, or fewer, which keeps more of the in-flight
+  // agents' stage blocks in L2); stage 2: the ADMM schedule on the best shape
+  std::vector<Cand> all;
+  std::vector<Cand> shape;
+  for (int v = 1; v <= 2; ++v)
+    for (int g = 0; g <= v; ++g)      // g = 0: all that fit (v + 1 blocks per SM)
+      shape.push_back(Cand{v, g, ctx->cfg.check_every, ctx->cfg.early_polish, 0.f, 0.f});
+  for (auto& c : shape) CK(run(c));
+  const Cand s1 = shape[pick(shape)];
+  std::vector<Cand> sched;
+  for (int c : {5, 10})
+    for (float ep : {30.f, 100.f, 1000.f}) sched.push_back(Cand{s1.variant, s1.grid_per_sm, c, ep, 0.f, 0.f});
+  for (auto& c : sched) CK(run(c));
+  const Cand best = sched[pick(sched)];
+  all = shape;
+  all.insert(all.end(), sched.begin(), sched.end());
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  ctx->cfg = saved;
-  ctx->cfg.variant = cands[best].variant;
-  ctx->cfg.check_every = cands[best].check_every;
-  ctx->cfg.early_polish = cands[best].early;
+  // the choice: the context's options (as before) and the entry of this key
+  ctx->cfg.variant = best.variant;
+  ctx->cfg.check_every = best.check_every;
+  ctx->cfg.early_polish = best.early;
+  TuneEntry te;
+  te.precision = ctx->cfg.precision; te.size_bin = size_bin(tk->b.n);
+  te.variant = best.variant; te.check_every = best.check_every; te.grid_per_sm = best.grid_per_sm;
+  te.early_polish = best.early; te.ms = best.ms; te.mean_horizon = mean_h;
+  bool found = false;
+  for (auto& t : ctx->tuned)
+    if (t.precision == te.precision && t.size_bin == te.size_bin) { t = te; found = true; }
+  if (!found) ctx->tuned.push_back(te);
   if (report && cap) {
-    std::string js = "{\"chosen\": {\"variant\": " + std::to_string(cands[best].variant) +
-                     ", \"check_every\": " + std::to_string(cands[best].check_every) +
-                     ", \"early_polish\": " + std::to_string(cands[best].early) + "}, \"candidates\": [";
-    for (size_t i = 0; i < cands.size(); ++i) {
-      char b[200];
-      snprintf(b, sizeof(b), "%s{\"variant\": %d, \"check_every\": %d, \"early_polish\": %g, \"ms\": %.4f, \"solved\": %.5f}",
-               i ? ", " : "", cands[i].variant, cands[i].check_every, cands[i].early, cands[i].ms, cands[i].solved);
+    char b[256];
+    snprintf(b, sizeof(b), "{\"chosen\": {\"variant\": %d, \"grid_per_sm\": %d, \"check_every\": %d, \"early_polish\": %g}, "
+             "\"key\": {\"precision\": %d, \"size_bin\": %d, \"mean_horizon\": %.2f}, \"candidates\": [",
+             best.variant, best.grid_per_sm, best.check_every, best.early, te.precision, te.size_bin, mean_h);
+    std::string js = b;
+    for (size_t i = 0; i < all.size(); ++i) {
+      snprintf(b, sizeof(b), "%s{\"variant\": %d, \"grid_per_sm\": %d, \"check_every\": %d, \"early_polish\": %g, "
+               "\"ms\": %.4f, \"solved\": %.5f}", i ? ", " : "", all[i].variant, all[i].grid_per_sm,
+               all[i].check_every, all[i].early, all[i].ms, all[i].solved);
+      js += b;
+    }
+    js += "], \"table\": [";
+    for (size_t i = 0; i < ctx->tuned.size(); ++i) {
+      const auto& t = ctx->tuned[i];
+      snprintf(b, sizeof(b), "%s{\"precision\": %d, \"size_bin\": %d, \"variant\": %d, \"grid_per_sm\": %d, "
+               "\"check_every\": %d, \"early_polish\": %g, \"ms\": %.4f, \"mean_horizon\": %.2f}", i ? ", " : "",
+               t.precision, t.size_bin, t.variant, t.grid_per_sm, t.check_every, t.early_polish, t.ms, t.mean_horizon);
       js += b;
     }
     js += "]}";

@@ -98,8 +98,12 @@ def test_autotune_picks_a_solving_configuration(mpcgpu):
     s.set_models(model, ids)
     tk = s.submit(ids_d, t["x0"], t["qd_meas"], t["cmd"], t["phase"])
     rep = s.autotune(tk, repeats=1)
-    assert len(rep["candidates"]) == 12
+    # shape stage (variant x resident blocks per SM: 2 + 3) then schedule stage (2 x 3)
+    assert len(rep["candidates"]) == 11
     ch = rep["chosen"]
+    assert rep["key"]["size_bin"] == 8 and len(rep["table"]) == 1      # 256 agents: floor(log2) = 8
+    assert abs(rep["key"]["mean_horizon"] - model["N"].mean()) <= 0.005      # reported to 2 decimals
+    assert rep["table"][0]["grid_per_sm"] == ch["grid_per_sm"]
     assert s.stats()["variant"] == ch["variant"] and s.stats()["check_every"] == ch["check_every"]
     s.solve(tk)
     tau = torch.empty((256, 18), device="cuda:0")
