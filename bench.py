@@ -56,6 +56,35 @@ def _measured_bf16_peak():
 
 
 BF16_PEAK_TFLOPS = _measured_bf16_peak()
+
+
+def _measured_hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+HBM_PEAK_GBS, HBM_PEAK_KIND = _measured_hbm_peak()
+
+
+# Literal form (MPC_FORM_LDL): algorithmic bytes of one OSQP iteration of one
+# agent.  Per stage the forward substitution reads L_k (4005 strictly-lower
+# entries of the 90 x 90 block) and the coupling block G_k (30 x 30, stages
+# k >= 1); the backward one reads L_k again, 1/D_k (90) and G_{k+1} (stages
+# k + 1 < N); the stage's iterate and row data are read and written once
+# (u_k, x_{k+1}, the dynamics multipliers: 3 x 30 read + written; the 56
+# rows' slack and multiplier read + written, bounds, classes read; the
+# references, affine term and forward vector: 3 x 30 + 90 written + read).
+LDL_L, LDL_G, LDL_D = 4005, 900, 90
+LDL_STATE = 2 * 3 * 30 + 2 * 2 * 56 + 3 * 56 + 3 * 30 + 2 * 90
+
+
+def ldl_bytes_per_iteration(N):
+    N = np.asarray(N, dtype=np.int64)
+    floats = N * (2 * LDL_L + LDL_D + LDL_STATE) + 2 * (N - 1) * LDL_G
+    return 4 * floats
 # DRAM bytes per agent of one solve step (order, set-up, persistent solve,
 # torque and RNEA kernels), measured with ncu on 2048 agents of the same
 # workload and kernel version and scaled per agent (the step's traffic grows
@@ -72,6 +101,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--agents", type=int, default=0, help="override agent count (0 = workload's)")
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--no-literal", action="store_true",
+                    help="skip the literal form (OSQP on the full KKT system, block LDL^T)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--variant", type=int, default=1, help="kernel variant (register cap), 1 or 2")
     ap.add_argument("--check-every", type=int, default=10)
@@ -509,6 +540,38 @@ def run_ours(args):
                       "note": "fixed N_QP = 25 ADMM iterations per replan, warm-started, no polish (the paper's "
                               "mode; speed only, not converged)"}
 
+    # the paper's literal solve (MPC_FORM_LDL): OSQP's ADMM on the full KKT
+    # system of Eq. kkt_system, one block LDL^T per replan (Eq. ldl) and
+    # N_QP = 25 substitution solves (Eqs. backsolve_1-2), from f_init; speed
+    # only (parity with the oracle's literal iteration: tests/test_gpu_ldl.py).
+    # The iteration kernel's time is the difference of the 25- and the
+    # 1-iteration replans over 24 (the same set-up, factor and torque map)
+    literal = None
+    if not args.no_literal:
+        K4 = min(args.steps, 3)
+        lt = {}
+        for fi in (25, 1):
+            sl, tl, perl, ll, _, statl, _, _ = timed(mpcgpu.FORM_LDL, K4, args.warmup, tune=False,
+                                                      keep_report=False, fixed_iters=fi)
+            lt[fi] = (tl / K4, perl, ll // K4, statl)
+            sl.close()
+        it_ms = (lt[25][0] - lt[1][0]) / 24.0
+        bytes_it = float(ldl_bytes_per_iteration(Nh).sum())
+        gbs = bytes_it / (it_ms / 1e3) / 1e9 if it_ms > 0 else None
+        literal = {"value": world * n / (lt[25][0] / 1e3), "ms_per_step": lt[25][0],
+                   "p50_ms": float(np.percentile(lt[25][1], 50)), "admm_iters": 25,
+                   "factor_and_one_iteration_ms": lt[1][0], "iteration_ms": it_ms,
+                   "gpu_launches_per_step": lt[25][2],
+                   "status_max_iter_frac": float((lt[25][3] == 1).mean()),
+                   "roofline": {"kernel": "mpc_k_ldl_admm (one OSQP iteration over all agents)", "bound": "hbm",
+                                "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                                "frac": None if gbs is None else gbs / HBM_PEAK_GBS,
+                                "bytes_per_iteration": bytes_it,
+                                "peak_basis": f"{HBM_PEAK_KIND} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+                   "note": "paper's literal Alg. 1: OSQP ADMM on the full KKT system, block LDL^T once per "
+                           "replan, 25 forward/backward substitutions, cold start f_init each replan, no polish; "
+                           "A/B against the Riccati form's paper_mode_fixed25"}
+
     precision = None
     if not args.no_precision:
         precision = precision_report(args, timed, cfg, n, world, mpcgpu)
@@ -548,6 +611,7 @@ def run_ours(args):
         "latency_budget_ms": 10.0, "per_step_ms": [round(v, 3) for v in per], "cold_solve": cold,
         "plain": plain,
         "paper_mode_fixed25": paper_mode,
+        "literal_ldl_fixed25": literal,
         "precision": precision,
         "residual_policy": policy,
         "serving": serving,

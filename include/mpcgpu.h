@@ -84,7 +84,20 @@ typedef enum {
  * cores (three mma per tile, FP32-level accuracy; Ootomo and Yokota 2022). */
 typedef enum { MPC_FP32 = 0, MPC_TF32 = 1, MPC_BF16 = 2, MPC_FP64 = 3, MPC_TF32X3 = 4 } mpc_precision;
 
-typedef enum { MPC_FORM_PLAIN = 0, MPC_FORM_FUSED = 1 } mpc_form;
+/* Launch form of a context's solves.  PLAIN and FUSED solve with the
+ * per-stage Riccati recursion (polish first, ADMM fallback).  LDL is the
+ * paper's literal solve (Alg. 1, Sec. III-B): OSQP's ADMM on the full KKT
+ * system of Eq. (kkt_system), factored once per solve by a batched block
+ * LDL^T (Eq. ldl; the inequality rows' pivots first, then per stage the
+ * block of u_k, the stage's dynamics multipliers and x_{k+1}) and solved by
+ * forward / backward substitution in every iteration (Eqs. backsolve_1-2);
+ * every solve starts from f_init (cold), rho stays at rho0, no polish.  With
+ * fixed_iters > 0 it runs exactly that many iterations (the paper's N_QP;
+ * agent_status MPC_AGENT_MAX_ITER), otherwise until OSQP's stopping test at
+ * a residual check every check_every iterations (MPC_AGENT_INACCURATE: not
+ * certified by a polish) or max_iter.  Its factors take about 36 KB per
+ * stage per agent of device memory (max_agents x max_horizon stages). */
+typedef enum { MPC_FORM_PLAIN = 0, MPC_FORM_FUSED = 1, MPC_FORM_LDL = 2 } mpc_form;
 
 /* Unit measured by mpc_measure_peak. */
 typedef enum {
@@ -128,7 +141,8 @@ typedef struct mpc_config {
                                  ADMM, polish, torque map; static grids); FUSED = a
                                  set-up kernel, one persistent kernel that solves
                                  every agent (polish first, ADMM fallback, polish) over
-                                 a longest-first work queue, and a torque-map kernel */
+                                 a longest-first work queue, and a torque-map kernel;
+                                 LDL = the paper's literal KKT solve (see mpc_form) */
   float rho0, sigma, alpha;   /* ADMM step size, proximal weight, relaxation */
   float eps_abs, eps_rel;     /* OSQP-style stopping tolerances */
   int max_iter;               /* iteration cap */

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(HERE, "libmpcgpu.so")
 SOURCES = ["solver_v1.cu", "solver_v2.cu", "solver_host.cu", "capi.cu", "static_solve.cu", "policy.cu", "peaks.cu",
-           "server.cu", "load.cu"]
+           "server.cu", "load.cu", "ldl.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

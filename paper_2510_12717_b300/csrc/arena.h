@@ -97,7 +97,21 @@ struct Arena {
   int* counter;           // [1] next queue position
   int* fault;             // [F_COUNT] device event counters (F_WAIT_TIMEOUTS: agents whose bounded
                           //   wait gave up; each retired its warp after draining its copies)
+  // literal form only (MPC_FORM_LDL; NULL otherwise): the block LDL^T factors of
+  // the full KKT system, per stage LDL_REC floats (strictly lower L by columns
+  // and by rows, 1/D, the coupling block of the stage's dynamics rows to the
+  // previous stage's x), the forward-substitution vectors, the dynamics
+  // multipliers
+  float* lL;              // [A][maxN*LDL_REC]
+  float* lw;              // [A][maxN*LDL_W]
+  float* ly;              // [A][maxN*VS]
 };
+// literal-form record of one stage: 90 block variables (u_k, the stage's 30
+// dynamics multipliers, x_{k+1}); strictly lower L packed by columns at
+// LDL_COL, the same entries packed by rows at LDL_ROW, 1/D at LDL_IND, the
+// 30 x 30 coupling block G_k (row-major) at LDL_G
+enum : int { LDL_NB = 90, LDL_COL = 0, LDL_ROW = 4008, LDL_IND = 8016, LDL_G = 8112, LDL_REC = 9024,
+             LDL_W = 96 };
 enum : int { F_WAIT_TIMEOUTS = 0, F_COUNT = 4 };
 
 // lin record layout: dense A_base and B (column-major, stride 23), their

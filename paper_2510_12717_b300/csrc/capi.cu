@@ -146,6 +146,13 @@ static size_t arena_bytes(size_t A, size_t n) {
   return f * 4;
 }
 
+// bytes of the literal form's extra arenas (block LDL^T factors, forward
+// vectors, dynamics multipliers)
+static size_t ldl_bytes(size_t A, size_t n) {
+  using namespace mpc;
+  return A * n * (size_t)(LDL_REC + LDL_W + VS) * 4;
+}
+
 extern "C" {
 
 mpc_status mpc_default_config(mpc_config* cfg) {
@@ -189,14 +196,16 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   if (cfg->refine_steps < -1 || cfg->refine_steps > 4) return MPC_ERR_INVALID;
   if (cfg->spin_limit <= 0 || cfg->wait_test_agent < -1 || cfg->wait_test_agent >= cfg->max_agents)
     return MPC_ERR_INVALID;
-  if (cfg->form != MPC_FORM_PLAIN && cfg->form != MPC_FORM_FUSED) return MPC_ERR_INVALID;
+  if (cfg->form != MPC_FORM_PLAIN && cfg->form != MPC_FORM_FUSED && cfg->form != MPC_FORM_LDL)
+    return MPC_ERR_INVALID;
   if (!(cfg->rho0 > 0.f) || !(cfg->sigma > 0.f) || !(cfg->alpha > 0.f && cfg->alpha < 2.f) ||
       !(cfg->eps_abs >= 0.f) || !(cfg->eps_rel >= 0.f) || cfg->max_iter <= 0 || cfg->fixed_iters < 0 ||
       cfg->graph < 0 || cfg->graph > 1 ||
       cfg->check_every <= 0 || cfg->variant < 1 || cfg->variant > 2 || !(cfg->early_polish >= 0.f))
     return MPC_ERR_INVALID;
   const size_t A = (size_t)cfg->max_agents, n = (size_t)cfg->max_horizon;
-  if (cfg->hbm_budget_bytes && arena_bytes(A, n) > cfg->hbm_budget_bytes) return MPC_ERR_BUDGET;
+  const size_t extra = cfg->form == MPC_FORM_LDL ? ldl_bytes(A, n) : 0;
+  if (cfg->hbm_budget_bytes && arena_bytes(A, n) + extra > cfg->hbm_budget_bytes) return MPC_ERR_BUDGET;
 
   mpc_ctx* ctx = new mpc_ctx();
   ctx->cfg = *cfg;
@@ -262,6 +271,11 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   AL(ctx->qcount, (size_t)kMaxTickets * 8);
   AL(ctx->gorder, (size_t)kMaxGraphs * A);
   AL(ctx->gcount, (size_t)kMaxGraphs * 8);
+  if (cfg->form == MPC_FORM_LDL) {
+    AL(a.lL, A * n * LDL_REC);
+    AL(a.lw, A * n * LDL_W);
+    AL(a.ly, A * n * VS);
+  }
 #undef AL
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -523,6 +537,8 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   p.refine_admm = c.refine_steps >= 0 ? c.refine_steps : low;
   p.trees = 0;
   p.split = 1;
+  // the literal form starts every solve from f_init: the set-up kernel's cold start
+  if (c.form == MPC_FORM_LDL) p.warm_start = 0;
   p.spin_limit = c.spin_limit;
   p.wait_test_slot = c.wait_test_agent;
   return p;
@@ -810,6 +826,7 @@ mpc_status mpc_autotune(mpc_ctx* ctx, uint64_t ticket, int32_t repeats, char* re
   Ticket* tk = find_ticket(ctx, ticket);
   if (!tk) return fail(ctx, MPC_ERR_NOT_READY, "autotune: unknown ticket");
   if (tk->state != 1) return fail(ctx, MPC_ERR_STATE, "autotune: ticket already solved");
+  if (ctx->cfg.form == MPC_FORM_LDL) return fail(ctx, MPC_ERR_INVALID, "autotune: not for the literal form");
   if (repeats < 1) repeats = 1;
   CK(cudaSetDevice(ctx->cfg.device));
   // the batch's horizon mix (host copy of its ids; recorded with the choice)
@@ -945,7 +962,7 @@ mpc_status mpc_get_stats(mpc_ctx* ctx, char* buf, size_t cap) {
            "\"early_polish\": %g, \"graph\": %d, \"wait_timeouts\": %d, "
            "\"polish_attempts\": [%lld, %lld, %lld, %lld, %lld, %lld, %lld, %lld, %lld]}",
            ctx->cfg.max_agents, ctx->cfg.max_horizon, live, ctx->bytes,
-           ctx->cfg.form == MPC_FORM_FUSED ? "fused" : "plain", ctx->launches, ctx->solves, ctx->graph_replays,
+           ctx->cfg.form == MPC_FORM_FUSED ? "fused" : ctx->cfg.form == MPC_FORM_LDL ? "ldl" : "plain", ctx->launches, ctx->solves, ctx->graph_replays,
            mpc::smem_bytes_per_block(), mpc::WARPS_PER_BLOCK, ctx->cfg.variant, ctx->cfg.check_every,
            (double)ctx->cfg.early_polish, ctx->cfg.graph, fault[mpc::F_WAIT_TIMEOUTS], hist[0], hist[1], hist[2], hist[3], hist[4], hist[5],
            hist[6], hist[7], hist[8]);

@@ -1,0 +1,666 @@
+// Literal form of the paper's QP solve (MPC_FORM_LDL): OSQP's ADMM on the
+// full KKT system of Eq. (kkt_system), factored once per solve into
+// L_K D_K L_K^T (Eq. ldl) and solved by forward substitution, diagonal
+// scaling and backward substitution in every iteration (Eqs. backsolve_1,
+// backsolve_2); Alg. 1 with cuDSS_fac / cuDSS_solve replaced by the kernels
+// below.  The ADMM update (f_ADMM) is OSQP's (Stellato et al. 2020, Sec. 3),
+// to which the paper defers after Eq. (backsolve_2):
+//
+//   [[P + sigma I, A^T], [A, -rho^-1]] [x~; nu] = [sigma x - q; z - rho^-1 y]
+//   z~ = z + rho^-1 (nu - y),  x <- alpha x~ + (1 - alpha) x,
+//   zr = alpha z~ + (1 - alpha) z,  z <- clip(zr + rho^-1 y, l, u),
+//   y <- y + rho (zr - z).
+//
+// The rows of A are the dynamics x_{k+1} - A_k x_k - B u_k = c_k (l = u, step
+// size rho_eq = 1e3 rho) and the stage inequality rows (wrench boxes,
+// friction pyramids, joint-rate boxes on u_k, joint boxes on x_{k+1}; rows
+// with l = u take rho_eq, free rows are left out).
+//
+// Elimination order (a symmetric permutation of A_K; A_K is quasi-definite,
+// so every order has an LDL^T factorisation with diagonal D): first the
+// inequality rows, one 1 x 1 pivot -1/rho_r each (their Schur complement adds
+// C^T diag(rho) C to the stage's u_k and x_{k+1} blocks and never leaves the
+// stage), then per stage k the 90 block variables (u_k, the stage's dynamics
+// multipliers, x_{k+1}).  In that order A_K is block tridiagonal in the
+// stages: the only coupling between blocks k-1 and k is the entry -A_k of the
+// dynamics rows of stage k on x_k.  The block factorisation: S_0 = M_0,
+// S_k = M_k - A_k X_{k-1} A_k^T on the multiplier block, where X_{k-1} is the
+// x_k block of S_{k-1}^-1 = L_xx^-T D_xx^-1 L_xx^-1 (x last in the block);
+// with Y_k = A_k L_xx^-T, the off-diagonal factor is L_{k,k-1} = -Y_k D_xx^-1
+// =: -G_k and the update is G_k Y_k^T.  The dense 90 x 90 blocks are factored
+// without pivoting.
+//
+// Kernels (one warp per agent):
+//   mpc_k_ldl_factor : assembles and factors the blocks stage by stage in
+//                      shared memory; writes L (packed by columns for the
+//                      forward substitution and by rows for the backward one,
+//                      so that both read coalesced), 1/D and G_k
+//   mpc_k_ldl_admm   : the iterations; per iteration a forward pass over the
+//                      stages (right-hand side, coupling, unit lower solve)
+//                      and a backward pass (1/D, coupling, unit upper solve,
+//                      then the stage's relaxation, projection and dual
+//                      updates); fixed N_QP (the paper's mode) or until OSQP's
+//                      stopping test with a residual check every check_every
+// The set-up kernel before them (schedule, references, bounds, linearisation,
+// the cold start of f_init) and the torque map after them are the solver's
+// own.  Every iteration reads each stage's factors from global memory.
+#include "solver_dev.cuh"
+#include "solver.h"
+
+namespace mpc {
+namespace {
+
+constexpr int NB = LDL_NB;
+constexpr int SLD = NB + 1;                              // row stride of the block in shared memory
+constexpr int F_FLOATS = NB * SLD + 96 + 2 * 30 * 31;    // factor kernel: shared floats per warp
+
+__host__ __device__ constexpr int col_off(int j) { return (NB - 1) * j - j * (j - 1) / 2; }
+__host__ __device__ constexpr int row_off(int i) { return i * (i - 1) / 2; }
+
+__device__ __forceinline__ bool live_row(const Arena& a, const Batch& b, int row) {
+  if (row >= b.n) return false;
+  const int s = b.ids[row];
+  return s >= 0 && s < a.max_agents && a.horizon[s] >= 2 && a.horizon[s] <= a.maxN;
+}
+
+// entry (r, c) of the dynamics matrix A_k of the coupled block and the arms
+// (A_base plus the contact-dependent leg-joint block dA_k of rows 9-11)
+__device__ __forceinline__ float a_entry(const float* lin, int k, int r, int c) {
+  if (r < NC) {
+    if (c >= NC) return 0.f;
+    float v = lin[L_ABASE + c * LDD + r];
+    if (r >= 9 && r < 12 && c >= 12) v += lin[L_STAGE + k * 64 + (r - 9) * 10 + (c - 12)];
+    return v;
+  }
+  return c == r ? 1.f : 0.f;
+}
+__device__ __forceinline__ float b_entry(const float* lin, float dt, int r, int c) {
+  if (r < NC) return c < NC ? lin[L_B + c * LDD + r] : 0.f;
+  return c == r ? dt : 0.f;
+}
+// coefficient of input c (0 f_x, 1 f_y, 2 f_z of one foot) in the foot's
+// friction-pyramid row t (f_x - mu f_z, -f_x - mu f_z, f_y - mu f_z, -f_y - mu f_z)
+__device__ __forceinline__ float pyr_coef(int c, int t, float mu) {
+  if (c == 2) return -mu;
+  if (c == 0) return t == 0 ? 1.f : (t == 1 ? -1.f : 0.f);
+  return t == 2 ? 1.f : (t == 3 ? -1.f : 0.f);
+}
+// value of inequality row r (0..55) of a stage at (u_k, x_{k+1})
+__device__ __forceinline__ float row_value(int r, const float* U, const float* X, float mu) {
+  if (r < 12) return U[r];
+  if (r < 20) {
+    const int f = (r - 12) >> 2, t = (r - 12) & 3, b = 6 * f;
+    const float s = (t < 2 ? U[b] : U[b + 1]) * ((t & 1) ? -1.f : 1.f);
+    return s - mu * U[b + 2];
+  }
+  if (r < 38) return U[r - 8];
+  return X[r - 26];
+}
+
+// ------------------------------------------------------------------ factor
+__global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverParams prm) {
+  const int lane = threadIdx.x;
+  const int row = blockIdx.x;
+  if (!live_row(a, b, row)) return;
+  const int slot = b.ids[row];
+  const AgentPtrs ap = agent_ptrs(a, slot);
+  if (ap.st[T_STATUS] == MPC_AGENT_NAN_) return;
+  extern __shared__ __align__(16) float fsm[];
+  float* S = fsm;                   // the stage's block, row-major (lower triangle used)
+  float* v = S + NB * SLD;          // column below the pivot
+  float* Y = v + 96;                // Y = A_{k+1} L_xx^-T, rows of stride 31
+  float* M = Y + 30 * 31;           // Y D_xx^-1 Y^T: carried into the next block
+  const float* md = ap.mdl;
+  const float* lin = ap.lin;
+  const int N = ap.N;
+  const float dt = md[M_DT], mu = md[M_MU], sigma = prm.sigma;
+  const float rho = *ap.rho, rho_eq = 1e3f * rho;
+  float* rec0 = a.lL + (size_t)slot * a.maxN * LDL_REC;
+  for (int k = 0; k < N; ++k) {
+    float* rec = rec0 + (size_t)k * LDL_REC;
+    const float* cls = ap.rcls + k * RS;
+    for (int t = lane; t < NB * SLD; t += 32) S[t] = 0.f;
+    __syncwarp();
+    // ---- assembly of M_k (the u_k block carries the Schur complement of
+    // the stage's inequality pivots: rho C_u^T C_u, the x_{k+1} block rho C_x^T C_x)
+    if (lane < 30) {
+      const int i = lane;
+      S[i * SLD + i] = 2.f * dt * md[M_R + i] + sigma + rho * cls[i < 12 ? i : i + 8];
+      S[(60 + i) * SLD + 60 + i] = 2.f * dt * md[M_Q + i] + sigma + (i >= 12 ? rho * cls[i + 26] : 0.f);
+      S[(60 + i) * SLD + 30 + i] = 1.f;
+      float* Sl = S + (30 + i) * SLD;
+      for (int c = 0; c < 30; ++c) Sl[c] = -b_entry(lin, dt, i, c);
+      for (int c = 0; c <= i; ++c) Sl[30 + c] = (c == i ? -1.f / rho_eq : 0.f) - (k ? M[i * 31 + c] : 0.f);
+    }
+    __syncwarp();
+    if (lane < 2) {
+      const int f = lane, b0 = 6 * f, p = 12 + 4 * f;
+      const float r0 = rho * cls[p], r1 = rho * cls[p + 1], r2 = rho * cls[p + 2], r3 = rho * cls[p + 3];
+      S[b0 * SLD + b0] += r0 + r1;
+      S[(b0 + 1) * SLD + b0 + 1] += r2 + r3;
+      S[(b0 + 2) * SLD + b0 + 2] += mu * mu * (r0 + r1 + r2 + r3);
+      S[(b0 + 2) * SLD + b0] += mu * (r1 - r0);
+      S[(b0 + 2) * SLD + b0 + 1] += mu * (r3 - r2);
+    }
+    __syncwarp();
+    // ---- dense LDL^T, right-looking, no pivoting; lane owns rows lane,
+    // lane + 32, lane + 64; the trailing update walks the columns in chunks of
+    // eight (independent shared-memory loads, then the updates, then stores)
+    for (int j = 0; j < NB; ++j) {
+      const float id = 1.f / S[j * SLD + j];
+      float l[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const int i = lane + 32 * m;
+        const bool own = i > j && i < NB;
+        const float t = own ? S[i * SLD + j] : 0.f;
+        if (own) v[i] = t;
+        l[m] = t * id;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const int i = lane + 32 * m;
+        if (i > j && i < NB) S[i * SLD + j] = l[m];
+      }
+      for (int c0 = j + 1; c0 < NB; c0 += 8) {
+        float vv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) vv[q] = v[min(c0 + q, NB - 1)];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) {
+          const int i = lane + 32 * m;
+          if (i < NB && i >= c0) {
+            float* Si = S + i * SLD + c0;
+            float sv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) sv[q] = c0 + q <= i ? Si[q] : 0.f;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+              if (c0 + q <= i) Si[q] = fmaf(-l[m], vv[q], sv[q]);
+          }
+        }
+      }
+      __syncwarp();
+    }
+    // ---- factors to global memory: L by columns and by rows, 1/D
+    for (int j = 0; j < NB - 1; ++j)
+      for (int i = j + 1 + lane; i < NB; i += 32) rec[LDL_COL + col_off(j) + i - j - 1] = S[i * SLD + j];
+    for (int i = 1; i < NB; ++i)
+      for (int j = lane; j < i; j += 32) rec[LDL_ROW + row_off(i) + j] = S[i * SLD + j];
+    for (int j = lane; j < NB; j += 32) rec[LDL_IND + j] = 1.f / S[j * SLD + j];
+    // ---- coupling to the next block: Y = A_{k+1} L_xx^-T (lane r: row r),
+    // G_{k+1} = Y D_xx^-1, and the update Y D_xx^-1 Y^T of its multiplier block
+    if (k + 1 < N) {
+      // rows of A_{k+1} into Y, then lane r solves its row in place
+      for (int t = lane; t < 900; t += 32) {
+        const int r = t / 30, c = t - 30 * r;
+        Y[r * 31 + c] = a_entry(lin, k + 1, r, c);
+      }
+      if (lane < 30) v[lane] = 1.f / S[(60 + lane) * SLD + 60 + lane];   // 1/D of x_{k+1}
+      __syncwarp();
+      if (lane < 30) {
+        float* y = Y + lane * 31;
+        for (int i = 1; i < 30; ++i) {
+          const float* Li = S + (60 + i) * SLD + 60;
+          float s = y[i];
+          for (int c = 0; c < i; ++c) s = fmaf(-Li[c], y[c], s);
+          y[i] = s;
+        }
+      }
+      __syncwarp();
+      float* G = rec0 + (size_t)(k + 1) * LDL_REC + LDL_G;
+      for (int t = lane; t < 900; t += 32) {
+        const int r = t / 30, c = t - 30 * r;
+        G[t] = Y[r * 31 + c] * v[c];
+      }
+      if (lane < 30) {
+        const int r = lane;
+        for (int s2 = 0; s2 < 30; ++s2) {
+          float acc = 0.f;
+#pragma unroll 6
+          for (int c = 0; c < 30; ++c) acc = fmaf(Y[r * 31 + c] * v[c], Y[s2 * 31 + c], acc);
+          M[r * 31 + s2] = acc;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// ------------------------------------------------------------------ solves
+// Unit lower solve L w = b of one block, L by columns (shared memory); the
+// lane holds entries lane, lane + 32, lane + 64 (< 90) in e0, e1, e2.
+__device__ __forceinline__ void fwd_sub(const float* Lc, float& e0, float& e1, float& e2, int lane) {
+#pragma unroll
+  for (int j = 0; j < NB - 1; ++j) {
+    const int o = col_off(j) - j - 1;             // L(i, j) at o + i, i > j
+    const float wj = j < 32 ? __shfl_sync(FULL, e0, j) : (j < 64 ? __shfl_sync(FULL, e1, j - 32)
+                                                                 : __shfl_sync(FULL, e2, j - 64));
+    if (lane > j) e0 = fmaf(-Lc[o + lane], wj, e0);
+    if (lane + 32 > j) e1 = fmaf(-Lc[o + lane + 32], wj, e1);
+    if (lane + 64 > j && lane < NB - 64) e2 = fmaf(-Lc[o + lane + 64], wj, e2);
+  }
+}
+// Unit upper solve L^T v = w of one block, L by rows (shared memory).
+__device__ __forceinline__ void bwd_sub(const float* Lr, float& e0, float& e1, float& e2, int lane) {
+#pragma unroll
+  for (int j = NB - 1; j >= 1; --j) {
+    const int o = row_off(j);                     // L(j, i) at o + i, i < j
+    const float vj = j < 32 ? __shfl_sync(FULL, e0, j) : (j < 64 ? __shfl_sync(FULL, e1, j - 32)
+                                                                 : __shfl_sync(FULL, e2, j - 64));
+    if (lane < j) e0 = fmaf(-Lr[o + lane], vj, e0);
+    if (lane + 32 < j) e1 = fmaf(-Lr[o + lane + 32], vj, e1);
+    if (lane + 64 < j) e2 = fmaf(-Lr[o + lane + 64], vj, e2);
+  }
+}
+
+// Staging of the factors: the iterations walk the stages forward (item
+// t = k: L_k by columns and G_k) and backward (item t = 2N-1-k: L_k by rows,
+// 1/D_k and G_{k+1}); each item is copied into one of two shared-memory
+// buffers by bulk copies (completion on the buffer's mbarrier) while the
+// previous item computes.  A wait gives up after `limit` polls: the warp then
+// issues nothing more, waits (bounded) for the copies in flight and ends the
+// agent's solve with MPC_AGENT_TIMEOUT.
+constexpr int BUF_L = 0, BUF_G = 4008, BUF_D = 4908, BUF_FLOATS = 5004;
+struct Stager {
+  float* buf[2];
+  uint64_t* bar;      // two mbarriers
+  uint32_t phase;     // bit b: parity of buffer b's next completion
+  uint32_t pending;   // bit b: a copy into buffer b not yet waited for
+  bool dead;
+  int limit;
+};
+__device__ __forceinline__ void stage_issue(Stager& sg, int b, const float* rec0, int N, int t, int lane) {
+  if (sg.dead) return;
+  __syncwarp();   // every lane is done with the buffer's previous contents
+  if (lane == 0) {
+    const bool fwd = t < N;
+    const int k = fwd ? t : 2 * N - 1 - t;
+    const float* rec = rec0 + (size_t)k * LDL_REC;
+    const bool g = fwd ? k >= 1 : k + 1 < N;
+    const float* gsrc = fwd ? rec + LDL_G : rec + LDL_REC + LDL_G;   // G_k or G_{k+1}
+    const uint32_t bl = 4008 * 4, bg = 900 * 4, bd = 96 * 4;
+    mbar_expect_tx(sg.bar + b, bl + (g ? bg : 0) + (fwd ? 0 : bd));
+    tma_load_1d(sg.buf[b] + BUF_L, rec + (fwd ? LDL_COL : LDL_ROW), bl, sg.bar + b);
+    if (g) tma_load_1d(sg.buf[b] + BUF_G, gsrc, bg, sg.bar + b);
+    if (!fwd) tma_load_1d(sg.buf[b] + BUF_D, rec + LDL_IND, bd, sg.bar + b);
+  }
+  sg.pending |= 1u << b;
+}
+__device__ __forceinline__ void stage_wait(Stager& sg, int b) {
+  if (sg.dead) return;
+  if (!__all_sync(FULL, mbar_wait(sg.bar + b, (sg.phase >> b) & 1u, sg.limit))) {
+    sg.dead = true;
+    return;
+  }
+  sg.phase ^= 1u << b;
+  sg.pending &= ~(1u << b);
+}
+__device__ __forceinline__ void stage_drain(Stager& sg) {
+  for (int b = 0; b < 2; ++b)
+    if (sg.pending & (1u << b)) mbar_wait(sg.bar + b, (sg.phase >> b) & 1u, sg.limit);
+  sg.pending = 0;
+  __syncwarp();
+}
+
+struct LdlRes { float rp, rd, sp, sd; };
+
+// OSQP's residuals of the iterate: primal |A x - z|, dual |P x + q + A^T y|
+// (inf-norms) and their scales max(|A x|, |z|), max(|P x|, |A^T y|, |q|)
+__device__ LdlRes ldl_residuals(const AgentPtrs& ap, const float* ly, float* xv, int lane) {
+  const int N = ap.N;
+  const float* md = ap.mdl;
+  const float* lin = ap.lin;
+  const float dt = md[M_DT], mu = md[M_MU];
+  LdlRes r{0.f, 0.f, 0.f, 0.f};
+  float* U = xv;          // u_k
+  float* X = xv + 32;     // x_{k+1}
+  for (int k = 0; k < N; ++k) {
+    U[lane] = ap.u[k * VS + lane];
+    X[lane] = ap.x[(k + 1) * VS + lane];
+    __syncwarp();
+    if (lane < 30) {
+      const int i = lane;
+      // dynamics row i: x_{k+1} - A_k x_k - B u_k - c_k
+      float ax = 0.f, bu = 0.f;
+      for (int c = 0; c < 30; ++c) {
+        ax = fmaf(a_entry(lin, k, i, c), ap.x[k * VS + c], ax);
+        bu = fmaf(b_entry(lin, dt, i, c), U[c], bu);
+      }
+      // the row's A x and z in OSQP's terms (x_0 is data: at k = 0 its term
+      // belongs to z)
+      const float ck = i < NC ? lin[L_STAGE + k * 64 + 32 + i] : 0.f;
+      const float axr = k ? X[i] - ax - bu : X[i] - bu;
+      const float zr = k ? ck : ck + ax;
+      r.rp = fmaxf(r.rp, fabsf(axr - zr));
+      r.sp = fmaxf(r.sp, fmaxf(fabsf(axr), fabsf(zr)));
+      // stationarity of u_k and x_{k+1}
+      const float yk = ly[k * VS + i];
+      float gu = 2.f * dt * md[M_R + i] * U[i], qu = -2.f * dt * md[M_R + i] * ap.uref[k * VS + i];
+      float gx = 2.f * dt * md[M_Q + i] * X[i], qx = -2.f * dt * md[M_Q + i] * ap.xref[(k + 1) * VS + i];
+      float atu = 0.f, atx = yk;
+      for (int c = 0; c < 30; ++c) atu = fmaf(-b_entry(lin, dt, c, i), ly[k * VS + c], atu);
+      if (k + 1 < N)
+        for (int c = 0; c < 30; ++c) atx = fmaf(-a_entry(lin, k + 1, c, i), ly[(k + 1) * VS + c], atx);
+      const float* cls = ap.rcls + k * RS;
+      const float* yy = ap.y + k * RS;
+      const int ru = i < 12 ? i : i + 8;
+      if (cls[ru] > 0.f) atu += yy[ru];
+      if (i < 12 && (i % 6) < 3) {
+        const int f = i / 6, c = i - 6 * f, p = 12 + 4 * f;
+        for (int t = 0; t < 4; ++t)
+          if (cls[p + t] > 0.f) atu = fmaf(pyr_coef(c, t, mu), yy[p + t], atu);
+      }
+      if (i >= 12 && cls[i + 26] > 0.f) atx += yy[i + 26];
+      r.rd = fmaxf(r.rd, fmaxf(fabsf(gu + qu + atu), fabsf(gx + qx + atx)));
+      r.sd = fmaxf(r.sd, fmaxf(fmaxf(fabsf(gu), fabsf(gx)), fmaxf(fmaxf(fabsf(atu), fabsf(atx)),
+                                                                   fmaxf(fabsf(qu), fabsf(qx)))));
+    }
+    // inequality rows
+    for (int h = 0; h < 2; ++h) {
+      const int rr = lane + 32 * h;
+      if (rr < NR && ap.rcls[k * RS + rr] > 0.f) {
+        const float cz = row_value(rr, U, X, mu), z = ap.w[k * RS + rr];
+        r.rp = fmaxf(r.rp, fabsf(cz - z));
+        r.sp = fmaxf(r.sp, fmaxf(fabsf(cz), fabsf(z)));
+      }
+    }
+    __syncwarp();
+  }
+  r.rp = warp_max(r.rp); r.rd = warp_max(r.rd); r.sp = warp_max(r.sp); r.sd = warp_max(r.sd);
+  return r;
+}
+
+// ------------------------------------------------------------------ iterations
+// Per-lane global inputs of one stage (lane i < 30: u_i, dynamics row i,
+// x_i), loaded one stage ahead of their use.  Forward pass: the iterate, the
+// references, the affine term, the dynamics multiplier, and the slack,
+// multiplier and class of every inequality row on u_i (its box row, and for a
+// force input the foot's four pyramid rows with their coefficients) and on
+// x_i (the joint box).
+struct FIn {
+  float u, ur, x, xr, yl, ck;
+  float cr, zr, yr;             // box row of u_i
+  float cq, zq, yq;             // joint box of x_i
+  float cp[4], zp[4], yp[4], kp[4];
+};
+__device__ __forceinline__ FIn load_fin(const AgentPtrs& ap, const float* ly, int k, int lane) {
+  FIn f;
+  f.u = f.ur = f.x = f.xr = f.yl = f.ck = 0.f;
+  f.cr = f.zr = f.yr = f.cq = f.zq = f.yq = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) f.cp[q] = f.zp[q] = f.yp[q] = f.kp[q] = 0.f;
+  if (lane < 30) {
+    const int i = lane;
+    const float* cls = ap.rcls + k * RS;
+    const float* zz = ap.w + k * RS;
+    const float* yy = ap.y + k * RS;
+    f.u = ap.u[k * VS + i];
+    f.ur = ap.uref[k * VS + i];
+    f.x = ap.x[(k + 1) * VS + i];
+    f.xr = ap.xref[(k + 1) * VS + i];
+    f.yl = ly[k * VS + i];
+    f.ck = i < NC ? ap.lin[L_STAGE + k * 64 + 32 + i] : 0.f;
+    const int ru = i < 12 ? i : i + 8;
+    f.cr = cls[ru]; f.zr = zz[ru]; f.yr = yy[ru];
+    if (i >= 12) { f.cq = cls[i + 26]; f.zq = zz[i + 26]; f.yq = yy[i + 26]; }
+    if (i < 12 && (i % 6) < 3) {
+      const int ff = i / 6, c = i - 6 * ff, p = 12 + 4 * ff;
+      const float mu = ap.mdl[M_MU];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        f.cp[q] = cls[p + q]; f.zp[q] = zz[p + q]; f.yp[q] = yy[p + q]; f.kp[q] = pyr_coef(c, q, mu);
+      }
+    }
+  }
+  return f;
+}
+// Backward pass: the forward vector w_k, the iterate, the dynamics
+// multiplier, and slack, multiplier, class and bounds of rows lane and lane + 32.
+struct BIn {
+  float w0, w1, w2, u, x, yl;
+  float c0, z0, y0, lo0, hi0, c1, z1, y1, lo1, hi1;
+};
+__device__ __forceinline__ BIn load_bin(const AgentPtrs& ap, const float* ly, const float* lw, int k, int lane) {
+  BIn b;
+  b.w0 = lw[k * LDL_W + lane];
+  b.w1 = lw[k * LDL_W + lane + 32];
+  b.w2 = lane < NB - 64 ? lw[k * LDL_W + lane + 64] : 0.f;
+  b.u = ap.u[k * VS + lane];
+  b.x = ap.x[(k + 1) * VS + lane];
+  b.yl = ly[k * VS + lane];
+  const int r0 = lane, r1 = lane + 32;
+  b.c0 = ap.rcls[k * RS + r0]; b.z0 = ap.w[k * RS + r0]; b.y0 = ap.y[k * RS + r0];
+  b.lo0 = ap.rlo[k * RS + r0]; b.hi0 = ap.rhi[k * RS + r0];
+  if (r1 < NR) {
+    b.c1 = ap.rcls[k * RS + r1]; b.z1 = ap.w[k * RS + r1]; b.y1 = ap.y[k * RS + r1];
+    b.lo1 = ap.rlo[k * RS + r1]; b.hi1 = ap.rhi[k * RS + r1];
+  } else {
+    b.c1 = b.z1 = b.y1 = b.lo1 = b.hi1 = 0.f;
+  }
+  return b;
+}
+
+constexpr int W_ADMM = 2 * BUF_FLOATS + 96 + 64 + 32 + 4;   // shared floats of the one warp of a block
+__global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverParams prm) {
+  const int lane = threadIdx.x;
+  const int row = blockIdx.x;
+  if (!live_row(a, b, row)) return;
+  const int slot = b.ids[row];
+  const AgentPtrs ap = agent_ptrs(a, slot);
+  if (ap.st[T_STATUS] == MPC_AGENT_NAN_) return;
+  extern __shared__ __align__(16) float asm_[];
+  float* rb = asm_ + 2 * BUF_FLOATS;    // the stage's 90-vector, by block index
+  float* xv = rb + 96;                  // residual scratch (u_k, x_{k+1})
+  float* cv = xv + 64;                  // coupling vector: x part of w_{k-1} / multiplier part of v_{k+1}
+  Stager sg;
+  sg.buf[0] = asm_;
+  sg.buf[1] = asm_ + BUF_FLOATS;
+  sg.bar = reinterpret_cast<uint64_t*>(cv + 32);
+  sg.phase = 0u; sg.pending = 0u; sg.dead = false;
+  sg.limit = prm.spin_limit > 0 ? prm.spin_limit : kSpinLimit;
+  if (lane == 0) {
+    mbar_init(sg.bar, 1);
+    mbar_init(sg.bar + 1, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  const float* md = ap.mdl;
+  const float* lin = ap.lin;
+  const int N = ap.N;
+  const float dt = md[M_DT], mu = md[M_MU];
+  const float sigma = prm.sigma, alpha = prm.alpha;
+  const float rho = *ap.rho, rho_eq = 1e3f * rho;
+  const float* rec0 = a.lL + (size_t)slot * a.maxN * LDL_REC;
+  float* lw = a.lw + (size_t)slot * a.maxN * LDL_W;
+  float* ly = a.ly + (size_t)slot * a.maxN * VS;
+  const int i = lane;   // lanes 0-29: u_i, dynamics row i, x_i of each stage
+  const float Ru = lane < 30 ? 2.f * dt * md[M_R + i] : 0.f;
+  const float Qx = lane < 30 ? 2.f * dt * md[M_Q + i] : 0.f;
+  // dynamics rows of stage 0: x_1 - B u_0 = c_0 + A_0 x0
+  float a0x0 = 0.f;
+  if (lane < 30)
+    for (int c = 0; c < 30; ++c) a0x0 = fmaf(a_entry(lin, 0, i, c), ap.inp[I_X0 + c], a0x0);
+  for (int k = 0; k < N; ++k) ly[k * VS + lane] = 0.f;
+  __syncwarp();
+  const bool fixed = prm.fixed_iters > 0;
+  const int max_it = fixed ? prm.fixed_iters : prm.max_iter;
+  const int every = prm.check_every > 0 ? prm.check_every : 10;
+  int status = MPC_AGENT_MAX_ITER_, it = 0;
+  LdlRes res{0.f, 0.f, 0.f, 0.f};
+  const int T = 2 * N;                 // staged items per iteration
+  stage_issue(sg, 0, rec0, N, 0, lane);
+  for (it = 1; it <= max_it && !sg.dead; ++it) {
+    const bool last = it == max_it;
+    // ---- forward pass: b_k (+ G_k w_{k-1,x}), w_k = L_k^-1 b_k; the
+    // stage's global inputs are loaded one stage ahead
+    FIn fin = load_fin(ap, ly, 0, lane);
+    for (int k = 0; k < N; ++k) {
+      const int t = k, bcur = t & 1;
+      stage_issue(sg, bcur ^ 1, rec0, N, t + 1, lane);
+      const FIn f = fin;
+      if (k + 1 < N) fin = load_fin(ap, ly, k + 1, lane);
+      float bu = 0.f, bl = 0.f, bx = 0.f;
+      if (lane < 30) {
+        bu = sigma * f.u + Ru * f.ur;
+        if (f.cr > 0.f) bu += rho * f.cr * f.zr - f.yr;
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (f.cp[q] > 0.f) bu = fmaf(f.kp[q], rho * f.cp[q] * f.zp[q] - f.yp[q], bu);
+        bl = f.ck + (k ? 0.f : a0x0) - f.yl / rho_eq;
+        bx = sigma * f.x + Qx * f.xr;
+        if (f.cq > 0.f) bx += rho * f.cq * f.zq - f.yq;
+      }
+      stage_wait(sg, bcur);
+      if (sg.dead) break;
+      const float* buf = sg.buf[bcur];
+      if (lane < 30) {
+        if (k) {
+          const float* g = buf + BUF_G + i * 30;
+          for (int c = 0; c < 30; ++c) bl = fmaf(g[c], cv[c], bl);
+        }
+        rb[i] = bu;
+        rb[30 + i] = bl;
+        rb[60 + i] = bx;
+      }
+      __syncwarp();
+      float e0 = rb[lane], e1 = rb[lane + 32], e2 = lane < NB - 64 ? rb[lane + 64] : 0.f;
+      fwd_sub(buf + BUF_L, e0, e1, e2, lane);
+      lw[k * LDL_W + lane] = e0;
+      lw[k * LDL_W + lane + 32] = e1;
+      if (lane < NB - 64) lw[k * LDL_W + lane + 64] = e2;
+      __syncwarp();
+      // x part of w_k for the next stage's coupling (entries 60-89)
+      if (lane >= 28) cv[lane - 28] = e1;
+      if (lane < NB - 64) cv[lane + 4] = e2;
+      __syncwarp();
+    }
+    if (sg.dead) break;
+    // ---- backward pass: v_k = L_k^-T (D_k^-1 w_k + G_{k+1}^T v_{k+1,mult}),
+    // then the stage's update; inputs one stage ahead
+    BIn bin = load_bin(ap, ly, lw, N - 1, lane);
+    for (int k = N - 1; k >= 0; --k) {
+      const int t = 2 * N - 1 - k, bcur = t & 1;
+      // the next item: this iteration's next stage, or the next iteration's first
+      if (t + 1 < T) stage_issue(sg, bcur ^ 1, rec0, N, t + 1, lane);
+      else if (!last) stage_issue(sg, bcur ^ 1, rec0, N, 0, lane);
+      const BIn q = bin;
+      if (k >= 1) bin = load_bin(ap, ly, lw, k - 1, lane);
+      stage_wait(sg, bcur);
+      if (sg.dead) break;
+      const float* buf = sg.buf[bcur];
+      const float* iD = buf + BUF_D;
+      rb[lane] = q.w0 * iD[lane];
+      rb[lane + 32] = q.w1 * iD[lane + 32];
+      if (lane < NB - 64) rb[lane + 64] = q.w2 * iD[lane + 64];
+      __syncwarp();
+      if (k + 1 < N && lane < 30) {
+        const float* g = buf + BUF_G;
+        float s = 0.f;
+        for (int r = 0; r < 30; ++r) s = fmaf(g[r * 30 + i], cv[r], s);
+        rb[60 + i] += s;
+      }
+      __syncwarp();
+      float e0 = rb[lane], e1 = rb[lane + 32], e2 = lane < NB - 64 ? rb[lane + 64] : 0.f;
+      bwd_sub(buf + BUF_L, e0, e1, e2, lane);
+      __syncwarp();
+      rb[lane] = e0;
+      rb[lane + 32] = e1;
+      if (lane < NB - 64) rb[lane + 64] = e2;
+      __syncwarp();
+      // rb = (x~ of u_k, nu of the dynamics rows, x~ of x_{k+1})
+      if (lane < 30) {
+        const float nu = rb[30 + i];
+        cv[i] = nu;
+        ap.u[k * VS + i] = alpha * rb[i] + (1.f - alpha) * q.u;
+        ap.x[(k + 1) * VS + i] = alpha * rb[60 + i] + (1.f - alpha) * q.x;
+        // dynamics rows (z = l = u always): zr - z = alpha (nu - y) / rho_eq
+        ly[k * VS + i] = (1.f - alpha) * q.yl + alpha * nu;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int rr = lane + 32 * h;
+        const float cl = h ? q.c1 : q.c0;
+        if (rr < NR && cl > 0.f) {
+          const float rr_rho = rho * cl;
+          const float zt = row_value(rr, rb, rb + 60, mu);
+          const float zo = h ? q.z1 : q.z0, yo = h ? q.y1 : q.y0;
+          const float zh = alpha * zt + (1.f - alpha) * zo;
+          const float zn = fminf(fmaxf(zh + yo / rr_rho, h ? q.lo1 : q.lo0), h ? q.hi1 : q.hi0);
+          ap.y[k * RS + rr] = yo + rr_rho * (zh - zn);
+          ap.w[k * RS + rr] = zn;
+        }
+      }
+      __syncwarp();
+    }
+    if (sg.dead) break;
+    const bool check = !fixed && (it % every == 0 || last);
+    if (check || (fixed && last)) {
+      res = ldl_residuals(ap, ly, xv, lane);
+      if (!(isfinite(res.rp) && isfinite(res.rd))) { status = MPC_AGENT_NAN_; break; }
+      if (check && res.rp <= prm.eps_abs + prm.eps_rel * res.sp && res.rd <= prm.eps_abs + prm.eps_rel * res.sd) {
+        status = MPC_AGENT_INACCURATE_;   // ADMM's stopping test, no polish: not certified
+        break;
+      }
+    }
+  }
+  if (it > max_it) it = max_it;
+  if (sg.dead) {
+    status = MPC_AGENT_TIMEOUT_;
+    if (lane == 0) atomicAdd(a.fault + F_WAIT_TIMEOUTS, 1);
+  }
+  // copies issued for an iteration that did not run (a stop after a check)
+  stage_drain(sg);
+  // a non-finite iterate leaves no torques
+  bool bad = false;
+  for (int k = 0; k <= N; ++k) bad |= lane < 30 && !isfinite(ap.x[k * VS + lane]);
+  for (int k = 0; k < N; ++k) bad |= lane < 30 && !isfinite(ap.u[k * VS + lane]);
+  if (warp_or(bad) && status != MPC_AGENT_TIMEOUT_) status = MPC_AGENT_NAN_;
+  if (lane == 0) {
+    ap.st[T_STATUS] = status;
+    ap.st[T_ITERS] = it;
+    ap.st[T_REFAC] = 0;
+    ap.st[T_POLISHED] = 0;
+    ap.st[T_ATTEMPTS] = 0;
+    ap.out[O_PRIM] = res.rp;
+    ap.out[O_DUAL] = res.rd;
+    ap.out[O_PRIM_N] = 0.f;
+    ap.out[O_DUAL_N] = 0.f;
+    *ap.warm = 0;   // every solve of this form starts from f_init
+  }
+}
+
+}  // namespace
+
+size_t ldl_factor_smem_bytes() { return F_FLOATS * sizeof(float); }
+
+cudaError_t launch_ldl(const Arena& a, const Batch& b, const SolverParams& prm, cudaStream_t st, int* launches) {
+  static int configured = -1;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (configured != dev) {
+    cudaError_t e = cudaFuncSetAttribute(mpc_k_ldl_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(F_FLOATS * sizeof(float)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mpc_k_ldl_admm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(W_ADMM * sizeof(float)));
+    // both kernels are one warp with about 40 KB of shared memory: ask for the
+    // largest shared-memory carveout, so that five of them fit on an SM
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mpc_k_ldl_factor, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mpc_k_ldl_admm, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    configured = dev;
+  }
+  if (b.n <= 0) return cudaSuccess;
+  mpc_k_ldl_factor<<<b.n, 32, F_FLOATS * sizeof(float), st>>>(a, b, prm);
+  mpc_k_ldl_admm<<<b.n, 32, W_ADMM * sizeof(float), st>>>(a, b, prm);
+  if (launches) *launches += 2;
+  return cudaGetLastError();
+}
+
+}  // namespace mpc

@@ -19,7 +19,8 @@ constexpr int MPC_AGENT_INACCURATE_ = 6;
 size_t smem_bytes_per_block();
 
 // Enqueue the whole hot path for a batch.  form 0 = plain (five step
-// kernels), 1 = fused (one kernel; grid_fused > 0 caps its grid).  variant:
+// kernels), 1 = fused (one kernel; grid_fused > 0 caps its grid), 2 =
+// literal (set-up, block LDL^T factor, OSQP iterations, torque map).  variant:
 // register cap of the solver kernels, 1 = 2 blocks/SM, 2 = 3 blocks/SM.
 // *launches is incremented by the number of kernels enqueued.
 cudaError_t launch_solve(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
@@ -28,6 +29,11 @@ cudaError_t launch_solve(const Arena& a, const Batch& b, const SolverParams& prm
 template <int MINB>
 cudaError_t launch_variant(const Arena& a, const Batch& b, const SolverParams& prm, int form, int grid_fused,
                            cudaStream_t st, int* launches);
+
+// Literal form (MPC_FORM_LDL): the block LDL^T factor of the full KKT system
+// and the OSQP iterations on it (ldl.cu), between the set-up kernel and the
+// torque map.
+cudaError_t launch_ldl(const Arena& a, const Batch& b, const SolverParams& prm, cudaStream_t st, int* launches);
 
 cudaError_t launch_gather(const Arena& a, int n, const int* ids, float* tau, float* qset, float* qdset,
                           float* value, int* status, cudaStream_t st);

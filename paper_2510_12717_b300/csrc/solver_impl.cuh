@@ -2534,6 +2534,14 @@ cudaError_t launch_prec(const Arena& a, const Batch& b, const SolverParams& prm,
       mpc_k_torque<<<blocks, thr, 0, st>>>(a, b);
       if (launches) *launches += 1;
     }
+  } else if (form == 2) {
+    // the paper's literal solve: f_init / f_param / linearisation, then the
+    // KKT system's block LDL^T and the OSQP iterations on it, then the torque map
+    mpc_k_setup_lean<<<blocks, thr, WARPS_PER_BLOCK * W_SETUP * sizeof(float), st>>>(a, b, prm);
+    cudaError_t e = launch_ldl(a, b, prm, st, launches);
+    if (e != cudaSuccess) return e;
+    mpc_k_torque<<<blocks, thr, 0, st>>>(a, b);
+    if (launches) *launches += 2;
   } else {
     mpc_k_setup<MINB><<<blocks, thr, smem, st>>>(a, b, prm);
     mpc_k_factor<MINB, PREC><<<blocks, thr, smem, st>>>(a, b, prm);

@@ -19,7 +19,7 @@ MPC_OK, MPC_ERR_INVALID, MPC_ERR_BUDGET, MPC_ERR_CUDA = 0, 1, 2, 3
 MPC_ERR_NOT_READY, MPC_ERR_TIMEOUT, MPC_ERR_STATE = 4, 5, 6
 AGENT_SOLVED, AGENT_MAX_ITER, AGENT_PRIMAL_INFEAS, AGENT_DUAL_INFEAS, AGENT_NAN, AGENT_TIMEOUT = 0, 1, 2, 3, 4, 5
 AGENT_INACCURATE = 6
-FORM_PLAIN, FORM_FUSED = 0, 1
+FORM_PLAIN, FORM_FUSED, FORM_LDL = 0, 1, 2
 FP32, TF32, BF16, FP64, TF32X3 = 0, 1, 2, 3, 4
 PEAK_FP32_FMA, PEAK_FP64_FMA, PEAK_TF32_MMA_SYNC, PEAK_BF16_MMA_SYNC = 0, 1, 2, 3
 

@@ -97,3 +97,10 @@ def test_pack_models_roundtrip():
     assert np.array_equal(recs["N"], m["N"])
     assert np.array_equal(recs["J_leg"], m["J_leg"])
     assert np.array_equal(recs["duty"], m["duty"])
+
+
+def test_form_values_match_header():
+    from paper_2510_12717_b300 import mpcgpu
+    src = open(HEADER).read()
+    m = re.search(r"MPC_FORM_PLAIN = (\d+), MPC_FORM_FUSED = (\d+), MPC_FORM_LDL = (\d+)", src)
+    assert m and tuple(int(v) for v in m.groups()) == (mpcgpu.FORM_PLAIN, mpcgpu.FORM_FUSED, mpcgpu.FORM_LDL)

@@ -1,0 +1,150 @@
+"""Parity of the literal form (MPC_FORM_LDL: the paper's Alg. 1 with OSQP's
+ADMM on the full KKT system of Eq. kkt_system, factored once by a block
+LDL^T, Eq. ldl, and solved by substitution every iteration, Eqs.
+backsolve_1-2) against the oracle's literal iteration (oracle/osqp.py: the
+same algorithm with a dense FP64 LU solve of the KKT system).
+
+The literal iteration is compared iterate for iterate: after a fixed number
+of iterations N_QP from f_init both sides hold the same ADMM iterate, not the
+QP's optimum (the paper's fixed-N_QP mode).  Bars: torques within the
+spec tolerance (1e-4 N m + 1e-3 |tau|); the primal iterate within 1e-4
+of its own scale (FP32 factors of a KKT matrix with entries from 1e-2 to
+1e3: measured 1e-6); in the converged mode the iteration count within one
+residual-check period of the oracle's, where the stopping test is met by a
+margin FP32 can resolve.
+"""
+import numpy as np
+import pytest
+
+from helpers import agents, device_inputs, oracle_view, torque_close
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2510_12717_b300 import mpcgpu
+    return mpcgpu
+
+
+def _solve(mpcgpu, model, inp32, **opts):
+    n = len(model["mass"])
+    s = mpcgpu.Solver(max_agents=n, max_horizon=20, form=mpcgpu.FORM_LDL,
+                      stream=torch.cuda.current_stream().cuda_stream, **opts)
+    s.set_models(model, np.arange(n))
+    r = s.solve_host(np.arange(n), inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+    r["state"] = [s.export_state(a, int(model["N"][a])) for a in range(n)]
+    r["stats"] = s.agent_stats(np.arange(n))
+    s.close()
+    return r
+
+
+def _oracle(model, inp32, a, iters):
+    from oracle import osqp
+    from oracle.solve import agent_params
+    mo, io = oracle_view(model, inp32)
+    m = agent_params(mo, a)
+    return osqp.literal_agent(m, io["x0"][a], io["cmd"][a], io["phase"][a], io["qd_meas"][a], iters)
+
+
+@pytest.mark.parametrize("name,n", [("small", 16), ("uneven", 10)])
+@pytest.mark.parametrize("iters", [1, 25])
+def test_literal_iterations_match_oracle(name, n, iters):
+    mpcgpu = _lib()
+    model, inp = agents(name, np.arange(n))
+    inp32 = device_inputs(inp)
+    r = _solve(mpcgpu, model, inp32, fixed_iters=iters)
+    assert (r["status"] == mpcgpu.AGENT_MAX_ITER).all()
+    assert (r["stats"]["iters"] == iters).all()
+    for a in range(n):
+        o = _oracle(model, inp32, a, iters)
+        st = r["state"][a]
+        su = 1.0 + np.abs(o["u"]).max()
+        sx = 1.0 + np.abs(o["x"]).max()
+        assert np.abs(st["u"] - o["u"]).max() <= 1e-4 * su, a
+        assert np.abs(st["x"] - o["x"]).max() <= 1e-4 * sx, a
+        ok = torque_close(r["tau"][a], o["tau"])
+        assert ok.all(), (a, np.abs(r["tau"][a] - o["tau"]).max())
+
+
+def test_literal_converged_mode_counts_oracle_iterations():
+    from oracle import osqp, qp as qpmod
+    from oracle.solve import agent_params
+    mpcgpu = _lib()
+    model, inp = agents("small", np.arange(16))
+    inp32 = device_inputs(inp)
+    r = _solve(mpcgpu, model, inp32, fixed_iters=0, max_iter=4000, check_every=10)
+    mo, io = oracle_view(model, inp32)
+    matched = 0
+    for a in range(16):
+        m = agent_params(mo, a)
+        qp, _ = qpmod.agent_qp(m, io["x0"][a], io["cmd"][a], io["phase"][a])
+        lq = osqp.literal_form(qp, 0.1)
+        x, z, y = osqp.start_point(lq, qp, io["x0"][a], np.asarray(m["q_nom"], float))
+        x, z, y, it = osqp.solve_until(lq, x, z, y, max_iter=4000, check_every=10)
+        got = int(r["stats"]["iters"][a])
+        if it < 1000:
+            # short runs: the stopping test is met by a margin FP32 resolves
+            assert abs(got - it) <= 10, (a, got, it)
+            assert r["status"][a] == mpcgpu.AGENT_INACCURATE
+            matched += 1
+        else:
+            # long runs hover at the tolerance; FP32 may stop a few checks apart
+            assert abs(got - it) <= 0.05 * it + 20, (a, got, it)
+    assert matched >= 10
+
+
+def test_literal_full_size_sampled():
+    # the bench configuration: 16384 agents of mixed horizons and gaits,
+    # N_QP = 25, one launch; a stratified sample against the oracle
+    mpcgpu = _lib()
+    n = 16384
+    model, inp = agents("mixed16k", np.arange(n))
+    inp32 = device_inputs(inp)
+    dev = torch.device("cuda:0")
+    t = {k: torch.from_numpy(v).to(dev) for k, v in inp32.items()}
+    ids = torch.arange(n, dtype=torch.int32, device=dev)
+    s = mpcgpu.Solver(max_agents=n, max_horizon=20, form=mpcgpu.FORM_LDL, fixed_iters=25,
+                      stream=torch.cuda.current_stream().cuda_stream)
+    s.set_models(model, np.arange(n))
+    tk = s.submit(ids, t["x0"], t["qd_meas"], t["cmd"], t["phase"])
+    s.solve(tk)
+    tau = torch.empty((n, 18), device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    s.get_torques(tk, tau=tau, status=st)
+    torch.cuda.synchronize()
+    s.close()
+    tau = tau.cpu().numpy()
+    st = st.cpu().numpy()
+    assert (st == mpcgpu.AGENT_MAX_ITER).all()
+    Nh = model["N"]
+    sample = [int(np.flatnonzero(Nh == h)[0]) for h in (5, 9, 13, 17, 20)] + [n - 1, n // 2]
+    for a in sample:
+        o = _oracle(model, inp32, a, 25)
+        ok = torque_close(tau[a], o["tau"])
+        assert ok.all(), (a, np.abs(tau[a] - o["tau"]).max())
+
+
+def test_literal_nonfinite_input_is_flagged():
+    mpcgpu = _lib()
+    model, inp = agents("small", np.arange(4))
+    inp32 = device_inputs(inp)
+    inp32["x0"][2, 7] = np.nan
+    r = _solve(mpcgpu, model, inp32, fixed_iters=5)
+    assert r["status"][2] == mpcgpu.AGENT_NAN
+    assert np.all(r["tau"][2] == 0.0)
+    assert (r["status"][[0, 1, 3]] == mpcgpu.AGENT_MAX_ITER).all()
+
+
+def test_literal_budget_counts_the_factors():
+    mpcgpu = _lib()
+    # the regular form of 256 agents fits in 64 MB; the literal form's factors
+    # (about 36 KB per stage per agent) do not
+    s = mpcgpu.Solver(max_agents=256, max_horizon=20, hbm_budget_bytes=64 << 20,
+                      stream=torch.cuda.current_stream().cuda_stream)
+    s.close()
+    with pytest.raises(mpcgpu.MpcError):
+        mpcgpu.Solver(max_agents=256, max_horizon=20, form=mpcgpu.FORM_LDL, fixed_iters=25,
+                      hbm_budget_bytes=64 << 20, stream=torch.cuda.current_stream().cuda_stream)
