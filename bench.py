@@ -70,14 +70,15 @@ HBM_PEAK_GBS, HBM_PEAK_KIND = _measured_hbm_peak()
 
 
 # Literal form (MPC_FORM_LDL): algorithmic bytes of one OSQP iteration of one
-# agent.  Per stage the forward substitution reads L_k (4005 strictly-lower
-# entries of the 90 x 90 block) and the coupling block G_k (30 x 30, stages
+# agent.  Per stage the forward substitution reads L_k (the 4005 strictly-lower
+# entries of the 90 x 90 block less the 900 of its structurally zero x-u
+# block) and the coupling block G_k (30 x 30, stages
 # k >= 1); the backward one reads L_k again, 1/D_k (90) and G_{k+1} (stages
 # k + 1 < N); the stage's iterate and row data are read and written once
 # (u_k, x_{k+1}, the dynamics multipliers: 3 x 30 read + written; the 56
 # rows' slack and multiplier read + written, bounds, classes read; the
 # references, affine term and forward vector: 3 x 30 + 90 written + read).
-LDL_L, LDL_G, LDL_D = 4005, 900, 90
+LDL_L, LDL_G, LDL_D = 3105, 900, 90
 LDL_STATE = 2 * 3 * 30 + 2 * 2 * 56 + 3 * 56 + 3 * 30 + 2 * 90
 
 

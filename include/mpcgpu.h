@@ -95,7 +95,7 @@ typedef enum { MPC_FP32 = 0, MPC_TF32 = 1, MPC_BF16 = 2, MPC_FP64 = 3, MPC_TF32X
  * fixed_iters > 0 it runs exactly that many iterations (the paper's N_QP;
  * agent_status MPC_AGENT_MAX_ITER), otherwise until OSQP's stopping test at
  * a residual check every check_every iterations (MPC_AGENT_INACCURATE: not
- * certified by a polish) or max_iter.  Its factors take about 36 KB per
+ * certified by a polish) or max_iter.  Its factors take about 29 KB per
  * stage per agent of device memory (max_agents x max_horizon stages). */
 typedef enum { MPC_FORM_PLAIN = 0, MPC_FORM_FUSED = 1, MPC_FORM_LDL = 2 } mpc_form;
 

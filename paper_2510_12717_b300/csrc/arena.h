@@ -107,11 +107,12 @@ struct Arena {
   float* ly;              // [A][maxN*VS]
 };
 // literal-form record of one stage: 90 block variables (u_k, the stage's 30
-// dynamics multipliers, x_{k+1}); strictly lower L packed by columns at
-// LDL_COL, the same entries packed by rows at LDL_ROW, 1/D at LDL_IND, the
-// 30 x 30 coupling block G_k (row-major) at LDL_G
-enum : int { LDL_NB = 90, LDL_COL = 0, LDL_ROW = 4008, LDL_IND = 8016, LDL_G = 8112, LDL_REC = 9024,
-             LDL_W = 96 };
+// dynamics multipliers, x_{k+1}); the strictly lower L without its
+// structurally zero block (the x_{k+1} rows against the u_k columns), packed
+// by columns at LDL_COL and by rows at LDL_ROW (3105 entries each), 1/D at
+// LDL_IND, the 30 x 30 coupling block G_k (row-major) at LDL_G
+enum : int { LDL_NB = 90, LDL_NL = 3105, LDL_COL = 0, LDL_ROW = 3108, LDL_IND = 6216, LDL_G = 6312,
+             LDL_REC = 7232, LDL_W = 96 };
 enum : int { F_WAIT_TIMEOUTS = 0, F_COUNT = 4 };
 
 // lin record layout: dense A_base and B (column-major, stride 23), their

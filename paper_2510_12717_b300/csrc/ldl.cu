@@ -31,11 +31,11 @@
 // without pivoting.
 //
 // Kernels (one warp per agent):
-//   mpc_k_ldl_factor : assembles and factors the blocks stage by stage in
-//                      shared memory; writes L (packed by columns for the
+//   mpc_k_ldl_factor : assembles and factors the blocks stage by stage, the
+//                      rows of its 30-wide sub-blocks in registers; writes L (packed by columns for the
 //                      forward substitution and by rows for the backward one,
 //                      so that both read coalesced), 1/D and G_k
-//   mpc_k_ldl_admm   : the iterations; per iteration a forward pass over the
+//   mpc_k_ldl_admm   : one warp runs the iterations; per iteration a forward pass over the
 //                      stages (right-hand side, coupling, unit lower solve)
 //                      and a backward pass (1/D, coupling, unit upper solve,
 //                      then the stage's relaxation, projection and dual
@@ -51,11 +51,18 @@ namespace mpc {
 namespace {
 
 constexpr int NB = LDL_NB;
-constexpr int SLD = NB + 1;                              // row stride of the block in shared memory
-constexpr int F_FLOATS = NB * SLD + 96 + 2 * 30 * 31;    // factor kernel: shared floats per warp
+constexpr int F_FLOATS = 30 * 32;                        // factor kernel: shared floats per warp
 
-__host__ __device__ constexpr int col_off(int j) { return (NB - 1) * j - j * (j - 1) / 2; }
-__host__ __device__ constexpr int row_off(int i) { return i * (i - 1) / 2; }
+// Packed strictly lower L without the zero block (rows 60-89 x columns
+// 0-29): column j holds rows j+1 .. 59 (j < 30) or j+1 .. 89; row i holds
+// columns 0 .. i-1 (i < 60) or 30 .. i-1.  L(i, j) is at col_off(j) + i - j - 1
+// by columns and at row_off(i) + j - row_skip(i) by rows.
+__host__ __device__ constexpr int col_off(int j) {
+  return j <= 30 ? 59 * j - j * (j - 1) / 2 : 1335 + 59 * (j - 30) - (j - 30) * (j - 31) / 2;
+}
+__host__ __device__ constexpr int row_off(int i) { return i <= 60 ? i * (i - 1) / 2 : 1770 + (i - 1) * (i - 60) / 2; }
+__host__ __device__ constexpr int row_skip(int i) { return i >= 60 ? 30 : 0; }
+static_assert(col_off(89) == LDL_NL && row_off(90) == LDL_NL, "packed layout size");
 
 __device__ __forceinline__ bool live_row(const Arena& a, const Batch& b, int row) {
   if (row >= b.n) return false;
@@ -98,6 +105,58 @@ __device__ __forceinline__ float row_value(int r, const float* U, const float* X
 }
 
 // ------------------------------------------------------------------ factor
+// One warp per agent; lane l (< 30) holds row l of each 30 x 30 block in
+// registers.  The stage's 90 x 90 block M_k = [[A11, ., .], [A21, A22, .],
+// [0, I, A33]] (u_k, multipliers, x_{k+1}; A11 = R_t with the pyramid
+// couplings, A21 = -B, A22 = -rho_eq^-1 I - A_k X_{k-1} A_k^T, A33 = Q_t) is
+// factored as a supernodal LDL^T over its three 30-wide groups:
+//   A11 = L11 D1 L11^T;  L21 = A21 L11^-T D1^-1;  L22 D2 L22^T = A22 - L21 D1 L21^T;
+//   L31 = 0 (the x_{k+1} rows have no entry on u_k);  L32 = L22^-T D2^-1;
+//   L33 D3 L33^T = A33 - L32 D2 L32^T,
+// the same factors as the dense right-looking LDL^T of M_k in this order.
+// A 30 x 30 LDL^T of rows held in registers: at pivot j the unscaled column
+// entry t_c = S(c, j) of row c is broadcast from lane c by a shuffle.
+__device__ __forceinline__ void ldl30(float (&a)[30], float& d, int lane) {
+#pragma unroll
+  for (int j = 0; j < 30; ++j) {
+    const float t = a[j];
+    const float ij = 1.f / __shfl_sync(FULL, t, j);
+    const float l = t * ij;
+#pragma unroll
+    for (int c = j + 1; c < 30; ++c) {
+      const float tc = __shfl_sync(FULL, t, c);
+      if (lane >= c) a[c] = fmaf(-l, tc, a[c]);
+    }
+    if (lane == j) d = t;
+    if (lane > j) a[j] = l;
+  }
+}
+// y L^T = a for row vectors (L unit lower, row c of L in register array Lr of
+// lane c): y_c = a_c - sum_{c' < c} L(c, c') y_c'
+__device__ __forceinline__ void trsv_rows(float (&y)[30], const float (&Lr)[30]) {
+#pragma unroll
+  for (int c = 1; c < 30; ++c) {
+#pragma unroll
+    for (int q = 0; q < c; ++q) y[c] = fmaf(-__shfl_sync(FULL, Lr[q], c), y[q], y[c]);
+  }
+}
+
+// row i of L, columns j0 .. j0 + 29 (only j < i when diag), into both layouts
+template <bool DIAG>
+__device__ __forceinline__ void put_row(float* rec, int i, int j0, const float (&v)[30], int lane) {
+  if (lane >= 30) return;
+  float* Lr = rec + LDL_ROW;
+  float* Lc = rec + LDL_COL;
+#pragma unroll
+  for (int c = 0; c < 30; ++c) {
+    const int j = j0 + c;
+    if (!DIAG || j < i) {
+      Lr[row_off(i) + j - row_skip(i)] = v[c];
+      Lc[col_off(j) + i - j - 1] = v[c];
+    }
+  }
+}
+
 __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverParams prm) {
   const int lane = threadIdx.x;
   const int row = blockIdx.x;
@@ -106,124 +165,103 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
   const AgentPtrs ap = agent_ptrs(a, slot);
   if (ap.st[T_STATUS] == MPC_AGENT_NAN_) return;
   extern __shared__ __align__(16) float fsm[];
-  float* S = fsm;                   // the stage's block, row-major (lower triangle used)
-  float* v = S + NB * SLD;          // column below the pivot
-  float* Y = v + 96;                // Y = A_{k+1} L_xx^-T, rows of stride 31
-  float* M = Y + 30 * 31;           // Y D_xx^-1 Y^T: carried into the next block
+  float* T = fsm;                   // 30 rows of stride 32: the scaled rows of the last solve
   const float* md = ap.mdl;
   const float* lin = ap.lin;
   const int N = ap.N;
   const float dt = md[M_DT], mu = md[M_MU], sigma = prm.sigma;
   const float rho = *ap.rho, rho_eq = 1e3f * rho;
+  const int l = lane < 30 ? lane : 29;   // lanes 30, 31 shadow row 29 (their results are unused)
   float* rec0 = a.lL + (size_t)slot * a.maxN * LDL_REC;
+  float mrow[30];                        // row l of A_k X_{k-1} A_k^T (0 at k = 0)
+#pragma unroll
+  for (int c = 0; c < 30; ++c) mrow[c] = 0.f;
   for (int k = 0; k < N; ++k) {
     float* rec = rec0 + (size_t)k * LDL_REC;
     const float* cls = ap.rcls + k * RS;
-    for (int t = lane; t < NB * SLD; t += 32) S[t] = 0.f;
-    __syncwarp();
-    // ---- assembly of M_k (the u_k block carries the Schur complement of
-    // the stage's inequality pivots: rho C_u^T C_u, the x_{k+1} block rho C_x^T C_x)
-    if (lane < 30) {
-      const int i = lane;
-      S[i * SLD + i] = 2.f * dt * md[M_R + i] + sigma + rho * cls[i < 12 ? i : i + 8];
-      S[(60 + i) * SLD + 60 + i] = 2.f * dt * md[M_Q + i] + sigma + (i >= 12 ? rho * cls[i + 26] : 0.f);
-      S[(60 + i) * SLD + 30 + i] = 1.f;
-      float* Sl = S + (30 + i) * SLD;
-      for (int c = 0; c < 30; ++c) Sl[c] = -b_entry(lin, dt, i, c);
-      for (int c = 0; c <= i; ++c) Sl[30 + c] = (c == i ? -1.f / rho_eq : 0.f) - (k ? M[i * 31 + c] : 0.f);
-    }
-    __syncwarp();
-    if (lane < 2) {
-      const int f = lane, b0 = 6 * f, p = 12 + 4 * f;
-      const float r0 = rho * cls[p], r1 = rho * cls[p + 1], r2 = rho * cls[p + 2], r3 = rho * cls[p + 3];
-      S[b0 * SLD + b0] += r0 + r1;
-      S[(b0 + 1) * SLD + b0 + 1] += r2 + r3;
-      S[(b0 + 2) * SLD + b0 + 2] += mu * mu * (r0 + r1 + r2 + r3);
-      S[(b0 + 2) * SLD + b0] += mu * (r1 - r0);
-      S[(b0 + 2) * SLD + b0 + 1] += mu * (r3 - r2);
-    }
-    __syncwarp();
-    // ---- dense LDL^T, right-looking, no pivoting; lane owns rows lane,
-    // lane + 32, lane + 64; the trailing update walks the columns in chunks of
-    // eight (independent shared-memory loads, then the updates, then stores)
-    for (int j = 0; j < NB; ++j) {
-      const float id = 1.f / S[j * SLD + j];
-      float l[3];
+    // ---- A11 = R_t: diagonal, and the pyramid couplings of row f_z of a foot
+    float av[30];
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const int i = lane + 32 * m;
-        const bool own = i > j && i < NB;
-        const float t = own ? S[i * SLD + j] : 0.f;
-        if (own) v[i] = t;
-        l[m] = t * id;
-      }
-      __syncwarp();
+    for (int c = 0; c < 30; ++c) av[c] = 0.f;
+    {
+      float dg = 2.f * dt * md[M_R + l] + sigma + rho * cls[l < 12 ? l : l + 8];
+      if (l < 12 && (l % 6) < 3) {
+        const int f = l / 6, cc = l - 6 * f, p = 12 + 4 * f;
+        const float r0 = rho * cls[p], r1 = rho * cls[p + 1], r2 = rho * cls[p + 2], r3 = rho * cls[p + 3];
+        dg += cc == 0 ? r0 + r1 : (cc == 1 ? r2 + r3 : mu * mu * (r0 + r1 + r2 + r3));
+        if (cc == 2) {
 #pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        const int i = lane + 32 * m;
-        if (i > j && i < NB) S[i * SLD + j] = l[m];
-      }
-      for (int c0 = j + 1; c0 < NB; c0 += 8) {
-        float vv[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) vv[q] = v[min(c0 + q, NB - 1)];
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          const int i = lane + 32 * m;
-          if (i < NB && i >= c0) {
-            float* Si = S + i * SLD + c0;
-            float sv[8];
-#pragma unroll
-            for (int q = 0; q < 8; ++q) sv[q] = c0 + q <= i ? Si[q] : 0.f;
-#pragma unroll
-            for (int q = 0; q < 8; ++q)
-              if (c0 + q <= i) Si[q] = fmaf(-l[m], vv[q], sv[q]);
+          for (int c = 0; c < 12; ++c) {
+            if (c == l - 2) av[c] = mu * (r1 - r0);
+            if (c == l - 1) av[c] = mu * (r3 - r2);
           }
         }
       }
+#pragma unroll
+      for (int c = 0; c < 30; ++c)
+        if (c == l) av[c] = dg;
+    }
+    const float q33 = 2.f * dt * md[M_Q + l] + sigma + (l >= 12 ? rho * cls[l + 26] : 0.f);
+    float dd0 = 1.f, dd1 = 1.f, dd2 = 1.f;
+    // ---- the three groups in turn: factor the (updated) diagonal block,
+    // store its rows, solve the next off-diagonal block's rows against it
+    // (A21 = -B, A32 = I, and for the coupling A_{k+1}), scale them by 1/D,
+    // and form the next diagonal block's update from the scaled rows
+#pragma unroll 1
+    for (int g = 0; g < 3; ++g) {
+      float d = 1.f;
+      ldl30(av, d, lane);
+      if (g == 0) dd0 = d;
+      else if (g == 1) dd1 = d;
+      else dd2 = d;
+      put_row<true>(rec, 30 * g + l, 30 * g, av, lane);
+      if (g == 2 && k + 1 == N) break;
+      float y[30];
+#pragma unroll
+      for (int c = 0; c < 30; ++c)
+        y[c] = g == 0 ? -b_entry(lin, dt, l, c) : (g == 1 ? (c == l ? 1.f : 0.f) : a_entry(lin, k + 1, l, c));
+      trsv_rows(y, av);
+      float ys[30];
+#pragma unroll
+      for (int c = 0; c < 30; ++c) ys[c] = y[c] / __shfl_sync(FULL, d, c);
+      if (g < 2) {
+        put_row<false>(rec, 30 * (g + 1) + l, 30 * g, ys, lane);
+      } else if (lane < 30) {
+        float* G = rec0 + (size_t)(k + 1) * LDL_REC + LDL_G;
+#pragma unroll
+        for (int c = 0; c < 30; ++c) G[lane * 30 + c] = ys[c];
+      }
+      __syncwarp();
+      if (lane < 30)
+#pragma unroll
+        for (int c = 0; c < 30; ++c) T[lane * 32 + c] = ys[c];
+      __syncwarp();
+      // row l of (unscaled rows) x (scaled rows)^T
+#pragma unroll
+      for (int s2 = 0; s2 < 30; ++s2) {
+        float acc = 0.f;
+        const float4* r4 = reinterpret_cast<const float4*>(T + s2 * 32);
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+          const float4 v = r4[q];
+          acc = fmaf(y[4 * q], v.x, acc);
+          acc = fmaf(y[4 * q + 1], v.y, acc);
+          acc = fmaf(y[4 * q + 2], v.z, acc);
+          acc = fmaf(y[4 * q + 3], v.w, acc);
+        }
+        acc = fmaf(y[28], T[s2 * 32 + 28], acc);
+        acc = fmaf(y[29], T[s2 * 32 + 29], acc);
+        if (g == 0) av[s2] = (s2 == l ? -1.f / rho_eq : 0.f) - mrow[s2] - acc;
+        else if (g == 1) av[s2] = (s2 == l ? q33 : 0.f) - acc;
+        else mrow[s2] = acc;
+      }
       __syncwarp();
     }
-    // ---- factors to global memory: L by columns and by rows, 1/D
-    for (int j = 0; j < NB - 1; ++j)
-      for (int i = j + 1 + lane; i < NB; i += 32) rec[LDL_COL + col_off(j) + i - j - 1] = S[i * SLD + j];
-    for (int i = 1; i < NB; ++i)
-      for (int j = lane; j < i; j += 32) rec[LDL_ROW + row_off(i) + j] = S[i * SLD + j];
-    for (int j = lane; j < NB; j += 32) rec[LDL_IND + j] = 1.f / S[j * SLD + j];
-    // ---- coupling to the next block: Y = A_{k+1} L_xx^-T (lane r: row r),
-    // G_{k+1} = Y D_xx^-1, and the update Y D_xx^-1 Y^T of its multiplier block
-    if (k + 1 < N) {
-      // rows of A_{k+1} into Y, then lane r solves its row in place
-      for (int t = lane; t < 900; t += 32) {
-        const int r = t / 30, c = t - 30 * r;
-        Y[r * 31 + c] = a_entry(lin, k + 1, r, c);
-      }
-      if (lane < 30) v[lane] = 1.f / S[(60 + lane) * SLD + 60 + lane];   // 1/D of x_{k+1}
-      __syncwarp();
-      if (lane < 30) {
-        float* y = Y + lane * 31;
-        for (int i = 1; i < 30; ++i) {
-          const float* Li = S + (60 + i) * SLD + 60;
-          float s = y[i];
-          for (int c = 0; c < i; ++c) s = fmaf(-Li[c], y[c], s);
-          y[i] = s;
-        }
-      }
-      __syncwarp();
-      float* G = rec0 + (size_t)(k + 1) * LDL_REC + LDL_G;
-      for (int t = lane; t < 900; t += 32) {
-        const int r = t / 30, c = t - 30 * r;
-        G[t] = Y[r * 31 + c] * v[c];
-      }
-      if (lane < 30) {
-        const int r = lane;
-        for (int s2 = 0; s2 < 30; ++s2) {
-          float acc = 0.f;
-#pragma unroll 6
-          for (int c = 0; c < 30; ++c) acc = fmaf(Y[r * 31 + c] * v[c], Y[s2 * 31 + c], acc);
-          M[r * 31 + s2] = acc;
-        }
-      }
-      __syncwarp();
+    if (lane < 30) {
+      // (the x_{k+1} rows have no entry on u_k: L31 = 0, not stored)
+      rec[LDL_IND + l] = 1.f / dd0;
+      rec[LDL_IND + 30 + l] = 1.f / dd1;
+      rec[LDL_IND + 60 + l] = 1.f / dd2;
     }
   }
 }
@@ -237,19 +275,20 @@ __device__ __forceinline__ void fwd_sub(const float* Lc, float& e0, float& e1, f
     const int o = col_off(j) - j - 1;             // L(i, j) at o + i, i > j
     const float wj = j < 32 ? __shfl_sync(FULL, e0, j) : (j < 64 ? __shfl_sync(FULL, e1, j - 32)
                                                                  : __shfl_sync(FULL, e2, j - 64));
+    // columns j < 30 have no rows 60-89 (the zero block)
     if (lane > j) e0 = fmaf(-Lc[o + lane], wj, e0);
-    if (lane + 32 > j) e1 = fmaf(-Lc[o + lane + 32], wj, e1);
-    if (lane + 64 > j && lane < NB - 64) e2 = fmaf(-Lc[o + lane + 64], wj, e2);
+    if (lane + 32 > j && (j >= 30 || lane + 32 < 60)) e1 = fmaf(-Lc[o + lane + 32], wj, e1);
+    if (lane + 64 > j && lane < NB - 64 && j >= 30) e2 = fmaf(-Lc[o + lane + 64], wj, e2);
   }
 }
 // Unit upper solve L^T v = w of one block, L by rows (shared memory).
 __device__ __forceinline__ void bwd_sub(const float* Lr, float& e0, float& e1, float& e2, int lane) {
 #pragma unroll
   for (int j = NB - 1; j >= 1; --j) {
-    const int o = row_off(j);                     // L(j, i) at o + i, i < j
+    const int o = row_off(j) - row_skip(j);       // L(j, i) at o + i, i < j (i >= 30 for j >= 60)
     const float vj = j < 32 ? __shfl_sync(FULL, e0, j) : (j < 64 ? __shfl_sync(FULL, e1, j - 32)
                                                                  : __shfl_sync(FULL, e2, j - 64));
-    if (lane < j) e0 = fmaf(-Lr[o + lane], vj, e0);
+    if (lane < j && (j < 60 || lane >= 30)) e0 = fmaf(-Lr[o + lane], vj, e0);
     if (lane + 32 < j) e1 = fmaf(-Lr[o + lane + 32], vj, e1);
     if (lane + 64 < j) e2 = fmaf(-Lr[o + lane + 64], vj, e2);
   }
@@ -262,7 +301,7 @@ __device__ __forceinline__ void bwd_sub(const float* Lr, float& e0, float& e1, f
 // previous item computes.  A wait gives up after `limit` polls: the warp then
 // issues nothing more, waits (bounded) for the copies in flight and ends the
 // agent's solve with MPC_AGENT_TIMEOUT.
-constexpr int BUF_L = 0, BUF_G = 4008, BUF_D = 4908, BUF_FLOATS = 5004;
+constexpr int BUF_L = 0, BUF_G = 3108, BUF_D = 4008, BUF_FLOATS = 4104;
 struct Stager {
   float* buf[2];
   uint64_t* bar;      // two mbarriers
@@ -280,7 +319,7 @@ __device__ __forceinline__ void stage_issue(Stager& sg, int b, const float* rec0
     const float* rec = rec0 + (size_t)k * LDL_REC;
     const bool g = fwd ? k >= 1 : k + 1 < N;
     const float* gsrc = fwd ? rec + LDL_G : rec + LDL_REC + LDL_G;   // G_k or G_{k+1}
-    const uint32_t bl = 4008 * 4, bg = 900 * 4, bd = 96 * 4;
+    const uint32_t bl = (LDL_ROW - LDL_COL) * 4, bg = 900 * 4, bd = 96 * 4;
     mbar_expect_tx(sg.bar + b, bl + (g ? bg : 0) + (fwd ? 0 : bd));
     tma_load_1d(sg.buf[b] + BUF_L, rec + (fwd ? LDL_COL : LDL_ROW), bl, sg.bar + b);
     if (g) tma_load_1d(sg.buf[b] + BUF_G, gsrc, bg, sg.bar + b);
@@ -645,11 +684,8 @@ cudaError_t launch_ldl(const Arena& a, const Batch& b, const SolverParams& prm, 
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mpc_k_ldl_admm, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(W_ADMM * sizeof(float)));
-    // both kernels are one warp with about 40 KB of shared memory: ask for the
-    // largest shared-memory carveout, so that five of them fit on an SM
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mpc_k_ldl_factor, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared);
+    // the iteration kernel's one-warp blocks hold about 40 KB of shared memory:
+    // ask for the largest shared-memory carveout, so that five fit on an SM
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(mpc_k_ldl_admm, cudaFuncAttributePreferredSharedMemoryCarveout,
                                cudaSharedmemCarveoutMaxShared);

@@ -141,7 +141,7 @@ def test_literal_nonfinite_input_is_flagged():
 def test_literal_budget_counts_the_factors():
     mpcgpu = _lib()
     # the regular form of 256 agents fits in 64 MB; the literal form's factors
-    # (about 36 KB per stage per agent) do not
+    # (about 29 KB per stage per agent) do not
     s = mpcgpu.Solver(max_agents=256, max_horizon=20, hbm_budget_bytes=64 << 20,
                       stream=torch.cuda.current_stream().cuda_stream)
     s.close()
