@@ -118,7 +118,7 @@ def parse():
     ap.add_argument("--no-precision", action="store_true", help="skip the per-precision speed/accuracy report")
     ap.add_argument("--no-policy", action="store_true", help="skip the residual-policy measurement")
     ap.add_argument("--precision-agents", type=int, default=48, help="agents per workload sample, precision report")
-    ap.add_argument("--serve-seconds", type=float, default=1.5, help="serving run length (0 = skip)")
+    ap.add_argument("--serve-seconds", type=float, default=3.0, help="serving run length (0 = skip)")
     ap.add_argument("--no-tree", action="store_true",
                     help="diagonal joint model in the torque map instead of RNEA over a kinematic tree")
     ap.add_argument("--serve-streams", type=int, default=2, help="serving: streams with a batch in flight")
@@ -741,7 +741,8 @@ def run_serving(args, model, replans, n, cfg=None):
         st["churned_agents"] = int(eng.churned)
         out[f"{f:g}x"] = st
     out["note"] = (f"native server (mpc_server_*), requests replayed by native threads (mpc_load_*); requests of one "
-                   f"agent coalesce (newest state wins); {args.serve_streams} batches in flight; ADMM cap 500 iterations; "
+                   f"agent coalesce (newest state wins); {args.serve_streams} batches in flight; agents whose polish "
+                   "first fails are deferred to batches of their own (ADMM from the saved start); ADMM cap 500 iterations; "
                    "churn: 5% of the agents "
                    "(between requests) swapped for reserve agents every 1 s = 100 replans at 100 Hz; "
                    "rates x 1.6384 M requests/s")

@@ -71,10 +71,15 @@ typedef enum {
                                   below on the dynamics (Q, R >= 0, x0 fixed) */
   MPC_AGENT_NAN = 4,           /* non-finite input or iterate; outputs zeroed */
   MPC_AGENT_TIMEOUT = 5,       /* a bounded device wait gave up; outputs zeroed */
-  MPC_AGENT_INACCURATE = 6     /* ADMM met its stopping test but no polish passed the KKT
+  MPC_AGENT_INACCURATE = 6,    /* ADMM met its stopping test but no polish passed the KKT
                                   check (or polish is off): the outputs are ADMM's iterate,
                                   as accurate as that test, not certified to be the
                                   optimum; the warm start is kept */
+  MPC_AGENT_DEFERRED = 7       /* only with MPC_SOLVE_DEFER_ADMM: the polish first failed its
+                                  KKT check, and the agent's ADMM start (the last polished
+                                  point, its row values and multipliers) was written to its
+                                  warm start instead of running ADMM; outputs zeroed.  Solve
+                                  it again with MPC_SOLVE_ADMM_ONLY and the same inputs */
 } mpc_agent_status;
 
 /* Precision of the Riccati factor's two dense 22 x 22 stage products per
@@ -284,6 +289,19 @@ mpc_status mpc_solve(mpc_ctx* ctx, uint64_t ticket);
  * results are gathered on the same stream by mpc_get_torques. */
 mpc_status mpc_solve_on(mpc_ctx* ctx, uint64_t ticket, void* stream);
 
+/* Flags of mpc_solve_ex (fused form only).  DEFER_ADMM: an agent whose
+ * polish first fails is not taken through ADMM in this solve; it ends with
+ * MPC_AGENT_DEFERRED (a latency-bound caller answers the rest of the batch
+ * at once and finishes such agents in a batch of their own).  ADMM_ONLY: no
+ * polish first; every agent runs ADMM from its warm start (with the polish
+ * attempts along the way and the final polish), the second half of a
+ * deferred solve. */
+typedef enum { MPC_SOLVE_DEFER_ADMM = 1, MPC_SOLVE_ADMM_ONLY = 2 } mpc_solve_flags;
+
+/* mpc_solve_on with flags (0 = mpc_solve_on).  MPC_ERR_INVALID for an
+ * unknown flag or flags on a form other than FUSED. */
+mpc_status mpc_solve_ex(mpc_ctx* ctx, uint64_t ticket, void* stream, int32_t flags);
+
 /* Tune the batching form's launch configuration on the ticket's batch by
  * timing candidates (`repeats` timed solves each, after one untimed solve) on
  * the context's stream, in two stages: the kernel shape (variant = register
@@ -459,10 +477,20 @@ typedef struct mpc_server mpc_server;
 
 /* pool: slots served (<= the context's max_agents, ids 0..pool-1, each given
  * a model by mpc_set_models before); max_batch: largest batch; max_inflight:
- * batches on the GPU at a time (1..4; each has its own stream and pinned and
- * device buffers, allocated here). */
+ * regular batches on the GPU at a time (1..4; each has its own stream and
+ * pinned and device buffers, allocated here, and one more lane of its own
+ * carries the batches of deferred agents, see mpc_server_set_defer). */
 mpc_status mpc_server_create(mpc_ctx* ctx, int32_t pool, int32_t max_batch, int32_t max_inflight,
                              mpc_server** out);
+/* Deferral of slow agents (off by default; set before mpc_server_start):
+ * batches are solved with MPC_SOLVE_DEFER_ADMM, so an agent whose polish
+ * first fails does not hold its batch's answers for the length of an ADMM
+ * solve; the worker keeps such agents (with their requests and states) and
+ * solves them in batches of their own with MPC_SOLVE_ADMM_ONLY, ahead of the
+ * next regular batch, answering their requests when those complete.
+ * mpc_server_deferred gives the number of agents deferred so far. */
+mpc_status mpc_server_set_defer(mpc_server* srv, int32_t on);
+int64_t mpc_server_deferred(mpc_server* srv);
 /* Starts the worker and the server's clock.  MPC_ERR_STATE if started. */
 mpc_status mpc_server_start(mpc_server* srv);
 /* n requests (host arrays): slots [n], x0 [n][30], qd_meas [n][18], cmd [n][4],

@@ -146,6 +146,8 @@ struct SolverParams {
   int spin_limit;  // polls of a bounded mbarrier wait before it gives up (MPC_AGENT_TIMEOUT)
   int wait_test_slot;  // failure-detection test: the first stage-block wait of this agent slot is
                        //   armed with no copy behind it, so it runs out (-1: off)
+  int defer;           // fused form: an agent whose polish first fails ends DEFERRED once its ADMM
+                       //   warm start is written (no ADMM in this launch)
 };
 
 }  // namespace mpc

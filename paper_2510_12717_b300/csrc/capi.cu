@@ -38,6 +38,7 @@ struct GraphEntry {
   const void* ptrs[5] = {};
   cudaStream_t stream = nullptr;
   int variant = 0, check_every = 0, trees = 0, grid = 0;
+  int flags = 0;                    // mpc_solve_ex flags of the captured solve
   int kernels = 0;                  // kernels the captured graph launches
   float early_polish = 0.f;
   cudaGraphExec_t exec = nullptr;
@@ -541,6 +542,7 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   if (c.form == MPC_FORM_LDL) p.warm_start = 0;
   p.spin_limit = c.spin_limit;
   p.wait_test_slot = c.wait_test_agent;
+  p.defer = 0;
   return p;
 }
 
@@ -553,7 +555,7 @@ static const TuneEntry* tuned_for(const mpc_ctx* ctx, int n) {
   return nullptr;
 }
 
-static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
+static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st, int flags) {
   int launches = 0;
   mpc_config cfg = ctx->cfg;
   int grid = 0;
@@ -563,6 +565,8 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
   }
   mpc::SolverParams prm = params_of(cfg);
   prm.trees = ctx->has_trees ? 1 : 0;
+  prm.defer = (flags & MPC_SOLVE_DEFER_ADMM) ? 1 : 0;
+  if (flags & MPC_SOLVE_ADMM_ONLY) prm.warm_polish = 0;
   const int form = ctx->cfg.form;
   // graph capture needs a non-default stream; on the legacy stream the
   // solve is launched directly
@@ -576,7 +580,7 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
     GraphEntry& g = ctx->graphs[gi];
     if (g.exec && g.n == tk->b.n && g.stream == st && g.variant == cfg.variant &&
         g.check_every == cfg.check_every && g.early_polish == cfg.early_polish && g.grid == grid &&
-        g.trees == prm.trees && !memcmp(g.ptrs, ptrs, sizeof(ptrs))) {
+        g.trees == prm.trees && g.flags == flags && !memcmp(g.ptrs, ptrs, sizeof(ptrs))) {
       ctx->graph_replays += 1;
       ctx->launches += g.kernels;       // the kernels recorded in the graph
       return cudaGraphLaunch(g.exec, st);
@@ -618,19 +622,24 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st) {
   g.early_polish = cfg.early_polish;
   g.grid = grid;
   g.trees = prm.trees;
+  g.flags = flags;
   g.kernels = launches;
   ctx->launches += launches;
   return cudaGraphLaunch(g.exec, st);
 }
 
-mpc_status mpc_solve_on(mpc_ctx* ctx, uint64_t ticket, void* stream) {
+mpc_status mpc_solve_ex(mpc_ctx* ctx, uint64_t ticket, void* stream, int32_t flags) {
   if (!ctx) return MPC_ERR_INVALID;
   Ticket* tk = find_ticket(ctx, ticket);
   if (!tk) return fail(ctx, MPC_ERR_NOT_READY, "solve: unknown ticket");
   if (tk->state != 1) return fail(ctx, MPC_ERR_STATE, "solve: ticket already solved");
+  if (flags & ~(MPC_SOLVE_DEFER_ADMM | MPC_SOLVE_ADMM_ONLY))
+    return fail(ctx, MPC_ERR_INVALID, "solve: unknown flag");
+  if (flags && ctx->cfg.form != MPC_FORM_FUSED)
+    return fail(ctx, MPC_ERR_INVALID, "solve: flags need the fused form");
   CK(cudaSetDevice(ctx->cfg.device));
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = enqueue_solve(ctx, tk, st);
+  cudaError_t e = enqueue_solve(ctx, tk, st, flags);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "solve: kernel launch");
   ctx->solves += 1;
   tk->state = 2;
@@ -638,7 +647,9 @@ mpc_status mpc_solve_on(mpc_ctx* ctx, uint64_t ticket, void* stream) {
   return MPC_OK;
 }
 
-mpc_status mpc_solve(mpc_ctx* ctx, uint64_t ticket) { return mpc_solve_on(ctx, ticket, ctx ? ctx->stream : nullptr); }
+mpc_status mpc_solve_on(mpc_ctx* ctx, uint64_t ticket, void* stream) { return mpc_solve_ex(ctx, ticket, stream, 0); }
+
+mpc_status mpc_solve(mpc_ctx* ctx, uint64_t ticket) { return mpc_solve_ex(ctx, ticket, ctx ? ctx->stream : nullptr, 0); }
 
 mpc_status mpc_get_torques(mpc_ctx* ctx, uint64_t ticket, float* tau, float* q_set, float* qd_set, float* value,
                            int32_t* agent_status) {

@@ -15,7 +15,11 @@
 // the batch covered is answered: its latency is the completion time minus its
 // arrival time, on one steady clock started by mpc_server_start.  Model swaps
 // (agents leaving and joining) are queued and applied by the worker to slots
-// with no batch in flight, between batches.
+// with no batch in flight, between batches.  With deferral on, batches are
+// solved with MPC_SOLVE_DEFER_ADMM: an agent whose polish first fails comes
+// back MPC_AGENT_DEFERRED, keeps its requests and state in a queue, stays in
+// flight, and is solved (MPC_SOLVE_ADMM_ONLY) in a batch of deferred agents
+// that the worker launches ahead of the next regular batch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,12 +44,19 @@ struct Lane {                            // one stream and its batch buffers
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   bool busy = false;
+  bool admm_only = false;              // a batch of deferred agents
   int n = 0;
   double t_launch = 0.0;
   int32_t* h_ids = nullptr;  float* h_in = nullptr;  float* h_tau = nullptr;  int32_t* h_st = nullptr;
   int32_t* d_ids = nullptr;  float* d_in = nullptr;  float* d_tau = nullptr;  int32_t* d_st = nullptr;
   std::vector<int32_t> slots;
   std::vector<std::vector<double>> arrivals;   // per batch row: arrival times it answers
+};
+
+struct Deferred {                      // an agent whose solve was deferred
+  int32_t slot;
+  std::vector<double> arrivals;
+  float state[kInF];
 };
 
 }  // namespace
@@ -63,13 +74,15 @@ struct mpc_server {
   std::vector<uint8_t> inflight;
   std::vector<int32_t> ready_order;               // scratch of the worker
   std::vector<std::pair<int32_t, mpc_agent_model>> swaps;
+  bool defer = false;                              // solve with MPC_SOLVE_DEFER_ADMM
+  std::vector<Deferred> deferred_q;                // deferred agents awaiting their ADMM batch
   double swaps_since = -1.0;                      // queue time of the oldest pending swap
   // results (guarded by mu)
   std::vector<double> latency;
   std::vector<double> batch_log;                   // per batch: launch time, completion time, agents
   std::vector<float> tau;                          // [pool][18] last answer per slot
   std::vector<int32_t> status;                     // [pool]
-  long long pushed = 0, answered = 0, batches = 0, solves = 0, not_solved = 0, swapped = 0;
+  long long pushed = 0, answered = 0, batches = 0, solves = 0, not_solved = 0, swapped = 0, deferred = 0;
   // worker
   std::thread worker;
   std::atomic<bool> stop{false};
@@ -93,8 +106,24 @@ void set_error(mpc_server* s, int code, const char* what) {
 void complete(mpc_server* s, Lane& L) {
   const double t = now_s(s);
   std::lock_guard<std::mutex> g(s->mu);
+  const int mb = s->max_batch;
+  int kept = 0;
   for (int i = 0; i < L.n; ++i) {
     const int slot = L.slots[i];
+    if (!L.admm_only && L.h_st[i] == MPC_AGENT_DEFERRED) {
+      // its requests wait for the agent's ADMM batch; the slot stays in flight
+      Deferred d;
+      d.slot = slot;
+      d.arrivals.swap(L.arrivals[i]);
+      std::memcpy(d.state, L.h_in + (size_t)i * 30, sizeof(float) * 30);
+      std::memcpy(d.state + 30, L.h_in + (size_t)mb * 30 + (size_t)i * 18, sizeof(float) * 18);
+      std::memcpy(d.state + 48, L.h_in + (size_t)mb * 48 + (size_t)i * 4, sizeof(float) * 4);
+      d.state[52] = L.h_in[(size_t)mb * 52 + i];
+      s->deferred_q.push_back(std::move(d));
+      s->deferred += 1;
+      ++kept;
+      continue;
+    }
     for (double ta : L.arrivals[i]) s->latency.push_back(t - ta);
     s->answered += (long long)L.arrivals[i].size();
     std::memcpy(&s->tau[(size_t)slot * kOutF], L.h_tau + (size_t)i * kOutF, sizeof(float) * kOutF);
@@ -102,7 +131,7 @@ void complete(mpc_server* s, Lane& L) {
     if (L.h_st[i] != 0) s->not_solved += 1;
     s->inflight[slot] = 0;
   }
-  s->solves += L.n;
+  s->solves += L.n - kept;
   s->batch_log.push_back(L.t_launch);
   s->batch_log.push_back(t);
   s->batch_log.push_back((double)L.n);
@@ -110,11 +139,38 @@ void complete(mpc_server* s, Lane& L) {
   L.n = 0;
 }
 
-// form and enqueue one batch on lane L; false when nothing is ready
-bool launch(mpc_server* s, Lane& L) {
+// form and enqueue one batch on lane L; false when nothing is ready.
+// deferred: a batch of deferred agents (the extra lane), else a regular one
+bool launch(mpc_server* s, Lane& L, bool deferred) {
   int n = 0;
-  {
+  if (deferred) {
     std::lock_guard<std::mutex> g(s->mu);
+    if (s->deferred_q.empty()) return false;
+    {
+      const int mb = s->max_batch;
+      n = std::min((int)s->deferred_q.size(), mb);
+      L.slots.resize(n);
+      L.arrivals.resize(n);
+      float* hx = L.h_in;
+      float* hq = hx + (size_t)mb * 30;
+      float* hc = hq + (size_t)mb * 18;
+      float* hp = hc + (size_t)mb * 4;
+      for (int i = 0; i < n; ++i) {
+        Deferred& d = s->deferred_q[i];
+        L.slots[i] = d.slot;
+        L.arrivals[i].swap(d.arrivals);
+        L.h_ids[i] = d.slot;
+        std::memcpy(hx + (size_t)i * 30, d.state, sizeof(float) * 30);
+        std::memcpy(hq + (size_t)i * 18, d.state + 30, sizeof(float) * 18);
+        std::memcpy(hc + (size_t)i * 4, d.state + 48, sizeof(float) * 4);
+        hp[i] = d.state[52];
+      }
+      s->deferred_q.erase(s->deferred_q.begin(), s->deferred_q.begin() + n);
+      L.admm_only = true;
+    }
+  } else {
+    std::lock_guard<std::mutex> g(s->mu);
+    L.admm_only = false;
     // oldest pending request first
     s->ready_order.clear();
     for (int slot = 0; slot < s->pool; ++slot)
@@ -167,7 +223,8 @@ bool launch(mpc_server* s, Lane& L) {
   if (e != cudaSuccess) { set_error(s, MPC_ERR_CUDA, cudaGetErrorString(e)); return false; }
   uint64_t tk = 0;
   mpc_status r = mpc_submit(s->ctx, n, L.d_ids, x0, qd, cmd, ph, &tk);
-  if (r == MPC_OK) r = mpc_solve_on(s->ctx, tk, st);
+  const int flags = L.admm_only ? MPC_SOLVE_ADMM_ONLY : (s->defer ? MPC_SOLVE_DEFER_ADMM : 0);
+  if (r == MPC_OK) r = mpc_solve_ex(s->ctx, tk, st, flags);
   if (r == MPC_OK) r = mpc_get_torques(s->ctx, tk, L.d_tau, nullptr, nullptr, nullptr, L.d_st);
   if (r != MPC_OK) { set_error(s, r, mpc_last_error(s->ctx)); return false; }
   e = cudaMemcpyAsync(L.h_tau, L.d_tau, sizeof(float) * kOutF * n, cudaMemcpyDeviceToHost, st);
@@ -207,20 +264,30 @@ void run_worker(mpc_server* s) {
   cudaSetDevice(s->device);
   while (!s->stop.load(std::memory_order_relaxed) && s->error.load() == MPC_OK) {
     bool work = false;
-    int busy = 0;
-    for (auto& L : s->lanes) {
+    int busy = 0;          // regular lanes with a batch on the GPU
+    bool busy_def = false; // the deferred agents' lane
+    for (int li = 0; li <= s->max_inflight; ++li) {
+      Lane& L = s->lanes[li];
       if (!L.busy) continue;
       const cudaError_t q = cudaEventQuery(L.done);
       if (q == cudaSuccess) { complete(s, L); work = true; }
       else if (q != cudaErrorNotReady) { set_error(s, MPC_ERR_CUDA, cudaGetErrorString(q)); return; }
-      else ++busy;
+      else if (li < s->max_inflight) ++busy;
+      else busy_def = true;
     }
-    for (auto& L : s->lanes) {
+    // regular batches on the first max_inflight lanes; deferred agents on the
+    // last lane, so that their ADMM solves never hold a regular lane
+    for (int li = 0; li < s->max_inflight; ++li) {
+      Lane& L = s->lanes[li];
       if (busy >= s->max_inflight) break;
       if (L.busy) continue;
-      if (!launch(s, L)) break;
+      if (!launch(s, L, false)) break;
       ++busy;
       work = true;
+    }
+    {
+      Lane& L = s->lanes[s->max_inflight];
+      if (!L.busy && launch(s, L, true)) { work = true; busy_def = true; }
     }
     // model swaps wait for the device (their upload queues behind the
     // batches that hold the SMs): apply them while every lane is busy, when
@@ -230,13 +297,13 @@ void run_worker(mpc_server* s) {
     {
       std::lock_guard<std::mutex> g(s->mu);
       due = !s->swaps.empty() &&
-            (busy >= s->max_inflight || busy == 0 || now_s(s) - s->swaps_since > 0.02);
+            (busy >= s->max_inflight || (busy == 0 && !busy_def) || now_s(s) - s->swaps_since > 0.02);
     }
     if (due) apply_swaps(s);
     if (!work) {
       // nothing completed or launched: wait briefly for a push or a completion
       std::unique_lock<std::mutex> lk(s->mu);
-      s->cv.wait_for(lk, std::chrono::microseconds(busy ? 20 : 200));
+      s->cv.wait_for(lk, std::chrono::microseconds(busy || busy_def ? 20 : 200));
     }
   }
 }
@@ -261,7 +328,7 @@ mpc_status mpc_server_create(mpc_ctx* ctx, int32_t pool, int32_t max_batch, int3
   s->latency.reserve(1 << 23);     // no reallocation (a copy under the lock) in a run of a few seconds
   s->batch_log.reserve(3 << 16);
   s->status.assign(pool, -1);
-  s->lanes.resize(max_inflight);
+  s->lanes.resize(max_inflight + 1);   // + the lane of the deferred agents' batches
   const int mb = s->max_batch;
   for (auto& L : s->lanes) {
     cudaError_t e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
@@ -278,6 +345,19 @@ mpc_status mpc_server_create(mpc_ctx* ctx, int32_t pool, int32_t max_batch, int3
   }
   *out = s;
   return MPC_OK;
+}
+
+mpc_status mpc_server_set_defer(mpc_server* s, int32_t on) {
+  if (!s) return MPC_ERR_INVALID;
+  if (s->worker.joinable()) return MPC_ERR_STATE;
+  s->defer = on != 0;
+  return MPC_OK;
+}
+
+int64_t mpc_server_deferred(mpc_server* s) {
+  if (!s) return 0;
+  std::lock_guard<std::mutex> g(s->mu);
+  return s->deferred;
 }
 
 mpc_status mpc_server_start(mpc_server* s) {

@@ -15,6 +15,7 @@ constexpr int MPC_AGENT_PRIMAL_INFEAS_ = 2;
 constexpr int MPC_AGENT_NAN_ = 4;
 constexpr int MPC_AGENT_TIMEOUT_ = 5;
 constexpr int MPC_AGENT_INACCURATE_ = 6;
+constexpr int MPC_AGENT_DEFERRED_ = 7;
 
 size_t smem_bytes_per_block();
 

@@ -1989,6 +1989,9 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
     factored = false;   // the polish overwrote the caches
     o.prec = fallback_precision(o.prec);
     polish_warm_start(ap, sm, lane, pat);
+    // deferred: the ADMM start is in the warm-start arrays; a later solve of
+    // this agent without the polish first runs the ADMM from it
+    if (prm.defer) { o.status = MPC_AGENT_DEFERRED_; return o; }
   }
   if (!factored) factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, o.prec);
   const bool fixed = prm.fixed_iters > 0;
@@ -2238,7 +2241,7 @@ template <int PREC>
 __device__ void final_polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Outcome& o,
                              const LanePat& pat, Pipe& pp) {
   if (!prm.polish || o.polished || o.status == MPC_AGENT_NAN_ || o.status == MPC_AGENT_TIMEOUT_ ||
-      o.status == MPC_AGENT_PRIMAL_INFEAS_)
+      o.status == MPC_AGENT_PRIMAL_INFEAS_ || o.status == MPC_AGENT_DEFERRED_)
     return;
   Res pr;
   if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, o.prec)) {
@@ -2433,8 +2436,8 @@ __global__ void __launch_bounds__(WARPS_PER_BLOCK * 32) mpc_k_torque(Arena a, Ba
   if (row >= b.n || !valid_slot(a, b, row)) return;
   const AgentPtrs ap = agent_ptrs(a, b.ids[row]);
   const int st = ap.st[T_STATUS];
-  if (st == MPC_AGENT_NAN_ || st == MPC_AGENT_TIMEOUT_) {
-    // a failed solve leaves no torques: zeroed outputs, as the status says
+  if (st == MPC_AGENT_NAN_ || st == MPC_AGENT_TIMEOUT_ || st == MPC_AGENT_DEFERRED_) {
+    // a failed or deferred solve leaves no torques: zeroed outputs, as the status says
     if (lane < 18) { ap.out[O_TAU + lane] = 0.f; ap.out[O_QSET + lane] = 0.f; ap.out[O_QDSET + lane] = 0.f; }
     if (lane == 0) ap.out[O_V] = 0.f;
     return;
@@ -2460,7 +2463,7 @@ static __global__ void __launch_bounds__(128) mpc_k_rnea(Arena a, Batch b) {
   const float* md = ap.mdl;
   if (md[M_TREE_ON] == 0.f) return;
   const int status = ap.st[T_STATUS];
-  if (status == MPC_AGENT_NAN_ || status == MPC_AGENT_TIMEOUT_) return;
+  if (status == MPC_AGENT_NAN_ || status == MPC_AGENT_TIMEOUT_ || status == MPC_AGENT_DEFERRED_) return;
   const int j0 = c < 2 ? 5 * c : 10 + 4 * (c - 2), len = c < 2 ? 5 : 4;
   const float dt = md[M_DT], idt = 1.f / dt;
   const float* x0 = ap.inp + I_X0;

@@ -18,7 +18,8 @@ LIB_PATH = os.path.join(HERE, "libmpcgpu.so")
 MPC_OK, MPC_ERR_INVALID, MPC_ERR_BUDGET, MPC_ERR_CUDA = 0, 1, 2, 3
 MPC_ERR_NOT_READY, MPC_ERR_TIMEOUT, MPC_ERR_STATE = 4, 5, 6
 AGENT_SOLVED, AGENT_MAX_ITER, AGENT_PRIMAL_INFEAS, AGENT_DUAL_INFEAS, AGENT_NAN, AGENT_TIMEOUT = 0, 1, 2, 3, 4, 5
-AGENT_INACCURATE = 6
+AGENT_INACCURATE, AGENT_DEFERRED = 6, 7
+SOLVE_DEFER_ADMM, SOLVE_ADMM_ONLY = 1, 2
 FORM_PLAIN, FORM_FUSED, FORM_LDL = 0, 1, 2
 FP32, TF32, BF16, FP64, TF32X3 = 0, 1, 2, 3, 4
 PEAK_FP32_FMA, PEAK_FP64_FMA, PEAK_TF32_MMA_SYNC, PEAK_BF16_MMA_SYNC = 0, 1, 2, 3
@@ -98,6 +99,7 @@ SIGNATURES = {
     "mpc_submit": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _U64P]),
     "mpc_solve": (C.c_int, [_P, C.c_uint64]),
     "mpc_solve_on": (C.c_int, [_P, C.c_uint64, _P]),
+    "mpc_solve_ex": (C.c_int, [_P, C.c_uint64, _P, C.c_int32]),
     "mpc_autotune": (C.c_int, [_P, C.c_uint64, C.c_int32, C.c_char_p, C.c_size_t]),
     "mpc_get_torques": (C.c_int, [_P, C.c_uint64, _P, _P, _P, _P, _P]),
     "mpc_solve_host": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -114,6 +116,8 @@ SIGNATURES = {
     "mpc_measure_peak": (C.c_int, [C.c_int32, _P, C.POINTER(C.c_double), C.POINTER(C.c_double)]),
     "mpc_server_create": (C.c_int, [_P, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_void_p)]),
     "mpc_server_start": (C.c_int, [_P]),
+    "mpc_server_set_defer": (C.c_int, [_P, C.c_int32]),
+    "mpc_server_deferred": (C.c_int64, [_P]),
     "mpc_server_push": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P]),
     "mpc_server_set_models": (C.c_int, [_P, C.c_int32, _P, _P]),
     "mpc_server_drain": (C.c_int, [_P, C.c_double]),
@@ -271,9 +275,12 @@ class Solver:
                                         _ptr(cmd), _ptr(phase), C.byref(t)))
         return t.value
 
-    def solve(self, ticket: int, stream=None):
-        """mpc_solve (context stream) or mpc_solve_on (stream: a cudaStream_t handle)."""
-        if stream is None:
+    def solve(self, ticket: int, stream=None, flags: int = 0):
+        """mpc_solve (context stream) or mpc_solve_on (stream: a cudaStream_t
+        handle); with flags (SOLVE_DEFER_ADMM, SOLVE_ADMM_ONLY) mpc_solve_ex."""
+        if flags:
+            self._check(self.lib.mpc_solve_ex(self.ctx, C.c_uint64(ticket), stream, int(flags)))
+        elif stream is None:
             self._check(self.lib.mpc_solve(self.ctx, C.c_uint64(ticket)))
         else:
             self._check(self.lib.mpc_solve_on(self.ctx, C.c_uint64(ticket), stream))
@@ -392,6 +399,14 @@ class Server:
     def _check(self, st):
         if st != MPC_OK:
             raise MpcError(st, self.lib.mpc_server_last_error(self.srv).decode())
+
+    def set_defer(self, on: bool = True):
+        """mpc_server_set_defer: agents whose polish first fails finish in
+        batches of their own (before start())."""
+        self._check(self.lib.mpc_server_set_defer(self.srv, int(bool(on))))
+
+    def deferred(self) -> int:
+        return int(self.lib.mpc_server_deferred(self.srv))
 
     def start(self):
         self._check(self.lib.mpc_server_start(self.srv))

@@ -9,6 +9,10 @@ pending one: the newest state wins) and a worker thread that, whenever fewer
 than `streams` batches are on the GPU, forms the next batch from every agent
 with pending requests and no batch in flight, copies it to the device,
 solves it on its own stream and answers its requests when it completes.
+With `defer` (the default) an agent whose polish first fails does not hold
+its batch: it comes back deferred and the server finishes it (ADMM from the
+saved start) in a batch of its own, so one slow agent delays only its own
+requests.
 This driver replays the arrival process in real time: every few hundred
 microseconds it pushes the requests that have arrived, with their states and
 arrival times.  Every `churn_period` seconds (1 s = 100 replans of an agent
@@ -39,7 +43,8 @@ from . import mpcgpu
 class ServingEngine:
     def __init__(self, model: dict, inputs, *, pool: int, streams: int = 2, max_batch: int = 0,
                  hbm_budget_bytes: int = 8 << 30, device: int = 0, step_sigma: float = 0.02,
-                 phase_step: float = 0.02, revert: float = 0.95, seed: int = 0, **solver_opts):
+                 phase_step: float = 0.02, revert: float = 0.95, seed: int = 0, defer: bool = True,
+                 **solver_opts):
         """model: SoA agent models (workload.make_agents layout) of every agent
         that may ever join (live + reserve); inputs: their initial per-agent
         input dict (x0, qd_meas, cmd, phase), or a list whose first entry is.
@@ -56,6 +61,7 @@ class ServingEngine:
         self.total = len(model["mass"])
         self.pool = pool
         self.streams = streams
+        self.defer = defer
         self.max_batch = max_batch or pool
         self.solver = mpcgpu.Solver(max_agents=pool, max_horizon=int(np.max(model["N"])), device=device,
                                     stream=torch.cuda.current_stream(self.dev).cuda_stream,
@@ -97,6 +103,7 @@ class ServingEngine:
             self.solver.solve_host(slots_all, x0, qd, cmd, ph)
         W = self.walk
         srv = mpcgpu.Server(self.solver, self.pool, self.max_batch, self.streams)
+        srv.set_defer(self.defer)
         load = None
         next_churn = churn_period if churn_period and churn_period > 0 else float("inf")
         try:
@@ -120,6 +127,7 @@ class ServingEngine:
             wall = srv.clock()
             res = srv.results()
             blog = srv.batches()
+            n_deferred = srv.deferred()
             srv.stop()
         finally:
             if load is not None:
@@ -139,7 +147,7 @@ class ServingEngine:
                     batch_ms_p50=float(np.percentile(dur, 50)) if len(dur) else None,
                     batch_ms_p99=float(np.percentile(dur, 99)) if len(dur) else None,
                     batch_ms_max=float(dur.max()) if len(dur) else None,
-                    push_lag_ms_p99=lag[1] * 1e3, push_lag_ms_max=lag[2] * 1e3)
+                    push_lag_ms_p99=lag[1] * 1e3, push_lag_ms_max=lag[2] * 1e3, deferred=n_deferred)
 
 
 class StateWalk:

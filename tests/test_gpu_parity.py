@@ -428,3 +428,51 @@ def test_primal_infeasible_agents_are_flagged(mpcgpu, form):
     ref = _oracle({k: v[good] for k, v in model.items()}, {k: v[good] for k, v in inp32.items()})
     ok = torque_close(r["tau"][good], ref["tau"])
     assert ok.all(), np.argwhere(~ok)
+
+
+def test_deferred_admm_agents_finish_in_their_own_solve(mpcgpu):
+    # the joints-near-limits change of the fallback test, solved with
+    # MPC_SOLVE_DEFER_ADMM: agents whose polish first fails come back
+    # DEFERRED with zeroed torques and the others are solved; the deferred
+    # ones, solved again on the same inputs with MPC_SOLVE_ADMM_ONLY, reach
+    # the FP64 optimum like everyone else
+    ids = np.arange(40)
+    model, _ = agents("uneven", ids)
+    dev = torch.device("cuda:0")
+    s = mpcgpu.Solver(max_agents=40, max_horizon=20, stream=torch.cuda.current_stream().cuda_stream)
+    s.set_models(model, ids)
+    for replan in (0, 1):
+        _, inp = agents("uneven", ids, replan=replan)
+        inp32 = device_inputs(inp)
+        s.solve_host(ids, inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+    _, inp = agents("uneven", ids, replan=2)
+    sign = np.sign(np.random.default_rng(11).standard_normal((len(ids), 18)))
+    inp["x0"][:, 12:30] = 1.45 * sign
+    inp32 = device_inputs(inp)
+    ref = _oracle(model, inp32)
+
+    def run(rows, flags):
+        t = {k: torch.from_numpy(np.ascontiguousarray(v[rows])).to(dev) for k, v in inp32.items()}
+        d_ids = torch.from_numpy(ids[rows].astype(np.int32)).to(dev)
+        tk = s.submit(d_ids, t["x0"], t["qd_meas"], t["cmd"], t["phase"])
+        s.solve(tk, flags=flags)
+        tau = torch.full((len(rows), 18), float("nan"), device=dev)
+        st = torch.full((len(rows),), -9, dtype=torch.int32, device=dev)
+        s.get_torques(tk, tau=tau, status=st)
+        torch.cuda.synchronize()
+        return tau.cpu().numpy(), st.cpu().numpy()
+
+    tau, st = run(np.arange(40), mpcgpu.SOLVE_DEFER_ADMM)
+    deferred = st == mpcgpu.AGENT_DEFERRED
+    assert deferred.sum() >= 2 and (st[~deferred] == 0).all(), st
+    assert np.all(tau[deferred] == 0.0)
+    ok = torque_close(tau[~deferred], ref["tau"][~deferred])
+    assert ok.all(), np.argwhere(~ok)
+    rows = np.flatnonzero(deferred)
+    tau2, st2 = run(rows, mpcgpu.SOLVE_ADMM_ONLY)
+    assert (st2 == 0).all(), st2
+    stats = s.agent_stats(ids[rows])
+    assert (stats["iters"] > 0).all()
+    ok = torque_close(tau2, ref["tau"][rows])
+    assert ok.all(), np.argwhere(~ok)
+    s.close()

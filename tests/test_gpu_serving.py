@@ -87,3 +87,47 @@ def test_server_answers_equal_direct_solves():
     assert a2["answered"] == n + len(both) and a2["solves"] == n + len(sub)   # the pairs coalesced
     assert np.array_equal(a2["tau"][sub], d2["tau"])
     assert len(a2["latency"]) == n + len(both) and (a2["latency"] >= 0).all()
+
+
+def test_server_with_deferral_answers_equal_direct_solves():
+    # joints moved next to their limits: the polish from the previous active
+    # set fails for several agents; with deferral on, the server answers the
+    # rest from the batch and finishes those in batches of their own; every
+    # answer equals a direct solve (which runs the same ADMM from the same start)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2510_12717_b300 import mpcgpu
+    from workload import make_inputs, make_agents
+    n = 40
+    ids = np.arange(n)
+    model, _ = make_agents("uneven", ids)
+    f32 = lambda x: {k: np.ascontiguousarray(v, np.float32) for k, v in x.items()}
+    reps = [f32(make_inputs("uneven", ids, r)[1]) for r in range(3)]
+    sign = np.sign(np.random.default_rng(11).standard_normal((n, 18)))
+    reps[2]["x0"][:, 12:30] = np.float32(1.45) * sign
+    stream = torch.cuda.current_stream().cuda_stream
+    direct = mpcgpu.Solver(max_agents=n, max_horizon=20, stream=stream)
+    served = mpcgpu.Solver(max_agents=n, max_horizon=20, stream=stream)
+    direct.set_models(model, ids)
+    served.set_models(model, ids)
+    slots = ids.astype(np.int32)
+    for r in (0, 1):
+        direct.solve_host(slots, reps[r]["x0"], reps[r]["qd_meas"], reps[r]["cmd"], reps[r]["phase"])
+        served.solve_host(slots, reps[r]["x0"], reps[r]["qd_meas"], reps[r]["cmd"], reps[r]["phase"])
+    d = direct.solve_host(slots, reps[2]["x0"], reps[2]["qd_meas"], reps[2]["cmd"], reps[2]["phase"])
+    fell_back = direct.agent_stats(slots)["polished"] != 2
+    srv = mpcgpu.Server(served, n, max_batch=n, max_inflight=2)
+    srv.set_defer(True)
+    srv.start()
+    srv.push(slots, reps[2]["x0"], reps[2]["qd_meas"], reps[2]["cmd"], reps[2]["phase"], np.zeros(n))
+    srv.drain(30.0)
+    a = srv.results()
+    deferred = srv.deferred()
+    srv.stop()
+    srv.close()
+    served.close()
+    direct.close()
+    assert fell_back.sum() >= 2 and deferred == fell_back.sum()
+    assert a["answered"] == n and a["solves"] == n and a["batches"] >= 2
+    assert (a["status"] == 0).all() and (d["status"] == 0).all()
+    assert np.array_equal(a["tau"], d["tau"])
