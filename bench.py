@@ -742,7 +742,8 @@ def run_serving(args, model, replans, n, cfg=None):
         out[f"{f:g}x"] = st
     out["note"] = (f"native server (mpc_server_*), requests replayed by native threads (mpc_load_*); requests of one "
                    f"agent coalesce (newest state wins); {args.serve_streams} batches in flight; agents whose polish "
-                   "first fails are deferred to batches of their own (ADMM from the saved start); ADMM cap 500 iterations; "
+                   "first fails are deferred to batches of their own (extra lane; ADMM from the saved start); "
+                   "ADMM cap 500 iterations; "
                    "churn: 5% of the agents "
                    "(between requests) swapped for reserve agents every 1 s = 100 replans at 100 Hz; "
                    "rates x 1.6384 M requests/s")

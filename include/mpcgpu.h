@@ -75,11 +75,15 @@ typedef enum {
                                   check (or polish is off): the outputs are ADMM's iterate,
                                   as accurate as that test, not certified to be the
                                   optimum; the warm start is kept */
-  MPC_AGENT_DEFERRED = 7       /* only with MPC_SOLVE_DEFER_ADMM: the polish first failed its
-                                  KKT check, and the agent's ADMM start (the last polished
-                                  point, its row values and multipliers) was written to its
-                                  warm start instead of running ADMM; outputs zeroed.  Solve
-                                  it again with MPC_SOLVE_ADMM_ONLY and the same inputs */
+  MPC_AGENT_DEFERRED = 7       /* only with a DEFER flag of mpc_solve_ex, outputs zeroed.
+                                  DEFER_ADMM: the polish first failed its KKT check and the
+                                  agent's ADMM start (the last polished point, its row values
+                                  and multipliers) was written to its warm start instead of
+                                  running ADMM: solve it again with MPC_SOLVE_ADMM_ONLY and
+                                  the same inputs.  DEFER_SLOW: the polish first had not
+                                  passed after two reduced KKT solves; its corrected active
+                                  set is kept: solve it again with no flag and the same
+                                  inputs, which continues from it */
 } mpc_agent_status;
 
 /* Precision of the Riccati factor's two dense 22 x 22 stage products per
@@ -289,14 +293,18 @@ mpc_status mpc_solve(mpc_ctx* ctx, uint64_t ticket);
  * results are gathered on the same stream by mpc_get_torques. */
 mpc_status mpc_solve_on(mpc_ctx* ctx, uint64_t ticket, void* stream);
 
-/* Flags of mpc_solve_ex (fused form only).  DEFER_ADMM: an agent whose
- * polish first fails is not taken through ADMM in this solve; it ends with
- * MPC_AGENT_DEFERRED (a latency-bound caller answers the rest of the batch
- * at once and finishes such agents in a batch of their own).  ADMM_ONLY: no
+/* Flags of mpc_solve_ex (fused form only), for latency-bound callers that
+ * answer most of a batch at once and finish its slow agents in a batch of
+ * their own.  DEFER_ADMM: an agent whose polish first fails is not taken
+ * through ADMM in this solve; it ends MPC_AGENT_DEFERRED.  ADMM_ONLY: no
  * polish first; every agent runs ADMM from its warm start (with the polish
  * attempts along the way and the final polish), the second half of a
- * deferred solve. */
-typedef enum { MPC_SOLVE_DEFER_ADMM = 1, MPC_SOLVE_ADMM_ONLY = 2 } mpc_solve_flags;
+ * DEFER_ADMM solve.  DEFER_SLOW (alone): the polish first stops after two
+ * reduced KKT solves (the active-set method's first guess and one
+ * correction); an agent it has not solved by then ends MPC_AGENT_DEFERRED and
+ * a solve without flags continues it (more corrections, then ADMM if needed),
+ * with the same result as an uninterrupted solve. */
+typedef enum { MPC_SOLVE_DEFER_ADMM = 1, MPC_SOLVE_ADMM_ONLY = 2, MPC_SOLVE_DEFER_SLOW = 4 } mpc_solve_flags;
 
 /* mpc_solve_on with flags (0 = mpc_solve_on).  MPC_ERR_INVALID for an
  * unknown flag or flags on a form other than FUSED. */
@@ -482,14 +490,16 @@ typedef struct mpc_server mpc_server;
  * carries the batches of deferred agents, see mpc_server_set_defer). */
 mpc_status mpc_server_create(mpc_ctx* ctx, int32_t pool, int32_t max_batch, int32_t max_inflight,
                              mpc_server** out);
-/* Deferral of slow agents (off by default; set before mpc_server_start):
- * batches are solved with MPC_SOLVE_DEFER_ADMM, so an agent whose polish
- * first fails does not hold its batch's answers for the length of an ADMM
- * solve; the worker keeps such agents (with their requests and states) and
- * solves them in batches of their own with MPC_SOLVE_ADMM_ONLY, ahead of the
- * next regular batch, answering their requests when those complete.
- * mpc_server_deferred gives the number of agents deferred so far. */
-mpc_status mpc_server_set_defer(mpc_server* srv, int32_t on);
+/* Deferral of slow agents (mode 0 = off, the default; set before
+ * mpc_server_start).  Mode 1: batches are solved with MPC_SOLVE_DEFER_ADMM,
+ * so an agent whose polish first fails does not hold its batch's answers
+ * for the length of an ADMM solve; mode 2: with MPC_SOLVE_DEFER_SLOW, neither
+ * does an agent that two reduced KKT solves of its polish do not settle.  The
+ * worker keeps such agents (with their requests and states) and finishes them
+ * (MPC_SOLVE_ADMM_ONLY, or no flag) in batches of their own on an extra lane,
+ * answering their requests when those complete.  mpc_server_deferred gives
+ * the number of agents deferred so far.  MPC_ERR_INVALID for another mode. */
+mpc_status mpc_server_set_defer(mpc_server* srv, int32_t mode);
 int64_t mpc_server_deferred(mpc_server* srv);
 /* Starts the worker and the server's clock.  MPC_ERR_STATE if started. */
 mpc_status mpc_server_start(mpc_server* srv);

@@ -146,8 +146,10 @@ struct SolverParams {
   int spin_limit;  // polls of a bounded mbarrier wait before it gives up (MPC_AGENT_TIMEOUT)
   int wait_test_slot;  // failure-detection test: the first stage-block wait of this agent slot is
                        //   armed with no copy behind it, so it runs out (-1: off)
-  int defer;           // fused form: an agent whose polish first fails ends DEFERRED once its ADMM
-                       //   warm start is written (no ADMM in this launch)
+  int defer;           // fused form: 1 = an agent whose polish first fails ends DEFERRED once its
+                       //   ADMM warm start is written (no ADMM in this launch); 2 = an agent whose
+                       //   polish first has not passed after 2 reduced solves ends DEFERRED with
+                       //   its corrected active set kept (a later solve continues from it)
 };
 
 }  // namespace mpc

@@ -565,7 +565,7 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st, int 
   }
   mpc::SolverParams prm = params_of(cfg);
   prm.trees = ctx->has_trees ? 1 : 0;
-  prm.defer = (flags & MPC_SOLVE_DEFER_ADMM) ? 1 : 0;
+  prm.defer = (flags & MPC_SOLVE_DEFER_SLOW) ? 2 : (flags & MPC_SOLVE_DEFER_ADMM) ? 1 : 0;
   if (flags & MPC_SOLVE_ADMM_ONLY) prm.warm_polish = 0;
   const int form = ctx->cfg.form;
   // graph capture needs a non-default stream; on the legacy stream the
@@ -633,8 +633,10 @@ mpc_status mpc_solve_ex(mpc_ctx* ctx, uint64_t ticket, void* stream, int32_t fla
   Ticket* tk = find_ticket(ctx, ticket);
   if (!tk) return fail(ctx, MPC_ERR_NOT_READY, "solve: unknown ticket");
   if (tk->state != 1) return fail(ctx, MPC_ERR_STATE, "solve: ticket already solved");
-  if (flags & ~(MPC_SOLVE_DEFER_ADMM | MPC_SOLVE_ADMM_ONLY))
+  if (flags & ~(MPC_SOLVE_DEFER_ADMM | MPC_SOLVE_ADMM_ONLY | MPC_SOLVE_DEFER_SLOW))
     return fail(ctx, MPC_ERR_INVALID, "solve: unknown flag");
+  if ((flags & MPC_SOLVE_DEFER_SLOW) && (flags & (MPC_SOLVE_DEFER_ADMM | MPC_SOLVE_ADMM_ONLY)))
+    return fail(ctx, MPC_ERR_INVALID, "solve: DEFER_SLOW combines with no other flag");
   if (flags && ctx->cfg.form != MPC_FORM_FUSED)
     return fail(ctx, MPC_ERR_INVALID, "solve: flags need the fused form");
   CK(cudaSetDevice(ctx->cfg.device));

@@ -16,10 +16,11 @@
 // arrival time, on one steady clock started by mpc_server_start.  Model swaps
 // (agents leaving and joining) are queued and applied by the worker to slots
 // with no batch in flight, between batches.  With deferral on, batches are
-// solved with MPC_SOLVE_DEFER_ADMM: an agent whose polish first fails comes
-// back MPC_AGENT_DEFERRED, keeps its requests and state in a queue, stays in
-// flight, and is solved (MPC_SOLVE_ADMM_ONLY) in a batch of deferred agents
-// that the worker launches ahead of the next regular batch.
+// solved with a DEFER flag of mpc_solve_ex: an agent whose polish first fails
+// (DEFER_ADMM), or that two reduced KKT solves of it do not settle
+// (DEFER_SLOW), comes back MPC_AGENT_DEFERRED, keeps its requests and state in
+// a queue, stays in flight, and is finished (ADMM from the saved start, or the
+// polish continued) in a batch of deferred agents on an extra lane of its own.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -44,7 +45,7 @@ struct Lane {                            // one stream and its batch buffers
   cudaStream_t stream = nullptr;
   cudaEvent_t done = nullptr;
   bool busy = false;
-  bool admm_only = false;              // a batch of deferred agents
+  bool deferred_batch = false;              // a batch of deferred agents
   int n = 0;
   double t_launch = 0.0;
   int32_t* h_ids = nullptr;  float* h_in = nullptr;  float* h_tau = nullptr;  int32_t* h_st = nullptr;
@@ -74,7 +75,7 @@ struct mpc_server {
   std::vector<uint8_t> inflight;
   std::vector<int32_t> ready_order;               // scratch of the worker
   std::vector<std::pair<int32_t, mpc_agent_model>> swaps;
-  bool defer = false;                              // solve with MPC_SOLVE_DEFER_ADMM
+  int defer = 0;                                   // 0 off, 1 DEFER_ADMM, 2 DEFER_SLOW (mpc_server_set_defer)
   std::vector<Deferred> deferred_q;                // deferred agents awaiting their ADMM batch
   double swaps_since = -1.0;                      // queue time of the oldest pending swap
   // results (guarded by mu)
@@ -110,7 +111,7 @@ void complete(mpc_server* s, Lane& L) {
   int kept = 0;
   for (int i = 0; i < L.n; ++i) {
     const int slot = L.slots[i];
-    if (!L.admm_only && L.h_st[i] == MPC_AGENT_DEFERRED) {
+    if (!L.deferred_batch && L.h_st[i] == MPC_AGENT_DEFERRED) {
       // its requests wait for the agent's ADMM batch; the slot stays in flight
       Deferred d;
       d.slot = slot;
@@ -166,11 +167,11 @@ bool launch(mpc_server* s, Lane& L, bool deferred) {
         hp[i] = d.state[52];
       }
       s->deferred_q.erase(s->deferred_q.begin(), s->deferred_q.begin() + n);
-      L.admm_only = true;
+      L.deferred_batch = true;
     }
   } else {
     std::lock_guard<std::mutex> g(s->mu);
-    L.admm_only = false;
+    L.deferred_batch = false;
     // oldest pending request first
     s->ready_order.clear();
     for (int slot = 0; slot < s->pool; ++slot)
@@ -223,7 +224,12 @@ bool launch(mpc_server* s, Lane& L, bool deferred) {
   if (e != cudaSuccess) { set_error(s, MPC_ERR_CUDA, cudaGetErrorString(e)); return false; }
   uint64_t tk = 0;
   mpc_status r = mpc_submit(s->ctx, n, L.d_ids, x0, qd, cmd, ph, &tk);
-  const int flags = L.admm_only ? MPC_SOLVE_ADMM_ONLY : (s->defer ? MPC_SOLVE_DEFER_ADMM : 0);
+  // regular batches defer their slow agents; a batch of deferred agents runs
+  // ADMM from the saved start (DEFER_ADMM) or continues the capped polish
+  // (DEFER_SLOW, no flag)
+  int flags = 0;
+  if (s->defer == 1) flags = L.deferred_batch ? MPC_SOLVE_ADMM_ONLY : MPC_SOLVE_DEFER_ADMM;
+  else if (s->defer == 2) flags = L.deferred_batch ? 0 : MPC_SOLVE_DEFER_SLOW;
   if (r == MPC_OK) r = mpc_solve_ex(s->ctx, tk, st, flags);
   if (r == MPC_OK) r = mpc_get_torques(s->ctx, tk, L.d_tau, nullptr, nullptr, nullptr, L.d_st);
   if (r != MPC_OK) { set_error(s, r, mpc_last_error(s->ctx)); return false; }
@@ -347,10 +353,10 @@ mpc_status mpc_server_create(mpc_ctx* ctx, int32_t pool, int32_t max_batch, int3
   return MPC_OK;
 }
 
-mpc_status mpc_server_set_defer(mpc_server* s, int32_t on) {
-  if (!s) return MPC_ERR_INVALID;
+mpc_status mpc_server_set_defer(mpc_server* s, int32_t mode) {
+  if (!s || mode < 0 || mode > 2) return MPC_ERR_INVALID;
   if (s->worker.joinable()) return MPC_ERR_STATE;
-  s->defer = on != 0;
+  s->defer = mode;
   return MPC_OK;
 }
 

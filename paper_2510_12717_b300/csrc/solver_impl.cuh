@@ -1810,17 +1810,20 @@ __device__ void init_active_min(const AgentPtrs& ap, int lane) {
 // final active set; POLISH_MIN the equality rows alone (cold agent)
 enum : int { POLISH_ADMM = 0, POLISH_PREV = 1, POLISH_MIN = 2 };
 
+// cap > 0: stop after cap reduced solves (the corrections of the last one
+// are still applied to the active set, for a later continuation)
 template <int PREC>
 __device__ __noinline__ bool polish(const AgentPtrs& ap, float* sm, int lane, const SolverParams& prm, Res* res,
-                       const LanePat& pat, Pipe& pp, int prec, int guess = POLISH_ADMM) {
+                       const LanePat& pat, Pipe& pp, int prec, int guess = POLISH_ADMM, int cap = 0) {
   if (guess == POLISH_PREV) init_active_prev(ap, lane);
   else if (guess == POLISH_MIN) init_active_min(ap, lane);
   else init_active(ap, lane);
   // before any ADMM iteration more corrections pay: the alternative is an
   // ADMM solve
   const int attempts = guess == POLISH_ADMM ? 4 : 8;
+  const int stop = cap > 0 && cap < attempts ? cap : attempts;
   const int nref = guess == POLISH_PREV ? prm.refine : prm.refine_admm;
-  for (int attempt = 0; attempt < attempts; ++attempt) {
+  for (int attempt = 0; attempt < stop; ++attempt) {
     if (!polish_solve<PREC>(ap, sm, lane, pat, pp, prm, nref, prec)) return false;
     const Res pr = polish_check<false>(ap, sm, lane, prm, nullptr, pat);
     const float tol_p = prm.eps_abs + prm.eps_rel * pr.ps;
@@ -1978,7 +1981,8 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
   if (lane == 0) { ap.st[T_FIRST] = 0; ap.st[T_ATTEMPTS] = 0; }
   if (prm.polish && prm.warm_polish && prm.fixed_iters == 0) {
     Res pr;
-    if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, o.prec, ap.st[T_WARM] ? POLISH_PREV : POLISH_MIN)) {
+    if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, o.prec, ap.st[T_WARM] ? POLISH_PREV : POLISH_MIN,
+                     prm.defer == 2 ? 2 : 0)) {
       o.polished = 1;
       o.status = MPC_AGENT_SOLVED_;
       o.r = pr;
@@ -1986,12 +1990,15 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
       return o;
     }
     if (pp.timed_out()) { o.status = MPC_AGENT_TIMEOUT_; return o; }
+    // deferred after a capped polish: the corrected active set is kept; a
+    // later solve of this agent (same inputs, no flag) continues from it
+    if (prm.defer == 2) { o.status = MPC_AGENT_DEFERRED_; return o; }
     factored = false;   // the polish overwrote the caches
     o.prec = fallback_precision(o.prec);
     polish_warm_start(ap, sm, lane, pat);
     // deferred: the ADMM start is in the warm-start arrays; a later solve of
     // this agent without the polish first runs the ADMM from it
-    if (prm.defer) { o.status = MPC_AGENT_DEFERRED_; return o; }
+    if (prm.defer == 1) { o.status = MPC_AGENT_DEFERRED_; return o; }
   }
   if (!factored) factor_admm<PREC>(ap, sm, lane, rho, prm.sigma, pat, o.prec);
   const bool fixed = prm.fixed_iters > 0;

@@ -19,7 +19,7 @@ MPC_OK, MPC_ERR_INVALID, MPC_ERR_BUDGET, MPC_ERR_CUDA = 0, 1, 2, 3
 MPC_ERR_NOT_READY, MPC_ERR_TIMEOUT, MPC_ERR_STATE = 4, 5, 6
 AGENT_SOLVED, AGENT_MAX_ITER, AGENT_PRIMAL_INFEAS, AGENT_DUAL_INFEAS, AGENT_NAN, AGENT_TIMEOUT = 0, 1, 2, 3, 4, 5
 AGENT_INACCURATE, AGENT_DEFERRED = 6, 7
-SOLVE_DEFER_ADMM, SOLVE_ADMM_ONLY = 1, 2
+SOLVE_DEFER_ADMM, SOLVE_ADMM_ONLY, SOLVE_DEFER_SLOW = 1, 2, 4
 FORM_PLAIN, FORM_FUSED, FORM_LDL = 0, 1, 2
 FP32, TF32, BF16, FP64, TF32X3 = 0, 1, 2, 3, 4
 PEAK_FP32_FMA, PEAK_FP64_FMA, PEAK_TF32_MMA_SYNC, PEAK_BF16_MMA_SYNC = 0, 1, 2, 3
@@ -400,10 +400,11 @@ class Server:
         if st != MPC_OK:
             raise MpcError(st, self.lib.mpc_server_last_error(self.srv).decode())
 
-    def set_defer(self, on: bool = True):
-        """mpc_server_set_defer: agents whose polish first fails finish in
-        batches of their own (before start())."""
-        self._check(self.lib.mpc_server_set_defer(self.srv, int(bool(on))))
+    def set_defer(self, mode: int = 1):
+        """mpc_server_set_defer (before start()): 1 = agents whose polish
+        first fails, 2 = also those two reduced KKT solves do not settle,
+        finish in batches of their own; 0 = off."""
+        self._check(self.lib.mpc_server_set_defer(self.srv, int(mode)))
 
     def deferred(self) -> int:
         return int(self.lib.mpc_server_deferred(self.srv))

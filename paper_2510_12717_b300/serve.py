@@ -9,10 +9,11 @@ pending one: the newest state wins) and a worker thread that, whenever fewer
 than `streams` batches are on the GPU, forms the next batch from every agent
 with pending requests and no batch in flight, copies it to the device,
 solves it on its own stream and answers its requests when it completes.
-With `defer` (the default) an agent whose polish first fails does not hold
-its batch: it comes back deferred and the server finishes it (ADMM from the
-saved start) in a batch of its own, so one slow agent delays only its own
-requests.
+With `defer` = 1 (the default) an agent whose polish first fails does not
+hold its batch for the length of an ADMM solve: it comes back deferred and
+the server finishes it (ADMM from the saved start) in a batch of its own, so
+one slow agent delays only its own requests (2: also agents that two reduced
+KKT solves of the polish do not settle; 0: off).
 This driver replays the arrival process in real time: every few hundred
 microseconds it pushes the requests that have arrived, with their states and
 arrival times.  Every `churn_period` seconds (1 s = 100 replans of an agent
@@ -43,7 +44,7 @@ from . import mpcgpu
 class ServingEngine:
     def __init__(self, model: dict, inputs, *, pool: int, streams: int = 2, max_batch: int = 0,
                  hbm_budget_bytes: int = 8 << 30, device: int = 0, step_sigma: float = 0.02,
-                 phase_step: float = 0.02, revert: float = 0.95, seed: int = 0, defer: bool = True,
+                 phase_step: float = 0.02, revert: float = 0.95, seed: int = 0, defer: int = 1,
                  **solver_opts):
         """model: SoA agent models (workload.make_agents layout) of every agent
         that may ever join (live + reserve); inputs: their initial per-agent

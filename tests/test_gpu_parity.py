@@ -430,12 +430,14 @@ def test_primal_infeasible_agents_are_flagged(mpcgpu, form):
     assert ok.all(), np.argwhere(~ok)
 
 
-def test_deferred_admm_agents_finish_in_their_own_solve(mpcgpu):
-    # the joints-near-limits change of the fallback test, solved with
-    # MPC_SOLVE_DEFER_ADMM: agents whose polish first fails come back
-    # DEFERRED with zeroed torques and the others are solved; the deferred
-    # ones, solved again on the same inputs with MPC_SOLVE_ADMM_ONLY, reach
-    # the FP64 optimum like everyone else
+@pytest.mark.parametrize("mode", ["admm", "slow"])
+def test_deferred_agents_finish_in_their_own_solve(mpcgpu, mode):
+    # the joints-near-limits change of the fallback test, solved with a DEFER
+    # flag: agents whose polish first fails (admm), or that its first two
+    # reduced solves do not settle (slow), come back DEFERRED with zeroed
+    # torques and the others are solved; the deferred ones, solved again on
+    # the same inputs (MPC_SOLVE_ADMM_ONLY, or no flag), reach the FP64
+    # optimum like everyone else
     ids = np.arange(40)
     model, _ = agents("uneven", ids)
     dev = torch.device("cuda:0")
@@ -462,17 +464,20 @@ def test_deferred_admm_agents_finish_in_their_own_solve(mpcgpu):
         torch.cuda.synchronize()
         return tau.cpu().numpy(), st.cpu().numpy()
 
-    tau, st = run(np.arange(40), mpcgpu.SOLVE_DEFER_ADMM)
+    first, second = ((mpcgpu.SOLVE_DEFER_ADMM, mpcgpu.SOLVE_ADMM_ONLY) if mode == "admm"
+                     else (mpcgpu.SOLVE_DEFER_SLOW, 0))
+    tau, st = run(np.arange(40), first)
     deferred = st == mpcgpu.AGENT_DEFERRED
     assert deferred.sum() >= 2 and (st[~deferred] == 0).all(), st
     assert np.all(tau[deferred] == 0.0)
     ok = torque_close(tau[~deferred], ref["tau"][~deferred])
     assert ok.all(), np.argwhere(~ok)
     rows = np.flatnonzero(deferred)
-    tau2, st2 = run(rows, mpcgpu.SOLVE_ADMM_ONLY)
+    tau2, st2 = run(rows, second)
     assert (st2 == 0).all(), st2
     stats = s.agent_stats(ids[rows])
-    assert (stats["iters"] > 0).all()
+    if mode == "admm":
+        assert (stats["iters"] > 0).all()
     ok = torque_close(tau2, ref["tau"][rows])
     assert ok.all(), np.argwhere(~ok)
     s.close()

@@ -89,11 +89,14 @@ def test_server_answers_equal_direct_solves():
     assert len(a2["latency"]) == n + len(both) and (a2["latency"] >= 0).all()
 
 
-def test_server_with_deferral_answers_equal_direct_solves():
+@pytest.mark.parametrize("mode", [1, 2])
+def test_server_with_deferral_answers_equal_direct_solves(mode):
     # joints moved next to their limits: the polish from the previous active
     # set fails for several agents; with deferral on, the server answers the
     # rest from the batch and finishes those in batches of their own; every
-    # answer equals a direct solve (which runs the same ADMM from the same start)
+    # answer is the optimum a direct solve finds (a deferred agent's
+    # active-set method may take another path to it: the bar is the torque
+    # tolerance)
     import __graft_entry__ as g
     g.build()
     from paper_2510_12717_b300 import mpcgpu
@@ -115,9 +118,10 @@ def test_server_with_deferral_answers_equal_direct_solves():
         direct.solve_host(slots, reps[r]["x0"], reps[r]["qd_meas"], reps[r]["cmd"], reps[r]["phase"])
         served.solve_host(slots, reps[r]["x0"], reps[r]["qd_meas"], reps[r]["cmd"], reps[r]["phase"])
     d = direct.solve_host(slots, reps[2]["x0"], reps[2]["qd_meas"], reps[2]["cmd"], reps[2]["phase"])
-    fell_back = direct.agent_stats(slots)["polished"] != 2
+    dst = direct.agent_stats(slots)
+    fell_back = dst["polished"] != 2
     srv = mpcgpu.Server(served, n, max_batch=n, max_inflight=2)
-    srv.set_defer(True)
+    srv.set_defer(mode)
     srv.start()
     srv.push(slots, reps[2]["x0"], reps[2]["qd_meas"], reps[2]["cmd"], reps[2]["phase"], np.zeros(n))
     srv.drain(30.0)
@@ -127,7 +131,8 @@ def test_server_with_deferral_answers_equal_direct_solves():
     srv.close()
     served.close()
     direct.close()
-    assert fell_back.sum() >= 2 and deferred == fell_back.sum()
+    assert fell_back.sum() >= 2 and deferred >= fell_back.sum()
     assert a["answered"] == n and a["solves"] == n and a["batches"] >= 2
     assert (a["status"] == 0).all() and (d["status"] == 0).all()
-    assert np.array_equal(a["tau"], d["tau"])
+    tol = 1e-4 + 1e-3 * np.abs(d["tau"])
+    assert (np.abs(a["tau"] - d["tau"]) <= tol).all()
