@@ -125,7 +125,8 @@ typedef enum {
  * rho0 0.1, sigma 1e-6, alpha 1.6, eps_abs = eps_rel = 1e-5, max_iter 4000,
  * fixed_iters 0, check_every 10, adaptive_rho 1, polish 1, warm_start 1,
  * form FUSED, precision FP32, max_horizon 20, variant 1, early_polish 100,
- * graph 0, warm_polish 1, refine_steps -1, spin_limit 4194304, wait_test_agent -1.
+ * graph 0, warm_polish 1, refine_steps -1, spin_limit 4194304, wait_test_agent -1,
+ * ruiz_iters 0.
  * OSQP's parameters (Stellato et al. 2020,
  * Sec. 3.2, to which the paper defers after Eq. (backsolve_2)). */
 typedef struct mpc_config {
@@ -187,6 +188,12 @@ typedef struct mpc_config {
                                  wait of this agent id is armed with no copy behind
                                  it, so it runs out after spin_limit polls with
                                  nothing in flight.  -1 = off (the default) */
+  int ruiz_iters;             /* literal form (MPC_FORM_LDL) only: iterations of OSQP's
+                                 modified Ruiz equilibration of the KKT system before
+                                 its factorisation (f_Ruiz of Alg. 1; 0..50, default 0
+                                 = unscaled: with the fixed step size of this form the
+                                 equilibrated problem converges more slowly on these
+                                 QPs; OSQP pairs its scaling with an adaptive rho) */
 } mpc_config;
 
 /* One agent's model (host memory, float64; stored as float32 on the device,

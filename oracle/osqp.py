@@ -30,6 +30,15 @@ Starting point (f_init, Alg. 1): x^0 = the current base pose and the nominal
 joint angles repeated over the horizon, every other entry zero; z^0 = the
 projection of A x^0 onto [l, u]; y^0 = 0.
 
+Scaling (f_Ruiz, Alg. 1): OSQP's modified Ruiz equilibration (Stellato et al.
+2020, Sec. 5.1).  Each of its iterations divides every column of the KKT
+matrix [[P, A^T], [A, 0]] by the square root of its inf-norm (variables:
+D, rows: E; norms below 1e-4 count as 1, above 1e4 as 1e4), then scales the
+cost by c = 1 / max(mean of the columns' inf-norms of P, |q|_inf) (same
+limits).  The scaled problem is (c D P D, c D q, E A D, E l, E u); the ADMM
+runs on it from the scaled start (D^-1 x^0, E z^0, 0) and its iterate maps
+back as x = D x_s, z = E^-1 z_s, y = E y_s / c.
+
 Oracle code: test infrastructure only.
 """
 from __future__ import annotations
@@ -81,6 +90,30 @@ def start_point(lq: LiteralQP, qp, x0, q_nom):
     return x, np.clip(lq.A @ x, lq.l, lq.u), np.zeros(len(lq.l))
 
 
+def _limit(v, lo=1e-4, hi=1e4):
+    v = np.asarray(v, dtype=float)
+    return np.where(v < lo, 1.0, np.minimum(v, hi))
+
+
+def ruiz(lq: LiteralQP, iters: int = 10):
+    """(scaled LiteralQP, D, E, c) after `iters` equilibration iterations."""
+    P, q, A = lq.P.copy(), lq.q.copy(), lq.A.copy()
+    n, m = P.shape[0], A.shape[0]
+    D, E, c = np.ones(n), np.ones(m), 1.0
+    for _ in range(iters):
+        col = np.maximum(np.abs(P).max(axis=0), np.abs(A).max(axis=0))
+        row = np.abs(A).max(axis=1)
+        dt = 1.0 / np.sqrt(_limit(col))
+        et = 1.0 / np.sqrt(_limit(row))
+        P = dt[:, None] * P * dt[None, :]
+        q = dt * q
+        A = et[:, None] * A * dt[None, :]
+        D, E = D * dt, E * et
+        g = 1.0 / float(_limit(max(np.abs(P).max(axis=0).mean(), np.abs(q).max())))
+        P, q, c = g * P, g * q, g * c
+    return LiteralQP(P, q, A, E * lq.l, E * lq.u, lq.rho, lq.n_dyn), D, E, c
+
+
 def kkt_matrix(lq: LiteralQP, sigma: float) -> np.ndarray:
     """A_K of Eq. (kkt_system) with a per-row rho."""
     n, m = lq.P.shape[0], lq.A.shape[0]
@@ -128,31 +161,45 @@ def residuals(lq: LiteralQP, x, z, y):
 
 
 def solve_until(lq: LiteralQP, x, z, y, *, eps_abs=1e-5, eps_rel=1e-5, max_iter=4000, check_every=10,
-                sigma=1e-6, alpha=1.6):
-    """Iterate until OSQP's stopping test (mixed absolute / relative form)
-    holds at a check, or max_iter; returns (x, z, y, iterations)."""
-    lu = sla.lu_factor(kkt_matrix(lq, sigma))
+                sigma=1e-6, alpha=1.6, scaling=0):
+    """Iterate until OSQP's stopping test (mixed absolute / relative form, on
+    the unscaled iterate) holds at a check, or max_iter; with `scaling` Ruiz
+    iterations the ADMM runs on the scaled problem.  Returns the unscaled
+    (x, z, y, iterations)."""
+    if scaling:
+        sq, D, E, c = ruiz(lq, scaling)
+        xs, zs, ys = x / D, E * z, c * y / E
+    else:
+        sq, D, E, c = lq, np.ones(len(x)), np.ones(len(z)), 1.0
+        xs, zs, ys = x, z, y
+    lu = sla.lu_factor(kkt_matrix(sq, sigma))
     it = 0
     while it < max_iter:
         step = min(check_every, max_iter - it)
-        x, z, y = iterate(lq, x, z, y, step, sigma=sigma, alpha=alpha, lu=lu)
+        xs, zs, ys = iterate(sq, xs, zs, ys, step, sigma=sigma, alpha=alpha, lu=lu)
         it += step
-        rp, rd, sp, sd = residuals(lq, x, z, y)
+        rp, rd, sp, sd = residuals(lq, D * xs, zs / E, E * ys / c)
         if rp <= eps_abs + eps_rel * sp and rd <= eps_abs + eps_rel * sd:
             break
-    return x, z, y, it
+    return D * xs, zs / E, E * ys / c, it
 
 
 def literal_agent(m: dict, x0, cmd, phase, qd_meas, iters: int, *, rho: float = 0.1, sigma: float = 1e-6,
-                  alpha: float = 1.6):
+                  alpha: float = 1.6, scaling: int = 0):
     """Alg. 1 for one agent with a fixed N_QP = iters: f_init, f_param, the
-    KKT system, one factorisation, iters OSQP iterations, the torque map of
-    the last iterate (line search alpha = 1)."""
+    KKT system, `scaling` Ruiz iterations (f_Ruiz), one factorisation, iters
+    OSQP iterations, the torque map of the last iterate (line search
+    alpha = 1)."""
     x0 = np.asarray(x0, float)
     qp, ex = qpmod.agent_qp(m, x0, cmd, phase)
     lq = literal_form(qp, rho)
     x, z, y = start_point(lq, qp, x0, np.asarray(m["q_nom"], float))
-    x, z, y = iterate(lq, x, z, y, iters, sigma=sigma, alpha=alpha)
+    if scaling:
+        sq, D, E, c = ruiz(lq, scaling)
+        xs, zs, ys = iterate(sq, x / D, E * z, np.zeros_like(y), iters, sigma=sigma, alpha=alpha)
+        x, z, y = D * xs, zs / E, E * ys / c
+    else:
+        x, z, y = iterate(lq, x, z, y, iters, sigma=sigma, alpha=alpha)
     N = qp.N
     u = np.stack([qp.u(x, k) for k in range(N)])
     xs = np.vstack([x0[None, :]] + [qp.x(x, k)[None, :] for k in range(1, N + 1)])

@@ -105,7 +105,14 @@ struct Arena {
   float* lL;              // [A][maxN*LDL_REC]
   float* lw;              // [A][maxN*LDL_W]
   float* ly;              // [A][maxN*VS]
+  float* lS;              // [A][maxN*LDL_S] Ruiz scaling per stage (D of u_k and x_{k+1}, E of the
+                          //   dynamics and inequality rows) and its per-iteration factors
+  float* lc;              // [A] Ruiz cost scale c
 };
+// Ruiz scaling record of one stage (floats): D of u_k at LS_DU, of x_{k+1} at
+// LS_DX, E of the stage's dynamics rows at LS_ED and of its 56 inequality rows
+// at LS_EI; LS_T + the same offsets: one iteration's factors
+enum : int { LS_DU = 0, LS_DX = 32, LS_ED = 64, LS_EI = 96, LS_T = 160, LDL_S = 320 };
 // literal-form record of one stage: 90 block variables (u_k, the stage's 30
 // dynamics multipliers, x_{k+1}); the strictly lower L without its
 // structurally zero block (the x_{k+1} rows against the u_k columns), packed
@@ -146,6 +153,7 @@ struct SolverParams {
   int spin_limit;  // polls of a bounded mbarrier wait before it gives up (MPC_AGENT_TIMEOUT)
   int wait_test_slot;  // failure-detection test: the first stage-block wait of this agent slot is
                        //   armed with no copy behind it, so it runs out (-1: off)
+  int ruiz;            // literal form: Ruiz equilibration iterations (0: none)
   int defer;           // fused form: 1 = an agent whose polish first fails ends DEFERRED once its
                        //   ADMM warm start is written (no ADMM in this launch); 2 = an agent whose
                        //   polish first has not passed after 2 reduced solves ends DEFERRED with

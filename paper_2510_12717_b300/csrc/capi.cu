@@ -151,7 +151,7 @@ static size_t arena_bytes(size_t A, size_t n) {
 // vectors, dynamics multipliers)
 static size_t ldl_bytes(size_t A, size_t n) {
   using namespace mpc;
-  return A * n * (size_t)(LDL_REC + LDL_W + VS) * 4;
+  return A * n * (size_t)(LDL_REC + LDL_W + VS + LDL_S) * 4 + A * 4;
 }
 
 extern "C" {
@@ -184,6 +184,7 @@ mpc_status mpc_default_config(mpc_config* cfg) {
   cfg->refine_steps = -1;
   cfg->spin_limit = mpc::kSpinLimit;
   cfg->wait_test_agent = -1;
+  cfg->ruiz_iters = 0;
   return MPC_OK;
 }
 
@@ -199,6 +200,7 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
     return MPC_ERR_INVALID;
   if (cfg->form != MPC_FORM_PLAIN && cfg->form != MPC_FORM_FUSED && cfg->form != MPC_FORM_LDL)
     return MPC_ERR_INVALID;
+  if (cfg->ruiz_iters < 0 || cfg->ruiz_iters > 50) return MPC_ERR_INVALID;
   if (!(cfg->rho0 > 0.f) || !(cfg->sigma > 0.f) || !(cfg->alpha > 0.f && cfg->alpha < 2.f) ||
       !(cfg->eps_abs >= 0.f) || !(cfg->eps_rel >= 0.f) || cfg->max_iter <= 0 || cfg->fixed_iters < 0 ||
       cfg->graph < 0 || cfg->graph > 1 ||
@@ -276,6 +278,8 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
     AL(a.lL, A * n * LDL_REC);
     AL(a.lw, A * n * LDL_W);
     AL(a.ly, A * n * VS);
+    AL(a.lS, A * n * LDL_S);
+    AL(a.lc, A);
   }
 #undef AL
   if (e != cudaSuccess) {
@@ -543,6 +547,7 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   p.spin_limit = c.spin_limit;
   p.wait_test_slot = c.wait_test_agent;
   p.defer = 0;
+  p.ruiz = c.ruiz_iters;
   return p;
 }
 

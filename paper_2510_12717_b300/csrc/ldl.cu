@@ -173,27 +173,38 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
   const float rho = *ap.rho, rho_eq = 1e3f * rho;
   const int l = lane < 30 ? lane : 29;   // lanes 30, 31 shadow row 29 (their results are unused)
   float* rec0 = a.lL + (size_t)slot * a.maxN * LDL_REC;
+  // Ruiz scaling (all ones without equilibration): the factor is that of the
+  // scaled system, P -> c D P D, A -> E A D
+  const float* S0 = a.lS + (size_t)slot * a.maxN * LDL_S;
+  const float cs = a.lc[slot];
   float mrow[30];                        // row l of A_k X_{k-1} A_k^T (0 at k = 0)
 #pragma unroll
   for (int c = 0; c < 30; ++c) mrow[c] = 0.f;
   for (int k = 0; k < N; ++k) {
     float* rec = rec0 + (size_t)k * LDL_REC;
     const float* cls = ap.rcls + k * RS;
+    const float* Sk = S0 + (size_t)k * LDL_S;
+    const float du = Sk[LS_DU + l], dx = Sk[LS_DX + l], ed = Sk[LS_ED + l];
+    const float* ei = Sk + LS_EI;
     // ---- A11 = R_t: diagonal, and the pyramid couplings of row f_z of a foot
     float av[30];
 #pragma unroll
     for (int c = 0; c < 30; ++c) av[c] = 0.f;
     {
-      float dg = 2.f * dt * md[M_R + l] + sigma + rho * cls[l < 12 ? l : l + 8];
+      const int ru = l < 12 ? l : l + 8;
+      float dg = cs * du * du * 2.f * dt * md[M_R + l] + sigma + rho * cls[ru] * (ei[ru] * du) * (ei[ru] * du);
       if (l < 12 && (l % 6) < 3) {
-        const int f = l / 6, cc = l - 6 * f, p = 12 + 4 * f;
-        const float r0 = rho * cls[p], r1 = rho * cls[p + 1], r2 = rho * cls[p + 2], r3 = rho * cls[p + 3];
-        dg += cc == 0 ? r0 + r1 : (cc == 1 ? r2 + r3 : mu * mu * (r0 + r1 + r2 + r3));
+        const int f = l / 6, cc = l - 6 * f, p = 12 + 4 * f, b0 = 6 * f;
+        float w[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) w[t] = rho * cls[p + t] * ei[p + t] * ei[p + t];
+        dg += du * du * (cc == 0 ? w[0] + w[1] : (cc == 1 ? w[2] + w[3] : mu * mu * (w[0] + w[1] + w[2] + w[3])));
         if (cc == 2) {
+          const float db0 = Sk[LS_DU + b0], db1 = Sk[LS_DU + b0 + 1];
 #pragma unroll
           for (int c = 0; c < 12; ++c) {
-            if (c == l - 2) av[c] = mu * (r1 - r0);
-            if (c == l - 1) av[c] = mu * (r3 - r2);
+            if (c == l - 2) av[c] = mu * (w[1] - w[0]) * db0 * du;
+            if (c == l - 1) av[c] = mu * (w[3] - w[2]) * db1 * du;
           }
         }
       }
@@ -201,7 +212,10 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
       for (int c = 0; c < 30; ++c)
         if (c == l) av[c] = dg;
     }
-    const float q33 = 2.f * dt * md[M_Q + l] + sigma + (l >= 12 ? rho * cls[l + 26] : 0.f);
+    const float q33 = cs * dx * dx * 2.f * dt * md[M_Q + l] + sigma +
+                      (l >= 12 ? rho * cls[l + 26] * (ei[l + 26] * dx) * (ei[l + 26] * dx) : 0.f);
+    const float a32 = ed * dx;           // the x_{k+1} entry of dynamics row l, scaled
+    const float ed1 = k + 1 < N ? Sk[LDL_S + LS_ED + l] : 1.f;   // E of the next stage's dynamics row l
     float dd0 = 1.f, dd1 = 1.f, dd2 = 1.f;
     // ---- the three groups in turn: factor the (updated) diagonal block,
     // store its rows, solve the next off-diagonal block's rows against it
@@ -219,7 +233,8 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
       float y[30];
 #pragma unroll
       for (int c = 0; c < 30; ++c)
-        y[c] = g == 0 ? -b_entry(lin, dt, l, c) : (g == 1 ? (c == l ? 1.f : 0.f) : a_entry(lin, k + 1, l, c));
+        y[c] = g == 0 ? -b_entry(lin, dt, l, c) * ed * __shfl_sync(FULL, du, c)
+                      : (g == 1 ? (c == l ? a32 : 0.f) : a_entry(lin, k + 1, l, c) * ed1 * __shfl_sync(FULL, dx, c));
       trsv_rows(y, av);
       float ys[30];
 #pragma unroll
@@ -264,6 +279,136 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
       rec[LDL_IND + 60 + l] = 1.f / dd2;
     }
   }
+}
+
+// ------------------------------------------------------------------ Ruiz (f_Ruiz)
+// OSQP's modified Ruiz equilibration of the KKT matrix [[P, A^T], [A, 0]]
+// (Stellato et al. 2020, Sec. 5.1), stage by stage: each iteration divides
+// every variable's and row's column by the square root of its inf-norm in the
+// currently scaled matrix (below 1e-4 counted as 1, above 1e4 as 1e4), then
+// scales the cost by 1 / max(mean column inf-norm of P, |q|_inf).  A column
+// of u_k meets P, the stage's dynamics rows (through B) and its box and
+// pyramid rows; one of x_{k+1} meets P, the stage's dynamics rows (identity),
+// the next stage's (through A_{k+1}) and its joint box; a dynamics row meets
+// x_{k+1}, u_k and (k >= 1) x_k.  One warp per agent; A_base and B (signed,
+// 30 x 30 with the arms) in shared memory.
+__device__ __forceinline__ float ruiz_lim(float v) { return v < 1e-4f ? 1.f : fminf(v, 1e4f); }
+
+__global__ void __launch_bounds__(32) mpc_k_ldl_ruiz(Arena a, Batch b, SolverParams prm) {
+  const int lane = threadIdx.x;
+  const int row = blockIdx.x;
+  if (!live_row(a, b, row)) return;
+  const int slot = b.ids[row];
+  const AgentPtrs ap = agent_ptrs(a, slot);
+  if (ap.st[T_STATUS] == MPC_AGENT_NAN_) return;
+  extern __shared__ __align__(16) float rsm[];
+  float* sA = rsm;                  // A_base (rows of stride 31)
+  float* sB = rsm + 30 * 31;        // B
+  const float* md = ap.mdl;
+  const float* lin = ap.lin;
+  const int N = ap.N;
+  const float dt = md[M_DT], mu = md[M_MU];
+  float* S0 = a.lS + (size_t)slot * a.maxN * LDL_S;
+  for (int k = 0; k < N; ++k)
+    for (int t = lane; t < LS_T; t += 32) S0[(size_t)k * LDL_S + t] = 1.f;
+  if (prm.ruiz <= 0) {        // no equilibration: every factor 1
+    if (lane == 0) a.lc[slot] = 1.f;
+    return;
+  }
+  for (int t = lane; t < 900; t += 32) {
+    const int r = t / 30, c = t - 30 * r;
+    sA[r * 31 + c] = r < NC ? (c < NC ? lin[L_ABASE + c * LDD + r] : 0.f) : (c == r ? 1.f : 0.f);
+    sB[r * 31 + c] = b_entry(lin, dt, r, c);
+  }
+  __syncwarp();
+  // entry (r, c) of A_k: A_base plus the stage's leg-joint block dA_k
+  auto ak = [&](int k, int r, int c) {
+    float v = sA[r * 31 + c];
+    if (r >= 9 && r < 12 && c >= 12 && c < NC) v += lin[L_STAGE + k * 64 + (r - 9) * 10 + (c - 12)];
+    return v;
+  };
+  float cs = 1.f;
+  const int j = lane < 30 ? lane : 29;
+  const float Ru = 2.f * dt * md[M_R + j], Qx = 2.f * dt * md[M_Q + j];
+  for (int it = 0; it < prm.ruiz; ++it) {
+    // ---- pass 1: the inf-norms of the current scaled matrix -> the factors
+    for (int k = 0; k < N; ++k) {
+      float* Sk = S0 + (size_t)k * LDL_S;
+      const float* Sn = k + 1 < N ? Sk + LDL_S : nullptr;
+      const float* Sp = k ? Sk - LDL_S : nullptr;
+      const float* cls = ap.rcls + k * RS;
+      if (lane < 30) {
+        // column u_k,j
+        const float du = Sk[LS_DU + j];
+        float m = 0.f;
+        for (int i = 0; i < 30; ++i) m = fmaxf(m, Sk[LS_ED + i] * fabsf(sB[i * 31 + j]));
+        const int ru = j < 12 ? j : j + 8;
+        if (cls[ru] > 0.f) m = fmaxf(m, Sk[LS_EI + ru]);
+        if (j < 12 && (j % 6) < 3) {
+          const int f = j / 6, cc = j - 6 * f, p = 12 + 4 * f;
+          for (int t = 0; t < 4; ++t)
+            if (cls[p + t] > 0.f) m = fmaxf(m, Sk[LS_EI + p + t] * fabsf(pyr_coef(cc, t, mu)));
+        }
+        const float colu = fmaxf(cs * du * du * Ru, du * m);
+        // column x_{k+1},j
+        const float dx = Sk[LS_DX + j];
+        m = Sk[LS_ED + j];
+        if (Sn)
+          for (int i = 0; i < 30; ++i) m = fmaxf(m, Sn[LS_ED + i] * fabsf(ak(k + 1, i, j)));
+        if (j >= 12 && cls[j + 26] > 0.f) m = fmaxf(m, Sk[LS_EI + j + 26]);
+        const float colx = fmaxf(cs * dx * dx * Qx, dx * m);
+        // dynamics row k, j: x_{k+1} - A_k x_k - B u_k
+        m = Sk[LS_DX + j];
+        for (int c = 0; c < 30; ++c) m = fmaxf(m, Sk[LS_DU + c] * fabsf(sB[j * 31 + c]));
+        if (Sp)
+          for (int c = 0; c < 30; ++c) m = fmaxf(m, Sp[LS_DX + c] * fabsf(ak(k, j, c)));
+        const float rowd = Sk[LS_ED + j] * m;
+        Sk[LS_T + LS_DU + j] = rsqrtf(ruiz_lim(colu));
+        Sk[LS_T + LS_DX + j] = rsqrtf(ruiz_lim(colx));
+        Sk[LS_T + LS_ED + j] = rsqrtf(ruiz_lim(rowd));
+      }
+      // inequality rows of the stage
+      for (int h = 0; h < 2; ++h) {
+        const int r = lane + 32 * h;
+        if (r >= NR) break;
+        float e = 1.f;
+        if (cls[r] > 0.f) {
+          float m;
+          if (r < 12) m = Sk[LS_DU + r];
+          else if (r < 20) {
+            const int f = (r - 12) >> 2, t = (r - 12) & 3, b0 = 6 * f;
+            m = fmaxf(Sk[LS_DU + b0 + (t < 2 ? 0 : 1)], mu * Sk[LS_DU + b0 + 2]);
+          } else if (r < 38) m = Sk[LS_DU + r - 8];
+          else m = Sk[LS_DX + r - 26];
+          e = rsqrtf(ruiz_lim(Sk[LS_EI + r] * m));
+        }
+        Sk[LS_T + LS_EI + r] = e;
+      }
+    }
+    __syncwarp();
+    // ---- pass 2: apply them; then the cost scale
+    float sum_p = 0.f, q_max = 0.f;
+    for (int k = 0; k < N; ++k) {
+      float* Sk = S0 + (size_t)k * LDL_S;
+      if (lane < 30) {
+        Sk[LS_DU + j] *= Sk[LS_T + LS_DU + j];
+        Sk[LS_DX + j] *= Sk[LS_T + LS_DX + j];
+        Sk[LS_ED + j] *= Sk[LS_T + LS_ED + j];
+        const float du = Sk[LS_DU + j], dx = Sk[LS_DX + j];
+        sum_p += cs * (du * du * Ru + dx * dx * Qx);
+        q_max = fmaxf(q_max, cs * fmaxf(fabsf(du * Ru * ap.uref[k * VS + j]), fabsf(dx * Qx * ap.xref[(k + 1) * VS + j])));
+      }
+      for (int h = 0; h < 2; ++h) {
+        const int r = lane + 32 * h;
+        if (r < NR) Sk[LS_EI + r] *= Sk[LS_T + LS_EI + r];
+      }
+    }
+    const float mean_p = warp_sum(sum_p) / (60.f * N);
+    const float g = 1.f / ruiz_lim(fmaxf(mean_p, warp_max(q_max)));
+    cs *= g;
+    __syncwarp();
+  }
+  if (lane == 0) a.lc[slot] = cs;
 }
 
 // ------------------------------------------------------------------ solves
@@ -345,26 +490,39 @@ __device__ __forceinline__ void stage_drain(Stager& sg) {
 
 struct LdlRes { float rp, rd, sp, sd; };
 
-// OSQP's residuals of the iterate: primal |A x - z|, dual |P x + q + A^T y|
-// (inf-norms) and their scales max(|A x|, |z|), max(|P x|, |A^T y|, |q|)
-__device__ LdlRes ldl_residuals(const AgentPtrs& ap, const float* ly, float* xv, int lane) {
+// OSQP's residuals of the unscaled iterate (x = D x_s, z = z_s / E,
+// y = E y_s / c): primal |A x - z|, dual |P x + q + A^T y| (inf-norms) and
+// their scales max(|A x|, |z|), max(|P x|, |A^T y|, |q|).  xv: 160 floats of
+// shared scratch (u_k, x_{k+1}, x_k, the dynamics multipliers of stages k, k+1).
+__device__ __noinline__ LdlRes ldl_residuals(const AgentPtrs& ap, const float* ly, const float* S0, float cs, float* xv,
+                                int lane) {
   const int N = ap.N;
   const float* md = ap.mdl;
   const float* lin = ap.lin;
   const float dt = md[M_DT], mu = md[M_MU];
+  const float ic = 1.f / cs;
   LdlRes r{0.f, 0.f, 0.f, 0.f};
   float* U = xv;          // u_k
   float* X = xv + 32;     // x_{k+1}
+  float* XP = xv + 64;    // x_k
+  float* Y0 = xv + 96;    // dynamics multipliers of stage k
+  float* Y1 = xv + 128;   // ... of stage k + 1
   for (int k = 0; k < N; ++k) {
-    U[lane] = ap.u[k * VS + lane];
-    X[lane] = ap.x[(k + 1) * VS + lane];
+    const float* Sk = S0 + (size_t)k * LDL_S;
+    const int c30 = lane < 30 ? lane : 29;
+    U[lane] = Sk[LS_DU + c30] * ap.u[k * VS + lane];
+    X[lane] = Sk[LS_DX + c30] * ap.x[(k + 1) * VS + lane];
+    XP[lane] = k ? Sk[LS_DX - LDL_S + c30] * ap.x[k * VS + lane] : ap.x[lane];
+    Y0[lane] = Sk[LS_ED + c30] * ly[k * VS + lane] * ic;
+    Y1[lane] = k + 1 < N ? Sk[LDL_S + LS_ED + c30] * ly[(k + 1) * VS + lane] * ic : 0.f;
     __syncwarp();
+    const float* ei = Sk + LS_EI;
     if (lane < 30) {
       const int i = lane;
       // dynamics row i: x_{k+1} - A_k x_k - B u_k - c_k
       float ax = 0.f, bu = 0.f;
       for (int c = 0; c < 30; ++c) {
-        ax = fmaf(a_entry(lin, k, i, c), ap.x[k * VS + c], ax);
+        ax = fmaf(a_entry(lin, k, i, c), XP[c], ax);
         bu = fmaf(b_entry(lin, dt, i, c), U[c], bu);
       }
       // the row's A x and z in OSQP's terms (x_0 is data: at k = 0 its term
@@ -375,23 +533,22 @@ __device__ LdlRes ldl_residuals(const AgentPtrs& ap, const float* ly, float* xv,
       r.rp = fmaxf(r.rp, fabsf(axr - zr));
       r.sp = fmaxf(r.sp, fmaxf(fabsf(axr), fabsf(zr)));
       // stationarity of u_k and x_{k+1}
-      const float yk = ly[k * VS + i];
       float gu = 2.f * dt * md[M_R + i] * U[i], qu = -2.f * dt * md[M_R + i] * ap.uref[k * VS + i];
       float gx = 2.f * dt * md[M_Q + i] * X[i], qx = -2.f * dt * md[M_Q + i] * ap.xref[(k + 1) * VS + i];
-      float atu = 0.f, atx = yk;
-      for (int c = 0; c < 30; ++c) atu = fmaf(-b_entry(lin, dt, c, i), ly[k * VS + c], atu);
+      float atu = 0.f, atx = Y0[i];
+      for (int c = 0; c < 30; ++c) atu = fmaf(-b_entry(lin, dt, c, i), Y0[c], atu);
       if (k + 1 < N)
-        for (int c = 0; c < 30; ++c) atx = fmaf(-a_entry(lin, k + 1, c, i), ly[(k + 1) * VS + c], atx);
+        for (int c = 0; c < 30; ++c) atx = fmaf(-a_entry(lin, k + 1, c, i), Y1[c], atx);
       const float* cls = ap.rcls + k * RS;
       const float* yy = ap.y + k * RS;
       const int ru = i < 12 ? i : i + 8;
-      if (cls[ru] > 0.f) atu += yy[ru];
+      if (cls[ru] > 0.f) atu += ei[ru] * yy[ru] * ic;
       if (i < 12 && (i % 6) < 3) {
         const int f = i / 6, c = i - 6 * f, p = 12 + 4 * f;
         for (int t = 0; t < 4; ++t)
-          if (cls[p + t] > 0.f) atu = fmaf(pyr_coef(c, t, mu), yy[p + t], atu);
+          if (cls[p + t] > 0.f) atu = fmaf(pyr_coef(c, t, mu), ei[p + t] * yy[p + t] * ic, atu);
       }
-      if (i >= 12 && cls[i + 26] > 0.f) atx += yy[i + 26];
+      if (i >= 12 && cls[i + 26] > 0.f) atx += ei[i + 26] * yy[i + 26] * ic;
       r.rd = fmaxf(r.rd, fmaxf(fabsf(gu + qu + atu), fabsf(gx + qx + atx)));
       r.sd = fmaxf(r.sd, fmaxf(fmaxf(fabsf(gu), fabsf(gx)), fmaxf(fmaxf(fabsf(atu), fabsf(atx)),
                                                                    fmaxf(fabsf(qu), fabsf(qx)))));
@@ -400,7 +557,7 @@ __device__ LdlRes ldl_residuals(const AgentPtrs& ap, const float* ly, float* xv,
     for (int h = 0; h < 2; ++h) {
       const int rr = lane + 32 * h;
       if (rr < NR && ap.rcls[k * RS + rr] > 0.f) {
-        const float cz = row_value(rr, U, X, mu), z = ap.w[k * RS + rr];
+        const float cz = row_value(rr, U, X, mu), z = ap.w[k * RS + rr] / ei[rr];
         r.rp = fmaxf(r.rp, fabsf(cz - z));
         r.sp = fmaxf(r.sp, fmaxf(fabsf(cz), fabsf(z)));
       }
@@ -420,21 +577,33 @@ __device__ LdlRes ldl_residuals(const AgentPtrs& ap, const float* ly, float* xv,
 // x_i (the joint box).
 struct FIn {
   float u, ur, x, xr, yl, ck;
-  float cr, zr, yr;             // box row of u_i
-  float cq, zq, yq;             // joint box of x_i
-  float cp[4], zp[4], yp[4], kp[4];
+  float du, dx, ed;             // scaling of u_i, x_i and dynamics row i
+  float cr, zr, yr, er;         // box row of u_i (class, slack, multiplier, scaling)
+  float cq, zq, yq, eq;         // joint box of x_i
+  float cp[4], zp[4], yp[4], kp[4], ep[4];
 };
-__device__ __forceinline__ FIn load_fin(const AgentPtrs& ap, const float* ly, int k, int lane) {
+// SC: the problem is Ruiz-scaled (otherwise every scaling factor is 1 and none is loaded)
+template <bool SC>
+__device__ __forceinline__ FIn load_fin(const AgentPtrs& ap, const float* ly, const float* S0, int k, int lane) {
   FIn f;
   f.u = f.ur = f.x = f.xr = f.yl = f.ck = 0.f;
+  f.du = f.dx = f.ed = 1.f;
   f.cr = f.zr = f.yr = f.cq = f.zq = f.yq = 0.f;
+  f.er = f.eq = 1.f;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) f.cp[q] = f.zp[q] = f.yp[q] = f.kp[q] = 0.f;
+  for (int q = 0; q < 4; ++q) { f.cp[q] = f.zp[q] = f.yp[q] = f.kp[q] = 0.f; f.ep[q] = 1.f; }
   if (lane < 30) {
     const int i = lane;
     const float* cls = ap.rcls + k * RS;
     const float* zz = ap.w + k * RS;
     const float* yy = ap.y + k * RS;
+    const float* Sk = S0 + (size_t)k * LDL_S;
+    const float* ei = Sk + LS_EI;
+    if (SC) {
+      f.du = Sk[LS_DU + i];
+      f.dx = Sk[LS_DX + i];
+      f.ed = Sk[LS_ED + i];
+    }
     f.u = ap.u[k * VS + i];
     f.ur = ap.uref[k * VS + i];
     f.x = ap.x[(k + 1) * VS + i];
@@ -443,13 +612,15 @@ __device__ __forceinline__ FIn load_fin(const AgentPtrs& ap, const float* ly, in
     f.ck = i < NC ? ap.lin[L_STAGE + k * 64 + 32 + i] : 0.f;
     const int ru = i < 12 ? i : i + 8;
     f.cr = cls[ru]; f.zr = zz[ru]; f.yr = yy[ru];
-    if (i >= 12) { f.cq = cls[i + 26]; f.zq = zz[i + 26]; f.yq = yy[i + 26]; }
+    if (SC) f.er = ei[ru];
+    if (i >= 12) { f.cq = cls[i + 26]; f.zq = zz[i + 26]; f.yq = yy[i + 26]; if (SC) f.eq = ei[i + 26]; }
     if (i < 12 && (i % 6) < 3) {
       const int ff = i / 6, c = i - 6 * ff, p = 12 + 4 * ff;
       const float mu = ap.mdl[M_MU];
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         f.cp[q] = cls[p + q]; f.zp[q] = zz[p + q]; f.yp[q] = yy[p + q]; f.kp[q] = pyr_coef(c, q, mu);
+        if (SC) f.ep[q] = ei[p + q];
       }
     }
   }
@@ -458,11 +629,22 @@ __device__ __forceinline__ FIn load_fin(const AgentPtrs& ap, const float* ly, in
 // Backward pass: the forward vector w_k, the iterate, the dynamics
 // multiplier, and slack, multiplier, class and bounds of rows lane and lane + 32.
 struct BIn {
-  float w0, w1, w2, u, x, yl;
-  float c0, z0, y0, lo0, hi0, c1, z1, y1, lo1, hi1;
+  float w0, w1, w2, u, x, yl, du, dx;
+  float c0, z0, y0, lo0, hi0, e0, c1, z1, y1, lo1, hi1, e1;
 };
-__device__ __forceinline__ BIn load_bin(const AgentPtrs& ap, const float* ly, const float* lw, int k, int lane) {
+template <bool SC>
+__device__ __forceinline__ BIn load_bin(const AgentPtrs& ap, const float* ly, const float* lw, const float* S0,
+                                        int k, int lane) {
   BIn b;
+  b.du = b.dx = b.e0 = b.e1 = 1.f;
+  if (SC) {
+    const float* Sk = S0 + (size_t)k * LDL_S;
+    const int c30 = lane < 30 ? lane : 29;
+    b.du = Sk[LS_DU + c30];
+    b.dx = Sk[LS_DX + c30];
+    b.e0 = Sk[LS_EI + lane];
+    b.e1 = lane + 32 < NR ? Sk[LS_EI + lane + 32] : 1.f;
+  }
   b.w0 = lw[k * LDL_W + lane];
   b.w1 = lw[k * LDL_W + lane + 32];
   b.w2 = lane < NB - 64 ? lw[k * LDL_W + lane + 64] : 0.f;
@@ -481,7 +663,8 @@ __device__ __forceinline__ BIn load_bin(const AgentPtrs& ap, const float* ly, co
   return b;
 }
 
-constexpr int W_ADMM = 2 * BUF_FLOATS + 96 + 64 + 32 + 4;   // shared floats of the one warp of a block
+constexpr int W_ADMM = 2 * BUF_FLOATS + 96 + 160 + 32 + 4;   // shared floats of the one warp of a block
+template <bool SC>
 __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverParams prm) {
   const int lane = threadIdx.x;
   const int row = blockIdx.x;
@@ -491,8 +674,8 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
   if (ap.st[T_STATUS] == MPC_AGENT_NAN_) return;
   extern __shared__ __align__(16) float asm_[];
   float* rb = asm_ + 2 * BUF_FLOATS;    // the stage's 90-vector, by block index
-  float* xv = rb + 96;                  // residual scratch (u_k, x_{k+1})
-  float* cv = xv + 64;                  // coupling vector: x part of w_{k-1} / multiplier part of v_{k+1}
+  float* xv = rb + 96;                  // scratch: the unscaled stage vectors (updates, residuals)
+  float* cv = xv + 160;                 // coupling vector: x part of w_{k-1} / multiplier part of v_{k+1}
   Stager sg;
   sg.buf[0] = asm_;
   sg.buf[1] = asm_ + BUF_FLOATS;
@@ -522,6 +705,21 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
   if (lane < 30)
     for (int c = 0; c < 30; ++c) a0x0 = fmaf(a_entry(lin, 0, i, c), ap.inp[I_X0 + c], a0x0);
   for (int k = 0; k < N; ++k) ly[k * VS + lane] = 0.f;
+  // the iterations run on the Ruiz-scaled problem (all ones without it): the
+  // f_init start scaled in, x_s = D^-1 x, z_s = E z (y = 0)
+  const float* S0 = a.lS + (size_t)slot * a.maxN * LDL_S;
+  const float cs = SC ? a.lc[slot] : 1.f;
+  for (int k = 0; SC && k < N; ++k) {
+    const float* Sk = S0 + (size_t)k * LDL_S;
+    if (lane < 30) {
+      ap.u[k * VS + lane] /= Sk[LS_DU + lane];
+      ap.x[(k + 1) * VS + lane] /= Sk[LS_DX + lane];
+    }
+    for (int h = 0; h < 2; ++h) {
+      const int r = lane + 32 * h;
+      if (r < NR && ap.rcls[k * RS + r] > 0.f) ap.w[k * RS + r] *= Sk[LS_EI + r];
+    }
+  }
   __syncwarp();
   const bool fixed = prm.fixed_iters > 0;
   const int max_it = fixed ? prm.fixed_iters : prm.max_iter;
@@ -534,22 +732,23 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
     const bool last = it == max_it;
     // ---- forward pass: b_k (+ G_k w_{k-1,x}), w_k = L_k^-1 b_k; the
     // stage's global inputs are loaded one stage ahead
-    FIn fin = load_fin(ap, ly, 0, lane);
+    FIn fin = load_fin<SC>(ap, ly, S0, 0, lane);
     for (int k = 0; k < N; ++k) {
       const int t = k, bcur = t & 1;
       stage_issue(sg, bcur ^ 1, rec0, N, t + 1, lane);
       const FIn f = fin;
-      if (k + 1 < N) fin = load_fin(ap, ly, k + 1, lane);
+      if (k + 1 < N) fin = load_fin<SC>(ap, ly, S0, k + 1, lane);
       float bu = 0.f, bl = 0.f, bx = 0.f;
       if (lane < 30) {
-        bu = sigma * f.u + Ru * f.ur;
-        if (f.cr > 0.f) bu += rho * f.cr * f.zr - f.yr;
+        // sigma x_s - q_s + C_s^T (rho z_s - y_s), q_s = c D q, C_s = E C D
+        bu = sigma * f.u + cs * f.du * Ru * f.ur;
+        if (f.cr > 0.f) bu += f.du * f.er * (rho * f.cr * f.zr - f.yr);
 #pragma unroll
         for (int q = 0; q < 4; ++q)
-          if (f.cp[q] > 0.f) bu = fmaf(f.kp[q], rho * f.cp[q] * f.zp[q] - f.yp[q], bu);
-        bl = f.ck + (k ? 0.f : a0x0) - f.yl / rho_eq;
-        bx = sigma * f.x + Qx * f.xr;
-        if (f.cq > 0.f) bx += rho * f.cq * f.zq - f.yq;
+          if (f.cp[q] > 0.f) bu = fmaf(f.kp[q] * f.du * f.ep[q], rho * f.cp[q] * f.zp[q] - f.yp[q], bu);
+        bl = f.ed * (f.ck + (k ? 0.f : a0x0)) - f.yl / rho_eq;
+        bx = sigma * f.x + cs * f.dx * Qx * f.xr;
+        if (f.cq > 0.f) bx += f.dx * f.eq * (rho * f.cq * f.zq - f.yq);
       }
       stage_wait(sg, bcur);
       if (sg.dead) break;
@@ -578,14 +777,14 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
     if (sg.dead) break;
     // ---- backward pass: v_k = L_k^-T (D_k^-1 w_k + G_{k+1}^T v_{k+1,mult}),
     // then the stage's update; inputs one stage ahead
-    BIn bin = load_bin(ap, ly, lw, N - 1, lane);
+    BIn bin = load_bin<SC>(ap, ly, lw, S0, N - 1, lane);
     for (int k = N - 1; k >= 0; --k) {
       const int t = 2 * N - 1 - k, bcur = t & 1;
       // the next item: this iteration's next stage, or the next iteration's first
       if (t + 1 < T) stage_issue(sg, bcur ^ 1, rec0, N, t + 1, lane);
       else if (!last) stage_issue(sg, bcur ^ 1, rec0, N, 0, lane);
       const BIn q = bin;
-      if (k >= 1) bin = load_bin(ap, ly, lw, k - 1, lane);
+      if (k >= 1) bin = load_bin<SC>(ap, ly, lw, S0, k - 1, lane);
       stage_wait(sg, bcur);
       if (sg.dead) break;
       const float* buf = sg.buf[bcur];
@@ -617,16 +816,21 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
         // dynamics rows (z = l = u always): zr - z = alpha (nu - y) / rho_eq
         ly[k * VS + i] = (1.f - alpha) * q.yl + alpha * nu;
       }
+      // the rows' z~ = E C D x~: the stage's x~ times D
+      xv[lane] = lane < 30 ? q.du * rb[lane] : 0.f;
+      xv[32 + lane] = lane < 30 ? q.dx * rb[60 + lane] : 0.f;
+      __syncwarp();
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int rr = lane + 32 * h;
         const float cl = h ? q.c1 : q.c0;
         if (rr < NR && cl > 0.f) {
           const float rr_rho = rho * cl;
-          const float zt = row_value(rr, rb, rb + 60, mu);
+          const float er = h ? q.e1 : q.e0;
+          const float zt = er * row_value(rr, xv, xv + 32, mu);
           const float zo = h ? q.z1 : q.z0, yo = h ? q.y1 : q.y0;
           const float zh = alpha * zt + (1.f - alpha) * zo;
-          const float zn = fminf(fmaxf(zh + yo / rr_rho, h ? q.lo1 : q.lo0), h ? q.hi1 : q.hi0);
+          const float zn = fminf(fmaxf(zh + yo / rr_rho, er * (h ? q.lo1 : q.lo0)), er * (h ? q.hi1 : q.hi0));
           ap.y[k * RS + rr] = yo + rr_rho * (zh - zn);
           ap.w[k * RS + rr] = zn;
         }
@@ -636,7 +840,7 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
     if (sg.dead) break;
     const bool check = !fixed && (it % every == 0 || last);
     if (check || (fixed && last)) {
-      res = ldl_residuals(ap, ly, xv, lane);
+      res = ldl_residuals(ap, ly, S0, cs, xv, lane);
       if (!(isfinite(res.rp) && isfinite(res.rd))) { status = MPC_AGENT_NAN_; break; }
       if (check && res.rp <= prm.eps_abs + prm.eps_rel * res.sp && res.rd <= prm.eps_abs + prm.eps_rel * res.sd) {
         status = MPC_AGENT_INACCURATE_;   // ADMM's stopping test, no polish: not certified
@@ -651,6 +855,23 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
   }
   // copies issued for an iteration that did not run (a stop after a check)
   stage_drain(sg);
+  // the iterate scaled back: x = D x_s, z = z_s / E, y = E y_s / c
+  for (int k = 0; SC && k < N; ++k) {
+    const float* Sk = S0 + (size_t)k * LDL_S;
+    if (lane < 30) {
+      ap.u[k * VS + lane] *= Sk[LS_DU + lane];
+      ap.x[(k + 1) * VS + lane] *= Sk[LS_DX + lane];
+      ly[k * VS + lane] *= Sk[LS_ED + lane] / cs;
+    }
+    for (int h = 0; h < 2; ++h) {
+      const int r = lane + 32 * h;
+      if (r < NR && ap.rcls[k * RS + r] > 0.f) {
+        ap.w[k * RS + r] /= Sk[LS_EI + r];
+        ap.y[k * RS + r] *= Sk[LS_EI + r] / cs;
+      }
+    }
+  }
+  __syncwarp();
   // a non-finite iterate leaves no torques
   bool bad = false;
   for (int k = 0; k <= N; ++k) bad |= lane < 30 && !isfinite(ap.x[k * VS + lane]);
@@ -682,20 +903,28 @@ cudaError_t launch_ldl(const Arena& a, const Batch& b, const SolverParams& prm, 
     cudaError_t e = cudaFuncSetAttribute(mpc_k_ldl_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(F_FLOATS * sizeof(float)));
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mpc_k_ldl_admm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      e = cudaFuncSetAttribute(mpc_k_ldl_admm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)(W_ADMM * sizeof(float)));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mpc_k_ldl_admm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)(W_ADMM * sizeof(float)));
     // the iteration kernel's one-warp blocks hold about 40 KB of shared memory:
     // ask for the largest shared-memory carveout, so that five fit on an SM
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mpc_k_ldl_admm, cudaFuncAttributePreferredSharedMemoryCarveout,
+      e = cudaFuncSetAttribute(mpc_k_ldl_admm<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                               cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(mpc_k_ldl_admm<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     configured = dev;
   }
   if (b.n <= 0) return cudaSuccess;
+  mpc_k_ldl_ruiz<<<b.n, 32, 2 * 30 * 31 * sizeof(float), st>>>(a, b, prm);
   mpc_k_ldl_factor<<<b.n, 32, F_FLOATS * sizeof(float), st>>>(a, b, prm);
-  mpc_k_ldl_admm<<<b.n, 32, W_ADMM * sizeof(float), st>>>(a, b, prm);
-  if (launches) *launches += 2;
+  if (prm.ruiz > 0) mpc_k_ldl_admm<true><<<b.n, 32, W_ADMM * sizeof(float), st>>>(a, b, prm);
+  else mpc_k_ldl_admm<false><<<b.n, 32, W_ADMM * sizeof(float), st>>>(a, b, prm);
+  if (launches) *launches += 3;
   return cudaGetLastError();
 }
 

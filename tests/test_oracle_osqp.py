@@ -85,3 +85,39 @@ def test_kkt_solve_gives_z_tilde_equal_A_x_tilde():
     osqp.iterate(lq, x, z, y, 5, trace=tr)
     for (xt, zt, _, _, _) in tr:
         assert np.abs(lq.A @ xt - zt).max() <= 1e-7 * (1.0 + np.abs(zt).max())
+
+
+def test_ruiz_one_iteration_by_hand():
+    # P = diag(4, 1), q = (2, 0), A = [[2, 0]]: KKT column norms (4, 1) of
+    # the variables and 2 of the row, so D = (1/2, 1), E = 1/sqrt(2); then
+    # P = diag(1, 1), q = (1, 0), A = [[1/sqrt(2), 0]]; the cost scale is
+    # 1 / max(mean(1, 1), 1) = 1; bounds scale by E
+    lq = osqp.LiteralQP(P=np.diag([4.0, 1.0]), q=np.array([2.0, 0.0]), A=np.array([[2.0, 0.0]]),
+                        l=np.array([-1.0]), u=np.array([3.0]), rho=np.array([0.1]), n_dyn=0)
+    sq, D, E, c = osqp.ruiz(lq, 1)
+    r = 1.0 / np.sqrt(2.0)
+    assert np.allclose(D, [0.5, 1.0], atol=1e-15) and np.allclose(E, [r], atol=1e-15) and c == 1.0
+    assert np.allclose(sq.P, np.eye(2), atol=1e-15) and np.allclose(sq.q, [1.0, 0.0], atol=1e-15)
+    assert np.allclose(sq.A, [[r, 0.0]], atol=1e-15)
+    assert np.allclose([sq.l[0], sq.u[0]], [-r, 3 * r], atol=1e-15)
+
+
+def test_ruiz_equilibrates_and_keeps_the_optimum():
+    m, x0, qp = _agent_qp(5, 4)
+    lq = osqp.literal_form(qp, rho=0.1)
+    sq, D, E, c = osqp.ruiz(lq, 10)
+    # the scaled KKT matrix's columns have inf-norms near 1 (the unscaled ones
+    # spread over orders of magnitude)
+    def spread(l):
+        col = np.maximum(np.abs(l.P).max(axis=0), np.abs(l.A).max(axis=0))
+        row = np.abs(l.A).max(axis=1)
+        v = np.concatenate([col, row])
+        return v.max() / v.min()
+    assert spread(lq) > 100.0 and spread(sq) < 1.1
+    # the scaled problem has the same optimum, mapped back by D
+    x, z, y = osqp.start_point(lq, qp, x0, m["q_nom"])
+    xs, zs, ys, it = osqp.solve_until(sq, x / D, E * z, np.zeros_like(y), eps_abs=1e-12, eps_rel=1e-12,
+                                      max_iter=60000, check_every=50)
+    ref = ipm.solve_qp(qp.P, qp.q, qp.E, qp.e, qp.C, qp.lo, qp.hi)
+    scale = 1.0 + np.abs(ref.z).max()
+    assert np.abs(D * xs - ref.z).max() <= 1e-7 * scale, (it, np.abs(D * xs - ref.z).max())
