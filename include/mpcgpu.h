@@ -83,7 +83,7 @@ typedef enum {
                                   the same inputs.  DEFER_SLOW: the polish first had not
                                   passed after two reduced KKT solves; its corrected active
                                   set is kept: solve it again with no flag and the same
-                                  inputs, which continues from it */
+                                  inputs, which continues from it (likewise DEFER_COLD) */
 } mpc_agent_status;
 
 /* Precision of the Riccati factor's two dense 22 x 22 stage products per
@@ -274,6 +274,18 @@ mpc_status mpc_set_model(mpc_ctx* ctx, int32_t agent_id, const mpc_agent_model* 
 mpc_status mpc_set_trees(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host,
                          const mpc_tree_model* trees_host);
 
+/* mpc_set_models without waiting: the models are packed into the context's
+ * pinned host staging (allocated by the first call) and uploaded on `stream`
+ * (a cudaStream_t), and the call returns at once.  The upload is complete when
+ * that stream has reached the point after the call; until then no batch may
+ * solve these agents, and no further model upload (of either kind) may
+ * start, since both reuse the context's staging buffers.  For a caller that
+ * swaps agents while other batches run (the server's churn).  A call with
+ * n = 0 only allocates the staging (page-locking it takes milliseconds; the
+ * server does it when it is created).  Errors as mpc_set_models. */
+mpc_status mpc_set_models_async(mpc_ctx* ctx, int32_t n, const int32_t* agent_ids_host,
+                                const mpc_agent_model* models_host, void* stream);
+
 /* Remove an agent: its slot no longer accepts submissions. */
 mpc_status mpc_release_agent(mpc_ctx* ctx, int32_t agent_id);
 
@@ -311,7 +323,12 @@ mpc_status mpc_solve_on(mpc_ctx* ctx, uint64_t ticket, void* stream);
  * correction); an agent it has not solved by then ends MPC_AGENT_DEFERRED and
  * a solve without flags continues it (more corrections, then ADMM if needed),
  * with the same result as an uninterrupted solve. */
-typedef enum { MPC_SOLVE_DEFER_ADMM = 1, MPC_SOLVE_ADMM_ONLY = 2, MPC_SOLVE_DEFER_SLOW = 4 } mpc_solve_flags;
+typedef enum {
+  MPC_SOLVE_DEFER_ADMM = 1, MPC_SOLVE_ADMM_ONLY = 2, MPC_SOLVE_DEFER_SLOW = 4,
+  MPC_SOLVE_DEFER_COLD = 8   /* alone: DEFER_SLOW for cold agents (no warm start: a first
+                                solve, or one after a model swap); a warm agent is deferred
+                                only when its polish first fails; continue with no flag */
+} mpc_solve_flags;
 
 /* mpc_solve_on with flags (0 = mpc_solve_on).  MPC_ERR_INVALID for an
  * unknown flag or flags on a form other than FUSED. */
@@ -501,11 +518,14 @@ mpc_status mpc_server_create(mpc_ctx* ctx, int32_t pool, int32_t max_batch, int3
  * mpc_server_start).  Mode 1: batches are solved with MPC_SOLVE_DEFER_ADMM,
  * so an agent whose polish first fails does not hold its batch's answers
  * for the length of an ADMM solve; mode 2: with MPC_SOLVE_DEFER_SLOW, neither
- * does an agent that two reduced KKT solves of its polish do not settle.  The
- * worker keeps such agents (with their requests and states) and finishes them
- * (MPC_SOLVE_ADMM_ONLY, or no flag) in batches of their own on an extra lane,
- * answering their requests when those complete.  mpc_server_deferred gives
- * the number of agents deferred so far.  MPC_ERR_INVALID for another mode. */
+ * does an agent that two reduced KKT solves of its polish do not settle;
+ * mode 3: with MPC_SOLVE_DEFER_COLD, as mode 2 for cold agents (the first
+ * requests after a model swap) and as mode 1 for the others.  The worker keeps
+ * such agents (with their requests and states) and finishes them
+ * (MPC_SOLVE_ADMM_ONLY in mode 1, no flag otherwise) in batches of their own
+ * on an extra lane, answering their requests when those complete.
+ * mpc_server_deferred gives the number of agents deferred so far.
+ * MPC_ERR_INVALID for another mode. */
 mpc_status mpc_server_set_defer(mpc_server* srv, int32_t mode);
 int64_t mpc_server_deferred(mpc_server* srv);
 /* Starts the worker and the server's clock.  MPC_ERR_STATE if started. */

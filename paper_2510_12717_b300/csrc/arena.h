@@ -157,7 +157,8 @@ struct SolverParams {
   int defer;           // fused form: 1 = an agent whose polish first fails ends DEFERRED once its
                        //   ADMM warm start is written (no ADMM in this launch); 2 = an agent whose
                        //   polish first has not passed after 2 reduced solves ends DEFERRED with
-                       //   its corrected active set kept (a later solve continues from it)
+                       //   its corrected active set kept (a later solve continues from it); 3 = as
+                       //   2 for a cold agent, and a warm one when its polish first fails
 };
 
 }  // namespace mpc

@@ -80,6 +80,11 @@ struct mpc_ctx {
   float* d_mstage = nullptr;
   double* d_sstage = nullptr;
   int* d_hstage = nullptr;
+  // pinned host staging of mpc_set_models_async (allocated by its first call)
+  int* h_ids = nullptr;
+  float* h_mstage = nullptr;
+  double* h_sstage = nullptr;
+  int* h_hstage = nullptr;
   int* qorder = nullptr;             // per-ticket work-queue buffers [kMaxTickets][A]
   int* qcount = nullptr;             // per-ticket queue counters [kMaxTickets][8]
   GraphEntry graphs[kMaxGraphs];
@@ -304,6 +309,10 @@ mpc_status mpc_destroy(mpc_ctx* ctx) {
   for (auto& t : ctx->tickets)
     if (t.done) cudaEventDestroy(t.done);
   for (void* p : ctx->allocs) cudaFree(p);
+  cudaFreeHost(ctx->h_ids);
+  cudaFreeHost(ctx->h_mstage);
+  cudaFreeHost(ctx->h_sstage);
+  cudaFreeHost(ctx->h_hstage);
   delete ctx;
   return MPC_OK;
 }
@@ -422,6 +431,45 @@ mpc_status mpc_set_models(mpc_ctx* ctx, int32_t n, const int32_t* ids, const mpc
   CK(cudaGetLastError());
   CK(cudaStreamSynchronize(ctx->stream));
   for (int i = 0; i < n; ++i) ctx->live[ids[i]] = hz[i];
+  return MPC_OK;
+}
+
+mpc_status mpc_set_models_async(mpc_ctx* ctx, int32_t n, const int32_t* ids, const mpc_agent_model* models,
+                                void* stream) {
+  if (!ctx) return MPC_ERR_INVALID;
+  if (n < 0 || n > ctx->cfg.max_agents || (n > 0 && (!ids || !models)))
+    return fail(ctx, MPC_ERR_INVALID, "set_models_async: bad count or NULL buffer");
+  for (int i = 0; i < n; ++i) {
+    if (ids[i] < 0 || ids[i] >= ctx->cfg.max_agents)
+      return fail(ctx, MPC_ERR_INVALID, "set_models_async: agent id out of range");
+    const char* why = check_model(models[i], ctx->cfg.max_horizon);
+    if (why) return fail(ctx, MPC_ERR_INVALID, std::string("set_models_async: ") + why);
+  }
+  CK(cudaSetDevice(ctx->cfg.device));
+  if (!ctx->h_mstage) {
+    const size_t A = (size_t)ctx->cfg.max_agents;
+    CK(cudaMallocHost(&ctx->h_ids, sizeof(int) * A));
+    CK(cudaMallocHost(&ctx->h_mstage, sizeof(float) * A * mpc::MODEL_F));
+    CK(cudaMallocHost(&ctx->h_sstage, sizeof(double) * A * mpc::SCHED_D));
+    CK(cudaMallocHost(&ctx->h_hstage, sizeof(int) * A));
+  }
+  if (n == 0) return MPC_OK;
+  for (int i = 0; i < n; ++i) {
+    pack_model(models[i], ctx->h_mstage + (size_t)i * mpc::MODEL_F, ctx->h_sstage + (size_t)i * mpc::SCHED_D);
+    ctx->h_hstage[i] = models[i].N;
+    ctx->h_ids[i] = ids[i];
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CK(cudaMemcpyAsync(ctx->d_ids, ctx->h_ids, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_mstage, ctx->h_mstage, sizeof(float) * (size_t)n * mpc::MODEL_F,
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_sstage, ctx->h_sstage, sizeof(double) * (size_t)n * mpc::SCHED_D,
+                     cudaMemcpyHostToDevice, st));
+  CK(cudaMemcpyAsync(ctx->d_hstage, ctx->h_hstage, sizeof(int) * n, cudaMemcpyHostToDevice, st));
+  mpc_k_scatter_models<<<n, 128, 0, st>>>(n, ctx->d_ids, ctx->d_mstage, ctx->d_sstage, ctx->d_hstage,
+                                          ctx->model, ctx->sched, ctx->horizon, ctx->ar.warm_valid);
+  CK(cudaGetLastError());
+  for (int i = 0; i < n; ++i) ctx->live[ids[i]] = models[i].N;
   return MPC_OK;
 }
 
@@ -570,7 +618,8 @@ static cudaError_t enqueue_solve(mpc_ctx* ctx, Ticket* tk, cudaStream_t st, int 
   }
   mpc::SolverParams prm = params_of(cfg);
   prm.trees = ctx->has_trees ? 1 : 0;
-  prm.defer = (flags & MPC_SOLVE_DEFER_SLOW) ? 2 : (flags & MPC_SOLVE_DEFER_ADMM) ? 1 : 0;
+  prm.defer = (flags & MPC_SOLVE_DEFER_COLD) ? 3 : (flags & MPC_SOLVE_DEFER_SLOW) ? 2
+                                                : (flags & MPC_SOLVE_DEFER_ADMM) ? 1 : 0;
   if (flags & MPC_SOLVE_ADMM_ONLY) prm.warm_polish = 0;
   const int form = ctx->cfg.form;
   // graph capture needs a non-default stream; on the legacy stream the
@@ -638,10 +687,12 @@ mpc_status mpc_solve_ex(mpc_ctx* ctx, uint64_t ticket, void* stream, int32_t fla
   Ticket* tk = find_ticket(ctx, ticket);
   if (!tk) return fail(ctx, MPC_ERR_NOT_READY, "solve: unknown ticket");
   if (tk->state != 1) return fail(ctx, MPC_ERR_STATE, "solve: ticket already solved");
-  if (flags & ~(MPC_SOLVE_DEFER_ADMM | MPC_SOLVE_ADMM_ONLY | MPC_SOLVE_DEFER_SLOW))
+  if (flags & ~(MPC_SOLVE_DEFER_ADMM | MPC_SOLVE_ADMM_ONLY | MPC_SOLVE_DEFER_SLOW | MPC_SOLVE_DEFER_COLD))
     return fail(ctx, MPC_ERR_INVALID, "solve: unknown flag");
-  if ((flags & MPC_SOLVE_DEFER_SLOW) && (flags & (MPC_SOLVE_DEFER_ADMM | MPC_SOLVE_ADMM_ONLY)))
-    return fail(ctx, MPC_ERR_INVALID, "solve: DEFER_SLOW combines with no other flag");
+  if ((flags & (MPC_SOLVE_DEFER_SLOW | MPC_SOLVE_DEFER_COLD)) && (flags & ~(MPC_SOLVE_DEFER_SLOW | MPC_SOLVE_DEFER_COLD)))
+    return fail(ctx, MPC_ERR_INVALID, "solve: DEFER_SLOW / DEFER_COLD combine with no other flag");
+  if ((flags & MPC_SOLVE_DEFER_SLOW) && (flags & MPC_SOLVE_DEFER_COLD))
+    return fail(ctx, MPC_ERR_INVALID, "solve: DEFER_SLOW and DEFER_COLD exclude each other");
   if (flags && ctx->cfg.form != MPC_FORM_FUSED)
     return fail(ctx, MPC_ERR_INVALID, "solve: flags need the fused form");
   CK(cudaSetDevice(ctx->cfg.device));

@@ -15,7 +15,9 @@
 // the batch covered is answered: its latency is the completion time minus its
 // arrival time, on one steady clock started by mpc_server_start.  Model swaps
 // (agents leaving and joining) are queued and applied by the worker to slots
-// with no batch in flight, between batches.  With deferral on, batches are
+// with no batch in flight: their upload runs on a stream of its own
+// (mpc_set_models_async) while batches continue, and the slots join batches
+// again once it has completed.  With deferral on, batches are
 // solved with a DEFER flag of mpc_solve_ex: an agent whose polish first fails
 // (DEFER_ADMM), or that two reduced KKT solves of it do not settle
 // (DEFER_SLOW), comes back MPC_AGENT_DEFERRED, keeps its requests and state in
@@ -75,9 +77,13 @@ struct mpc_server {
   std::vector<uint8_t> inflight;
   std::vector<int32_t> ready_order;               // scratch of the worker
   std::vector<std::pair<int32_t, mpc_agent_model>> swaps;
-  int defer = 0;                                   // 0 off, 1 DEFER_ADMM, 2 DEFER_SLOW (mpc_server_set_defer)
+  int defer = 0;                                   // 0 off, 1 DEFER_ADMM, 2 DEFER_SLOW, 3 DEFER_COLD
   std::vector<Deferred> deferred_q;                // deferred agents awaiting their ADMM batch
   double swaps_since = -1.0;                      // queue time of the oldest pending swap
+  std::vector<int32_t> swapping;                  // slots whose new model is being uploaded
+  bool swap_busy = false;                         // an upload is in flight (worker only)
+  cudaStream_t swap_stream = nullptr;
+  cudaEvent_t swap_done = nullptr;
   // results (guarded by mu)
   std::vector<double> latency;
   std::vector<double> batch_log;                   // per batch: launch time, completion time, agents
@@ -230,6 +236,7 @@ bool launch(mpc_server* s, Lane& L, bool deferred) {
   int flags = 0;
   if (s->defer == 1) flags = L.deferred_batch ? MPC_SOLVE_ADMM_ONLY : MPC_SOLVE_DEFER_ADMM;
   else if (s->defer == 2) flags = L.deferred_batch ? 0 : MPC_SOLVE_DEFER_SLOW;
+  else if (s->defer == 3) flags = L.deferred_batch ? 0 : MPC_SOLVE_DEFER_COLD;
   if (r == MPC_OK) r = mpc_solve_ex(s->ctx, tk, st, flags);
   if (r == MPC_OK) r = mpc_get_torques(s->ctx, tk, L.d_tau, nullptr, nullptr, nullptr, L.d_st);
   if (r != MPC_OK) { set_error(s, r, mpc_last_error(s->ctx)); return false; }
@@ -244,8 +251,11 @@ bool launch(mpc_server* s, Lane& L, bool deferred) {
   return true;
 }
 
-// queued model swaps whose slots have no batch in flight
+// queued model swaps whose slots have no batch in flight: uploaded without
+// waiting (mpc_set_models_async on the swap stream); the slots stay in
+// flight, so that no batch takes them, until the upload's event completes
 void apply_swaps(mpc_server* s) {
+  if (s->swap_busy) return;
   std::vector<int32_t> ids;
   std::vector<mpc_agent_model> models;
   {
@@ -254,16 +264,32 @@ void apply_swaps(mpc_server* s) {
     std::vector<std::pair<int32_t, mpc_agent_model>> keep;
     for (auto& sw : s->swaps) {
       if (s->inflight[sw.first]) keep.push_back(sw);
-      else { ids.push_back(sw.first); models.push_back(sw.second); }
+      else { ids.push_back(sw.first); models.push_back(sw.second); s->inflight[sw.first] = 1; }
     }
     s->swaps.swap(keep);
     s->swaps_since = keep.empty() ? -1.0 : now_s(s);
+    s->swapping.assign(ids.begin(), ids.end());
   }
   if (ids.empty()) return;
-  const mpc_status r = mpc_set_models(s->ctx, (int32_t)ids.size(), ids.data(), models.data());
+  mpc_status r = mpc_set_models_async(s->ctx, (int32_t)ids.size(), ids.data(), models.data(), s->swap_stream);
   if (r != MPC_OK) { set_error(s, r, mpc_last_error(s->ctx)); return; }
+  const cudaError_t e = cudaEventRecord(s->swap_done, s->swap_stream);
+  if (e != cudaSuccess) { set_error(s, MPC_ERR_CUDA, cudaGetErrorString(e)); return; }
+  s->swap_busy = true;
+}
+
+// the upload of the last swap has completed: its slots are free again
+bool finish_swap(mpc_server* s) {
+  if (!s->swap_busy) return false;
+  const cudaError_t q = cudaEventQuery(s->swap_done);
+  if (q == cudaErrorNotReady) return false;
+  if (q != cudaSuccess) { set_error(s, MPC_ERR_CUDA, cudaGetErrorString(q)); return false; }
   std::lock_guard<std::mutex> g(s->mu);
-  s->swapped += (long long)ids.size();
+  for (int32_t slot : s->swapping) s->inflight[slot] = 0;
+  s->swapped += (long long)s->swapping.size();
+  s->swapping.clear();
+  s->swap_busy = false;
+  return true;
 }
 
 void run_worker(mpc_server* s) {
@@ -295,17 +321,16 @@ void run_worker(mpc_server* s) {
       Lane& L = s->lanes[s->max_inflight];
       if (!L.busy && launch(s, L, true)) { work = true; busy_def = true; }
     }
-    // model swaps wait for the device (their upload queues behind the
-    // batches that hold the SMs): apply them while every lane is busy, when
-    // the worker could launch nothing anyway, when the GPU is idle, or once
-    // the oldest has waited 20 ms
+    // model swaps: a finished upload frees its slots; pending swaps start
+    // their upload at once (it runs on its own stream and the worker does not
+    // wait for it)
+    if (finish_swap(s)) work = true;
     bool due = false;
     {
       std::lock_guard<std::mutex> g(s->mu);
-      due = !s->swaps.empty() &&
-            (busy >= s->max_inflight || (busy == 0 && !busy_def) || now_s(s) - s->swaps_since > 0.02);
+      due = !s->swaps.empty();
     }
-    if (due) apply_swaps(s);
+    if (due && !s->swap_busy) apply_swaps(s);
     if (!work) {
       // nothing completed or launched: wait briefly for a push or a completion
       std::unique_lock<std::mutex> lk(s->mu);
@@ -349,12 +374,20 @@ mpc_status mpc_server_create(mpc_ctx* ctx, int32_t pool, int32_t max_batch, int3
     if (e == cudaSuccess) e = cudaMalloc(&L.d_st, sizeof(int32_t) * mb);
     if (e != cudaSuccess) { mpc_server_destroy(s); return MPC_ERR_CUDA; }
   }
+  // the context's pinned staging of model uploads, allocated now rather than
+  // on the worker's first swap
+  if (cudaStreamCreateWithFlags(&s->swap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&s->swap_done, cudaEventDisableTiming) != cudaSuccess ||
+      mpc_set_models_async(ctx, 0, nullptr, nullptr, s->swap_stream) != MPC_OK) {
+    mpc_server_destroy(s);
+    return MPC_ERR_CUDA;
+  }
   *out = s;
   return MPC_OK;
 }
 
 mpc_status mpc_server_set_defer(mpc_server* s, int32_t mode) {
-  if (!s || mode < 0 || mode > 2) return MPC_ERR_INVALID;
+  if (!s || mode < 0 || mode > 3) return MPC_ERR_INVALID;
   if (s->worker.joinable()) return MPC_ERR_STATE;
   s->defer = mode;
   return MPC_OK;
@@ -413,7 +446,7 @@ mpc_status mpc_server_drain(mpc_server* s, double timeout_s) {
     if (s->error.load() != MPC_OK) return (mpc_status)s->error.load();
     {
       std::lock_guard<std::mutex> g(s->mu);
-      if (s->answered == s->pushed && s->swaps.empty()) return MPC_OK;
+      if (s->answered == s->pushed && s->swaps.empty() && s->swapping.empty()) return MPC_OK;
     }
     if (Clock::now() > end) return MPC_ERR_TIMEOUT;
     std::this_thread::sleep_for(std::chrono::microseconds(100));
@@ -430,6 +463,10 @@ mpc_status mpc_server_stop(mpc_server* s) {
       cudaEventSynchronize(L.done);
       complete(s, L);
     }
+  if (s->swap_busy) {
+    cudaEventSynchronize(s->swap_done);
+    finish_swap(s);
+  }
   return (mpc_status)s->error.load();
 }
 
@@ -470,6 +507,9 @@ mpc_status mpc_server_destroy(mpc_server* s) {
     if (L.done) cudaEventDestroy(L.done);
     if (L.stream) cudaStreamDestroy(L.stream);
   }
+  if (s->swap_stream) cudaStreamSynchronize(s->swap_stream);
+  if (s->swap_done) cudaEventDestroy(s->swap_done);
+  if (s->swap_stream) cudaStreamDestroy(s->swap_stream);
   delete s;
   return MPC_OK;
 }

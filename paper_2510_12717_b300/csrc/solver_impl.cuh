@@ -1982,7 +1982,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
   if (prm.polish && prm.warm_polish && prm.fixed_iters == 0) {
     Res pr;
     if (polish<PREC>(ap, sm, lane, prm, &pr, pat, pp, o.prec, ap.st[T_WARM] ? POLISH_PREV : POLISH_MIN,
-                     prm.defer == 2 ? 2 : 0)) {
+                     prm.defer == 2 || (prm.defer == 3 && !ap.st[T_WARM]) ? 2 : 0)) {
       o.polished = 1;
       o.status = MPC_AGENT_SOLVED_;
       o.r = pr;
@@ -1992,7 +1992,7 @@ __device__ Outcome admm_solve(const AgentPtrs& ap, float* sm, int lane, const So
     if (pp.timed_out()) { o.status = MPC_AGENT_TIMEOUT_; return o; }
     // deferred after a capped polish: the corrected active set is kept; a
     // later solve of this agent (same inputs, no flag) continues from it
-    if (prm.defer == 2) { o.status = MPC_AGENT_DEFERRED_; return o; }
+    if (prm.defer >= 2) { o.status = MPC_AGENT_DEFERRED_; return o; }
     factored = false;   // the polish overwrote the caches
     o.prec = fallback_precision(o.prec);
     polish_warm_start(ap, sm, lane, pat);

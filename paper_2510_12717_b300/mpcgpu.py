@@ -19,7 +19,7 @@ MPC_OK, MPC_ERR_INVALID, MPC_ERR_BUDGET, MPC_ERR_CUDA = 0, 1, 2, 3
 MPC_ERR_NOT_READY, MPC_ERR_TIMEOUT, MPC_ERR_STATE = 4, 5, 6
 AGENT_SOLVED, AGENT_MAX_ITER, AGENT_PRIMAL_INFEAS, AGENT_DUAL_INFEAS, AGENT_NAN, AGENT_TIMEOUT = 0, 1, 2, 3, 4, 5
 AGENT_INACCURATE, AGENT_DEFERRED = 6, 7
-SOLVE_DEFER_ADMM, SOLVE_ADMM_ONLY, SOLVE_DEFER_SLOW = 1, 2, 4
+SOLVE_DEFER_ADMM, SOLVE_ADMM_ONLY, SOLVE_DEFER_SLOW, SOLVE_DEFER_COLD = 1, 2, 4, 8
 FORM_PLAIN, FORM_FUSED, FORM_LDL = 0, 1, 2
 FP32, TF32, BF16, FP64, TF32X3 = 0, 1, 2, 3, 4
 PEAK_FP32_FMA, PEAK_FP64_FMA, PEAK_TF32_MMA_SYNC, PEAK_BF16_MMA_SYNC = 0, 1, 2, 3
@@ -101,6 +101,7 @@ SIGNATURES = {
     "mpc_solve": (C.c_int, [_P, C.c_uint64]),
     "mpc_solve_on": (C.c_int, [_P, C.c_uint64, _P]),
     "mpc_solve_ex": (C.c_int, [_P, C.c_uint64, _P, C.c_int32]),
+    "mpc_set_models_async": (C.c_int, [_P, C.c_int32, _P, _P, _P]),
     "mpc_autotune": (C.c_int, [_P, C.c_uint64, C.c_int32, C.c_char_p, C.c_size_t]),
     "mpc_get_torques": (C.c_int, [_P, C.c_uint64, _P, _P, _P, _P, _P]),
     "mpc_solve_host": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]),
@@ -259,6 +260,14 @@ class Solver:
         if "tree_axis" in model:
             self.set_trees(model, ids, idx)
 
+    def set_models_async(self, model: dict, agent_ids, stream, idx=None):
+        """mpc_set_models_async: the upload is enqueued on `stream` (a
+        cudaStream_t handle) and the call returns at once (no trees)."""
+        recs = pack_models(model, idx)
+        ids = np.ascontiguousarray(agent_ids, dtype=np.int32)
+        assert len(ids) == len(recs)
+        self._check(self.lib.mpc_set_models_async(self.ctx, len(ids), _ptr(ids), recs.ctypes.data, stream))
+
     def set_trees(self, trees: dict, agent_ids, idx=None):
         """mpc_set_trees: kinematic trees for the agents' torque maps."""
         recs = pack_trees(trees, idx)
@@ -404,7 +413,8 @@ class Server:
     def set_defer(self, mode: int = 1):
         """mpc_server_set_defer (before start()): 1 = agents whose polish
         first fails, 2 = also those two reduced KKT solves do not settle,
-        finish in batches of their own; 0 = off."""
+        3 = as 2 for cold agents and as 1 for warm ones, finish in batches
+        of their own; 0 = off."""
         self._check(self.lib.mpc_server_set_defer(self.srv, int(mode)))
 
     def deferred(self) -> int:

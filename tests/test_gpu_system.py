@@ -137,3 +137,30 @@ def test_polish_attempt_histogram(mpcgpu):
         assert hist[0] == int((st["polished"] == 0).sum())
     assert hist[1] >= 0.75 * 64
     s.close()
+
+
+def test_async_model_upload_equals_sync(mpcgpu):
+    # mpc_set_models_async on a stream of its own, ordered before the solve
+    # by waiting on that stream: the same models as mpc_set_models, so the
+    # same torques, bit for bit; a swap replaces an agent's model either way
+    from workload import make_agents
+    n = 24
+    ids = np.arange(n)
+    model, inp = make_agents("uneven", ids)
+    other, _ = make_agents("uneven", np.arange(100, 100 + n))
+    f32 = {k: np.ascontiguousarray(v, np.float32) for k, v in inp.items()}
+    cur = torch.cuda.current_stream().cuda_stream
+    side = torch.cuda.Stream()
+    a = mpcgpu.Solver(max_agents=n, max_horizon=20, stream=cur)
+    b = mpcgpu.Solver(max_agents=n, max_horizon=20, stream=cur)
+    a.set_models(other, ids)
+    a.set_models(model, ids)
+    b.set_models(other, ids)
+    b.set_models_async(model, ids, side.cuda_stream)
+    side.synchronize()
+    ra = a.solve_host(ids, f32["x0"], f32["qd_meas"], f32["cmd"], f32["phase"])
+    rb = b.solve_host(ids, f32["x0"], f32["qd_meas"], f32["cmd"], f32["phase"])
+    a.close()
+    b.close()
+    assert (ra["status"] == 0).all()
+    assert np.array_equal(ra["tau"], rb["tau"]) and np.array_equal(ra["status"], rb["status"])
