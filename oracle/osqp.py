@@ -185,13 +185,13 @@ def solve_until(lq: LiteralQP, x, z, y, *, eps_abs=1e-5, eps_rel=1e-5, max_iter=
 
 
 def literal_agent(m: dict, x0, cmd, phase, qd_meas, iters: int, *, rho: float = 0.1, sigma: float = 1e-6,
-                  alpha: float = 1.6, scaling: int = 0):
+                  alpha: float = 1.6, scaling: int = 0, kin=None):
     """Alg. 1 for one agent with a fixed N_QP = iters: f_init, f_param, the
     KKT system, `scaling` Ruiz iterations (f_Ruiz), one factorisation, iters
     OSQP iterations, the torque map of the last iterate (line search
-    alpha = 1)."""
+    alpha = 1).  kin: the kinematic rows' parameters (qp.agent_qp), or None."""
     x0 = np.asarray(x0, float)
-    qp, ex = qpmod.agent_qp(m, x0, cmd, phase)
+    qp, ex = qpmod.agent_qp(m, x0, cmd, phase, kin=kin)
     lq = literal_form(qp, rho)
     x, z, y = start_point(lq, qp, x0, np.asarray(m["q_nom"], float))
     if scaling:

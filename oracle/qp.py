@@ -4,6 +4,7 @@
             + dt (x_N - xr_N)^T Q (x_N - xr_N)
   s.t.      x_{k+1} = A_k x_k + B_k u_k + c_k,   x_0 = x0 (fixed)
             lo_k <= C_u u_k + C_x x_{k+1} <= hi_k,   k = 0..N-1
+            (56 rows per stage, refs.stage_rows; 64 with the kinematic rows)
 
 The stage cost is weighted by dt (Eq. mpc_formulation); there is no 1/2, so
 the Hessian is 2 dt diag(Q), 2 dt diag(R).
@@ -78,12 +79,13 @@ def build_qp(A, B, c, Q, R, dt, x0, x_ref, u_ref, rows):
         else:
             E[r, 60 * (k - 1) + 30:60 * (k - 1) + 60] = -A[k]   # x_k
             e[r] = c[k]
-    C = np.zeros((56 * N, n))
-    lo = np.zeros(56 * N)
-    hi = np.zeros(56 * N)
+    nr = rows[0][0].shape[0]
+    C = np.zeros((nr * N, n))
+    lo = np.zeros(nr * N)
+    hi = np.zeros(nr * N)
     for k in range(N):
         Cu, Cx, l_k, h_k = rows[k]
-        r = slice(56 * k, 56 * k + 56)
+        r = slice(nr * k, nr * k + nr)
         C[r, 60 * k:60 * k + 30] = Cu
         C[r, 60 * k + 30:60 * k + 60] = Cx
         lo[r] = l_k
@@ -91,12 +93,19 @@ def build_qp(A, B, c, Q, R, dt, x0, x_ref, u_ref, rows):
     return DenseQP(P, qv, float(const), E, e, C, lo, hi, N)
 
 
-def agent_qp(model, x0, cmd, phase0):
-    """Everything of f_init/f_param/f_KKT for one agent: (qp, extras)."""
+def agent_qp(model, x0, cmd, phase0, kin=None):
+    """Everything of f_init/f_param/f_KKT for one agent: (qp, extras).
+
+    kin: None, or dict(z_swing, v_to, v_td) to append each stage's eight
+    kinematic rows (no-slip, swing height; refs.kin_rows) as rows 56-63."""
     stance = refs.contact_schedule(model, phase0)
     x_ref, u_ref = refs.references(model, x0, cmd, stance)
     A, B, c = mdl.linearise(model, x0, u_ref)
     rows = [refs.stage_rows(model, stance[k]) for k in range(int(model["N"]))]
+    if kin is not None:
+        for k in range(len(rows)):
+            ek = refs.kin_rows(model, cmd, phase0, k, kin)
+            rows[k] = tuple(np.concatenate([a, b]) for a, b in zip(rows[k], ek))
     qp = build_qp(A, B, c, np.asarray(model["Q"], float), np.asarray(model["R"], float),
                   float(model["dt"]), np.asarray(x0, float), x_ref, u_ref, rows)
     extras = dict(stance=stance, x_ref=x_ref, u_ref=u_ref, A=A, B=B, c=c, rows=rows)

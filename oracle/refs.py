@@ -106,3 +106,92 @@ def stage_rows(model, stance_k):
         Cx[38 + j, 12 + j] = 1.0
         lo[38 + j], hi[38 + j] = -float(model["q_lim"]), float(model["q_lim"])
     return Cu, Cx, lo, hi
+
+
+# ---------------------------------------------------------------- kinematic rows
+# The no-slip and swing-height rows of Eq. (mpc_formulation) (Contact: the
+# stance foot's velocity J(q) qdot is zero; Swing: the foot height equals
+# h_des, a fifth-order Bezier curve over the swing, Eqs. bezier_1..5).
+#
+# Readings used:
+#  * Node n's generalised velocity is (v_n, w_n, u_{n-1} joint rates): the
+#    joint rates that carry q_{n-1} to q_n, as in the semi-implicit step
+#    q_{i+1} = q_i + dt qdot_{i+1} of Eq. (mpc_formulation).  So the rows of
+#    node k+1 read (u_k, x_{k+1}), the API's stage-row form.  Node 0 is data
+#    and has none.
+#  * Foot position p + r_i(q) with the model's lever r_i(q) (model.py); its
+#    velocity is v + J_leg_i[0:3] qdot_leg_i and its height p_z + r_i(q)_z.
+#  * Ground level: the height of the foot at the nominal joint angles with the
+#    base at the commanded height c_h, i.e. the row p_z + J_z (q_leg - q_nom)
+#    equals c_h + B(t_sw) (the lever's own z cancels).
+#  * The quintic has six control points and Eqs. bezier_1..5 fix five; the
+#    sixth condition is dB/dt(0.5) = 0 (the apex of the swing at mid-swing).
+#  * Contact state and swing progress of node n from the same phase as the
+#    schedule: s = frac(frac(phi_0 + n dt / T) + o_i), stance if s < d_i,
+#    else t_sw = (s - d_i) / (1 - d_i).
+#
+# Row layout of the eight kinematic rows of stage k (rows 56-63 when enabled):
+#   56 + 3i + r  no-slip of foot i, component r (x, y, z), node k+1 in stance
+#   62 + i       swing height of foot i, node k+1 in swing
+# Rows whose foot is in the other contact state are free.
+
+def bezier_points(z_swing, v_to, v_td):
+    """Control points b_0..b_5 of the swing-height quintic
+    B(t) = sum_j C(5, j) t^j (1 - t)^(5 - j) b_j with B(0) = B(1) = 0,
+    B(0.5) = z_swing, dB/dt(0) = v_to, dB/dt(1) = v_td, dB/dt(0.5) = 0."""
+    b0 = b5 = 0.0
+    b1 = float(v_to) / 5.0                 # dB/dt(0) = 5 (b1 - b0)
+    b4 = -float(v_td) / 5.0                # dB/dt(1) = 5 (b5 - b4)
+    # B(0.5) = (b0 + 5 b1 + 10 b2 + 10 b3 + 5 b4 + b5) / 32
+    s = (32.0 * float(z_swing) - b0 - 5.0 * b1 - 5.0 * b4 - b5) / 10.0      # b2 + b3
+    # dB/dt(0.5) = 5/16 (-b0 - 3 b1 - 2 b2 + 2 b3 + 3 b4 + b5)
+    d = (b0 + 3.0 * b1 - 3.0 * b4 - b5) / 2.0                                # b3 - b2
+    return np.array([b0, b1, 0.5 * (s - d), 0.5 * (s + d), b4, b5])
+
+
+def bezier(t, b):
+    """B(t) for control points b (Bernstein form)."""
+    t = float(t)
+    return sum(math.comb(5, j) * t ** j * (1.0 - t) ** (5 - j) * b[j] for j in range(6))
+
+
+def node_contact(model, phase0, n):
+    """(stance (2,) bool, t_sw (2,)) of node n; t_sw is 0 in stance."""
+    step = float(model["dt"]) / float(model["period"])
+    ph = float(phase0) + float(n) * step
+    ph = ph - math.floor(ph)
+    st = np.zeros(2, dtype=bool)
+    tsw = np.zeros(2)
+    for i in range(2):
+        s = ph + float(model["offset"][i])
+        s = s - math.floor(s)
+        d = float(model["duty"][i])
+        st[i] = s < d
+        if not st[i]:
+            tsw[i] = (s - d) / (1.0 - d)
+    return st, tsw
+
+
+def kin_rows(model, cmd, phase0, k, kin):
+    """(C_u (8,30), C_x (8,30), lo (8,), hi (8,)) of stage k's kinematic rows
+    (node k+1); kin = dict(z_swing, v_to, v_td)."""
+    Cu = np.zeros((8, 30))
+    Cx = np.zeros((8, 30))
+    lo = np.full(8, -INF)
+    hi = np.full(8, INF)
+    st, tsw = node_contact(model, phase0, k + 1)
+    b = bezier_points(kin["z_swing"], kin["v_to"], kin["v_td"])
+    for i in range(2):
+        J = np.asarray(model["J_leg"][i], float)
+        legs = slice(12 + 5 * i, 17 + 5 * i)
+        for r in range(3):
+            Cu[3 * i + r, legs] = J[r]
+            Cx[3 * i + r, 6 + r] = 1.0
+            if st[i]:
+                lo[3 * i + r] = hi[3 * i + r] = 0.0
+        Cx[6 + i, 2] = 1.0
+        Cx[6 + i, legs] = J[2]
+        if not st[i]:
+            h = float(cmd[0]) + bezier(tsw[i], b) + J[2] @ np.asarray(model["q_nom"][5 * i:5 * i + 5], float)
+            lo[6 + i] = hi[6 + i] = h
+    return Cu, Cx, lo, hi
