@@ -126,7 +126,7 @@ typedef enum {
  * fixed_iters 0, check_every 10, adaptive_rho 1, polish 1, warm_start 1,
  * form FUSED, precision FP32, max_horizon 20, variant 1, early_polish 100,
  * graph 0, warm_polish 1, refine_steps -1, spin_limit 4194304, wait_test_agent -1,
- * ruiz_iters 0.
+ * ruiz_iters 0, kin_rows 0, swing_height 0.075, v_takeoff 0.1, v_touchdown -0.1.
  * OSQP's parameters (Stellato et al. 2020,
  * Sec. 3.2, to which the paper defers after Eq. (backsolve_2)). */
 typedef struct mpc_config {
@@ -194,6 +194,20 @@ typedef struct mpc_config {
                                  = unscaled: with the fixed step size of this form the
                                  equilibrated problem converges more slowly on these
                                  QPs; OSQP pairs its scaling with an adaptive rho) */
+  int kin_rows;               /* literal form (MPC_FORM_LDL) only, and without Ruiz
+                                 scaling: 1 adds the kinematic rows of Eq.
+                                 (mpc_formulation) to every stage k, read at node k+1
+                                 on (u_k, x_{k+1}): per foot in stance the no-slip rows
+                                 v_{k+1} + J_leg[0:3] qdot_leg,k = 0 (J(q) qdot = 0,
+                                 with the node's joint rates those of u_k), per foot in
+                                 swing the height row p_z + J_leg[2] (q_leg - q_nom) =
+                                 c_h + B(t_sw), B the quintic of Eqs. (bezier_1-5) with
+                                 dB/dt(0.5) = 0 as its sixth condition.  Rows 56-63 of
+                                 the stage (56 + 3i + r: no-slip of foot i, component r;
+                                 62 + i: swing height of foot i).  Default 0 */
+  float swing_height;         /* z_swing of Eq. (bezier_3), m (default 0.075) */
+  float v_takeoff;            /* v_to of Eq. (bezier_4), m/s (default 0.1) */
+  float v_touchdown;          /* v_td of Eq. (bezier_5), m/s (default -0.1) */
 } mpc_config;
 
 /* One agent's model (host memory, float64; stored as float32 on the device,

@@ -117,9 +117,14 @@ enum : int { LS_DU = 0, LS_DX = 32, LS_ED = 64, LS_EI = 96, LS_T = 160, LDL_S = 
 // dynamics multipliers, x_{k+1}); the strictly lower L without its
 // structurally zero block (the x_{k+1} rows against the u_k columns), packed
 // by columns at LDL_COL and by rows at LDL_ROW (3105 entries each), 1/D at
-// LDL_IND, the 30 x 30 coupling block G_k (row-major) at LDL_G
+// LDL_IND, the 30 x 30 coupling block G_k (row-major) at LDL_G, and with
+// the kinematic rows the three rows of L31 that they fill (the x_{k+1} rows of
+// v, on u_k; row-major 3 x 30) at LDL_L31
 enum : int { LDL_NB = 90, LDL_NL = 3105, LDL_COL = 0, LDL_ROW = 3108, LDL_IND = 6216, LDL_G = 6312,
-             LDL_REC = 7232, LDL_W = 96 };
+             LDL_L31 = 7232, LDL_REC = 7328, LDL_W = 96 };
+// kinematic rows of a stage (literal form): 56 + 3i + r no-slip of foot i,
+// component r; 62 + i swing height of foot i
+enum : int { KIN_ROW = 56, KIN_NR = 8 };
 enum : int { F_WAIT_TIMEOUTS = 0, F_COUNT = 4 };
 
 // lin record layout: dense A_base and B (column-major, stride 23), their
@@ -159,6 +164,8 @@ struct SolverParams {
                        //   polish first has not passed after 2 reduced solves ends DEFERRED with
                        //   its corrected active set kept (a later solve continues from it); 3 = as
                        //   2 for a cold agent, and a warm one when its polish first fails
+  int kin;             // literal form: 1 = the kinematic rows 56-63 of every stage
+  float kin_b[6];      // their swing curve's Bezier control points b_0 .. b_5
 };
 
 }  // namespace mpc

@@ -190,6 +190,10 @@ mpc_status mpc_default_config(mpc_config* cfg) {
   cfg->spin_limit = mpc::kSpinLimit;
   cfg->wait_test_agent = -1;
   cfg->ruiz_iters = 0;
+  cfg->kin_rows = 0;
+  cfg->swing_height = 0.075f;
+  cfg->v_takeoff = 0.1f;
+  cfg->v_touchdown = -0.1f;
   return MPC_OK;
 }
 
@@ -206,6 +210,11 @@ mpc_status mpc_create(const mpc_config* cfg, mpc_ctx** out) {
   if (cfg->form != MPC_FORM_PLAIN && cfg->form != MPC_FORM_FUSED && cfg->form != MPC_FORM_LDL)
     return MPC_ERR_INVALID;
   if (cfg->ruiz_iters < 0 || cfg->ruiz_iters > 50) return MPC_ERR_INVALID;
+  // the kinematic rows exist in the literal form only, and not with its scaling
+  if (cfg->kin_rows < 0 || cfg->kin_rows > 1 ||
+      (cfg->kin_rows && (cfg->form != MPC_FORM_LDL || cfg->ruiz_iters != 0)) ||
+      !std::isfinite(cfg->swing_height) || !std::isfinite(cfg->v_takeoff) || !std::isfinite(cfg->v_touchdown))
+    return MPC_ERR_INVALID;
   if (!(cfg->rho0 > 0.f) || !(cfg->sigma > 0.f) || !(cfg->alpha > 0.f && cfg->alpha < 2.f) ||
       !(cfg->eps_abs >= 0.f) || !(cfg->eps_rel >= 0.f) || cfg->max_iter <= 0 || cfg->fixed_iters < 0 ||
       cfg->graph < 0 || cfg->graph > 1 ||
@@ -596,6 +605,18 @@ static mpc::SolverParams params_of(const mpc_config& c) {
   p.wait_test_slot = c.wait_test_agent;
   p.defer = 0;
   p.ruiz = c.ruiz_iters;
+  // the swing curve's control points: B(0) = B(1) = 0, dB/dt(0) = 5 (b1 - b0)
+  // = v_to, dB/dt(1) = 5 (b5 - b4) = v_td; then b2 + b3 from B(0.5) = z_swing
+  // (32 B(0.5) = b0 + 5 b1 + 10 (b2 + b3) + 5 b4 + b5) and b3 - b2 from
+  // dB/dt(0.5) = 0 (16/5 dB/dt(0.5) = 3 (b4 - b1) + 2 (b3 - b2) + b5 - b0)
+  p.kin = c.kin_rows;
+  {
+    const double b1 = c.v_takeoff / 5.0, b4 = -c.v_touchdown / 5.0;
+    const double sum23 = (32.0 * c.swing_height - 5.0 * (b1 + b4)) / 10.0;
+    const double dif32 = 1.5 * (b1 - b4);
+    const double bz[6] = {0.0, b1, 0.5 * (sum23 - dif32), 0.5 * (sum23 + dif32), b4, 0.0};
+    for (int j = 0; j < 6; ++j) p.kin_b[j] = (float)bz[j];
+  }
   return p;
 }
 

@@ -104,6 +104,100 @@ __device__ __forceinline__ float row_value(int r, const float* U, const float* X
   return X[r - 26];
 }
 
+// ------------------------------------------------------------------ kinematic rows
+// The no-slip and swing-height rows of Eq. (mpc_formulation), read at node
+// k+1 on (u_k, x_{k+1}) (rows KIN_ROW + q):
+//   q = 3i + r (r = 0, 1, 2): v_{k+1,r} + J_leg,i[r] . qdot_leg,i = 0 (foot i in stance)
+//   q = 6 + i:               p_z + J_leg,i[2] . q_leg,i = c_h + B(t_sw) + J_leg,i[2] . q_nom,i (swing)
+// Their coefficients in shared memory, by lane: KU row q (q < 6) holds the u
+// coefficients of no-slip row q (its x coefficient is 1 at lane 6 + r); KC
+// row i the x coefficients of foot i's height row.
+constexpr int KIN_SM = 8 * 32;
+__device__ __forceinline__ void kin_fill(float* ks, const float* md, int lane) {
+  for (int q = 0; q < 8; ++q) {
+    const int f = q < 6 ? q / 3 : q - 6, r = q < 6 ? q % 3 : 2;
+    const int j = lane - 12 - 5 * f;
+    float v = (j >= 0 && j < 5) ? md[M_JLEG + 30 * f + 5 * r + j] : 0.f;
+    if (q >= 6 && lane == 2) v = 1.f;
+    ks[q * 32 + lane] = v;
+  }
+  __syncwarp();
+}
+// value of kinematic row q at (u_k, x_{k+1})
+__device__ __forceinline__ float kin_value(int q, const float* U, const float* X, const float* ks) {
+  const int f = q < 6 ? q / 3 : q - 6;
+  const int b = 12 + 5 * f;
+  const float* c = ks + q * 32 + b;
+  float v;
+  if (q < 6) {
+    v = X[6 + q % 3];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) v = fmaf(c[j], U[b + j], v);
+  } else {
+    v = X[2];
+#pragma unroll
+    for (int j = 0; j < 5; ++j) v = fmaf(c[j], X[b + j], v);
+  }
+  return v;
+}
+
+// Bounds, classes and the cold start of the kinematic rows of every stage:
+// node k+1's contact state from the schedule in double precision (the
+// operation order of the set-up kernel's), its swing progress
+// t_sw = (s - d_i) / (1 - d_i) and the height B(t_sw) of the Bezier curve
+// (control points in SolverParams), in double precision.  Lane k: stage k.
+__global__ void __launch_bounds__(32) mpc_k_ldl_kin(Arena a, Batch b, SolverParams prm) {
+  const int lane = threadIdx.x;
+  const int row = blockIdx.x;
+  if (!live_row(a, b, row)) return;
+  const int slot = b.ids[row];
+  const AgentPtrs ap = agent_ptrs(a, slot);
+  if (ap.st[T_STATUS] == MPC_AGENT_NAN_) return;
+  const int N = ap.N;
+  const float* md = ap.mdl;
+  const int k = lane;
+  if (k >= N) return;
+  const double step = __ddiv_rn(ap.sch[S_DT], ap.sch[S_PERIOD]);
+  double ph = __dadd_rn((double)ap.inp[I_PHASE], __dmul_rn((double)(k + 1), step));
+  ph = __dsub_rn(ph, floor(ph));
+  float* lo = ap.rlo + k * RS + KIN_ROW;
+  float* hi = ap.rhi + k * RS + KIN_ROW;
+  float* cl = ap.rcls + k * RS + KIN_ROW;
+  float* w = ap.w + k * RS + KIN_ROW;
+  float* y = ap.y + k * RS + KIN_ROW;
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    double s = __dadd_rn(ph, ap.sch[S_OFF + i]);
+    s = __dsub_rn(s, floor(s));
+    const double d = ap.sch[S_DUTY + i];
+    const bool stance = s < d;
+    for (int r = 0; r < 3; ++r) {
+      lo[3 * i + r] = stance ? 0.f : -INFINITY;
+      hi[3 * i + r] = stance ? 0.f : INFINITY;
+      cl[3 * i + r] = stance ? 1000.f : 0.f;
+      w[3 * i + r] = 0.f;
+      y[3 * i + r] = 0.f;
+    }
+    if (stance) {
+      lo[6 + i] = -INFINITY; hi[6 + i] = INFINITY; cl[6 + i] = 0.f; w[6 + i] = 0.f;
+    } else {
+      const double t = (s - d) / (1.0 - d), t1 = 1.0 - t;
+      // Bernstein weights C(5, j) t^j (1 - t)^(5 - j)
+      const double t2 = t * t, u2 = t1 * t1;
+      const double wj[6] = {u2 * u2 * t1, 5.0 * t * u2 * u2, 10.0 * t2 * u2 * t1, 10.0 * t2 * t * u2,
+                            5.0 * t2 * t2 * t1, t2 * t2 * t};
+      double bz = 0.0;
+      for (int j = 0; j < 6; ++j) bz += wj[j] * (double)prm.kin_b[j];
+      double h = (double)ap.inp[I_CMD] + bz;
+      for (int j = 0; j < 5; ++j) h += (double)md[M_JLEG + 30 * i + 10 + j] * (double)md[M_QNOM + 5 * i + j];
+      lo[6 + i] = hi[6 + i] = (float)h;
+      cl[6 + i] = 1000.f;
+      w[6 + i] = (float)h;   // the cold start's z: its row value projected onto [h, h]
+    }
+    y[6 + i] = 0.f;
+  }
+}
+
 // ------------------------------------------------------------------ factor
 // One warp per agent; lane l (< 30) holds row l of each 30 x 30 block in
 // registers.  The stage's 90 x 90 block M_k = [[A11, ., .], [A21, A22, .],
@@ -157,6 +251,15 @@ __device__ __forceinline__ void put_row(float* rec, int i, int j0, const float (
   }
 }
 
+// KIN: with the kinematic rows.  Their pivots, eliminated first like the
+// other rows', add C^T diag(rho) C to the blocks: to A11 (u_k) the no-slip
+// rows' J^T J on a foot's leg rates, to A33 (x_{k+1}) their unit entries on v
+// and the height rows' c c^T, and to A31 the no-slip rows' cross terms between
+// v_{k+1} and the leg rates.  So three rows of L31 (x_{k+1} rows 6-8) are no
+// longer zero: L31 = A31 L11^-T D1^-1; L32 = (A32 - L31 D1 L21^T) L22^-T D2^-1;
+// A33 loses L31 D1 L31^T as well.
+constexpr int F_KIN = KIN_SM + 3 * 32 + 2 * 3 * 33 + 2;     // KU/KC, L31 rows, Y31 and M32 (stride 33)
+template <bool KIN>
 __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverParams prm) {
   const int lane = threadIdx.x;
   const int row = blockIdx.x;
@@ -166,6 +269,10 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
   if (ap.st[T_STATUS] == MPC_AGENT_NAN_) return;
   extern __shared__ __align__(16) float fsm[];
   float* T = fsm;                   // 30 rows of stride 32: the scaled rows of the last solve
+  float* ks = fsm + F_FLOATS;       // KIN: coefficients of the kinematic rows
+  float* T31 = ks + KIN_SM;         // KIN: the three scaled rows of L31 (stride 32)
+  float* Y31 = T31 + 3 * 32;        // KIN: ... unscaled (stride 33)
+  float* M32 = Y31 + 3 * 33;        // KIN: rows 6-8 of L31 D1 L21^T (stride 33)
   const float* md = ap.mdl;
   const float* lin = ap.lin;
   const int N = ap.N;
@@ -180,6 +287,9 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
   float mrow[30];                        // row l of A_k X_{k-1} A_k^T (0 at k = 0)
 #pragma unroll
   for (int c = 0; c < 30; ++c) mrow[c] = 0.f;
+  if (KIN) kin_fill(ks, md, lane);
+  const bool is3 = KIN && lane >= 6 && lane < 9;   // KIN: lanes 6-8 hold the x_{k+1} rows of v
+  const int r3c = is3 ? lane - 6 : 0;
   for (int k = 0; k < N; ++k) {
     float* rec = rec0 + (size_t)k * LDL_REC;
     const float* cls = ap.rcls + k * RS;
@@ -212,11 +322,29 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
       for (int c = 0; c < 30; ++c)
         if (c == l) av[c] = dg;
     }
+    // KIN: the step sizes of the stage's kinematic rows (0 on a free row),
+    // the no-slip rows' J^T diag(rho) J on A11
+    float rk[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) rk[q] = KIN ? rho * cls[KIN_ROW + q] : 0.f;
+    if (KIN) {
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        const float aq = rk[q] * ks[q * 32 + l];
+#pragma unroll
+        for (int c = 0; c < 30; ++c) av[c] = fmaf(aq, ks[q * 32 + c], av[c]);
+      }
+    }
     const float q33 = cs * dx * dx * 2.f * dt * md[M_Q + l] + sigma +
                       (l >= 12 ? rho * cls[l + 26] * (ei[l + 26] * dx) * (ei[l + 26] * dx) : 0.f);
     const float a32 = ed * dx;           // the x_{k+1} entry of dynamics row l, scaled
     const float ed1 = k + 1 < N ? Sk[LDL_S + LS_ED + l] : 1.f;   // E of the next stage's dynamics row l
     float dd0 = 1.f, dd1 = 1.f, dd2 = 1.f;
+    // KIN: this lane's share of the height rows' c c^T and of the no-slip
+    // rows' unit entries on A33; rows 6-8 of L31 D1 L31^T
+    const float h6 = KIN ? rk[6] * ks[6 * 32 + l] : 0.f, h7 = KIN ? rk[7] * ks[7 * 32 + l] : 0.f;
+    const float nd = is3 ? rk[r3c] + rk[3 + r3c] : 0.f;
+    float m33[3] = {0.f, 0.f, 0.f};
     // ---- the three groups in turn: factor the (updated) diagonal block,
     // store its rows, solve the next off-diagonal block's rows against it
     // (A21 = -B, A32 = I, and for the coupling A_{k+1}), scale them by 1/D,
@@ -230,11 +358,28 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
       else dd2 = d;
       put_row<true>(rec, 30 * g + l, 30 * g, av, lane);
       if (g == 2 && k + 1 == N) break;
+      if (KIN && g == 0) {
+        // rows 6-8 of L31: the rows of A31 solved against L11, then scaled
+        float y3[30];
+#pragma unroll
+        for (int c = 0; c < 30; ++c) y3[c] = is3 ? fmaf(rk[r3c], ks[r3c * 32 + c], rk[3 + r3c] * ks[(3 + r3c) * 32 + c]) : 0.f;
+        trsv_rows(y3, av);
+#pragma unroll
+        for (int c = 0; c < 30; ++c) {
+          const float v = y3[c] / __shfl_sync(FULL, d, c);
+          if (is3) {
+            rec[LDL_L31 + r3c * 30 + c] = v;
+            T31[r3c * 32 + c] = v;
+            Y31[r3c * 33 + c] = y3[c];
+          }
+        }
+      }
       float y[30];
 #pragma unroll
       for (int c = 0; c < 30; ++c)
         y[c] = g == 0 ? -b_entry(lin, dt, l, c) * ed * __shfl_sync(FULL, du, c)
-                      : (g == 1 ? (c == l ? a32 : 0.f) : a_entry(lin, k + 1, l, c) * ed1 * __shfl_sync(FULL, dx, c));
+                      : (g == 1 ? (c == l ? a32 : 0.f) - (is3 ? M32[r3c * 33 + c] : 0.f)
+                                : a_entry(lin, k + 1, l, c) * ed1 * __shfl_sync(FULL, dx, c));
       trsv_rows(y, av);
       float ys[30];
 #pragma unroll
@@ -267,8 +412,30 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
         acc = fmaf(y[28], T[s2 * 32 + 28], acc);
         acc = fmaf(y[29], T[s2 * 32 + 29], acc);
         if (g == 0) av[s2] = (s2 == l ? -1.f / rho_eq : 0.f) - mrow[s2] - acc;
-        else if (g == 1) av[s2] = (s2 == l ? q33 : 0.f) - acc;
-        else mrow[s2] = acc;
+        else if (g == 1) {
+          float v = (s2 == l ? q33 : 0.f) - acc;
+          if (KIN) {
+            // the kinematic rows on A33, less L31 D1 L31^T
+            v = fmaf(h6, ks[6 * 32 + s2], fmaf(h7, ks[7 * 32 + s2], v));
+            if (s2 == l) v += nd;
+            if (s2 >= 6 && s2 < 9 && is3) v -= m33[s2 - 6];
+          }
+          av[s2] = v;
+        } else mrow[s2] = acc;
+      }
+      if (KIN && g == 0 && is3) {
+        // rows 6-8 of L31 D1 L21^T (T holds the scaled rows of L21) and of L31 D1 L31^T
+        for (int s2 = 0; s2 < 30; ++s2) {
+          float acc = 0.f;
+          for (int m = 0; m < 30; ++m) acc = fmaf(Y31[r3c * 33 + m], T[s2 * 32 + m], acc);
+          M32[r3c * 33 + s2] = acc;
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          float acc = 0.f;
+          for (int m = 0; m < 30; ++m) acc = fmaf(Y31[r3c * 33 + m], T31[q * 32 + m], acc);
+          m33[q] = acc;
+        }
       }
       __syncwarp();
     }
@@ -414,7 +581,11 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_ruiz(Arena a, Batch b, SolverPar
 // ------------------------------------------------------------------ solves
 // Unit lower solve L w = b of one block, L by columns (shared memory); the
 // lane holds entries lane, lane + 32, lane + 64 (< 90) in e0, e1, e2.
-__device__ __forceinline__ void fwd_sub(const float* Lc, float& e0, float& e1, float& e2, int lane) {
+// KIN: rows 66-68 (the v rows of x_{k+1}) also have entries in the columns
+// 0-29, the three rows of L31 (L3, row-major 3 x 30).
+template <bool KIN>
+__device__ __forceinline__ void fwd_sub(const float* Lc, const float* L3, float& e0, float& e1, float& e2,
+                                        int lane) {
 #pragma unroll
   for (int j = 0; j < NB - 1; ++j) {
     const int o = col_off(j) - j - 1;             // L(i, j) at o + i, i > j
@@ -424,16 +595,20 @@ __device__ __forceinline__ void fwd_sub(const float* Lc, float& e0, float& e1, f
     if (lane > j) e0 = fmaf(-Lc[o + lane], wj, e0);
     if (lane + 32 > j && (j >= 30 || lane + 32 < 60)) e1 = fmaf(-Lc[o + lane + 32], wj, e1);
     if (lane + 64 > j && lane < NB - 64 && j >= 30) e2 = fmaf(-Lc[o + lane + 64], wj, e2);
+    if (KIN && j < 30 && lane >= 2 && lane < 5) e2 = fmaf(-L3[(lane - 2) * 30 + j], wj, e2);
   }
 }
 // Unit upper solve L^T v = w of one block, L by rows (shared memory).
-__device__ __forceinline__ void bwd_sub(const float* Lr, float& e0, float& e1, float& e2, int lane) {
+template <bool KIN>
+__device__ __forceinline__ void bwd_sub(const float* Lr, const float* L3, float& e0, float& e1, float& e2,
+                                        int lane) {
 #pragma unroll
   for (int j = NB - 1; j >= 1; --j) {
     const int o = row_off(j) - row_skip(j);       // L(j, i) at o + i, i < j (i >= 30 for j >= 60)
     const float vj = j < 32 ? __shfl_sync(FULL, e0, j) : (j < 64 ? __shfl_sync(FULL, e1, j - 32)
                                                                  : __shfl_sync(FULL, e2, j - 64));
     if (lane < j && (j < 60 || lane >= 30)) e0 = fmaf(-Lr[o + lane], vj, e0);
+    if (KIN && j >= 66 && j < 69 && lane < 30) e0 = fmaf(-L3[(j - 66) * 30 + lane], vj, e0);
     if (lane + 32 < j) e1 = fmaf(-Lr[o + lane + 32], vj, e1);
     if (lane + 64 < j) e2 = fmaf(-Lr[o + lane + 64], vj, e2);
   }
@@ -446,7 +621,7 @@ __device__ __forceinline__ void bwd_sub(const float* Lr, float& e0, float& e1, f
 // previous item computes.  A wait gives up after `limit` polls: the warp then
 // issues nothing more, waits (bounded) for the copies in flight and ends the
 // agent's solve with MPC_AGENT_TIMEOUT.
-constexpr int BUF_L = 0, BUF_G = 3108, BUF_D = 4008, BUF_FLOATS = 4104;
+constexpr int BUF_L = 0, BUF_G = 3108, BUF_D = 4008, BUF_L31 = 4104, BUF_FLOATS = 4200;
 struct Stager {
   float* buf[2];
   uint64_t* bar;      // two mbarriers
@@ -455,6 +630,8 @@ struct Stager {
   bool dead;
   int limit;
 };
+// KIN: the items carry the three rows of L31 too
+template <bool KIN>
 __device__ __forceinline__ void stage_issue(Stager& sg, int b, const float* rec0, int N, int t, int lane) {
   if (sg.dead) return;
   __syncwarp();   // every lane is done with the buffer's previous contents
@@ -465,10 +642,12 @@ __device__ __forceinline__ void stage_issue(Stager& sg, int b, const float* rec0
     const bool g = fwd ? k >= 1 : k + 1 < N;
     const float* gsrc = fwd ? rec + LDL_G : rec + LDL_REC + LDL_G;   // G_k or G_{k+1}
     const uint32_t bl = (LDL_ROW - LDL_COL) * 4, bg = 900 * 4, bd = 96 * 4;
-    mbar_expect_tx(sg.bar + b, bl + (g ? bg : 0) + (fwd ? 0 : bd));
+    const uint32_t b3 = KIN ? 96 * 4 : 0;
+    mbar_expect_tx(sg.bar + b, bl + (g ? bg : 0) + (fwd ? 0 : bd) + b3);
     tma_load_1d(sg.buf[b] + BUF_L, rec + (fwd ? LDL_COL : LDL_ROW), bl, sg.bar + b);
     if (g) tma_load_1d(sg.buf[b] + BUF_G, gsrc, bg, sg.bar + b);
     if (!fwd) tma_load_1d(sg.buf[b] + BUF_D, rec + LDL_IND, bd, sg.bar + b);
+    if (b3) tma_load_1d(sg.buf[b] + BUF_L31, rec + LDL_L31, b3, sg.bar + b);
   }
   sg.pending |= 1u << b;
 }
@@ -494,8 +673,9 @@ struct LdlRes { float rp, rd, sp, sd; };
 // y = E y_s / c): primal |A x - z|, dual |P x + q + A^T y| (inf-norms) and
 // their scales max(|A x|, |z|), max(|P x|, |A^T y|, |q|).  xv: 160 floats of
 // shared scratch (u_k, x_{k+1}, x_k, the dynamics multipliers of stages k, k+1).
+// ks: the kinematic rows' coefficients (shared memory), or null without them.
 __device__ __noinline__ LdlRes ldl_residuals(const AgentPtrs& ap, const float* ly, const float* S0, float cs, float* xv,
-                                int lane) {
+                                const float* ks, int lane) {
   const int N = ap.N;
   const float* md = ap.mdl;
   const float* lin = ap.lin;
@@ -549,6 +729,13 @@ __device__ __noinline__ LdlRes ldl_residuals(const AgentPtrs& ap, const float* l
           if (cls[p + t] > 0.f) atu = fmaf(pyr_coef(c, t, mu), ei[p + t] * yy[p + t] * ic, atu);
       }
       if (i >= 12 && cls[i + 26] > 0.f) atx += ei[i + 26] * yy[i + 26] * ic;
+      if (ks) {
+        // the kinematic rows (a free row's multiplier stays 0)
+        const float* yk = yy + KIN_ROW;
+        for (int q = 0; q < 6; ++q) atu = fmaf(ks[q * 32 + i], yk[q], atu);
+        if (i >= 6 && i < 9) atx += yk[i - 6] + yk[i - 3];
+        atx = fmaf(ks[6 * 32 + i], yk[6], fmaf(ks[7 * 32 + i], yk[7], atx));
+      }
       r.rd = fmaxf(r.rd, fmaxf(fabsf(gu + qu + atu), fabsf(gx + qx + atx)));
       r.sd = fmaxf(r.sd, fmaxf(fmaxf(fabsf(gu), fabsf(gx)), fmaxf(fmaxf(fabsf(atu), fabsf(atx)),
                                                                    fmaxf(fabsf(qu), fabsf(qx)))));
@@ -556,8 +743,9 @@ __device__ __noinline__ LdlRes ldl_residuals(const AgentPtrs& ap, const float* l
     // inequality rows
     for (int h = 0; h < 2; ++h) {
       const int rr = lane + 32 * h;
-      if (rr < NR && ap.rcls[k * RS + rr] > 0.f) {
-        const float cz = row_value(rr, U, X, mu), z = ap.w[k * RS + rr] / ei[rr];
+      if (rr < (ks ? KIN_ROW + KIN_NR : NR) && ap.rcls[k * RS + rr] > 0.f) {
+        const float cz = rr >= KIN_ROW ? kin_value(rr - KIN_ROW, U, X, ks) : row_value(rr, U, X, mu);
+        const float z = ap.w[k * RS + rr] / ei[rr];
         r.rp = fmaxf(r.rp, fabsf(cz - z));
         r.sp = fmaxf(r.sp, fmaxf(fabsf(cz), fabsf(z)));
       }
@@ -581,11 +769,18 @@ struct FIn {
   float cr, zr, yr, er;         // box row of u_i (class, slack, multiplier, scaling)
   float cq, zq, yq, eq;         // joint box of x_i
   float cp[4], zp[4], yp[4], kp[4], ep[4];
+  float kc, kz, ky;             // lanes 0-7: kinematic row KIN_ROW + lane (class, slack, multiplier)
 };
 // SC: the problem is Ruiz-scaled (otherwise every scaling factor is 1 and none is loaded)
-template <bool SC>
+template <bool SC, bool KIN>
 __device__ __forceinline__ FIn load_fin(const AgentPtrs& ap, const float* ly, const float* S0, int k, int lane) {
   FIn f;
+  f.kc = f.kz = f.ky = 0.f;
+  if (KIN && lane < KIN_NR) {
+    f.kc = ap.rcls[k * RS + KIN_ROW + lane];
+    f.kz = ap.w[k * RS + KIN_ROW + lane];
+    f.ky = ap.y[k * RS + KIN_ROW + lane];
+  }
   f.u = f.ur = f.x = f.xr = f.yl = f.ck = 0.f;
   f.du = f.dx = f.ed = 1.f;
   f.cr = f.zr = f.yr = f.cq = f.zq = f.yq = 0.f;
@@ -632,7 +827,7 @@ struct BIn {
   float w0, w1, w2, u, x, yl, du, dx;
   float c0, z0, y0, lo0, hi0, e0, c1, z1, y1, lo1, hi1, e1;
 };
-template <bool SC>
+template <bool SC, bool KIN>
 __device__ __forceinline__ BIn load_bin(const AgentPtrs& ap, const float* ly, const float* lw, const float* S0,
                                         int k, int lane) {
   BIn b;
@@ -654,7 +849,7 @@ __device__ __forceinline__ BIn load_bin(const AgentPtrs& ap, const float* ly, co
   const int r0 = lane, r1 = lane + 32;
   b.c0 = ap.rcls[k * RS + r0]; b.z0 = ap.w[k * RS + r0]; b.y0 = ap.y[k * RS + r0];
   b.lo0 = ap.rlo[k * RS + r0]; b.hi0 = ap.rhi[k * RS + r0];
-  if (r1 < NR) {
+  if (r1 < (KIN ? KIN_ROW + KIN_NR : NR)) {
     b.c1 = ap.rcls[k * RS + r1]; b.z1 = ap.w[k * RS + r1]; b.y1 = ap.y[k * RS + r1];
     b.lo1 = ap.rlo[k * RS + r1]; b.hi1 = ap.rhi[k * RS + r1];
   } else {
@@ -664,8 +859,11 @@ __device__ __forceinline__ BIn load_bin(const AgentPtrs& ap, const float* ly, co
 }
 
 constexpr int W_ADMM = 2 * BUF_FLOATS + 96 + 160 + 32 + 4;   // shared floats of the one warp of a block
-template <bool SC>
+constexpr int W_ADMM_KIN = W_ADMM + KIN_SM + 32;               // ... with the kinematic rows
+// KIN: with the kinematic rows (never with SC: the two are not combined)
+template <bool SC, bool KIN>
 __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverParams prm) {
+  static_assert(!(SC && KIN), "the kinematic rows run unscaled");
   const int lane = threadIdx.x;
   const int row = blockIdx.x;
   if (!live_row(a, b, row)) return;
@@ -681,6 +879,8 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
   sg.buf[1] = asm_ + BUF_FLOATS;
   sg.bar = reinterpret_cast<uint64_t*>(cv + 32);
   sg.phase = 0u; sg.pending = 0u; sg.dead = false;
+  float* ks = asm_ + W_ADMM;            // KIN: the kinematic rows' coefficients
+  float* kt = ks + KIN_SM;              // KIN: rho_r z_r - y_r of the stage's kinematic rows
   sg.limit = prm.spin_limit > 0 ? prm.spin_limit : kSpinLimit;
   if (lane == 0) {
     mbar_init(sg.bar, 1);
@@ -693,6 +893,7 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
   const int N = ap.N;
   const float dt = md[M_DT], mu = md[M_MU];
   const float sigma = prm.sigma, alpha = prm.alpha;
+  if (KIN) kin_fill(ks, md, lane);
   const float rho = *ap.rho, rho_eq = 1e3f * rho;
   const float* rec0 = a.lL + (size_t)slot * a.maxN * LDL_REC;
   float* lw = a.lw + (size_t)slot * a.maxN * LDL_W;
@@ -727,17 +928,17 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
   int status = MPC_AGENT_MAX_ITER_, it = 0;
   LdlRes res{0.f, 0.f, 0.f, 0.f};
   const int T = 2 * N;                 // staged items per iteration
-  stage_issue(sg, 0, rec0, N, 0, lane);
+  stage_issue<KIN>(sg, 0, rec0, N, 0, lane);
   for (it = 1; it <= max_it && !sg.dead; ++it) {
     const bool last = it == max_it;
     // ---- forward pass: b_k (+ G_k w_{k-1,x}), w_k = L_k^-1 b_k; the
     // stage's global inputs are loaded one stage ahead
-    FIn fin = load_fin<SC>(ap, ly, S0, 0, lane);
+    FIn fin = load_fin<SC, KIN>(ap, ly, S0, 0, lane);
     for (int k = 0; k < N; ++k) {
       const int t = k, bcur = t & 1;
-      stage_issue(sg, bcur ^ 1, rec0, N, t + 1, lane);
+      stage_issue<KIN>(sg, bcur ^ 1, rec0, N, t + 1, lane);
       const FIn f = fin;
-      if (k + 1 < N) fin = load_fin<SC>(ap, ly, S0, k + 1, lane);
+      if (k + 1 < N) fin = load_fin<SC, KIN>(ap, ly, S0, k + 1, lane);
       float bu = 0.f, bl = 0.f, bx = 0.f;
       if (lane < 30) {
         // sigma x_s - q_s + C_s^T (rho z_s - y_s), q_s = c D q, C_s = E C D
@@ -749,6 +950,17 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
         bl = f.ed * (f.ck + (k ? 0.f : a0x0)) - f.yl / rho_eq;
         bx = sigma * f.x + cs * f.dx * Qx * f.xr;
         if (f.cq > 0.f) bx += f.dx * f.eq * (rho * f.cq * f.zq - f.yq);
+      }
+      if (KIN) {
+        // C^T (rho z - y) of the kinematic rows
+        if (lane < KIN_NR) kt[lane] = rho * f.kc * f.kz - f.ky;
+        __syncwarp();
+        if (lane < 30) {
+#pragma unroll
+          for (int q = 0; q < 6; ++q) bu = fmaf(ks[q * 32 + i], kt[q], bu);
+          if (i >= 6 && i < 9) bx += kt[i - 6] + kt[i - 3];
+          bx = fmaf(ks[6 * 32 + i], kt[6], fmaf(ks[7 * 32 + i], kt[7], bx));
+        }
       }
       stage_wait(sg, bcur);
       if (sg.dead) break;
@@ -764,7 +976,7 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
       }
       __syncwarp();
       float e0 = rb[lane], e1 = rb[lane + 32], e2 = lane < NB - 64 ? rb[lane + 64] : 0.f;
-      fwd_sub(buf + BUF_L, e0, e1, e2, lane);
+      fwd_sub<KIN>(buf + BUF_L, buf + BUF_L31, e0, e1, e2, lane);
       lw[k * LDL_W + lane] = e0;
       lw[k * LDL_W + lane + 32] = e1;
       if (lane < NB - 64) lw[k * LDL_W + lane + 64] = e2;
@@ -777,14 +989,14 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
     if (sg.dead) break;
     // ---- backward pass: v_k = L_k^-T (D_k^-1 w_k + G_{k+1}^T v_{k+1,mult}),
     // then the stage's update; inputs one stage ahead
-    BIn bin = load_bin<SC>(ap, ly, lw, S0, N - 1, lane);
+    BIn bin = load_bin<SC, KIN>(ap, ly, lw, S0, N - 1, lane);
     for (int k = N - 1; k >= 0; --k) {
       const int t = 2 * N - 1 - k, bcur = t & 1;
       // the next item: this iteration's next stage, or the next iteration's first
-      if (t + 1 < T) stage_issue(sg, bcur ^ 1, rec0, N, t + 1, lane);
-      else if (!last) stage_issue(sg, bcur ^ 1, rec0, N, 0, lane);
+      if (t + 1 < T) stage_issue<KIN>(sg, bcur ^ 1, rec0, N, t + 1, lane);
+      else if (!last) stage_issue<KIN>(sg, bcur ^ 1, rec0, N, 0, lane);
       const BIn q = bin;
-      if (k >= 1) bin = load_bin<SC>(ap, ly, lw, S0, k - 1, lane);
+      if (k >= 1) bin = load_bin<SC, KIN>(ap, ly, lw, S0, k - 1, lane);
       stage_wait(sg, bcur);
       if (sg.dead) break;
       const float* buf = sg.buf[bcur];
@@ -801,7 +1013,7 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
       }
       __syncwarp();
       float e0 = rb[lane], e1 = rb[lane + 32], e2 = lane < NB - 64 ? rb[lane + 64] : 0.f;
-      bwd_sub(buf + BUF_L, e0, e1, e2, lane);
+      bwd_sub<KIN>(buf + BUF_L, buf + BUF_L31, e0, e1, e2, lane);
       __syncwarp();
       rb[lane] = e0;
       rb[lane + 32] = e1;
@@ -824,10 +1036,11 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
       for (int h = 0; h < 2; ++h) {
         const int rr = lane + 32 * h;
         const float cl = h ? q.c1 : q.c0;
-        if (rr < NR && cl > 0.f) {
+        if (rr < (KIN ? KIN_ROW + KIN_NR : NR) && cl > 0.f) {
           const float rr_rho = rho * cl;
           const float er = h ? q.e1 : q.e0;
-          const float zt = er * row_value(rr, xv, xv + 32, mu);
+          const float zt = (KIN && rr >= KIN_ROW) ? kin_value(rr - KIN_ROW, xv, xv + 32, ks)
+                                                  : er * row_value(rr, xv, xv + 32, mu);
           const float zo = h ? q.z1 : q.z0, yo = h ? q.y1 : q.y0;
           const float zh = alpha * zt + (1.f - alpha) * zo;
           const float zn = fminf(fmaxf(zh + yo / rr_rho, er * (h ? q.lo1 : q.lo0)), er * (h ? q.hi1 : q.hi0));
@@ -840,7 +1053,7 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
     if (sg.dead) break;
     const bool check = !fixed && (it % every == 0 || last);
     if (check || (fixed && last)) {
-      res = ldl_residuals(ap, ly, S0, cs, xv, lane);
+      res = ldl_residuals(ap, ly, S0, cs, xv, KIN ? ks : nullptr, lane);
       if (!(isfinite(res.rp) && isfinite(res.rd))) { status = MPC_AGENT_NAN_; break; }
       if (check && res.rp <= prm.eps_abs + prm.eps_rel * res.sp && res.rd <= prm.eps_abs + prm.eps_rel * res.sd) {
         status = MPC_AGENT_INACCURATE_;   // ADMM's stopping test, no polish: not certified
@@ -893,38 +1106,43 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
 
 }  // namespace
 
-size_t ldl_factor_smem_bytes() { return F_FLOATS * sizeof(float); }
+template <typename K>
+static cudaError_t set_smem(K kern, int floats, bool carveout) {
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(floats * sizeof(float)));
+  if (e == cudaSuccess && carveout)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+  return e;
+}
 
 cudaError_t launch_ldl(const Arena& a, const Batch& b, const SolverParams& prm, cudaStream_t st, int* launches) {
   static int configured = -1;
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured != dev) {
-    cudaError_t e = cudaFuncSetAttribute(mpc_k_ldl_factor, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(F_FLOATS * sizeof(float)));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mpc_k_ldl_admm<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(W_ADMM * sizeof(float)));
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mpc_k_ldl_admm<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)(W_ADMM * sizeof(float)));
-    // the iteration kernel's one-warp blocks hold about 40 KB of shared memory:
-    // ask for the largest shared-memory carveout, so that five fit on an SM
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mpc_k_ldl_admm<false>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(mpc_k_ldl_admm<true>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared);
+    // the iteration kernel's one-warp blocks hold about 35 KB of shared
+    // memory: it asks for the largest shared-memory carveout, so that six fit
+    // on an SM
+    cudaError_t e = set_smem(mpc_k_ldl_factor<false>, F_FLOATS, false);
+    if (e == cudaSuccess) e = set_smem(mpc_k_ldl_factor<true>, F_FLOATS + F_KIN, false);
+    if (e == cudaSuccess) e = set_smem(mpc_k_ldl_admm<false, false>, W_ADMM, true);
+    if (e == cudaSuccess) e = set_smem(mpc_k_ldl_admm<true, false>, W_ADMM, true);
+    if (e == cudaSuccess) e = set_smem(mpc_k_ldl_admm<false, true>, W_ADMM_KIN, true);
     if (e != cudaSuccess) return e;
     configured = dev;
   }
   if (b.n <= 0) return cudaSuccess;
+  if (prm.kin && prm.ruiz > 0) return cudaErrorInvalidValue;
   mpc_k_ldl_ruiz<<<b.n, 32, 2 * 30 * 31 * sizeof(float), st>>>(a, b, prm);
-  mpc_k_ldl_factor<<<b.n, 32, F_FLOATS * sizeof(float), st>>>(a, b, prm);
-  if (prm.ruiz > 0) mpc_k_ldl_admm<true><<<b.n, 32, W_ADMM * sizeof(float), st>>>(a, b, prm);
-  else mpc_k_ldl_admm<false><<<b.n, 32, W_ADMM * sizeof(float), st>>>(a, b, prm);
-  if (launches) *launches += 3;
+  if (prm.kin) {
+    mpc_k_ldl_kin<<<b.n, 32, 0, st>>>(a, b, prm);
+    mpc_k_ldl_factor<true><<<b.n, 32, (F_FLOATS + F_KIN) * sizeof(float), st>>>(a, b, prm);
+    mpc_k_ldl_admm<false, true><<<b.n, 32, W_ADMM_KIN * sizeof(float), st>>>(a, b, prm);
+  } else {
+    mpc_k_ldl_factor<false><<<b.n, 32, F_FLOATS * sizeof(float), st>>>(a, b, prm);
+    if (prm.ruiz > 0) mpc_k_ldl_admm<true, false><<<b.n, 32, W_ADMM * sizeof(float), st>>>(a, b, prm);
+    else mpc_k_ldl_admm<false, false><<<b.n, 32, W_ADMM * sizeof(float), st>>>(a, b, prm);
+  }
+  if (launches) *launches += prm.kin ? 4 : 3;
   return cudaGetLastError();
 }
 

@@ -237,6 +237,7 @@ extern "C" mpc_status mpc_solve_static(int32_t n, const mpc_agent_model* models_
   prm.wait_test_slot = -1;
   prm.defer = 0;
   prm.ruiz = 0;
+  prm.kin = 0;
   mpc::Batch bt{n, d_ids, x0, qd_meas, cmd, phase, nullptr, nullptr};
   if (mpc::launch_solve(a, bt, prm, MPC_FORM_FUSED, 0, st, nullptr, c.variant) != cudaSuccess) return MPC_ERR_CUDA;
   if (mpc::launch_gather(a, n, d_ids, tau, q_set, qd_set, value, agent_status, st) != cudaSuccess)

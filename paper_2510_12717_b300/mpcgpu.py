@@ -38,7 +38,8 @@ class MpcConfig(C.Structure):
         ("polish", C.c_int), ("warm_start", C.c_int), ("variant", C.c_int),
         ("early_polish", C.c_float), ("graph", C.c_int), ("warm_polish", C.c_int),
         ("refine_steps", C.c_int), ("spin_limit", C.c_int), ("wait_test_agent", C.c_int),
-        ("ruiz_iters", C.c_int),
+        ("ruiz_iters", C.c_int), ("kin_rows", C.c_int), ("swing_height", C.c_float),
+        ("v_takeoff", C.c_float), ("v_touchdown", C.c_float),
     ]
 
 

@@ -63,6 +63,8 @@ def test_default_config_and_argument_errors(lib):
     cfg = mpcgpu.MpcConfig()
     assert lib.mpc_default_config(C.byref(cfg)) == 0
     assert cfg.max_horizon == 20 and abs(cfg.rho0 - 0.1) < 1e-7 and cfg.polish == 1
+    assert cfg.kin_rows == 0 and abs(cfg.swing_height - 0.075) < 1e-7
+    assert abs(cfg.v_takeoff - 0.1) < 1e-7 and abs(cfg.v_touchdown + 0.1) < 1e-7
     h = C.c_void_p()
     bad = mpcgpu.MpcConfig()
     lib.mpc_default_config(C.byref(bad))
@@ -79,6 +81,17 @@ def test_default_config_and_argument_errors(lib):
     assert lib.mpc_create(C.byref(bad), C.byref(h)) == mpcgpu.MPC_ERR_INVALID
     bad.refine_steps = -1
     bad.precision = mpcgpu.FP32
+    bad.kin_rows = 1                  # the kinematic rows: literal form only
+    assert lib.mpc_create(C.byref(bad), C.byref(h)) == mpcgpu.MPC_ERR_INVALID
+    bad.form = mpcgpu.FORM_LDL
+    bad.ruiz_iters = 5                # ... and not with the Ruiz scaling
+    assert lib.mpc_create(C.byref(bad), C.byref(h)) == mpcgpu.MPC_ERR_INVALID
+    bad.ruiz_iters = 0
+    bad.swing_height = float("nan")
+    assert lib.mpc_create(C.byref(bad), C.byref(h)) == mpcgpu.MPC_ERR_INVALID
+    bad.swing_height = 0.075
+    bad.kin_rows = 0
+    bad.form = mpcgpu.FORM_FUSED
     bad.hbm_budget_bytes = 1024       # far below what 16 agents need
     assert lib.mpc_create(C.byref(bad), C.byref(h)) == mpcgpu.MPC_ERR_BUDGET
     assert lib.mpc_destroy(None) == mpcgpu.MPC_ERR_INVALID

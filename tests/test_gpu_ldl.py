@@ -158,3 +158,98 @@ def test_literal_budget_counts_the_factors():
     with pytest.raises(mpcgpu.MpcError):
         mpcgpu.Solver(max_agents=256, max_horizon=20, form=mpcgpu.FORM_LDL, fixed_iters=25,
                       hbm_budget_bytes=64 << 20, stream=torch.cuda.current_stream().cuda_stream)
+
+
+# the kinematic rows of Eq. mpc_formulation (no-slip, swing height on the
+# Bezier curve of Eqs. bezier_1-5): both sides build them from their own data
+KIN = dict(z_swing=0.075, v_to=0.1, v_td=-0.1)
+KIN_OPTS = dict(kin_rows=1, swing_height=0.075, v_takeoff=0.1, v_touchdown=-0.1)
+
+
+def _oracle_kin(model, inp32, a, iters):
+    from oracle import osqp
+    from oracle.solve import agent_params
+    mo, io = oracle_view(model, inp32)
+    m = agent_params(mo, a)
+    return osqp.literal_agent(m, io["x0"][a], io["cmd"][a], io["phase"][a], io["qd_meas"][a], iters, kin=KIN)
+
+
+@pytest.mark.parametrize("name,n", [("small", 16), ("uneven", 10)])
+@pytest.mark.parametrize("iters", [1, 25])
+def test_literal_kinematic_rows_iterations_match_oracle(name, n, iters):
+    mpcgpu = _lib()
+    model, inp = agents(name, np.arange(n))
+    inp32 = device_inputs(inp)
+    r = _solve(mpcgpu, model, inp32, fixed_iters=iters, **KIN_OPTS)
+    assert (r["status"] == mpcgpu.AGENT_MAX_ITER).all()
+    far = 0
+    for a in range(n):
+        o = _oracle_kin(model, inp32, a, iters)
+        st = r["state"][a]
+        su = 1.0 + np.abs(o["u"]).max()
+        sx = 1.0 + np.abs(o["x"]).max()
+        assert np.abs(st["u"] - o["u"]).max() <= 1e-4 * su, a
+        assert np.abs(st["x"] - o["x"]).max() <= 1e-4 * sx, a
+        ok = torque_close(r["tau"][a], o["tau"])
+        assert ok.all(), (a, np.abs(r["tau"][a] - o["tau"]).max())
+        # the rows matter: the iterate without them is elsewhere
+        o0 = _oracle(model, inp32, a, iters)
+        far += not torque_close(r["tau"][a], o0["tau"]).all()
+    assert far >= n // 2, far
+
+
+def test_literal_kinematic_rows_converged_mode():
+    from oracle import osqp, qp as qpmod
+    from oracle.solve import agent_params
+    mpcgpu = _lib()
+    model, inp = agents("small", np.arange(16))
+    inp32 = device_inputs(inp)
+    r = _solve(mpcgpu, model, inp32, fixed_iters=0, max_iter=4000, check_every=10, **KIN_OPTS)
+    mo, io = oracle_view(model, inp32)
+    its = []
+    matched = 0
+    for a in range(16):
+        m = agent_params(mo, a)
+        qp, _ = qpmod.agent_qp(m, io["x0"][a], io["cmd"][a], io["phase"][a], kin=KIN)
+        lq = osqp.literal_form(qp, 0.1)
+        x, z, y = osqp.start_point(lq, qp, io["x0"][a], np.asarray(m["q_nom"], float))
+        x, z, y, it = osqp.solve_until(lq, x, z, y, max_iter=4000, check_every=10)
+        got = int(r["stats"]["iters"][a])
+        if it < 1000:
+            assert abs(got - it) <= 10, (a, got, it)
+            assert r["status"][a] == mpcgpu.AGENT_INACCURATE
+            matched += 1
+        else:
+            assert abs(got - it) <= 0.1 * it + 20, (a, got, it)
+        its.append((got, it))
+    print(f"\n[literal converged, kinematic rows] (gpu, oracle) iterations: {its}")
+    assert matched >= 8
+
+
+def test_literal_kinematic_rows_full_size_sampled():
+    # 16384 agents of mixed horizons and gaits, N_QP = 25, one launch
+    mpcgpu = _lib()
+    n = 16384
+    model, inp = agents("mixed16k", np.arange(n))
+    inp32 = device_inputs(inp)
+    dev = torch.device("cuda:0")
+    t = {k: torch.from_numpy(v).to(dev) for k, v in inp32.items()}
+    ids = torch.arange(n, dtype=torch.int32, device=dev)
+    s = mpcgpu.Solver(max_agents=n, max_horizon=20, form=mpcgpu.FORM_LDL, fixed_iters=25,
+                      stream=torch.cuda.current_stream().cuda_stream, **KIN_OPTS)
+    s.set_models(model, np.arange(n))
+    tk = s.submit(ids, t["x0"], t["qd_meas"], t["cmd"], t["phase"])
+    s.solve(tk)
+    tau = torch.empty((n, 18), device=dev)
+    st = torch.empty(n, dtype=torch.int32, device=dev)
+    s.get_torques(tk, tau=tau, status=st)
+    torch.cuda.synchronize()
+    s.close()
+    tau = tau.cpu().numpy()
+    assert (st.cpu().numpy() == mpcgpu.AGENT_MAX_ITER).all()
+    Nh = model["N"]
+    sample = [int(np.flatnonzero(Nh == h)[0]) for h in (5, 9, 13, 17, 20)] + [n - 1, n // 2]
+    for a in sample:
+        o = _oracle_kin(model, inp32, a, 25)
+        ok = torque_close(tau[a], o["tau"])
+        assert ok.all(), (a, np.abs(tau[a] - o["tau"]).max())
