@@ -82,9 +82,15 @@ LDL_L, LDL_G, LDL_D = 3105, 900, 90
 LDL_STATE = 2 * 3 * 30 + 2 * 2 * 56 + 3 * 56 + 3 * 30 + 2 * 90
 
 
-def ldl_bytes_per_iteration(N):
+# With the kinematic rows each pass also reads the three rows of L31 that they
+# fill (96 floats staged), and their eight rows' slack and multiplier are read
+# and written, their bounds and classes read.
+LDL_KIN = 2 * 96 + 2 * 2 * 8 + 3 * 8
+
+
+def ldl_bytes_per_iteration(N, kin=0):
     N = np.asarray(N, dtype=np.int64)
-    floats = N * (2 * LDL_L + LDL_D + LDL_STATE) + 2 * (N - 1) * LDL_G
+    floats = N * (2 * LDL_L + LDL_D + LDL_STATE + (LDL_KIN if kin else 0)) + 2 * (N - 1) * LDL_G
     return 4 * floats
 # DRAM bytes per agent of one solve step (order, set-up, persistent solve,
 # torque and RNEA kernels), measured with ncu on 2048 agents of the same
@@ -547,31 +553,37 @@ def run_ours(args):
     # only (parity with the oracle's literal iteration: tests/test_gpu_ldl.py).
     # The iteration kernel's time is the difference of the 25- and the
     # 1-iteration replans over 24 (the same set-up, factor and torque map)
-    literal = None
-    if not args.no_literal:
+    def literal_leg(kin):
         K4 = min(args.steps, 3)
         lt = {}
         for fi in (25, 1):
             sl, tl, perl, ll, _, statl, _, _ = timed(mpcgpu.FORM_LDL, K4, args.warmup, tune=False,
-                                                      keep_report=False, fixed_iters=fi)
+                                                      keep_report=False, fixed_iters=fi, kin_rows=kin)
             lt[fi] = (tl / K4, perl, ll // K4, statl)
             sl.close()
         it_ms = (lt[25][0] - lt[1][0]) / 24.0
-        bytes_it = float(ldl_bytes_per_iteration(Nh).sum())
+        bytes_it = float(ldl_bytes_per_iteration(Nh, kin).sum())
         gbs = bytes_it / (it_ms / 1e3) / 1e9 if it_ms > 0 else None
-        literal = {"value": world * n / (lt[25][0] / 1e3), "ms_per_step": lt[25][0],
-                   "p50_ms": float(np.percentile(lt[25][1], 50)), "admm_iters": 25,
-                   "factor_and_one_iteration_ms": lt[1][0], "iteration_ms": it_ms,
-                   "gpu_launches_per_step": lt[25][2],
-                   "status_max_iter_frac": float((lt[25][3] == 1).mean()),
-                   "roofline": {"kernel": "mpc_k_ldl_admm (one OSQP iteration over all agents)", "bound": "hbm",
-                                "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
-                                "frac": None if gbs is None else gbs / HBM_PEAK_GBS,
-                                "bytes_per_iteration": bytes_it,
-                                "peak_basis": f"{HBM_PEAK_KIND} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
-                   "note": "paper's literal Alg. 1: OSQP ADMM on the full KKT system, block LDL^T once per "
-                           "replan, 25 forward/backward substitutions, cold start f_init each replan, no polish; "
-                           "A/B against the Riccati form's paper_mode_fixed25"}
+        rows = ("with the kinematic rows of Eq. mpc_formulation (no-slip, swing height on the Bezier curve), "
+                if kin else "")
+        return {"value": world * n / (lt[25][0] / 1e3), "ms_per_step": lt[25][0],
+                "p50_ms": float(np.percentile(lt[25][1], 50)), "admm_iters": 25,
+                "factor_and_one_iteration_ms": lt[1][0], "iteration_ms": it_ms,
+                "gpu_launches_per_step": lt[25][2],
+                "status_max_iter_frac": float((lt[25][3] == 1).mean()),
+                "roofline": {"kernel": "mpc_k_ldl_admm (one OSQP iteration over all agents)", "bound": "hbm",
+                             "achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s",
+                             "frac": None if gbs is None else gbs / HBM_PEAK_GBS,
+                             "bytes_per_iteration": bytes_it,
+                             "peak_basis": f"{HBM_PEAK_KIND} copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
+                "note": "paper's literal Alg. 1: OSQP ADMM on the full KKT system " + rows +
+                        "block LDL^T once per replan, 25 forward/backward substitutions, cold start f_init each "
+                        "replan, no polish; A/B against the Riccati form's paper_mode_fixed25"}
+
+    literal = literal_kin = None
+    if not args.no_literal:
+        literal = literal_leg(0)
+        literal_kin = literal_leg(1)
 
     precision = None
     if not args.no_precision:
@@ -613,6 +625,7 @@ def run_ours(args):
         "plain": plain,
         "paper_mode_fixed25": paper_mode,
         "literal_ldl_fixed25": literal,
+        "literal_ldl_kin_fixed25": literal_kin,
         "precision": precision,
         "residual_policy": policy,
         "serving": serving,

@@ -373,6 +373,7 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
             Y31[r3c * 33 + c] = y3[c];
           }
         }
+        __syncwarp();
       }
       float y[30];
 #pragma unroll
@@ -384,6 +385,16 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
       float ys[30];
 #pragma unroll
       for (int c = 0; c < 30; ++c) ys[c] = y[c] / __shfl_sync(FULL, d, c);
+      if (KIN && g == 0) {
+        // column l of rows 6-8 of L31 D1 L21^T, from this lane's row of L21
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+          float acc = 0.f;
+#pragma unroll
+          for (int m = 0; m < 30; ++m) acc = fmaf(Y31[q * 33 + m], ys[m], acc);
+          if (lane < 30) M32[q * 33 + l] = acc;
+        }
+      }
       if (g < 2) {
         put_row<false>(rec, 30 * (g + 1) + l, 30 * g, ys, lane);
       } else if (lane < 30) {
@@ -424,12 +435,7 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_factor(Arena a, Batch b, SolverP
         } else mrow[s2] = acc;
       }
       if (KIN && g == 0 && is3) {
-        // rows 6-8 of L31 D1 L21^T (T holds the scaled rows of L21) and of L31 D1 L31^T
-        for (int s2 = 0; s2 < 30; ++s2) {
-          float acc = 0.f;
-          for (int m = 0; m < 30; ++m) acc = fmaf(Y31[r3c * 33 + m], T[s2 * 32 + m], acc);
-          M32[r3c * 33 + s2] = acc;
-        }
+        // rows 6-8 of L31 D1 L31^T
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
           float acc = 0.f;
