@@ -81,3 +81,15 @@ def test_flop_model():
     two = b.flops_per_agent(N, zero, zero, np.array([2, 2]), attempts=2.0)
     assert np.allclose(two - polished, polished)          # a second reduced solve costs the same
     assert b.attempts_mean([0, 3, 1]) == 1.25
+
+
+def test_literal_bytes_per_iteration():
+    b = _bench()
+    # per stage: L by columns and by rows (3105 each), 1/D (90), the state and
+    # row data; G_k in both passes for the stages that couple to a neighbour
+    one = 4 * (2 * 3105 + 90 + b.LDL_STATE)
+    assert b.ldl_bytes_per_iteration(np.array([1]))[0] == one
+    assert b.ldl_bytes_per_iteration(np.array([3]))[0] == 3 * one + 4 * 2 * 2 * 900
+    # the kinematic rows: the L31 rows staged in both passes, the eight rows' data
+    kin = b.ldl_bytes_per_iteration(np.array([3]), kin=1)[0] - b.ldl_bytes_per_iteration(np.array([3]))[0]
+    assert kin == 3 * 4 * (2 * 96 + 2 * 2 * 8 + 3 * 8)
