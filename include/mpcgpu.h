@@ -435,7 +435,10 @@ mpc_status mpc_import_state(mpc_ctx* ctx, int32_t agent_id, const float* x_host,
  * every GPU loading this library holds until the process exits; no call
  * allocates or frees device memory.
  *   - The first call on a device resolves the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current).
+ *   - A call cannot be captured into a CUDA graph: it copies the packed
+ *     models from pageable host staging, and a replay would read whatever a
+ *     later call packed there.
  *   - Every call shares the one device array, which keeps the previous
  *     call's contents (warm-start markers and the horizons of unused slots
  *     are cleared each call), and the packed models pass through host
