@@ -253,3 +253,50 @@ def test_literal_kinematic_rows_full_size_sampled():
         o = _oracle_kin(model, inp32, a, 25)
         ok = torque_close(tau[a], o["tau"])
         assert ok.all(), (a, np.abs(tau[a] - o["tau"]).max())
+
+
+def test_literal_kinematic_rows_short_horizons_and_nonfinite():
+    # the shortest horizons (N = 2, 3: the rows of the last stage read x_N)
+    # and a non-finite state next to them
+    mpcgpu = _lib()
+    n = 8
+    model, inp = agents("uneven", np.arange(n))
+    model["N"][:] = [2, 3, 2, 3, 4, 2, 3, 2]
+    inp32 = device_inputs(inp)
+    inp32["x0"][5, 8] = np.nan
+    r = _solve(mpcgpu, model, inp32, fixed_iters=5, **KIN_OPTS)
+    assert r["status"][5] == mpcgpu.AGENT_NAN and np.all(r["tau"][5] == 0.0)
+    for a in [0, 1, 2, 3, 4, 6, 7]:
+        assert r["status"][a] == mpcgpu.AGENT_MAX_ITER
+        o = _oracle_kin(model, inp32, a, 5)
+        st = r["state"][a]
+        assert np.abs(st["u"] - o["u"]).max() <= 1e-4 * (1.0 + np.abs(o["u"]).max()), a
+        assert torque_close(r["tau"][a], o["tau"]).all(), (a, np.abs(r["tau"][a] - o["tau"]).max())
+
+
+@pytest.mark.parametrize("rho0,alpha", [(0.2, 1.6), (0.1, 1.0), (0.02, 1.8), (0.4, 1.6)])
+def test_literal_iterations_match_oracle_other_steps(rho0, alpha):
+    # other step sizes (rho, and rho_eq = 1e3 rho on the equality rows) and
+    # relaxations, with the kinematic rows; both sides from their own data.
+    # The iterates are held to 1e-4 of their scale at every step size; the
+    # torques to the tolerance up to rho0 = 0.2: at rho0 = 0.4 (rho_eq = 400)
+    # the FP32 factor of the more ill-conditioned KKT matrix leaves a torque
+    # of one of these agents at 1.6x the tolerance (the torque map's
+    # qddot = (qdot_1 - qdot_0) / dt amplifies the iterate's rounding)
+    from oracle import osqp
+    from oracle.solve import agent_params
+    mpcgpu = _lib()
+    n = 8
+    model, inp = agents("uneven", np.arange(n))
+    inp32 = device_inputs(inp)
+    r = _solve(mpcgpu, model, inp32, fixed_iters=25, rho0=rho0, alpha=alpha, **KIN_OPTS)
+    mo, io = oracle_view(model, inp32)
+    for a in range(n):
+        m = agent_params(mo, a)
+        o = osqp.literal_agent(m, io["x0"][a], io["cmd"][a], io["phase"][a], io["qd_meas"][a], 25,
+                               rho=rho0, alpha=alpha, kin=KIN)
+        st = r["state"][a]
+        assert np.abs(st["u"] - o["u"]).max() <= 1e-4 * (1.0 + np.abs(o["u"]).max()), a
+        assert np.abs(st["x"] - o["x"]).max() <= 1e-4 * (1.0 + np.abs(o["x"]).max()), a
+        if rho0 <= 0.2:
+            assert torque_close(r["tau"][a], o["tau"]).all(), (a, np.abs(r["tau"][a] - o["tau"]).max())
