@@ -25,6 +25,10 @@ Sec. III-B Eq. (kkt_system); Sec. III-C Alg. 1, Eqs. (rnea), (mpc_torque)):
   kkt.py     KKT stationarity / feasibility / complementarity checks (a pin)
   feasibility.py  primal feasibility of the QP's constraint set (an LP by
              HiGHS), the reference for the solver's infeasibility status
+  osqp.py    the literal iteration: OSQP's ADMM on the full KKT system
+             (Eq. kkt_system), with the optional Ruiz equilibration
+  admm.py    the Riccati forms' iteration: the same ADMM with the dynamics
+             exact in every x-update (the paper's fixed-N_QP mode)
 
 Pins (tests/test_oracle_*.py, all CPU): closed-form LQR when no constraint is
 active, brute-force active sets on toy QPs, KKT invariants on every solve,

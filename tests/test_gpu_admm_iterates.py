@@ -1,0 +1,72 @@
+"""Iterate-for-iterate parity of the Riccati forms' ADMM (the paper's
+fixed-N_QP mode: Alg. 1 with N_QP iterations, no polish) against the oracle's
+ADMM with exact dynamics in the x-update (oracle/admm.py).
+
+Cold start (f_init), fixed rho, no polish: after N_QP iterations both sides
+hold the same iterate (u, x, the row slacks w and multipliers y), not the
+QP's optimum.  Bars: the iterate within 1e-4 of its own scale (FP32 Riccati
+factors; the literal form meets the same bar), torques within the north-star
+tolerance.
+"""
+import numpy as np
+import pytest
+
+from helpers import agents, device_inputs, oracle_view, torque_close
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _lib():
+    import __graft_entry__ as g
+    g.build()
+    from paper_2510_12717_b300 import mpcgpu
+    return mpcgpu
+
+
+def _oracle(model, inp32, a, iters, rho=0.1, alpha=1.6):
+    from oracle import admm, qp as qpmod, torque
+    from oracle.solve import agent_params
+    mo, io = oracle_view(model, inp32)
+    m = agent_params(mo, a)
+    x0 = io["x0"][a]
+    qp, _ = qpmod.agent_qp(m, x0, io["cmd"][a], io["phase"][a])
+    z, w, y = admm.start_point(qp, x0, np.asarray(m["q_nom"], float), rho)
+    z, w, y = admm.iterate(qp, z, w, y, iters, rho=rho, alpha=alpha)
+    N = qp.N
+    u = np.stack([qp.u(z, k) for k in range(N)])
+    xs = np.vstack([x0[None, :]] + [qp.x(z, k)[None, :] for k in range(1, N + 1)])
+    tau, _, _ = torque.torque_map(m, x0, io["qd_meas"][a], u[0], u[1], x1=xs[1])
+    keep, _ = admm.row_steps(qp, rho)
+    return dict(u=u, x=xs, w=w, y=y, keep=keep, tau=tau)
+
+
+@pytest.mark.parametrize("form", ["fused", "plain"])
+@pytest.mark.parametrize("name,n", [("small", 16), ("uneven", 12)])
+@pytest.mark.parametrize("iters", [1, 25])
+def test_admm_iterates_match_oracle(form, name, n, iters):
+    mpcgpu = _lib()
+    model, inp = agents(name, np.arange(n))
+    inp32 = device_inputs(inp)
+    fm = mpcgpu.FORM_FUSED if form == "fused" else mpcgpu.FORM_PLAIN
+    s = mpcgpu.Solver(max_agents=n, max_horizon=20, form=fm, fixed_iters=iters, polish=0, warm_polish=0,
+                      early_polish=0.0, adaptive_rho=0, warm_start=0,
+                      stream=torch.cuda.current_stream().cuda_stream)
+    s.set_models(model, np.arange(n))
+    r = s.solve_host(np.arange(n), inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+    states = [s.export_state(a, int(model["N"][a])) for a in range(n)]
+    s.close()
+    assert (r["status"] == mpcgpu.AGENT_MAX_ITER).all()
+    for a in range(n):
+        o = _oracle(model, inp32, a, iters)
+        st = states[a]
+        su = 1.0 + np.abs(o["u"]).max()
+        sx = 1.0 + np.abs(o["x"]).max()
+        assert np.abs(st["u"] - o["u"]).max() <= 1e-4 * su, (a, np.abs(st["u"] - o["u"]).max())
+        assert np.abs(st["x"] - o["x"]).max() <= 1e-4 * sx, (a, np.abs(st["x"] - o["x"]).max())
+        w = st["w"].reshape(-1)[o["keep"]]
+        y = st["y"].reshape(-1)[o["keep"]]
+        assert np.abs(w - o["w"]).max() <= 1e-4 * (1.0 + np.abs(o["w"]).max()), a
+        assert np.abs(y - o["y"]).max() <= 1e-4 * (1.0 + np.abs(o["y"]).max()), a
+        ok = torque_close(r["tau"][a], o["tau"])
+        assert ok.all(), (a, np.abs(r["tau"][a] - o["tau"]).max())
