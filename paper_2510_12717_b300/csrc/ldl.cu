@@ -626,7 +626,9 @@ __device__ __forceinline__ void bwd_sub(const float* Lr, const float* L3, float&
 // buffers by bulk copies (completion on the buffer's mbarrier) while the
 // previous item computes.  A wait gives up after `limit` polls: the warp then
 // issues nothing more, waits (bounded) for the copies in flight and ends the
-// agent's solve with MPC_AGENT_TIMEOUT.
+// agent's solve with MPC_AGENT_TIMEOUT.  `dry` (failure-detection test only)
+// arms the first item's barrier with no copy behind it, so that its wait runs
+// out with nothing in flight into that buffer.
 constexpr int BUF_L = 0, BUF_G = 3108, BUF_D = 4008, BUF_L31 = 4104, BUF_FLOATS = 4200;
 struct Stager {
   float* buf[2];
@@ -634,6 +636,7 @@ struct Stager {
   uint32_t phase;     // bit b: parity of buffer b's next completion
   uint32_t pending;   // bit b: a copy into buffer b not yet waited for
   bool dead;
+  bool dry;
   int limit;
 };
 // KIN: the items carry the three rows of L31 too
@@ -641,6 +644,12 @@ template <bool KIN>
 __device__ __forceinline__ void stage_issue(Stager& sg, int b, const float* rec0, int N, int t, int lane) {
   if (sg.dead) return;
   __syncwarp();   // every lane is done with the buffer's previous contents
+  if (sg.dry) {
+    // armed for a copy that is never issued (nothing in flight: not pending)
+    if (lane == 0) mbar_expect_tx(sg.bar + b, (LDL_ROW - LDL_COL) * 4);
+    sg.dry = false;
+    return;
+  }
   if (lane == 0) {
     const bool fwd = t < N;
     const int k = fwd ? t : 2 * N - 1 - t;
@@ -885,6 +894,7 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
   sg.buf[1] = asm_ + BUF_FLOATS;
   sg.bar = reinterpret_cast<uint64_t*>(cv + 32);
   sg.phase = 0u; sg.pending = 0u; sg.dead = false;
+  sg.dry = slot == prm.wait_test_slot;
   float* ks = asm_ + W_ADMM;            // KIN: the kinematic rows' coefficients
   float* kt = ks + KIN_SM;              // KIN: rho_r z_r - y_r of the stage's kinematic rows
   sg.limit = prm.spin_limit > 0 ? prm.spin_limit : kSpinLimit;

@@ -64,3 +64,34 @@ def test_spin_limit_and_test_agent_are_validated(mpcgpu):
         mpcgpu.Solver(max_agents=4, max_horizon=10, spin_limit=0)
     with pytest.raises(mpcgpu.MpcError):
         mpcgpu.Solver(max_agents=4, max_horizon=10, wait_test_agent=4)
+
+
+def test_literal_form_wait_that_runs_out_times_out_one_agent(mpcgpu):
+    # the literal form's bulk copies of the stage factors (one warp per agent):
+    # the first staged item of one agent is armed with no copy behind it
+    n, bad = 12, 5
+    ids = np.arange(n)
+    model, inp = agents("uneven", ids)
+    inp32 = device_inputs(inp)
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def solve(**opts):
+        s = mpcgpu.Solver(max_agents=n, max_horizon=20, form=mpcgpu.FORM_LDL, fixed_iters=5, stream=stream,
+                          **opts)
+        s.set_models(model, ids)
+        out = s.solve_host(ids, inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+        stats = s.stats()
+        s.close()
+        return out, stats
+
+    ref, ref_stats = solve()
+    got, stats = solve(spin_limit=1 << 12, wait_test_agent=bad)
+    assert ref_stats["wait_timeouts"] == 0 and stats["wait_timeouts"] == 1
+    others = np.setdiff1d(ids, [bad])
+    assert (ref["status"] == mpcgpu.AGENT_MAX_ITER).all()
+    assert got["status"][bad] == mpcgpu.AGENT_TIMEOUT
+    assert (got["tau"][bad] == 0).all()
+    assert (got["status"][others] == mpcgpu.AGENT_MAX_ITER).all()
+    assert np.array_equal(got["tau"][others], ref["tau"][others])
+    again, again_stats = solve()
+    assert again_stats["wait_timeouts"] == 0 and np.array_equal(again["tau"], ref["tau"])
