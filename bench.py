@@ -96,7 +96,7 @@ def ldl_bytes_per_iteration(N, kin=0):
 # torque and RNEA kernels), measured with ncu on 2048 agents of the same
 # workload and kernel version and scaled per agent (the step's traffic grows
 # with the agents it solves); None once the kernels have changed since.
-TRAFFIC_BYTES_PER_AGENT = (287.37e6 + 190.97e6) / 2048
+TRAFFIC_BYTES_PER_AGENT = (285.39e6 + 192.59e6) / 2048
 
 
 def parse():
