@@ -183,6 +183,7 @@ def pack_models(model: dict, idx=None) -> np.ndarray:
 
 STATIC_MAX_AGENTS = 64
 STATIC_MAX_HORIZON = 20
+MAX_HORIZON = 32          # MPC_MAX_HORIZON: the largest horizon a context may take
 
 
 def solve_static(model: dict, x0, qd_meas, cmd, phase, *, tau=None, q_set=None, qd_set=None,

@@ -117,3 +117,11 @@ def test_form_values_match_header():
     src = open(HEADER).read()
     m = re.search(r"MPC_FORM_PLAIN = (\d+), MPC_FORM_FUSED = (\d+), MPC_FORM_LDL = (\d+)", src)
     assert m and tuple(int(v) for v in m.groups()) == (mpcgpu.FORM_PLAIN, mpcgpu.FORM_FUSED, mpcgpu.FORM_LDL)
+
+
+def test_max_horizon_matches_header():
+    import re
+    from paper_2510_12717_b300 import mpcgpu
+    src = open(os.path.join(ROOT, "include", "mpcgpu.h")).read()
+    m = re.search(r"#define MPC_MAX_HORIZON (\d+)", src)
+    assert m and int(m.group(1)) == mpcgpu.MAX_HORIZON

@@ -125,3 +125,27 @@ def test_warm_started_admm_iterates_match_oracle(form):
         xs = np.vstack([io["x0"][a][None, :], x])
         tau, _, _ = torque.torque_map(m, io["x0"][a], io["qd_meas"][a], u[0], u[1], x1=xs[1])
         assert torque_close(r["tau"][a], tau).all(), (a, np.abs(r["tau"][a] - tau).max())
+
+
+@pytest.mark.parametrize("form", ["fused", "plain"])
+def test_admm_iterates_longest_horizon(form):
+    # the largest horizon the API allows (32 stages)
+    mpcgpu = _lib()
+    n = 4
+    model, inp = agents("uneven", np.arange(n))
+    model["N"][:] = mpcgpu.MAX_HORIZON
+    inp32 = device_inputs(inp)
+    fm = mpcgpu.FORM_FUSED if form == "fused" else mpcgpu.FORM_PLAIN
+    s = mpcgpu.Solver(max_agents=n, max_horizon=mpcgpu.MAX_HORIZON, form=fm, fixed_iters=5, polish=0,
+                      warm_polish=0, early_polish=0.0, adaptive_rho=0, warm_start=0,
+                      stream=torch.cuda.current_stream().cuda_stream)
+    s.set_models(model, np.arange(n))
+    r = s.solve_host(np.arange(n), inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+    states = [s.export_state(a, mpcgpu.MAX_HORIZON) for a in range(n)]
+    s.close()
+    assert (r["status"] == mpcgpu.AGENT_MAX_ITER).all()
+    for a in range(n):
+        o = _oracle(model, inp32, a, 5)
+        assert np.abs(states[a]["u"] - o["u"]).max() <= 1e-4 * (1.0 + np.abs(o["u"]).max()), a
+        assert np.abs(states[a]["x"] - o["x"]).max() <= 1e-4 * (1.0 + np.abs(o["x"]).max()), a
+        assert torque_close(r["tau"][a], o["tau"]).all(), (a, np.abs(r["tau"][a] - o["tau"]).max())

@@ -300,3 +300,26 @@ def test_literal_iterations_match_oracle_other_steps(rho0, alpha):
         assert np.abs(st["x"] - o["x"]).max() <= 1e-4 * (1.0 + np.abs(o["x"]).max()), a
         if rho0 <= 0.2:
             assert torque_close(r["tau"][a], o["tau"]).all(), (a, np.abs(r["tau"][a] - o["tau"]).max())
+
+
+@pytest.mark.parametrize("kin", [0, 1])
+def test_literal_longest_horizon(kin):
+    # the largest horizon the API allows (MPC_MAX_HORIZON = 32 stages): the
+    # staged items, the record strides and (kin) the one-lane-per-stage row
+    # set-up at their limits
+    mpcgpu = _lib()
+    n = 3
+    model, inp = agents("uneven", np.arange(n))
+    model["N"][:] = mpcgpu.MAX_HORIZON
+    inp32 = device_inputs(inp)
+    s = mpcgpu.Solver(max_agents=n, max_horizon=mpcgpu.MAX_HORIZON, form=mpcgpu.FORM_LDL, fixed_iters=5,
+                      stream=torch.cuda.current_stream().cuda_stream, **(KIN_OPTS if kin else {}))
+    s.set_models(model, np.arange(n))
+    r = s.solve_host(np.arange(n), inp32["x0"], inp32["qd_meas"], inp32["cmd"], inp32["phase"])
+    states = [s.export_state(a, mpcgpu.MAX_HORIZON) for a in range(n)]
+    s.close()
+    assert (r["status"] == mpcgpu.AGENT_MAX_ITER).all()
+    for a in range(n):
+        o = _oracle_kin(model, inp32, a, 5) if kin else _oracle(model, inp32, a, 5)
+        assert np.abs(states[a]["u"] - o["u"]).max() <= 1e-4 * (1.0 + np.abs(o["u"]).max()), a
+        assert torque_close(r["tau"][a], o["tau"]).all(), (a, np.abs(r["tau"][a] - o["tau"]).max())
