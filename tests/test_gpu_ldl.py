@@ -323,3 +323,27 @@ def test_literal_longest_horizon(kin):
         o = _oracle_kin(model, inp32, a, 5) if kin else _oracle(model, inp32, a, 5)
         assert np.abs(states[a]["u"] - o["u"]).max() <= 1e-4 * (1.0 + np.abs(o["u"]).max()), a
         assert torque_close(r["tau"][a], o["tau"]).all(), (a, np.abs(r["tau"][a] - o["tau"]).max())
+
+
+def test_literal_batch_of_some_slots_in_any_order():
+    # a batch that names some of the context's agent slots, out of order, and
+    # one id that is out of range: the rows map to their slots, the bad row is
+    # skipped (status -1, zero outputs)
+    mpcgpu = _lib()
+    n = 10
+    model, inp = agents("uneven", np.arange(n))
+    inp32 = device_inputs(inp)
+    s = mpcgpu.Solver(max_agents=n, max_horizon=20, form=mpcgpu.FORM_LDL, fixed_iters=5,
+                      stream=torch.cuda.current_stream().cuda_stream, **KIN_OPTS)
+    s.set_models(model, np.arange(n))
+    ids = np.array([7, 2, 9, 4])
+    sub = {k: np.ascontiguousarray(v[ids]) for k, v in inp32.items()}
+    bad_ids = np.concatenate([ids, [n + 3]])
+    sub_bad = {k: np.concatenate([v, v[:1]]) for k, v in sub.items()}
+    r = s.solve_host(bad_ids, sub_bad["x0"], sub_bad["qd_meas"], sub_bad["cmd"], sub_bad["phase"])
+    s.close()
+    assert r["status"][-1] == -1 and np.all(r["tau"][-1] == 0.0)
+    assert (r["status"][:-1] == mpcgpu.AGENT_MAX_ITER).all()
+    for row, a in enumerate(ids):
+        o = _oracle_kin(model, inp32, int(a), 5)
+        assert torque_close(r["tau"][row], o["tau"]).all(), (a, np.abs(r["tau"][row] - o["tau"]).max())
