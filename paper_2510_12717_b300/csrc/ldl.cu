@@ -63,6 +63,25 @@ __host__ __device__ constexpr int col_off(int j) {
 __host__ __device__ constexpr int row_off(int i) { return i <= 60 ? i * (i - 1) / 2 : 1770 + (i - 1) * (i - 60) / 2; }
 __host__ __device__ constexpr int row_skip(int i) { return i >= 60 ? 30 : 0; }
 static_assert(col_off(89) == LDL_NL && row_off(90) == LDL_NL, "packed layout size");
+// Stored positions: one float of padding before the second and two before the
+// third 30-wide group of columns (of rows), so that each group starts on a
+// 16-byte boundary and the iterations can stage it by a bulk copy of its own
+// (3107 of the 3108 floats of each layout in use).
+__host__ __device__ constexpr int col_pos(int j) { return col_off(j) + (j >= 30) + (j >= 60); }
+__host__ __device__ constexpr int row_pos(int i) { return row_off(i) + (i >= 30) + (i >= 60); }
+// the three staged parts of a pass: forward part p = columns 30p .. 30p + 29
+// (88 for p = 2), backward part p = rows 89 .. 60, 59 .. 30, 29 .. 1; their
+// start in the layout and the floats copied (rounded up to 16 bytes)
+__host__ __device__ constexpr int fwd_start(int p) { return col_pos(30 * p); }
+__host__ __device__ constexpr int bwd_start(int p) { return p == 0 ? row_pos(60) : p == 1 ? row_pos(30) : 0; }
+__host__ __device__ constexpr int part_floats(int p) { return p == 2 ? 436 : 1336; }
+static_assert(fwd_start(1) % 4 == 0 && fwd_start(2) % 4 == 0 && bwd_start(0) % 4 == 0 && bwd_start(1) % 4 == 0,
+              "staged parts start on 16-byte boundaries");
+static_assert(fwd_start(2) + part_floats(2) <= LDL_ROW - LDL_COL && bwd_start(0) + part_floats(0) <= LDL_ROW - LDL_COL &&
+              col_pos(88) + 1 <= fwd_start(2) + part_floats(2) && row_pos(89) + 59 <= bwd_start(0) + part_floats(0) &&
+              col_pos(59) + 30 <= fwd_start(1) + part_floats(1) && row_pos(59) + 59 <= bwd_start(1) + part_floats(1) &&
+              col_pos(29) + 30 <= fwd_start(0) + part_floats(0) && row_pos(29) + 29 <= bwd_start(2) + part_floats(2),
+              "each part holds its columns (rows) within its layout");
 
 __device__ __forceinline__ bool live_row(const Arena& a, const Batch& b, int row) {
   if (row >= b.n) return false;
@@ -245,8 +264,8 @@ __device__ __forceinline__ void put_row(float* rec, int i, int j0, const float (
   for (int c = 0; c < 30; ++c) {
     const int j = j0 + c;
     if (!DIAG || j < i) {
-      Lr[row_off(i) + j - row_skip(i)] = v[c];
-      Lc[col_off(j) + i - j - 1] = v[c];
+      Lr[row_pos(i) + j - row_skip(i)] = v[c];
+      Lc[col_pos(j) + i - j - 1] = v[c];
     }
   }
 }
@@ -585,16 +604,16 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_ruiz(Arena a, Batch b, SolverPar
 }
 
 // ------------------------------------------------------------------ solves
-// Unit lower solve L w = b of one block, L by columns (shared memory); the
-// lane holds entries lane, lane + 32, lane + 64 (< 90) in e0, e1, e2.
-// KIN: rows 66-68 (the v rows of x_{k+1}) also have entries in the columns
-// 0-29, the three rows of L31 (L3, row-major 3 x 30).
-template <bool KIN>
-__device__ __forceinline__ void fwd_sub(const float* Lc, const float* L3, float& e0, float& e1, float& e2,
-                                        int lane) {
+// Unit lower solve L w = b of one block, part p of L by columns (shared
+// memory, the part's first column at Lc); the lane holds entries lane,
+// lane + 32, lane + 64 (< 90) in e0, e1, e2.  Part 0 is columns 0-29, 1 is
+// 30-59, 2 is 60-88.  KIN: rows 66-68 (the v rows of x_{k+1}) also have
+// entries in columns 0-29, the three rows of L31 (L3, row-major 3 x 30).
+template <int P, bool KIN>
+__device__ __forceinline__ void fwd_part(const float* Lc, const float* L3, float& e0, float& e1, float& e2, int lane) {
 #pragma unroll
-  for (int j = 0; j < NB - 1; ++j) {
-    const int o = col_off(j) - j - 1;             // L(i, j) at o + i, i > j
+  for (int j = 30 * P; j < (P == 2 ? NB - 1 : 30 * P + 30); ++j) {
+    const int o = col_pos(j) - fwd_start(P) - j - 1;   // L(i, j) at o + i, i > j
     const float wj = j < 32 ? __shfl_sync(FULL, e0, j) : (j < 64 ? __shfl_sync(FULL, e1, j - 32)
                                                                  : __shfl_sync(FULL, e2, j - 64));
     // columns j < 30 have no rows 60-89 (the zero block)
@@ -604,32 +623,35 @@ __device__ __forceinline__ void fwd_sub(const float* Lc, const float* L3, float&
     if (KIN && j < 30 && lane >= 2 && lane < 5) e2 = fmaf(-L3[(lane - 2) * 30 + j], wj, e2);
   }
 }
-// Unit upper solve L^T v = w of one block, L by rows (shared memory).
-template <bool KIN>
-__device__ __forceinline__ void bwd_sub(const float* Lr, const float* L3, float& e0, float& e1, float& e2,
-                                        int lane) {
+// Unit upper solve L^T v = w of one block, part p of L by rows (the part's
+// first row at Lr): part 0 is rows 89-60, 1 is 59-30, 2 is 29-1.
+template <int P, bool KIN>
+__device__ __forceinline__ void bwd_part(const float* Lr, const float* L3, float& e0, float& e1, float& e2, int lane) {
 #pragma unroll
-  for (int j = NB - 1; j >= 1; --j) {
-    const int o = row_off(j) - row_skip(j);       // L(j, i) at o + i, i < j (i >= 30 for j >= 60)
+  for (int j = (P == 0 ? NB - 1 : P == 1 ? 59 : 29); j >= (P == 0 ? 60 : P == 1 ? 30 : 1); --j) {
+    const int o = row_pos(j) - bwd_start(P) - row_skip(j);   // L(j, i) at o + i, i < j (i >= 30 for j >= 60)
     const float vj = j < 32 ? __shfl_sync(FULL, e0, j) : (j < 64 ? __shfl_sync(FULL, e1, j - 32)
                                                                  : __shfl_sync(FULL, e2, j - 64));
     if (lane < j && (j < 60 || lane >= 30)) e0 = fmaf(-Lr[o + lane], vj, e0);
-    if (KIN && j >= 66 && j < 69 && lane < 30) e0 = fmaf(-L3[(j - 66) * 30 + lane], vj, e0);
     if (lane + 32 < j) e1 = fmaf(-Lr[o + lane + 32], vj, e1);
     if (lane + 64 < j) e2 = fmaf(-Lr[o + lane + 64], vj, e2);
+    if (KIN && j >= 66 && j < 69 && lane < 30) e0 = fmaf(-L3[(j - 66) * 30 + lane], vj, e0);
   }
 }
 
-// Staging of the factors: the iterations walk the stages forward (item
-// t = k: L_k by columns and G_k) and backward (item t = 2N-1-k: L_k by rows,
-// 1/D_k and G_{k+1}); each item is copied into one of two shared-memory
-// buffers by bulk copies (completion on the buffer's mbarrier) while the
-// previous item computes.  A wait gives up after `limit` polls: the warp then
-// issues nothing more, waits (bounded) for the copies in flight and ends the
-// agent's solve with MPC_AGENT_TIMEOUT.  `dry` (failure-detection test only)
-// arms the first item's barrier with no copy behind it, so that its wait runs
-// out with nothing in flight into that buffer.
-constexpr int BUF_L = 0, BUF_G = 3108, BUF_D = 4008, BUF_L31 = 4104, BUF_FLOATS = 4200;
+// Staging of the factors: the iterations walk the stages forward (items
+// t = 3k + p: part p of L_k by columns, with G_k in part 0) and backward
+// (items t = 3N + 3(N-1-k) + p: part p of L_k by rows, with 1/D_k and G_{k+1}
+// in part 0); each item is copied into one of two shared-memory buffers by
+// bulk copies (completion on the buffer's mbarrier) while the previous item
+// computes.  Parts of about 5.3 KB instead of whole 12.4 KB stage blocks keep
+// the buffers small, so that more warps fit on an SM.  A wait gives up after
+// `limit` polls: the warp then issues nothing more, waits (bounded) for the
+// copies in flight and ends the agent's solve with MPC_AGENT_TIMEOUT.  `dry`
+// (failure-detection test only) arms the first item's barrier with no copy
+// behind it, so that its wait runs out with nothing in flight into that
+// buffer.
+constexpr int BUF_L = 0, BUF_G = 1336, BUF_D = 2236, BUF_L31 = 2332, BUF_FLOATS = 2432;
 struct Stager {
   float* buf[2];
   uint64_t* bar;      // two mbarriers
@@ -640,28 +662,31 @@ struct Stager {
   int limit;
 };
 // KIN: the items carry the three rows of L31 too
+// KIN: part 0 carries the three rows of L31 too
 template <bool KIN>
 __device__ __forceinline__ void stage_issue(Stager& sg, int b, const float* rec0, int N, int t, int lane) {
   if (sg.dead) return;
   __syncwarp();   // every lane is done with the buffer's previous contents
   if (sg.dry) {
     // armed for a copy that is never issued (nothing in flight: not pending)
-    if (lane == 0) mbar_expect_tx(sg.bar + b, (LDL_ROW - LDL_COL) * 4);
+    if (lane == 0) mbar_expect_tx(sg.bar + b, part_floats(0) * 4);
     sg.dry = false;
     return;
   }
   if (lane == 0) {
-    const bool fwd = t < N;
-    const int k = fwd ? t : 2 * N - 1 - t;
+    const bool fwd = t < 3 * N;
+    const int u = fwd ? t : t - 3 * N;
+    const int k = fwd ? u / 3 : N - 1 - u / 3;
+    const int p = u - 3 * (u / 3);
     const float* rec = rec0 + (size_t)k * LDL_REC;
-    const bool g = fwd ? k >= 1 : k + 1 < N;
-    const float* gsrc = fwd ? rec + LDL_G : rec + LDL_REC + LDL_G;   // G_k or G_{k+1}
-    const uint32_t bl = (LDL_ROW - LDL_COL) * 4, bg = 900 * 4, bd = 96 * 4;
-    const uint32_t b3 = KIN ? 96 * 4 : 0;
-    mbar_expect_tx(sg.bar + b, bl + (g ? bg : 0) + (fwd ? 0 : bd) + b3);
-    tma_load_1d(sg.buf[b] + BUF_L, rec + (fwd ? LDL_COL : LDL_ROW), bl, sg.bar + b);
-    if (g) tma_load_1d(sg.buf[b] + BUF_G, gsrc, bg, sg.bar + b);
-    if (!fwd) tma_load_1d(sg.buf[b] + BUF_D, rec + LDL_IND, bd, sg.bar + b);
+    const uint32_t bl = part_floats(p) * 4, bg = 900 * 4, bd = 96 * 4;
+    const bool g = p == 0 && (fwd ? k >= 1 : k + 1 < N);
+    const bool d = p == 0 && !fwd;
+    const uint32_t b3 = KIN && p == 0 ? 96 * 4 : 0;
+    mbar_expect_tx(sg.bar + b, bl + (g ? bg : 0) + (d ? bd : 0) + b3);
+    tma_load_1d(sg.buf[b] + BUF_L, rec + (fwd ? LDL_COL + fwd_start(p) : LDL_ROW + bwd_start(p)), bl, sg.bar + b);
+    if (g) tma_load_1d(sg.buf[b] + BUF_G, fwd ? rec + LDL_G : rec + LDL_REC + LDL_G, bg, sg.bar + b);   // G_k or G_{k+1}
+    if (d) tma_load_1d(sg.buf[b] + BUF_D, rec + LDL_IND, bd, sg.bar + b);
     if (b3) tma_load_1d(sg.buf[b] + BUF_L31, rec + LDL_L31, b3, sg.bar + b);
   }
   sg.pending |= 1u << b;
@@ -876,8 +901,9 @@ __device__ __forceinline__ BIn load_bin(const AgentPtrs& ap, const float* ly, co
 constexpr int W_ADMM = 2 * BUF_FLOATS + 96 + 160 + 32 + 4;   // shared floats of the one warp of a block
 constexpr int W_ADMM_KIN = W_ADMM + KIN_SM + 32;               // ... with the kinematic rows
 // KIN: with the kinematic rows (never with SC: the two are not combined)
+// (ten resident blocks per SM: the register allocation for them spills least)
 template <bool SC, bool KIN>
-__global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverParams prm) {
+__global__ void __launch_bounds__(32, 10) mpc_k_ldl_admm(Arena a, Batch b, SolverParams prm) {
   static_assert(!(SC && KIN), "the kinematic rows run unscaled");
   const int lane = threadIdx.x;
   const int row = blockIdx.x;
@@ -943,7 +969,7 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
   const int every = prm.check_every > 0 ? prm.check_every : 10;
   int status = MPC_AGENT_MAX_ITER_, it = 0;
   LdlRes res{0.f, 0.f, 0.f, 0.f};
-  const int T = 2 * N;                 // staged items per iteration
+  const int T = 6 * N;                 // staged items per iteration (three parts per stage and pass)
   stage_issue<KIN>(sg, 0, rec0, N, 0, lane);
   for (it = 1; it <= max_it && !sg.dead; ++it) {
     const bool last = it == max_it;
@@ -951,7 +977,7 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
     // stage's global inputs are loaded one stage ahead
     FIn fin = load_fin<SC, KIN>(ap, ly, S0, 0, lane);
     for (int k = 0; k < N; ++k) {
-      const int t = k, bcur = t & 1;
+      const int t = 3 * k, bcur = t & 1;
       stage_issue<KIN>(sg, bcur ^ 1, rec0, N, t + 1, lane);
       const FIn f = fin;
       if (k + 1 < N) fin = load_fin<SC, KIN>(ap, ly, S0, k + 1, lane);
@@ -992,7 +1018,16 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
       }
       __syncwarp();
       float e0 = rb[lane], e1 = rb[lane + 32], e2 = lane < NB - 64 ? rb[lane + 64] : 0.f;
-      fwd_sub<KIN>(buf + BUF_L, buf + BUF_L31, e0, e1, e2, lane);
+      fwd_part<0, KIN>(buf + BUF_L, buf + BUF_L31, e0, e1, e2, lane);
+      // parts 1 and 2 (the last stage's part 2 issues the backward pass's first item)
+      stage_issue<KIN>(sg, bcur, rec0, N, t + 2, lane);
+      stage_wait(sg, bcur ^ 1);
+      if (sg.dead) break;
+      fwd_part<1, KIN>(sg.buf[bcur ^ 1] + BUF_L, nullptr, e0, e1, e2, lane);
+      stage_issue<KIN>(sg, bcur ^ 1, rec0, N, t + 3, lane);
+      stage_wait(sg, bcur);
+      if (sg.dead) break;
+      fwd_part<2, KIN>(sg.buf[bcur] + BUF_L, nullptr, e0, e1, e2, lane);
       lw[k * LDL_W + lane] = e0;
       lw[k * LDL_W + lane + 32] = e1;
       if (lane < NB - 64) lw[k * LDL_W + lane + 64] = e2;
@@ -1007,10 +1042,8 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
     // then the stage's update; inputs one stage ahead
     BIn bin = load_bin<SC, KIN>(ap, ly, lw, S0, N - 1, lane);
     for (int k = N - 1; k >= 0; --k) {
-      const int t = 2 * N - 1 - k, bcur = t & 1;
-      // the next item: this iteration's next stage, or the next iteration's first
-      if (t + 1 < T) stage_issue<KIN>(sg, bcur ^ 1, rec0, N, t + 1, lane);
-      else if (!last) stage_issue<KIN>(sg, bcur ^ 1, rec0, N, 0, lane);
+      const int t = 3 * N + 3 * (N - 1 - k), bcur = t & 1;
+      stage_issue<KIN>(sg, bcur ^ 1, rec0, N, t + 1, lane);
       const BIn q = bin;
       if (k >= 1) bin = load_bin<SC, KIN>(ap, ly, lw, S0, k - 1, lane);
       stage_wait(sg, bcur);
@@ -1029,7 +1062,18 @@ __global__ void __launch_bounds__(32) mpc_k_ldl_admm(Arena a, Batch b, SolverPar
       }
       __syncwarp();
       float e0 = rb[lane], e1 = rb[lane + 32], e2 = lane < NB - 64 ? rb[lane + 64] : 0.f;
-      bwd_sub<KIN>(buf + BUF_L, buf + BUF_L31, e0, e1, e2, lane);
+      bwd_part<0, KIN>(buf + BUF_L, buf + BUF_L31, e0, e1, e2, lane);
+      // parts 1 and 2; the next item: this iteration's next stage, or the
+      // next iteration's first
+      stage_issue<KIN>(sg, bcur, rec0, N, t + 2, lane);
+      stage_wait(sg, bcur ^ 1);
+      if (sg.dead) break;
+      bwd_part<1, KIN>(sg.buf[bcur ^ 1] + BUF_L, nullptr, e0, e1, e2, lane);
+      if (t + 3 < T) stage_issue<KIN>(sg, bcur ^ 1, rec0, N, t + 3, lane);
+      else if (!last) stage_issue<KIN>(sg, bcur ^ 1, rec0, N, 0, lane);
+      stage_wait(sg, bcur);
+      if (sg.dead) break;
+      bwd_part<2, KIN>(sg.buf[bcur] + BUF_L, nullptr, e0, e1, e2, lane);
       __syncwarp();
       rb[lane] = e0;
       rb[lane + 32] = e1;
@@ -1135,8 +1179,8 @@ cudaError_t launch_ldl(const Arena& a, const Batch& b, const SolverParams& prm, 
   int dev = 0;
   cudaGetDevice(&dev);
   if (configured != dev) {
-    // the iteration kernel's one-warp blocks hold about 35 KB of shared
-    // memory: it asks for the largest shared-memory carveout, so that six fit
+    // the iteration kernel's one-warp blocks hold about 21 KB of shared
+    // memory: it asks for the largest shared-memory carveout, so that ten fit
     // on an SM
     cudaError_t e = set_smem(mpc_k_ldl_factor<false>, F_FLOATS, false);
     if (e == cudaSuccess) e = set_smem(mpc_k_ldl_factor<true>, F_FLOATS + F_KIN, false);
