@@ -5,7 +5,7 @@ ADMM with exact dynamics in the x-update (oracle/admm.py).
 Cold start (f_init), fixed rho, no polish: after N_QP iterations both sides
 hold the same iterate (u, x, the row slacks w and multipliers y), not the
 QP's optimum.  Bars: the iterate within 1e-4 of its own scale (FP32 Riccati
-factors; the literal form meets the same bar), torques within the north-star
+factors; the literal form meets the same bar), torques within the torque
 tolerance.
 """
 import numpy as np

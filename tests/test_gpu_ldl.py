@@ -8,7 +8,7 @@ The literal iteration is compared iterate for iterate: after a fixed number
 of iterations N_QP from f_init both sides hold the same ADMM iterate, not the
 QP's optimum (the paper's fixed-N_QP mode); with and without the Ruiz
 equilibration (f_Ruiz), computed on each side from its own data.  Bars: torques within the
-spec tolerance (1e-4 N m + 1e-3 |tau|); the primal iterate within 1e-4
+torque tolerance (1e-4 N m + 1e-3 |tau|); the primal iterate within 1e-4
 of its own scale (FP32 factors of a KKT matrix with entries from 1e-2 to
 1e3: measured 1e-6); in the converged mode the iteration count within one
 residual-check period of the oracle's, where the stopping test is met by a
